@@ -1,0 +1,200 @@
+/*
+ * mhfd.h - C ABI of the GB300 (sm_103a) multi-scale histologic feature
+ * detector (MHFD, arXiv 2108.12050).
+ *
+ * The detector computes, for one grey-level image I (H x W, row pitch in
+ * bytes, uint8 / uint16 / float32, resident in device memory):
+ *
+ *   1. the histogram stretch of §3 (Algorithm 1, first step): lo/hi are the
+ *      k-th smallest and (N-1-k)-th smallest pixel values, k = floor(clip*N),
+ *      N = H*W, and I' = clamp((I - lo)/(hi - lo), 0, 1);
+ *   2. the Gaussian scale-space stack of §2.2 over the linear ladder
+ *      t_i = t_min + (i-1)(t_max - t_min)/n, i = 1..n+1: each level is the
+ *      separable convolution of I' with the sampled Gaussian of variance t_i^2,
+ *      truncated at R_i = ceil(truncate * t_i), normalised, reflect boundary;
+ *   3. the DoG responses of Eq. 2: D_i = t_i (L_{i+1} - L_i), i = 1..n;
+ *   4. local maxima (Eq. 3): either the paper's rule (M = max_i D_i, first
+ *      argmax i_hat; keep when M > threshold and M equals its 3x3 max-pool,
+ *      out-of-image neighbours ignored) or 3x3x3 scale-space maxima;
+ *   5. greedy overlap pruning of the blobs (radius sqrt(2) t_i): visited by
+ *      radius, then response (both descending), then row-major position; a
+ *      blob is dropped when a kept blob covers more than `overlap` of the
+ *      smaller circle; overlap >= 1 keeps every candidate;
+ *   6. the focus score of §3 / Algorithm 1: the number of features kept.
+ *
+ * Every step runs in this library's own CUDA kernels on the caller's stream;
+ * there is no CPU fallback.  All calls return an int status: MHFD_OK (0), a
+ * negative error code, or the positive warning MHFD_WARN_OVERFLOW.  The text of
+ * the last error of the calling thread is available from mhfd_last_error().
+ */
+#ifndef MHFD_H
+#define MHFD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MHFD_OK 0
+#define MHFD_WARN_OVERFLOW 1        /* candidate list truncated; true count reported */
+#define MHFD_ERR_INVALID_ARG (-1)   /* bad size, pointer, ladder or parameter */
+#define MHFD_ERR_UNSUPPORTED (-2)   /* ladder too wide for the on-chip tile */
+#define MHFD_ERR_OOM (-3)           /* device or pinned allocation failed */
+#define MHFD_ERR_CUDA (-4)          /* a CUDA runtime/driver call failed */
+#define MHFD_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
+#define MHFD_ERR_JIT (-6)           /* run-time compilation of the kernel failed */
+
+typedef enum { MHFD_U8 = 0, MHFD_U16 = 1, MHFD_F32 = 2 } mhfd_dtype;
+typedef enum { MHFD_NMS_PAPER = 0, MHFD_NMS_LOCAL26 = 1 } mhfd_nms;
+
+typedef struct mhfd_detector mhfd_detector;  /* opaque, owned by the library */
+
+/* Detector configuration (Algorithm 1's inputs n, min_t, max_t plus the
+ * threshold, pruning and stretch parameters).  Fill with
+ * mhfd_default_params() and override fields. */
+typedef struct {
+    int32_t n;              /* DoG layers; n+1 Gaussian scales; 1 <= n <= 63 */
+    double t_min, t_max;    /* ladder ends, 0 < t_min < t_max */
+    const double *sigmas;   /* optional explicit ladder of n+1 increasing scales
+                               (host memory, read during create); overrides
+                               t_min/t_max when non-NULL */
+    float threshold;        /* a feature needs response > threshold (finite) */
+    float overlap;          /* prune fraction in [0, 1]; >= 1 disables pruning */
+    int32_t nms;            /* mhfd_nms */
+    float truncate;         /* kernel radius R = ceil(truncate * t); > 0 */
+    double clip_frac;       /* stretch saturation per end, 0 <= clip < 0.5 */
+    int64_t max_candidates; /* capacity of the candidate and blob lists */
+    int32_t device;         /* CUDA device ordinal; -1 = the current device */
+    int32_t keep_candidates;/* 1: also expose the pre-prune candidate list */
+    int32_t tile_override;  /* 0 = built-in tile choice; k > 0 = row k-1 of
+                               mhfd_tile_configs() (autotuner use) */
+    int32_t timing;         /* 1: record CUDA events around the kernels of each
+                               detection (read with mhfd_last_timing) */
+} mhfd_params;
+
+/* A detected feature.  scale_idx is the 0-based DoG layer i-1; sigma = t_i,
+ * radius = sqrt(2) t_i. */
+typedef struct {
+    int32_t x, y, scale_idx;
+    float sigma, radius, response;
+} mhfd_blob;
+
+/* Results of one detection, valid until the next detect on the detector. */
+typedef struct {
+    const mhfd_blob *blobs;       /* kept features (detector-owned pinned host
+                                     memory), in tile order */
+    int64_t n_blobs;
+    const mhfd_blob *candidates;  /* pre-prune list if keep_candidates, else NULL */
+    int64_t n_candidates;         /* candidates stored (<= max_candidates) */
+    int64_t n_candidates_true;    /* candidates found (> stored on overflow) */
+    float focus_score;            /* = n_blobs, the paper's criterion */
+    float mean_response;          /* mean response of the kept features */
+    int32_t per_scale[64];        /* kept features per scale index */
+    float lo, hi;                 /* stretch bounds (in input units) */
+    int32_t status;               /* MHFD_OK or MHFD_WARN_OVERFLOW */
+} mhfd_result;
+
+/* Writes the default parameters: n = 10, t in [1, 10], threshold 0.1,
+ * overlap 0.5, paper NMS, truncate 4, clip 0.00175, 1<<20 candidates,
+ * current device. */
+void mhfd_default_params(mhfd_params *p);
+
+/* Creates a detector.  Validates the parameters, builds the ladder and the
+ * kernel taps, and compiles (or loads from the on-disk cache) the fused
+ * kernel specialised for the ladder's radii; this may take seconds the first
+ * time a ladder is used.  *out receives the handle.  Device scratch grows on
+ * first use with a larger image.  Errors: INVALID_ARG, UNSUPPORTED, JIT,
+ * CUDA, OOM. */
+int mhfd_create_detector(const mhfd_params *p, mhfd_detector **out);
+
+/* Releases every resource of the detector (synchronises its last work). */
+int mhfd_destroy_detector(mhfd_detector *det);
+
+/* Enqueues one detection on `stream` (a cudaStream_t; NULL = legacy default
+ * stream).  d_img is device memory owned by the caller, H rows of W pixels
+ * of `dtype`, rows `pitch_bytes` apart (>= W * element size), and must stay
+ * alive and unchanged until the stream work completes.  Nothing is
+ * synchronised on the host.  Results are read with mhfd_result_wait.
+ * One detector must not be used from two streams at once.
+ * Errors: INVALID_ARG (H, W < 1; pitch too small; NULL image), CUDA, OOM. */
+int mhfd_detect(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H, int32_t W,
+                size_t pitch_bytes, void *stream);
+
+/* Blocks until the last detection enqueued on `det` has finished and fills
+ * *out.  Returns the detection's status (MHFD_OK or MHFD_WARN_OVERFLOW) or an
+ * error. */
+int mhfd_result_wait(mhfd_detector *det, mhfd_result *out);
+
+/* End-to-end convenience: h_img is HOST memory (pinned or pageable); the
+ * image is copied to detector-owned device memory on `stream`, detected and
+ * the results are waited for and written to *out.  Same errors as above. */
+int mhfd_detect_host(mhfd_detector *det, const void *h_img, int32_t dtype, int32_t H, int32_t W,
+                     size_t pitch_bytes, void *stream, mhfd_result *out);
+
+/* Same detection as mhfd_detect, computed by the unfused "plain" pipeline:
+ * one blur kernel pair per Gaussian level writing every L_i to device
+ * memory, then a DoG/argmax kernel, an NMS kernel and the same pruning.  It
+ * is the comparison baseline of the fused kernel.  Results through
+ * mhfd_result_wait. */
+int mhfd_detect_plain(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H, int32_t W,
+                      size_t pitch_bytes, void *stream);
+
+/* Test and inspection entry point: runs the fused kernel in its stack-storing
+ * variant and writes the responses D (n planes of H x W float32, plane i =
+ * layer i), the per-pixel maximum M (H x W float32) and its first argmax
+ * (H x W int32) to caller-owned device buffers (any of them may be NULL).
+ * Also leaves a full detection for mhfd_result_wait. */
+int mhfd_debug_stack(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H, int32_t W,
+                     size_t pitch_bytes, void *stream, float *d_D, float *d_M, int32_t *d_arg);
+
+/* Runs only the overlap prune (step 5) on a caller-supplied candidate list
+ * in device memory: d_x, d_y, d_i (int32 scale index < n), d_resp (float32),
+ * n_cand entries, positions inside an H x W image (entries outside are
+ * clamped into it).  d_keep (uint8, device) receives 1 for kept candidates.
+ * Asynchronous on `stream`. */
+int mhfd_prune(mhfd_detector *det, const int32_t *d_x, const int32_t *d_y, const int32_t *d_i,
+               const float *d_resp, int64_t n_cand, int32_t H, int32_t W, uint8_t *d_keep,
+               void *stream);
+
+/* Tile configurations the fused kernel can be specialised with for the
+ * ladder of `p` (autotuner menu): returns their count; if `desc` is not NULL
+ * writes up to `cap` rows of five int32 (tile width and height including the
+ * one-pixel NMS border, rows per step, threads per block, level groups).
+ * Row k is selected by params.tile_override = k + 1.  Host only. */
+int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap);
+
+/* The configuration mhfd_create_detector would use for `p` (same five
+ * fields as above).  Host only. */
+int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5);
+
+/* Compiles the fused kernel for the ladder and tile of `p` (store = 1: the
+ * stack-storing variant of mhfd_debug_stack) into the on-disk kernel cache
+ * without using a GPU, so that a later mhfd_create_detector starts at once.
+ * The cache directory is $MHFD_JIT_CACHE, else `_jit_cache` next to the
+ * library.  Errors: INVALID_ARG, UNSUPPORTED, JIT. */
+int mhfd_precompile(const mhfd_params *p, int32_t store);
+
+/* Kernel timing of the last mhfd_detect / mhfd_detect_plain on `det` (waits
+ * for it): writes the device time in milliseconds of the fused kernel (or of
+ * the plain path's blur/DoG/NMS kernels) and of the whole detection, measured
+ * with CUDA events recorded on the launching stream.  Needs params.timing. */
+int mhfd_last_timing(mhfd_detector *det, float *ms_detect_kernel, float *ms_total);
+
+/* Measures the FP32 FFMA issue peak of the current device with a register-
+ * only probe kernel: returns FFMA lane-operations per second (one FFMA = 1)
+ * in *ops_per_s, timed with CUDA events on `stream`. */
+int mhfd_probe_ffma_peak(void *stream, double *ops_per_s);
+
+/* Last error message of the calling thread ("" if none). */
+const char *mhfd_last_error(void);
+
+/* Library version string. */
+const char *mhfd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHFD_H */

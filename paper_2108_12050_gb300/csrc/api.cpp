@@ -1,0 +1,633 @@
+// C ABI of the detector (include/mhfd.h): parameter validation, the ladder
+// and taps (§2.2), device scratch, and the asynchronous pipeline
+//   stretch select (§3) -> fused detection kernel (§2.2, Eq. 2, Eq. 3)
+//   -> tile-ordered gather -> overlap prune -> compaction into pinned memory.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace mhfd {
+
+thread_local std::string t_err;
+
+void set_error(const std::string &msg) { t_err = msg; }
+
+int fail(int code, const std::string &msg) {
+    t_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    const int code = (e == cudaErrorMemoryAllocation) ? MHFD_ERR_OOM : MHFD_ERR_CUDA;
+    return fail(code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace mhfd
+
+using namespace mhfd;
+
+struct mhfd_detector {
+    mhfd_params p{};
+    int device = 0;
+    int n = 0;                   // DoG layers
+    std::vector<double> t;       // n+1 Gaussian scales
+    std::vector<int> R;          // their radii
+    std::vector<float> taps;     // level l: g_l[0..R_l] at tapoff[l]
+    std::vector<int> tapoff;
+    std::vector<float> tsc;      // t_l as f32 (DoG factor)
+    std::vector<double> radius;  // blob radius per DoG layer, sqrt(2) t_i
+    double radius_max = 0.0;
+    TileConfig cfg;
+    Variant *var = nullptr;
+    Variant *var_store = nullptr;
+    std::vector<uint64_t> params;  // by-value parameter block of the fused kernel
+
+    // fixed device buffers
+    SelState *sel = nullptr;
+    MhfdStretch *st = nullptr;
+    Counters *cnt = nullptr;
+    double *d_radius = nullptr;
+    float *d_sigma = nullptr, *d_radius_f = nullptr, *d_taps = nullptr, *d_tsc = nullptr;
+    int *d_tapoff = nullptr;
+    int *block_tmp = nullptr;
+    double *block_sum = nullptr;
+    long long cap = 0;           // candidate list capacity
+    MhfdCand *cand = nullptr;
+    // grown with the image
+    int cap_tile = 0;
+    size_t tiles_cap = 0;
+    int *tile_count = nullptr, *tile_off = nullptr;
+    MhfdCand *stage = nullptr;
+    size_t stage_cap = 0;        // entries
+    PruneBuffers pb;
+    // plain path scratch
+    size_t plain_px = 0;
+    float *pI = nullptr, *pT = nullptr, *pL = nullptr, *pM = nullptr, *pD = nullptr;
+    int *pA = nullptr;
+    // host end-to-end copy of the image
+    void *d_img_copy = nullptr;
+    size_t img_copy_bytes = 0;
+    // pinned, device-mapped results
+    HostResult *h_res = nullptr, *h_res_dev = nullptr;
+    mhfd_blob *h_blobs = nullptr, *h_blobs_dev = nullptr;
+    mhfd_blob *h_cands = nullptr, *h_cands_dev = nullptr;
+    cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_k0 = nullptr, ev_k1 = nullptr,
+                ev_end = nullptr;
+    bool pending = false;
+    bool timed = false;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int elem_size(int dtype) { return dtype == MHFD_U8 ? 1 : (dtype == MHFD_U16 ? 2 : 4); }
+
+int build_ladder(const mhfd_params &p, std::vector<double> *t, std::vector<int> *R) {
+    if (p.n < 1 || p.n > 63) return fail(MHFD_ERR_INVALID_ARG, "n must be in [1, 63]");
+    if (!(p.truncate > 0.0f) || !std::isfinite(p.truncate))
+        return fail(MHFD_ERR_INVALID_ARG, "truncate must be positive");
+    t->assign(p.n + 1, 0.0);
+    if (p.sigmas) {
+        for (int i = 0; i <= p.n; ++i) {
+            (*t)[i] = p.sigmas[i];
+            if (!(p.sigmas[i] > 0.0) || !std::isfinite(p.sigmas[i]))
+                return fail(MHFD_ERR_INVALID_ARG, "sigmas must be positive and finite");
+            if (i && !(p.sigmas[i] > p.sigmas[i - 1]))
+                return fail(MHFD_ERR_INVALID_ARG, "sigmas must increase");
+        }
+    } else {
+        if (!(p.t_min > 0.0) || !(p.t_max > p.t_min) || !std::isfinite(p.t_max))
+            return fail(MHFD_ERR_INVALID_ARG, "need 0 < t_min < t_max");
+        // §2.2: dt = (max_t - min_t)/n, t_i = min_t + (i-1) dt, i = 1..n+1
+        const double dt = (p.t_max - p.t_min) / (double)p.n;
+        for (int i = 1; i <= p.n + 1; ++i) (*t)[i - 1] = p.t_min + (double)(i - 1) * dt;
+    }
+    R->assign(p.n + 1, 0);
+    for (int i = 0; i <= p.n; ++i) {
+        const double r = std::ceil((double)p.truncate * (*t)[i]);
+        if (r < 1.0 || r > 255.0) return fail(MHFD_ERR_UNSUPPORTED, "kernel radius out of range [1, 255]");
+        (*R)[i] = (int)r;
+    }
+    return MHFD_OK;
+}
+
+int validate_params(const mhfd_params &p) {
+    if (!std::isfinite(p.threshold)) return fail(MHFD_ERR_INVALID_ARG, "threshold must be finite");
+    if (!(p.overlap >= 0.0f)) return fail(MHFD_ERR_INVALID_ARG, "overlap must be >= 0");
+    if (!(p.clip_frac >= 0.0 && p.clip_frac < 0.5))
+        return fail(MHFD_ERR_INVALID_ARG, "clip_frac must be in [0, 0.5)");
+    if (p.nms != MHFD_NMS_PAPER && p.nms != MHFD_NMS_LOCAL26)
+        return fail(MHFD_ERR_INVALID_ARG, "nms must be MHFD_NMS_PAPER or MHFD_NMS_LOCAL26");
+    if (p.max_candidates < 1 || p.max_candidates > (1ll << 30))
+        return fail(MHFD_ERR_INVALID_ARG, "max_candidates must be in [1, 2^30]");
+    return MHFD_OK;
+}
+
+template <class T>
+int dalloc(T **ptr, size_t count) {
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    MHFD_CUDA(cudaMalloc(reinterpret_cast<void **>(ptr), count * sizeof(T)));
+    return MHFD_OK;
+}
+
+int tiles_of(const mhfd_detector *d, int H, int W, int *tx, int *ty) {
+    const int TX = d->cfg.tx2 - 2, TY = d->cfg.ty2 - 2;
+    *tx = (W + TX - 1) / TX;
+    *ty = (H + TY - 1) / TY;
+    return (*tx) * (*ty);
+}
+
+int ensure_image_capacity(mhfd_detector *d, int H, int W, bool plain) {
+    int tx, ty;
+    const size_t n_tiles_fused = (size_t)tiles_of(d, H, W, &tx, &ty);
+    const size_t n_tiles_plain = (size_t)((W + 15) / 16) * ((H + 15) / 16);
+    const size_t cap_tile_plain = d->p.nms == MHFD_NMS_PAPER ? 256 : 1024;
+    const size_t need_tiles = n_tiles_fused > n_tiles_plain ? n_tiles_fused : n_tiles_plain;
+    size_t need_stage = n_tiles_fused * (size_t)d->cap_tile;
+    if (n_tiles_plain * cap_tile_plain > need_stage) need_stage = n_tiles_plain * cap_tile_plain;
+    int rc;
+    if (need_tiles > d->tiles_cap) {
+        if ((rc = dalloc(&d->tile_count, need_tiles)) || (rc = dalloc(&d->tile_off, need_tiles))) return rc;
+        d->tiles_cap = need_tiles;
+    }
+    if (need_stage > d->stage_cap) {
+        if ((rc = dalloc(&d->stage, need_stage))) return rc;
+        d->stage_cap = need_stage;
+    }
+    const int cs = (int)std::ceil(2.0 * d->radius_max) + 1;
+    const size_t ncells = (size_t)((W + cs - 1) / cs) * ((H + cs - 1) / cs) + 1;
+    if (ncells > d->pb.ncells_cap) {
+        if ((rc = dalloc(&d->pb.cell_cnt, ncells)) || (rc = dalloc(&d->pb.cell_start, ncells)))
+            return rc;
+        d->pb.ncells_cap = ncells;
+    }
+    if (plain) {
+        const size_t px = (size_t)H * W;
+        if (px > d->plain_px) {
+            const size_t nl = d->R.size();
+            if ((rc = dalloc(&d->pI, px)) || (rc = dalloc(&d->pT, px)) ||
+                (rc = dalloc(&d->pL, px * nl)) || (rc = dalloc(&d->pM, px)) ||
+                (rc = dalloc(&d->pA, px)) ||
+                (rc = dalloc(&d->pD, d->p.nms == MHFD_NMS_LOCAL26 ? px * (nl - 1) : 1)))
+                return rc;
+            d->plain_px = px;
+        }
+    }
+    return MHFD_OK;
+}
+
+int check_image(const void *img, int dtype, int H, int W, size_t pitch) {
+    if (!img) return fail(MHFD_ERR_INVALID_ARG, "image pointer is NULL");
+    if (dtype != MHFD_U8 && dtype != MHFD_U16 && dtype != MHFD_F32)
+        return fail(MHFD_ERR_INVALID_ARG, "dtype must be MHFD_U8, MHFD_U16 or MHFD_F32");
+    if (H < 1 || W < 1) return fail(MHFD_ERR_INVALID_ARG, "H and W must be >= 1");
+    if ((long long)H * (long long)W > 2147483647ll) return fail(MHFD_ERR_INVALID_ARG, "H*W must be < 2^31");
+    if (pitch < (size_t)W * elem_size(dtype)) return fail(MHFD_ERR_INVALID_ARG, "pitch smaller than a row");
+    if (pitch % elem_size(dtype)) return fail(MHFD_ERR_INVALID_ARG, "pitch not a multiple of the element size");
+    return MHFD_OK;
+}
+
+long long clip_rank(const mhfd_detector *d, int H, int W) {
+    const double N = (double)H * (double)W;
+    return (long long)std::floor(d->p.clip_frac * N);
+}
+
+// fill and launch the fused kernel
+int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H, int W,
+                 size_t pitch, cudaStream_t s, float *d_D, float *d_M, int *d_A) {
+    int tx, ty;
+    const int n_tiles = tiles_of(d, H, W, &tx, &ty);
+    const size_t nl = d->R.size();
+    const size_t need = sizeof(MhfdKHeader) + 4 * (nl + d->taps.size());
+    if ((size_t)v->param_bytes < need || v->ntaps != (int)d->taps.size())
+        return fail(MHFD_ERR_JIT, "kernel parameter layout mismatch");
+    d->params.assign((v->param_bytes + 7) / 8 + 1, 0);
+    char *pb = reinterpret_cast<char *>(d->params.data());
+    MhfdKHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.img = img;
+    h.st = d->st;
+    h.stage = d->stage;
+    h.tile_count = d->tile_count;
+    h.stack_out = d_D;
+    h.m_out = d_M;
+    h.arg_out = d_A;
+    h.pitch = (long long)pitch;
+    h.plane = (long long)H * W;
+    h.H = H;
+    h.W = W;
+    h.dtype = dtype;
+    h.tiles_x = tx;
+    h.cap_tile = d->cap_tile;
+    h.thr = d->p.threshold;
+    std::memcpy(pb, &h, sizeof(h));
+    std::memcpy(pb + sizeof(h), d->tsc.data(), 4 * nl);
+    std::memcpy(pb + sizeof(h) + 4 * nl, d->taps.data(), 4 * d->taps.size());
+    void *args[] = {pb};
+    const CUresult r = drv().launchKernel(v->fn, (unsigned)n_tiles, 1, 1, (unsigned)v->cfg.nt, 1,
+                                          1, (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
+    if (r != CUDA_SUCCESS) {
+        const char *es = nullptr;
+        drv().getErrorString(r, &es);
+        return fail(MHFD_ERR_CUDA, std::string("cuLaunchKernel: ") + (es ? es : "?"));
+    }
+    return MHFD_OK;
+}
+
+int finish_pipeline(mhfd_detector *d, int n_tiles, int cap_tile, int H, int W, cudaStream_t s) {
+    int rc = enqueue_gather(d->tile_count, d->stage, n_tiles, cap_tile, d->cap, d->tile_off,
+                            d->cand, d->cnt, s);
+    if (rc) return rc;
+    rc = enqueue_prune(d->cand, d->cnt, d->cap, H, W, d->d_radius, d->radius_max,
+                       (double)d->p.overlap, &d->pb, s);
+    if (rc) return rc;
+    rc = enqueue_output(d->cand, d->pb.state, d->cnt, d->cap, d->d_sigma, d->d_radius_f, 1,
+                        d->h_res_dev, d->h_blobs_dev, d->p.keep_candidates ? d->h_cands_dev : nullptr,
+                        d->st, d->block_tmp, d->block_sum, s);
+    if (rc) return rc;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_end, s));
+    MHFD_CUDA(cudaEventRecord(d->ev_done, s));
+    d->pending = true;
+    return MHFD_OK;
+}
+
+int detect_impl(mhfd_detector *d, const void *img, int dtype, int H, int W, size_t pitch,
+                cudaStream_t s, bool store, float *d_D, float *d_M, int *d_A) {
+    int rc = check_image(img, dtype, H, W, pitch);
+    if (rc) return rc;
+    DeviceGuard g(d->device);
+    Variant *v = d->var;
+    if (store) {
+        if (!d->var_store) {
+            rc = get_variant(d->R, d->p.nms, 1, d->cfg, &d->var_store);
+            if (rc) return rc;
+        }
+        v = d->var_store;
+    }
+    if ((rc = ensure_image_capacity(d, H, W, false))) return rc;
+    d->timed = d->p.timing != 0;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_t0, s));
+    rc = enqueue_stretch(img, dtype, H, W, (long long)pitch, clip_rank(d, H, W), d->sel, d->st, s);
+    if (rc) return rc;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k0, s));
+    if ((rc = launch_fused(d, v, img, dtype, H, W, pitch, s, d_D, d_M, d_A))) return rc;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k1, s));
+    int tx, ty;
+    const int n_tiles = tiles_of(d, H, W, &tx, &ty);
+    return finish_pipeline(d, n_tiles, d->cap_tile, H, W, s);
+}
+
+int pinned_alloc(void **h, void **dev, size_t bytes) {
+    MHFD_CUDA(cudaHostAlloc(h, bytes ? bytes : 1, cudaHostAllocMapped | cudaHostAllocPortable));
+    MHFD_CUDA(cudaHostGetDevicePointer(dev, *h, 0));
+    return MHFD_OK;
+}
+
+void release(mhfd_detector *d) {
+    DeviceGuard g(d->device);
+    if (d->pending && d->ev_done) cudaEventSynchronize(d->ev_done);
+    void *dev_ptrs[] = {d->sel, d->st, d->cnt, d->d_radius, d->d_sigma, d->d_radius_f, d->d_taps,
+                        d->d_tsc, d->d_tapoff, d->block_tmp, d->block_sum, d->cand, d->tile_count,
+                        d->tile_off, d->stage, d->pb.cell_cnt, d->pb.cell_start, d->pb.cell_items,
+                        d->pb.state, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
+    for (void *p : dev_ptrs)
+        if (p) cudaFree(p);
+    if (d->h_res) cudaFreeHost(d->h_res);
+    if (d->h_blobs) cudaFreeHost(d->h_blobs);
+    if (d->h_cands) cudaFreeHost(d->h_cands);
+    cudaEvent_t evs[] = {d->ev_done, d->ev_t0, d->ev_k0, d->ev_k1, d->ev_end};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    delete d;
+}
+
+int resolve_tile(const std::vector<int> &R, const mhfd_params &p, TileConfig *cfg) {
+    std::string why;
+    if (p.tile_override > 0) {
+        const std::vector<TileConfig> menu = tile_menu(R, p.nms);
+        if (p.tile_override > (int)menu.size()) return fail(MHFD_ERR_INVALID_ARG, "tile_override out of range");
+        *cfg = menu[p.tile_override - 1];
+        return MHFD_OK;
+    }
+    if (!choose_tile(R, p.nms, cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+    return MHFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mhfd_default_params(mhfd_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n = 10;
+    p->t_min = 1.0;
+    p->t_max = 10.0;
+    p->sigmas = nullptr;
+    p->threshold = 0.1f;
+    p->overlap = 0.5f;
+    p->nms = MHFD_NMS_PAPER;
+    p->truncate = 4.0f;
+    p->clip_frac = 0.00175;
+    p->max_candidates = 1 << 20;
+    p->device = -1;
+    p->keep_candidates = 0;
+    p->tile_override = 0;
+    p->timing = 0;
+}
+
+const char *mhfd_last_error(void) { return mhfd::t_err.c_str(); }
+
+const char *mhfd_version(void) { return "mhfd-gb300 0.1 (sm_103a)"; }
+
+int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
+    if (!pp || !out) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    int rc = validate_params(*pp);
+    if (rc) return rc;
+    mhfd_detector *d = new mhfd_detector();
+    d->p = *pp;
+    d->p.sigmas = nullptr;  // copied below; the caller's array is not kept
+    if ((rc = build_ladder(*pp, &d->t, &d->R))) {
+        delete d;
+        return rc;
+    }
+    d->n = pp->n;
+    if (pp->device >= 0) {
+        d->device = pp->device;
+    } else if (cudaGetDevice(&d->device) != cudaSuccess) {
+        delete d;
+        return fail(MHFD_ERR_CUDA, "no CUDA device");
+    }
+    DeviceGuard g(d->device);
+    const int nl = d->n + 1;
+    // §2.2: sampled Gaussian of variance t^2 on k = -R..R, normalised in FP64
+    d->tapoff.assign(nl + 1, 0);
+    for (int l = 0; l < nl; ++l) {
+        const double t = d->t[l];
+        const int R = d->R[l];
+        std::vector<double> g(2 * R + 1);
+        double sum = 0.0;
+        for (int k = -R; k <= R; ++k) {
+            g[k + R] = std::exp(-((double)k * (double)k) / (2.0 * t * t));
+            sum += g[k + R];
+        }
+        d->tapoff[l + 1] = d->tapoff[l] + R + 1;
+        for (int k = 0; k <= R; ++k) d->taps.push_back((float)(g[k + R] / sum));
+        d->tsc.push_back((float)t);
+    }
+    for (int i = 0; i < d->n; ++i) d->radius.push_back(std::sqrt(2.0) * d->t[i]);
+    d->radius_max = d->radius[d->n - 1];
+    if ((rc = resolve_tile(d->R, d->p, &d->cfg))) {
+        delete d;
+        return rc;
+    }
+    const int TXY = (d->cfg.tx2 - 2) * (d->cfg.ty2 - 2);
+    d->cap_tile = d->p.nms == MHFD_NMS_PAPER ? (TXY + 1) / 2 : TXY;
+    d->cap = d->p.max_candidates;
+    if ((rc = get_variant(d->R, d->p.nms, 0, d->cfg, &d->var))) {
+        delete d;
+        return rc;
+    }
+    std::vector<float> sig(64, 0.0f), radf(64, 0.0f);
+    std::vector<double> rad(64, 0.0);
+    for (int i = 0; i < d->n; ++i) {
+        sig[i] = (float)d->t[i];
+        radf[i] = (float)d->radius[i];
+        rad[i] = d->radius[i];
+    }
+    if ((rc = dalloc(&d->sel, 1)) || (rc = dalloc(&d->st, 1)) || (rc = dalloc(&d->cnt, 1)) ||
+        (rc = dalloc(&d->d_radius, 64)) || (rc = dalloc(&d->d_sigma, 64)) ||
+        (rc = dalloc(&d->d_radius_f, 64)) || (rc = dalloc(&d->d_taps, d->taps.size())) ||
+        (rc = dalloc(&d->d_tsc, nl)) || (rc = dalloc(&d->d_tapoff, nl + 1)) ||
+        (rc = dalloc(&d->block_tmp, 256 + 64)) || (rc = dalloc(&d->block_sum, 256 + 1)) ||
+        (rc = dalloc(&d->cand, (size_t)d->cap)) || (rc = dalloc(&d->pb.cell_items, (size_t)d->cap)) ||
+        (rc = dalloc(&d->pb.state, (size_t)d->cap))) {
+        release(d);
+        return rc;
+    }
+    if (cudaMemcpy(d->d_radius, rad.data(), 64 * sizeof(double), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d->d_sigma, sig.data(), 64 * sizeof(float), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d->d_radius_f, radf.data(), 64 * sizeof(float), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d->d_taps, d->taps.data(), d->taps.size() * sizeof(float), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d->d_tsc, d->tsc.data(), nl * sizeof(float), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(d->d_tapoff, d->tapoff.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice)) {
+        release(d);
+        return fail(MHFD_ERR_CUDA, "uploading ladder tables failed");
+    }
+    void *hd = nullptr;
+    if ((rc = pinned_alloc(reinterpret_cast<void **>(&d->h_res), &hd, sizeof(HostResult)))) {
+        release(d);
+        return rc;
+    }
+    d->h_res_dev = reinterpret_cast<HostResult *>(hd);
+    if ((rc = pinned_alloc(reinterpret_cast<void **>(&d->h_blobs), &hd, sizeof(mhfd_blob) * d->cap))) {
+        release(d);
+        return rc;
+    }
+    d->h_blobs_dev = reinterpret_cast<mhfd_blob *>(hd);
+    if (d->p.keep_candidates) {
+        if ((rc = pinned_alloc(reinterpret_cast<void **>(&d->h_cands), &hd, sizeof(mhfd_blob) * d->cap))) {
+            release(d);
+            return rc;
+        }
+        d->h_cands_dev = reinterpret_cast<mhfd_blob *>(hd);
+    }
+    std::memset(d->h_res, 0, sizeof(HostResult));
+    if (cudaEventCreateWithFlags(&d->ev_done, cudaEventBlockingSync | cudaEventDisableTiming) ||
+        cudaEventCreate(&d->ev_t0) || cudaEventCreate(&d->ev_k0) || cudaEventCreate(&d->ev_k1) ||
+        cudaEventCreate(&d->ev_end)) {
+        release(d);
+        return fail(MHFD_ERR_CUDA, "event creation failed");
+    }
+    *out = d;
+    return MHFD_OK;
+}
+
+int mhfd_destroy_detector(mhfd_detector *det) {
+    if (!det) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    release(det);
+    return MHFD_OK;
+}
+
+int mhfd_detect(mhfd_detector *d, const void *img, int32_t dtype, int32_t H, int32_t W,
+                size_t pitch, void *stream) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    return detect_impl(d, img, dtype, H, W, pitch, (cudaStream_t)stream, false, nullptr, nullptr,
+                       nullptr);
+}
+
+int mhfd_debug_stack(mhfd_detector *d, const void *img, int32_t dtype, int32_t H, int32_t W,
+                     size_t pitch, void *stream, float *d_D, float *d_M, int32_t *d_arg) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    return detect_impl(d, img, dtype, H, W, pitch, (cudaStream_t)stream, true, d_D, d_M, d_arg);
+}
+
+int mhfd_result_wait(mhfd_detector *d, mhfd_result *out) {
+    if (!d || !out) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    if (!d->pending) return fail(MHFD_ERR_INVALID_ARG, "no detection enqueued on this detector");
+    DeviceGuard g(d->device);
+    MHFD_CUDA(cudaEventSynchronize(d->ev_done));
+    MHFD_CUDA(cudaGetLastError());
+    const HostResult &h = *d->h_res;
+    std::memset(out, 0, sizeof(*out));
+    out->blobs = d->h_blobs;
+    out->n_blobs = (int64_t)h.c.n_blobs;
+    out->candidates = d->p.keep_candidates ? d->h_cands : nullptr;
+    out->n_candidates = (int64_t)h.c.n_stored;
+    out->n_candidates_true = (int64_t)h.c.n_true;
+    out->focus_score = (float)h.c.n_blobs;
+    out->mean_response = h.c.n_blobs ? (float)(h.sum_resp / (double)h.c.n_blobs) : 0.0f;
+    for (int i = 0; i < 64; ++i) out->per_scale[i] = h.per_scale[i];
+    out->lo = h.lo;
+    out->hi = h.hi;
+    if (h.c.timeout) {
+        out->status = MHFD_ERR_TIMEOUT;
+        return fail(MHFD_ERR_TIMEOUT, "overlap prune did not settle within its wait limit");
+    }
+    out->status = h.c.overflow ? MHFD_WARN_OVERFLOW : MHFD_OK;
+    return out->status;
+}
+
+int mhfd_detect_host(mhfd_detector *d, const void *h_img, int32_t dtype, int32_t H, int32_t W,
+                     size_t pitch, void *stream, mhfd_result *out) {
+    if (!d || !out) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    int rc = check_image(h_img, dtype, H, W, pitch);
+    if (rc) return rc;
+    DeviceGuard g(d->device);
+    const size_t row = (size_t)W * elem_size(dtype);
+    const size_t bytes = row * (size_t)H;
+    if (bytes > d->img_copy_bytes) {
+        if ((rc = dalloc(reinterpret_cast<char **>(&d->d_img_copy), bytes))) return rc;
+        d->img_copy_bytes = bytes;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    MHFD_CUDA(cudaMemcpy2DAsync(d->d_img_copy, row, h_img, pitch, row, (size_t)H,
+                                cudaMemcpyHostToDevice, s));
+    rc = detect_impl(d, d->d_img_copy, dtype, H, W, row, s, false, nullptr, nullptr, nullptr);
+    if (rc) return rc;
+    return mhfd_result_wait(d, out);
+}
+
+int mhfd_detect_plain(mhfd_detector *d, const void *img, int32_t dtype, int32_t H, int32_t W,
+                      size_t pitch, void *stream) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    int rc = check_image(img, dtype, H, W, pitch);
+    if (rc) return rc;
+    DeviceGuard g(d->device);
+    if ((rc = ensure_image_capacity(d, H, W, true))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    d->timed = d->p.timing != 0;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_t0, s));
+    rc = enqueue_stretch(img, dtype, H, W, (long long)pitch, clip_rank(d, H, W), d->sel, d->st, s);
+    if (rc) return rc;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k0, s));
+    const int cap_tile = d->p.nms == MHFD_NMS_PAPER ? 256 : 1024;
+    int n_tiles = 0;
+    rc = enqueue_plain(img, dtype, H, W, (long long)pitch, d->st, (int)d->R.size(), d->R,
+                       d->d_taps, d->d_tapoff, d->d_tsc, d->p.nms, d->p.threshold, d->pI, d->pT,
+                       d->pL, d->pM, d->pA, d->pD, d->tile_count, d->stage, cap_tile, 0, &n_tiles,
+                       s);
+    if (rc) return rc;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k1, s));
+    return finish_pipeline(d, n_tiles, cap_tile, H, W, s);
+}
+
+int mhfd_prune(mhfd_detector *d, const int32_t *x, const int32_t *y, const int32_t *i,
+               const float *resp, int64_t n, int32_t H, int32_t W, uint8_t *keep, void *stream) {
+    if (!d || !x || !y || !i || !resp || !keep) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0 || n > d->cap) return fail(MHFD_ERR_INVALID_ARG, "n_cand out of [0, max_candidates]");
+    if (H < 1 || W < 1) return fail(MHFD_ERR_INVALID_ARG, "H and W must be >= 1");
+    DeviceGuard g(d->device);
+    int rc = ensure_image_capacity(d, H, W, false);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return MHFD_OK;
+    if ((rc = enqueue_pack(x, y, i, resp, n, H, W, d->n, d->cand, d->cnt, s))) return rc;
+    if ((rc = enqueue_prune(d->cand, d->cnt, d->cap, H, W, d->d_radius, d->radius_max,
+                            (double)d->p.overlap, &d->pb, s)))
+        return rc;
+    return enqueue_keep(d->pb.state, d->cnt, n, 1, keep, s);
+}
+
+int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap) {
+    if (!p) return fail(MHFD_ERR_INVALID_ARG, "NULL params");
+    std::vector<double> t;
+    std::vector<int> R;
+    int rc = build_ladder(*p, &t, &R);
+    if (rc) return rc;
+    const std::vector<TileConfig> menu = tile_menu(R, p->nms);
+    if (desc) {
+        for (int k = 0; k < (int)menu.size() && k < cap; ++k) {
+            desc[5 * k + 0] = menu[k].tx2;
+            desc[5 * k + 1] = menu[k].ty2;
+            desc[5 * k + 2] = menu[k].rb;
+            desc[5 * k + 3] = menu[k].nt;
+            desc[5 * k + 4] = (int)menu[k].gb.size() - 1;
+        }
+    }
+    return (int)menu.size();
+}
+
+int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5) {
+    if (!p || !desc5) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    std::vector<double> t;
+    std::vector<int> R;
+    int rc = build_ladder(*p, &t, &R);
+    if (rc) return rc;
+    TileConfig c;
+    if ((rc = resolve_tile(R, *p, &c))) return rc;
+    desc5[0] = c.tx2;
+    desc5[1] = c.ty2;
+    desc5[2] = c.rb;
+    desc5[3] = c.nt;
+    desc5[4] = (int)c.gb.size() - 1;
+    return MHFD_OK;
+}
+
+int mhfd_precompile(const mhfd_params *p, int32_t store) {
+    if (!p) return fail(MHFD_ERR_INVALID_ARG, "NULL params");
+    int rc = validate_params(*p);
+    if (rc) return rc;
+    std::vector<double> t;
+    std::vector<int> R;
+    if ((rc = build_ladder(*p, &t, &R))) return rc;
+    return mhfd_jit_precompile(R.data(), (int)R.size(), p->nms, store, p->tile_override);
+}
+
+int mhfd_last_timing(mhfd_detector *d, float *ms_kernel, float *ms_total) {
+    if (!d || !ms_kernel || !ms_total) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    if (!d->pending || !d->timed) return fail(MHFD_ERR_INVALID_ARG, "no timed detection (set params.timing)");
+    DeviceGuard g(d->device);
+    MHFD_CUDA(cudaEventSynchronize(d->ev_done));
+    MHFD_CUDA(cudaEventSynchronize(d->ev_k1));
+    MHFD_CUDA(cudaEventSynchronize(d->ev_end));
+    MHFD_CUDA(cudaEventElapsedTime(ms_kernel, d->ev_k0, d->ev_k1));
+    MHFD_CUDA(cudaEventElapsedTime(ms_total, d->ev_t0, d->ev_end));
+    return MHFD_OK;
+}
+
+int mhfd_probe_ffma_peak(void *stream, double *ops_per_s) {
+    if (!ops_per_s) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    return probe_ffma((cudaStream_t)stream, ops_per_s);
+}
+
+}  // extern "C"

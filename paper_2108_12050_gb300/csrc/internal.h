@@ -1,0 +1,143 @@
+// Internal declarations of the detector library (not part of the C ABI).
+#ifndef MHFD_INTERNAL_H
+#define MHFD_INTERNAL_H
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mhfd.h"
+#include "mhfd_types.h"
+
+namespace mhfd {
+
+// ------------------------------------------------------ driver API (lazy)
+// The few driver entry points the run-time compiled kernel needs are
+// resolved through the runtime (cudaGetDriverEntryPointByVersion), so the
+// library itself loads on machines without a GPU driver.
+struct DrvApi {
+    CUresult (*moduleLoadData)(CUmodule *, const void *);
+    CUresult (*moduleUnload)(CUmodule);
+    CUresult (*moduleGetFunction)(CUfunction *, CUmodule, const char *);
+    CUresult (*moduleGetGlobal)(CUdeviceptr *, size_t *, CUmodule, const char *);
+    CUresult (*memcpyDtoH)(void *, CUdeviceptr, size_t);
+    CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int);
+    CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
+                             unsigned, unsigned, CUstream, void **, void **);
+    CUresult (*getErrorString)(CUresult, const char **);
+    bool ok;
+};
+const DrvApi &drv();
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define MHFD_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------- stretch (§3)
+// Order-statistic select state (device): one radix-select target per bound.
+struct SelState {
+    unsigned prefix[2];            // decided high digits of the lo / hi keys
+    unsigned long long rank[2];    // remaining rank inside the current prefix
+    unsigned hist[2][256];         // digit histograms of the current pass
+};
+
+// Enqueue the whole select (init + passes) writing *st.  k = floor(clip*N).
+int enqueue_stretch(const void *img, int dtype, int H, int W, long long pitch, long long k,
+                    SelState *sel, MhfdStretch *st, cudaStream_t s);
+
+// ---------------------------------------------------- fused kernel (JIT)
+struct TileConfig {
+    int tx2, ty2, rb, nt;
+    std::vector<int> gb;   // level-group boundaries
+};
+
+struct Variant {
+    std::string key;
+    CUmodule mod = nullptr;
+    CUfunction fn = nullptr;
+    int smem_bytes = 0;
+    int param_bytes = 0;
+    int ntaps = 0;
+    TileConfig cfg;
+};
+
+// Choose a tile configuration for the radii and mode (built-in heuristic).
+bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why);
+// Enumerate the configurations offered to the autotuner.
+std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode);
+int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c);
+// Compile (or fetch from cache) the fused kernel for this ladder/config.
+int get_variant(const std::vector<int> &R, int mode, int store, const TileConfig &cfg,
+                Variant **out);
+
+// -------------------------------------------------- post-processing kernels
+struct Counters {
+    unsigned long long n_true;      // candidates found
+    unsigned long long n_stored;    // candidates kept in the list
+    unsigned long long n_blobs;     // survivors
+    int overflow;
+    int timeout;
+    int pad[2];
+};
+
+struct HostResult {               // mirrored in pinned, device-mapped memory
+    Counters c;
+    double sum_resp;
+    int per_scale[64];
+    float lo, hi;
+};
+
+struct PruneBuffers {
+    int *cell_cnt = nullptr;      // ncells + 1
+    int *cell_start = nullptr;    // ncells + 1
+    int *cell_items = nullptr;    // cap
+    int *state = nullptr;         // cap
+    size_t ncells_cap = 0;
+};
+
+int enqueue_gather(const int *tile_count, const MhfdCand *stage, int n_tiles, int cap_tile,
+                   long long cap, int *tile_off, MhfdCand *cand, Counters *cnt,
+                   cudaStream_t s);
+int enqueue_prune(const MhfdCand *cand, const Counters *cnt, long long cap, int H, int W,
+                  const double *d_radius, double radius_max, double overlap, PruneBuffers *pb,
+                  cudaStream_t s);
+int enqueue_output(const MhfdCand *cand, const int *state, const Counters *cnt, long long cap,
+                   const float *d_sigma, const float *d_radius_f, int prune_on,
+                   HostResult *h_res_dev, mhfd_blob *h_blobs_dev, mhfd_blob *h_cands_dev,
+                   const MhfdStretch *st, int *block_tmp, double *block_sum,
+                   cudaStream_t s);
+// pack caller SoA candidates into the internal list
+int enqueue_pack(const int32_t *x, const int32_t *y, const int32_t *i, const float *r,
+                 long long n, int H, int W, int n_levels, MhfdCand *cand, Counters *cnt,
+                 cudaStream_t s);
+int enqueue_keep(const int *state, const Counters *cnt, long long n, int prune_on, uint8_t *keep,
+                 cudaStream_t s);
+
+// ---------------------------------------------------------- plain path
+int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
+                  const MhfdStretch *st, int n_levels, const std::vector<int> &R,
+                  const float *d_taps, const int *d_tapoff, const float *d_tsc, int mode,
+                  float thr, float *scratch_I, float *scratch_T, float *scratch_L,
+                  float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
+                  MhfdCand *stage, int cap_tile, int tile, int *n_tiles_out, cudaStream_t s);
+
+// ------------------------------------------------------------- probe
+int probe_ffma(cudaStream_t s, double *ops_per_s);
+
+}  // namespace mhfd
+
+// Compile one fused-kernel variant into the on-disk cache (no GPU needed).
+extern "C" int mhfd_jit_precompile(const int32_t *R, int32_t nl, int32_t mode, int32_t store,
+                                   int32_t tile_index);
+
+#endif  // MHFD_INTERNAL_H

@@ -1,0 +1,379 @@
+// Run-time specialisation of the fused detection kernel.
+//
+// The kernel source (detect_kernel.cuh, embedded at build time) is compiled
+// by NVRTC for sm_103a once per (ladder radii, tile configuration, mode,
+// store flag), with the radii baked in as compile-time constants so that the
+// scale and tap loops unroll completely.  Cubins are cached on disk (keyed by
+// a hash of the full source text and options) and modules per device in
+// process memory.
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+#include "internal.h"
+
+namespace mhfd {
+
+namespace {
+
+#include "kernel_src.inc"  // kTypesSrc, kKernelSrc
+
+constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block (227 KB)
+
+std::mutex g_mu;
+std::map<std::string, Variant *> g_variants;
+
+unsigned long long fnv1a(const std::string &s) {
+    unsigned long long h = 1469598103934665603ull;
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::string lib_dir() {
+    Dl_info info;
+    if (dladdr(reinterpret_cast<void *>(&fnv1a), &info) && info.dli_fname) {
+        std::string p(info.dli_fname);
+        const size_t k = p.rfind('/');
+        if (k != std::string::npos) return p.substr(0, k);
+    }
+    return ".";
+}
+
+std::string cache_dir() {
+    const char *e = std::getenv("MHFD_JIT_CACHE");
+    std::string d = (e && *e) ? std::string(e) : lib_dir() + "/_jit_cache";
+    mkdir(d.c_str(), 0755);
+    return d;
+}
+
+std::string join(const std::vector<int> &v) {
+    std::ostringstream o;
+    for (size_t i = 0; i < v.size(); ++i) o << (i ? "," : "") << v[i];
+    return o.str();
+}
+
+std::string make_source(const std::vector<int> &R, int mode, int store, const TileConfig &c) {
+    std::ostringstream o;
+    o << "#define MHFD_NL " << R.size() << "\n"
+      << "#define MHFD_RLIST " << join(R) << "\n"
+      << "#define MHFD_NGROUPS " << (c.gb.size() - 1) << "\n"
+      << "#define MHFD_GB " << join(c.gb) << "\n"
+      << "#define MHFD_TX2 " << c.tx2 << "\n"
+      << "#define MHFD_TY2 " << c.ty2 << "\n"
+      << "#define MHFD_RB " << c.rb << "\n"
+      << "#define MHFD_NT " << c.nt << "\n"
+      << "#define MHFD_MODE " << mode << "\n"
+      << "#define MHFD_STORE " << store << "\n";
+    return o.str() + kTypesSrc + kKernelSrc;
+}
+
+const char *kOpts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
+
+bool read_file(const std::string &path, std::string *out) {
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return false;
+    std::ostringstream ss;
+    ss << f.rdbuf();
+    *out = ss.str();
+    return !out->empty();
+}
+
+void write_file_atomic(const std::string &path, const std::string &data) {
+    const std::string tmp = path + ".tmp." + std::to_string(getpid());
+    {
+        std::ofstream f(tmp, std::ios::binary);
+        if (!f) return;
+        f.write(data.data(), (std::streamsize)data.size());
+    }
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+int compile_cubin(const std::string &src, std::string *cubin) {
+    nvrtcProgram prog;
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "mhfd_fused.cu", 0, nullptr, nullptr);
+    if (r != NVRTC_SUCCESS) return fail(MHFD_ERR_JIT, std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r));
+    r = nvrtcCompileProgram(prog, (int)(sizeof(kOpts) / sizeof(kOpts[0])), kOpts);
+    if (r != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        if (n) nvrtcGetProgramLog(prog, &log[0]);
+        nvrtcDestroyProgram(&prog);
+        if (log.size() > 4000) log = log.substr(0, 4000);
+        return fail(MHFD_ERR_JIT, "NVRTC compile failed: " + log);
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin->assign(n, '\0');
+    nvrtcGetCUBIN(prog, &(*cubin)[0]);
+    nvrtcDestroyProgram(&prog);
+    return MHFD_OK;
+}
+
+int drv_fail(CUresult r, const char *what) {
+    const char *s = nullptr;
+    if (drv().getErrorString) drv().getErrorString(r, &s);
+    return fail(MHFD_ERR_CUDA, std::string(what) + ": " + (s ? s : "unknown driver error"));
+}
+
+template <class F>
+void resolve(const char *name, F *fp, bool *ok) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 13000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+        *ok = false;
+        *fp = nullptr;
+        return;
+    }
+    *fp = reinterpret_cast<F>(p);
+}
+
+}  // namespace
+
+const DrvApi &drv() {
+    static DrvApi api = [] {
+        DrvApi a;
+        std::memset(&a, 0, sizeof(a));
+        a.ok = true;
+        resolve("cuModuleLoadData", &a.moduleLoadData, &a.ok);
+        resolve("cuModuleUnload", &a.moduleUnload, &a.ok);
+        resolve("cuModuleGetFunction", &a.moduleGetFunction, &a.ok);
+        resolve("cuModuleGetGlobal", &a.moduleGetGlobal, &a.ok);
+        resolve("cuMemcpyDtoH", &a.memcpyDtoH, &a.ok);
+        resolve("cuFuncSetAttribute", &a.funcSetAttribute, &a.ok);
+        resolve("cuLaunchKernel", &a.launchKernel, &a.ok);
+        resolve("cuGetErrorString", &a.getErrorString, &a.ok);
+        return a;
+    }();
+    return api;
+}
+
+int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
+    int rmax = 0;
+    for (int r : R) rmax = r > rmax ? r : rmax;
+    const int nl = (int)R.size();
+    const int wextp = (c.tx2 + 2 * rmax + 3) & ~3;
+    const int rows_in = c.ty2 + 2 * rmax;
+    int vrow = 0;
+    for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
+        int o = 0;
+        for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) o += (c.tx2 + 2 * R[l] + 3) & ~3;
+        vrow = o > vrow ? o : vrow;
+    }
+    const int ring = c.rb + 2;
+    const int ring_f = mode == 0 ? ring * c.tx2 : ring * (nl - 1) * c.tx2;
+    const int ring_b = mode == 0 ? ((ring * c.tx2 + 15) & ~15) : 0;
+    return 4 * (rows_in * wextp + c.rb * vrow + ring_f) + ring_b + 4 * 64;
+}
+
+namespace {
+
+std::vector<int> groups_for(int nl, int max_per_group) {
+    const int ng = (nl + max_per_group - 1) / max_per_group;
+    std::vector<int> gb(ng + 1);
+    for (int g = 0; g <= ng; ++g) gb[g] = (int)((long long)nl * g / ng);
+    return gb;
+}
+
+// relative instruction cost per output pixel (FMA-dominated model)
+double cost_model(const std::vector<int> &R, const TileConfig &c) {
+    int rmax = 0;
+    for (int r : R) rmax = r > rmax ? r : rmax;
+    const double tx = c.tx2 - 2, ty = c.ty2 - 2;
+    const double wext = c.tx2 + 2 * rmax;
+    double v = 0, h = 0;
+    for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
+        v += R[c.gb[g + 1] - 1];  // folded sums of the group
+        for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) v += R[l] + 1;
+    }
+    for (int r : R) h += 2 * r + 1;
+    const double vthreads = ((int)(wext + c.nt - 1) / c.nt) * (double)c.nt;
+    const double v_eff = v * vthreads / tx * (c.ty2 / ty);
+    const double h_items = c.rb * (c.tx2 / 4.0);
+    const double h_slots = ((int)((h_items + c.nt - 1) / c.nt)) * (double)c.nt;
+    const double h_eff = h * (c.tx2 / tx) * (c.ty2 / ty) * (h_slots / h_items);
+    const double load = 12.0 * (c.ty2 + 2 * rmax) * wext / (tx * ty);
+    return v_eff + h_eff + load;
+}
+
+}  // namespace
+
+std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode) {
+    std::vector<TileConfig> out;
+    const int nl = (int)R.size();
+    int rmax = 0;
+    for (int r : R) rmax = r > rmax ? r : rmax;
+    const int widths[] = {64, 96, 128, 160, 192, 256};
+    const int gmax[] = {8, 10, 12};
+    for (int tx2 : widths) {
+        const int wext = tx2 + 2 * rmax;
+        for (int nt = 64; nt <= 512; nt += 32) {
+            if (nt < wext / 3) continue;
+            const int rb_full = nt / (tx2 / 4);  // horizontal items == threads
+            for (int rb = 2; rb <= 12; ++rb) {
+                if (rb != rb_full && rb != rb_full / 2 && rb != 4 && rb != 8) continue;
+                for (int gm : gmax) {
+                    TileConfig c;
+                    c.tx2 = tx2;
+                    c.nt = nt;
+                    c.rb = rb;
+                    c.gb = groups_for(nl, gm);
+                    int best_ty = 0;
+                    for (int k = 1; k * rb <= 256; ++k) {
+                        c.ty2 = k * rb;
+                        if (c.ty2 < 8) continue;
+                        if (smem_estimate(R, mode, c) <= kSmemLimit) best_ty = c.ty2;
+                    }
+                    if (best_ty == 0) continue;
+                    c.ty2 = best_ty;
+                    out.push_back(c);
+                }
+            }
+        }
+    }
+    return out;
+}
+
+bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why) {
+    const std::vector<TileConfig> menu = tile_menu(R, mode);
+    double best = 1e300;
+    bool found = false;
+    for (const TileConfig &c : menu) {
+        // balanced shapes: vertical-pass columns fit the block, every
+        // horizontal item has a thread
+        int rmax = 0;
+        for (int r : R) rmax = r > rmax ? r : rmax;
+        const int wext = c.tx2 + 2 * rmax;
+        if (c.nt < wext - 31 || c.nt > wext + 31) continue;
+        if (c.rb * (c.tx2 / 4) > c.nt) continue;
+        const double cost = cost_model(R, c);
+        if (cost < best) {
+            best = cost;
+            *cfg = c;
+            found = true;
+        }
+    }
+    if (!found && why) *why = "no tile configuration fits in shared memory for this ladder";
+    return found;
+}
+
+int get_variant(const std::vector<int> &R, int mode, int store, const TileConfig &cfg,
+                Variant **out) {
+    int dev = 0;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaFree(nullptr));  // make sure the primary context exists and is current
+    const std::string src = make_source(R, mode, store, cfg);
+    std::string opts;
+    for (const char *o : kOpts) opts += std::string(o) + " ";
+    int ver_major = 0, ver_minor = 0;
+    nvrtcVersion(&ver_major, &ver_minor);
+    char hbuf[32];
+    std::snprintf(hbuf, sizeof(hbuf), "%016llx",
+                  fnv1a(src + opts + std::to_string(ver_major) + "." + std::to_string(ver_minor)));
+    const std::string key = std::string(hbuf) + "@" + std::to_string(dev);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_variants.find(key);
+        if (it != g_variants.end()) {
+            *out = it->second;
+            return MHFD_OK;
+        }
+    }
+    if (smem_estimate(R, mode, cfg) > kSmemLimit)
+        return fail(MHFD_ERR_UNSUPPORTED, "tile configuration exceeds shared memory");
+    const std::string path = cache_dir() + "/" + hbuf + ".cubin";
+    std::string cubin;
+    if (!read_file(path, &cubin)) {
+        const int rc = compile_cubin(src, &cubin);
+        if (rc != MHFD_OK) return rc;
+        write_file_atomic(path, cubin);
+    }
+    if (!drv().ok) return fail(MHFD_ERR_CUDA, "CUDA driver entry points unavailable");
+    Variant *v = new Variant();
+    v->key = key;
+    v->cfg = cfg;
+    CUresult r = drv().moduleLoadData(&v->mod, cubin.data());
+    if (r != CUDA_SUCCESS) {
+        delete v;
+        return drv_fail(r, "cuModuleLoadData");
+    }
+    r = drv().moduleGetFunction(&v->fn, v->mod, "mhfd_fused_detect");
+    if (r != CUDA_SUCCESS) return drv_fail(r, "cuModuleGetFunction");
+    CUdeviceptr gp;
+    size_t gsz;
+    int vals[3] = {0, 0, 0};
+    const char *names[3] = {"mhfd_smem_bytes", "mhfd_param_bytes", "mhfd_ntaps"};
+    for (int i = 0; i < 3; ++i) {
+        r = drv().moduleGetGlobal(&gp, &gsz, v->mod, names[i]);
+        if (r != CUDA_SUCCESS) return drv_fail(r, "cuModuleGetGlobal");
+        r = drv().memcpyDtoH(&vals[i], gp, sizeof(int));
+        if (r != CUDA_SUCCESS) return drv_fail(r, "cuMemcpyDtoH");
+    }
+    v->smem_bytes = vals[0];
+    v->param_bytes = vals[1];
+    v->ntaps = vals[2];
+    if (v->smem_bytes > kSmemLimit) return fail(MHFD_ERR_UNSUPPORTED, "kernel shared memory too large");
+    r = drv().funcSetAttribute(v->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, v->smem_bytes);
+    if (r != CUDA_SUCCESS) return drv_fail(r, "cuFuncSetAttribute");
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_variants.find(key);
+    if (it != g_variants.end()) {  // another thread won the race
+        drv().moduleUnload(v->mod);
+        delete v;
+        *out = it->second;
+        return MHFD_OK;
+    }
+    g_variants[key] = v;
+    *out = v;
+    return MHFD_OK;
+}
+
+}  // namespace mhfd
+
+using namespace mhfd;
+
+// Compile a variant into the disk cache without touching any GPU (used by
+// the build step to warm the cache for the standard ladders).
+extern "C" int mhfd_jit_precompile(const int32_t *R, int32_t nl, int32_t mode, int32_t store,
+                                   int32_t tile_index) {
+    std::vector<int> r(R, R + nl);
+    TileConfig cfg;
+    std::string why;
+    if (tile_index <= 0) {
+        if (!choose_tile(r, mode, &cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+    } else {
+        std::vector<TileConfig> menu = tile_menu(r, mode);
+        if (tile_index > (int)menu.size()) return fail(MHFD_ERR_INVALID_ARG, "tile index");
+        cfg = menu[tile_index - 1];
+    }
+    const std::string src = make_source(r, mode, store, cfg);
+    std::string opts;
+    for (const char *o : kOpts) opts += std::string(o) + " ";
+    int ver_major = 0, ver_minor = 0;
+    nvrtcVersion(&ver_major, &ver_minor);
+    char hbuf[32];
+    std::snprintf(hbuf, sizeof(hbuf), "%016llx",
+                  fnv1a(src + opts + std::to_string(ver_major) + "." + std::to_string(ver_minor)));
+    const std::string path = cache_dir() + "/" + hbuf + ".cubin";
+    std::string cubin;
+    if (read_file(path, &cubin)) return MHFD_OK;
+    const int rc = compile_cubin(src, &cubin);
+    if (rc != MHFD_OK) return rc;
+    write_file_atomic(path, cubin);
+    return MHFD_OK;
+}
+
+

@@ -1,0 +1,42 @@
+// Device-visible records shared by the library's kernels and by the fused
+// detection kernel, which is compiled at run time with NVRTC for each ladder
+// (this header is embedded verbatim in that kernel's source).  Plain C
+// layout only: no CUDA or host headers.
+#ifndef MHFD_TYPES_H
+#define MHFD_TYPES_H
+
+// Histogram-stretch bounds of one image (§3), written on the device by the
+// order-statistic select kernels and read by the detection kernels.
+struct MhfdStretch {
+    float lo, hi;    // k-th and (N-1-k)-th smallest values, input units
+    float inv;       // 1 / (hi - lo) rounded to f32; 0 for a constant image
+    float off;       // -0.5 (centres I' on 0; exact for the DoG), 0 if constant
+    int lo_i, hi_i;  // the same bounds as integers (uint8 / uint16 inputs)
+    int constant;    // hi == lo
+    int pad;
+};
+
+// One scale-space maximum: pixel, 0-based DoG layer, response.
+struct MhfdCand {
+    int x, y, i;
+    float resp;
+};
+
+// Fixed head of the fused kernel's by-value parameter block; the ladder's
+// scale factors t_i and the Gaussian taps follow it (sizes depend on the
+// ladder the kernel was compiled for).
+struct MhfdKHeader {
+    const void *img;          // device image, `pitch` bytes per row
+    const MhfdStretch *st;    // stretch bounds of this image
+    MhfdCand *stage;          // per-tile candidate slots, cap_tile each
+    int *tile_count;          // per-tile true candidate count
+    float *stack_out;         // optional D output, n planes of H*W
+    float *m_out;             // optional max-over-scales output (H*W)
+    int *arg_out;             // optional first-argmax output (H*W)
+    long long pitch;          // bytes between rows of img
+    long long plane;          // H*W (stack plane stride)
+    int H, W, dtype, tiles_x, cap_tile;
+    float thr;                // feature threshold (strict >)
+};
+
+#endif  // MHFD_TYPES_H

@@ -1,0 +1,490 @@
+// Candidate gather, greedy overlap prune and result compaction.
+//
+// * gather: per-tile candidate slots written by the fused kernel are packed
+//   into one list in tile order (a one-block scan over tile counts, then one
+//   block per tile copies) - the order is deterministic.
+// * prune: the greedy rule "visit blobs by (radius desc, response desc,
+//   row-major position asc); drop a blob when an already kept blob covers more
+//   than `overlap` of the smaller circle" equals the lexicographically first
+//   maximal independent set of the conflict graph under that priority.  It is
+//   computed in parallel: candidates are bucketed in a uniform grid of cells
+//   no smaller than the largest possible conflict distance, and every thread
+//   repeatedly settles its own candidates: drop if a higher-priority
+//   conflicting neighbour is kept, keep once all higher-priority conflicting
+//   neighbours are dropped.  The result does not depend on timing or order.
+//   The lens overlap is evaluated in FP64 in the same operation order as the
+//   CPU oracle (no FMA contraction).
+// * output: kept candidates are compacted in list order (per-block counts,
+//   a one-block scan, ordered writes) straight into pinned host memory
+//   mapped into the device address space.
+#include "internal.h"
+
+#include <cooperative_groups.h>
+
+namespace mhfd {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ long long block_scan_excl_ll(long long v, long long *sh, long long *tot) {
+    // sh: 32 entries
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) sh[lane] = w;
+    }
+    __syncthreads();
+    const long long ex = (warp ? sh[warp - 1] : 0) + x - v;
+    *tot = sh[nw - 1];
+    __syncthreads();
+    return ex;
+}
+
+// ---------------------------------------------------------------- gather
+
+__global__ void __launch_bounds__(kScanThreads)
+    gather_scan(const int *tile_count, int n_tiles, int cap_tile, long long cap, int *tile_off,
+                Counters *cnt) {
+    __shared__ long long sh[32];
+    const int per = (n_tiles + blockDim.x - 1) / blockDim.x;
+    const int beg = min(n_tiles, (int)threadIdx.x * per);
+    const int end = min(n_tiles, beg + per);
+    long long stored = 0, truth = 0;
+    for (int t = beg; t < end; ++t) {
+        const int c = tile_count[t];
+        truth += c;
+        stored += c < cap_tile ? c : cap_tile;
+    }
+    long long tot_s, tot_t;
+    long long off = block_scan_excl_ll(stored, sh, &tot_s);
+    block_scan_excl_ll(truth, sh, &tot_t);
+    for (int t = beg; t < end; ++t) {
+        tile_off[t] = (int)off;
+        const int c = tile_count[t];
+        off += c < cap_tile ? c : cap_tile;
+    }
+    if (threadIdx.x == 0) {
+        cnt->n_true = (unsigned long long)tot_t;
+        cnt->n_stored = (unsigned long long)(tot_s < cap ? tot_s : cap);
+        cnt->overflow = (tot_t > cnt->n_stored) ? 1 : 0;
+        cnt->n_blobs = 0;
+        cnt->timeout = 0;
+    }
+}
+
+__global__ void gather_copy(const int *tile_count, const MhfdCand *stage, int cap_tile,
+                            long long cap, const int *tile_off, MhfdCand *cand) {
+    const int t = blockIdx.x;
+    int m = tile_count[t];
+    m = m < cap_tile ? m : cap_tile;
+    const long long o = tile_off[t];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        if (o + k < cap) cand[o + k] = stage[(long long)t * cap_tile + k];
+    }
+}
+
+// ----------------------------------------------------------------- prune
+
+__global__ void grid_count(const MhfdCand *cand, const Counters *cnt, int cs, int ncx,
+                           int *cell_cnt) {
+    const long long n = (long long)cnt->n_stored;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const MhfdCand c = cand[j];
+        atomicAdd(&cell_cnt[(c.y / cs) * ncx + c.x / cs], 1);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    grid_scan(int *cell_cnt, int ncells, int *cell_start) {
+    __shared__ long long sh[32];
+    const int per = (ncells + blockDim.x - 1) / blockDim.x;
+    const int beg = min(ncells, (int)threadIdx.x * per);
+    const int end = min(ncells, beg + per);
+    long long s = 0;
+    for (int c = beg; c < end; ++c) s += cell_cnt[c];
+    long long tot;
+    long long off = block_scan_excl_ll(s, sh, &tot);
+    for (int c = beg; c < end; ++c) {
+        cell_start[c] = (int)off;
+        off += cell_cnt[c];
+        cell_cnt[c] = 0;  // reused as the fill cursor
+    }
+    if (threadIdx.x == 0) cell_start[ncells] = (int)tot;
+}
+
+__global__ void grid_fill(const MhfdCand *cand, const Counters *cnt, int cs, int ncx,
+                          const int *cell_start, int *cursor, int *items, int *state) {
+    const long long n = (long long)cnt->n_stored;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const MhfdCand c = cand[j];
+        const int cell = (c.y / cs) * ncx + c.x / cs;
+        items[cell_start[cell] + atomicAdd(&cursor[cell], 1)] = (int)j;
+        state[j] = 0;
+    }
+}
+
+// Fraction of the smaller circle covered by the lens of two circles, in the
+// same operation order as the CPU oracle (round-to-nearest, no contraction).
+__device__ double lens_overlap(double r1, double r2, double d) {
+    const double rmin = r1 < r2 ? r1 : r2;
+    if (d >= __dadd_rn(r1, r2)) return 0.0;
+    if (d <= fabs(__dsub_rn(r1, r2))) return 1.0;
+    const double dd = __dmul_rn(d, d), r11 = __dmul_rn(r1, r1), r22 = __dmul_rn(r2, r2);
+    double a1 = __ddiv_rn(__dsub_rn(__dadd_rn(dd, r11), r22), __dmul_rn(__dmul_rn(2.0, d), r1));
+    double a2 = __ddiv_rn(__dsub_rn(__dadd_rn(dd, r22), r11), __dmul_rn(__dmul_rn(2.0, d), r2));
+    a1 = a1 > 1.0 ? 1.0 : (a1 < -1.0 ? -1.0 : a1);
+    a2 = a2 > 1.0 ? 1.0 : (a2 < -1.0 ? -1.0 : a2);
+    const double f1 = __dadd_rn(__dadd_rn(-d, r1), r2);
+    const double f2 = __dsub_rn(__dadd_rn(d, r1), r2);
+    const double f3 = __dadd_rn(__dsub_rn(d, r1), r2);
+    const double f4 = __dadd_rn(__dadd_rn(d, r1), r2);
+    double k = __dmul_rn(__dmul_rn(__dmul_rn(f1, f2), f3), f4);
+    if (k < 0.0) k = 0.0;
+    const double area = __dsub_rn(__dadd_rn(__dmul_rn(r11, acos(a1)), __dmul_rn(r22, acos(a2))),
+                                  __dmul_rn(0.5, __dsqrt_rn(k)));
+    return __ddiv_rn(area, __dmul_rn(__dmul_rn(3.14159265358979323846, rmin), rmin));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool higher(const MhfdCand &b, const MhfdCand &a, int W) {
+    if (b.i != a.i) return b.i > a.i;
+    if (b.resp != a.resp) return b.resp > a.resp;
+    return (long long)b.y * W + b.x < (long long)a.y * W + a.x;
+}
+
+// 0 = undecided, 1 = kept, 2 = dropped
+__device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
+                      const int *cell_start, const int *items, const double *radius,
+                      double overlap, int W, const volatile int *state) {
+    const MhfdCand a = cand[j];
+    const double ra = radius[a.i];
+    const int cx = a.x / cs, cy = a.y / cs;
+    bool waiting = false;
+    for (int gy = max(0, cy - 1); gy <= min(ncy - 1, cy + 1); ++gy)
+        for (int gx = max(0, cx - 1); gx <= min(ncx - 1, cx + 1); ++gx) {
+            const int c = gy * ncx + gx;
+            for (int p = cell_start[c]; p < cell_start[c + 1]; ++p) {
+                const int b = items[p];
+                if (b == j) continue;
+                const MhfdCand cb = cand[b];
+                if (!higher(cb, a, W)) continue;
+                const int s = state[b];
+                if (s == 2) continue;
+                const double dx = (double)(a.x - cb.x), dy = (double)(a.y - cb.y);
+                const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+                if (!(lens_overlap(radius[cb.i], ra, d) > overlap)) continue;
+                if (s == 1) return 2;
+                waiting = true;
+            }
+        }
+    return waiting ? 0 : 1;
+}
+
+__global__ void __launch_bounds__(256)
+    lfmis_kernel(const MhfdCand *cand, Counters *cnt, int cs, int ncx, int ncy,
+                 const int *cell_start, const int *items, const double *radius, double overlap,
+                 int W, int *state, long long max_sweeps, unsigned long long max_ns) {
+    // Every thread settles its own candidates; a candidate waits only on
+    // higher-priority ones, so the highest undecided candidate can always be
+    // settled and the sweeps end.  The waits are bounded in count and time;
+    // on expiry the detection reports MHFD_ERR_TIMEOUT instead of spinning.
+    const long long n = (long long)cnt->n_stored;
+    volatile int *vs = state;
+    const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    const unsigned long long t0 = globaltimer_ns();
+    long long sweep = 0;
+    bool pending = true;
+    for (; sweep < max_sweeps; ++sweep) {
+        pending = false;
+        for (long long j = g0; j < n; j += gs) {
+            if (vs[j] != 0) continue;
+            const int r = settle((int)j, cand, cs, ncx, ncy, cell_start, items, radius, overlap,
+                                 W, vs);
+            if (r == 0)
+                pending = true;
+            else
+                vs[j] = r;
+        }
+        if (!pending) break;
+        __nanosleep(200);
+        if ((sweep & 63) == 63 && globaltimer_ns() - t0 > max_ns) break;
+    }
+    if (pending) atomicExch(&cnt->timeout, 1);
+}
+
+__global__ void keep_all(const Counters *cnt, int *state) {
+    const long long n = (long long)cnt->n_stored;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        state[j] = 1;
+}
+
+// ---------------------------------------------------------------- output
+
+struct DevAcc {
+    int per_scale[64];
+};
+
+__global__ void __launch_bounds__(256)
+    out_count(const MhfdCand *cand, const int *state, const Counters *cnt, int *block_cnt,
+              double *block_sum) {
+    __shared__ long long shc[256];
+    __shared__ double shs[256];
+    const long long n = (long long)cnt->n_stored;
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long beg = min(n, (long long)blockIdx.x * per), end = min(n, beg + per);
+    long long c = 0;
+    double s = 0.0;
+    for (long long j = beg + threadIdx.x; j < end; j += blockDim.x)
+        if (state[j] == 1) {
+            ++c;
+            s += (double)cand[j].resp;
+        }
+    shc[threadIdx.x] = c;
+    shs[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {  // fixed-order tree: deterministic sum
+        if ((int)threadIdx.x < o) {
+            shc[threadIdx.x] += shc[threadIdx.x + o];
+            shs[threadIdx.x] += shs[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        block_cnt[blockIdx.x] = (int)shc[0];
+        block_sum[blockIdx.x] = shs[0];
+    }
+}
+
+__global__ void out_scan(int *block_cnt, const double *block_sum, int nb, Counters *cnt,
+                         double *sum_out, int *per_scale) {
+    if (threadIdx.x == 0) {
+        long long o = 0;
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const int c = block_cnt[b];
+            block_cnt[b] = (int)o;
+            o += c;
+            s += block_sum[b];
+        }
+        cnt->n_blobs = (unsigned long long)o;
+        *sum_out = s;
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) per_scale[i] = 0;
+}
+
+__global__ void __launch_bounds__(256)
+    out_write(const MhfdCand *cand, const int *state, const Counters *cnt, const int *block_off,
+              const float *sigma, const float *radius_f, mhfd_blob *blobs, mhfd_blob *cands,
+              int *per_scale) {
+    __shared__ int sh_scale[64];
+    __shared__ int sh_w[8];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) sh_scale[i] = 0;
+    __syncthreads();
+    const long long n = (long long)cnt->n_stored;
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long beg = min(n, (long long)blockIdx.x * per), end = min(n, beg + per);
+    long long out = block_off[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long base = beg; base < end; base += blockDim.x) {
+        const long long j = base + threadIdx.x;
+        const bool valid = j < end;
+        MhfdCand c;
+        c.x = c.y = c.i = 0;
+        c.resp = 0.0f;
+        int keep = 0;
+        if (valid) {
+            c = cand[j];
+            keep = state[j] == 1;
+            if (cands) {
+                mhfd_blob b;
+                b.x = c.x;
+                b.y = c.y;
+                b.scale_idx = c.i;
+                b.sigma = sigma[c.i];
+                b.radius = radius_f[c.i];
+                b.response = c.resp;
+                cands[j] = b;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) sh_w[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += sh_w[w];
+            total += sh_w[w];
+        }
+        if (keep) {
+            const long long pos = out + before + __popc(bal & ((1u << lane) - 1u));
+            mhfd_blob b;
+            b.x = c.x;
+            b.y = c.y;
+            b.scale_idx = c.i;
+            b.sigma = sigma[c.i];
+            b.radius = radius_f[c.i];
+            b.response = c.resp;
+            blobs[pos] = b;
+            atomicAdd(&sh_scale[c.i & 63], 1);
+        }
+        out += total;
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64; i += blockDim.x)
+        if (sh_scale[i]) atomicAdd(&per_scale[i], sh_scale[i]);
+}
+
+__global__ void out_publish(const Counters *cnt, const double *sum, const int *per_scale,
+                            const MhfdStretch *st, HostResult *h) {
+    const int t = threadIdx.x;
+    if (t < 64) h->per_scale[t] = per_scale[t];
+    if (t == 0) {
+        h->c = *cnt;
+        h->sum_resp = *sum;
+        h->lo = st ? st->lo : 0.0f;
+        h->hi = st ? st->hi : 0.0f;
+    }
+}
+
+// Positions and scale indices are clamped into the image and the ladder so
+// that a malformed list cannot address memory outside the prune grid.
+__global__ void pack_kernel(const int32_t *x, const int32_t *y, const int32_t *i, const float *r,
+                            long long n, int H, int W, int n_levels, MhfdCand *cand,
+                            Counters *cnt) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        MhfdCand c;
+        c.x = min(max(x[j], 0), W - 1);
+        c.y = min(max(y[j], 0), H - 1);
+        c.i = min(max(i[j], 0), n_levels - 1);
+        c.resp = r[j];
+        cand[j] = c;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cnt->n_true = cnt->n_stored = (unsigned long long)n;
+        cnt->overflow = 0;
+        cnt->timeout = 0;
+        cnt->n_blobs = 0;
+    }
+}
+
+__global__ void keep_kernel(const int *state, const Counters *cnt, long long n, int prune_on,
+                            uint8_t *keep) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        keep[j] = prune_on ? (state[j] == 1 ? 1 : 0) : 1;
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+int enqueue_gather(const int *tile_count, const MhfdCand *stage, int n_tiles, int cap_tile,
+                   long long cap, int *tile_off, MhfdCand *cand, Counters *cnt, cudaStream_t s) {
+    gather_scan<<<1, kScanThreads, 0, s>>>(tile_count, n_tiles, cap_tile, cap, tile_off, cnt);
+    gather_copy<<<n_tiles, 128, 0, s>>>(tile_count, stage, cap_tile, cap, tile_off, cand);
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
+
+int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, int H, int W,
+                  const double *d_radius, double radius_max, double overlap, PruneBuffers *pb,
+                  cudaStream_t s) {
+    (void)cap;
+    Counters *cnt = const_cast<Counters *>(cnt_c);
+    if (overlap >= 1.0) {
+        keep_all<<<sm_count() * 4, 256, 0, s>>>(cnt, pb->state);
+        MHFD_CUDA(cudaGetLastError());
+        return MHFD_OK;
+    }
+    // cell edge >= the largest conflict distance r1 + r2 <= 2 * radius_max
+    const int cs = (int)ceil(2.0 * radius_max) + 1;
+    const int ncx = (W + cs - 1) / cs, ncy = (H + cs - 1) / cs;
+    const int ncells = ncx * ncy;
+    if ((size_t)ncells + 1 > pb->ncells_cap) return fail(MHFD_ERR_INVALID_ARG, "prune grid too large");
+    MHFD_CUDA(cudaMemsetAsync(pb->cell_cnt, 0, sizeof(int) * (ncells + 1), s));
+    const int sms = sm_count();
+    grid_count<<<sms * 4, 256, 0, s>>>(cand, cnt, cs, ncx, pb->cell_cnt);
+    grid_scan<<<1, kScanThreads, 0, s>>>(pb->cell_cnt, ncells, pb->cell_start);
+    grid_fill<<<sms * 4, 256, 0, s>>>(cand, cnt, cs, ncx, pb->cell_start, pb->cell_cnt,
+                                      pb->cell_items, pb->state);
+    MHFD_CUDA(cudaGetLastError());
+    int per_sm = 0;
+    MHFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lfmis_kernel, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int grid = sms * (per_sm < 4 ? per_sm : 4);
+    long long max_sweeps = 1ll << 24;
+    unsigned long long max_ns = 2000000000ull;  // 2 s of device time
+    void *args[] = {(void *)&cand, (void *)&cnt, (void *)&cs, (void *)&ncx, (void *)&ncy,
+                    (void *)&pb->cell_start, (void *)&pb->cell_items, (void *)&d_radius,
+                    (void *)&overlap, (void *)&W, (void *)&pb->state, (void *)&max_sweeps,
+                    (void *)&max_ns};
+    MHFD_CUDA(cudaLaunchCooperativeKernel((const void *)lfmis_kernel, grid, 256, args, 0, s));
+    return MHFD_OK;
+}
+
+int enqueue_output(const MhfdCand *cand, const int *state, const Counters *cnt_c, long long cap,
+                   const float *d_sigma, const float *d_radius_f, int prune_on,
+                   HostResult *h_res_dev, mhfd_blob *h_blobs_dev, mhfd_blob *h_cands_dev,
+                   const MhfdStretch *st, int *block_tmp, double *block_sum, cudaStream_t s) {
+    (void)cap;
+    (void)prune_on;
+    Counters *cnt = const_cast<Counters *>(cnt_c);
+    const int nb = 256;
+    // block_tmp: nb block counts followed by 64 per-scale counters
+    int *per_scale = block_tmp + nb;
+    double *sum = block_sum + nb;
+    out_count<<<nb, 256, 0, s>>>(cand, state, cnt, block_tmp, block_sum);
+    out_scan<<<1, 64, 0, s>>>(block_tmp, block_sum, nb, cnt, sum, per_scale);
+    out_write<<<nb, 256, 0, s>>>(cand, state, cnt, block_tmp, d_sigma, d_radius_f, h_blobs_dev,
+                                 h_cands_dev, per_scale);
+    out_publish<<<1, 64, 0, s>>>(cnt, sum, per_scale, st, h_res_dev);
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
+
+int enqueue_pack(const int32_t *x, const int32_t *y, const int32_t *i, const float *r,
+                 long long n, int H, int W, int n_levels, MhfdCand *cand, Counters *cnt,
+                 cudaStream_t s) {
+    pack_kernel<<<sm_count() * 2, 256, 0, s>>>(x, y, i, r, n, H, W, n_levels, cand, cnt);
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
+
+int enqueue_keep(const int *state, const Counters *cnt, long long n, int prune_on, uint8_t *keep,
+                 cudaStream_t s) {
+    keep_kernel<<<sm_count() * 2, 256, 0, s>>>(state, cnt, n, prune_on, keep);
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
+
+}  // namespace mhfd

@@ -1,0 +1,167 @@
+// Histogram stretch bounds of §3 on the device: the k-th and (N-1-k)-th
+// smallest pixel values found exactly by an MSD radix select over 8-bit
+// digits (1 pass for uint8, 2 for uint16, 4 for float32 keys), entirely on
+// the stream (no host round trip).  Each pass builds, per target, the digit
+// histogram of the pixels whose higher digits match the target's prefix,
+// with warp-aggregated shared-memory atomics; a one-block select kernel then
+// picks the digit that contains the remaining rank.
+#include "internal.h"
+
+namespace mhfd {
+
+namespace {
+
+__device__ __forceinline__ unsigned key_u8(unsigned char v) { return v; }
+__device__ __forceinline__ unsigned key_u16(unsigned short v) { return v; }
+// order-preserving map of float bits onto unsigned integers
+__device__ __forceinline__ unsigned key_f32(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float unkey_f32(unsigned k) {
+    const unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
+__global__ void sel_init(SelState *sel, unsigned long long k, unsigned long long n) {
+    const int t = threadIdx.x;
+    if (t == 0) {
+        sel->prefix[0] = sel->prefix[1] = 0;
+        sel->rank[0] = k;
+        sel->rank[1] = n - 1 - k;
+    }
+    for (int i = t; i < 512; i += blockDim.x) (&sel->hist[0][0])[i] = 0;
+}
+
+template <int DT>
+__device__ __forceinline__ unsigned load_key(const char *row, int x) {
+    if (DT == 0) return key_u8(__ldg(reinterpret_cast<const unsigned char *>(row) + x));
+    if (DT == 1) return key_u16(__ldg(reinterpret_cast<const unsigned short *>(row) + x));
+    return key_f32(__ldg(reinterpret_cast<const float *>(row) + x));
+}
+
+// Pass PASS of the select: BITS = key width.  Pixels are visited by a
+// grid-stride loop over (row, column).
+template <int DT, int BITS>
+__global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, long long pitch,
+                                                int pass, SelState *sel) {
+    __shared__ unsigned h[2][256];
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int shift = BITS - 8 * (pass + 1);
+    const unsigned p0 = sel->prefix[0], p1 = sel->prefix[1];
+    const bool first = (pass == 0);
+    const int lane = threadIdx.x & 31;
+    // rows are spread over blocks, columns over the block's threads; the
+    // column loop bound is uniform so every lane reaches the warp votes
+    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+        const char *row = img + (long long)y * pitch;
+        for (int x0 = 0; x0 < W; x0 += blockDim.x) {
+            const int x = x0 + threadIdx.x;
+            const bool valid = x < W;
+            const unsigned key = valid ? load_key<DT>(row, x) : 0u;
+            const unsigned digit = (key >> shift) & 0xffu;
+            const unsigned hi = first ? 0u : (key >> (shift + 8));
+            const bool t0 = valid && (first || hi == p0);
+            const bool t1 = valid && !first && hi == p1;
+            // warp-aggregated increments: one shared atomic per distinct digit
+            const unsigned m0 = __match_any_sync(0xffffffffu, t0 ? (int)digit : -1);
+            if (t0 && lane == __ffs(m0) - 1) atomicAdd(&h[0][digit], __popc(m0));
+            const unsigned m1 = __match_any_sync(0xffffffffu, t1 ? (int)digit : -1);
+            if (t1 && lane == __ffs(m1) - 1) atomicAdd(&h[1][digit], __popc(m1));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+        const unsigned v = (&h[0][0])[i];
+        if (v) atomicAdd(&(&sel->hist[0][0])[i], v);
+    }
+}
+
+// Pick the digit holding each target's remaining rank; after the last pass
+// turn the two keys into the stretch parameters.
+template <int DT, int BITS>
+__global__ void sel_pick(int pass, SelState *sel, MhfdStretch *st) {
+    __shared__ unsigned cum[2][256];
+    __shared__ unsigned pick[2];
+    const int t = threadIdx.x;  // 256 threads
+    const bool first = (pass == 0);
+    for (int g = 0; g < 2; ++g) cum[g][t] = sel->hist[first ? 0 : g][t];
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {  // inclusive scan (Hillis-Steele)
+        unsigned a0 = 0, a1 = 0;
+        if (t >= o) {
+            a0 = cum[0][t - o];
+            a1 = cum[1][t - o];
+        }
+        __syncthreads();
+        cum[0][t] += a0;
+        cum[1][t] += a1;
+        __syncthreads();
+    }
+    for (int g = 0; g < 2; ++g) {
+        const unsigned long long r = sel->rank[g];
+        const unsigned long long below = t ? cum[g][t - 1] : 0ull;
+        if (r >= below && r < (unsigned long long)cum[g][t]) pick[g] = (unsigned)t;
+    }
+    __syncthreads();
+    if (t < 2) {
+        const unsigned d = pick[t];
+        const unsigned long long below = d ? cum[t][d - 1] : 0ull;
+        sel->rank[t] -= below;
+        sel->prefix[t] = (sel->prefix[t] << 8) | d;
+    }
+    __syncthreads();
+    sel->hist[0][t] = 0;
+    sel->hist[1][t] = 0;
+    if (t == 0 && 8 * (pass + 1) == BITS) {
+        const unsigned klo = sel->prefix[0], khi = sel->prefix[1];
+        MhfdStretch s;
+        if (DT == 2) {
+            s.lo = unkey_f32(klo);
+            s.hi = unkey_f32(khi);
+            s.lo_i = s.hi_i = 0;
+        } else {
+            s.lo_i = (int)klo;
+            s.hi_i = (int)khi;
+            s.lo = (float)klo;
+            s.hi = (float)khi;
+        }
+        s.constant = (s.hi == s.lo) ? 1 : 0;
+        s.inv = s.constant ? 0.0f : 1.0f / (s.hi - s.lo);
+        s.off = s.constant ? 0.0f : -0.5f;
+        s.pad = 0;
+        *st = s;
+    }
+}
+
+template <int DT, int BITS>
+int run_select(const void *img, int H, int W, long long pitch, SelState *sel, MhfdStretch *st,
+               cudaStream_t s) {
+    int dev = 0, sms = 0;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int grid = H < sms * 8 ? H : sms * 8;
+    if (grid < 1) grid = 1;
+    for (int pass = 0; pass < BITS / 8; ++pass) {
+        sel_hist<DT, BITS><<<grid, 256, 0, s>>>(reinterpret_cast<const char *>(img), H, W, pitch,
+                                               pass, sel);
+        sel_pick<DT, BITS><<<1, 256, 0, s>>>(pass, sel, st);
+    }
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
+
+}  // namespace
+
+int enqueue_stretch(const void *img, int dtype, int H, int W, long long pitch, long long k,
+                    SelState *sel, MhfdStretch *st, cudaStream_t s) {
+    const unsigned long long n = (unsigned long long)H * (unsigned long long)W;
+    sel_init<<<1, 256, 0, s>>>(sel, (unsigned long long)k, n);
+    MHFD_CUDA(cudaGetLastError());
+    if (dtype == MHFD_U8) return run_select<0, 8>(img, H, W, pitch, sel, st, s);
+    if (dtype == MHFD_U16) return run_select<1, 16>(img, H, W, pitch, sel, st, s);
+    return run_select<2, 32>(img, H, W, pitch, sel, st, s);
+}
+
+}  // namespace mhfd

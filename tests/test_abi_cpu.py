@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol include/mhfd.h declares, validates parameters before touching a
+device, and its host-only helpers (ladder, tile menu, kernel compilation)
+work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2108_12050_gb300 import _build, _native
+    _build.build_lib()
+    return _native
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "mhfd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mhfd_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(native):
+    lib = native.lib()
+    declared = _declared_symbols()
+    assert len(declared) >= 15
+    missing = [s for s in declared if not hasattr(lib, s)]
+    assert not missing, missing
+    assert sorted(native.EXPORTS) == declared
+
+
+def test_no_cpu_fallback_symbols(native):
+    # the product path has no host implementation of the method: the only
+    # host arithmetic is ladder/tap construction
+    out = os.popen("nm -D --defined-only %s" % native.LIB_PATH).read()
+    assert "oracle" not in out
+
+
+def test_version_and_defaults(native):
+    lib = native.lib()
+    assert b"sm_103a" in lib.mhfd_version()
+    p = native.Params()
+    lib.mhfd_default_params(ctypes.byref(p))
+    assert (p.n, p.t_min, p.t_max) == (10, 1.0, 10.0)
+    assert abs(p.threshold - 0.1) < 1e-7 and abs(p.overlap - 0.5) < 1e-7
+    assert p.truncate == 4.0 and p.clip_frac == 0.00175 and p.device == -1
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(n=0), -1), (dict(n=64), -1), (dict(t_min=0.0), -1), (dict(t_min=3, t_max=2), -1),
+    (dict(threshold=float("nan")), -1), (dict(overlap=-0.1), -1), (dict(clip_frac=0.5), -1),
+    (dict(nms=7), -1), (dict(max_candidates=0), -1), (dict(truncate=0.0), -1),
+    (dict(sigmas=[1.0, 3.0, 2.0] + [4.0] * 8), -1), (dict(t_min=1, t_max=200), -2),
+])
+def test_create_rejects_bad_parameters_before_any_device_work(native, kw, code):
+    p = native.make_params(**kw)
+    h = ctypes.c_void_p()
+    rc = native.lib().mhfd_create_detector(ctypes.byref(p), ctypes.byref(h))
+    assert rc == code, native.lib().mhfd_last_error()
+    assert not h.value
+    assert native.lib().mhfd_last_error()
+
+
+def test_null_arguments(native):
+    lib = native.lib()
+    assert lib.mhfd_create_detector(None, None) == -1
+    assert lib.mhfd_destroy_detector(None) == -1
+    assert lib.mhfd_detect(None, None, 0, 1, 1, 1, None) == -1
+    assert lib.mhfd_result_wait(None, None) == -1
+
+
+def test_tile_menu_fits_shared_memory(native):
+    for kw in (dict(n=10, t_min=1, t_max=10), dict(n=16, t_min=1, t_max=12),
+               dict(n=16, t_min=1, t_max=12, nms=1)):
+        menu = native.tile_configs(**kw)
+        assert len(menu) > 10
+        for tx2, ty2, rb, nt, ng in menu:
+            assert tx2 % 4 == 0 and ty2 % rb == 0 and nt % 32 == 0 and ng >= 1
+        chosen = native.chosen_tile(**kw)
+        assert chosen in menu
+
+
+def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
+    monkeypatch.setenv("MHFD_JIT_CACHE", str(tmp_path))
+    rc = native.precompile(n=2, t_min=1.0, t_max=1.5, nms=0, store=0)
+    assert rc == 0
+    files = os.listdir(tmp_path)
+    assert any(f.endswith(".cubin") for f in files)

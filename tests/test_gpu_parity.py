@@ -1,0 +1,277 @@
+"""CUDA path vs FP64 oracle on seeded synthetic images (through the C ABI).
+
+Sizes span several fused-kernel tiles and ragged tails; edge cases cover
+1-pixel-wide images, images narrower than the kernel radius, pitched rows,
+all three dtypes and a constant image."""
+import math
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import (ambiguous_26, ambiguous_paper, assert_stack_close,
+                         compare_feature_sets, conflict_components, layer_eps)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    torch.cuda.set_device(0)
+
+
+_DETS = {}
+
+
+def detector(**kw):
+    import paper_2108_12050_gb300 as mhfd
+    key = tuple(sorted((k, tuple(v) if isinstance(v, list) else v) for k, v in kw.items()))
+    if key not in _DETS:
+        _DETS[key] = mhfd.Detector(**kw)
+    return _DETS[key]
+
+
+def to_dev(img):
+    if img.dtype == np.uint16:
+        return torch.from_numpy(img.view(np.int16)).cuda()
+    return torch.from_numpy(img).cuda()
+
+
+def scene(seed, H, W, dtype="u8", sigma_d=0.0):
+    if dtype == "u8":
+        return synth.make_scene(seed, synth.config1_spec(sigma_d, H, W))
+    return synth.make_scene(seed, synth.config2_spec(sigma_d, H, W, dtype))
+
+
+def ref_stack(img, n, tmin, tmax):
+    lo, hi = oracle.stretch_bounds(img)
+    t = oracle.ladder(n, tmin, tmax)
+    return oracle.dog_stack(oracle.stretch(img, lo, hi), t), (lo, hi), t
+
+
+# ----------------------------------------------------------------- stretch
+
+@pytest.mark.parametrize("dtype,shape", [("u8", (96, 80)), ("u16", (130, 257)),
+                                         ("f32", (77, 61)), ("u8", (1, 1)), ("u16", (1, 300)),
+                                         ("u8", (300, 1)), ("u16", (512, 512))])
+def test_stretch_bounds_bit_exact(dtype, shape):
+    rng = np.random.default_rng(zlib.crc32(repr((dtype, shape)).encode()))
+    if dtype == "f32":
+        img = rng.normal(3.0, 2.0, shape).astype(np.float32)
+    elif dtype == "u8":
+        img = rng.integers(0, 256, shape).astype(np.uint8)
+    else:
+        img = rng.integers(0, 4096, shape).astype(np.uint16)
+    det = detector(n=4, t_min=1.0, t_max=4.0, threshold=0.1)
+    res = det(to_dev(img))
+    lo, hi = oracle.stretch_bounds(img)
+    assert (res.lo, res.hi) == (np.float32(lo), np.float32(hi))
+
+
+# ------------------------------------------------------------------- stack
+
+STACK_CASES = [
+    # (name, seed, H, W, dtype, n, tmin, tmax)
+    ("c1_ladder_multi_tile", 31, 150, 390, "u8", 10, 1.0, 10.0),
+    ("small_ladder_ragged", 32, 101, 203, "u8", 4, 1.0, 4.0),
+    ("u16_scene", 33, 140, 170, "u16", 4, 1.0, 4.0),
+    ("f32_scene", 34, 90, 100, "f32", 4, 1.0, 4.0),
+    ("narrower_than_radius", 35, 7, 30, "u8", 4, 1.0, 4.0),
+    ("one_pixel_wide", 36, 40, 1, "u8", 4, 1.0, 4.0),
+    ("one_pixel_high", 37, 1, 57, "u8", 4, 1.0, 4.0),
+]
+
+
+@pytest.mark.parametrize("case", STACK_CASES, ids=lambda c: c[0])
+def test_response_stack_within_tolerance(case):
+    name, seed, H, W, dtype, n, tmin, tmax = case
+    img = scene(seed, H, W, dtype)
+    det = detector(n=n, t_min=tmin, t_max=tmax, threshold=0.1)
+    D, M, A, res = det.debug_stack(to_dev(img))
+    D_ref, (lo, hi), t = ref_stack(img, n, tmin, tmax)
+    assert (res.lo, res.hi) == (np.float32(lo), np.float32(hi))
+    assert_stack_close(D.cpu().numpy(), D_ref, name)
+    M_ref = D_ref.max(axis=0)
+    eps = layer_eps(D_ref).max()
+    assert np.abs(M.cpu().numpy() - M_ref).max() <= eps
+    A_ref = D_ref.argmax(axis=0)
+    _, amb_scale, _ = ambiguous_paper(D_ref, 0.1)
+    A_gpu = A.cpu().numpy()
+    assert np.all((A_gpu == A_ref) | amb_scale)
+
+
+def test_pitched_rows_match_contiguous():
+    img = scene(38, 100, 120, "u8")
+    padded = np.zeros((100, 160), np.uint8)
+    padded[:, :120] = img
+    det = detector(n=4, t_min=1.0, t_max=4.0, threshold=0.1)
+    dev = to_dev(padded)[:, :120]
+    assert dev.stride(0) == 160
+    D1, _, _, r1 = det.debug_stack(dev)
+    D2, _, _, r2 = det.debug_stack(to_dev(img))
+    assert torch.equal(D1, D2)
+    assert np.array_equal(r1.blobs, r2.blobs)
+
+
+# ------------------------------------------------------------- detections
+
+def _features(arr):
+    return {(int(b["x"]), int(b["y"]), int(b["scale_idx"])) for b in arr}
+
+
+def _check_detection(img, n, tmin, tmax, thr, overlap, nms):
+    det = detector(n=n, t_min=tmin, t_max=tmax, threshold=thr, overlap=overlap, nms=nms,
+                   keep_candidates=True)
+    res = det(to_dev(img))
+    D_ref, (lo, hi), t = ref_stack(img, n, tmin, tmax)
+    mode = 0 if nms == "paper" else 1
+    ref = oracle.detect(img, n, tmin, tmax, threshold=thr, overlap=overlap, mode=mode)
+    got_c = _features(res.candidates)
+    want_c = set(zip(ref.x.tolist(), ref.y.tolist(), ref.i.tolist()))
+    if mode == 0:
+        amb, amb_scale, eps = ambiguous_paper(D_ref, thr)
+        is_amb = lambda f: amb[f[1], f[0]] or amb_scale[f[1], f[0]]  # noqa: E731
+        got_px = {(x, y) for x, y, _ in got_c}
+        want_px = {(x, y) for x, y, _ in want_c}
+        bad = [p for p in got_px ^ want_px if not amb[p[1], p[0]]]
+        assert not bad, bad[:10]
+        for x, y, i in got_c:
+            if (x, y) in want_px and not amb_scale[y, x]:
+                assert (x, y, i) in want_c
+    else:
+        amb, eps = ambiguous_26(D_ref, thr)
+        is_amb = lambda f: amb[f[2], f[1], f[0]]  # noqa: E731
+        compare_feature_sets(got_c, want_c, is_amb)
+    assert res.n_candidates == res.n_candidates_true == len(got_c)
+    # responses of common features within the stack tolerance
+    resp_ref = {(int(x), int(y), int(i)): r for x, y, i, r in zip(ref.x, ref.y, ref.i, ref.resp)}
+    for b in res.candidates:
+        key = (int(b["x"]), int(b["y"]), int(b["scale_idx"]))
+        if key in resp_ref:
+            assert abs(float(b["response"]) - resp_ref[key]) <= eps
+    # pruning: compare kept/dropped outside components touched by ambiguity
+    kept_got = _features(res.blobs)
+    kept_want = {f for f, k in zip(zip(ref.x.tolist(), ref.y.tolist(), ref.i.tolist()), ref.keep)
+                 if k}
+    feats = sorted(got_c | want_c)
+    radius = list(math.sqrt(2.0) * t[:n])
+    comp, pairs = conflict_components(feats, radius, overlap)
+    tainted = {comp[k] for k, f in enumerate(feats) if is_amb(f) or (f in got_c) != (f in want_c)}
+    resp_any = dict(resp_ref)
+    for b in res.candidates:
+        resp_any.setdefault((int(b["x"]), int(b["y"]), int(b["scale_idx"])), float(b["response"]))
+    for a, b in pairs:
+        fa, fb = feats[a], feats[b]
+        if fa[2] == fb[2] and abs(resp_any[fa] - resp_any[fb]) <= eps:
+            tainted.add(comp[a])
+    mism = [f for k, f in enumerate(feats)
+            if comp[k] not in tainted and ((f in kept_got) != (f in kept_want))]
+    assert not mism, mism[:10]
+    if not tainted:
+        assert res.n_blobs == ref.score
+    assert res.focus_score == res.n_blobs == len(kept_got)
+    per_scale = np.bincount([f[2] for f in kept_got], minlength=n)[:n] if kept_got else np.zeros(n)
+    assert np.array_equal(res.per_scale[:n], per_scale)
+    return res, ref
+
+
+@pytest.mark.parametrize("which", ["A", "B"])
+def test_config1_512_uint8_end_to_end(which):
+    a, b = synth.config1_pair(seed=1)
+    img = a if which == "A" else b
+    _check_detection(img, 10, 1.0, 10.0, 0.1, 0.5, "paper")
+
+
+def test_config1_local26_end_to_end():
+    a, _ = synth.config1_pair(seed=1, H=256, W=300)
+    _check_detection(a, 10, 1.0, 10.0, 0.1, 0.5, "local26")
+
+
+@pytest.mark.parametrize("shape,dtype", [((257, 383), "u16"), ((64, 64), "u8"),
+                                         ((33, 500), "u8"), ((120, 90), "f32")])
+def test_small_ladder_end_to_end(shape, dtype):
+    img = scene(40 + shape[0], shape[0], shape[1], dtype)
+    _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "paper")
+    _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "local26")
+
+
+@pytest.mark.parametrize("overlap", [0.0, 0.3, 1.0])
+def test_prune_overlap_settings(overlap):
+    a, _ = synth.config1_pair(seed=2, H=200, W=200)
+    _check_detection(a, 10, 1.0, 10.0, 0.1, overlap, "paper")
+
+
+def test_constant_image_has_no_features():
+    img = np.full((70, 90), 77, np.uint8)
+    det = detector(n=4, t_min=1.0, t_max=4.0, threshold=0.1)
+    res = det(to_dev(img))
+    assert res.lo == res.hi == 77.0
+    assert res.n_blobs == 0 and res.n_candidates_true == 0
+
+
+def test_overflow_reports_true_count():
+    a, _ = synth.config1_pair(seed=1)
+    full = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1)(to_dev(a))
+    small = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1, max_candidates=100)
+    res = small(to_dev(a))
+    assert res.overflow
+    assert res.n_candidates == 100
+    assert res.n_candidates_true == full.n_candidates_true > 100
+
+
+def test_results_are_deterministic():
+    img = scene(41, 300, 420, "u16")
+    det = detector(n=4, t_min=1.0, t_max=4.0, threshold=0.05)
+    r1 = det(to_dev(img))
+    r2 = det(to_dev(img))
+    assert np.array_equal(r1.blobs, r2.blobs)
+
+
+def test_host_entry_point_matches_device_entry_point():
+    a, _ = synth.config1_pair(seed=3, H=200, W=180)
+    det = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1)
+    r_dev = det(to_dev(a))
+    r_host = det.detect_host(a)
+    assert np.array_equal(r_dev.blobs, r_host.blobs)
+
+
+# -------------------------------------------------------------------- prune
+
+@pytest.mark.parametrize("seed,n,cluster,overlap", [(0, 3000, 0.0, 0.5), (1, 4000, 0.9, 0.5),
+                                                    (2, 2500, 0.95, 0.1), (3, 1, 0.0, 0.5),
+                                                    (4, 5000, 0.8, 0.0)])
+def test_prune_bit_exact_on_identical_inputs(seed, n, cluster, overlap):
+    H, W = 700, 900
+    x, y, i, resp = synth.random_candidates(seed, n, H, W, 10, cluster=cluster)
+    t = oracle.ladder(10, 1.0, 10.0)
+    radius = math.sqrt(2.0) * t[:10]
+    want = oracle.prune(x, y, i, resp.astype(np.float64), radius, overlap, W)
+    det = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1, overlap=overlap)
+    keep = det.prune(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(),
+                     torch.from_numpy(i).cuda(), torch.from_numpy(resp).cuda(), H, W)
+    torch.cuda.synchronize()
+    assert np.array_equal(keep.cpu().numpy(), want)
+
+
+# -------------------------------------------------------------- plain path
+
+def test_plain_path_matches_oracle():
+    a, _ = synth.config1_pair(seed=4, H=260, W=300)
+    det = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1, keep_candidates=True)
+    det.detect_plain(to_dev(a))
+    res = det.wait()
+    ref = oracle.detect(a, 10, 1.0, 10.0, threshold=0.1, overlap=0.5)
+    D_ref, _, _ = ref_stack(a, 10, 1.0, 10.0)
+    amb, _, _ = ambiguous_paper(D_ref, 0.1)
+    got = {(x, y) for x, y, _ in _features(res.candidates)}
+    want = set(zip(ref.x.tolist(), ref.y.tolist()))
+    bad = [p for p in got ^ want if not amb[p[1], p[0]]]
+    assert not bad, bad[:10]
+    fused = det(to_dev(a))
+    assert abs(fused.n_blobs - res.n_blobs) <= len(got ^ want) + 2
