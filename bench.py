@@ -1,0 +1,355 @@
+"""Throughput benchmark of the fused multi-scale feature detector (one GB300).
+
+Workload (one "step"): the 4096 x 4096 uint16 (12-bit) SEM-like tile scene
+(mean 2000, noise std 80, 20 000 dark blobs of radius 2-12 px, 300 membrane
+lines 2-5 px wide) at the five defocus levels sigma_d in {0, 1, 2, 4, 8};
+detector: 16 DoG layers over t = 1..12, FP32 compute, threshold 0.05, overlap
+prune 0.5, the paper's argmax / 3x3 max-pool rule.  Each step runs the whole
+hot path (stretch, scale-space stack, DoG, maxima, compaction, prune, score)
+on all five tiles, which are resident in device memory; together they are
+larger than L2, so consecutive steps do not hit in L2.
+
+Prints ONE JSON line.  `value` is whole-job Mpixel/s (all ranks); extra keys
+give p50/p99 ms per tile, the unfused plain path on the same tiles, the
+roofline of the fused kernel (FP32 FFMA issue bound), the FP64 CPU oracle on a
+bounded sample, the end-to-end rate through the host-buffer entry point, the
+SM clocks sampled during the timed region and the focus scores of the sweep.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_LAYERS, T_MIN, T_MAX, THR, OVERLAP = 16, 1.0, 12.0, 0.05, 0.5
+SIGMA_D = (0.0, 1.0, 2.0, 4.0, 8.0)
+H = W = 4096
+METRIC = "Mpixel/s"
+WORKLOAD = ("4096x4096 uint16 SEM-like tiles, defocus sweep sigma_d in {0,1,2,4,8} (one "
+            "step = 5 tiles), n=16 scales t=1..12, FP32, threshold 0.05, overlap prune 0.5, "
+            "paper argmax + 3x3 max-pool rule")
+
+
+def ladder_radii():
+    dt = (T_MAX - T_MIN) / N_LAYERS
+    t = [T_MIN + i * dt for i in range(N_LAYERS + 1)]
+    return t, [int(math.ceil(4.0 * x)) for x in t]
+
+
+def algorithmic_ops_per_px():
+    """FP32 instructions per output pixel of the method (one FFMA = 1):
+    two separable passes of 2R+1 taps per Gaussian level, one DoG op and
+    one max/argmax op per layer, and the 3x3 comparison."""
+    _, R = ladder_radii()
+    return sum(2 * (2 * r + 1) for r in R) + 2 * N_LAYERS + 8
+
+
+def nominal_alu_peak():
+    """FP32 FFMA lane-ops per second from unit counts and the maximum clock:
+    152 SMs x 128 FP32 lanes x 2.07 GHz."""
+    return 152 * 128 * 2.07e9
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(img, side=2048):
+    """The FP64 oracle as it stands on a bounded crop of one tile."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    crop = np.ascontiguousarray(img[:side, :side])
+    t0 = time.perf_counter()
+    oracle.detect(crop, N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP)
+    dt = time.perf_counter() - t0
+    return {"value": crop.size / dt / 1e6, "unit": METRIC, "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": "%dx%d crop of the sigma_d=0 tile, full method (stretch, 17-level "
+                      "stack, DoG, NMS, prune), %.1f s" % (side, side, dt)}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    img = synth.config2_tile(0.0)
+    side = int(os.environ.get("MHFD_REF_SIDE", "1024"))
+    crops = [np.ascontiguousarray(img[y:y + side, x:x + side])
+             for y in range(0, H, side) for x in range(0, W, side)]
+    for k in range(args.warmup):
+        oracle.detect(crops[k % len(crops)], N_LAYERS, T_MIN, T_MAX, threshold=THR,
+                      overlap=OVERLAP)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.detect(crops[(args.warmup + k) % len(crops)], N_LAYERS, T_MIN, T_MAX,
+                      threshold=THR, overlap=OVERLAP)
+        times.append(time.perf_counter() - t0)
+    px = side * side
+    value = px * len(times) / sum(times) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "%dx%d crops, one per step" % (side, side)},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.get_threads(),
+                             "kind": "oracle",
+                             "sample": "%dx%d crops of the sigma_d=0 tile per step" % (side, side)},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import synth
+    import paper_2108_12050_gb300 as mhfd
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # inputs: the sweep tiles, resident in HBM (uint16 bits held as int16)
+    host = [synth.config2_tile(sd) for sd in SIGMA_D]
+    tiles = [torch.from_numpy(h.view(np.int16)).cuda() for h in host]
+    stream = torch.cuda.current_stream()
+    # one detector per tile of the step, so that the five detections of a
+    # step are enqueued back to back and read afterwards (each detector owns
+    # its result buffers); they share one compiled kernel
+    dets = [mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP, nms="paper",
+                          timing=True) for _ in tiles]
+    det = dets[0]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    scores = [0.0] * len(tiles)
+    for _ in range(args.warmup):
+        for j, t in enumerate(tiles):
+            scores[j] = dets[j](t).focus_score
+
+    # ---- timed region: K steps of 5 tiles, events on the launching stream
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(tiles) + 1)]
+          for _ in range(args.steps)]
+    kernel_ms = []
+    launches_per_tile = 16  # stretch 5, fused 1, gather 2, prune 4, output 4
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            for j, t in enumerate(tiles):
+                dets[j].detect(t, stream)
+                ev[k][j + 1].record(stream)
+            for j in range(len(tiles)):
+                scores[j] = dets[j].wait().focus_score
+                kernel_ms.append(dets[j].last_timing()[0])
+        t_end.record(stream)
+        barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    per_tile = [ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(args.steps)
+                for j in range(len(tiles))]
+    if dist is not None:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    px_step = len(tiles) * H * W
+    value = world * args.steps * px_step / (total_ms * 1e-3) / 1e6
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the fused kernel (FP32 FFMA issue bound)
+    ops = algorithmic_ops_per_px() * H * W
+    k_avg = statistics.mean(kernel_ms)
+    achieved = ops / (k_avg * 1e-3) / 1e12
+    peak = nominal_alu_peak() / 1e12
+    probe = mhfd.probe_ffma_peak() / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "fused_detect_4096_u16_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("kernel_source_digest") == kernel_digest():
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 FFMA)",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_note": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal; no FP32 figure in "
+                         "MEASURED_PEAKS)", "probe_measured_peak": probe,
+            "frac_of_probe": achieved / probe, "ops_per_px": algorithmic_ops_per_px(),
+            "kernel_ms_avg": k_avg}
+
+    # ---- plain (unfused) path on the same tiles
+    plain = None
+    if not args.no_plain:
+        pt = []
+        for j, t in enumerate(tiles):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            det.detect_plain(t, stream)
+            det.wait()
+            e0.record(stream)
+            det.detect_plain(t, stream)
+            e1.record(stream)
+            det.wait()
+            pt.append(e0.elapsed_time(e1))
+        plain = {"value": H * W / (statistics.mean(pt) * 1e-3) / 1e6, "unit": METRIC,
+                 "p50_ms_per_tile": statistics.median(pt), "tiles": len(pt)}
+
+    # ---- end to end through the host-buffer entry point (pinned host tiles)
+    pinned = []
+    for h in host:
+        pt_ = torch.empty(h.shape, dtype=torch.int16, pin_memory=True)
+        pt_.numpy()[:] = h.view(np.int16)
+        pinned.append(pt_.numpy().view(np.uint16))
+    res_bytes = 0
+    for h in pinned:
+        det.detect_host(h, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        for h in pinned:
+            r = det.detect_host(h, stream)
+            res_bytes += 8 * 40 + 24 * r.n_blobs
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": e2e_steps * px_step / e2e_dt / 1e6, "unit": METRIC,
+           "h2d_bytes_per_step": sum(h.nbytes for h in pinned),
+           "d2h_bytes_per_step": int(res_bytes / e2e_steps)}
+
+    cpu = None if args.no_cpu_baseline else cpu_baseline(host[0])
+
+    per_tile.sort()
+    p99 = per_tile[min(len(per_tile) - 1, int(math.ceil(0.99 * len(per_tile))) - 1)]
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (5 x 32 MiB tiles per step)",
+                   "tile": list(mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "p50_ms_per_tile": statistics.median(per_tile), "p99_ms_per_tile": p99,
+        "plain": plain,
+        "fused_vs_plain": (value / world / plain["value"]) if plain else None,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_per_tile * len(tiles) * args.steps,
+        "clocks": clk.summary(),
+        "focus_scores": dict(zip([str(s) for s in SIGMA_D], scores)),
+        "focus_monotone_drop": all(scores[j] > scores[j + 1] for j in range(len(scores) - 1)),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("detect_kernel.cuh", "mhfd_types.h"):
+        h.update(open(os.path.join(ROOT, "paper_2108_12050_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()
