@@ -42,6 +42,7 @@ struct mhfd_detector {
     std::vector<double> radius;  // blob radius per DoG layer, sqrt(2) t_i
     double radius_max = 0.0;
     TileConfig cfg;
+    LadderKey lk;
     Variant *var = nullptr;
     Variant *var_store = nullptr;
     std::vector<uint64_t> params;  // by-value parameter block of the fused kernel
@@ -125,6 +126,28 @@ int build_ladder(const mhfd_params &p, std::vector<double> *t, std::vector<int> 
         (*R)[i] = (int)r;
     }
     return MHFD_OK;
+}
+
+// §2.2: the sampled Gaussian of variance t^2 on k = -R..R, normalised in
+// FP64 and rounded to f32; only the symmetric half g[0..R] is kept.
+void make_taps(const std::vector<double> &t, const std::vector<int> &R, std::vector<float> *taps,
+               std::vector<int> *tapoff, std::vector<float> *tsc) {
+    const int nl = (int)t.size();
+    taps->clear();
+    tsc->clear();
+    tapoff->assign(nl + 1, 0);
+    for (int l = 0; l < nl; ++l) {
+        const int r = R[l];
+        std::vector<double> g(2 * r + 1);
+        double sum = 0.0;
+        for (int k = -r; k <= r; ++k) {
+            g[k + r] = std::exp(-((double)k * (double)k) / (2.0 * t[l] * t[l]));
+            sum += g[k + r];
+        }
+        (*tapoff)[l + 1] = (*tapoff)[l] + r + 1;
+        for (int k = 0; k <= r; ++k) taps->push_back((float)(g[k + r] / sum));
+        tsc->push_back((float)t[l]);
+    }
 }
 
 int validate_params(const mhfd_params &p) {
@@ -216,8 +239,8 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
     int tx, ty;
     const int n_tiles = tiles_of(d, H, W, &tx, &ty);
     const size_t nl = d->R.size();
-    const size_t need = sizeof(MhfdKHeader) + 4 * (nl + d->taps.size());
-    if ((size_t)v->param_bytes < need || v->ntaps != (int)d->taps.size())
+    (void)nl;
+    if ((size_t)v->param_bytes < sizeof(MhfdKHeader) || v->ntaps != (int)d->taps.size())
         return fail(MHFD_ERR_JIT, "kernel parameter layout mismatch");
     d->params.assign((v->param_bytes + 7) / 8 + 1, 0);
     char *pb = reinterpret_cast<char *>(d->params.data());
@@ -239,8 +262,6 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
     h.cap_tile = d->cap_tile;
     h.thr = d->p.threshold;
     std::memcpy(pb, &h, sizeof(h));
-    std::memcpy(pb + sizeof(h), d->tsc.data(), 4 * nl);
-    std::memcpy(pb + sizeof(h) + 4 * nl, d->taps.data(), 4 * d->taps.size());
     void *args[] = {pb};
     const CUresult r = drv().launchKernel(v->fn, (unsigned)n_tiles, 1, 1, (unsigned)v->cfg.nt, 1,
                                           1, (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
@@ -277,7 +298,7 @@ int detect_impl(mhfd_detector *d, const void *img, int dtype, int H, int W, size
     Variant *v = d->var;
     if (store) {
         if (!d->var_store) {
-            rc = get_variant(d->R, d->p.nms, 1, d->cfg, &d->var_store);
+            rc = get_variant(d->lk, d->p.nms, 1, d->cfg, &d->var_store);
             if (rc) return rc;
         }
         v = d->var_store;
@@ -307,7 +328,7 @@ void release(mhfd_detector *d) {
     void *dev_ptrs[] = {d->sel, d->st, d->cnt, d->d_radius, d->d_sigma, d->d_radius_f, d->d_taps,
                         d->d_tsc, d->d_tapoff, d->block_tmp, d->block_sum, d->cand, d->tile_count,
                         d->tile_off, d->stage, d->pb.cell_cnt, d->pb.cell_start, d->pb.cell_items,
-                        d->pb.state, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
+                        d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
     for (void *p : dev_ptrs)
         if (p) cudaFree(p);
     if (d->h_res) cudaFreeHost(d->h_res);
@@ -379,21 +400,10 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
     }
     DeviceGuard g(d->device);
     const int nl = d->n + 1;
-    // §2.2: sampled Gaussian of variance t^2 on k = -R..R, normalised in FP64
-    d->tapoff.assign(nl + 1, 0);
-    for (int l = 0; l < nl; ++l) {
-        const double t = d->t[l];
-        const int R = d->R[l];
-        std::vector<double> g(2 * R + 1);
-        double sum = 0.0;
-        for (int k = -R; k <= R; ++k) {
-            g[k + R] = std::exp(-((double)k * (double)k) / (2.0 * t * t));
-            sum += g[k + R];
-        }
-        d->tapoff[l + 1] = d->tapoff[l] + R + 1;
-        for (int k = 0; k <= R; ++k) d->taps.push_back((float)(g[k + R] / sum));
-        d->tsc.push_back((float)t);
-    }
+    make_taps(d->t, d->R, &d->taps, &d->tapoff, &d->tsc);
+    d->lk.R = d->R;
+    d->lk.taps = d->taps;
+    d->lk.tsc = d->tsc;
     for (int i = 0; i < d->n; ++i) d->radius.push_back(std::sqrt(2.0) * d->t[i]);
     d->radius_max = d->radius[d->n - 1];
     if ((rc = resolve_tile(d->R, d->p, &d->cfg))) {
@@ -403,7 +413,7 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
     const int TXY = (d->cfg.tx2 - 2) * (d->cfg.ty2 - 2);
     d->cap_tile = d->p.nms == MHFD_NMS_PAPER ? (TXY + 1) / 2 : TXY;
     d->cap = d->p.max_candidates;
-    if ((rc = get_variant(d->R, d->p.nms, 0, d->cfg, &d->var))) {
+    if ((rc = get_variant(d->lk, d->p.nms, 0, d->cfg, &d->var))) {
         delete d;
         return rc;
     }
@@ -420,7 +430,9 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
         (rc = dalloc(&d->d_tsc, nl)) || (rc = dalloc(&d->d_tapoff, nl + 1)) ||
         (rc = dalloc(&d->block_tmp, 256 + 64)) || (rc = dalloc(&d->block_sum, 256 + 1)) ||
         (rc = dalloc(&d->cand, (size_t)d->cap)) || (rc = dalloc(&d->pb.cell_items, (size_t)d->cap)) ||
-        (rc = dalloc(&d->pb.state, (size_t)d->cap))) {
+        (rc = dalloc(&d->pb.state, (size_t)d->cap)) ||
+        (rc = dalloc(&d->pb.nb_idx, (size_t)d->cap * 16)) ||
+        (rc = dalloc(&d->pb.nb_cnt, (size_t)d->cap))) {
         release(d);
         return rc;
     }
@@ -610,7 +622,13 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     std::vector<double> t;
     std::vector<int> R;
     if ((rc = build_ladder(*p, &t, &R))) return rc;
-    return mhfd_jit_precompile(R.data(), (int)R.size(), p->nms, store, p->tile_override);
+    LadderKey lk;
+    lk.R = R;
+    std::vector<int> tapoff;
+    make_taps(t, R, &lk.taps, &tapoff, &lk.tsc);
+    TileConfig cfg;
+    if ((rc = resolve_tile(R, *p, &cfg))) return rc;
+    return precompile_variant(lk, p->nms, store, cfg);
 }
 
 int mhfd_last_timing(mhfd_detector *d, float *ms_kernel, float *ms_total) {

@@ -1,10 +1,10 @@
 // Fused multi-scale feature detection kernel (sm_103a).
 //
-// Compiled at run time with NVRTC once per ladder shape: the host prepends
-// MHFD_* macros (number of Gaussian levels, their radii, tile geometry, mode)
-// so that every loop over scales and taps is fully unrolled and every tap is
-// a constant-bank operand of its FFMA.  The tap values themselves travel in
-// the by-value parameter block, so detectors with equal radii share a module.
+// Compiled at run time with NVRTC once per ladder: the host prepends MHFD_*
+// macros (number of Gaussian levels, their radii, the f32 tap values and
+// scale factors as exact hexadecimal literals, tile geometry, mode) so that
+// every loop over scales and taps is fully unrolled and every tap is an
+// immediate operand of its FFMA (no constant-memory load per multiply).
 //
 // One CTA produces the features of one (TY x TX) output tile:
 //   1. load the tile plus a halo of RMAX+1 pixels from global memory (reflect
@@ -56,6 +56,12 @@ MK_HD constexpr int kGB(int g) {
     constexpr int b[NGROUPS + 1] = {MHFD_GB};
     return b[g];
 }
+// f32 Gaussian taps (level l: g_l[0..R_l] at tapoff(l)) and DoG factors t_l;
+// immutable device tables whose loads fold to immediates at constant indices
+__device__ constexpr float kTapArr[] = {MHFD_TAPS};
+__device__ constexpr float kTscArr[] = {MHFD_TSC};
+#define kTap(i) (kTapArr[(i)])
+#define kTsc(i) (kTscArr[(i)])
 MK_HD constexpr int rmax_of() {
     int m = 0;
     for (int l = 0; l < NL; ++l) m = kR(l) > m ? kR(l) : m;
@@ -116,8 +122,6 @@ static_assert(kGB(0) == 0 && kGB(NGROUPS) == NL, "level groups");
 
 struct KParams {
     MhfdKHeader h;
-    float tsc[NL];      // t_l, the DoG scale factor of layer l (Eq. 2)
-    float taps[NTAPS];  // level l: g_l[0..R_l] at tapoff(l) (symmetric halves)
 };
 
 struct HState {
@@ -199,7 +203,7 @@ __device__ __forceinline__ void vcol(const KParams &p, const float *__restrict__
     for (int j = 0; j < ROWS; ++j) {
         const float x = colp[j * WEXTP];
 #pragma unroll
-        for (int l = 0; l < NG; ++l) acc[j][l] = p.taps[tapoff(LB + l)] * x;
+        for (int l = 0; l < NG; ++l) acc[j][l] = kTap(tapoff(LB + l)) * x;
     }
 #pragma unroll
     for (int k = 1; k <= RG; ++k) {
@@ -208,7 +212,7 @@ __device__ __forceinline__ void vcol(const KParams &p, const float *__restrict__
             const float sum = colp[(j + k) * WEXTP] + colp[(j - k) * WEXTP];
 #pragma unroll
             for (int l = 0; l < NG; ++l)
-                if (k <= kR(LB + l)) acc[j][l] = fmaf(p.taps[tapoff(LB + l) + k], sum, acc[j][l]);
+                if (k <= kR(LB + l)) acc[j][l] = fmaf(kTap(tapoff(LB + l) + k), sum, acc[j][l]);
         }
     }
 #pragma unroll
@@ -248,7 +252,7 @@ __device__ __forceinline__ void hacc(const KParams &p, float v, float (&a)[4]) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int k = M - u - R;
-        if (k >= -R && k <= R) a[u] = fmaf(p.taps[TO + (k < 0 ? -k : k)], v, a[u]);
+        if (k >= -R && k <= R) a[u] = fmaf(kTap(TO + (k < 0 ? -k : k)), v, a[u]);
     }
 }
 
@@ -295,7 +299,7 @@ __device__ __forceinline__ void hlevel(const KParams &p, const float *vrow, cons
         }
     } else {
         constexpr int I = (L > 0 ? L - 1 : 0);
-        const float ts = p.tsc[I];
+        const float ts = kTsc(I);
         float d[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {

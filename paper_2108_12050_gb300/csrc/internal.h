@@ -71,14 +71,23 @@ struct Variant {
     TileConfig cfg;
 };
 
+// The ladder as the fused kernel is specialised on: radii, f32 taps (level
+// l: g_l[0..R_l] concatenated) and f32 DoG factors t_l.
+struct LadderKey {
+    std::vector<int> R;
+    std::vector<float> taps;
+    std::vector<float> tsc;
+};
+
 // Choose a tile configuration for the radii and mode (built-in heuristic).
 bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why);
 // Enumerate the configurations offered to the autotuner.
 std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode);
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c);
 // Compile (or fetch from cache) the fused kernel for this ladder/config.
-int get_variant(const std::vector<int> &R, int mode, int store, const TileConfig &cfg,
-                Variant **out);
+int get_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg, Variant **out);
+// Compile into the on-disk cache only (no GPU needed).
+int precompile_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg);
 
 // -------------------------------------------------- post-processing kernels
 struct Counters {
@@ -102,6 +111,8 @@ struct PruneBuffers {
     int *cell_start = nullptr;    // ncells + 1
     int *cell_items = nullptr;    // cap
     int *state = nullptr;         // cap
+    int *nb_idx = nullptr;        // cap * 16 conflicting higher-priority neighbours
+    int *nb_cnt = nullptr;        // cap (-1: more than 16, rescan)
     size_t ncells_cap = 0;
 };
 
@@ -135,9 +146,5 @@ int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
 int probe_ffma(cudaStream_t s, double *ops_per_s);
 
 }  // namespace mhfd
-
-// Compile one fused-kernel variant into the on-disk cache (no GPU needed).
-extern "C" int mhfd_jit_precompile(const int32_t *R, int32_t nl, int32_t mode, int32_t store,
-                                   int32_t tile_index);
 
 #endif  // MHFD_INTERNAL_H

@@ -64,10 +64,23 @@ std::string join(const std::vector<int> &v) {
     return o.str();
 }
 
-std::string make_source(const std::vector<int> &R, int mode, int store, const TileConfig &c) {
+std::string join_f(const std::vector<float> &v) {
+    std::string o;
+    char buf[64];
+    for (size_t i = 0; i < v.size(); ++i) {
+        std::snprintf(buf, sizeof(buf), "%s%af", i ? "," : "", (double)v[i]);
+        o += buf;
+    }
+    return o;
+}
+
+std::string make_source(const LadderKey &lk, int mode, int store, const TileConfig &c) {
+    const std::vector<int> &R = lk.R;
     std::ostringstream o;
     o << "#define MHFD_NL " << R.size() << "\n"
       << "#define MHFD_RLIST " << join(R) << "\n"
+      << "#define MHFD_TAPS " << join_f(lk.taps) << "\n"
+      << "#define MHFD_TSC " << join_f(lk.tsc) << "\n"
       << "#define MHFD_NGROUPS " << (c.gb.size() - 1) << "\n"
       << "#define MHFD_GB " << join(c.gb) << "\n"
       << "#define MHFD_TX2 " << c.tx2 << "\n"
@@ -270,12 +283,8 @@ bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::stri
     return found;
 }
 
-int get_variant(const std::vector<int> &R, int mode, int store, const TileConfig &cfg,
-                Variant **out) {
-    int dev = 0;
-    MHFD_CUDA(cudaGetDevice(&dev));
-    MHFD_CUDA(cudaFree(nullptr));  // make sure the primary context exists and is current
-    const std::string src = make_source(R, mode, store, cfg);
+namespace {
+std::string source_hash(const std::string &src) {
     std::string opts;
     for (const char *o : kOpts) opts += std::string(o) + " ";
     int ver_major = 0, ver_minor = 0;
@@ -283,9 +292,33 @@ int get_variant(const std::vector<int> &R, int mode, int store, const TileConfig
     char hbuf[32];
     std::snprintf(hbuf, sizeof(hbuf), "%016llx",
                   fnv1a(src + opts + std::to_string(ver_major) + "." + std::to_string(ver_minor)));
-    const std::string key = std::string(hbuf) + "@" + std::to_string(dev);
+    return hbuf;
+}
+}  // namespace
+
+int precompile_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg) {
+    if (smem_estimate(lk.R, mode, cfg) > kSmemLimit)
+        return fail(MHFD_ERR_UNSUPPORTED, "tile configuration exceeds shared memory");
+    const std::string src = make_source(lk, mode, store, cfg);
+    const std::string path = cache_dir() + "/" + source_hash(src) + ".cubin";
+    std::string cubin;
+    if (read_file(path, &cubin)) return MHFD_OK;
+    const int rc = compile_cubin(src, &cubin);
+    if (rc != MHFD_OK) return rc;
+    write_file_atomic(path, cubin);
+    return MHFD_OK;
+}
+
+int get_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg, Variant **out) {
+    const std::vector<int> &R = lk.R;
+    int dev = 0;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaFree(nullptr));  // make sure the primary context exists and is current
+    const std::string src = make_source(lk, mode, store, cfg);
+    const std::string hbuf = source_hash(src);
+    const std::string key = hbuf + "@" + std::to_string(dev);
     {
-        std::lock_guard<std::mutex> lk(g_mu);
+        std::lock_guard<std::mutex> guard(g_mu);
         auto it = g_variants.find(key);
         if (it != g_variants.end()) {
             *out = it->second;
@@ -328,7 +361,7 @@ int get_variant(const std::vector<int> &R, int mode, int store, const TileConfig
     if (v->smem_bytes > kSmemLimit) return fail(MHFD_ERR_UNSUPPORTED, "kernel shared memory too large");
     r = drv().funcSetAttribute(v->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, v->smem_bytes);
     if (r != CUDA_SUCCESS) return drv_fail(r, "cuFuncSetAttribute");
-    std::lock_guard<std::mutex> lk(g_mu);
+    std::lock_guard<std::mutex> guard(g_mu);
     auto it = g_variants.find(key);
     if (it != g_variants.end()) {  // another thread won the race
         drv().moduleUnload(v->mod);
@@ -342,38 +375,3 @@ int get_variant(const std::vector<int> &R, int mode, int store, const TileConfig
 }
 
 }  // namespace mhfd
-
-using namespace mhfd;
-
-// Compile a variant into the disk cache without touching any GPU (used by
-// the build step to warm the cache for the standard ladders).
-extern "C" int mhfd_jit_precompile(const int32_t *R, int32_t nl, int32_t mode, int32_t store,
-                                   int32_t tile_index) {
-    std::vector<int> r(R, R + nl);
-    TileConfig cfg;
-    std::string why;
-    if (tile_index <= 0) {
-        if (!choose_tile(r, mode, &cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
-    } else {
-        std::vector<TileConfig> menu = tile_menu(r, mode);
-        if (tile_index > (int)menu.size()) return fail(MHFD_ERR_INVALID_ARG, "tile index");
-        cfg = menu[tile_index - 1];
-    }
-    const std::string src = make_source(r, mode, store, cfg);
-    std::string opts;
-    for (const char *o : kOpts) opts += std::string(o) + " ";
-    int ver_major = 0, ver_minor = 0;
-    nvrtcVersion(&ver_major, &ver_minor);
-    char hbuf[32];
-    std::snprintf(hbuf, sizeof(hbuf), "%016llx",
-                  fnv1a(src + opts + std::to_string(ver_major) + "." + std::to_string(ver_minor)));
-    const std::string path = cache_dir() + "/" + hbuf + ".cubin";
-    std::string cubin;
-    if (read_file(path, &cubin)) return MHFD_OK;
-    const int rc = compile_cubin(src, &cubin);
-    if (rc != MHFD_OK) return rc;
-    write_file_atomic(path, cubin);
-    return MHFD_OK;
-}
-
-

@@ -57,31 +57,34 @@ __device__ __forceinline__ long long block_scan_excl_ll(long long v, long long *
 
 // ---------------------------------------------------------------- gather
 
+// inclusive block scan (kScanThreads threads); *tot gets the block total
+__device__ __forceinline__ long long block_scan_incl(long long v, long long *sh, long long *tot) {
+    long long tot_;
+    const long long ex = block_scan_excl_ll(v, sh, &tot_);
+    *tot = tot_;
+    return ex + v;
+}
+
 __global__ void __launch_bounds__(kScanThreads)
     gather_scan(const int *tile_count, int n_tiles, int cap_tile, long long cap, int *tile_off,
                 Counters *cnt) {
     __shared__ long long sh[32];
-    const int per = (n_tiles + blockDim.x - 1) / blockDim.x;
-    const int beg = min(n_tiles, (int)threadIdx.x * per);
-    const int end = min(n_tiles, beg + per);
-    long long stored = 0, truth = 0;
-    for (int t = beg; t < end; ++t) {
-        const int c = tile_count[t];
-        truth += c;
-        stored += c < cap_tile ? c : cap_tile;
-    }
-    long long tot_s, tot_t;
-    long long off = block_scan_excl_ll(stored, sh, &tot_s);
-    block_scan_excl_ll(truth, sh, &tot_t);
-    for (int t = beg; t < end; ++t) {
-        tile_off[t] = (int)off;
-        const int c = tile_count[t];
-        off += c < cap_tile ? c : cap_tile;
+    long long carry_s = 0, carry_t = 0;
+    for (int base = 0; base < n_tiles; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const int c = t < n_tiles ? tile_count[t] : 0;
+        const long long st = c < cap_tile ? c : cap_tile;
+        long long tot_s, tot_t;
+        const long long inc = block_scan_incl(st, sh, &tot_s);
+        block_scan_incl((long long)c, sh, &tot_t);
+        if (t < n_tiles) tile_off[t] = (int)(carry_s + inc - st);
+        carry_s += tot_s;
+        carry_t += tot_t;
     }
     if (threadIdx.x == 0) {
-        cnt->n_true = (unsigned long long)tot_t;
-        cnt->n_stored = (unsigned long long)(tot_s < cap ? tot_s : cap);
-        cnt->overflow = (tot_t > cnt->n_stored) ? 1 : 0;
+        cnt->n_true = (unsigned long long)carry_t;
+        cnt->n_stored = (unsigned long long)(carry_s < cap ? carry_s : cap);
+        cnt->overflow = (carry_t > (long long)cnt->n_stored) ? 1 : 0;
         cnt->n_blobs = 0;
         cnt->timeout = 0;
     }
@@ -113,19 +116,19 @@ __global__ void grid_count(const MhfdCand *cand, const Counters *cnt, int cs, in
 __global__ void __launch_bounds__(kScanThreads)
     grid_scan(int *cell_cnt, int ncells, int *cell_start) {
     __shared__ long long sh[32];
-    const int per = (ncells + blockDim.x - 1) / blockDim.x;
-    const int beg = min(ncells, (int)threadIdx.x * per);
-    const int end = min(ncells, beg + per);
-    long long s = 0;
-    for (int c = beg; c < end; ++c) s += cell_cnt[c];
-    long long tot;
-    long long off = block_scan_excl_ll(s, sh, &tot);
-    for (int c = beg; c < end; ++c) {
-        cell_start[c] = (int)off;
-        off += cell_cnt[c];
-        cell_cnt[c] = 0;  // reused as the fill cursor
+    long long carry = 0;
+    for (int base = 0; base < ncells; base += blockDim.x) {
+        const int c = base + threadIdx.x;
+        const long long v = c < ncells ? cell_cnt[c] : 0;
+        long long tot;
+        const long long inc = block_scan_incl(v, sh, &tot);
+        if (c < ncells) {
+            cell_start[c] = (int)(carry + inc - v);
+            cell_cnt[c] = 0;  // reused as the fill cursor
+        }
+        carry += tot;
     }
-    if (threadIdx.x == 0) cell_start[ncells] = (int)tot;
+    if (threadIdx.x == 0) cell_start[ncells] = (int)carry;
 }
 
 __global__ void grid_fill(const MhfdCand *cand, const Counters *cnt, int cs, int ncx,
@@ -174,10 +177,70 @@ __device__ __forceinline__ bool higher(const MhfdCand &b, const MhfdCand &a, int
     return (long long)b.y * W + b.x < (long long)a.y * W + a.x;
 }
 
+// For candidate j, the higher-priority candidates it conflicts with (overlap
+// above the threshold), found once by scanning the 3x3 cells around it.
+// Up to kMaxNb are listed; more mark the list as overflowed (-1) and the
+// settle loop then rescans the cells instead.
+constexpr int kMaxNb = 16;
+
+__device__ __forceinline__ bool conflicts(const MhfdCand &b, const MhfdCand &a, double rb,
+                                          double ra, double overlap) {
+    const double dx = (double)(a.x - b.x), dy = (double)(a.y - b.y);
+    const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+    return lens_overlap(rb, ra, d) > overlap;
+}
+
+__global__ void __launch_bounds__(256)
+    prune_neighbors(const MhfdCand *cand, const Counters *cnt, int cs, int ncx, int ncy,
+                    const int *cell_start, const int *items, const double *radius,
+                    double overlap, int W, int *nb_idx, int *nb_cnt, int *state) {
+    const long long n = (long long)cnt->n_stored;
+    for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < n;
+         jj += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)jj;
+        const MhfdCand a = cand[j];
+        const double ra = radius[a.i];
+        const int cx = a.x / cs, cy = a.y / cs;
+        int found = 0;
+        for (int gy = max(0, cy - 1); gy <= min(ncy - 1, cy + 1); ++gy)
+            for (int gx = max(0, cx - 1); gx <= min(ncx - 1, cx + 1); ++gx) {
+                const int c = gy * ncx + gx;
+                for (int p = cell_start[c]; p < cell_start[c + 1]; ++p) {
+                    const int b = items[p];
+                    if (b == j) continue;
+                    const MhfdCand cb = cand[b];
+                    if (!higher(cb, a, W)) continue;
+                    // overlap is zero unless the centres are closer than r1 + r2
+                    // (conservative: exact ties go to the full test below)
+                    const int ddx = a.x - cb.x, ddy = a.y - cb.y;
+                    const double rs = __dadd_rn(radius[cb.i], ra);
+                    if ((double)(ddx * ddx + ddy * ddy) > __dmul_rn(rs, rs) * (1.0 + 1e-9) + 1e-9)
+                        continue;
+                    if (!conflicts(cb, a, radius[cb.i], ra, overlap)) continue;
+                    if (found < kMaxNb) nb_idx[(long long)j * kMaxNb + found] = b;
+                    ++found;
+                }
+            }
+        nb_cnt[j] = found <= kMaxNb ? found : -1;
+        state[j] = found == 0 ? 1 : 0;
+    }
+}
+
 // 0 = undecided, 1 = kept, 2 = dropped
 __device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
                       const int *cell_start, const int *items, const double *radius,
-                      double overlap, int W, const volatile int *state) {
+                      double overlap, int W, const int *nb_idx, const int *nb_cnt,
+                      const volatile int *state) {
+    const int m = nb_cnt[j];
+    if (m >= 0) {
+        bool waiting = false;
+        for (int q = 0; q < m; ++q) {
+            const int s = state[nb_idx[(long long)j * kMaxNb + q]];
+            if (s == 1) return 2;
+            if (s == 0) waiting = true;
+        }
+        return waiting ? 0 : 1;
+    }
     const MhfdCand a = cand[j];
     const double ra = radius[a.i];
     const int cx = a.x / cs, cy = a.y / cs;
@@ -192,9 +255,7 @@ __device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
                 if (!higher(cb, a, W)) continue;
                 const int s = state[b];
                 if (s == 2) continue;
-                const double dx = (double)(a.x - cb.x), dy = (double)(a.y - cb.y);
-                const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-                if (!(lens_overlap(radius[cb.i], ra, d) > overlap)) continue;
+                if (!conflicts(cb, a, radius[cb.i], ra, overlap)) continue;
                 if (s == 1) return 2;
                 waiting = true;
             }
@@ -205,7 +266,8 @@ __device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
 __global__ void __launch_bounds__(256)
     lfmis_kernel(const MhfdCand *cand, Counters *cnt, int cs, int ncx, int ncy,
                  const int *cell_start, const int *items, const double *radius, double overlap,
-                 int W, int *state, long long max_sweeps, unsigned long long max_ns) {
+                 int W, const int *nb_idx, const int *nb_cnt, int *state, long long max_sweeps,
+                 unsigned long long max_ns) {
     // Every thread settles its own candidates; a candidate waits only on
     // higher-priority ones, so the highest undecided candidate can always be
     // settled and the sweeps end.  The waits are bounded in count and time;
@@ -222,14 +284,14 @@ __global__ void __launch_bounds__(256)
         for (long long j = g0; j < n; j += gs) {
             if (vs[j] != 0) continue;
             const int r = settle((int)j, cand, cs, ncx, ncy, cell_start, items, radius, overlap,
-                                 W, vs);
+                                 W, nb_idx, nb_cnt, vs);
             if (r == 0)
                 pending = true;
             else
                 vs[j] = r;
         }
         if (!pending) break;
-        __nanosleep(200);
+        __nanosleep(100);
         if ((sweep & 63) == 63 && globaltimer_ns() - t0 > max_ns) break;
     }
     if (pending) atomicExch(&cnt->timeout, 1);
@@ -279,21 +341,29 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-__global__ void out_scan(int *block_cnt, const double *block_sum, int nb, Counters *cnt,
-                         double *sum_out, int *per_scale) {
-    if (threadIdx.x == 0) {
-        long long o = 0;
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            const int c = block_cnt[b];
-            block_cnt[b] = (int)o;
-            o += c;
-            s += block_sum[b];
-        }
-        cnt->n_blobs = (unsigned long long)o;
-        *sum_out = s;
+// nb = 256 blocks: one thread per block count; the response sum is added in
+// block order by a fixed tree (deterministic)
+__global__ void __launch_bounds__(256)
+    out_scan(int *block_cnt, const double *block_sum, int nb, Counters *cnt, double *sum_out,
+             int *per_scale) {
+    __shared__ long long sh[32];
+    __shared__ double ss[256];
+    const int b = threadIdx.x;
+    const long long v = b < nb ? block_cnt[b] : 0;
+    ss[b] = b < nb ? block_sum[b] : 0.0;
+    long long tot;
+    const long long ex = block_scan_excl_ll(v, sh, &tot);
+    if (b < nb) block_cnt[b] = (int)ex;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (b < o) ss[b] += ss[b + o];
+        __syncthreads();
     }
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) per_scale[i] = 0;
+    if (b == 0) {
+        cnt->n_blobs = (unsigned long long)tot;
+        *sum_out = ss[0];
+    }
+    if (b < 64) per_scale[b] = 0;
 }
 
 __global__ void __launch_bounds__(256)
@@ -437,6 +507,9 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
     grid_scan<<<1, kScanThreads, 0, s>>>(pb->cell_cnt, ncells, pb->cell_start);
     grid_fill<<<sms * 4, 256, 0, s>>>(cand, cnt, cs, ncx, pb->cell_start, pb->cell_cnt,
                                       pb->cell_items, pb->state);
+    prune_neighbors<<<sms * 8, 256, 0, s>>>(cand, cnt, cs, ncx, ncy, pb->cell_start,
+                                            pb->cell_items, d_radius, overlap, W, pb->nb_idx,
+                                            pb->nb_cnt, pb->state);
     MHFD_CUDA(cudaGetLastError());
     int per_sm = 0;
     MHFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lfmis_kernel, 256, 0));
@@ -446,8 +519,8 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
     unsigned long long max_ns = 2000000000ull;  // 2 s of device time
     void *args[] = {(void *)&cand, (void *)&cnt, (void *)&cs, (void *)&ncx, (void *)&ncy,
                     (void *)&pb->cell_start, (void *)&pb->cell_items, (void *)&d_radius,
-                    (void *)&overlap, (void *)&W, (void *)&pb->state, (void *)&max_sweeps,
-                    (void *)&max_ns};
+                    (void *)&overlap, (void *)&W, (void *)&pb->nb_idx, (void *)&pb->nb_cnt,
+                    (void *)&pb->state, (void *)&max_sweeps, (void *)&max_ns};
     MHFD_CUDA(cudaLaunchCooperativeKernel((const void *)lfmis_kernel, grid, 256, args, 0, s));
     return MHFD_OK;
 }
@@ -464,7 +537,7 @@ int enqueue_output(const MhfdCand *cand, const int *state, const Counters *cnt_c
     int *per_scale = block_tmp + nb;
     double *sum = block_sum + nb;
     out_count<<<nb, 256, 0, s>>>(cand, state, cnt, block_tmp, block_sum);
-    out_scan<<<1, 64, 0, s>>>(block_tmp, block_sum, nb, cnt, sum, per_scale);
+    out_scan<<<1, 256, 0, s>>>(block_tmp, block_sum, nb, cnt, sum, per_scale);
     out_write<<<nb, 256, 0, s>>>(cand, state, cnt, block_tmp, d_sigma, d_radius_f, h_blobs_dev,
                                  h_cands_dev, per_scale);
     out_publish<<<1, 64, 0, s>>>(cnt, sum, per_scale, st, h_res_dev);

@@ -40,37 +40,72 @@ __device__ __forceinline__ unsigned load_key(const char *row, int x) {
     return key_f32(__ldg(reinterpret_cast<const float *>(row) + x));
 }
 
-// Pass PASS of the select: BITS = key width.  Pixels are visited by a
-// grid-stride loop over (row, column).
+// One pass of the select (BITS = key width).  Rows are spread over blocks;
+// each thread reads VEC consecutive pixels of a row per step (one 16-byte
+// load when the image is 16-byte aligned) and aggregates runs of equal
+// digits in registers before adding them to the block's shared histograms,
+// which are merged into the global histograms at the end.
+struct RunAcc {
+    unsigned cur = 0xffffffffu, n = 0;
+    __device__ __forceinline__ void add(unsigned d, unsigned *h) {
+        if (d == cur) {
+            ++n;
+        } else {
+            if (n) atomicAdd(&h[cur], n);
+            cur = d;
+            n = 1;
+        }
+    }
+    __device__ __forceinline__ void flush(unsigned *h) {
+        if (n) atomicAdd(&h[cur], n);
+        n = 0;
+    }
+};
+
 template <int DT, int BITS>
 __global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, long long pitch,
                                                 int pass, SelState *sel) {
+    constexpr int ES = DT == 0 ? 1 : (DT == 1 ? 2 : 4);
+    constexpr int VEC = 16 / ES;
     __shared__ unsigned h[2][256];
     for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
     const int shift = BITS - 8 * (pass + 1);
     const unsigned p0 = sel->prefix[0], p1 = sel->prefix[1];
     const bool first = (pass == 0);
-    const int lane = threadIdx.x & 31;
-    // rows are spread over blocks, columns over the block's threads; the
-    // column loop bound is uniform so every lane reaches the warp votes
+    const bool vec_ok = ((reinterpret_cast<unsigned long long>(img) | (unsigned long long)pitch) & 15ull) == 0;
+    RunAcc r0, r1;
+    auto take = [&](unsigned key) {
+        const unsigned digit = (key >> shift) & 0xffu;
+        const unsigned hi = first ? 0u : (key >> (shift + 8));
+        if (first || hi == p0) r0.add(digit, h[0]);
+        if (!first && hi == p1) r1.add(digit, h[1]);
+    };
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
         const char *row = img + (long long)y * pitch;
-        for (int x0 = 0; x0 < W; x0 += blockDim.x) {
-            const int x = x0 + threadIdx.x;
-            const bool valid = x < W;
-            const unsigned key = valid ? load_key<DT>(row, x) : 0u;
-            const unsigned digit = (key >> shift) & 0xffu;
-            const unsigned hi = first ? 0u : (key >> (shift + 8));
-            const bool t0 = valid && (first || hi == p0);
-            const bool t1 = valid && !first && hi == p1;
-            // warp-aggregated increments: one shared atomic per distinct digit
-            const unsigned m0 = __match_any_sync(0xffffffffu, t0 ? (int)digit : -1);
-            if (t0 && lane == __ffs(m0) - 1) atomicAdd(&h[0][digit], __popc(m0));
-            const unsigned m1 = __match_any_sync(0xffffffffu, t1 ? (int)digit : -1);
-            if (t1 && lane == __ffs(m1) - 1) atomicAdd(&h[1][digit], __popc(m1));
+        for (int x0 = threadIdx.x * VEC; x0 < W; x0 += blockDim.x * VEC) {
+            if (vec_ok && x0 + VEC <= W) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + (long long)x0 * ES));
+                const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (DT == 0) {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) take((w[e] >> (8 * b)) & 0xffu);
+                    } else if (DT == 1) {
+                        take(w[e] & 0xffffu);
+                        take(w[e] >> 16);
+                    } else {
+                        take(key_f32(__uint_as_float(w[e])));
+                    }
+                }
+            } else {
+                for (int x = x0; x < x0 + VEC && x < W; ++x) take(load_key<DT>(row, x));
+            }
         }
     }
+    r0.flush(h[0]);
+    r1.flush(h[1]);
     __syncthreads();
     for (int i = threadIdx.x; i < 512; i += blockDim.x) {
         const unsigned v = (&h[0][0])[i];
