@@ -56,12 +56,22 @@ MK_HD constexpr int kGB(int g) {
     constexpr int b[NGROUPS + 1] = {MHFD_GB};
     return b[g];
 }
-// f32 Gaussian taps (level l: g_l[0..R_l] at tapoff(l)) and DoG factors t_l;
-// immutable device tables whose loads fold to immediates at constant indices
-__device__ constexpr float kTapArr[] = {MHFD_TAPS};
-__device__ constexpr float kTscArr[] = {MHFD_TSC};
-#define kTap(i) (kTapArr[(i)])
-#define kTsc(i) (kTscArr[(i)])
+// f32 Gaussian taps (level l: g_l[0..R_l] at tapoff(l)) and DoG factors t_l.
+// Only ever evaluated in constant expressions (template-constant indices),
+// so every tap becomes an immediate operand of its FFMA.
+MK_HD constexpr float kTap(int i) {
+    constexpr float a[] = {MHFD_TAPS};
+    return a[i];
+}
+MK_HD constexpr float kTsc(int l) {
+    constexpr float a[] = {MHFD_TSC};
+    return a[l];
+}
+template <int I>
+__device__ __forceinline__ float tap() {
+    constexpr float v = kTap(I);
+    return v;
+}
 MK_HD constexpr int rmax_of() {
     int m = 0;
     for (int l = 0; l < NL; ++l) m = kR(l) > m ? kR(l) : m;
@@ -188,6 +198,40 @@ __device__ __forceinline__ void load_block(const KParams &p, const MhfdStretch &
 
 // ------------------------------------------------------- 2. vertical pass
 
+// Fold step K of the vertical pass for the levels L.. of group G: every
+// level whose radius reaches K takes tap K times the folded sum.
+template <int G, int K, int L>
+__device__ __forceinline__ void vlev(float sum, float *a) {
+    constexpr int LB = kGB(G);
+    constexpr int NG = kGB(G + 1) - LB;
+    if constexpr (L < NG) {
+        if constexpr (K <= kR(LB + L)) a[L] = fmaf(tap<tapoff(LB + L) + K>(), sum, a[L]);
+        vlev<G, K, L + 1>(sum, a);
+    }
+}
+
+template <int G, int L>
+__device__ __forceinline__ void vinit(float x, float *a) {
+    constexpr int LB = kGB(G);
+    constexpr int NG = kGB(G + 1) - LB;
+    if constexpr (L < NG) {
+        a[L] = tap<tapoff(LB + L)>() * x;
+        vinit<G, L + 1>(x, a);
+    }
+}
+
+template <int G, int ROWS, int K>
+__device__ __forceinline__ void vstep(const float *colp, float (*acc)[kGB(G + 1) - kGB(G)]) {
+    if constexpr (K <= kR(kGB(G + 1) - 1)) {
+#pragma unroll
+        for (int j = 0; j < ROWS; ++j) {
+            const float sum = colp[(j + K) * WEXTP] + colp[(j - K) * WEXTP];
+            vlev<G, K, 0>(sum, acc[j]);
+        }
+        vstep<G, ROWS, K + 1>(colp, acc);
+    }
+}
+
 // V_l(o0 + j, c) for the ROWS rows starting at tile row o0 and every level l
 // of group G.  Row o of the tile sits at row o + RMAX of the halo'd block.
 template <int G, int ROWS>
@@ -196,25 +240,11 @@ __device__ __forceinline__ void vcol(const KParams &p, const float *__restrict__
     constexpr int LB = kGB(G);
     constexpr int LE = kGB(G + 1);
     constexpr int NG = LE - LB;
-    constexpr int RG = kR(LE - 1);
     float acc[ROWS][NG];
     const float *colp = s_in + (o0 + RMAX) * WEXTP + c;
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-        const float x = colp[j * WEXTP];
-#pragma unroll
-        for (int l = 0; l < NG; ++l) acc[j][l] = kTap(tapoff(LB + l)) * x;
-    }
-#pragma unroll
-    for (int k = 1; k <= RG; ++k) {
-#pragma unroll
-        for (int j = 0; j < ROWS; ++j) {
-            const float sum = colp[(j + k) * WEXTP] + colp[(j - k) * WEXTP];
-#pragma unroll
-            for (int l = 0; l < NG; ++l)
-                if (k <= kR(LB + l)) acc[j][l] = fmaf(kTap(tapoff(LB + l) + k), sum, acc[j][l]);
-        }
-    }
+    for (int j = 0; j < ROWS; ++j) vinit<G, 0>(colp[j * WEXTP], acc[j]);
+    vstep<G, ROWS, 1>(colp, acc);
 #pragma unroll
     for (int l = 0; l < NG; ++l) {
         const int cc = c - (RMAX - kR(LB + l));
@@ -247,13 +277,19 @@ __device__ __forceinline__ void vpass(const KParams &p, const float *s_in, float
 
 // ----------------------------------------------------- 3. horizontal pass
 
+// value number M of the window feeds output U with tap |M - U - R|
+template <int R, int TO, int M, int U>
+__device__ __forceinline__ void hacc1(float v, float (&a)[4]) {
+    constexpr int k = M - U - R;
+    if constexpr (k >= -R && k <= R) a[U] = fmaf(tap<TO + (k < 0 ? -k : k)>(), v, a[U]);
+}
+
 template <int R, int TO, int M>
-__device__ __forceinline__ void hacc(const KParams &p, float v, float (&a)[4]) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int k = M - u - R;
-        if (k >= -R && k <= R) a[u] = fmaf(kTap(TO + (k < 0 ? -k : k)), v, a[u]);
-    }
+__device__ __forceinline__ void hacc(const KParams &, float v, float (&a)[4]) {
+    hacc1<R, TO, M, 0>(v, a);
+    hacc1<R, TO, M, 1>(v, a);
+    hacc1<R, TO, M, 2>(v, a);
+    hacc1<R, TO, M, 3>(v, a);
 }
 
 template <int R, int TO, int M4>
@@ -299,7 +335,7 @@ __device__ __forceinline__ void hlevel(const KParams &p, const float *vrow, cons
         }
     } else {
         constexpr int I = (L > 0 ? L - 1 : 0);
-        const float ts = kTsc(I);
+        constexpr float ts = kTsc(I);
         float d[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
