@@ -122,8 +122,10 @@ int mhfd_destroy_detector(mhfd_detector *det);
 int mhfd_detect(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H, int32_t W,
                 size_t pitch_bytes, void *stream);
 
-/* Blocks until the last detection enqueued on `det` has finished and fills
- * *out.  Returns the detection's status (MHFD_OK or MHFD_WARN_OVERFLOW) or an
+/* Blocks until the last detection enqueued on `det` has finished, copies its
+ * blob list (exactly n_blobs entries; and the candidate list when kept) from
+ * device memory into the detector's pinned host buffers and fills *out.
+ * Returns the detection's status (MHFD_OK or MHFD_WARN_OVERFLOW) or an
  * error. */
 int mhfd_result_wait(mhfd_detector *det, mhfd_result *out);
 

@@ -65,6 +65,7 @@ struct mhfd_detector {
     MhfdCand *stage = nullptr;
     size_t stage_cap = 0;        // entries
     PruneBuffers pb;
+    ConflictTable ct;
     // plain path scratch
     size_t plain_px = 0;
     float *pI = nullptr, *pT = nullptr, *pL = nullptr, *pM = nullptr, *pD = nullptr;
@@ -76,6 +77,9 @@ struct mhfd_detector {
     HostResult *h_res = nullptr, *h_res_dev = nullptr;
     mhfd_blob *h_blobs = nullptr, *h_blobs_dev = nullptr;
     mhfd_blob *h_cands = nullptr, *h_cands_dev = nullptr;
+    // device-side result lists, copied (count-exact) at result_wait
+    mhfd_blob *d_blobs = nullptr, *d_cands = nullptr;
+    bool copied = false;
     cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_k0 = nullptr, ev_k1 = nullptr,
                 ev_end = nullptr;
     bool pending = false;
@@ -277,16 +281,17 @@ int finish_pipeline(mhfd_detector *d, int n_tiles, int cap_tile, int H, int W, c
     int rc = enqueue_gather(d->tile_count, d->stage, n_tiles, cap_tile, d->cap, d->tile_off,
                             d->cand, d->cnt, s);
     if (rc) return rc;
-    rc = enqueue_prune(d->cand, d->cnt, d->cap, H, W, d->d_radius, d->radius_max,
+    rc = enqueue_prune(d->cand, d->cnt, d->cap, H, W, d->ct, d->radius_max,
                        (double)d->p.overlap, &d->pb, s);
     if (rc) return rc;
     rc = enqueue_output(d->cand, d->pb.state, d->cnt, d->cap, d->d_sigma, d->d_radius_f, 1,
-                        d->h_res_dev, d->h_blobs_dev, d->p.keep_candidates ? d->h_cands_dev : nullptr,
+                        d->h_res_dev, d->d_blobs, d->p.keep_candidates ? d->d_cands : nullptr,
                         d->st, d->block_tmp, d->block_sum, s);
     if (rc) return rc;
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_end, s));
     MHFD_CUDA(cudaEventRecord(d->ev_done, s));
     d->pending = true;
+    d->copied = false;
     return MHFD_OK;
 }
 
@@ -328,9 +333,10 @@ void release(mhfd_detector *d) {
     void *dev_ptrs[] = {d->sel, d->st, d->cnt, d->d_radius, d->d_sigma, d->d_radius_f, d->d_taps,
                         d->d_tsc, d->d_tapoff, d->block_tmp, d->block_sum, d->cand, d->tile_count,
                         d->tile_off, d->stage, d->pb.cell_cnt, d->pb.cell_start, d->pb.cell_items,
-                        d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
+                        d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->d_blobs, d->d_cands, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
     for (void *p : dev_ptrs)
         if (p) cudaFree(p);
+    free_conflict_table(&d->ct);
     if (d->h_res) cudaFreeHost(d->h_res);
     if (d->h_blobs) cudaFreeHost(d->h_blobs);
     if (d->h_cands) cudaFreeHost(d->h_cands);
@@ -432,7 +438,9 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
         (rc = dalloc(&d->cand, (size_t)d->cap)) || (rc = dalloc(&d->pb.cell_items, (size_t)d->cap)) ||
         (rc = dalloc(&d->pb.state, (size_t)d->cap)) ||
         (rc = dalloc(&d->pb.nb_idx, (size_t)d->cap * 16)) ||
-        (rc = dalloc(&d->pb.nb_cnt, (size_t)d->cap))) {
+        (rc = dalloc(&d->pb.nb_cnt, (size_t)d->cap)) ||
+        (rc = dalloc(&d->d_blobs, (size_t)d->cap)) ||
+        (d->p.keep_candidates && (rc = dalloc(&d->d_cands, (size_t)d->cap)))) {
         release(d);
         return rc;
     }
@@ -444,6 +452,11 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
         cudaMemcpy(d->d_tapoff, d->tapoff.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice)) {
         release(d);
         return fail(MHFD_ERR_CUDA, "uploading ladder tables failed");
+    }
+    if (d->p.overlap < 1.0f && (rc = build_conflict_table(d->d_radius, d->radius,
+                                                          (double)d->p.overlap, &d->ct))) {
+        release(d);
+        return rc;
     }
     void *hd = nullptr;
     if ((rc = pinned_alloc(reinterpret_cast<void **>(&d->h_res), &hd, sizeof(HostResult)))) {
@@ -500,6 +513,15 @@ int mhfd_result_wait(mhfd_detector *d, mhfd_result *out) {
     MHFD_CUDA(cudaEventSynchronize(d->ev_done));
     MHFD_CUDA(cudaGetLastError());
     const HostResult &h = *d->h_res;
+    if (!d->copied) {
+        const size_t nb = (size_t)(h.c.n_blobs < (unsigned long long)d->cap ? h.c.n_blobs : d->cap);
+        if (nb) MHFD_CUDA(cudaMemcpy(d->h_blobs, d->d_blobs, nb * sizeof(mhfd_blob),
+                                     cudaMemcpyDeviceToHost));
+        if (d->p.keep_candidates && h.c.n_stored)
+            MHFD_CUDA(cudaMemcpy(d->h_cands, d->d_cands, (size_t)h.c.n_stored * sizeof(mhfd_blob),
+                                 cudaMemcpyDeviceToHost));
+        d->copied = true;
+    }
     std::memset(out, 0, sizeof(*out));
     out->blobs = d->h_blobs;
     out->n_blobs = (int64_t)h.c.n_blobs;
@@ -574,7 +596,7 @@ int mhfd_prune(mhfd_detector *d, const int32_t *x, const int32_t *y, const int32
     cudaStream_t s = (cudaStream_t)stream;
     if (n == 0) return MHFD_OK;
     if ((rc = enqueue_pack(x, y, i, resp, n, H, W, d->n, d->cand, d->cnt, s))) return rc;
-    if ((rc = enqueue_prune(d->cand, d->cnt, d->cap, H, W, d->d_radius, d->radius_max,
+    if ((rc = enqueue_prune(d->cand, d->cnt, d->cap, H, W, d->ct, d->radius_max,
                             (double)d->p.overlap, &d->pb, s)))
         return rc;
     return enqueue_keep(d->pb.state, d->cnt, n, 1, keep, s);

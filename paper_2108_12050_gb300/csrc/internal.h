@@ -116,11 +116,23 @@ struct PruneBuffers {
     size_t ncells_cap = 0;
 };
 
+// Per-detector table of overlap decisions by (scale of kept blob, scale of
+// current blob, squared centre distance); see post.cu.
+struct ConflictTable {
+    int nl = 0;
+    const int *lim = nullptr;   // nl*nl: first d2 with zero overlap (0: pair unused)
+    const int *off = nullptr;   // nl*nl: word offset of the pair's bitset
+    const unsigned *tab = nullptr;
+};
+int build_conflict_table(const double *d_radius, const std::vector<double> &radius,
+                         double overlap, ConflictTable *ct);
+void free_conflict_table(ConflictTable *ct);
+
 int enqueue_gather(const int *tile_count, const MhfdCand *stage, int n_tiles, int cap_tile,
                    long long cap, int *tile_off, MhfdCand *cand, Counters *cnt,
                    cudaStream_t s);
 int enqueue_prune(const MhfdCand *cand, const Counters *cnt, long long cap, int H, int W,
-                  const double *d_radius, double radius_max, double overlap, PruneBuffers *pb,
+                  const ConflictTable &ct, double radius_max, double overlap, PruneBuffers *pb,
                   cudaStream_t s);
 int enqueue_output(const MhfdCand *cand, const int *state, const Counters *cnt, long long cap,
                    const float *d_sigma, const float *d_radius_f, int prune_on,

@@ -19,7 +19,8 @@
 //   mapped into the device address space.
 #include "internal.h"
 
-#include <cooperative_groups.h>
+#include <cmath>
+#include <vector>
 
 namespace mhfd {
 
@@ -177,29 +178,55 @@ __device__ __forceinline__ bool higher(const MhfdCand &b, const MhfdCand &a, int
     return (long long)b.y * W + b.x < (long long)a.y * W + a.x;
 }
 
+// Conflict table.  Radii depend only on the scale index and centres sit on
+// integer pixels, so whether a kept blob of scale ib overlaps a blob of scale
+// ia by more than the threshold depends only on (ib, ia, d2 = dx^2 + dy^2).
+// It is evaluated once per detector, for every d2 below the distance where
+// the circles separate, with the FP64 lens formula (same operation order as
+// the oracle) and stored as bits; the per-pair test in the prune is then
+// integer only.  Word w of pair (ib, ia) holds d2 = 32 w .. 32 w + 31.
+__global__ void conflict_table_kernel(const double *radius, int nl, const int *lim,
+                                      const int *off, double overlap, unsigned *tab) {
+    const int pair = blockIdx.y;
+    const int ib = pair / nl, ia = pair - ib * nl;
+    const int T = lim[pair];
+    const int nw = (T + 31) / 32;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+        unsigned bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int d2 = 32 * w + b;
+            if (d2 >= T) break;
+            const double d = __dsqrt_rn((double)d2);
+            if (lens_overlap(radius[ib], radius[ia], d) > overlap) bits |= 1u << b;
+        }
+        tab[off[pair] + w] = bits;
+    }
+}
+
+__device__ __forceinline__ bool conflict_bit(const MhfdCand &b, const MhfdCand &a,
+                                             const ConflictTable &ct) {
+    const int dx = a.x - b.x, dy = a.y - b.y;
+    const int d2 = dx * dx + dy * dy;
+    const int pair = b.i * ct.nl + a.i;
+    if (d2 >= __ldg(ct.lim + pair)) return false;
+    return (__ldg(ct.tab + __ldg(ct.off + pair) + (d2 >> 5)) >> (d2 & 31)) & 1u;
+}
+
 // For candidate j, the higher-priority candidates it conflicts with (overlap
 // above the threshold), found once by scanning the 3x3 cells around it.
 // Up to kMaxNb are listed; more mark the list as overflowed (-1) and the
 // settle loop then rescans the cells instead.
 constexpr int kMaxNb = 16;
 
-__device__ __forceinline__ bool conflicts(const MhfdCand &b, const MhfdCand &a, double rb,
-                                          double ra, double overlap) {
-    const double dx = (double)(a.x - b.x), dy = (double)(a.y - b.y);
-    const double d = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-    return lens_overlap(rb, ra, d) > overlap;
-}
-
 __global__ void __launch_bounds__(256)
     prune_neighbors(const MhfdCand *cand, const Counters *cnt, int cs, int ncx, int ncy,
-                    const int *cell_start, const int *items, const double *radius,
-                    double overlap, int W, int *nb_idx, int *nb_cnt, int *state) {
+                    const int *cell_start, const int *items, ConflictTable ct, int W,
+                    int *nb_idx, int *nb_cnt, int *state) {
     const long long n = (long long)cnt->n_stored;
     for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < n;
          jj += (long long)gridDim.x * blockDim.x) {
         const int j = (int)jj;
         const MhfdCand a = cand[j];
-        const double ra = radius[a.i];
         const int cx = a.x / cs, cy = a.y / cs;
         int found = 0;
         for (int gy = max(0, cy - 1); gy <= min(ncy - 1, cy + 1); ++gy)
@@ -210,13 +237,7 @@ __global__ void __launch_bounds__(256)
                     if (b == j) continue;
                     const MhfdCand cb = cand[b];
                     if (!higher(cb, a, W)) continue;
-                    // overlap is zero unless the centres are closer than r1 + r2
-                    // (conservative: exact ties go to the full test below)
-                    const int ddx = a.x - cb.x, ddy = a.y - cb.y;
-                    const double rs = __dadd_rn(radius[cb.i], ra);
-                    if ((double)(ddx * ddx + ddy * ddy) > __dmul_rn(rs, rs) * (1.0 + 1e-9) + 1e-9)
-                        continue;
-                    if (!conflicts(cb, a, radius[cb.i], ra, overlap)) continue;
+                    if (!conflict_bit(cb, a, ct)) continue;
                     if (found < kMaxNb) nb_idx[(long long)j * kMaxNb + found] = b;
                     ++found;
                 }
@@ -228,9 +249,8 @@ __global__ void __launch_bounds__(256)
 
 // 0 = undecided, 1 = kept, 2 = dropped
 __device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
-                      const int *cell_start, const int *items, const double *radius,
-                      double overlap, int W, const int *nb_idx, const int *nb_cnt,
-                      const volatile int *state) {
+                      const int *cell_start, const int *items, const ConflictTable &ct, int W,
+                      const int *nb_idx, const int *nb_cnt, const volatile int *state) {
     const int m = nb_cnt[j];
     if (m >= 0) {
         bool waiting = false;
@@ -242,7 +262,6 @@ __device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
         return waiting ? 0 : 1;
     }
     const MhfdCand a = cand[j];
-    const double ra = radius[a.i];
     const int cx = a.x / cs, cy = a.y / cs;
     bool waiting = false;
     for (int gy = max(0, cy - 1); gy <= min(ncy - 1, cy + 1); ++gy)
@@ -255,7 +274,7 @@ __device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
                 if (!higher(cb, a, W)) continue;
                 const int s = state[b];
                 if (s == 2) continue;
-                if (!conflicts(cb, a, radius[cb.i], ra, overlap)) continue;
+                if (!conflict_bit(cb, a, ct)) continue;
                 if (s == 1) return 2;
                 waiting = true;
             }
@@ -265,8 +284,8 @@ __device__ int settle(int j, const MhfdCand *cand, int cs, int ncx, int ncy,
 
 __global__ void __launch_bounds__(256)
     lfmis_kernel(const MhfdCand *cand, Counters *cnt, int cs, int ncx, int ncy,
-                 const int *cell_start, const int *items, const double *radius, double overlap,
-                 int W, const int *nb_idx, const int *nb_cnt, int *state, long long max_sweeps,
+                 const int *cell_start, const int *items, ConflictTable ct, int W,
+                 const int *nb_idx, const int *nb_cnt, int *state, long long max_sweeps,
                  unsigned long long max_ns) {
     // Every thread settles its own candidates; a candidate waits only on
     // higher-priority ones, so the highest undecided candidate can always be
@@ -283,8 +302,8 @@ __global__ void __launch_bounds__(256)
         pending = false;
         for (long long j = g0; j < n; j += gs) {
             if (vs[j] != 0) continue;
-            const int r = settle((int)j, cand, cs, ncx, ncy, cell_start, items, radius, overlap,
-                                 W, nb_idx, nb_cnt, vs);
+            const int r = settle((int)j, cand, cs, ncx, ncy, cell_start, items, ct, W, nb_idx,
+                                 nb_cnt, vs);
             if (r == 0)
                 pending = true;
             else
@@ -486,8 +505,47 @@ int enqueue_gather(const int *tile_count, const MhfdCand *stage, int n_tiles, in
     return MHFD_OK;
 }
 
+int build_conflict_table(const double *d_radius, const std::vector<double> &radius,
+                         double overlap, ConflictTable *ct) {
+    const int nl = (int)radius.size();
+    std::vector<int> lim(nl * nl, 0), off(nl * nl, 0);
+    int words = 0;
+    for (int ib = 0; ib < nl; ++ib)
+        for (int ia = 0; ia < nl; ++ia) {
+            const int pair = ib * nl + ia;
+            off[pair] = words;
+            if (ib < ia) continue;  // a kept, higher-priority blob never has a smaller scale
+            const double rs = radius[ib] + radius[ia];
+            lim[pair] = (int)std::ceil(rs * rs) + 2;  // overlap is 0 from here on
+            words += (lim[pair] + 31) / 32;
+        }
+    ct->nl = nl;
+    int *d_lim = nullptr, *d_off = nullptr;
+    unsigned *d_tab = nullptr;
+    MHFD_CUDA(cudaMalloc(&d_lim, sizeof(int) * nl * nl));
+    MHFD_CUDA(cudaMalloc(&d_off, sizeof(int) * nl * nl));
+    MHFD_CUDA(cudaMalloc(&d_tab, sizeof(unsigned) * (words > 0 ? words : 1)));
+    ct->lim = d_lim;
+    ct->off = d_off;
+    ct->tab = d_tab;
+    MHFD_CUDA(cudaMemcpy(d_lim, lim.data(), sizeof(int) * nl * nl, cudaMemcpyHostToDevice));
+    MHFD_CUDA(cudaMemcpy(d_off, off.data(), sizeof(int) * nl * nl, cudaMemcpyHostToDevice));
+    conflict_table_kernel<<<dim3(8, nl * nl), 128>>>(d_radius, nl, d_lim, d_off, overlap, d_tab);
+    MHFD_CUDA(cudaGetLastError());
+    MHFD_CUDA(cudaDeviceSynchronize());
+    return MHFD_OK;
+}
+
+void free_conflict_table(ConflictTable *ct) {
+    if (ct->lim) cudaFree((void *)ct->lim);
+    if (ct->off) cudaFree((void *)ct->off);
+    if (ct->tab) cudaFree((void *)ct->tab);
+    ct->lim = ct->off = nullptr;
+    ct->tab = nullptr;
+}
+
 int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, int H, int W,
-                  const double *d_radius, double radius_max, double overlap, PruneBuffers *pb,
+                  const ConflictTable &ct, double radius_max, double overlap, PruneBuffers *pb,
                   cudaStream_t s) {
     (void)cap;
     Counters *cnt = const_cast<Counters *>(cnt_c);
@@ -508,8 +566,8 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
     grid_fill<<<sms * 4, 256, 0, s>>>(cand, cnt, cs, ncx, pb->cell_start, pb->cell_cnt,
                                       pb->cell_items, pb->state);
     prune_neighbors<<<sms * 8, 256, 0, s>>>(cand, cnt, cs, ncx, ncy, pb->cell_start,
-                                            pb->cell_items, d_radius, overlap, W, pb->nb_idx,
-                                            pb->nb_cnt, pb->state);
+                                            pb->cell_items, ct, W, pb->nb_idx, pb->nb_cnt,
+                                            pb->state);
     MHFD_CUDA(cudaGetLastError());
     int per_sm = 0;
     MHFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lfmis_kernel, 256, 0));
@@ -517,10 +575,11 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
     const int grid = sms * (per_sm < 4 ? per_sm : 4);
     long long max_sweeps = 1ll << 24;
     unsigned long long max_ns = 2000000000ull;  // 2 s of device time
+    ConflictTable ctv = ct;
     void *args[] = {(void *)&cand, (void *)&cnt, (void *)&cs, (void *)&ncx, (void *)&ncy,
-                    (void *)&pb->cell_start, (void *)&pb->cell_items, (void *)&d_radius,
-                    (void *)&overlap, (void *)&W, (void *)&pb->nb_idx, (void *)&pb->nb_cnt,
-                    (void *)&pb->state, (void *)&max_sweeps, (void *)&max_ns};
+                    (void *)&pb->cell_start, (void *)&pb->cell_items, (void *)&ctv, (void *)&W,
+                    (void *)&pb->nb_idx, (void *)&pb->nb_cnt, (void *)&pb->state,
+                    (void *)&max_sweeps, (void *)&max_ns};
     MHFD_CUDA(cudaLaunchCooperativeKernel((const void *)lfmis_kernel, grid, 256, args, 0, s));
     return MHFD_OK;
 }

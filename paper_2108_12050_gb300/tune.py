@@ -1,0 +1,156 @@
+"""Autotuner of the fused kernel's tile configuration.
+
+The fused detection kernel is specialised per ladder and per tile shape
+(tile width/height including the 1-pixel NMS border, rows per step, threads
+per block, level groups).  The built-in heuristic picks a shape from a cost
+model; this module measures instead: it compiles a filtered menu of shapes in
+parallel (NVRTC, CPU processes), times each one's fused kernel with CUDA
+events on a synthetic tile of the workload, and records the winner per
+(ladder, mode, SM count) in a JSON table that ``Detector`` consults.
+
+    python -m paper_2108_12050_gb300.tune --n 16 --tmin 1 --tmax 12 --side 4096
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import multiprocessing as mp
+import os
+import statistics
+import sys
+import time
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+TABLE = os.path.join(PKG, "tuned_tiles.json")
+
+
+def ladder_key(n, t_min, t_max, nms, truncate=4.0):
+    return "n%d_t%g-%g_%s_tr%g" % (n, t_min, t_max, "paper" if nms in (0, "paper") else "local26",
+                                   truncate)
+
+
+def load_table():
+    try:
+        with open(TABLE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def lookup(n, t_min, t_max, nms, sms, truncate=4.0):
+    """Tuned tile index (1-based, for params.tile_override) or 0."""
+    ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate))
+    if not ent:
+        return 0
+    best = ent.get(str(sms)) or ent.get("any")
+    return int(best["tile_override"]) if best else 0
+
+
+def candidates(n, t_min, t_max, nms, limit=None):
+    """Balanced shapes of the menu: every horizontal item has a thread and the
+    vertical pass keeps most threads busy."""
+    from . import _native
+    menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms)
+    dt = (t_max - t_min) / n
+    import math
+    rmax = max(int(math.ceil(4.0 * (t_min + i * dt))) for i in range(n + 1))
+    seen, out = set(), []
+    for k, (tx2, ty2, rb, nt, ng) in enumerate(menu):
+        wext = tx2 + 2 * rmax
+        hitems = rb * tx2 // 4
+        if hitems > nt or hitems < 0.85 * nt:
+            continue
+        vutil = wext / (nt * -(-wext // nt))
+        if vutil < 0.75 or ty2 < 24:
+            continue
+        key = (tx2, ty2, rb, nt, ng)
+        if key in seen:
+            continue
+        seen.add(key)
+        out.append((k + 1, key))
+    return out[:limit] if limit else out
+
+
+def _compile_one(args):
+    n, t_min, t_max, nms, idx = args
+    sys.path.insert(0, os.path.dirname(PKG))
+    from paper_2108_12050_gb300 import _native
+    t0 = time.time()
+    try:
+        _native.precompile(n=n, t_min=t_min, t_max=t_max, nms=nms, tile_override=idx)
+        return idx, time.time() - t0, None
+    except Exception as e:  # a shape the compiler rejects is skipped
+        return idx, time.time() - t0, str(e)
+
+
+def precompile_all(n, t_min, t_max, nms, cands, workers=None):
+    ctx = mp.get_context("spawn")
+    workers = workers or (os.cpu_count() or 4)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+        return list(ex.map(_compile_one, [(n, t_min, t_max, nms, i) for i, _ in cands]))
+
+
+def measure(n, t_min, t_max, nms, threshold, img_dev, cands, reps=5):
+    import paper_2108_12050_gb300 as mhfd
+    res = []
+    for idx, shape in cands:
+        try:
+            det = mhfd.Detector(n, t_min, t_max, threshold=threshold, nms=nms, tile_override=idx,
+                                timing=True)
+        except Exception as e:
+            res.append((idx, shape, None, str(e)))
+            continue
+        det(img_dev)
+        ks = []
+        for _ in range(reps):
+            det(img_dev)
+            ks.append(det.last_timing()[0])
+        det.close()
+        res.append((idx, shape, statistics.median(ks), None))
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=16)
+    ap.add_argument("--tmin", type=float, default=1.0)
+    ap.add_argument("--tmax", type=float, default=12.0)
+    ap.add_argument("--nms", default="paper")
+    ap.add_argument("--threshold", type=float, default=0.05)
+    ap.add_argument("--side", type=int, default=4096)
+    ap.add_argument("--limit", type=int, default=0)
+    ap.add_argument("--write", action="store_true", help="record the winner in tuned_tiles.json")
+    args = ap.parse_args()
+    nms = 0 if args.nms == "paper" else 1
+    cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None)
+    t0 = time.time()
+    comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands)
+    print("compiled %d shapes in %.1f s" % (len(comp), time.time() - t0), flush=True)
+    bad = {i for i, _, e in comp if e}
+    cands = [c for c in cands if c[0] not in bad]
+
+    import numpy as np
+    import torch
+    sys.path.insert(0, os.path.dirname(PKG))
+    import synth
+    img = synth.config2_tile(0.0)[:args.side, :args.side].copy()
+    dev = torch.from_numpy(img.view(np.int16)).cuda()
+    res = measure(args.n, args.tmin, args.tmax, nms, args.threshold, dev, cands)
+    res.sort(key=lambda r: (r[2] is None, r[2] or 0))
+    for idx, shape, ms, err in res:
+        print("%4d %-28s %s" % (idx, shape, ("%.3f ms" % ms) if ms else err), flush=True)
+    best = res[0]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    print("best", best, "SMs", sms)
+    if args.write and best[2]:
+        tab = load_table()
+        ent = tab.setdefault(ladder_key(args.n, args.tmin, args.tmax, nms), {})
+        ent[str(sms)] = {"tile_override": best[0], "shape": list(best[1]), "ms": best[2],
+                         "side": args.side}
+        with open(TABLE, "w") as f:
+            json.dump(tab, f, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main()
