@@ -180,7 +180,14 @@ def main():
     ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="R",
+                    help="only run R detections of the sigma_d=0 tile (for ncu captures)")
+    ap.add_argument("--plain", action="store_true", help="with --profile-case: plain path")
+    ap.add_argument("--side", type=int, default=H, help="with --profile-case: crop side")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -341,6 +348,24 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def profile_case(args):
+    """A few detections of one workload tile, nothing else (ncu target)."""
+    import torch
+    import synth
+    import paper_2108_12050_gb300 as mhfd
+    torch.cuda.set_device(0)
+    img = synth.config2_tile(0.0)[:args.side, :args.side].copy()
+    dev = torch.from_numpy(img.view(np.int16)).cuda()
+    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP, nms="paper")
+    for _ in range(args.profile_case):
+        if args.plain:
+            det.detect_plain(dev)
+            r = det.wait()
+        else:
+            r = det(dev)
+    print("blobs", r.n_blobs, "candidates", r.n_candidates_true)
 
 
 def kernel_digest():

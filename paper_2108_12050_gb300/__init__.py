@@ -123,10 +123,18 @@ class Detector:
 
     def __init__(self, n=10, t_min=1.0, t_max=10.0, *, sigmas=None, threshold=0.1, overlap=0.5,
                  nms="paper", truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
-                 device=None, keep_candidates=False, tile_override=0, timing=False):
+                 device=None, keep_candidates=False, tile_override=None, timing=False):
         import torch
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
+        if tile_override is None:
+            # a measured tile shape for this ladder and GPU, if the autotuner
+            # recorded one; otherwise the library's built-in choice
+            tile_override = 0
+            if sigmas is None and device >= 0:
+                from . import tune
+                sms = torch.cuda.get_device_properties(device).multi_processor_count
+                tile_override = tune.lookup(n, t_min, t_max, nms, sms, truncate)
         self.n = int(n)
         self.device = device
         self._p = _n.make_params(n=n, t_min=t_min, t_max=t_max, sigmas=sigmas,

@@ -107,16 +107,38 @@ STANDARD_VARIANTS = [
 
 
 def _precompile_one(args):
-    n, tmin, tmax, nms, store = args
+    n, tmin, tmax, nms, store = args[:5]
+    tile = args[5] if len(args) > 5 else 0
     sys.path.insert(0, os.path.dirname(PKG))
     from paper_2108_12050_gb300 import _native
-    return _native.precompile(n=n, t_min=tmin, t_max=tmax, nms=nms, store=store)
+    return _native.precompile(n=n, t_min=tmin, t_max=tmax, nms=nms, store=store,
+                              tile_override=tile)
+
+
+def _tuned_variants():
+    """Variants the autotuner recorded (tuned_tiles.json), all GPU models."""
+    import json
+    import re
+    path = os.path.join(PKG, "tuned_tiles.json")
+    out = []
+    try:
+        tab = json.load(open(path))
+    except Exception:
+        return out
+    for key, ent in tab.items():
+        m = re.match(r"n(\d+)_t([0-9.e+-]+)-([0-9.e+-]+)_(paper|local26)_tr4$", key)
+        if not m:
+            continue
+        for best in ent.values():
+            out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)),
+                        0 if m.group(4) == "paper" else 1, 0, int(best["tile_override"])))
+    return out
 
 
 def warm(variants=None, workers=None):
     """Precompile fused-kernel variants into the cache (CPU only)."""
     build_lib()
-    variants = list(variants or STANDARD_VARIANTS)
+    variants = list(variants or (STANDARD_VARIANTS + _tuned_variants()))
     workers = workers or min(len(variants), os.cpu_count() or 4)
     ctx = mp.get_context("spawn")
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:

@@ -39,12 +39,24 @@ def load_table():
 
 
 def lookup(n, t_min, t_max, nms, sms, truncate=4.0):
-    """Tuned tile index (1-based, for params.tile_override) or 0."""
+    """Tuned tile index (1-based, for params.tile_override) or 0.  The
+    recorded shape must still be the menu's entry at that index (the menu is
+    a function of the library version), else the built-in choice is used."""
     ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate))
     if not ent:
         return 0
     best = ent.get(str(sms)) or ent.get("any")
-    return int(best["tile_override"]) if best else 0
+    if not best:
+        return 0
+    idx = int(best["tile_override"])
+    try:
+        from . import _native
+        menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms, truncate=truncate)
+        if idx < 1 or idx > len(menu) or list(menu[idx - 1]) != list(best["shape"]):
+            return 0
+    except Exception:
+        return 0
+    return idx
 
 
 def candidates(n, t_min, t_max, nms, limit=None):
