@@ -160,6 +160,27 @@ int mhfd_prune(mhfd_detector *det, const int32_t *d_x, const int32_t *d_y, const
                const float *d_resp, int64_t n_cand, int32_t H, int32_t W, uint8_t *d_keep,
                void *stream);
 
+/* Allocation-free variant of mhfd_prune.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory, such as
+ * code running in a host callback or a real-time thread that must not block
+ * on the allocator's implicit synchronisation, or a framework that owns every
+ * device allocation.  It needs no detector and calls no cudaMalloc/cudaFree:
+ * its working memory is one fixed file-scope device array of about 6.6 MB
+ * that every GPU which loads this library holds until the process exits.
+ * radius: host array of n_levels (1..64) blob radii, one per scale index
+ * (sqrt(2) t_i for the detector's ladder); overlap as in mhfd_params;
+ * d_x, d_y, d_i, d_resp, n_cand, H, W, d_keep as in mhfd_prune (entries
+ * outside the image or the ladder are clamped into it).  Limits: n_cand <=
+ * 65536 and ceil(W/c)*ceil(H/c) <= 65536 with c = ceil(2 max(radius)) + 1;
+ * larger calls return MHFD_ERR_INVALID_ARG and do nothing.  Asynchronous on
+ * `stream`.  All calls share the one array (each clears what must start at
+ * zero), so calls whose work overlaps on the GPU race: serialise them.  The
+ * first call on a device looks up the array's device address with that
+ * device current; make it before any stream capture. */
+int mhfd_prune_noalloc(const double *radius, int32_t n_levels, float overlap, const int32_t *d_x,
+                       const int32_t *d_y, const int32_t *d_i, const float *d_resp,
+                       int64_t n_cand, int32_t H, int32_t W, uint8_t *d_keep, void *stream);
+
 /* Tile configurations the fused kernel can be specialised with for the
  * ladder of `p` (autotuner menu): returns their count; if `desc` is not NULL
  * writes up to `cap` rows of five int32 (tile width and height including the
