@@ -270,15 +270,7 @@ def main():
     achieved = ops / (k_avg * 1e-3) / 1e12
     peak = nominal_alu_peak() / 1e12
     probe = mhfd.probe_ffma_peak() / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "fused_detect_4096_u16_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            if tj.get("kernel_source_digest") == kernel_digest():
-                traffic = tj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 FFMA)",
             "frac": achieved / peak, "traffic": traffic,
             "peak_note": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal; no FP32 figure in "
@@ -334,7 +326,7 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (5 x 32 MiB tiles per step)",
-                   "tile": list(mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)),
+                   "tile": tile_used(mhfd),
                    "parallelism": "replicas" if world > 1 else "single"},
         "p50_ms_per_tile": statistics.median(per_tile), "p99_ms_per_tile": p99,
         "plain": plain,
@@ -348,6 +340,19 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def tile_used(mhfd):
+    """The fused kernel's tile shape as the benchmark's Detector uses it."""
+    import torch
+    from paper_2108_12050_gb300 import tune
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    idx = tune.lookup(N_LAYERS, T_MIN, T_MAX, "paper", sms)
+    shape = mhfd.tile_configs(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)[idx - 1] if idx else \
+        mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)
+    return {"width": shape[0], "height": shape[1], "rows_per_step": shape[2],
+            "threads": shape[3], "level_groups": shape[4],
+            "source": "autotuned" if idx else "heuristic"}
 
 
 def profile_case(args):
@@ -366,6 +371,24 @@ def profile_case(args):
         else:
             r = det(dev)
     print("blobs", r.n_blobs, "candidates", r.n_candidates_true)
+
+
+def profiled_traffic():
+    """DRAM bytes per fused-kernel launch from the committed ncu summary, if
+    that summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fused_detect_4096_u16.md")
+    try:
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.strip().split(":")[0] in ("kernel_source_digest",
+                                                               "dram_bytes_per_launch"):
+                k, v = line.strip().split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("kernel_source_digest") == kernel_digest():
+            return int(fields["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
 
 
 def kernel_digest():
