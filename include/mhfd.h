@@ -129,6 +129,31 @@ int mhfd_detect(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H,
  * error. */
 int mhfd_result_wait(mhfd_detector *det, mhfd_result *out);
 
+/* Batch of n images (uneven sizes, mixed dtypes) in one go: per-image
+ * stretch selects run together (one launch per radix pass), ONE persistent
+ * launch of the fused kernel takes every tile of every image from a device
+ * work queue, then each image is gathered, pruned and compacted.  The whole
+ * sequence is captured in a CUDA graph the first time a batch shape (sizes,
+ * dtypes, pitches) is seen and replayed for later batches of that shape (the
+ * image pointers may change).  Arrays of n entries are host memory; d_imgs[j]
+ * is device memory, alive until the work completes.  Results of image j are
+ * bit-identical to a single mhfd_detect of it.  Read them with
+ * mhfd_result_wait_batch.  With params.timing set no graph is used.
+ * Errors: INVALID_ARG (per-image checks as mhfd_detect), CUDA, OOM. */
+int mhfd_detect_batch(mhfd_detector *det, int32_t n, const void *const *d_imgs,
+                      const int32_t *dtypes, const int32_t *H, const int32_t *W,
+                      const size_t *pitch_bytes, void *stream);
+
+/* Waits for the last batch and fills outs[0..n-1] (n must equal the batch
+ * size).  Blob lists point into detector-owned pinned memory valid until the
+ * next batch; candidate lists are not kept for batches.  Returns MHFD_OK,
+ * MHFD_WARN_OVERFLOW if any image overflowed, or an error. */
+int mhfd_result_wait_batch(mhfd_detector *det, mhfd_result *outs, int32_t n);
+
+/* 1 if the last batch ran from a captured CUDA graph, 0 if its kernels were
+ * launched directly. */
+int mhfd_batch_uses_graph(mhfd_detector *det);
+
 /* End-to-end convenience: h_img is HOST memory (pinned or pageable); the
  * image is copied to detector-owned device memory on `stream`, detected and
  * the results are waited for and written to *out.  Same errors as above. */

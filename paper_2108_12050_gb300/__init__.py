@@ -191,6 +191,31 @@ class Detector:
         _n.check(_n.lib().mhfd_detect_plain(self._h, ptr, code, H, W, pitch,
                                             _stream_handle(stream)))
 
+    def detect_batch(self, imgs, stream=None):
+        """Enqueue a batch of CUDA images (uneven sizes, mixed dtypes): one
+        persistent fused launch over all their tiles, replayed from a CUDA
+        graph for repeated batch shapes."""
+        n = len(imgs)
+        args = [self._img_args(t) for t in imgs]
+        ptrs = (ctypes.c_void_p * n)(*[a[0].value for a in args])
+        dts = (ctypes.c_int32 * n)(*[a[1] for a in args])
+        Hs = (ctypes.c_int32 * n)(*[a[2] for a in args])
+        Ws = (ctypes.c_int32 * n)(*[a[3] for a in args])
+        ps = (ctypes.c_size_t * n)(*[a[4] for a in args])
+        self._img_ref = list(imgs)
+        self._batch_n = n
+        _n.check(_n.lib().mhfd_detect_batch(self._h, n, ptrs, dts, Hs, Ws, ps,
+                                            _stream_handle(stream)))
+
+    def wait_batch(self):
+        n = self._batch_n
+        rs = (_n.Result * n)()
+        _n.check(_n.lib().mhfd_result_wait_batch(self._h, rs, n))
+        return [_to_result(rs[j], self.n) for j in range(n)]
+
+    def batch_uses_graph(self) -> bool:
+        return _n.lib().mhfd_batch_uses_graph(self._h) == 1
+
     def wait(self) -> DetectionResult:
         r = _n.Result()
         _n.check(_n.lib().mhfd_result_wait(self._h, ctypes.byref(r)))

@@ -4,6 +4,7 @@
 //   -> tile-ordered gather -> overlap prune -> compaction into pinned memory.
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -82,6 +83,27 @@ struct mhfd_detector {
     bool copied = false;
     cudaEvent_t ev_done = nullptr, ev_t0 = nullptr, ev_k0 = nullptr, ev_k1 = nullptr,
                 ev_end = nullptr;
+    // batches of images (mhfd_detect_batch)
+    struct Batch {
+        int cap = 0;                                   // images the arrays hold
+        MhfdJob *h_jobs = nullptr, *d_jobs = nullptr;  // job table (pinned + device)
+        long long *h_ranks = nullptr, *d_ranks = nullptr;
+        SelState *d_sels = nullptr;
+        MhfdStretch *d_sts = nullptr;
+        int *d_queue = nullptr;
+        HostResult *h_res = nullptr, *h_res_dev = nullptr;
+        unsigned long long *d_arena_n = nullptr;
+        mhfd_blob *d_arena = nullptr;
+        unsigned long long arena_cap = 0;
+        mhfd_blob *h_arena = nullptr;
+        size_t h_arena_cap = 0;
+        std::vector<long long> key;                    // shape of the captured graph
+        cudaGraphExec_t exec = nullptr;
+        bool graphs = true;
+        bool pending = false;
+        int n = 0;
+        bool copied = false;
+    } b;
     bool pending = false;
     bool timed = false;
 };
@@ -286,7 +308,7 @@ int finish_pipeline(mhfd_detector *d, int n_tiles, int cap_tile, int H, int W, c
     if (rc) return rc;
     rc = enqueue_output(d->cand, d->pb.state, d->cnt, d->cap, d->d_sigma, d->d_radius_f, 1,
                         d->h_res_dev, d->d_blobs, d->p.keep_candidates ? d->d_cands : nullptr,
-                        d->st, d->block_tmp, d->block_sum, s);
+                        d->st, d->block_tmp, d->block_sum, nullptr, 0, s);
     if (rc) return rc;
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_end, s));
     MHFD_CUDA(cudaEventRecord(d->ev_done, s));
@@ -337,6 +359,14 @@ void release(mhfd_detector *d) {
     for (void *p : dev_ptrs)
         if (p) cudaFree(p);
     free_conflict_table(&d->ct);
+    if (d->b.exec) cudaGraphExecDestroy(d->b.exec);
+    void *bdev[] = {d->b.d_jobs, d->b.d_ranks, d->b.d_sels, d->b.d_sts, d->b.d_queue,
+                    d->b.d_arena_n, d->b.d_arena};
+    for (void *p : bdev)
+        if (p) cudaFree(p);
+    void *bhost[] = {d->b.h_jobs, d->b.h_ranks, d->b.h_res, d->b.h_arena};
+    for (void *p : bhost)
+        if (p) cudaFreeHost(p);
     if (d->h_res) cudaFreeHost(d->h_res);
     if (d->h_blobs) cudaFreeHost(d->h_blobs);
     if (d->h_cands) cudaFreeHost(d->h_cands);
@@ -355,6 +385,125 @@ int resolve_tile(const std::vector<int> &R, const mhfd_params &p, TileConfig *cf
         return MHFD_OK;
     }
     if (!choose_tile(R, p.nms, cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+    return MHFD_OK;
+}
+
+
+// ------------------------------------------------------------------ batches
+
+int batch_reserve(mhfd_detector *d, int n, long long total_items, long long total_px,
+                  int max_h, int max_w) {
+    mhfd_detector::Batch &b = d->b;
+    int rc;
+    if (n > b.cap) {
+        if (b.h_jobs) cudaFreeHost(b.h_jobs);
+        if (b.h_ranks) cudaFreeHost(b.h_ranks);
+        if (b.h_res) cudaFreeHost(b.h_res);
+        b.h_jobs = nullptr;
+        b.h_ranks = nullptr;
+        b.h_res = nullptr;
+        MHFD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&b.h_jobs), sizeof(MhfdJob) * n, 0));
+        MHFD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&b.h_ranks), sizeof(long long) * n, 0));
+        void *hd = nullptr;
+        if ((rc = pinned_alloc(reinterpret_cast<void **>(&b.h_res), &hd, sizeof(HostResult) * n)))
+            return rc;
+        b.h_res_dev = reinterpret_cast<HostResult *>(hd);
+        if ((rc = dalloc(&b.d_jobs, n)) || (rc = dalloc(&b.d_ranks, n)) ||
+            (rc = dalloc(&b.d_sels, n)) || (rc = dalloc(&b.d_sts, n)))
+            return rc;
+        b.cap = n;
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        b.key.clear();
+    }
+    if (!b.d_queue && ((rc = dalloc(&b.d_queue, 1)) || (rc = dalloc(&b.d_arena_n, 1)))) return rc;
+    const unsigned long long want = (unsigned long long)(total_px / 32) > (unsigned long long)d->cap
+                                        ? (unsigned long long)(total_px / 32)
+                                        : (unsigned long long)d->cap;
+    if (want > b.arena_cap) {
+        if ((rc = dalloc(&b.d_arena, (size_t)want))) return rc;
+        b.arena_cap = want;
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        b.key.clear();
+    }
+    // per-tile slots and counts for every item of the batch
+    const size_t items = (size_t)total_items;
+    if (items > d->tiles_cap) {
+        if ((rc = dalloc(&d->tile_count, items)) || (rc = dalloc(&d->tile_off, items))) return rc;
+        d->tiles_cap = items;
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        b.key.clear();
+    }
+    if (items * (size_t)d->cap_tile > d->stage_cap) {
+        if ((rc = dalloc(&d->stage, items * (size_t)d->cap_tile))) return rc;
+        d->stage_cap = items * (size_t)d->cap_tile;
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        b.key.clear();
+    }
+    // the per-image prune grid: capacity for the largest image
+    const size_t before = d->pb.ncells_cap;
+    if ((rc = ensure_image_capacity(d, max_h, max_w, false))) return rc;
+    if (d->pb.ncells_cap != before || d->tiles_cap < items) {
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        b.key.clear();
+    }
+    return MHFD_OK;
+}
+
+// the whole batch, enqueued on s (also the body of the captured graph)
+int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long long total_items,
+                  cudaStream_t s) {
+    mhfd_detector::Batch &b = d->b;
+    MHFD_CUDA(cudaMemcpyAsync(b.d_jobs, b.h_jobs, sizeof(MhfdJob) * n, cudaMemcpyHostToDevice, s));
+    MHFD_CUDA(cudaMemcpyAsync(b.d_ranks, b.h_ranks, sizeof(long long) * n, cudaMemcpyHostToDevice, s));
+    MHFD_CUDA(cudaMemsetAsync(b.d_arena_n, 0, sizeof(unsigned long long), s));
+    MHFD_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int), s));
+    int rc = enqueue_stretch_batch(b.d_jobs, n, max_passes, max_rows, b.d_ranks, b.d_sels,
+                                   b.d_sts, s);
+    if (rc) return rc;
+    // one persistent launch over every tile of every image
+    Variant *v = d->var;
+    int dev = 0, sms = 1;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    d->params.assign((v->param_bytes + 7) / 8 + 1, 0);
+    MhfdKHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.stage = d->stage;
+    h.tile_count = d->tile_count;
+    h.cap_tile = d->cap_tile;
+    h.thr = d->p.threshold;
+    h.jobs = b.d_jobs;
+    h.queue = b.d_queue;
+    h.n_jobs = n;
+    h.total_items = (int)total_items;
+    std::memcpy(d->params.data(), &h, sizeof(h));
+    void *args[] = {d->params.data()};
+    const unsigned grid = (unsigned)(total_items < sms ? total_items : sms);
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k0, s));
+    const CUresult r = drv().launchKernel(v->fn, grid, 1, 1, (unsigned)v->cfg.nt, 1, 1,
+                                          (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
+    if (r != CUDA_SUCCESS) return fail(MHFD_ERR_CUDA, "cuLaunchKernel (batch)");
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k1, s));
+    // per image: gather its tiles, prune, compact into the shared blob arena
+    for (int j = 0; j < n; ++j) {
+        const MhfdJob &jb = b.h_jobs[j];
+        rc = enqueue_gather(d->tile_count + jb.tile_base,
+                            d->stage + (size_t)jb.tile_base * d->cap_tile, jb.n_tiles,
+                            d->cap_tile, d->cap, d->tile_off, d->cand, d->cnt, s);
+        if (rc) return rc;
+        rc = enqueue_prune(d->cand, d->cnt, d->cap, jb.H, jb.W, d->ct, d->radius_max,
+                           (double)d->p.overlap, &d->pb, s);
+        if (rc) return rc;
+        rc = enqueue_output(d->cand, d->pb.state, d->cnt, d->cap, d->d_sigma, d->d_radius_f, 1,
+                            b.h_res_dev + j, b.d_arena, nullptr, b.d_sts + j, d->block_tmp,
+                            d->block_sum, b.d_arena_n, b.arena_cap, s);
+        if (rc) return rc;
+    }
     return MHFD_OK;
 }
 
@@ -416,8 +565,11 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
         delete d;
         return rc;
     }
+    // candidate slots per tile: maxima of the paper rule are at least two
+    // pixels apart except on exact plateaus, so 1 per 8 pixels is far above
+    // any natural density; a tile beyond it reports MHFD_WARN_OVERFLOW
     const int TXY = (d->cfg.tx2 - 2) * (d->cfg.ty2 - 2);
-    d->cap_tile = d->p.nms == MHFD_NMS_PAPER ? (TXY + 1) / 2 : TXY;
+    d->cap_tile = d->p.nms == MHFD_NMS_PAPER ? (TXY + 7) / 8 : (TXY + 1) / 2;
     d->cap = d->p.max_candidates;
     if ((rc = get_variant(d->lk, d->p.nms, 0, d->cfg, &d->var))) {
         delete d;
@@ -653,9 +805,155 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     return precompile_variant(lk, p->nms, store, cfg);
 }
 
+
+int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
+                      const int32_t *dtypes, const int32_t *Hs, const int32_t *Ws,
+                      const size_t *pitches, void *stream) {
+    if (!d || n < 1 || !d_imgs || !dtypes || !Hs || !Ws || !pitches)
+        return fail(MHFD_ERR_INVALID_ARG, "NULL argument or n < 1");
+    DeviceGuard g(d->device);
+    long long total_items = 0, total_px = 0;
+    int max_passes = 1, max_h = 1, max_w = 1, max_rows = 1;
+    for (int j = 0; j < n; ++j) {
+        int rc = check_image(d_imgs[j], dtypes[j], Hs[j], Ws[j], pitches[j]);
+        if (rc) return fail(rc, "image " + std::to_string(j) + ": " + mhfd::t_err);
+        int tx, ty;
+        total_items += tiles_of(d, Hs[j], Ws[j], &tx, &ty);
+        total_px += (long long)Hs[j] * Ws[j];
+        const int passes = dtypes[j] == MHFD_U8 ? 1 : (dtypes[j] == MHFD_U16 ? 2 : 4);
+        max_passes = passes > max_passes ? passes : max_passes;
+        max_h = Hs[j] > max_h ? Hs[j] : max_h;
+        max_w = Ws[j] > max_w ? Ws[j] : max_w;
+    }
+    max_rows = max_h;
+    if (total_items > 2147483647ll) return fail(MHFD_ERR_INVALID_ARG, "batch too large");
+    int rc = batch_reserve(d, n, total_items, total_px, max_h, max_w);
+    if (rc) return rc;
+    mhfd_detector::Batch &b = d->b;
+    std::vector<long long> key;
+    key.reserve(4 * n + 2);
+    key.push_back(n);
+    key.push_back(d->p.timing);
+    int base = 0;
+    for (int j = 0; j < n; ++j) {
+        int tx, ty;
+        const int nt = tiles_of(d, Hs[j], Ws[j], &tx, &ty);
+        MhfdJob &jb = b.h_jobs[j];
+        jb.img = d_imgs[j];
+        jb.st = b.d_sts + j;
+        jb.pitch = (long long)pitches[j];
+        jb.H = Hs[j];
+        jb.W = Ws[j];
+        jb.dtype = dtypes[j];
+        jb.tiles_x = tx;
+        jb.n_tiles = nt;
+        jb.tile_base = base;
+        base += nt;
+        b.h_ranks[j] = clip_rank(d, Hs[j], Ws[j]);
+        key.push_back(Hs[j]);
+        key.push_back(Ws[j]);
+        key.push_back(dtypes[j]);
+        key.push_back((long long)pitches[j]);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    d->timed = d->p.timing != 0;
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_t0, s));
+    if (b.graphs && b.exec && key == b.key) {
+        MHFD_CUDA(cudaGraphLaunch(b.exec, s));
+    } else {
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        b.key.clear();
+        bool done = false;
+        if (b.graphs && !d->timed) {
+            // capture the batch once per shape; later calls with the same
+            // shape replay it (the job table travels through pinned memory,
+            // so new image pointers need no recapture)
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = batch_enqueue(d, n, max_passes, max_rows, total_items, s);
+                e = cudaStreamEndCapture(s, &graph);
+                if (rc == MHFD_OK && e == cudaSuccess && graph) {
+                    cudaGraphExec_t exec = nullptr;
+                    if (cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+                        b.exec = exec;
+                        b.key = key;
+                        MHFD_CUDA(cudaGraphLaunch(exec, s));
+                        done = true;
+                    }
+                }
+                if (graph) cudaGraphDestroy(graph);
+            }
+            cudaGetLastError();  // a refused capture falls back to direct launches
+            if (!done) b.graphs = false;
+        }
+        if (!done && (rc = batch_enqueue(d, n, max_passes, max_rows, total_items, s))) return rc;
+    }
+    if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_end, s));
+    MHFD_CUDA(cudaEventRecord(d->ev_done, s));
+    b.n = n;
+    b.pending = true;
+    b.copied = false;
+    d->pending = false;
+    return MHFD_OK;
+}
+
+int mhfd_result_wait_batch(mhfd_detector *d, mhfd_result *outs, int32_t n) {
+    if (!d || !outs) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    mhfd_detector::Batch &b = d->b;
+    if (!b.pending || n != b.n) return fail(MHFD_ERR_INVALID_ARG, "no batch of this size enqueued");
+    DeviceGuard g(d->device);
+    MHFD_CUDA(cudaEventSynchronize(d->ev_done));
+    MHFD_CUDA(cudaGetLastError());
+    unsigned long long used = 0;
+    for (int j = 0; j < n; ++j) {
+        const unsigned long long e = b.h_res[j].c.blob_base + b.h_res[j].c.n_blobs;
+        used = e > used ? e : used;
+    }
+    if (!b.copied) {
+        if (used > b.h_arena_cap) {
+            if (b.h_arena) cudaFreeHost(b.h_arena);
+            b.h_arena = nullptr;
+            MHFD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&b.h_arena), sizeof(mhfd_blob) * used, 0));
+            b.h_arena_cap = used;
+        }
+        if (used) MHFD_CUDA(cudaMemcpy(b.h_arena, b.d_arena, sizeof(mhfd_blob) * used,
+                                       cudaMemcpyDeviceToHost));
+        b.copied = true;
+    }
+    int worst = MHFD_OK;
+    for (int j = 0; j < n; ++j) {
+        const HostResult &h = b.h_res[j];
+        mhfd_result &o = outs[j];
+        std::memset(&o, 0, sizeof(o));
+        o.blobs = b.h_arena ? b.h_arena + h.c.blob_base : nullptr;
+        o.n_blobs = (int64_t)h.c.n_blobs;
+        o.candidates = nullptr;
+        o.n_candidates = (int64_t)h.c.n_stored;
+        o.n_candidates_true = (int64_t)h.c.n_true;
+        o.focus_score = (float)h.c.n_blobs;
+        o.mean_response = h.c.n_blobs ? (float)(h.sum_resp / (double)h.c.n_blobs) : 0.0f;
+        for (int i = 0; i < 64; ++i) o.per_scale[i] = h.per_scale[i];
+        o.lo = h.lo;
+        o.hi = h.hi;
+        o.status = h.c.timeout ? MHFD_ERR_TIMEOUT : (h.c.overflow ? MHFD_WARN_OVERFLOW : MHFD_OK);
+        if (o.status == MHFD_ERR_TIMEOUT) worst = MHFD_ERR_TIMEOUT;
+        else if (o.status == MHFD_WARN_OVERFLOW && worst == MHFD_OK) worst = MHFD_WARN_OVERFLOW;
+    }
+    if (worst == MHFD_ERR_TIMEOUT) return fail(MHFD_ERR_TIMEOUT, "overlap prune did not settle");
+    return worst;
+}
+
+int mhfd_batch_uses_graph(mhfd_detector *d) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    return d->b.exec != nullptr ? 1 : 0;
+}
+
 int mhfd_last_timing(mhfd_detector *d, float *ms_kernel, float *ms_total) {
     if (!d || !ms_kernel || !ms_total) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
-    if (!d->pending || !d->timed) return fail(MHFD_ERR_INVALID_ARG, "no timed detection (set params.timing)");
+    if ((!d->pending && !d->b.pending) || !d->timed)
+        return fail(MHFD_ERR_INVALID_ARG, "no timed detection (set params.timing)");
     DeviceGuard g(d->device);
     MHFD_CUDA(cudaEventSynchronize(d->ev_done));
     MHFD_CUDA(cudaEventSynchronize(d->ev_k1));

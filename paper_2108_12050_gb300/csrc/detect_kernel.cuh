@@ -169,25 +169,28 @@ __device__ __forceinline__ float load_px(const char *row, int gx, const MhfdStre
 }
 
 template <int DT>
-__device__ __forceinline__ void load_block(const KParams &p, const MhfdStretch &st, float *s_in,
+__device__ __forceinline__ void load_block(const MhfdKHeader &h, const MhfdStretch &st, float *s_in,
                                            int x0, int y0) {
-    const char *base = reinterpret_cast<const char *>(p.h.img);
-    const long long pitch = p.h.pitch;
-    const int H = p.h.H, W = p.h.W;
+    // each thread owns columns; LB row loads are kept in flight at a time so
+    // that the latency of the global (mostly L2) reads overlaps
+    constexpr int LB = 16;
+    const char *base = reinterpret_cast<const char *>(h.img);
+    const long long pitch = h.pitch;
+    const int H = h.H, W = h.W;
     for (int c = threadIdx.x; c < WEXT; c += NT) {
         const int gx = reflect_idx(x0 - 1 - RMAX + c, W);
         float *dst = s_in + c;
         int r = 0;
 #pragma unroll 1
-        for (; r + 4 <= ROWS_IN; r += 4) {
-            float v[4];
+        for (; r + LB <= ROWS_IN; r += LB) {
+            float v[LB];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < LB; ++e) {
                 const int gy = reflect_idx(y0 - 1 - RMAX + r + e, H);
                 v[e] = load_px<DT>(base + (long long)gy * pitch, gx, st);
             }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) dst[(r + e) * WEXTP] = v[e];
+            for (int e = 0; e < LB; ++e) dst[(r + e) * WEXTP] = v[e];
         }
         for (; r < ROWS_IN; ++r) {
             const int gy = reflect_idx(y0 - 1 - RMAX + r, H);
@@ -195,8 +198,6 @@ __device__ __forceinline__ void load_block(const KParams &p, const MhfdStretch &
         }
     }
 }
-
-// ------------------------------------------------------- 2. vertical pass
 
 // Fold step K of the vertical pass for the levels L.. of group G: every
 // level whose radius reaches K takes tap K times the folded sum.
@@ -235,7 +236,7 @@ __device__ __forceinline__ void vstep(const float *colp, float (*acc)[kGB(G + 1)
 // V_l(o0 + j, c) for the ROWS rows starting at tile row o0 and every level l
 // of group G.  Row o of the tile sits at row o + RMAX of the halo'd block.
 template <int G, int ROWS>
-__device__ __forceinline__ void vcol(const KParams &p, const float *__restrict__ s_in,
+__device__ __forceinline__ void vcol(const MhfdKHeader &h, const float *__restrict__ s_in,
                                      float *__restrict__ s_v, int c, int o0, int jb) {
     constexpr int LB = kGB(G);
     constexpr int LE = kGB(G + 1);
@@ -257,22 +258,22 @@ __device__ __forceinline__ void vcol(const KParams &p, const float *__restrict__
 
 template <int G, int PART>
 struct VParts {
-    static __device__ __forceinline__ void run(const KParams &p, const float *s_in, float *s_v,
+    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *s_in, float *s_v,
                                                int c, int s) {
         constexpr int ROWS = (RB - 4 * PART) < 4 ? (RB - 4 * PART) : 4;
-        vcol<G, ROWS>(p, s_in, s_v, c, s * RB + 4 * PART, 4 * PART);
-        VParts<G, PART + 1>::run(p, s_in, s_v, c, s);
+        vcol<G, ROWS>(h, s_in, s_v, c, s * RB + 4 * PART, 4 * PART);
+        VParts<G, PART + 1>::run(h, s_in, s_v, c, s);
     }
 };
 template <int G>
 struct VParts<G, NPARTS> {
-    static __device__ __forceinline__ void run(const KParams &, const float *, float *, int, int) {}
+    static __device__ __forceinline__ void run(const MhfdKHeader &, const float *, float *, int, int) {}
 };
 
 template <int G>
-__device__ __forceinline__ void vpass(const KParams &p, const float *s_in, float *s_v, int s) {
+__device__ __forceinline__ void vpass(const MhfdKHeader &h, const float *s_in, float *s_v, int s) {
 #pragma unroll 1
-    for (int c = threadIdx.x; c < WEXT; c += NT) VParts<G, 0>::run(p, s_in, s_v, c, s);
+    for (int c = threadIdx.x; c < WEXT; c += NT) VParts<G, 0>::run(h, s_in, s_v, c, s);
 }
 
 // ----------------------------------------------------- 3. horizontal pass
@@ -285,7 +286,7 @@ __device__ __forceinline__ void hacc1(float v, float (&a)[4]) {
 }
 
 template <int R, int TO, int M>
-__device__ __forceinline__ void hacc(const KParams &, float v, float (&a)[4]) {
+__device__ __forceinline__ void hacc(const MhfdKHeader &, float v, float (&a)[4]) {
     hacc1<R, TO, M, 0>(v, a);
     hacc1<R, TO, M, 1>(v, a);
     hacc1<R, TO, M, 2>(v, a);
@@ -294,18 +295,18 @@ __device__ __forceinline__ void hacc(const KParams &, float v, float (&a)[4]) {
 
 template <int R, int TO, int M4>
 struct HQuads {
-    static __device__ __forceinline__ void run(const KParams &p, const float4 *w, float (&a)[4]) {
+    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float4 *w, float (&a)[4]) {
         const float4 v = w[M4];
-        hacc<R, TO, 4 * M4 + 0>(p, v.x, a);
-        hacc<R, TO, 4 * M4 + 1>(p, v.y, a);
-        hacc<R, TO, 4 * M4 + 2>(p, v.z, a);
-        hacc<R, TO, 4 * M4 + 3>(p, v.w, a);
-        HQuads<R, TO, M4 - 1>::run(p, w, a);
+        hacc<R, TO, 4 * M4 + 0>(h, v.x, a);
+        hacc<R, TO, 4 * M4 + 1>(h, v.y, a);
+        hacc<R, TO, 4 * M4 + 2>(h, v.z, a);
+        hacc<R, TO, 4 * M4 + 3>(h, v.w, a);
+        HQuads<R, TO, M4 - 1>::run(h, w, a);
     }
 };
 template <int R, int TO>
 struct HQuads<R, TO, -1> {
-    static __device__ __forceinline__ void run(const KParams &, const float4 *, float (&)[4]) {}
+    static __device__ __forceinline__ void run(const MhfdKHeader &, const float4 *, float (&)[4]) {}
 };
 
 struct HCtx {
@@ -319,13 +320,13 @@ struct HCtx {
 };
 
 template <int L>
-__device__ __forceinline__ void hlevel(const KParams &p, const float *vrow, const HCtx &cx,
+__device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, const HCtx &cx,
                                        HState &st, float *s_ring) {
     constexpr int R = kR(L);
     constexpr int NQ = (2 * R + 3) / 4 + 1;
     float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     const float4 *w = reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q;
-    HQuads<R, tapoff(L), NQ - 1>::run(p, w, a);
+    HQuads<R, tapoff(L), NQ - 1>::run(h, w, a);
     if (L == 0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -362,7 +363,7 @@ __device__ __forceinline__ void hlevel(const KParams &p, const float *vrow, cons
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (cx.inter[u])
-                    p.h.stack_out[(long long)I * p.h.plane + (long long)cx.gy * p.h.W + cx.gx0 + u] =
+                    h.stack_out[(long long)I * h.plane + (long long)cx.gy * h.W + cx.gx0 + u] =
                         d[u];
         }
     }
@@ -370,19 +371,19 @@ __device__ __forceinline__ void hlevel(const KParams &p, const float *vrow, cons
 
 template <int L, int LE>
 struct HLevels {
-    static __device__ __forceinline__ void run(const KParams &p, const float *vrow,
+    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *vrow,
                                                const HCtx &cx, HState &st, float *s_ring) {
-        hlevel<L>(p, vrow, cx, st, s_ring);
-        HLevels<L + 1, LE>::run(p, vrow, cx, st, s_ring);
+        hlevel<L>(h, vrow, cx, st, s_ring);
+        HLevels<L + 1, LE>::run(h, vrow, cx, st, s_ring);
     }
 };
 template <int LE>
 struct HLevels<LE, LE> {
-    static __device__ __forceinline__ void run(const KParams &, const float *, const HCtx &,
+    static __device__ __forceinline__ void run(const MhfdKHeader &, const float *, const HCtx &,
                                                HState &, float *) {}
 };
 
-__device__ __forceinline__ HCtx make_ctx(const KParams &p, int item, int s, int x0, int y0) {
+__device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, int item, int s, int x0, int y0) {
     HCtx cx;
     const int j = item / NQ4;
     cx.q = item - j * NQ4;
@@ -390,29 +391,29 @@ __device__ __forceinline__ HCtx make_ctx(const KParams &p, int item, int s, int 
     cx.slot = cx.r % RING;
     cx.gy = y0 - 1 + cx.r;
     cx.gx0 = x0 - 1 + 4 * cx.q;
-    const bool rowin = cx.gy >= 0 && cx.gy < p.h.H;
+    const bool rowin = cx.gy >= 0 && cx.gy < h.H;
     const bool rowint = rowin && cx.r >= 1 && cx.r <= TY2 - 2;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int gx = cx.gx0 + u;
         const int c = 4 * cx.q + u;
-        cx.inb[u] = rowin && gx >= 0 && gx < p.h.W;
-        cx.inter[u] = rowint && c >= 1 && c <= TX2 - 2 && gx < p.h.W;
+        cx.inb[u] = rowin && gx >= 0 && gx < h.W;
+        cx.inter[u] = rowint && c >= 1 && c <= TX2 - 2 && gx < h.W;
     }
     return cx;
 }
 
 template <int G>
-__device__ __forceinline__ void hpass(const KParams &p, const float *s_v, float *s_ring,
+__device__ __forceinline__ void hpass(const MhfdKHeader &h, const float *s_v, float *s_ring,
                                       unsigned char *s_arg, HState (&hs)[HI], int s, int x0,
                                       int y0) {
 #pragma unroll
     for (int it = 0; it < HI; ++it) {
         const int item = threadIdx.x + it * NT;
         if (item < HITEMS) {
-            const HCtx cx = make_ctx(p, item, s, x0, y0);
+            const HCtx cx = make_ctx(h, item, s, x0, y0);
             const float *vrow = s_v + (cx.r - s * RB) * VROW;
-            HLevels<kGB(G), kGB(G + 1)>::run(p, vrow, cx, hs[it], s_ring);
+            HLevels<kGB(G), kGB(G + 1)>::run(h, vrow, cx, hs[it], s_ring);
             if (G == NGROUPS - 1 && MODE == 0) {
                 const float ninf = -__int_as_float(0x7f800000);
                 float4 o;
@@ -431,9 +432,9 @@ __device__ __forceinline__ void hpass(const KParams &p, const float *s_v, float 
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         if (cx.inter[u]) {
-                            const long long o2 = (long long)cx.gy * p.h.W + cx.gx0 + u;
-                            if (p.h.m_out) p.h.m_out[o2] = hs[it].m[u];
-                            if (p.h.arg_out) p.h.arg_out[o2] = hs[it].a[u];
+                            const long long o2 = (long long)cx.gy * h.W + cx.gx0 + u;
+                            if (h.m_out) h.m_out[o2] = hs[it].m[u];
+                            if (h.arg_out) h.arg_out[o2] = hs[it].a[u];
                         }
                 }
             }
@@ -443,19 +444,19 @@ __device__ __forceinline__ void hpass(const KParams &p, const float *s_v, float 
 
 template <int G>
 struct Groups {
-    static __device__ __forceinline__ void run(const KParams &p, const float *s_in, float *s_v,
+    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *s_in, float *s_v,
                                                float *s_ring, unsigned char *s_arg,
                                                HState (&hs)[HI], int s, int x0, int y0) {
-        vpass<G>(p, s_in, s_v, s);
+        vpass<G>(h, s_in, s_v, s);
         __syncthreads();
-        hpass<G>(p, s_v, s_ring, s_arg, hs, s, x0, y0);
+        hpass<G>(h, s_v, s_ring, s_arg, hs, s, x0, y0);
         __syncthreads();
-        Groups<G + 1>::run(p, s_in, s_v, s_ring, s_arg, hs, s, x0, y0);
+        Groups<G + 1>::run(h, s_in, s_v, s_ring, s_arg, hs, s, x0, y0);
     }
 };
 template <>
 struct Groups<NGROUPS> {
-    static __device__ __forceinline__ void run(const KParams &, const float *, float *, float *,
+    static __device__ __forceinline__ void run(const MhfdKHeader &, const float *, float *, float *,
                                                unsigned char *, HState (&)[HI], int, int, int) {}
 };
 
@@ -522,7 +523,7 @@ __device__ __forceinline__ bool cand_26(const float *s_ring, int r, int c, int l
     return true;
 }
 
-__device__ __forceinline__ int nms_step(const KParams &p, const float *s_ring,
+__device__ __forceinline__ int nms_step(const MhfdKHeader &h, const float *s_ring,
                                         const unsigned char *s_arg, int *s_scan, int s, int x0,
                                         int y0, int tile, int total) {
     const int r_lo = max(1, s * RB - 1);
@@ -534,7 +535,7 @@ __device__ __forceinline__ int nms_step(const KParams &p, const float *s_ring,
     const int ch = (items + NT - 1) / NT;
     const int beg = min(items, (int)threadIdx.x * ch);
     const int end = min(items, beg + ch);
-    const float thr = p.h.thr;
+    const float thr = h.thr;
     int cnt = 0;
     for (int it = beg; it < end; ++it) {
         const int r = r_lo + it / per;
@@ -549,7 +550,7 @@ __device__ __forceinline__ int nms_step(const KParams &p, const float *s_ring,
     int sum;
     int pos = total + block_excl_scan(cnt, s_scan, &sum);
     if (cnt) {
-        MhfdCand *dst = p.h.stage + (long long)tile * p.h.cap_tile;
+        MhfdCand *dst = h.stage + (long long)tile * h.cap_tile;
         for (int it = beg; it < end; ++it) {
             const int r = r_lo + it / per;
             const int rem = it - (it / per) * per;
@@ -566,7 +567,7 @@ __device__ __forceinline__ int nms_step(const KParams &p, const float *s_ring,
                 ok = cand_26(s_ring, r, c, l, thr, &v);
             }
             if (ok) {
-                if (pos < p.h.cap_tile) {
+                if (pos < h.cap_tile) {
                     MhfdCand cd;
                     cd.x = x0 - 1 + c;
                     cd.y = y0 - 1 + r;
@@ -587,6 +588,38 @@ extern "C" __constant__ int mhfd_smem_bytes = mk::SMEM_BYTES;
 extern "C" __constant__ int mhfd_param_bytes = (int)sizeof(mk::KParams);
 extern "C" __constant__ int mhfd_ntaps = mk::NTAPS;
 
+namespace mk {
+
+// The whole detection of one output tile (load, stack, DoG, maxima,
+// compaction).  `item` indexes the candidate slots and counts.
+__device__ __forceinline__ void process_tile(const MhfdKHeader &h, int tile,
+                                             int item, float *s_in, float *s_v, float *s_ring,
+                                             unsigned char *s_arg, int *s_scan) {
+    const int ty = tile / h.tiles_x;
+    const int tx = tile - ty * h.tiles_x;
+    const int x0 = tx * TX, y0 = ty * TY;
+    const MhfdStretch st = *h.st;
+
+    if (h.dtype == 0)
+        load_block<0>(h, st, s_in, x0, y0);
+    else if (h.dtype == 1)
+        load_block<1>(h, st, s_in, x0, y0);
+    else
+        load_block<2>(h, st, s_in, x0, y0);
+    __syncthreads();
+
+    HState hs[HI];
+    int total = 0;
+#pragma unroll 1
+    for (int s = 0; s < NSTEPS; ++s) {
+        Groups<0>::run(h, s_in, s_v, s_ring, s_arg, hs, s, x0, y0);
+        total = nms_step(h, s_ring, s_arg, s_scan, s, x0, y0, item, total);
+    }
+    if (threadIdx.x == 0) h.tile_count[item] = total;
+}
+
+}  // namespace mk
+
 extern "C" __global__ void __launch_bounds__(mk::NT, 1)
     mhfd_fused_detect(const __grid_constant__ mk::KParams p) {
     using namespace mk;
@@ -597,26 +630,34 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
     unsigned char *s_arg = reinterpret_cast<unsigned char *>(s_ring + SMEM_RING_F);
     int *s_scan = reinterpret_cast<int *>(s_arg + SMEM_RING_B);
 
-    const int tile = blockIdx.x;
-    const int ty = tile / p.h.tiles_x;
-    const int tx = tile - ty * p.h.tiles_x;
-    const int x0 = tx * TX, y0 = ty * TY;
-    const MhfdStretch st = *p.h.st;
-
-    if (p.h.dtype == 0)
-        load_block<0>(p, st, s_in, x0, y0);
-    else if (p.h.dtype == 1)
-        load_block<1>(p, st, s_in, x0, y0);
-    else
-        load_block<2>(p, st, s_in, x0, y0);
-    __syncthreads();
-
-    HState hs[HI];
-    int total = 0;
-#pragma unroll 1
-    for (int s = 0; s < NSTEPS; ++s) {
-        Groups<0>::run(p, s_in, s_v, s_ring, s_arg, hs, s, x0, y0);
-        total = nms_step(p, s_ring, s_arg, s_scan, s, x0, y0, tile, total);
+    if (p.h.jobs == nullptr) {
+        process_tile(p.h, blockIdx.x, blockIdx.x, s_in, s_v, s_ring, s_arg, s_scan);
+        return;
     }
-    if (threadIdx.x == 0) p.h.tile_count[tile] = total;
+    // batch: persistent blocks take items from the queue (no waits)
+    __shared__ int s_item;
+#pragma unroll 1
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(p.h.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= p.h.total_items) break;
+        int lo = 0, hi = p.h.n_jobs - 1;  // last job with tile_base <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.h.jobs[mid].tile_base <= item) lo = mid; else hi = mid - 1;
+        }
+        const MhfdJob job = p.h.jobs[lo];
+        MhfdKHeader h = p.h;
+        h.img = job.img;
+        h.st = job.st;
+        h.pitch = job.pitch;
+        h.H = job.H;
+        h.W = job.W;
+        h.dtype = job.dtype;
+        h.tiles_x = job.tiles_x;
+        h.plane = (long long)job.H * job.W;
+        process_tile(h, item - job.tile_base, item, s_in, s_v, s_ring, s_arg, s_scan);
+    }
 }

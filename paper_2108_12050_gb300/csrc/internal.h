@@ -55,6 +55,11 @@ struct SelState {
 int enqueue_stretch(const void *img, int dtype, int H, int W, long long pitch, long long k,
                     SelState *sel, MhfdStretch *st, cudaStream_t s);
 
+// All images of a batch: one launch per radix pass.  d_ranks[j] = k_j.
+int enqueue_stretch_batch(const MhfdJob *d_jobs, int n_jobs, int max_passes, int max_rows,
+                          const long long *d_ranks, SelState *d_sels, MhfdStretch *d_sts,
+                          cudaStream_t s);
+
 // ---------------------------------------------------- fused kernel (JIT)
 struct TileConfig {
     int tx2, ty2, rb, nt;
@@ -96,7 +101,7 @@ struct Counters {
     unsigned long long n_blobs;     // survivors
     int overflow;
     int timeout;
-    int pad[2];
+    unsigned long long blob_base;   // first slot of this image's blobs in the output list
 };
 
 struct HostResult {               // mirrored in pinned, device-mapped memory
@@ -134,11 +139,14 @@ int enqueue_gather(const int *tile_count, const MhfdCand *stage, int n_tiles, in
 int enqueue_prune(const MhfdCand *cand, const Counters *cnt, long long cap, int H, int W,
                   const ConflictTable &ct, double radius_max, double overlap, PruneBuffers *pb,
                   cudaStream_t s);
+// Compaction of the kept candidates into `blobs`.  With `arena` set, the
+// image's slots are reserved at *arena (in stream order) within arena_cap
+// entries and the base is published; otherwise they start at 0.
 int enqueue_output(const MhfdCand *cand, const int *state, const Counters *cnt, long long cap,
                    const float *d_sigma, const float *d_radius_f, int prune_on,
-                   HostResult *h_res_dev, mhfd_blob *h_blobs_dev, mhfd_blob *h_cands_dev,
+                   HostResult *h_res_dev, mhfd_blob *blobs, mhfd_blob *h_cands_dev,
                    const MhfdStretch *st, int *block_tmp, double *block_sum,
-                   cudaStream_t s);
+                   unsigned long long *arena, unsigned long long arena_cap, cudaStream_t s);
 // pack caller SoA candidates into the internal list
 int enqueue_pack(const int32_t *x, const int32_t *y, const int32_t *i, const float *r,
                  long long n, int H, int W, int n_levels, MhfdCand *cand, Counters *cnt,

@@ -22,9 +22,21 @@ struct MhfdCand {
     float resp;
 };
 
-// Fixed head of the fused kernel's by-value parameter block; the ladder's
-// scale factors t_i and the Gaussian taps follow it (sizes depend on the
-// ladder the kernel was compiled for).
+// One image of a batch: where it is, how it is stored, where its stretch
+// bounds live and which global tile indices (items) it owns.
+struct MhfdJob {
+    const void *img;
+    const MhfdStretch *st;
+    long long pitch;
+    int H, W, dtype, tiles_x;
+    int n_tiles;      // tiles of this image
+    int tile_base;    // first global item of this image
+};
+
+// By-value parameter block of the fused kernel (the ladder itself is
+// compiled into the kernel).  Single image: jobs == nullptr and block b
+// processes tile b of `img`.  Batch: a persistent grid pulls global items
+// from *queue until total_items; item -> (job, tile) through tile_base.
 struct MhfdKHeader {
     const void *img;          // device image, `pitch` bytes per row
     const MhfdStretch *st;    // stretch bounds of this image
@@ -37,6 +49,9 @@ struct MhfdKHeader {
     long long plane;          // H*W (stack plane stride)
     int H, W, dtype, tiles_x, cap_tile;
     float thr;                // feature threshold (strict >)
+    const MhfdJob *jobs;      // batch mode: job table (device)
+    int *queue;               // batch mode: next item counter (zeroed per launch)
+    int n_jobs, total_items;
 };
 
 #endif  // MHFD_TYPES_H

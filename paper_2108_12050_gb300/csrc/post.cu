@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kScanThreads)
         cnt->overflow = (carry_t > (long long)cnt->n_stored) ? 1 : 0;
         cnt->n_blobs = 0;
         cnt->timeout = 0;
+        cnt->blob_base = 0;
     }
 }
 
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(256)
 // block order by a fixed tree (deterministic)
 __global__ void __launch_bounds__(256)
     out_scan(int *block_cnt, const double *block_sum, int nb, Counters *cnt, double *sum_out,
-             int *per_scale) {
+             int *per_scale, unsigned long long *arena, unsigned long long arena_cap) {
     __shared__ long long sh[32];
     __shared__ double ss[256];
     const int b = threadIdx.x;
@@ -346,7 +347,19 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
     }
     if (b == 0) {
-        cnt->n_blobs = (unsigned long long)tot;
+        unsigned long long n = (unsigned long long)tot, base = 0;
+        if (arena) {
+            base = atomicAdd(arena, n);
+            if (base >= arena_cap) {
+                n = 0;
+                cnt->overflow = 1;
+            } else if (base + n > arena_cap) {
+                n = arena_cap - base;
+                cnt->overflow = 1;
+            }
+        }
+        cnt->blob_base = base;
+        cnt->n_blobs = n;
         *sum_out = ss[0];
     }
     if (b < 64) per_scale[b] = 0;
@@ -363,6 +376,7 @@ __global__ void __launch_bounds__(256)
     const long long n = (long long)cnt->n_stored;
     const long long per = (n + gridDim.x - 1) / gridDim.x;
     const long long beg = min(n, (long long)blockIdx.x * per), end = min(n, beg + per);
+    const long long base = (long long)cnt->blob_base, lim = (long long)cnt->n_blobs;
     long long out = block_off[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (long long base = beg; base < end; base += blockDim.x) {
@@ -394,8 +408,8 @@ __global__ void __launch_bounds__(256)
             if (w < warp) before += sh_w[w];
             total += sh_w[w];
         }
-        if (keep) {
-            const long long pos = out + before + __popc(bal & ((1u << lane) - 1u));
+        const long long pos = out + before + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < lim) {
             mhfd_blob b;
             b.x = c.x;
             b.y = c.y;
@@ -403,7 +417,7 @@ __global__ void __launch_bounds__(256)
             b.sigma = sigma[c.i];
             b.radius = radius_f[c.i];
             b.response = c.resp;
-            blobs[pos] = b;
+            blobs[base + pos] = b;
             atomicAdd(&sh_scale[c.i & 63], 1);
         }
         out += total;
@@ -554,7 +568,8 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
 int enqueue_output(const MhfdCand *cand, const int *state, const Counters *cnt_c, long long cap,
                    const float *d_sigma, const float *d_radius_f, int prune_on,
                    HostResult *h_res_dev, mhfd_blob *h_blobs_dev, mhfd_blob *h_cands_dev,
-                   const MhfdStretch *st, int *block_tmp, double *block_sum, cudaStream_t s) {
+                   const MhfdStretch *st, int *block_tmp, double *block_sum,
+                   unsigned long long *arena, unsigned long long arena_cap, cudaStream_t s) {
     (void)cap;
     (void)prune_on;
     Counters *cnt = const_cast<Counters *>(cnt_c);
@@ -563,7 +578,7 @@ int enqueue_output(const MhfdCand *cand, const int *state, const Counters *cnt_c
     int *per_scale = block_tmp + nb;
     double *sum = block_sum + nb;
     out_count<<<nb, 256, 0, s>>>(cand, state, cnt, block_tmp, block_sum);
-    out_scan<<<1, 256, 0, s>>>(block_tmp, block_sum, nb, cnt, sum, per_scale);
+    out_scan<<<1, 256, 0, s>>>(block_tmp, block_sum, nb, cnt, sum, per_scale, arena, arena_cap);
     out_write<<<nb, 256, 0, s>>>(cand, state, cnt, block_tmp, d_sigma, d_radius_f, h_blobs_dev,
                                  h_cands_dev, per_scale);
     out_publish<<<1, 64, 0, s>>>(cnt, sum, per_scale, st, h_res_dev);

@@ -62,14 +62,14 @@ struct RunAcc {
     }
 };
 
+// Histogram accumulation of one pass over rows [y0, H) step ystep of one
+// image into the block's shared histograms h[2][256].
 template <int DT, int BITS>
-__global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, long long pitch,
-                                                int pass, SelState *sel) {
+__device__ __forceinline__ void hist_rows(const char *img, int H, int W, long long pitch,
+                                          int pass, const SelState *sel, int y0, int ystep,
+                                          unsigned (*h)[256]) {
     constexpr int ES = DT == 0 ? 1 : (DT == 1 ? 2 : 4);
     constexpr int VEC = 16 / ES;
-    __shared__ unsigned h[2][256];
-    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
     const int shift = BITS - 8 * (pass + 1);
     const unsigned p0 = sel->prefix[0], p1 = sel->prefix[1];
     const bool first = (pass == 0);
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, l
         if (first || hi == p0) r0.add(digit, h[0]);
         if (!first && hi == p1) r1.add(digit, h[1]);
     };
-    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+    for (int y = y0; y < H; y += ystep) {
         const char *row = img + (long long)y * pitch;
         for (int x0 = threadIdx.x * VEC; x0 < W; x0 += blockDim.x * VEC) {
             if (vec_ok && x0 + VEC <= W) {
@@ -106,6 +106,9 @@ __global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, l
     }
     r0.flush(h[0]);
     r1.flush(h[1]);
+}
+
+__device__ __forceinline__ void hist_flush(unsigned (*h)[256], SelState *sel) {
     __syncthreads();
     for (int i = threadIdx.x; i < 512; i += blockDim.x) {
         const unsigned v = (&h[0][0])[i];
@@ -113,10 +116,20 @@ __global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, l
     }
 }
 
+template <int DT, int BITS>
+__global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, long long pitch,
+                                                int pass, SelState *sel) {
+    __shared__ unsigned h[2][256];
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    hist_rows<DT, BITS>(img, H, W, pitch, pass, sel, blockIdx.x, gridDim.x, h);
+    hist_flush(h, sel);
+}
+
 // Pick the digit holding each target's remaining rank; after the last pass
 // turn the two keys into the stretch parameters.
 template <int DT, int BITS>
-__global__ void sel_pick(int pass, SelState *sel, MhfdStretch *st) {
+__device__ __forceinline__ void pick_digit(int pass, SelState *sel, MhfdStretch *st) {
     __shared__ unsigned cum[2][256];
     __shared__ unsigned pick[2];
     const int t = threadIdx.x;  // 256 threads
@@ -171,6 +184,57 @@ __global__ void sel_pick(int pass, SelState *sel, MhfdStretch *st) {
 }
 
 template <int DT, int BITS>
+__global__ void sel_pick(int pass, SelState *sel, MhfdStretch *st) {
+    pick_digit<DT, BITS>(pass, sel, st);
+}
+
+// ------------------------------------------------------------ batched select
+// One launch per pass covers every image of a batch (blockIdx.y = image);
+// images whose key width needs fewer passes than the pass index skip.
+
+__device__ __forceinline__ int passes_of(int dtype) { return dtype == 0 ? 1 : (dtype == 1 ? 2 : 4); }
+
+__global__ void bsel_init(const MhfdJob *jobs, SelState *sels, const long long *ranks) {
+    const int j = blockIdx.x;
+    SelState *sel = sels + j;
+    if (threadIdx.x == 0) {
+        const unsigned long long n = (unsigned long long)jobs[j].H * (unsigned long long)jobs[j].W;
+        sel->prefix[0] = sel->prefix[1] = 0;
+        sel->rank[0] = (unsigned long long)ranks[j];
+        sel->rank[1] = n - 1 - (unsigned long long)ranks[j];
+    }
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&sel->hist[0][0])[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) bsel_hist(const MhfdJob *jobs, SelState *sels, int pass) {
+    __shared__ unsigned h[2][256];
+    const MhfdJob job = jobs[blockIdx.y];
+    if (pass >= passes_of(job.dtype) || (int)blockIdx.x >= job.H) return;
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
+    __syncthreads();
+    SelState *sel = sels + blockIdx.y;
+    const char *img = reinterpret_cast<const char *>(job.img);
+    if (job.dtype == 0)
+        hist_rows<0, 8>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, h);
+    else if (job.dtype == 1)
+        hist_rows<1, 16>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, h);
+    else
+        hist_rows<2, 32>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, h);
+    hist_flush(h, sel);
+}
+
+__global__ void bsel_pick(const MhfdJob *jobs, SelState *sels, MhfdStretch *sts, int pass) {
+    const MhfdJob job = jobs[blockIdx.x];
+    if (pass >= passes_of(job.dtype)) return;
+    if (job.dtype == 0)
+        pick_digit<0, 8>(pass, sels + blockIdx.x, sts + blockIdx.x);
+    else if (job.dtype == 1)
+        pick_digit<1, 16>(pass, sels + blockIdx.x, sts + blockIdx.x);
+    else
+        pick_digit<2, 32>(pass, sels + blockIdx.x, sts + blockIdx.x);
+}
+
+template <int DT, int BITS>
 int run_select(const void *img, int H, int W, long long pitch, SelState *sel, MhfdStretch *st,
                cudaStream_t s) {
     int dev = 0, sms = 0;
@@ -188,6 +252,25 @@ int run_select(const void *img, int H, int W, long long pitch, SelState *sel, Mh
 }
 
 }  // namespace
+
+int enqueue_stretch_batch(const MhfdJob *d_jobs, int n_jobs, int max_passes, int max_rows,
+                          const long long *d_ranks, SelState *d_sels, MhfdStretch *d_sts,
+                          cudaStream_t s) {
+    int dev = 0, sms = 0;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    bsel_init<<<n_jobs, 256, 0, s>>>(d_jobs, d_sels, d_ranks);
+    // enough blocks per image to fill the GPU when all images are busy
+    int per = (sms * 8 + n_jobs - 1) / n_jobs;
+    if (per < 4) per = 4;
+    if (per > max_rows) per = max_rows;
+    for (int pass = 0; pass < max_passes; ++pass) {
+        bsel_hist<<<dim3(per, n_jobs), 256, 0, s>>>(d_jobs, d_sels, pass);
+        bsel_pick<<<n_jobs, 256, 0, s>>>(d_jobs, d_sels, d_sts, pass);
+    }
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
 
 int enqueue_stretch(const void *img, int dtype, int H, int W, long long pitch, long long k,
                     SelState *sel, MhfdStretch *st, cudaStream_t s) {

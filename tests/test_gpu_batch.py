@@ -1,0 +1,68 @@
+"""Batched detection (one persistent launch, CUDA graph) vs single detections.
+
+Each image's result in a batch of uneven sizes and mixed dtypes must be
+bit-identical to detecting it alone (the fused kernel is deterministic per
+tile and the per-image post-processing runs in the same order)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev(img):
+    if img.dtype == np.uint16:
+        return torch.from_numpy(img.view(np.int16)).cuda()
+    return torch.from_numpy(img).cuda()
+
+
+def _batch_images():
+    imgs = []
+    for j, (H, W, dt) in enumerate([(300, 410, "u16"), (256, 256, "u8"), (517, 130, "u16"),
+                                    (64, 900, "u8"), (401, 333, "u16"), (97, 97, "f32")]):
+        imgs.append(synth.make_scene(700 + j, synth.config2_spec(1.0 + j, H, W, dt)))
+    return imgs
+
+
+def test_batch_equals_single_detections():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2108_12050_gb300 as mhfd
+    torch.cuda.set_device(0)
+    imgs = _batch_images()
+    devs = [_dev(i) for i in imgs]
+    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5)
+    singles = [det(d) for d in devs]
+    for rep in range(3):          # capture, then replays of the graph
+        det.detect_batch(devs)
+        outs = det.wait_batch()
+        assert len(outs) == len(imgs)
+        for s, o in zip(singles, outs):
+            assert (o.lo, o.hi) == (s.lo, s.hi)
+            assert o.n_blobs == s.n_blobs and o.n_candidates_true == s.n_candidates_true
+            assert np.array_equal(o.blobs, s.blobs)
+            assert np.array_equal(o.per_scale, s.per_scale)
+    # new image contents with the same shapes replay the graph
+    devs2 = [d.flip(0).contiguous() for d in devs]
+    det.detect_batch(devs2)
+    outs2 = det.wait_batch()
+    for d, o in zip(devs2, outs2):
+        assert np.array_equal(det(d).blobs, o.blobs)
+    det.close()
+
+
+def test_batch_reports_graph_use():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2108_12050_gb300 as mhfd
+    imgs = _batch_images()[:3]
+    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5)
+    det.detect_batch([_dev(i) for i in imgs])
+    det.wait_batch()
+    # informative: the batch runs either from a captured graph or, where the
+    # capture is refused, from direct launches with identical results
+    assert det.batch_uses_graph() in (True, False)
+    det.close()
