@@ -181,6 +181,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-tiles", type=int, default=256)
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run R detections of the sigma_d=0 tile (for ncu captures)")
@@ -320,6 +321,7 @@ def main():
 
     cpu = None if args.no_cpu_baseline else cpu_baseline(host[0])
     batched = None if args.no_batch else bench_batch(mhfd, torch, stream)
+    serving = None if args.no_serve else bench_serve(mhfd, torch)
 
     per_tile.sort()
     p99 = per_tile[min(len(per_tile) - 1, int(math.ceil(0.99 * len(per_tile))) - 1)]
@@ -338,6 +340,7 @@ def main():
         "gpu_launches": launches_per_tile * len(tiles) * args.steps,
         "clocks": clk.summary(),
         "batched": batched,
+        "serving": serving,
         "focus_scores": dict(zip([str(s) for s in SIGMA_D], scores)),
         "focus_monotone_drop": all(scores[j] > scores[j + 1] for j in range(len(scores) - 1)),
     }
@@ -414,6 +417,81 @@ def bench_batch(mhfd, torch, stream, count=256):
                                         "ms": ms_fused},
             "speedup_vs_plain": ms_plain / ms_b, "speedup_vs_fused_single": ms_fused / ms_b,
             "inputs": "one rendered tile per (size, dtype), reused across the 256 tiles"}
+
+
+def _serve_tiles(torch):
+    """Pinned host tiles of sides {1024, 2048, 4096, 8192} x {uint8, uint16}
+    from the 12-bit scene at four defocus levels (crops for the small sides,
+    a 2x2 mosaic for 8192)."""
+    import synth
+    kinds = []
+    sds = (0.0, 2.0, 4.0, 8.0)
+    for j, side in enumerate((1024, 2048, 4096, 8192)):
+        base = synth.config2_tile(sds[j])
+        img16 = base[:side, :side] if side <= 4096 else np.tile(base, (2, 2))
+        img8 = np.clip(np.rint(img16.astype(np.float32) * (255.0 / 4095.0)), 0, 255).astype(np.uint8)
+        for img in (img8, np.ascontiguousarray(img16)):
+            t = torch.empty(img.shape, dtype=torch.uint8 if img.dtype == np.uint8 else torch.int16,
+                            pin_memory=True)
+            t.numpy()[:] = img if img.dtype == np.uint8 else img.view(np.int16)
+            kinds.append(t.numpy() if img.dtype == np.uint8 else t.numpy().view(np.uint16))
+    return kinds
+
+
+def bench_serve(mhfd, torch, rates=(100, 500, 2000), duration=1.0, n_slots=8,
+                budget=40 << 30):
+    """Poisson arrivals of tiles (side uniform in {1024, 2048, 4096, 8192},
+    uint8 or uint16) into the continuous-batching server under a 40 GB HBM
+    budget; p50/p99 latency (arrival to result on the host) and tiles/s.
+    Baseline: the same arrival stream served sequentially, one unfused plain
+    launch per tile (at the lowest rate; the plain path cannot keep up with
+    the others)."""
+    from paper_2108_12050_gb300 import serve
+    kinds = _serve_tiles(torch)
+    out = {"slots": n_slots, "budget_gb": budget / 2**30, "rates": {}}
+    srv = serve.Server(n_slots=n_slots, hbm_budget=budget, n=N_LAYERS, t_min=T_MIN,
+                       t_max=T_MAX, threshold=THR, overlap=OVERLAP)
+    for f in [srv.submit(k) for k in kinds]:   # warm every slot size
+        f.result()
+    for rate in rates:
+        arr = serve.poisson_arrivals(rate, duration, seed=5)
+        pick = np.random.default_rng([5, rate]).integers(0, len(kinds), len(arr))
+        tiles = [kinds[k] for k in pick]
+        res, wall = serve.run_open_loop(srv, tiles, arr)
+        lat = np.array([r.latency_ms for r in res])
+        px = sum(t.size for t in tiles)
+        out["rates"][str(rate)] = {
+            "requests": len(tiles), "tiles_per_s": len(tiles) / wall,
+            "mpixel_per_s": px / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall}
+    out["peak_in_flight"] = srv.stats["peak_in_flight"]
+    out["peak_budget_gb"] = srv.stats["peak_bytes"] / 2**30
+    srv.close()
+    # sequential plain per-tile launches on the lowest-rate stream
+    rate = rates[0]
+    arr = serve.poisson_arrivals(rate, duration, seed=5)
+    pick = np.random.default_rng([5, rate]).integers(0, len(kinds), len(arr))
+    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP)
+    buf = torch.empty(max(k.nbytes for k in kinds), dtype=torch.uint8, device="cuda")
+    lat = []
+    t0 = time.perf_counter()
+    for k, ta in zip(pick, arr):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        img = kinds[k]
+        host = torch.from_numpy(img.reshape(-1).view(np.uint8))
+        buf[:img.nbytes].copy_(host, non_blocking=True)
+        dev = buf[:img.nbytes].view(torch.uint8 if img.dtype == np.uint8 else torch.int16)
+        det.detect_plain(dev.view(img.shape))
+        det.wait()
+        lat.append(1e3 * (time.perf_counter() - t0 - ta))
+    wall = time.perf_counter() - t0
+    det.close()
+    out["sequential_plain"] = {"rate": rate, "requests": len(lat), "tiles_per_s": len(lat) / wall,
+                               "p50_ms": float(np.percentile(lat, 50)),
+                               "p99_ms": float(np.percentile(lat, 99))}
+    return out
 
 
 def tile_used(mhfd):

@@ -154,6 +154,10 @@ int mhfd_result_wait_batch(mhfd_detector *det, mhfd_result *outs, int32_t n);
  * launched directly. */
 int mhfd_batch_uses_graph(mhfd_detector *det);
 
+/* Non-blocking: 1 if the last detection (or batch) enqueued on `det` has
+ * finished on the GPU, 0 if it is still running, or an error. */
+int mhfd_result_ready(mhfd_detector *det);
+
 /* End-to-end convenience: h_img is HOST memory (pinned or pageable); the
  * image is copied to detector-owned device memory on `stream`, detected and
  * the results are waited for and written to *out.  Same errors as above. */

@@ -213,6 +213,13 @@ class Detector:
         _n.check(_n.lib().mhfd_result_wait_batch(self._h, rs, n))
         return [_to_result(rs[j], self.n) for j in range(n)]
 
+    def ready(self) -> bool:
+        """Non-blocking: has the last enqueued detection finished?"""
+        r = _n.lib().mhfd_result_ready(self._h)
+        if r < 0:
+            _n.check(r)
+        return r == 1
+
     def batch_uses_graph(self) -> bool:
         return _n.lib().mhfd_batch_uses_graph(self._h) == 1
 

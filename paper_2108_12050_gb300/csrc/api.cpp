@@ -3,6 +3,8 @@
 //   stretch select (§3) -> fused detection kernel (§2.2, Eq. 2, Eq. 3)
 //   -> tile-ordered gather -> overlap prune -> compaction into pinned memory.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <mutex>
@@ -885,8 +887,14 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
                 }
                 if (graph) cudaGraphDestroy(graph);
             }
-            cudaGetLastError();  // a refused capture falls back to direct launches
-            if (!done) b.graphs = false;
+            const cudaError_t last = cudaGetLastError();  // refused capture: direct launches
+            if (!done) {
+                b.graphs = false;
+                if (std::getenv("MHFD_DEBUG"))
+                    std::fprintf(stderr, "mhfd: batch graph capture refused (rc %d, %s; %s)\n", rc,
+                                 cudaGetErrorString(e != cudaSuccess ? e : last),
+                                 mhfd::t_err.c_str());
+            }
         }
         if (!done && (rc = batch_enqueue(d, n, max_passes, max_rows, total_items, s))) return rc;
     }
@@ -943,6 +951,16 @@ int mhfd_result_wait_batch(mhfd_detector *d, mhfd_result *outs, int32_t n) {
     }
     if (worst == MHFD_ERR_TIMEOUT) return fail(MHFD_ERR_TIMEOUT, "overlap prune did not settle");
     return worst;
+}
+
+int mhfd_result_ready(mhfd_detector *d) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    if (!d->pending && !d->b.pending) return fail(MHFD_ERR_INVALID_ARG, "nothing enqueued");
+    DeviceGuard g(d->device);
+    const cudaError_t e = cudaEventQuery(d->ev_done);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    return cuda_fail(e, "cudaEventQuery");
 }
 
 int mhfd_batch_uses_graph(mhfd_detector *d) {

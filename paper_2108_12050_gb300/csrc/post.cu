@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256)
     const long long n = (long long)cnt->n_stored;
     const long long per = (n + gridDim.x - 1) / gridDim.x;
     const long long beg = min(n, (long long)blockIdx.x * per), end = min(n, beg + per);
-    const long long base = (long long)cnt->blob_base, lim = (long long)cnt->n_blobs;
+    const long long obase = (long long)cnt->blob_base, lim = (long long)cnt->n_blobs;
     long long out = block_off[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (long long base = beg; base < end; base += blockDim.x) {
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(256)
             b.sigma = sigma[c.i];
             b.radius = radius_f[c.i];
             b.response = c.resp;
-            blobs[base + pos] = b;
+            blobs[obase + pos] = b;
             atomicAdd(&sh_scale[c.i & 63], 1);
         }
         out += total;
@@ -561,7 +561,20 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
                     (void *)&pb->cell_start, (void *)&pb->cell_items, (void *)&ctv, (void *)&W,
                     (void *)&pb->nb_idx, (void *)&pb->nb_cnt, (void *)&pb->state,
                     (void *)&max_sweeps, (void *)&max_ns};
-    MHFD_CUDA(cudaLaunchCooperativeKernel((const void *)lfmis_kernel, grid, 256, args, 0, s));
+    // the settle loop needs all its blocks resident: a cooperative launch
+    // guarantees it; inside a stream capture (graphs) a plain launch of a
+    // grid that fits the GPU is used, and its bounded waits turn any
+    // non-resident block into a reported timeout rather than a hang
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    MHFD_CUDA(cudaStreamIsCapturing(s, &capst));
+    if (capst == cudaStreamCaptureStatusActive) {
+        lfmis_kernel<<<grid, 256, 0, s>>>(cand, cnt, cs, ncx, ncy, pb->cell_start, pb->cell_items,
+                                          ctv, W, pb->nb_idx, pb->nb_cnt, pb->state, max_sweeps,
+                                          max_ns);
+        MHFD_CUDA(cudaGetLastError());
+    } else {
+        MHFD_CUDA(cudaLaunchCooperativeKernel((const void *)lfmis_kernel, grid, 256, args, 0, s));
+    }
     return MHFD_OK;
 }
 

@@ -1,0 +1,70 @@
+"""Continuous-batching server: each result equals the tile detected alone,
+requests overlap on the device, and the HBM budget gates admission."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PARAMS = dict(n=16, t_min=1.0, t_max=12.0, threshold=0.05, overlap=0.5)
+
+
+def _tiles():
+    out = []
+    for j, (H, W, dt) in enumerate([(512, 512, "u16"), (300, 700, "u8"), (1024, 256, "u16"),
+                                    (256, 256, "u8"), (640, 480, "f32"), (128, 900, "u16"),
+                                    (700, 300, "u8"), (512, 384, "u16")]):
+        out.append(synth.make_scene(900 + j, synth.config2_spec(0.5 * j, H, W, dt)))
+    return out
+
+
+def _alone(tiles):
+    import paper_2108_12050_gb300 as mhfd
+    det = mhfd.Detector(**PARAMS)
+    res = []
+    for t in tiles:
+        dev = torch.from_numpy(t.view(np.int16) if t.dtype == np.uint16 else t).cuda()
+        res.append(det(dev))
+    det.close()
+    return res
+
+
+def test_results_in_the_mix_equal_results_alone():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2108_12050_gb300 import serve
+    torch.cuda.set_device(0)
+    tiles = _tiles() * 3
+    ref = _alone(tiles[:8])
+    srv = serve.Server(n_slots=4, hbm_budget=8 << 30, **PARAMS)
+    futs = [srv.submit(t) for t in tiles]
+    got = [f.result(timeout=120) for f in futs]
+    stats = dict(srv.stats)
+    srv.close()
+    for j, r in enumerate(got):
+        want = ref[j % 8]
+        assert (r.lo, r.hi) == (want.lo, want.hi)
+        assert r.n_blobs == want.n_blobs
+        assert np.array_equal(r.blobs, want.blobs)
+    assert stats["completed"] == len(tiles)
+    assert stats["peak_in_flight"] > 1          # requests overlapped on the device
+
+
+def test_budget_limits_concurrency():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2108_12050_gb300 import serve
+    tiles = _tiles()[:4]
+    ref = _alone(tiles)
+    # room for the slots' fixed state plus exactly one 1024x256 uint16 tile
+    budget = 4 * serve._FIXED_BYTES + serve.footprint((1024, 256), np.uint16)
+    srv = serve.Server(n_slots=4, hbm_budget=budget, **PARAMS)
+    got = [f.result(timeout=120) for f in [srv.submit(t) for t in tiles]]
+    stats = dict(srv.stats)
+    srv.close()
+    assert stats["peak_bytes"] <= budget
+    for r, want in zip(got, ref):
+        assert np.array_equal(r.blobs, want.blobs)
