@@ -85,6 +85,10 @@ def _load():
         lib.oracle_detect.argtypes = [P, i32, i64, i64, i64, i32, dbl, dbl, dbl, dbl, dbl, dbl,
                                       i32, P, P, P, P, P, i64, P, P, P]
         lib.oracle_detect.restype = i64
+        lib.oracle_blur_adjoint.argtypes = [P, i64, i64, P, i32, i32, P]
+        lib.oracle_soft_score.argtypes = [P, i32, i64, i64, i64, dbl, dbl, P, i32, dbl, dbl, dbl, P,
+                                          P, P]
+        lib.oracle_soft_score.restype = dbl
         lib.oracle_set_threads.argtypes = [i32]
         lib.oracle_get_threads.restype = i32
         _lib = lib
@@ -221,6 +225,34 @@ def dog_at(img, lo, hi, t, xs, ys, truncate=4.0):
         _load().oracle_dog_at_many(_ptr(img), code, H, W, rs, float(lo), float(hi), _ptr(t), n,
                                    float(truncate), _ptr(xs), _ptr(ys), xs.size, _ptr(D))
     return D
+
+
+def blur_adjoint(img2d, g, boundary=REFLECT):
+    """Transpose of ``blur`` (same taps and boundary)."""
+    a = np.ascontiguousarray(img2d, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    H, W = a.shape
+    out = np.empty_like(a)
+    _load().oracle_blur_adjoint(_ptr(a), H, W, _ptr(g), (g.size - 1) // 2, int(boundary), _ptr(out))
+    return out
+
+
+def soft_score(img, n, tmin, tmax, w, *, tau, T=0.01, lo=None, hi=None, truncate=4.0,
+               grad=True):
+    """Soft focus score S = sum_i w_i mean sigmoid((D_i - tau)/T) with the
+    stretch bounds held fixed (computed from the image if not given).
+    Returns (S, mean_sig (= dS/dw), dS/dI or None)."""
+    img, code, H, W, rs = _img_args(img)
+    if lo is None or hi is None:
+        lo, hi = stretch_bounds(img)
+    t = ladder(n, tmin, tmax)
+    w = np.ascontiguousarray(w, np.float64)
+    ms = np.empty(n, np.float64)
+    dimg = np.empty((H, W), np.float64) if grad else None
+    S = _load().oracle_soft_score(_ptr(img), code, H, W, rs, float(lo), float(hi), _ptr(t), n,
+                                  float(truncate), float(tau), float(T), _ptr(w), _ptr(ms),
+                                  _ptr(dimg) if grad else None)
+    return S, ms, dimg
 
 
 class OracleResult(dict):

@@ -374,6 +374,96 @@ void oracle_dog_at(const void *img, int dtype, int64_t H, int64_t W, int64_t row
     }
 }
 
+/* Adjoint (transpose) of oracle_blur: out = B^T in for B = rows o columns.
+ * Every value in[y][x] is scattered with weight g[k] to the input positions
+ * the forward pass read it from; the transpose of the row pass comes first,
+ * then the transpose of the column pass.  With the reflect boundary the
+ * mirrored reads scatter back to their mirrored sources. */
+void oracle_blur_adjoint(const double *in, int64_t H, int64_t W, const double *g, int R,
+                         int boundary, double *out) {
+    double *tmp = (double *)calloc((size_t)(H * W), sizeof(double));
+    for (int64_t y = 0; y < H; ++y)
+        for (int64_t x = 0; x < W; ++x) {
+            const double v = in[y * W + x];
+            for (int k = -R; k <= R; ++k) tmp[y * W + boundary_index(x + k, W, boundary)] += g[k + R] * v;
+        }
+    for (int64_t p = 0; p < H * W; ++p) out[p] = 0.0;
+    for (int64_t y = 0; y < H; ++y)
+        for (int64_t x = 0; x < W; ++x) {
+            const double v = tmp[y * W + x];
+            for (int k = -R; k <= R; ++k) out[boundary_index(y + k, H, boundary) * W + x] += g[k + R] * v;
+        }
+    free(tmp);
+}
+
+/* Soft focus score over the ladder t[0..n] (n DoG layers), the stretch
+ * bounds lo/hi held fixed:
+ *   S = sum_i w_i mean_{x,y} sigmoid((D_i(x,y) - tau) / T),  D_i of Eq. 2.
+ * mean_sig[i] receives mean_{x,y} sigmoid(...) (= dS/dw_i).  If dimg is not
+ * NULL it receives dS/dI in input units by the exact transpose of every
+ * linear step: dD_i = w_i s (1 - s) / (T N); dL_l = t_{l-1} dD_{l-1} -
+ * t_l dD_l; dI' = sum_l B_l^T dL_l; dI = dI' / (hi - lo) where lo < I < hi
+ * (the clamp of the stretch passes nothing elsewhere).  Returns S. */
+double oracle_soft_score(const void *img, int dtype, int64_t H, int64_t W, int64_t row_stride_bytes,
+                         double lo, double hi, const double *t, int n, double truncate, double tau,
+                         double T, const double *w, double *mean_sig, double *dimg) {
+    const int64_t P = H * W;
+    double *Ip = (double *)malloc((size_t)P * sizeof(double));
+    oracle_stretch(img, dtype, H, W, row_stride_bytes, lo, hi, Ip);
+    double *L = (double *)malloc((size_t)(P * (n + 1)) * sizeof(double));
+    int *Rs = (int *)malloc((size_t)(n + 1) * sizeof(int));
+    double **G = (double **)malloc((size_t)(n + 1) * sizeof(double *));
+    for (int l = 0; l <= n; ++l) {
+        Rs[l] = oracle_kernel_radius(t[l], truncate);
+        G[l] = (double *)malloc((size_t)(2 * Rs[l] + 1) * sizeof(double));
+        oracle_kernel(t[l], Rs[l], G[l]);
+        oracle_blur(Ip, H, W, G[l], Rs[l], OR_REFLECT, L + (int64_t)l * P);
+    }
+    double S = 0.0;
+    double *gD = dimg ? (double *)calloc((size_t)(P * n), sizeof(double)) : NULL;
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int64_t p = 0; p < P; ++p) {
+            const double d = t[i] * (L[(int64_t)(i + 1) * P + p] - L[(int64_t)i * P + p]);
+            const double sg = 1.0 / (1.0 + exp(-(d - tau) / T));
+            acc += sg;
+            if (gD) gD[(int64_t)i * P + p] = w[i] * sg * (1.0 - sg) / (T * (double)P);
+        }
+        mean_sig[i] = acc / (double)P;
+        S += w[i] * mean_sig[i];
+    }
+    if (dimg) {
+        double *h = (double *)malloc((size_t)P * sizeof(double));
+        double *adj = (double *)malloc((size_t)P * sizeof(double));
+        double *gI = (double *)calloc((size_t)P, sizeof(double));
+        for (int l = 0; l <= n; ++l) {
+            for (int64_t p = 0; p < P; ++p) {
+                double v = 0.0;
+                if (l >= 1) v += t[l - 1] * gD[(int64_t)(l - 1) * P + p];
+                if (l <= n - 1) v -= t[l] * gD[(int64_t)l * P + p];
+                h[p] = v;
+            }
+            oracle_blur_adjoint(h, H, W, G[l], Rs[l], OR_REFLECT, adj);
+            for (int64_t p = 0; p < P; ++p) gI[p] += adj[p];
+        }
+        for (int64_t y = 0; y < H; ++y)
+            for (int64_t x = 0; x < W; ++x) {
+                const double v = value_at(img, dtype, row_stride_bytes, y, x);
+                dimg[y * W + x] = (hi > lo && v > lo && v < hi) ? gI[y * W + x] / (hi - lo) : 0.0;
+            }
+        free(h);
+        free(adj);
+        free(gI);
+        free(gD);
+    }
+    for (int l = 0; l <= n; ++l) free(G[l]);
+    free(G);
+    free(Rs);
+    free(L);
+    free(Ip);
+    return S;
+}
+
 /* oracle_dog_at for a list of pixels; D laid out [m][n]. */
 void oracle_dog_at_many(const void *img, int dtype, int64_t H, int64_t W, int64_t row_stride_bytes,
                         double lo, double hi, const double *t, int n, double truncate,

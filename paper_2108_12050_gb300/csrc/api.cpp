@@ -101,6 +101,8 @@ struct mhfd_detector {
         size_t h_arena_cap = 0;
         std::vector<long long> key;                    // shape of the captured graph
         cudaGraphExec_t exec = nullptr;
+        cudaStream_t own = nullptr;                    // capture/replay stream
+        cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
         bool graphs = true;
         bool pending = false;
         int n = 0;
@@ -362,6 +364,9 @@ void release(mhfd_detector *d) {
         if (p) cudaFree(p);
     free_conflict_table(&d->ct);
     if (d->b.exec) cudaGraphExecDestroy(d->b.exec);
+    if (d->b.own) cudaStreamDestroy(d->b.own);
+    if (d->b.ev_fork) cudaEventDestroy(d->b.ev_fork);
+    if (d->b.ev_join) cudaEventDestroy(d->b.ev_join);
     void *bdev[] = {d->b.d_jobs, d->b.d_ranks, d->b.d_sels, d->b.d_sts, d->b.d_queue,
                     d->b.d_arena_n, d->b.d_arena};
     for (void *p : bdev)
@@ -857,8 +862,19 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
         key.push_back(dtypes[j]);
         key.push_back((long long)pitches[j]);
     }
-    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t user = (cudaStream_t)stream;
     d->timed = d->p.timing != 0;
+    // the batch runs on a detector-owned stream ordered after the caller's
+    // stream and joined back into it (the caller's stream may be the legacy
+    // default stream, which cannot be captured)
+    if (!b.own) {
+        MHFD_CUDA(cudaStreamCreateWithFlags(&b.own, cudaStreamNonBlocking));
+        MHFD_CUDA(cudaEventCreateWithFlags(&b.ev_fork, cudaEventDisableTiming));
+        MHFD_CUDA(cudaEventCreateWithFlags(&b.ev_join, cudaEventDisableTiming));
+    }
+    MHFD_CUDA(cudaEventRecord(b.ev_fork, user));
+    MHFD_CUDA(cudaStreamWaitEvent(b.own, b.ev_fork, 0));
+    cudaStream_t s = b.own;
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_t0, s));
     if (b.graphs && b.exec && key == b.key) {
         MHFD_CUDA(cudaGraphLaunch(b.exec, s));
@@ -900,6 +916,8 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
     }
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_end, s));
     MHFD_CUDA(cudaEventRecord(d->ev_done, s));
+    MHFD_CUDA(cudaEventRecord(b.ev_join, s));
+    MHFD_CUDA(cudaStreamWaitEvent(user, b.ev_join, 0));
     b.n = n;
     b.pending = true;
     b.copied = false;

@@ -188,13 +188,17 @@ class Server:
                     res = s["det"].wait()
                     res.latency_ms = 1e3 * (time.perf_counter() - req.t_arrive)
                     res.queue_ms = 1e3 * (req.t_admit - req.t_arrive)
-                    req.future.set_result(res)
+                    err = None
                 except Exception as e:  # pragma: no cover - surfaced to the client
-                    req.future.set_exception(e)
+                    err = e
                 with self.cv:
                     s["req"] = None
                     s["host_ref"] = None
                     self.stats["completed"] += 1
+                if err is None:
+                    req.future.set_result(res)
+                else:
+                    req.future.set_exception(err)
                 done_any = True
             if not done_any:
                 time.sleep(20e-6)
