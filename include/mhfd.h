@@ -154,6 +154,23 @@ int mhfd_result_wait_batch(mhfd_detector *det, mhfd_result *outs, int32_t n);
  * launched directly. */
 int mhfd_batch_uses_graph(mhfd_detector *det);
 
+/* Differentiable soft focus score of one image, with the stretch bounds of
+ * §3 held fixed (detached):
+ *   S = sum_i w_i mean_{x,y} sigmoid((D_i(x,y) - tau) / temperature),
+ * D_i the DoG responses of Eq. 2 over the detector's ladder.  d_w: n floats
+ * (device).  Writes *d_S and d_mean_sig[i] = mean sigmoid of layer i (device).
+ * If d_dimg is not NULL (device, H x W float32) the backward pass also runs,
+ * for the upstream gradient grad_s: d_dimg = grad_s dS/dI in input units (the
+ * exact transpose of the DoG, of both reflect-boundary blur passes and of the
+ * clamp, which passes gradient only strictly between lo and hi) and, if d_dw
+ * is not NULL, d_dw[i] = grad_s * mean sigmoid of layer i.  The Gaussian
+ * levels are recomputed on every call (nothing is kept between calls).
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA, OOM. */
+int mhfd_soft_score(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H, int32_t W,
+                    size_t pitch_bytes, const float *d_w, float tau, float temperature,
+                    float grad_s, void *stream, float *d_S, float *d_mean_sig, float *d_dimg,
+                    float *d_dw);
+
 /* Non-blocking: 1 if the last detection (or batch) enqueued on `det` has
  * finished on the GPU, 0 if it is still running, or an error. */
 int mhfd_result_ready(mhfd_detector *det);

@@ -24,7 +24,8 @@ LIB = os.path.join(PKG, "libmhfd.so")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "jit.cpp", "stretch.cu", "post.cu", "plain.cu", "probe.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "jit.cpp", "stretch.cu", "post.cu", "plain.cu", "probe.cu", "noalloc.cu",
+           "soft.cu"]
 EMBED = ["mhfd_types.h", "detect_kernel.cuh"]
 
 

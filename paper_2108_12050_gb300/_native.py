@@ -28,7 +28,7 @@ NMS_PAPER, NMS_LOCAL26 = 0, 1
 EXPORTS = [
     "mhfd_default_params", "mhfd_create_detector", "mhfd_destroy_detector", "mhfd_detect",
     "mhfd_result_wait", "mhfd_detect_batch", "mhfd_result_wait_batch", "mhfd_batch_uses_graph",
-    "mhfd_result_ready",
+    "mhfd_result_ready", "mhfd_soft_score",
     "mhfd_detect_host", "mhfd_detect_plain", "mhfd_debug_stack",
     "mhfd_prune", "mhfd_prune_noalloc", "mhfd_tile_configs", "mhfd_chosen_tile", "mhfd_precompile",
     "mhfd_last_timing", "mhfd_probe_ffma_peak", "mhfd_last_error", "mhfd_version",
@@ -109,6 +109,8 @@ def lib():
         L.mhfd_result_wait_batch.argtypes = [P, ctypes.POINTER(Result), I32]
         L.mhfd_batch_uses_graph.argtypes = [P]
         L.mhfd_result_ready.argtypes = [P]
+        L.mhfd_soft_score.argtypes = [P, P, I32, I32, I32, SZ, P, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float, P, P, P, P, P]
         L.mhfd_detect_plain.argtypes = [P, P, I32, I32, I32, SZ, P]
         L.mhfd_debug_stack.argtypes = [P, P, I32, I32, I32, SZ, P, P, P, P]
         L.mhfd_prune.argtypes = [P, P, P, P, P, I64, I32, I32, P, P]

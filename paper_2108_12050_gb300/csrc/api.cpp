@@ -59,6 +59,7 @@ struct mhfd_detector {
     int *d_tapoff = nullptr;
     int *block_tmp = nullptr;
     double *block_sum = nullptr;
+    double *soft_part = nullptr;   // per-block layer sums of the soft score
     long long cap = 0;           // candidate list capacity
     MhfdCand *cand = nullptr;
     // grown with the image
@@ -359,7 +360,8 @@ void release(mhfd_detector *d) {
     void *dev_ptrs[] = {d->sel, d->st, d->cnt, d->d_radius, d->d_sigma, d->d_radius_f, d->d_taps,
                         d->d_tsc, d->d_tapoff, d->block_tmp, d->block_sum, d->cand, d->tile_count,
                         d->tile_off, d->stage, d->pb.cell_cnt, d->pb.cell_start, d->pb.cell_items,
-                        d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->d_blobs, d->d_cands, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
+                        d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->d_blobs, d->d_cands,
+                        d->soft_part, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
     for (void *p : dev_ptrs)
         if (p) cudaFree(p);
     free_conflict_table(&d->ct);
@@ -969,6 +971,26 @@ int mhfd_result_wait_batch(mhfd_detector *d, mhfd_result *outs, int32_t n) {
     }
     if (worst == MHFD_ERR_TIMEOUT) return fail(MHFD_ERR_TIMEOUT, "overlap prune did not settle");
     return worst;
+}
+
+int mhfd_soft_score(mhfd_detector *d, const void *img, int32_t dtype, int32_t H, int32_t W,
+                    size_t pitch, const float *d_w, float tau, float temperature, float grad_s,
+                    void *stream, float *d_S, float *d_mean_sig, float *d_dimg, float *d_dw) {
+    if (!d || !d_w || !d_S || !d_mean_sig) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    if (!(temperature > 0.0f) || !std::isfinite(tau))
+        return fail(MHFD_ERR_INVALID_ARG, "temperature must be > 0 and tau finite");
+    int rc = check_image(img, dtype, H, W, pitch);
+    if (rc) return rc;
+    DeviceGuard g(d->device);
+    if ((rc = ensure_image_capacity(d, H, W, true))) return rc;
+    constexpr int kMaxBlocks = 2048;
+    if (!d->soft_part && (rc = dalloc(&d->soft_part, (size_t)kMaxBlocks * 64))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = enqueue_stretch(img, dtype, H, W, (long long)pitch, clip_rank(d, H, W), d->sel, d->st, s);
+    if (rc) return rc;
+    return enqueue_soft(img, dtype, H, W, (long long)pitch, d->st, (int)d->R.size(), d->R,
+                        d->d_taps, d->d_tsc, d_w, tau, temperature, grad_s, d->pL, d->pT, d->pI,
+                        d->soft_part, kMaxBlocks, d_S, d_mean_sig, d_dimg, d_dw, s);
 }
 
 int mhfd_result_ready(mhfd_detector *d) {

@@ -155,12 +155,25 @@ int enqueue_keep(const int *state, const Counters *cnt, long long n, int prune_o
                  cudaStream_t s);
 
 // ---------------------------------------------------------- plain path
+// I' (stretched, centred) and every Gaussian level L_l as full planes.
+int enqueue_stack(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
+                  int n_levels, const std::vector<int> &R, const float *d_taps, float *scratch_I,
+                  float *scratch_T, float *scratch_L, cudaStream_t s);
 int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
                   const MhfdStretch *st, int n_levels, const std::vector<int> &R,
                   const float *d_taps, const int *d_tapoff, const float *d_tsc, int mode,
                   float thr, float *scratch_I, float *scratch_T, float *scratch_L,
                   float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
                   MhfdCand *stage, int cap_tile, int tile, int *n_tiles_out, cudaStream_t s);
+
+// ------------------------------------------------------------ soft score
+// Forward (and, with d_dimg, the adjoint) of the soft focus score on the
+// level planes L (n_levels planes of H*W, overwritten by the backward).
+int enqueue_soft(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
+                 int n_levels, const std::vector<int> &R, const float *d_taps, const float *d_tsc,
+                 const float *d_w, float tau, float temp, float grad_s, float *scratch_L,
+                 float *scratch_T, float *scratch_G, double *block_part, int max_blocks,
+                 float *d_S, float *d_mean_sig, float *d_dimg, float *d_dw, cudaStream_t s);
 
 // ------------------------------------------------------------- probe
 int probe_ffma(cudaStream_t s, double *ops_per_s);

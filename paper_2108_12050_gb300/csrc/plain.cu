@@ -192,14 +192,9 @@ __global__ void __launch_bounds__(kT *kT)
 
 }  // namespace
 
-int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
-                  const MhfdStretch *st, int n_levels, const std::vector<int> &R,
-                  const float *d_taps, const int *d_tapoff, const float *d_tsc, int mode,
-                  float thr, float *scratch_I, float *scratch_T, float *scratch_L,
-                  float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
-                  MhfdCand *stage, int cap_tile, int tile, int *n_tiles_out, cudaStream_t s) {
-    (void)d_tapoff;
-    (void)tile;
+int enqueue_stack(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
+                  int n_levels, const std::vector<int> &R, const float *d_taps, float *scratch_I,
+                  float *scratch_T, float *scratch_L, cudaStream_t s) {
     const dim3 blk(256);
     const dim3 grd((W + 255) / 256, H);
     plain_stretch<<<grd, blk, 0, s>>>(reinterpret_cast<const char *>(img), dtype, H, W, pitch, st,
@@ -212,6 +207,22 @@ int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
                                         scratch_L + (long long)l * plane);
         off += R[l] + 1;
     }
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
+
+int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
+                  const MhfdStretch *st, int n_levels, const std::vector<int> &R,
+                  const float *d_taps, const int *d_tapoff, const float *d_tsc, int mode,
+                  float thr, float *scratch_I, float *scratch_T, float *scratch_L,
+                  float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
+                  MhfdCand *stage, int cap_tile, int tile, int *n_tiles_out, cudaStream_t s) {
+    (void)d_tapoff;
+    (void)tile;
+    int rc = enqueue_stack(img, dtype, H, W, pitch, st, n_levels, R, d_taps, scratch_I, scratch_T,
+                           scratch_L, s);
+    if (rc) return rc;
+    const long long plane = (long long)H * W;
     plain_dog<<<(unsigned)((plane + 255) / 256), 256, 0, s>>>(scratch_L, plane, n_levels, d_tsc,
                                                               mode, scratch_M, scratch_A,
                                                               scratch_D);

@@ -1,0 +1,90 @@
+"""Differentiable soft focus score (autograd wrapper of mhfd_soft_score).
+
+    S(I, w) = sum_i w_i mean_{x,y} sigmoid((D_i(x,y) - tau) / T)
+
+where D_i are the DoG responses (Eq. 2) of the stretched image (§3; the
+stretch bounds are held fixed).  The hard detector counts features above the
+threshold; this score replaces the count by a smooth per-scale occupancy so
+that per-scale weights can be calibrated against known defocus by gradient
+descent.  Forward and backward both run in the library's CUDA kernels; the
+backward recomputes the Gaussian levels instead of keeping them.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import Detector, _native as _n, _stream_handle, _dtype_code
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def soft_score(det: Detector, img: torch.Tensor, w: torch.Tensor, tau: float, T: float = 0.01,
+               grad_s: float = 0.0, want_grad: bool = False, stream=None):
+    """Returns (S, mean_sig, dS/dI * grad_s or None, dS/dw * grad_s or None)."""
+    ptr, code, H, W, pitch = det._img_args(img)
+    w = w.detach().to(device=img.device, dtype=torch.float32).contiguous()
+    S = torch.empty(1, dtype=torch.float32, device=img.device)
+    ms = torch.empty(det.n, dtype=torch.float32, device=img.device)
+    dimg = torch.empty((H, W), dtype=torch.float32, device=img.device) if want_grad else None
+    dw = torch.empty(det.n, dtype=torch.float32, device=img.device) if want_grad else None
+    _n.check(_n.lib().mhfd_soft_score(det._h, ptr, code, H, W, pitch, _vp(w), ctypes.c_float(tau),
+                                      ctypes.c_float(T), ctypes.c_float(grad_s),
+                                      _stream_handle(stream), _vp(S), _vp(ms), _vp(dimg),
+                                      _vp(dw)))
+    return S[0], ms, dimg, dw
+
+
+class SoftFocus(torch.autograd.Function):
+    """S = soft focus score of `img` (float32, CUDA) with per-scale weights
+    `w` (n,); differentiable in both."""
+
+    @staticmethod
+    def forward(ctx, img, w, det, tau, T):
+        S, ms, _, _ = soft_score(det, img, w, tau, T)
+        ctx.save_for_backward(img, w)
+        ctx.det, ctx.tau, ctx.T = det, tau, T
+        ctx.ms = ms
+        return S
+
+    @staticmethod
+    def backward(ctx, gS):
+        img, w = ctx.saved_tensors
+        g = float(gS)
+        need_img = ctx.needs_input_grad[0]
+        if need_img:
+            _, _, dimg, dw = soft_score(ctx.det, img, w, ctx.tau, ctx.T, grad_s=g,
+                                        want_grad=True)
+        else:
+            dimg, dw = None, ctx.ms * g
+        return dimg, dw, None, None, None
+
+
+def features(det, imgs, tau, T=0.01):
+    """Per-image mean sigmoid of every layer (S is linear in w: S = w . f)."""
+    n = det.n
+    ones = torch.ones(n, device="cuda")
+    return torch.stack([soft_score(det, im, ones, tau, T)[1] for im in imgs])
+
+
+def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0):
+    """Calibrate per-scale weights w and bias b so that S(I, w) + b regresses
+    `targets` (e.g. the known defocus sigma_d), by Adam through SoftFocus.
+    Returns (w, b, losses)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    w = (0.1 * torch.randn(det.n, generator=g)).cuda().requires_grad_(True)
+    b = torch.zeros(1, device="cuda", requires_grad=True)
+    y = torch.as_tensor(targets, dtype=torch.float32, device="cuda")
+    opt = torch.optim.Adam([w, b], lr=lr)
+    losses = []
+    for _ in range(steps):
+        opt.zero_grad()
+        pred = torch.stack([SoftFocus.apply(im, w, det, tau, T) for im in imgs]) + b
+        loss = torch.mean((pred - y) ** 2)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    return w.detach(), b.detach(), losses

@@ -1,0 +1,81 @@
+"""Soft focus score on the GPU vs the FP64 oracle (score, per-layer means,
+image gradient by the hand-written adjoint), the autograd wrapper, and the
+per-scale weight calibration against known defocus (Adam, 200 steps)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    torch.cuda.set_device(0)
+
+
+def _f32_tile(j, H, W):
+    img, sd = synth.config4_tile(j, H=H, W=W)
+    return img, sd
+
+
+@pytest.mark.parametrize("n,tmin,tmax,shape", [(4, 1.0, 4.0, (96, 80)), (16, 1.0, 12.0, (64, 64)),
+                                               (16, 1.0, 12.0, (150, 130))])
+def test_soft_score_and_gradient_match_oracle(n, tmin, tmax, shape):
+    import paper_2108_12050_gb300 as mhfd
+    from paper_2108_12050_gb300 import soft
+    img, _ = _f32_tile(3, *shape)
+    w = np.linspace(-0.5, 1.5, n)
+    tau, T = 0.05, 0.01
+    det = mhfd.Detector(n, tmin, tmax, threshold=tau)
+    dev = torch.from_numpy(img).cuda()
+    S, ms, dimg, dw = soft.soft_score(det, dev, torch.tensor(w, dtype=torch.float32), tau, T,
+                                      grad_s=1.0, want_grad=True)
+    lo, hi = oracle.stretch_bounds(img)
+    S_ref, ms_ref, g_ref = oracle.soft_score(img, n, tmin, tmax, w, tau=tau, T=T, lo=lo, hi=hi)
+    np.testing.assert_allclose(ms.cpu().numpy(), ms_ref, rtol=0, atol=1e-4)
+    assert abs(float(S) - S_ref) <= 1e-4 * np.abs(w).sum()
+    np.testing.assert_allclose(dw.cpu().numpy(), ms_ref, rtol=0, atol=1e-4)
+    g = dimg.cpu().numpy()
+    scale = np.abs(g_ref).max()
+    assert scale > 0
+    err = np.abs(g - g_ref).max()
+    assert err <= 2e-3 * scale, (err, scale)
+    det.close()
+
+
+def test_autograd_wrapper():
+    import paper_2108_12050_gb300 as mhfd
+    from paper_2108_12050_gb300 import soft
+    img, _ = _f32_tile(4, 80, 90)
+    det = mhfd.Detector(4, 1.0, 4.0, threshold=0.05)
+    x = torch.from_numpy(img).cuda().requires_grad_(True)
+    w = torch.tensor([0.5, 1.0, -0.3, 0.8], device="cuda", requires_grad=True)
+    S = soft.SoftFocus.apply(x, w, det, 0.05, 0.01)
+    (2.0 * S).backward()
+    _, ms, dimg, _ = soft.soft_score(det, x.detach(), w.detach(), 0.05, 0.01, grad_s=2.0,
+                                     want_grad=True)
+    assert torch.allclose(w.grad, 2.0 * ms, atol=1e-6)
+    assert torch.allclose(x.grad, dimg, atol=1e-7)
+    det.close()
+
+
+def test_weight_fit_regresses_defocus():
+    import paper_2108_12050_gb300 as mhfd
+    from paper_2108_12050_gb300 import soft
+    tiles, sds = [], []
+    for j in range(16):
+        img, sd = _f32_tile(j, 192, 192)
+        tiles.append(torch.from_numpy(img).cuda())
+        sds.append(sd)
+    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05)
+    w, b, losses = soft.fit_weights(det, tiles, sds, tau=0.05, steps=200)
+    var = float(np.var(sds))
+    assert losses[-1] < 0.5 * var, (losses[0], losses[-1], var)
+    assert losses[-1] < losses[0]
+    det.close()
