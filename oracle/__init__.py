@@ -85,6 +85,10 @@ def _load():
         lib.oracle_detect.argtypes = [P, i32, i64, i64, i64, i32, dbl, dbl, dbl, dbl, dbl, dbl,
                                       i32, P, P, P, P, P, i64, P, P, P]
         lib.oracle_detect.restype = i64
+        lib.oracle_log_stack.argtypes = [P, i64, i64, P, i32, dbl, i32, P]
+        lib.oracle_detect_ex.argtypes = [P, i32, i64, i64, i64, i32, dbl, dbl, dbl, dbl, dbl, dbl,
+                                         i32, i32, i32, P, P, P, P, P, i64, P, P, P]
+        lib.oracle_detect_ex.restype = i64
         lib.oracle_blur_adjoint.argtypes = [P, i64, i64, P, i32, i32, P]
         lib.oracle_soft_score.argtypes = [P, i32, i64, i64, i64, dbl, dbl, P, i32, dbl, dbl, dbl, P,
                                           P, P]
@@ -175,6 +179,17 @@ def dog_stack(Ip, t, truncate=4.0, boundary=REFLECT):
     return D
 
 
+def log_stack(Ip, t, truncate=4.0, boundary=REFLECT):
+    """§2.2: t_i^2 grad^2 L(t_i) for the first n scales (5-point Laplacian) -> (n, H, W)."""
+    a = np.ascontiguousarray(Ip, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    H, W = a.shape
+    n = t.size - 1
+    D = np.empty((n, H, W), np.float64)
+    _load().oracle_log_stack(_ptr(a), H, W, _ptr(t), n, float(truncate), int(boundary), _ptr(D))
+    return D
+
+
 def _nms(fn, D, thr, cap):
     D = np.ascontiguousarray(D, dtype=np.float64)
     n, H, W = D.shape
@@ -259,19 +274,24 @@ class OracleResult(dict):
     __getattr__ = dict.__getitem__
 
 
+RESP_DOG, RESP_LOG = 0, 1
+
+
 def detect(img, n, tmin, tmax, *, threshold, overlap=0.5, mode=MODE_PAPER, truncate=4.0,
-           clip=0.00175, cap=None):
-    """Algorithm 1 (stretch, stack, DoG, argmax + max-pool) plus threshold and prune."""
+           clip=0.00175, cap=None, response=RESP_DOG, boundary=REFLECT):
+    """Algorithm 1 (stretch, stack, DoG, argmax + max-pool) plus threshold and prune;
+    optionally the scale-normalised Laplacian response and the periodic boundary."""
     img, code, H, W, rs = _img_args(img)
     cap = int(cap if cap is not None else H * W * (1 if mode == MODE_PAPER else n))
     cap = max(cap, 1)
     x = np.empty(cap, np.int32); y = np.empty(cap, np.int32); i = np.empty(cap, np.int32)
     r = np.empty(cap, np.float64); keep = np.zeros(cap, np.uint8)
     nk = ctypes.c_int64(); lo = ctypes.c_double(); hi = ctypes.c_double()
-    cnt = _load().oracle_detect(_ptr(img), code, H, W, rs, int(n), float(tmin), float(tmax),
-                                float(truncate), float(clip), float(threshold), float(overlap),
-                                int(mode), _ptr(x), _ptr(y), _ptr(i), _ptr(r), _ptr(keep), cap,
-                                ctypes.byref(nk), ctypes.byref(lo), ctypes.byref(hi))
+    cnt = _load().oracle_detect_ex(_ptr(img), code, H, W, rs, int(n), float(tmin), float(tmax),
+                                   float(truncate), float(clip), float(threshold), float(overlap),
+                                   int(mode), int(response), int(boundary), _ptr(x), _ptr(y),
+                                   _ptr(i), _ptr(r), _ptr(keep), cap, ctypes.byref(nk),
+                                   ctypes.byref(lo), ctypes.byref(hi))
     if cnt < 0:
         raise ValueError("oracle_detect failed")
     m = min(cnt, cap)

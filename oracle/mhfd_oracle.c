@@ -184,6 +184,33 @@ void oracle_dog_stack(const double *Ip, int64_t H, int64_t W, const double *t, i
     free(Lcur);
 }
 
+/* §2.2, the response the DoG approximates: the scale-normalised Laplacian
+ * t_i^2 grad^2 L(., t_i), i = 0..n-1 (scales t_1..t_n), with the Laplacian
+ * discretised by the 5-point stencil on the level (neighbours through the
+ * same boundary as the blur).  D laid out as n planes of H x W. */
+void oracle_log_stack(const double *Ip, int64_t H, int64_t W, const double *t, int n,
+                      double truncate, int boundary, double *D) {
+    int64_t P = H * W;
+    double *L = (double *)malloc((size_t)P * sizeof(double));
+    for (int i = 0; i < n; ++i) {
+        int R = oracle_kernel_radius(t[i], truncate);
+        double *g = (double *)malloc((size_t)(2 * R + 1) * sizeof(double));
+        oracle_kernel(t[i], R, g);
+        oracle_blur(Ip, H, W, g, R, boundary, L);
+        free(g);
+        for (int64_t y = 0; y < H; ++y)
+            for (int64_t x = 0; x < W; ++x) {
+                const double c = L[y * W + x];
+                const double lap = L[y * W + boundary_index(x - 1, W, boundary)] +
+                                   L[y * W + boundary_index(x + 1, W, boundary)] +
+                                   L[boundary_index(y - 1, H, boundary) * W + x] +
+                                   L[boundary_index(y + 1, H, boundary) * W + x] - 4.0 * c;
+                D[(int64_t)i * P + y * W + x] = t[i] * t[i] * lap;
+            }
+    }
+    free(L);
+}
+
 /* Eq. 3, the paper's mode: M = max_i D_i, i_hat = first maximiser; (x, y)
  * is kept when M > thr and M >= M at every in-image 8-neighbour (comparison
  * with a 3x3 max-pool).  Returns the number of features; writes at most
@@ -474,6 +501,12 @@ void oracle_dog_at_many(const void *img, int dtype, int64_t H, int64_t W, int64_
                       D + j * n);
 }
 
+int64_t oracle_detect_ex(const void *img, int dtype, int64_t H, int64_t W, int64_t row_stride_bytes,
+                         int n, double tmin, double tmax, double truncate, double clip, double thr,
+                         double overlap, int mode, int response, int boundary, int32_t *cx,
+                         int32_t *cy, int32_t *ci, double *cresp, uint8_t *keep, int64_t cap,
+                         int64_t *n_kept, double *lo_out, double *hi_out);
+
 /* Whole method on one image (Algorithm 1 without distribution, plus the
  * threshold and the prune): stretch, ladder, stack, NMS, prune.
  * mode 0 = the paper's argmax/max-pool, 1 = 26-neighbour.
@@ -484,6 +517,18 @@ int64_t oracle_detect(const void *img, int dtype, int64_t H, int64_t W, int64_t 
                       int n, double tmin, double tmax, double truncate, double clip, double thr,
                       double overlap, int mode, int32_t *cx, int32_t *cy, int32_t *ci, double *cresp,
                       uint8_t *keep, int64_t cap, int64_t *n_kept, double *lo_out, double *hi_out) {
+    return oracle_detect_ex(img, dtype, H, W, row_stride_bytes, n, tmin, tmax, truncate, clip, thr,
+                            overlap, mode, 0, OR_REFLECT, cx, cy, ci, cresp, keep, cap, n_kept,
+                            lo_out, hi_out);
+}
+
+/* As oracle_detect with a choice of response (0: DoG of Eq. 2, 1: the
+ * scale-normalised Laplacian t^2 grad^2 L) and boundary (reflect/periodic). */
+int64_t oracle_detect_ex(const void *img, int dtype, int64_t H, int64_t W, int64_t row_stride_bytes,
+                         int n, double tmin, double tmax, double truncate, double clip, double thr,
+                         double overlap, int mode, int response, int boundary, int32_t *cx,
+                         int32_t *cy, int32_t *ci, double *cresp, uint8_t *keep, int64_t cap,
+                         int64_t *n_kept, double *lo_out, double *hi_out) {
     double lo, hi;
     if (oracle_stretch_bounds(img, dtype, H, W, row_stride_bytes, clip, &lo, &hi) != 0) return -1;
     *lo_out = lo;
@@ -493,7 +538,10 @@ int64_t oracle_detect(const void *img, int dtype, int64_t H, int64_t W, int64_t 
     double *t = (double *)malloc((size_t)(n + 1) * sizeof(double));
     oracle_ladder(n, tmin, tmax, t);
     double *D = (double *)malloc((size_t)(H * W) * (size_t)n * sizeof(double));
-    oracle_dog_stack(Ip, H, W, t, n, truncate, OR_REFLECT, D);
+    if (response == 1)
+        oracle_log_stack(Ip, H, W, t, n, truncate, boundary, D);
+    else
+        oracle_dog_stack(Ip, H, W, t, n, truncate, boundary, D);
     int64_t cnt = mode == 0 ? oracle_nms_paper(D, n, H, W, thr, cx, cy, ci, cresp, cap)
                             : oracle_nms_local26(D, n, H, W, thr, cx, cy, ci, cresp, cap);
     double *radius = (double *)malloc((size_t)n * sizeof(double));

@@ -409,3 +409,57 @@ def test_defocus_lowers_the_feature_count():
     ra = oracle.detect(a, 10, 1.0, 10.0, threshold=0.1, overlap=0.5)
     rb = oracle.detect(b, 10, 1.0, 10.0, threshold=0.1, overlap=0.5)
     assert rb.score < ra.score
+
+
+# ------------------------------------------------------- variants of §2.2 / §3
+
+@pytest.mark.parametrize("s", [2.5, 4.0])
+def test_log_response_of_gaussian_blob_closed_form(s):
+    # L of a sampled Gaussian blob is (up to exp(-2 pi^2 v) aliasing) the
+    # Gaussian of variance v = s^2 + t^2 and amplitude A s^2 / v; its 5-point
+    # Laplacian at the centre is 4 L0 (exp(-1/(2v)) - 1) exactly.
+    A = -0.6
+    t = oracle.ladder(6, 1.0, 6.0)
+    N = 181
+    D = oracle.log_stack(_gauss_image(N, s, A), t, truncate=8.0)[:, N // 2, N // 2]
+    v = s * s + t[:-1] ** 2
+    L0 = A * s * s / v
+    want = t[:-1] ** 2 * 4.0 * L0 * (np.exp(-1.0 / (2.0 * v)) - 1.0)
+    np.testing.assert_allclose(D, want, rtol=0, atol=1e-7)
+    assert np.all(D > 0)                      # dark blob -> positive, like the DoG
+
+
+def test_log_and_dog_agree_in_sign_and_peak():
+    # the DoG of Eq. 2 is the delta-t discretisation of t^2 grad^2 L
+    s, A = 4.0, -0.6
+    t = oracle.ladder(10, 1.0, 10.0)
+    img = _gauss_image(201, s, A)
+    dog = oracle.dog_stack(img, t)[:, 100, 100]
+    log = oracle.log_stack(img, t)[:, 100, 100]
+    assert abs(int(np.argmax(dog)) - int(np.argmax(log))) <= 1
+    assert np.all(np.sign(dog) == np.sign(log))
+
+
+def test_periodic_detection_commutes_with_circular_shift():
+    # the blur wraps around; the 3x3 max-pool of Eq. 3 pads with -inf and
+    # does not, so features on the outermost pixel ring are excluded
+    H, W, dy, dx = 96, 128, 17, -30
+    img = synth.config1_pair(seed=5, H=H, W=W)[0]
+    r0 = oracle.detect(img, 4, 1.0, 4.0, threshold=0.1, overlap=1.0, boundary=oracle.PERIODIC)
+    sh = np.roll(img, (dy, dx), axis=(0, 1))
+    r1 = oracle.detect(sh, 4, 1.0, 4.0, threshold=0.1, overlap=1.0, boundary=oracle.PERIODIC)
+
+    def inner(x, y):
+        return 0 < x < W - 1 and 0 < y < H - 1
+
+    a = set()
+    for x, y, i in zip(r0.x.tolist(), r0.y.tolist(), r0.i.tolist()):
+        xs, ys = (x + dx) % W, (y + dy) % H
+        if inner(x, y) and inner(xs, ys):
+            a.add((xs, ys, i))
+    b = set()
+    for x, y, i in zip(r1.x.tolist(), r1.y.tolist(), r1.i.tolist()):
+        x0, y0 = (x - dx) % W, (y - dy) % H
+        if inner(x, y) and inner(x0, y0):
+            b.add((x, y, i))
+    assert a == b and len(a) > 10
