@@ -48,6 +48,13 @@ extern "C" {
 
 typedef enum { MHFD_U8 = 0, MHFD_U16 = 1, MHFD_F32 = 2 } mhfd_dtype;
 typedef enum { MHFD_NMS_PAPER = 0, MHFD_NMS_LOCAL26 = 1 } mhfd_nms;
+/* Response: the DoG of Eq. 2, or the scale-normalised Laplacian t_i^2 grad^2 L
+ * of §2.2 that the DoG approximates (5-point stencil on each level; it lacks
+ * the DoG's factor dt, so thresholds scale by 1/dt). */
+typedef enum { MHFD_RESPONSE_DOG = 0, MHFD_RESPONSE_LOG = 1 } mhfd_response;
+/* Boundary of the blur: reflect, or periodic (the circular convolution of the
+ * paper's Fourier formulation, §3). */
+typedef enum { MHFD_BOUNDARY_REFLECT = 0, MHFD_BOUNDARY_PERIODIC = 1 } mhfd_boundary;
 
 typedef struct mhfd_detector mhfd_detector;  /* opaque, owned by the library */
 
@@ -72,6 +79,10 @@ typedef struct {
                                mhfd_tile_configs() (autotuner use) */
     int32_t timing;         /* 1: record CUDA events around the kernels of each
                                detection (read with mhfd_last_timing) */
+    int32_t response;       /* mhfd_response; the fused entry points (detect,
+                               batch, debug_stack, soft score) need DoG */
+    int32_t boundary;       /* mhfd_boundary; the fused entry points need
+                               reflect; mhfd_detect_plain supports all */
 } mhfd_params;
 
 /* A detected feature.  scale_idx is the 0-based DoG layer i-1; sigma = t_i,

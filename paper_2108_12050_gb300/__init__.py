@@ -123,7 +123,8 @@ class Detector:
 
     def __init__(self, n=10, t_min=1.0, t_max=10.0, *, sigmas=None, threshold=0.1, overlap=0.5,
                  nms="paper", truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
-                 device=None, keep_candidates=False, tile_override=None, timing=False):
+                 device=None, keep_candidates=False, tile_override=None, timing=False,
+                 response="dog", boundary="reflect"):
         import torch
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
@@ -142,7 +143,7 @@ class Detector:
                                  truncate=truncate, clip_frac=clip_frac,
                                  max_candidates=max_candidates, device=device,
                                  keep_candidates=keep_candidates, tile_override=tile_override,
-                                 timing=timing)
+                                 timing=timing, response=response, boundary=boundary)
         h = ctypes.c_void_p()
         _n.check(_n.lib().mhfd_create_detector(ctypes.byref(self._p), ctypes.byref(h)))
         self._h = h

@@ -57,6 +57,8 @@ class Params(ctypes.Structure):
         ("keep_candidates", ctypes.c_int32),
         ("tile_override", ctypes.c_int32),
         ("timing", ctypes.c_int32),
+        ("response", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
     ]
 
 
@@ -140,7 +142,8 @@ def check(rc, allow_overflow=True):
 
 def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap=0.5,
                 nms=NMS_PAPER, truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
-                device=-1, keep_candidates=False, tile_override=0, timing=False):
+                device=-1, keep_candidates=False, tile_override=0, timing=False,
+                response=0, boundary=0):
     p = Params()
     lib().mhfd_default_params(ctypes.byref(p))
     p.n = int(n)
@@ -163,6 +166,12 @@ def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap
     p.keep_candidates = 1 if keep_candidates else 0
     p.tile_override = int(tile_override)
     p.timing = 1 if timing else 0
+    if isinstance(response, str):
+        response = {"dog": 0, "log": 1}[response]
+    if isinstance(boundary, str):
+        boundary = {"reflect": 0, "periodic": 1}[boundary]
+    p.response = int(response)
+    p.boundary = int(boundary)
     p._keepalive = keep
     return p
 

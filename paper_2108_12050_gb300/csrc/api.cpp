@@ -190,6 +190,10 @@ int validate_params(const mhfd_params &p) {
         return fail(MHFD_ERR_INVALID_ARG, "nms must be MHFD_NMS_PAPER or MHFD_NMS_LOCAL26");
     if (p.max_candidates < 1 || p.max_candidates > (1ll << 30))
         return fail(MHFD_ERR_INVALID_ARG, "max_candidates must be in [1, 2^30]");
+    if (p.response != MHFD_RESPONSE_DOG && p.response != MHFD_RESPONSE_LOG)
+        return fail(MHFD_ERR_INVALID_ARG, "response must be MHFD_RESPONSE_DOG or MHFD_RESPONSE_LOG");
+    if (p.boundary != MHFD_BOUNDARY_REFLECT && p.boundary != MHFD_BOUNDARY_PERIODIC)
+        return fail(MHFD_ERR_INVALID_ARG, "boundary must be reflect or periodic");
     return MHFD_OK;
 }
 
@@ -322,10 +326,19 @@ int finish_pipeline(mhfd_detector *d, int n_tiles, int cap_tile, int H, int W, c
     return MHFD_OK;
 }
 
+int fused_supported(const mhfd_detector *d) {
+    if (d->p.response != MHFD_RESPONSE_DOG || d->p.boundary != MHFD_BOUNDARY_REFLECT)
+        return fail(MHFD_ERR_UNSUPPORTED,
+                    "the fused kernel computes the DoG with the reflect boundary; use "
+                    "mhfd_detect_plain for the LoG response or the periodic boundary");
+    return MHFD_OK;
+}
+
 int detect_impl(mhfd_detector *d, const void *img, int dtype, int H, int W, size_t pitch,
                 cudaStream_t s, bool store, float *d_D, float *d_M, int *d_A) {
     int rc = check_image(img, dtype, H, W, pitch);
     if (rc) return rc;
+    if ((rc = fused_supported(d))) return rc;
     DeviceGuard g(d->device);
     Variant *v = d->var;
     if (store) {
@@ -537,6 +550,8 @@ void mhfd_default_params(mhfd_params *p) {
     p->keep_candidates = 0;
     p->tile_override = 0;
     p->timing = 0;
+    p->response = MHFD_RESPONSE_DOG;
+    p->boundary = MHFD_BOUNDARY_REFLECT;
 }
 
 const char *mhfd_last_error(void) { return mhfd::t_err.c_str(); }
@@ -739,8 +754,8 @@ int mhfd_detect_plain(mhfd_detector *d, const void *img, int32_t dtype, int32_t 
     int n_tiles = 0;
     rc = enqueue_plain(img, dtype, H, W, (long long)pitch, d->st, (int)d->R.size(), d->R,
                        d->d_taps, d->d_tapoff, d->d_tsc, d->p.nms, d->p.threshold, d->pI, d->pT,
-                       d->pL, d->pM, d->pA, d->pD, d->tile_count, d->stage, cap_tile, 0, &n_tiles,
-                       s);
+                       d->pL, d->pM, d->pA, d->pD, d->tile_count, d->stage, cap_tile,
+                       d->p.response, d->p.boundary, &n_tiles, s);
     if (rc) return rc;
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k1, s));
     return finish_pipeline(d, n_tiles, cap_tile, H, W, s);
@@ -820,6 +835,7 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
                       const size_t *pitches, void *stream) {
     if (!d || n < 1 || !d_imgs || !dtypes || !Hs || !Ws || !pitches)
         return fail(MHFD_ERR_INVALID_ARG, "NULL argument or n < 1");
+    if (int rcs = fused_supported(d)) return rcs;
     DeviceGuard g(d->device);
     long long total_items = 0, total_px = 0;
     int max_passes = 1, max_h = 1, max_w = 1, max_rows = 1;
@@ -979,6 +995,7 @@ int mhfd_soft_score(mhfd_detector *d, const void *img, int32_t dtype, int32_t H,
     if (!d || !d_w || !d_S || !d_mean_sig) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
     if (!(temperature > 0.0f) || !std::isfinite(tau))
         return fail(MHFD_ERR_INVALID_ARG, "temperature must be > 0 and tau finite");
+    if (int rcs = fused_supported(d)) return rcs;
     int rc = check_image(img, dtype, H, W, pitch);
     if (rc) return rc;
     DeviceGuard g(d->device);

@@ -158,13 +158,14 @@ int enqueue_keep(const int *state, const Counters *cnt, long long n, int prune_o
 // I' (stretched, centred) and every Gaussian level L_l as full planes.
 int enqueue_stack(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
                   int n_levels, const std::vector<int> &R, const float *d_taps, float *scratch_I,
-                  float *scratch_T, float *scratch_L, cudaStream_t s);
+                  float *scratch_T, float *scratch_L, cudaStream_t s, int boundary = 0);
 int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
                   const MhfdStretch *st, int n_levels, const std::vector<int> &R,
                   const float *d_taps, const int *d_tapoff, const float *d_tsc, int mode,
                   float thr, float *scratch_I, float *scratch_T, float *scratch_L,
                   float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
-                  MhfdCand *stage, int cap_tile, int tile, int *n_tiles_out, cudaStream_t s);
+                  MhfdCand *stage, int cap_tile, int response, int boundary, int *n_tiles_out,
+                  cudaStream_t s);
 
 // ------------------------------------------------------------ soft score
 // Forward (and, with d_dimg, the adjoint) of the soft focus score on the

@@ -16,8 +16,13 @@ namespace {
 
 constexpr int kT = 16;  // NMS tile edge
 
-__device__ __forceinline__ int reflect_i(int i, int n) {
+// boundary 0: reflect ("d c b a | a b c d | d c b a"); 1: periodic
+__device__ __forceinline__ int reflect_i(int i, int n, int boundary = 0) {
     if ((unsigned)i < (unsigned)n) return i;
+    if (boundary == 1) {
+        int m = i % n;
+        return m < 0 ? m + n : m;
+    }
     const int p = 2 * n;
     int m = i % p;
     if (m < 0) m += p;
@@ -47,24 +52,25 @@ __global__ void plain_stretch(const char *img, int dtype, int H, int W, long lon
 }
 
 __global__ void plain_vblur(const float *in, int H, int W, const float *taps, int R,
-                            float *out) {
+                            float *out, int boundary) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W) return;
     float acc = 0.0f;
     for (int k = -R; k <= R; ++k)
-        acc = fmaf(taps[k < 0 ? -k : k], in[(long long)reflect_i(y + k, H) * W + x], acc);
+        acc = fmaf(taps[k < 0 ? -k : k], in[(long long)reflect_i(y + k, H, boundary) * W + x], acc);
     out[(long long)y * W + x] = acc;
 }
 
 __global__ void plain_hblur(const float *in, int H, int W, const float *taps, int R,
-                            float *out) {
+                            float *out, int boundary) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W) return;
     const float *row = in + (long long)y * W;
     float acc = 0.0f;
-    for (int k = -R; k <= R; ++k) acc = fmaf(taps[k < 0 ? -k : k], row[reflect_i(x + k, W)], acc);
+    for (int k = -R; k <= R; ++k)
+        acc = fmaf(taps[k < 0 ? -k : k], row[reflect_i(x + k, W, boundary)], acc);
     out[(long long)y * W + x] = acc;
 }
 
@@ -86,6 +92,40 @@ __global__ void plain_dog(const float *L, long long plane, int n_levels, const f
             }
         } else {
             D[(long long)(l - 1) * plane + p] = d;
+        }
+    }
+    if (mode == 0) {
+        M[p] = m;
+        A[p] = a;
+    }
+}
+
+// the scale-normalised Laplacian response t_i^2 grad^2 L_i (5-point stencil,
+// neighbours through the blur's boundary), i = 0..n_levels-2, with the same
+// max/argmax or stack outputs as plain_dog
+__global__ void plain_log(const float *L, int H, int W, int n_levels, const float *tsc, int mode,
+                          int boundary, float *M, int *A, float *D) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    const long long plane = (long long)H * W;
+    const long long p = (long long)y * W + x;
+    const int xl = reflect_i(x - 1, W, boundary), xr = reflect_i(x + 1, W, boundary);
+    const int yu = reflect_i(y - 1, H, boundary), yd = reflect_i(y + 1, H, boundary);
+    float m = -__int_as_float(0x7f800000);
+    int a = 0;
+    for (int l = 0; l + 1 < n_levels; ++l) {
+        const float *Ll = L + (long long)l * plane;
+        const float lap = (Ll[(long long)y * W + xl] + Ll[(long long)y * W + xr]) +
+                          (Ll[(long long)yu * W + x] + Ll[(long long)yd * W + x]) - 4.0f * Ll[p];
+        const float d = tsc[l] * tsc[l] * lap;
+        if (mode == 0) {
+            if (d > m) {
+                m = d;
+                a = l;
+            }
+        } else {
+            D[(long long)l * plane + p] = d;
         }
     }
     if (mode == 0) {
@@ -194,7 +234,7 @@ __global__ void __launch_bounds__(kT *kT)
 
 int enqueue_stack(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
                   int n_levels, const std::vector<int> &R, const float *d_taps, float *scratch_I,
-                  float *scratch_T, float *scratch_L, cudaStream_t s) {
+                  float *scratch_T, float *scratch_L, cudaStream_t s, int boundary) {
     const dim3 blk(256);
     const dim3 grd((W + 255) / 256, H);
     plain_stretch<<<grd, blk, 0, s>>>(reinterpret_cast<const char *>(img), dtype, H, W, pitch, st,
@@ -202,9 +242,9 @@ int enqueue_stack(const void *img, int dtype, int H, int W, long long pitch, con
     const long long plane = (long long)H * W;
     int off = 0;
     for (int l = 0; l < n_levels; ++l) {
-        plain_vblur<<<grd, blk, 0, s>>>(scratch_I, H, W, d_taps + off, R[l], scratch_T);
+        plain_vblur<<<grd, blk, 0, s>>>(scratch_I, H, W, d_taps + off, R[l], scratch_T, boundary);
         plain_hblur<<<grd, blk, 0, s>>>(scratch_T, H, W, d_taps + off, R[l],
-                                        scratch_L + (long long)l * plane);
+                                        scratch_L + (long long)l * plane, boundary);
         off += R[l] + 1;
     }
     MHFD_CUDA(cudaGetLastError());
@@ -216,16 +256,22 @@ int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
                   const float *d_taps, const int *d_tapoff, const float *d_tsc, int mode,
                   float thr, float *scratch_I, float *scratch_T, float *scratch_L,
                   float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
-                  MhfdCand *stage, int cap_tile, int tile, int *n_tiles_out, cudaStream_t s) {
+                  MhfdCand *stage, int cap_tile, int response, int boundary, int *n_tiles_out,
+                  cudaStream_t s) {
     (void)d_tapoff;
-    (void)tile;
     int rc = enqueue_stack(img, dtype, H, W, pitch, st, n_levels, R, d_taps, scratch_I, scratch_T,
-                           scratch_L, s);
+                           scratch_L, s, boundary);
     if (rc) return rc;
     const long long plane = (long long)H * W;
-    plain_dog<<<(unsigned)((plane + 255) / 256), 256, 0, s>>>(scratch_L, plane, n_levels, d_tsc,
-                                                              mode, scratch_M, scratch_A,
-                                                              scratch_D);
+    if (response == 1) {
+        plain_log<<<dim3((W + 255) / 256, H), 256, 0, s>>>(scratch_L, H, W, n_levels, d_tsc, mode,
+                                                           boundary, scratch_M, scratch_A,
+                                                           scratch_D);
+    } else {
+        plain_dog<<<(unsigned)((plane + 255) / 256), 256, 0, s>>>(scratch_L, plane, n_levels,
+                                                                  d_tsc, mode, scratch_M,
+                                                                  scratch_A, scratch_D);
+    }
     const int tiles_x = (W + kT - 1) / kT, tiles_y = (H + kT - 1) / kT;
     plain_nms<<<tiles_x * tiles_y, kT * kT, 0, s>>>(scratch_M, scratch_A, scratch_D, n_levels - 1,
                                                    H, W, mode, thr, tiles_x, cap_tile, tile_count,

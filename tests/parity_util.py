@@ -45,9 +45,25 @@ def _shift(a, dy, dx, fill):
     return out
 
 
-def ambiguous_paper(D_ref, thr):
+def log_eps(D_ref, t, R, Lmax):
+    """Per-layer tolerance of the scale-normalised Laplacian response.
+
+    The 5-point stencil subtracts level values of size |L| to leave a
+    curvature about t^2 times smaller, so the f32 rounding of L (about
+    sqrt(2R+1) roundings of size 2^-24 |L| per pass) reaches the response
+    multiplied by t^2 and by the stencil's weight sum 8:
+        eps_i = max(1e-4 ||D_ref,i||, 16 sqrt(2R_i+1) t_i^2 2^-24 max|L|)
+    (twice the 8 of the stencil: two blur passes)."""
+    base = layer_eps(D_ref)
+    t = np.asarray(t, dtype=np.float64)[: D_ref.shape[0]]
+    R = np.asarray(R, dtype=np.float64)[: D_ref.shape[0]]
+    cancel = 16.0 * np.sqrt(2 * R + 1) * t ** 2 * 2.0 ** -24 * Lmax
+    return np.maximum(base, cancel)
+
+
+def ambiguous_paper(D_ref, thr, eps=None):
     """Boolean (H, W) map of pixels whose paper-rule decision is ambiguous."""
-    eps = float(layer_eps(D_ref).max())
+    eps = float(layer_eps(D_ref).max() if eps is None else np.max(eps))
     M = D_ref.max(axis=0)
     amb = np.abs(M - thr) <= eps
     for dy in (-1, 0, 1):
@@ -61,9 +77,9 @@ def ambiguous_paper(D_ref, thr):
     return amb, amb_scale, eps
 
 
-def ambiguous_26(D_ref, thr):
+def ambiguous_26(D_ref, thr, eps=None):
     """Boolean (n, H, W) map of ambiguous 26-neighbour decisions."""
-    eps = layer_eps(D_ref).max()
+    eps = layer_eps(D_ref).max() if eps is None else np.max(eps)
     n = D_ref.shape[0]
     amb = np.abs(D_ref - thr) <= eps
     for di in (-1, 0, 1):

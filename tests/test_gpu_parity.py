@@ -12,7 +12,7 @@ import pytest
 import oracle
 import synth
 from parity_util import (ambiguous_26, ambiguous_paper, assert_stack_close,
-                         compare_feature_sets, conflict_components, layer_eps)
+                         compare_feature_sets, conflict_components, layer_eps, log_eps)
 
 pytestmark = pytest.mark.gpu
 
@@ -125,17 +125,38 @@ def _features(arr):
     return {(int(b["x"]), int(b["y"]), int(b["scale_idx"])) for b in arr}
 
 
-def _check_detection(img, n, tmin, tmax, thr, overlap, nms):
+def _variant_stack(img, n, tmin, tmax, response, boundary):
+    """Oracle response stack of a variant and its per-layer tolerance."""
+    lo, hi = oracle.stretch_bounds(img)
+    t = oracle.ladder(n, tmin, tmax)
+    Ip = oracle.stretch(img, lo, hi)
+    bnd = oracle.PERIODIC if boundary == "periodic" else oracle.REFLECT
+    if response == "log":
+        D = oracle.log_stack(Ip, t, boundary=bnd)
+        R = [oracle.kernel_radius(ti) for ti in t[:n]]
+        return D, log_eps(D, t, R, float(np.abs(Ip).max())), t
+    D = oracle.dog_stack(Ip, t, boundary=bnd)
+    return D, layer_eps(D), t
+
+
+def _check_detection(img, n, tmin, tmax, thr, overlap, nms, response="dog",
+                     boundary="reflect", plain=False):
     det = detector(n=n, t_min=tmin, t_max=tmax, threshold=thr, overlap=overlap, nms=nms,
-                   keep_candidates=True)
-    res = det(to_dev(img))
-    D_ref, (lo, hi), t = ref_stack(img, n, tmin, tmax)
+                   keep_candidates=True, response=response, boundary=boundary)
+    if plain:
+        det.detect_plain(to_dev(img))
+        res = det.wait()
+    else:
+        res = det(to_dev(img))
+    D_ref, layer_tol, t = _variant_stack(img, n, tmin, tmax, response, boundary)
     mode = 0 if nms == "paper" else 1
-    ref = oracle.detect(img, n, tmin, tmax, threshold=thr, overlap=overlap, mode=mode)
+    ref = oracle.detect(img, n, tmin, tmax, threshold=thr, overlap=overlap, mode=mode,
+                        response=oracle.RESP_LOG if response == "log" else oracle.RESP_DOG,
+                        boundary=oracle.PERIODIC if boundary == "periodic" else oracle.REFLECT)
     got_c = _features(res.candidates)
     want_c = set(zip(ref.x.tolist(), ref.y.tolist(), ref.i.tolist()))
     if mode == 0:
-        amb, amb_scale, eps = ambiguous_paper(D_ref, thr)
+        amb, amb_scale, eps = ambiguous_paper(D_ref, thr, layer_tol)
         is_amb = lambda f: amb[f[1], f[0]] or amb_scale[f[1], f[0]]  # noqa: E731
         got_px = {(x, y) for x, y, _ in got_c}
         want_px = {(x, y) for x, y, _ in want_c}
@@ -145,7 +166,7 @@ def _check_detection(img, n, tmin, tmax, thr, overlap, nms):
             if (x, y) in want_px and not amb_scale[y, x]:
                 assert (x, y, i) in want_c
     else:
-        amb, eps = ambiguous_26(D_ref, thr)
+        amb, eps = ambiguous_26(D_ref, thr, layer_tol)
         is_amb = lambda f: amb[f[2], f[1], f[0]]  # noqa: E731
         compare_feature_sets(got_c, want_c, is_amb)
     assert res.n_candidates == res.n_candidates_true == len(got_c)
@@ -275,3 +296,50 @@ def test_plain_path_matches_oracle():
     assert not bad, bad[:10]
     fused = det(to_dev(a))
     assert abs(fused.n_blobs - res.n_blobs) <= len(got ^ want) + 2
+
+
+# -------------------------------------------------- variants (plain path)
+
+@pytest.mark.parametrize("response,boundary,nms", [
+    ("dog", "reflect", "paper"), ("log", "reflect", "paper"), ("dog", "periodic", "paper"),
+    ("log", "periodic", "paper"), ("log", "reflect", "local26"), ("dog", "periodic", "local26")])
+def test_variants_match_oracle(response, boundary, nms):
+    a, _ = synth.config1_pair(seed=6, H=200, W=270)
+    # the LoG response lacks the DoG's factor dt (0.9 here): threshold scaled
+    thr = 0.1 / 0.9 if response == "log" else 0.1
+    _check_detection(a, 10, 1.0, 10.0, thr, 0.5, nms, response=response, boundary=boundary,
+                     plain=True)
+
+
+def test_periodic_plain_commutes_with_circular_shift():
+    import paper_2108_12050_gb300 as mhfd  # noqa: F401
+    a = scene(77, 128, 160, "u16")
+    det = detector(n=6, t_min=1.0, t_max=5.0, threshold=0.05, keep_candidates=True,
+                   boundary="periodic")
+    dy, dx = 37, 51
+    det.detect_plain(to_dev(a))
+    r0 = det.wait()
+    det.detect_plain(to_dev(np.ascontiguousarray(np.roll(a, (dy, dx), axis=(0, 1)))))
+    r1 = det.wait()
+    H, W = a.shape
+    inner = lambda x, y: 0 < x < W - 1 and 0 < y < H - 1  # noqa: E731
+    f0 = {((x + dx) % W, (y + dy) % H, i) for x, y, i in _features(r0.candidates)}
+    f0 = {f for f in f0 if inner(f[0], f[1])}
+    f1 = {f for f in _features(r1.candidates) if inner(f[0], f[1])}
+    # the 3x3 comparison window does not wrap: features whose window crosses
+    # the image edge in either frame may differ
+    edge0 = lambda x, y: x in (0, W - 1) or y in (0, H - 1)  # noqa: E731
+    near = lambda f: any(edge0((f[0] - dx + ex) % W, (f[1] - dy + ey) % H)  # noqa: E731
+                         for ex in (-1, 0, 1) for ey in (-1, 0, 1))
+    diff = [f for f in f0 ^ f1 if not near(f)]
+    assert not diff, diff[:10]
+
+
+def test_fused_entry_points_reject_variants():
+    import paper_2108_12050_gb300 as mhfd
+    a, _ = synth.config1_pair(seed=6, H=64, W=64)
+    for kw in ({"response": "log"}, {"boundary": "periodic"}):
+        det = detector(n=4, t_min=1.0, t_max=4.0, threshold=0.1, **kw)
+        with pytest.raises(mhfd.MhfdError) as e:
+            det(to_dev(a))
+        assert e.value.code == -2

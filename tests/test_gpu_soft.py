@@ -76,6 +76,11 @@ def test_weight_fit_regresses_defocus():
     det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05)
     w, b, losses = soft.fit_weights(det, tiles, sds, tau=0.05, steps=200)
     var = float(np.var(sds))
-    assert losses[-1] < 0.5 * var, (losses[0], losses[-1], var)
+    # 16 images and 17 parameters: the least-squares optimum interpolates, so
+    # a converged fit leaves a small fraction of the target variance
+    assert losses[-1] < 0.1 * var, (losses[0], losses[-1], var)
     assert losses[-1] < losses[0]
+    # the returned (w, b) reproduce the fitted predictions through the score
+    pred = np.array([float(soft.soft_score(det, t, w, 0.05, 0.01)[0]) for t in tiles]) + float(b)
+    assert np.mean((pred - np.array(sds)) ** 2) < 0.1 * var
     det.close()
