@@ -294,12 +294,20 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
     h.W = W;
     h.dtype = dtype;
     h.tiles_x = tx;
+    h.tiles_y = ty;
+    h.total_items = n_tiles;
     h.cap_tile = d->cap_tile;
     h.thr = d->p.threshold;
     std::memcpy(pb, &h, sizeof(h));
     void *args[] = {pb};
-    const CUresult r = drv().launchKernel(v->fn, (unsigned)n_tiles, 1, 1, (unsigned)v->cfg.nt, 1,
-                                          1, (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
+    // one resident wave: every block marches down an equal share of tiles
+    int dev = 0, sms = 1;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long wave = (long long)sms * v->occupancy;
+    const unsigned grid = (unsigned)(n_tiles < wave ? n_tiles : wave);
+    const CUresult r = drv().launchKernel(v->fn, grid, 1, 1, (unsigned)v->cfg.nt, 1, 1,
+                                          (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
     if (r != CUDA_SUCCESS) {
         const char *es = nullptr;
         drv().getErrorString(r, &es);
@@ -476,8 +484,17 @@ int batch_reserve(mhfd_detector *d, int n, long long total_items, long long tota
     return MHFD_OK;
 }
 
+// tiles per queue item of a batch: runs of about 256 rows of one strip, long
+// enough that the start of a march (the window's first rows, two
+// neighbour rows) costs little, short enough to balance the blocks
+int batch_chunk(const mhfd_detector *d) {
+    const int TY = d->cfg.ty2 - 2;
+    const int c = (256 + TY - 1) / TY;
+    return c < 1 ? 1 : c;
+}
+
 // the whole batch, enqueued on s (also the body of the captured graph)
-int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long long total_items,
+int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long long total_chunks,
                   cudaStream_t s) {
     mhfd_detector::Batch &b = d->b;
     MHFD_CUDA(cudaMemcpyAsync(b.d_jobs, b.h_jobs, sizeof(MhfdJob) * n, cudaMemcpyHostToDevice, s));
@@ -502,10 +519,12 @@ int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long lo
     h.jobs = b.d_jobs;
     h.queue = b.d_queue;
     h.n_jobs = n;
-    h.total_items = (int)total_items;
+    h.total_items = (int)total_chunks;
+    h.chunk = batch_chunk(d);
     std::memcpy(d->params.data(), &h, sizeof(h));
     void *args[] = {d->params.data()};
-    const unsigned grid = (unsigned)(total_items < sms ? total_items : sms);
+    const long long wave = (long long)sms * v->occupancy;
+    const unsigned grid = (unsigned)(total_chunks < wave ? total_chunks : wave);
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k0, s));
     const CUresult r = drv().launchKernel(v->fn, grid, 1, 1, (unsigned)v->cfg.nt, 1, 1,
                                           (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
@@ -860,10 +879,13 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
     key.push_back(n);
     key.push_back(d->p.timing);
     int base = 0;
+    long long chunks = 0;
+    const int chunk = batch_chunk(d);
     for (int j = 0; j < n; ++j) {
         int tx, ty;
         const int nt = tiles_of(d, Hs[j], Ws[j], &tx, &ty);
         MhfdJob &jb = b.h_jobs[j];
+        std::memset(&jb, 0, sizeof(jb));
         jb.img = d_imgs[j];
         jb.st = b.d_sts + j;
         jb.pitch = (long long)pitches[j];
@@ -871,9 +893,12 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
         jb.W = Ws[j];
         jb.dtype = dtypes[j];
         jb.tiles_x = tx;
+        jb.tiles_y = ty;
         jb.n_tiles = nt;
         jb.tile_base = base;
+        jb.chunk_base = (int)chunks;
         base += nt;
+        chunks += (nt + chunk - 1) / chunk;
         b.h_ranks[j] = clip_rank(d, Hs[j], Ws[j]);
         key.push_back(Hs[j]);
         key.push_back(Ws[j]);
@@ -908,7 +933,7 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                rc = batch_enqueue(d, n, max_passes, max_rows, total_items, s);
+                rc = batch_enqueue(d, n, max_passes, max_rows, chunks, s);
                 e = cudaStreamEndCapture(s, &graph);
                 if (rc == MHFD_OK && e == cudaSuccess && graph) {
                     cudaGraphExec_t exec = nullptr;
@@ -930,7 +955,7 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
                                  mhfd::t_err.c_str());
             }
         }
-        if (!done && (rc = batch_enqueue(d, n, max_passes, max_rows, total_items, s))) return rc;
+        if (!done && (rc = batch_enqueue(d, n, max_passes, max_rows, chunks, s))) return rc;
     }
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_end, s));
     MHFD_CUDA(cudaEventRecord(d->ev_done, s));

@@ -6,24 +6,30 @@
 // every loop over scales and taps is fully unrolled and every tap is an
 // immediate operand of its FFMA (no constant-memory load per multiply).
 //
-// One CTA produces the features of one (TY x TX) output tile:
-//   1. load the tile plus a halo of RMAX+1 pixels from global memory (reflect
-//      boundary: "d c b a | a b c d | d c b a"), apply the histogram stretch
-//      of §3 on the fly and keep the f32 block in shared memory;
-//   2. march over the tile in steps of RB rows.  Per step and per group of
-//      levels, a vertical pass computes V_l = g_l (*)_y I' for every column of
-//      the halo'd width: each thread owns a column, forms the folded sums
-//      I'(y+k) + I'(y-k) once and feeds them to all levels of the group
-//      (taps are symmetric, §2.2), for up to four rows at a time;
+// The image is cut into vertical strips TX pixels wide; a strip into tiles
+// of TY rows, the unit of candidate storage.  A CTA marches down a run of
+// consecutive tiles of one strip (a "chunk"), RB output rows per step:
+//   1. the input rows of the halo'd strip (RMAX+1 pixels of halo, reflect
+//      boundary "d c b a | a b c d | d c b a", histogram stretch of §3 applied
+//      on the fly) live in a sliding shared-memory window of BROWS rows; the
+//      RB rows the next step needs are fetched into registers at the start of
+//      a step and written after it (their latency hides behind the step), and
+//      every few steps the window is shifted back to the buffer's start;
+//   2. per step and per group of levels, a vertical pass computes
+//      V_l = g_l (*)_y I' for every column of the group's halo'd width: each
+//      thread owns a column, forms the folded sums I'(y+k) + I'(y-k) once and
+//      feeds them to all levels of the group (taps are symmetric, §2.2), for
+//      up to four rows at a time;
 //   3. a horizontal pass computes L_l = g_l (*)_x V_l for four adjacent
 //      outputs per thread from float4 shared-memory reads and forms the DoG
 //      of Eq. 2, D_{l-1} = t_{l-1} (L_l - L_{l-1}), in registers;
 //   4. the paper's rule (Eq. 3) keeps the running max over scales and its
 //      first argmax in registers and compares it with its 3x3 neighbourhood
 //      from a (RB+2)-row ring in shared memory; the 26-neighbour mode keeps a
-//      ring of the whole response stack instead;
-//   5. features above the threshold are compacted in tile order (block scan)
-//      into the tile's slots of the candidate list.
+//      ring of the whole response stack instead.  The ring carries over from
+//      step to step, so rows are computed once per chunk, not once per tile;
+//   5. features above the threshold are compacted in row-major order within
+//      each tile (block scan) into that tile's slots of the candidate list.
 // The response stack never reaches global memory (except in the STORE
 // variant used by the tests).
 
@@ -39,9 +45,8 @@ constexpr int NL = MHFD_NL;
 constexpr int NDOG = NL - 1;
 constexpr int NGROUPS = MHFD_NGROUPS;
 constexpr int TX2 = MHFD_TX2;
-constexpr int TX = TX2 - 2;
-constexpr int TY2 = MHFD_TY2;
-constexpr int TY = TY2 - 2;
+constexpr int TX = TX2 - 2;       // output columns of a strip
+constexpr int TY = MHFD_TY2 - 2;  // output rows of a tile (candidate storage unit)
 constexpr int RB = MHFD_RB;
 constexpr int NT = MHFD_NT;
 constexpr int MODE = MHFD_MODE;  // 0: paper (argmax over scales + 3x3), 1: 3x3x3
@@ -78,10 +83,11 @@ MK_HD constexpr int rmax_of() {
     return m;
 }
 constexpr int RMAX = rmax_of();
-constexpr int WEXT = TX2 + 2 * RMAX;           // columns of the halo'd block
+constexpr int WEXT = TX2 + 2 * RMAX;           // columns of the halo'd strip
 constexpr int WEXTP = (WEXT + 3) & ~3;
-constexpr int ROWS_IN = TY2 + 2 * RMAX;        // rows of the halo'd block
-constexpr int NSTEPS = TY2 / RB;
+constexpr int WIN = RB + 2 * RMAX;             // input rows one step reads
+constexpr int BROWS = MHFD_BROWS;              // rows of the sliding input window
+constexpr int NT_COLS = (WEXT + MHFD_NT - 1) / MHFD_NT;  // input columns per thread
 constexpr int RING = RB + 2;
 constexpr int NQ4 = TX2 / 4;
 constexpr int HITEMS = RB * NQ4;
@@ -118,14 +124,15 @@ MK_HD constexpr int vrow_max() {
 }
 constexpr int NTAPS = tapoff(NL);
 constexpr int VROW = vrow_max();
-constexpr int SMEM_IN = ROWS_IN * WEXTP;
+constexpr int SMEM_IN = BROWS * WEXTP;
 constexpr int SMEM_V = RB * VROW;
 constexpr int SMEM_RING_F = MODE == 0 ? RING * TX2 : RING * NDOG * TX2;
 constexpr int SMEM_RING_B = MODE == 0 ? ((RING * TX2 + 15) & ~15) : 0;
 constexpr int SMEM_BYTES = 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64;
 
 static_assert(TX2 % 4 == 0, "tile width must be a multiple of 4");
-static_assert(TY2 % RB == 0, "tile height must be a multiple of the step");
+static_assert(TY >= 1, "tile height");
+static_assert(BROWS >= WIN, "the input window must hold one step");
 static_assert(NT % 32 == 0 && NT <= 1024, "threads per block");
 static_assert(NL >= 2 && NL <= 64, "levels");
 static_assert(kGB(0) == 0 && kGB(NGROUPS) == NL, "level groups");
@@ -150,51 +157,132 @@ __device__ __forceinline__ int reflect_idx(int i, int n) {
 
 // ---------------------------------------------------------------- 1. load
 
+// raw pixel bits (the stretch is applied when the value is stored, so that
+// a prefetched load is not waited for until then)
 template <int DT>
-__device__ __forceinline__ float load_px(const char *row, int gx, const MhfdStretch &st) {
-    if (DT == 0) {
-        int v = __ldg(reinterpret_cast<const unsigned char *>(row) + gx);
-        v = min(max(v, st.lo_i), st.hi_i);
-        return fmaf((float)(v - st.lo_i), st.inv, st.off);
-    } else if (DT == 1) {
-        int v = __ldg(reinterpret_cast<const unsigned short *>(row) + gx);
-        v = min(max(v, st.lo_i), st.hi_i);
-        return fmaf((float)(v - st.lo_i), st.inv, st.off);
-    } else {
-        const float v = __ldg(reinterpret_cast<const float *>(row) + gx);
-        float u = (v - st.lo) * st.inv;
-        u = fminf(fmaxf(u, 0.0f), 1.0f);
-        return u + st.off;
-    }
+__device__ __forceinline__ unsigned raw_px(const char *row, int gx) {
+    if (DT == 0) return __ldg(reinterpret_cast<const unsigned char *>(row) + gx);
+    if (DT == 1) return __ldg(reinterpret_cast<const unsigned short *>(row) + gx);
+    return __float_as_uint(__ldg(reinterpret_cast<const float *>(row) + gx));
 }
 
 template <int DT>
-__device__ __forceinline__ void load_block(const MhfdKHeader &h, const MhfdStretch &st, float *s_in,
-                                           int x0, int y0) {
-    // each thread owns columns; LB row loads are kept in flight at a time so
-    // that the latency of the global (mostly L2) reads overlaps
+__device__ __forceinline__ float stretch_px(unsigned raw, const MhfdStretch &st) {
+    if (DT == 2) {
+        float u = (__uint_as_float(raw) - st.lo) * st.inv;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        return u + st.off;
+    }
+    const int v = min(max((int)raw, st.lo_i), st.hi_i);
+    return fmaf((float)(v - st.lo_i), st.inv, st.off);
+}
+
+// Strip geometry of one march: input row i of the window is image row
+// reflect(yin + i); input column c is image column reflect(xin + c).
+struct Strip {
+    const char *img;
+    long long pitch;
+    int H, W, dtype;
+    int xin, yin;
+};
+
+// Load input rows [r0, r1) into window rows [r0 - base, r1 - base), LB row
+// loads in flight per thread.
+template <int DT>
+__device__ __forceinline__ void load_rows_t(const Strip &sp, const MhfdStretch &st, float *s_in,
+                                            int r0, int r1, int base) {
     constexpr int LB = 16;
-    const char *base = reinterpret_cast<const char *>(h.img);
-    const long long pitch = h.pitch;
-    const int H = h.H, W = h.W;
     for (int c = threadIdx.x; c < WEXT; c += NT) {
-        const int gx = reflect_idx(x0 - 1 - RMAX + c, W);
+        const int gx = reflect_idx(sp.xin + c, sp.W);
         float *dst = s_in + c;
-        int r = 0;
 #pragma unroll 1
-        for (; r + LB <= ROWS_IN; r += LB) {
-            float v[LB];
+        for (int r = r0; r < r1; r += LB) {
+            unsigned v[LB];
 #pragma unroll
-            for (int e = 0; e < LB; ++e) {
-                const int gy = reflect_idx(y0 - 1 - RMAX + r + e, H);
-                v[e] = load_px<DT>(base + (long long)gy * pitch, gx, st);
-            }
+            for (int e = 0; e < LB; ++e)
+                if (r + e < r1)
+                    v[e] = raw_px<DT>(sp.img + (long long)reflect_idx(sp.yin + r + e, sp.H) * sp.pitch,
+                                      gx);
 #pragma unroll
-            for (int e = 0; e < LB; ++e) dst[(r + e) * WEXTP] = v[e];
+            for (int e = 0; e < LB; ++e)
+                if (r + e < r1) dst[(r + e - base) * WEXTP] = stretch_px<DT>(v[e], st);
         }
-        for (; r < ROWS_IN; ++r) {
-            const int gy = reflect_idx(y0 - 1 - RMAX + r, H);
-            dst[r * WEXTP] = load_px<DT>(base + (long long)gy * pitch, gx, st);
+    }
+}
+
+__device__ __forceinline__ void load_rows(const Strip &sp, const MhfdStretch &st, float *s_in,
+                                          int r0, int r1, int base) {
+    if (sp.dtype == 0)
+        load_rows_t<0>(sp, st, s_in, r0, r1, base);
+    else if (sp.dtype == 1)
+        load_rows_t<1>(sp, st, s_in, r0, r1, base);
+    else
+        load_rows_t<2>(sp, st, s_in, r0, r1, base);
+}
+
+// The RB input rows of the next step, held in registers across a step.
+struct Prefetch {
+    unsigned v[NT_COLS][RB];
+
+    template <int DT>
+    __device__ __forceinline__ void issue_t(const Strip &sp, int r0) {
+#pragma unroll
+        for (int k = 0; k < NT_COLS; ++k) {
+            const int c = threadIdx.x + k * NT;
+            if (c < WEXT) {
+                const int gx = reflect_idx(sp.xin + c, sp.W);
+#pragma unroll
+                for (int e = 0; e < RB; ++e)
+                    v[k][e] = raw_px<DT>(
+                        sp.img + (long long)reflect_idx(sp.yin + r0 + e, sp.H) * sp.pitch, gx);
+            }
+        }
+    }
+    __device__ __forceinline__ void issue(const Strip &sp, int r0) {
+        if (sp.dtype == 0)
+            issue_t<0>(sp, r0);
+        else if (sp.dtype == 1)
+            issue_t<1>(sp, r0);
+        else
+            issue_t<2>(sp, r0);
+    }
+    template <int DT>
+    __device__ __forceinline__ void store_t(const MhfdStretch &st, float *s_in, int prow) const {
+#pragma unroll
+        for (int k = 0; k < NT_COLS; ++k) {
+            const int c = threadIdx.x + k * NT;
+            if (c < WEXT) {
+#pragma unroll
+                for (int e = 0; e < RB; ++e) s_in[(prow + e) * WEXTP + c] = stretch_px<DT>(v[k][e], st);
+            }
+        }
+    }
+    __device__ __forceinline__ void store(int dtype, const MhfdStretch &st, float *s_in,
+                                          int prow) const {
+        if (dtype == 0)
+            store_t<0>(st, s_in, prow);
+        else if (dtype == 1)
+            store_t<1>(st, s_in, prow);
+        else
+            store_t<2>(st, s_in, prow);
+    }
+};
+
+// Move window rows [from, from + n) to [0, n) (each thread its own columns;
+// the destination lies below the source, batches are read before written).
+__device__ __forceinline__ void shift_window(float *s_in, int from, int n) {
+    constexpr int SB = 8;
+    for (int c = threadIdx.x; c < WEXT; c += NT) {
+        float *col = s_in + c;
+#pragma unroll 1
+        for (int r = 0; r < n; r += SB) {
+            float v[SB];
+#pragma unroll
+            for (int e = 0; e < SB; ++e)
+                if (r + e < n) v[e] = col[(from + r + e) * WEXTP];
+#pragma unroll
+            for (int e = 0; e < SB; ++e)
+                if (r + e < n) col[(r + e) * WEXTP] = v[e];
         }
     }
 }
@@ -233,16 +321,17 @@ __device__ __forceinline__ void vstep(const float *colp, float (*acc)[kGB(G + 1)
     }
 }
 
-// V_l(o0 + j, c) for the ROWS rows starting at tile row o0 and every level l
-// of group G.  Row o of the tile sits at row o + RMAX of the halo'd block.
+// V_l(o0 + j, c) for the ROWS rows starting at step row o0 and every level l
+// of group G.  `win` is the window row of the step's first input row: step
+// row o sits at window row o + RMAX.
 template <int G, int ROWS>
-__device__ __forceinline__ void vcol(const MhfdKHeader &h, const float *__restrict__ s_in,
-                                     float *__restrict__ s_v, int c, int o0, int jb) {
+__device__ __forceinline__ void vcol(const float *__restrict__ win, float *__restrict__ s_v, int c,
+                                     int o0) {
     constexpr int LB = kGB(G);
     constexpr int LE = kGB(G + 1);
     constexpr int NG = LE - LB;
     float acc[ROWS][NG];
-    const float *colp = s_in + (o0 + RMAX) * WEXTP + c;
+    const float *colp = win + (o0 + RMAX) * WEXTP + c;
 #pragma unroll
     for (int j = 0; j < ROWS; ++j) vinit<G, 0>(colp[j * WEXTP], acc[j]);
     vstep<G, ROWS, 1>(colp, acc);
@@ -251,29 +340,38 @@ __device__ __forceinline__ void vcol(const MhfdKHeader &h, const float *__restri
         const int cc = c - (RMAX - kR(LB + l));
         if (cc >= 0 && cc < TX2 + 2 * kR(LB + l)) {
 #pragma unroll
-            for (int j = 0; j < ROWS; ++j) s_v[(jb + j) * VROW + voff(LB + l) + cc] = acc[j][l];
+            for (int j = 0; j < ROWS; ++j) s_v[(o0 + j) * VROW + voff(LB + l) + cc] = acc[j][l];
         }
     }
 }
 
 template <int G, int PART>
 struct VParts {
-    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *s_in, float *s_v,
-                                               int c, int s) {
+    static __device__ __forceinline__ void run(const float *win, float *s_v, int c) {
         constexpr int ROWS = (RB - 4 * PART) < 4 ? (RB - 4 * PART) : 4;
-        vcol<G, ROWS>(h, s_in, s_v, c, s * RB + 4 * PART, 4 * PART);
-        VParts<G, PART + 1>::run(h, s_in, s_v, c, s);
+        vcol<G, ROWS>(win, s_v, c, 4 * PART);
+        VParts<G, PART + 1>::run(win, s_v, c);
     }
 };
 template <int G>
 struct VParts<G, NPARTS> {
-    static __device__ __forceinline__ void run(const MhfdKHeader &, const float *, float *, int, int) {}
+    static __device__ __forceinline__ void run(const float *, float *, int) {}
 };
 
+// the columns group G needs: the strip plus the group's largest radius
+MK_HD constexpr int group_rmax(int g) {
+    int m = 0;
+    for (int l = kGB(g); l < kGB(g + 1); ++l) m = kR(l) > m ? kR(l) : m;
+    return m;
+}
+
 template <int G>
-__device__ __forceinline__ void vpass(const MhfdKHeader &h, const float *s_in, float *s_v, int s) {
+__device__ __forceinline__ void vpass(const float *win, float *s_v) {
+    constexpr int RG = group_rmax(G);
+    constexpr int CB = RMAX - RG;
+    constexpr int CE = RMAX + TX2 + RG;
 #pragma unroll 1
-    for (int c = threadIdx.x; c < WEXT; c += NT) VParts<G, 0>::run(h, s_in, s_v, c, s);
+    for (int c = CB + threadIdx.x; c < CE; c += NT) VParts<G, 0>::run(win, s_v, c);
 }
 
 // ----------------------------------------------------- 3. horizontal pass
@@ -383,16 +481,23 @@ struct HLevels<LE, LE> {
                                                HState &, float *) {}
 };
 
-__device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, int item, int s, int x0, int y0) {
+// Chunk geometry: chunk row r is image row yb + r; rows 1..Y are output
+// rows, rows 0 and Y + 1 their NMS neighbours.  Output column c of the
+// strip (1..TX) is image column x0 - 1 + c.
+struct March {
+    int x0, yb, Y;
+};
+
+__device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, const March &m, int item, int s) {
     HCtx cx;
     const int j = item / NQ4;
     cx.q = item - j * NQ4;
     cx.r = s * RB + j;
     cx.slot = cx.r % RING;
-    cx.gy = y0 - 1 + cx.r;
-    cx.gx0 = x0 - 1 + 4 * cx.q;
+    cx.gy = m.yb + cx.r;
+    cx.gx0 = m.x0 - 1 + 4 * cx.q;
     const bool rowin = cx.gy >= 0 && cx.gy < h.H;
-    const bool rowint = rowin && cx.r >= 1 && cx.r <= TY2 - 2;
+    const bool rowint = rowin && cx.r >= 1 && cx.r <= m.Y;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int gx = cx.gx0 + u;
@@ -404,14 +509,14 @@ __device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, int item, int s, 
 }
 
 template <int G>
-__device__ __forceinline__ void hpass(const MhfdKHeader &h, const float *s_v, float *s_ring,
-                                      unsigned char *s_arg, HState (&hs)[HI], int s, int x0,
-                                      int y0) {
+__device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, const float *s_v,
+                                      float *s_ring, unsigned char *s_arg, HState (&hs)[HI],
+                                      int s) {
 #pragma unroll
     for (int it = 0; it < HI; ++it) {
         const int item = threadIdx.x + it * NT;
         if (item < HITEMS) {
-            const HCtx cx = make_ctx(h, item, s, x0, y0);
+            const HCtx cx = make_ctx(h, m, item, s);
             const float *vrow = s_v + (cx.r - s * RB) * VROW;
             HLevels<kGB(G), kGB(G + 1)>::run(h, vrow, cx, hs[it], s_ring);
             if (G == NGROUPS - 1 && MODE == 0) {
@@ -444,20 +549,21 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const float *s_v, fl
 
 template <int G>
 struct Groups {
-    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *s_in, float *s_v,
-                                               float *s_ring, unsigned char *s_arg,
-                                               HState (&hs)[HI], int s, int x0, int y0) {
-        vpass<G>(h, s_in, s_v, s);
+    static __device__ __forceinline__ void run(const MhfdKHeader &h, const March &m,
+                                               const float *win, float *s_v, float *s_ring,
+                                               unsigned char *s_arg, HState (&hs)[HI], int s) {
+        vpass<G>(win, s_v);
         __syncthreads();
-        hpass<G>(h, s_v, s_ring, s_arg, hs, s, x0, y0);
+        hpass<G>(h, m, s_v, s_ring, s_arg, hs, s);
         __syncthreads();
-        Groups<G + 1>::run(h, s_in, s_v, s_ring, s_arg, hs, s, x0, y0);
+        Groups<G + 1>::run(h, m, win, s_v, s_ring, s_arg, hs, s);
     }
 };
 template <>
 struct Groups<NGROUPS> {
-    static __device__ __forceinline__ void run(const MhfdKHeader &, const float *, float *, float *,
-                                               unsigned char *, HState (&)[HI], int, int, int) {}
+    static __device__ __forceinline__ void run(const MhfdKHeader &, const March &, const float *,
+                                               float *, float *, unsigned char *, HState (&)[HI],
+                                               int) {}
 };
 
 // ------------------------------------------------------ 4-5. NMS, compaction
@@ -523,13 +629,12 @@ __device__ __forceinline__ bool cand_26(const float *s_ring, int r, int c, int l
     return true;
 }
 
-__device__ __forceinline__ int nms_step(const MhfdKHeader &h, const float *s_ring,
-                                        const unsigned char *s_arg, int *s_scan, int s, int x0,
-                                        int y0, int tile, int total) {
-    const int r_lo = max(1, s * RB - 1);
-    const int r_hi = min(TY2 - 2, s * RB + RB - 2);
-    if (r_lo > r_hi) return total;
-    const int nrows = r_hi - r_lo + 1;
+// Candidates of chunk rows [ra, rb] (all in one tile) appended after `total`
+// candidates of that tile's slots; returns the tile's new count.
+__device__ __forceinline__ int nms_rows(const MhfdKHeader &h, const March &m,
+                                        const float *s_ring, const unsigned char *s_arg,
+                                        int *s_scan, int ra, int rb, long long slot, int total) {
+    const int nrows = rb - ra + 1;
     const int per = (MODE == 0) ? TX : TX * NDOG;
     const int items = nrows * per;
     const int ch = (items + NT - 1) / NT;
@@ -538,7 +643,7 @@ __device__ __forceinline__ int nms_step(const MhfdKHeader &h, const float *s_rin
     const float thr = h.thr;
     int cnt = 0;
     for (int it = beg; it < end; ++it) {
-        const int r = r_lo + it / per;
+        const int r = ra + it / per;
         const int rem = it - (it / per) * per;
         float v;
         if (MODE == 0) {
@@ -550,9 +655,9 @@ __device__ __forceinline__ int nms_step(const MhfdKHeader &h, const float *s_rin
     int sum;
     int pos = total + block_excl_scan(cnt, s_scan, &sum);
     if (cnt) {
-        MhfdCand *dst = h.stage + (long long)tile * h.cap_tile;
+        MhfdCand *dst = h.stage + slot * h.cap_tile;
         for (int it = beg; it < end; ++it) {
-            const int r = r_lo + it / per;
+            const int r = ra + it / per;
             const int rem = it - (it / per) * per;
             float v;
             bool ok;
@@ -569,8 +674,8 @@ __device__ __forceinline__ int nms_step(const MhfdKHeader &h, const float *s_rin
             if (ok) {
                 if (pos < h.cap_tile) {
                     MhfdCand cd;
-                    cd.x = x0 - 1 + c;
-                    cd.y = y0 - 1 + r;
+                    cd.x = m.x0 - 1 + c;
+                    cd.y = m.yb + r;
                     cd.i = l;
                     cd.resp = v;
                     dst[pos] = cd;
@@ -590,32 +695,87 @@ extern "C" __constant__ int mhfd_ntaps = mk::NTAPS;
 
 namespace mk {
 
-// The whole detection of one output tile (load, stack, DoG, maxima,
-// compaction).  `item` indexes the candidate slots and counts.
-__device__ __forceinline__ void process_tile(const MhfdKHeader &h, int tile,
-                                             int item, float *s_in, float *s_v, float *s_ring,
-                                             unsigned char *s_arg, int *s_scan) {
-    const int ty = tile / h.tiles_x;
-    const int tx = tile - ty * h.tiles_x;
-    const int x0 = tx * TX, y0 = ty * TY;
-    const MhfdStretch st = *h.st;
+struct Smem {
+    float *in, *v, *ring;
+    unsigned char *arg;
+    int *scan;
+};
 
-    if (h.dtype == 0)
-        load_block<0>(h, st, s_in, x0, y0);
-    else if (h.dtype == 1)
-        load_block<1>(h, st, s_in, x0, y0);
-    else
-        load_block<2>(h, st, s_in, x0, y0);
+// One march down strip `tx` over its tiles [ta, tb): tile k's candidates go
+// to slot slot0 + k * tiles_x + tx.  `sp` carries the image of the job.
+__device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &st, int tiles_x,
+                                      int tx, int ta, int tb, long long slot0, const Smem &sm) {
+    March m;
+    m.x0 = tx * TX;
+    m.yb = ta * TY - 1;
+    m.Y = min((tb - ta) * TY, h.H - ta * TY);
+    Strip sp;
+    sp.img = reinterpret_cast<const char *>(h.img);
+    sp.pitch = h.pitch;
+    sp.H = h.H;
+    sp.W = h.W;
+    sp.dtype = h.dtype;
+    sp.xin = m.x0 - 1 - RMAX;
+    sp.yin = m.yb - RMAX;
+    const int nsteps = (m.Y + 2 + RB - 1) / RB;
+
+    __syncthreads();  // the previous march's last reads of shared memory
+    load_rows(sp, st, sm.in, 0, WIN, 0);
     __syncthreads();
 
     HState hs[HI];
-    int total = 0;
+    int base = 0;       // input row held in window row 0
+    int tile = 0;       // tile (relative to ta) now receiving candidates
+    int total = 0;      // its candidates so far
 #pragma unroll 1
-    for (int s = 0; s < NSTEPS; ++s) {
-        Groups<0>::run(h, s_in, s_v, s_ring, s_arg, hs, s, x0, y0);
-        total = nms_step(h, s_ring, s_arg, s_scan, s, x0, y0, item, total);
+    for (int s = 0; s < nsteps; ++s) {
+        const bool more = s + 1 < nsteps;
+        Prefetch pf;
+        if (more) pf.issue(sp, s * RB + WIN);
+        Groups<0>::run(h, m, sm.in + (s * RB - base) * WEXTP, sm.v, sm.ring, sm.arg, hs, s);
+        // maxima of the rows whose lower neighbour is now known
+        int ra = max(1, s * RB - 1);
+        const int rb = min(m.Y, s * RB + RB - 2);
+        while (ra <= rb) {
+            const int tend = min(m.Y, (tile + 1) * TY);  // last row of the tile
+            const int re = min(rb, tend);
+            total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, ra, re,
+                             slot0 + (long long)(ta + tile) * tiles_x + tx, total);
+            if (re == tend) {
+                if (threadIdx.x == 0)
+                    h.tile_count[slot0 + (long long)(ta + tile) * tiles_x + tx] = total;
+                ++tile;
+                total = 0;
+            }
+            ra = re + 1;
+        }
+        if (more) {
+            // keep the window inside the buffer: the next step reads input
+            // rows [(s+1) RB, (s+1) RB + WIN)
+            if ((s + 1) * RB + WIN - base > BROWS) {
+                shift_window(sm.in, (s + 1) * RB - base, s * RB + WIN - (s + 1) * RB);
+                base = (s + 1) * RB;
+            }
+            pf.store(sp.dtype, st, sm.in, s * RB + WIN - base);
+        }
+        __syncthreads();
     }
-    if (threadIdx.x == 0) h.tile_count[item] = total;
+}
+
+// Tiles [k0, k1) of an image in strip-major order (k -> strip k / tiles_y,
+// tile row k % tiles_y), as one march per strip touched.
+__device__ __forceinline__ void run_range(const MhfdKHeader &h, long long k0, long long k1,
+                                          int tiles_x, int tiles_y, long long slot0,
+                                          const Smem &sm) {
+    const MhfdStretch st = *h.st;
+    long long k = k0;
+    while (k < k1) {
+        const int tx = (int)(k / tiles_y);
+        const int ta = (int)(k - (long long)tx * tiles_y);
+        const int tb = (int)min((long long)tiles_y, ta + (k1 - k));
+        march(h, st, tiles_x, tx, ta, tb, slot0, sm);
+        k += tb - ta;
+    }
 }
 
 }  // namespace mk
@@ -624,17 +784,23 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
     mhfd_fused_detect(const __grid_constant__ mk::KParams p) {
     using namespace mk;
     extern __shared__ __align__(16) float smem[];
-    float *s_in = smem;
-    float *s_v = smem + SMEM_IN;
-    float *s_ring = s_v + SMEM_V;
-    unsigned char *s_arg = reinterpret_cast<unsigned char *>(s_ring + SMEM_RING_F);
-    int *s_scan = reinterpret_cast<int *>(s_arg + SMEM_RING_B);
+    Smem sm;
+    sm.in = smem;
+    sm.v = smem + SMEM_IN;
+    sm.ring = sm.v + SMEM_V;
+    sm.arg = reinterpret_cast<unsigned char *>(sm.ring + SMEM_RING_F);
+    sm.scan = reinterpret_cast<int *>(sm.arg + SMEM_RING_B);
 
     if (p.h.jobs == nullptr) {
-        process_tile(p.h, blockIdx.x, blockIdx.x, s_in, s_v, s_ring, s_arg, s_scan);
+        // one image: block b takes an equal share of its tiles
+        const long long T = (long long)p.h.tiles_x * p.h.tiles_y;
+        const long long k0 = T * blockIdx.x / gridDim.x;
+        const long long k1 = T * (blockIdx.x + 1) / gridDim.x;
+        run_range(p.h, k0, k1, p.h.tiles_x, p.h.tiles_y, 0, sm);
         return;
     }
-    // batch: persistent blocks take items from the queue (no waits)
+    // batch: persistent blocks take chunks of `chunk` tiles from the queue
+    // (no waits); chunk -> (job, tiles) through chunk_base
     __shared__ int s_item;
 #pragma unroll 1
     for (;;) {
@@ -643,10 +809,10 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
         __syncthreads();
         const int item = s_item;
         if (item >= p.h.total_items) break;
-        int lo = 0, hi = p.h.n_jobs - 1;  // last job with tile_base <= item
+        int lo = 0, hi = p.h.n_jobs - 1;  // last job with chunk_base <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (p.h.jobs[mid].tile_base <= item) lo = mid; else hi = mid - 1;
+            if (p.h.jobs[mid].chunk_base <= item) lo = mid; else hi = mid - 1;
         }
         const MhfdJob job = p.h.jobs[lo];
         MhfdKHeader h = p.h;
@@ -657,7 +823,11 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
         h.W = job.W;
         h.dtype = job.dtype;
         h.tiles_x = job.tiles_x;
+        h.tiles_y = job.tiles_y;
         h.plane = (long long)job.H * job.W;
-        process_tile(h, item - job.tile_base, item, s_in, s_v, s_ring, s_arg, s_scan);
+        const long long n_tiles = (long long)job.tiles_x * job.tiles_y;
+        const long long k0 = (long long)(item - job.chunk_base) * p.h.chunk;
+        const long long k1 = min(n_tiles, k0 + p.h.chunk);
+        run_range(h, k0, k1, job.tiles_x, job.tiles_y, job.tile_base, sm);
     }
 }

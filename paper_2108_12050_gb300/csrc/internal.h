@@ -28,6 +28,7 @@ struct DrvApi {
     CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
                              unsigned, unsigned, CUstream, void **, void **);
     CUresult (*getErrorString)(CUresult, const char **);
+    CUresult (*occupancy)(int *, CUfunction, int, size_t);
     bool ok;
 };
 const DrvApi &drv();
@@ -61,6 +62,9 @@ int enqueue_stretch_batch(const MhfdJob *d_jobs, int n_jobs, int max_passes, int
                           cudaStream_t s);
 
 // ---------------------------------------------------- fused kernel (JIT)
+// Fused-kernel geometry: strips tx2 - 2 output columns wide, tiles
+// (candidate storage units) ty2 - 2 rows high, rb rows per step, nt threads,
+// level groups gb.  The input window height follows from these (brows_for).
 struct TileConfig {
     int tx2, ty2, rb, nt;
     std::vector<int> gb;   // level-group boundaries
@@ -73,6 +77,7 @@ struct Variant {
     int smem_bytes = 0;
     int param_bytes = 0;
     int ntaps = 0;
+    int occupancy = 1;  // resident blocks per SM
     TileConfig cfg;
 };
 
@@ -88,6 +93,7 @@ struct LadderKey {
 bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why);
 // Enumerate the configurations offered to the autotuner.
 std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode);
+int brows_for(const std::vector<int> &R, int mode, const TileConfig &c);
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c);
 // Compile (or fetch from cache) the fused kernel for this ladder/config.
 int get_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg, Variant **out);

@@ -27,7 +27,9 @@ namespace {
 
 #include "kernel_src.inc"  // kTypesSrc, kKernelSrc
 
-constexpr int kSmemLimit = 232448;  // opt-in dynamic shared memory per block (227 KB)
+// opt-in shared memory per block (227 KB) less the kernel's static shared
+// variables (the batch loop's queue slot), which count against the same limit
+constexpr int kSmemLimit = 232448 - 64;
 
 std::mutex g_mu;
 std::map<std::string, Variant *> g_variants;
@@ -85,6 +87,7 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_GB " << join(c.gb) << "\n"
       << "#define MHFD_TX2 " << c.tx2 << "\n"
       << "#define MHFD_TY2 " << c.ty2 << "\n"
+      << "#define MHFD_BROWS " << brows_for(R, mode, c) << "\n"
       << "#define MHFD_RB " << c.rb << "\n"
       << "#define MHFD_NT " << c.nt << "\n"
       << "#define MHFD_MODE " << mode << "\n"
@@ -169,17 +172,23 @@ const DrvApi &drv() {
         resolve("cuFuncSetAttribute", &a.funcSetAttribute, &a.ok);
         resolve("cuLaunchKernel", &a.launchKernel, &a.ok);
         resolve("cuGetErrorString", &a.getErrorString, &a.ok);
+        resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &a.occupancy, &a.ok);
         return a;
     }();
     return api;
 }
 
-int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
-    int rmax = 0;
-    for (int r : R) rmax = r > rmax ? r : rmax;
+namespace {
+
+int rmax_of(const std::vector<int> &R) {
+    int m = 0;
+    for (int r : R) m = r > m ? r : m;
+    return m;
+}
+
+// bytes of everything but the input window
+int smem_fixed(const std::vector<int> &R, int mode, const TileConfig &c) {
     const int nl = (int)R.size();
-    const int wextp = (c.tx2 + 2 * rmax + 3) & ~3;
-    const int rows_in = c.ty2 + 2 * rmax;
     int vrow = 0;
     for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
         int o = 0;
@@ -189,7 +198,28 @@ int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
     const int ring = c.rb + 2;
     const int ring_f = mode == 0 ? ring * c.tx2 : ring * (nl - 1) * c.tx2;
     const int ring_b = mode == 0 ? ((ring * c.tx2 + 15) & ~15) : 0;
-    return 4 * (rows_in * wextp + c.rb * vrow + ring_f) + ring_b + 4 * 64;
+    return 4 * (c.rb * vrow + ring_f) + ring_b + 4 * 64;
+}
+
+int wextp_of(const std::vector<int> &R, const TileConfig &c) {
+    return (c.tx2 + 2 * rmax_of(R) + 3) & ~3;
+}
+
+}  // namespace
+
+// Input window rows: one step's rows (rb + 2 rmax) plus up to four steps of
+// slack (the window shifts back once the slack is used up), as many as fit.
+int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
+    const int win = c.rb + 2 * rmax_of(R);
+    const int row_bytes = 4 * wextp_of(R, c);
+    const int room = (kSmemLimit - smem_fixed(R, mode, c)) / row_bytes;
+    int b = win + 4 * c.rb;
+    if (b > room) b = room;
+    return b < win ? win : b;
+}
+
+int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
+    return smem_fixed(R, mode, c) + 4 * brows_for(R, mode, c) * wextp_of(R, c);
 }
 
 namespace {
@@ -201,25 +231,34 @@ std::vector<int> groups_for(int nl, int max_per_group) {
     return gb;
 }
 
-// relative instruction cost per output pixel (FMA-dominated model)
-double cost_model(const std::vector<int> &R, const TileConfig &c) {
-    int rmax = 0;
-    for (int r : R) rmax = r > rmax ? r : rmax;
-    const double tx = c.tx2 - 2, ty = c.ty2 - 2;
-    const double wext = c.tx2 + 2 * rmax;
+// relative instruction cost per output pixel (FMA-dominated model): the
+// vertical pass over each group's halo'd columns in rounds of nt threads,
+// the horizontal pass over the strip's columns in rounds of nt items, and
+// the window shifts
+double cost_model(const std::vector<int> &R, int mode, const TileConfig &c) {
+    const int rmax = rmax_of(R);
+    const double tx = c.tx2 - 2;
     double v = 0, h = 0;
     for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
-        v += R[c.gb[g + 1] - 1];  // folded sums of the group
-        for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) v += R[l] + 1;
+        int rg = 0;
+        double w = 0;
+        for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) {
+            rg = R[l] > rg ? R[l] : rg;
+            w += R[l] + 1;
+        }
+        w += rg;  // folded sums of the group
+        const int cols = c.tx2 + 2 * rg;
+        v += w * ((cols + c.nt - 1) / c.nt) * (double)c.nt / tx;
     }
     for (int r : R) h += 2 * r + 1;
-    const double vthreads = ((int)(wext + c.nt - 1) / c.nt) * (double)c.nt;
-    const double v_eff = v * vthreads / tx * (c.ty2 / ty);
     const double h_items = c.rb * (c.tx2 / 4.0);
     const double h_slots = ((int)((h_items + c.nt - 1) / c.nt)) * (double)c.nt;
-    const double h_eff = h * (c.tx2 / tx) * (c.ty2 / ty) * (h_slots / h_items);
-    const double load = 12.0 * (c.ty2 + 2 * rmax) * wext / (tx * ty);
-    return v_eff + h_eff + load;
+    const double h_eff = h * (c.tx2 / tx) * (h_slots / h_items);
+    const int brows = brows_for(R, mode, c);
+    const int steps_per_shift = (brows - (c.rb + 2 * rmax)) / c.rb + 1;
+    const double wext = c.tx2 + 2 * rmax;
+    const double shift = 4.0 * 2 * rmax * wext / (steps_per_shift * c.rb * tx);
+    return v + h_eff + shift;
 }
 
 }  // namespace
@@ -227,10 +266,9 @@ double cost_model(const std::vector<int> &R, const TileConfig &c) {
 std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode) {
     std::vector<TileConfig> out;
     const int nl = (int)R.size();
-    int rmax = 0;
-    for (int r : R) rmax = r > rmax ? r : rmax;
-    const int widths[] = {64, 96, 128, 160, 192, 256};
-    const int gmax[] = {8, 10, 12};
+    const int rmax = rmax_of(R);
+    const int widths[] = {64, 96, 128, 160, 192, 224, 256, 288, 320};
+    const int gmax[] = {6, 8, 10, 12};
     for (int tx2 : widths) {
         const int wext = tx2 + 2 * rmax;
         for (int nt = 64; nt <= 512; nt += 32) {
@@ -244,14 +282,8 @@ std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode) {
                     c.nt = nt;
                     c.rb = rb;
                     c.gb = groups_for(nl, gm);
-                    int best_ty = 0;
-                    for (int k = 1; k * rb <= 256; ++k) {
-                        c.ty2 = k * rb;
-                        if (c.ty2 < 8) continue;
-                        if (smem_estimate(R, mode, c) <= kSmemLimit) best_ty = c.ty2;
-                    }
-                    if (best_ty == 0) continue;
-                    c.ty2 = best_ty;
+                    c.ty2 = 2 + 16;  // tiles of 16 output rows
+                    if (smem_estimate(R, mode, c) > kSmemLimit) continue;
                     out.push_back(c);
                 }
             }
@@ -272,7 +304,7 @@ bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::stri
         const int wext = c.tx2 + 2 * rmax;
         if (c.nt < wext - 31 || c.nt > wext + 31) continue;
         if (c.rb * (c.tx2 / 4) > c.nt) continue;
-        const double cost = cost_model(R, c);
+        const double cost = cost_model(R, mode, c);
         if (cost < best) {
             best = cost;
             *cfg = c;
@@ -361,6 +393,9 @@ int get_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg,
     if (v->smem_bytes > kSmemLimit) return fail(MHFD_ERR_UNSUPPORTED, "kernel shared memory too large");
     r = drv().funcSetAttribute(v->fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, v->smem_bytes);
     if (r != CUDA_SUCCESS) return drv_fail(r, "cuFuncSetAttribute");
+    r = drv().occupancy(&v->occupancy, v->fn, cfg.nt, (size_t)v->smem_bytes);
+    if (r != CUDA_SUCCESS) return drv_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (v->occupancy < 1) return fail(MHFD_ERR_UNSUPPORTED, "fused kernel does not fit on an SM");
     std::lock_guard<std::mutex> guard(g_mu);
     auto it = g_variants.find(key);
     if (it != g_variants.end()) {  // another thread won the race

@@ -23,20 +23,24 @@ struct MhfdCand {
 };
 
 // One image of a batch: where it is, how it is stored, where its stretch
-// bounds live and which global tile indices (items) it owns.
+// bounds live, which global tile slots and which queue items it owns.
 struct MhfdJob {
     const void *img;
     const MhfdStretch *st;
     long long pitch;
-    int H, W, dtype, tiles_x;
-    int n_tiles;      // tiles of this image
-    int tile_base;    // first global item of this image
+    int H, W, dtype, tiles_x, tiles_y;
+    int n_tiles;      // tiles of this image (tiles_x * tiles_y)
+    int tile_base;    // first global tile slot of this image
+    int chunk_base;   // first queue item (chunk of tiles) of this image
+    int pad;
 };
 
 // By-value parameter block of the fused kernel (the ladder itself is
-// compiled into the kernel).  Single image: jobs == nullptr and block b
-// processes tile b of `img`.  Batch: a persistent grid pulls global items
-// from *queue until total_items; item -> (job, tile) through tile_base.
+// compiled into the kernel).  Single image: jobs == nullptr and block b of
+// the grid processes the b-th equal share of the image's tiles in
+// strip-major order.  Batch: a persistent grid pulls items (chunks of
+// `chunk` tiles) from *queue until total_items; item -> (job, tiles)
+// through chunk_base.
 struct MhfdKHeader {
     const void *img;          // device image, `pitch` bytes per row
     const MhfdStretch *st;    // stretch bounds of this image
@@ -47,11 +51,13 @@ struct MhfdKHeader {
     int *arg_out;             // optional first-argmax output (H*W)
     long long pitch;          // bytes between rows of img
     long long plane;          // H*W (stack plane stride)
-    int H, W, dtype, tiles_x, cap_tile;
+    int H, W, dtype, tiles_x, tiles_y, cap_tile;
     float thr;                // feature threshold (strict >)
     const MhfdJob *jobs;      // batch mode: job table (device)
     int *queue;               // batch mode: next item counter (zeroed per launch)
-    int n_jobs, total_items;
+    int n_jobs, total_items;  // batch mode: jobs, queue items (chunks)
+    int chunk;                // batch mode: tiles per queue item
+    int pad;
 };
 
 #endif  // MHFD_TYPES_H

@@ -1,8 +1,8 @@
 """Autotuner of the fused kernel's tile configuration.
 
 The fused detection kernel is specialised per ladder and per tile shape
-(tile width/height including the 1-pixel NMS border, rows per step, threads
-per block, level groups).  The built-in heuristic picks a shape from a cost
+(strip width and tile height including the 1-pixel NMS border, rows per
+step, threads per block, level groups).  The built-in heuristic picks a shape from a cost
 model; this module measures instead: it compiles a filtered menu of shapes in
 parallel (NVRTC, CPU processes), times each one's fused kernel with CUDA
 events on a synthetic tile of the workload, and records the winner per
@@ -59,7 +59,7 @@ def lookup(n, t_min, t_max, nms, sms, truncate=4.0):
     return idx
 
 
-def candidates(n, t_min, t_max, nms, limit=None):
+def candidates(n, t_min, t_max, nms, limit=None, min_width=0):
     """Balanced shapes of the menu: every horizontal item has a thread and the
     vertical pass keeps most threads busy."""
     from . import _native
@@ -69,12 +69,14 @@ def candidates(n, t_min, t_max, nms, limit=None):
     rmax = max(int(math.ceil(4.0 * (t_min + i * dt))) for i in range(n + 1))
     seen, out = set(), []
     for k, (tx2, ty2, rb, nt, ng) in enumerate(menu):
+        if tx2 < min_width:
+            continue
         wext = tx2 + 2 * rmax
         hitems = rb * tx2 // 4
         if hitems > nt or hitems < 0.85 * nt:
             continue
         vutil = wext / (nt * -(-wext // nt))
-        if vutil < 0.75 or ty2 < 24:
+        if vutil < 0.75:
             continue
         key = (tx2, ty2, rb, nt, ng)
         if key in seen:
@@ -132,10 +134,11 @@ def main():
     ap.add_argument("--threshold", type=float, default=0.05)
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--limit", type=int, default=0)
+    ap.add_argument("--min-width", type=int, default=0, help="skip strips narrower than this")
     ap.add_argument("--write", action="store_true", help="record the winner in tuned_tiles.json")
     args = ap.parse_args()
     nms = 0 if args.nms == "paper" else 1
-    cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None)
+    cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None, args.min_width)
     t0 = time.time()
     comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands)
     print("compiled %d shapes in %.1f s" % (len(comp), time.time() - t0), flush=True)

@@ -79,7 +79,7 @@ def test_tile_menu_fits_shared_memory(native):
         menu = native.tile_configs(**kw)
         assert len(menu) > 10
         for tx2, ty2, rb, nt, ng in menu:
-            assert tx2 % 4 == 0 and ty2 % rb == 0 and nt % 32 == 0 and ng >= 1
+            assert tx2 % 4 == 0 and ty2 >= 3 and rb >= 2 and nt % 32 == 0 and ng >= 1
         chosen = native.chosen_tile(**kw)
         assert chosen in menu
 
