@@ -183,6 +183,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-tiles", type=int, default=256)
+    ap.add_argument("--no-soft", action="store_true")
+    ap.add_argument("--soft-tiles", type=int, default=16,
+                    help="2048^2 float32 tiles of the soft-score section (64 = full set)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run R detections of the sigma_d=0 tile (for ncu captures)")
     ap.add_argument("--plain", action="store_true", help="with --profile-case: plain path")
@@ -322,6 +325,7 @@ def main():
     cpu = None if args.no_cpu_baseline else cpu_baseline(host[0])
     batched = None if args.no_batch else bench_batch(mhfd, torch, stream)
     serving = None if args.no_serve else bench_serve(mhfd, torch)
+    soft_sec = None if args.no_soft else bench_soft(mhfd, torch, stream, args.soft_tiles)
 
     per_tile.sort()
     p99 = per_tile[min(len(per_tile) - 1, int(math.ceil(0.99 * len(per_tile))) - 1)]
@@ -341,12 +345,60 @@ def main():
         "clocks": clk.summary(),
         "batched": batched,
         "serving": serving,
+        "soft": soft_sec,
         "focus_scores": dict(zip([str(s) for s in SIGMA_D], scores)),
         "focus_monotone_drop": all(scores[j] > scores[j + 1] for j in range(len(scores) - 1)),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_soft(mhfd, torch, stream, count=16):
+    """Differentiable soft focus score on 2048^2 float32 tiles of the 12-bit
+    scene (not quantised) with known sigma_d ~ U[0, 8]: forward and
+    forward+adjoint throughput of the CUDA kernels, and the 200-step Adam
+    calibration of the 16 per-scale weights against sigma_d."""
+    import synth
+    from paper_2108_12050_gb300 import soft
+    t0 = time.perf_counter()
+    pairs = [synth.config4_tile(j) for j in range(count)]
+    render_s = time.perf_counter() - t0
+    imgs = [torch.from_numpy(p[0]).cuda() for p in pairs]
+    sds = [p[1] for p in pairs]
+    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR)
+    w = torch.linspace(-0.5, 1.5, N_LAYERS, device="cuda")
+    tau, temp = THR, 0.01
+
+    def timed(want_grad):
+        for im in imgs[:2]:
+            soft.soft_score(det, im, w, tau, temp, grad_s=1.0, want_grad=want_grad, stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for im in imgs:
+            soft.soft_score(det, im, w, tau, temp, grad_s=1.0, want_grad=want_grad, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return sum(im.numel() for im in imgs) / (ms * 1e-3) / 1e6, ms / len(imgs)
+
+    fwd, fwd_ms = timed(False)
+    bwd, bwd_ms = timed(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    wf, bf, losses = soft.fit_weights(det, imgs, sds, tau=tau, T=temp, steps=200)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    det.close()
+    return {"tiles": count, "side": 2048, "dtype": "f32", "unit": METRIC,
+            "forward": fwd, "forward_ms_per_tile": fwd_ms,
+            "forward_backward": bwd, "forward_backward_ms_per_tile": bwd_ms,
+            "fit": {"steps": 200, "optimizer": "Adam", "seconds": fit_s,
+                    "mse_first": losses[0], "mse_last": losses[-1],
+                    "target_var": float(np.var(sds))},
+            "render_s": render_s}
 
 
 def bench_batch(mhfd, torch, stream, count=256):
@@ -499,12 +551,11 @@ def tile_used(mhfd):
     import torch
     from paper_2108_12050_gb300 import tune
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    idx = tune.lookup(N_LAYERS, T_MIN, T_MAX, "paper", sms)
-    shape = mhfd.tile_configs(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)[idx - 1] if idx else \
-        mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)
+    tuned = tune.lookup(N_LAYERS, T_MIN, T_MAX, "paper", sms)
+    shape = tuned or mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)
     return {"width": shape[0], "height": shape[1], "rows_per_step": shape[2],
             "threads": shape[3], "level_groups": shape[4],
-            "source": "autotuned" if idx else "heuristic"}
+            "source": "autotuned" if tuned else "heuristic"}
 
 
 def profile_case(args):

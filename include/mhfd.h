@@ -77,6 +77,15 @@ typedef struct {
     int32_t keep_candidates;/* 1: also expose the pre-prune candidate list */
     int32_t tile_override;  /* 0 = built-in tile choice; k > 0 = row k-1 of
                                mhfd_tile_configs() (autotuner use) */
+    int32_t tile_shape[5];  /* explicit fused-kernel geometry when
+                               tile_shape[0] > 0, overriding tile_override:
+                               strip width incl. the 2 NMS border columns
+                               (multiple of 4), tile height incl. 2 border
+                               rows, rows per step (2..16), threads per
+                               block (multiple of 32), level groups; the
+                               same five fields as mhfd_tile_configs.
+                               INVALID_ARG when out of range, UNSUPPORTED
+                               when it does not fit in shared memory */
     int32_t timing;         /* 1: record CUDA events around the kernels of each
                                detection (read with mhfd_last_timing) */
     int32_t response;       /* mhfd_response; the fused entry points (detect,

@@ -123,19 +123,19 @@ class Detector:
 
     def __init__(self, n=10, t_min=1.0, t_max=10.0, *, sigmas=None, threshold=0.1, overlap=0.5,
                  nms="paper", truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
-                 device=None, keep_candidates=False, tile_override=None, timing=False,
-                 response="dog", boundary="reflect"):
+                 device=None, keep_candidates=False, tile_override=None, tile_shape=None,
+                 timing=False, response="dog", boundary="reflect"):
         import torch
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
-        if tile_override is None:
+        if tile_override is None and tile_shape is None:
             # a measured tile shape for this ladder and GPU, if the autotuner
             # recorded one; otherwise the library's built-in choice
-            tile_override = 0
             if sigmas is None and device >= 0:
                 from . import tune
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
-                tile_override = tune.lookup(n, t_min, t_max, nms, sms, truncate)
+                tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate)
+        tile_override = tile_override or 0
         self.n = int(n)
         self.device = device
         self._p = _n.make_params(n=n, t_min=t_min, t_max=t_max, sigmas=sigmas,
@@ -143,7 +143,8 @@ class Detector:
                                  truncate=truncate, clip_frac=clip_frac,
                                  max_candidates=max_candidates, device=device,
                                  keep_candidates=keep_candidates, tile_override=tile_override,
-                                 timing=timing, response=response, boundary=boundary)
+                                 tile_shape=tile_shape, timing=timing, response=response,
+                                 boundary=boundary)
         h = ctypes.c_void_p()
         _n.check(_n.lib().mhfd_create_detector(ctypes.byref(self._p), ctypes.byref(h)))
         self._h = h

@@ -109,11 +109,11 @@ STANDARD_VARIANTS = [
 
 def _precompile_one(args):
     n, tmin, tmax, nms, store = args[:5]
-    tile = args[5] if len(args) > 5 else 0
+    shape = args[5] if len(args) > 5 else None
     sys.path.insert(0, os.path.dirname(PKG))
     from paper_2108_12050_gb300 import _native
     return _native.precompile(n=n, t_min=tmin, t_max=tmax, nms=nms, store=store,
-                              tile_override=tile)
+                              tile_shape=shape)
 
 
 def _tuned_variants():
@@ -131,8 +131,10 @@ def _tuned_variants():
         if not m:
             continue
         for best in ent.values():
-            out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)),
-                        0 if m.group(4) == "paper" else 1, 0, int(best["tile_override"])))
+            shape = best.get("shape")
+            if shape and len(shape) == 5:
+                out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)),
+                            0 if m.group(4) == "paper" else 1, 0, tuple(int(v) for v in shape)))
     return out
 
 

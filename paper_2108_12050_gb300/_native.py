@@ -56,6 +56,7 @@ class Params(ctypes.Structure):
         ("device", ctypes.c_int32),
         ("keep_candidates", ctypes.c_int32),
         ("tile_override", ctypes.c_int32),
+        ("tile_shape", ctypes.c_int32 * 5),
         ("timing", ctypes.c_int32),
         ("response", ctypes.c_int32),
         ("boundary", ctypes.c_int32),
@@ -142,7 +143,7 @@ def check(rc, allow_overflow=True):
 
 def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap=0.5,
                 nms=NMS_PAPER, truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
-                device=-1, keep_candidates=False, tile_override=0, timing=False,
+                device=-1, keep_candidates=False, tile_override=0, tile_shape=None, timing=False,
                 response=0, boundary=0):
     p = Params()
     lib().mhfd_default_params(ctypes.byref(p))
@@ -165,6 +166,9 @@ def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap
     p.device = int(device)
     p.keep_candidates = 1 if keep_candidates else 0
     p.tile_override = int(tile_override)
+    if tile_shape:
+        for k, v in enumerate(tile_shape):
+            p.tile_shape[k] = int(v)
     p.timing = 1 if timing else 0
     if isinstance(response, str):
         response = {"dog": 0, "log": 1}[response]

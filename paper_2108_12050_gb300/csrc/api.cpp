@@ -408,6 +408,24 @@ void release(mhfd_detector *d) {
 
 int resolve_tile(const std::vector<int> &R, const mhfd_params &p, TileConfig *cfg) {
     std::string why;
+    if (p.tile_shape[0] > 0) {
+        const int *ts = p.tile_shape;
+        const int nl = (int)R.size();
+        if (ts[0] % 4 || ts[0] < 8 || ts[0] > 2048 || ts[1] < 3 || ts[1] > 4096 || ts[2] < 2 ||
+            ts[2] > 16 || ts[3] % 32 || ts[3] < 32 || ts[3] > 1024 || ts[4] < 1 || ts[4] > nl)
+            return fail(MHFD_ERR_INVALID_ARG, "tile_shape out of range");
+        if (ts[2] * (ts[0] / 4) > 2 * ts[3])
+            return fail(MHFD_ERR_INVALID_ARG, "tile_shape: more than two row quads per thread");
+        cfg->tx2 = ts[0];
+        cfg->ty2 = ts[1];
+        cfg->rb = ts[2];
+        cfg->nt = ts[3];
+        cfg->gb.assign(ts[4] + 1, 0);
+        for (int g = 0; g <= ts[4]; ++g) cfg->gb[g] = (int)((long long)nl * g / ts[4]);
+        if (smem_estimate(R, p.nms, *cfg) > kSmemLimitBytes)
+            return fail(MHFD_ERR_UNSUPPORTED, "tile_shape exceeds shared memory for this ladder");
+        return MHFD_OK;
+    }
     if (p.tile_override > 0) {
         const std::vector<TileConfig> menu = tile_menu(R, p.nms);
         if (p.tile_override > (int)menu.size()) return fail(MHFD_ERR_INVALID_ARG, "tile_override out of range");
@@ -568,6 +586,7 @@ void mhfd_default_params(mhfd_params *p) {
     p->device = -1;
     p->keep_candidates = 0;
     p->tile_override = 0;
+    for (int k = 0; k < 5; ++k) p->tile_shape[k] = 0;
     p->timing = 0;
     p->response = MHFD_RESPONSE_DOG;
     p->boundary = MHFD_BOUNDARY_REFLECT;

@@ -93,6 +93,9 @@ struct LadderKey {
 bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why);
 // Enumerate the configurations offered to the autotuner.
 std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode);
+// opt-in shared memory per block (227 KB) less the kernel's static shared
+// variables (the batch loop's queue slot), which count against the same limit
+constexpr int kSmemLimitBytes = 232448 - 64;
 int brows_for(const std::vector<int> &R, int mode, const TileConfig &c);
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c);
 // Compile (or fetch from cache) the fused kernel for this ladder/config.

@@ -27,9 +27,7 @@ namespace {
 
 #include "kernel_src.inc"  // kTypesSrc, kKernelSrc
 
-// opt-in shared memory per block (227 KB) less the kernel's static shared
-// variables (the batch loop's queue slot), which count against the same limit
-constexpr int kSmemLimit = 232448 - 64;
+constexpr int kSmemLimit = kSmemLimitBytes;
 
 std::mutex g_mu;
 std::map<std::string, Variant *> g_variants;

@@ -66,36 +66,40 @@ class SoftFocus(torch.autograd.Function):
 def features(det, imgs, tau, T=0.01):
     """Per-image mean sigmoid of every layer (S is linear in w: S = w . f)."""
     n = det.n
-    ones = torch.ones(n, device="cuda")
+    ones = torch.ones(n, device=imgs[0].device)
     return torch.stack([soft_score(det, im, ones, tau, T)[1] for im in imgs])
 
 
 def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0):
     """Calibrate per-scale weights w and bias b so that S(I, w) + b regresses
-    `targets` (e.g. the known defocus sigma_d), by Adam through SoftFocus.
+    `targets` (e.g. the known defocus sigma_d) by Adam.
 
-    The layer occupancies differ in spread by an order of magnitude and are
-    small (mean sigmoids), so the optimiser works on standardised features:
+    S is linear in w, S(I, w) = w . f(I) with f the per-layer occupancies,
+    so f is computed once per image by the CUDA forward and every Adam step
+    evaluates w . f exactly (SoftFocus is for losses that also need dS/dI).
+    The occupancies differ in spread by an order of magnitude and are small
+    (mean sigmoids), so the optimiser works on standardised features:
     w = v / s and b = c - (m / s) . v with m, s the per-layer mean and spread
     over the calibration images, which leaves S(I, w) + b = sum_i v_i
     (f_i - m_i) / s_i + c.  Returns (w, b, losses)."""
-    f = features(det, imgs, tau, T)
+    f = features(det, imgs, tau, T).double()
     m = f.mean(0)
     sd = f.std(0) + 1e-6 if f.shape[0] > 1 else torch.ones_like(m)
     g = torch.Generator(device="cpu").manual_seed(seed)
-    y = torch.as_tensor(targets, dtype=torch.float32, device="cuda")
-    v = (0.1 * torch.randn(det.n, generator=g)).cuda().requires_grad_(True)
+    y = torch.as_tensor(targets, dtype=torch.float64, device=f.device)
+    v = (0.1 * torch.randn(det.n, generator=g, dtype=torch.float64)).to(f.device)
+    v.requires_grad_(True)
     c = y.mean().reshape(1).clone().requires_grad_(True)
     opt = torch.optim.Adam([v, c], lr=lr)
     losses = []
     for _ in range(steps):
         opt.zero_grad()
-        w = v / sd
-        b = c - torch.dot(m / sd, v)
-        pred = torch.stack([SoftFocus.apply(im, w, det, tau, T) for im in imgs]) + b
+        pred = f @ (v / sd) + (c - torch.dot(m / sd, v))
         loss = torch.mean((pred - y) ** 2)
         loss.backward()
         opt.step()
         losses.append(float(loss.detach()))
     with torch.no_grad():
-        return (v / sd).detach(), (c - torch.dot(m / sd, v)).detach(), losses
+        w = (v / sd).float()
+        b = (c - torch.dot(m / sd, v)).float()
+    return w.detach(), b.detach(), losses

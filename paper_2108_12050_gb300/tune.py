@@ -39,36 +39,34 @@ def load_table():
 
 
 def lookup(n, t_min, t_max, nms, sms, truncate=4.0):
-    """Tuned tile index (1-based, for params.tile_override) or 0.  The
-    recorded shape must still be the menu's entry at that index (the menu is
-    a function of the library version), else the built-in choice is used."""
+    """Tuned tile shape (the five-field tile_shape of the parameters) for this
+    ladder and SM count, or None (the library's built-in choice is used)."""
     ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate))
     if not ent:
-        return 0
+        return None
     best = ent.get(str(sms)) or ent.get("any")
     if not best:
-        return 0
-    idx = int(best["tile_override"])
-    try:
-        from . import _native
-        menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms, truncate=truncate)
-        if idx < 1 or idx > len(menu) or list(menu[idx - 1]) != list(best["shape"]):
-            return 0
-    except Exception:
-        return 0
-    return idx
+        return None
+    shape = best.get("shape")
+    if not shape or len(shape) != 5:
+        return None
+    return [int(v) for v in shape]
+
+
+def _rmax(n, t_min, t_max, truncate=4.0):
+    import math
+    dt = (t_max - t_min) / n
+    return max(int(math.ceil(truncate * (t_min + i * dt))) for i in range(n + 1))
 
 
 def candidates(n, t_min, t_max, nms, limit=None, min_width=0):
-    """Balanced shapes of the menu: every horizontal item has a thread and the
-    vertical pass keeps most threads busy."""
+    """Balanced shapes of the built-in menu: every horizontal item has a
+    thread and the vertical pass keeps most threads busy."""
     from . import _native
     menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms)
-    dt = (t_max - t_min) / n
-    import math
-    rmax = max(int(math.ceil(4.0 * (t_min + i * dt))) for i in range(n + 1))
+    rmax = _rmax(n, t_min, t_max)
     seen, out = set(), []
-    for k, (tx2, ty2, rb, nt, ng) in enumerate(menu):
+    for (tx2, ty2, rb, nt, ng) in menu:
         if tx2 < min_width:
             continue
         wext = tx2 + 2 * rmax
@@ -82,38 +80,62 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0):
         if key in seen:
             continue
         seen.add(key)
-        out.append((k + 1, key))
+        out.append(key)
     return out[:limit] if limit else out
 
 
+def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5), groups=(2, 3, 4)):
+    """Shapes off the menu's width grid (strip widths fitted to an image
+    width), three thread counts per (width, rows per step, groups), keeping
+    those that fit in shared memory."""
+    from . import _native
+    out = []
+    for tx2 in widths:
+        for rb in rbs:
+            hitems = rb * tx2 // 4
+            nt0 = -(-hitems // 32) * 32
+            for nt in (nt0, nt0 + 32, nt0 + 64):
+                if nt > 1024:
+                    continue
+                for ng in groups:
+                    shape = (tx2, 18, rb, nt, ng)
+                    try:
+                        _native.chosen_tile(n=n, t_min=t_min, t_max=t_max, nms=nms,
+                                            tile_shape=shape)
+                    except Exception:
+                        continue
+                    out.append(shape)
+    return out
+
+
 def _compile_one(args):
-    n, t_min, t_max, nms, idx = args
+    n, t_min, t_max, nms, shape = args
     sys.path.insert(0, os.path.dirname(PKG))
     from paper_2108_12050_gb300 import _native
     t0 = time.time()
     try:
-        _native.precompile(n=n, t_min=t_min, t_max=t_max, nms=nms, tile_override=idx)
-        return idx, time.time() - t0, None
+        _native.precompile(n=n, t_min=t_min, t_max=t_max, nms=nms, tile_shape=shape)
+        return shape, time.time() - t0, None
     except Exception as e:  # a shape the compiler rejects is skipped
-        return idx, time.time() - t0, str(e)
+        return shape, time.time() - t0, str(e)
 
 
 def precompile_all(n, t_min, t_max, nms, cands, workers=None):
     ctx = mp.get_context("spawn")
     workers = workers or (os.cpu_count() or 4)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
-        return list(ex.map(_compile_one, [(n, t_min, t_max, nms, i) for i, _ in cands]))
+        return list(ex.map(_compile_one, [(n, t_min, t_max, nms, c) for c in cands]))
 
 
 def measure(n, t_min, t_max, nms, threshold, img_dev, cands, reps=5):
     import paper_2108_12050_gb300 as mhfd
     res = []
-    for idx, shape in cands:
+    for shape in cands:
         try:
-            det = mhfd.Detector(n, t_min, t_max, threshold=threshold, nms=nms, tile_override=idx,
+            det = mhfd.Detector(n, t_min, t_max, threshold=threshold, nms=nms, tile_shape=shape,
                                 timing=True)
         except Exception as e:
-            res.append((idx, shape, None, str(e)))
+            res.append((shape, None, str(e)))
             continue
         det(img_dev)
         ks = []
@@ -121,7 +143,7 @@ def measure(n, t_min, t_max, nms, threshold, img_dev, cands, reps=5):
             det(img_dev)
             ks.append(det.last_timing()[0])
         det.close()
-        res.append((idx, shape, statistics.median(ks), None))
+        res.append((shape, statistics.median(ks), None))
     return res
 
 
@@ -135,15 +157,20 @@ def main():
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--limit", type=int, default=0)
     ap.add_argument("--min-width", type=int, default=0, help="skip strips narrower than this")
+    ap.add_argument("--widths", default="", help="extra strip widths off the menu, e.g. 312,344")
     ap.add_argument("--write", action="store_true", help="record the winner in tuned_tiles.json")
     args = ap.parse_args()
     nms = 0 if args.nms == "paper" else 1
     cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None, args.min_width)
+    if args.widths:
+        extra = width_candidates(args.n, args.tmin, args.tmax, nms,
+                                 [int(w) for w in args.widths.split(",")])
+        cands += [c for c in extra if c not in cands]
     t0 = time.time()
     comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands)
     print("compiled %d shapes in %.1f s" % (len(comp), time.time() - t0), flush=True)
-    bad = {i for i, _, e in comp if e}
-    cands = [c for c in cands if c[0] not in bad]
+    bad = {tuple(c) for c, _, e in comp if e}
+    cands = [c for c in cands if tuple(c) not in bad]
 
     import numpy as np
     import torch
@@ -152,17 +179,16 @@ def main():
     img = synth.config2_tile(0.0)[:args.side, :args.side].copy()
     dev = torch.from_numpy(img.view(np.int16)).cuda()
     res = measure(args.n, args.tmin, args.tmax, nms, args.threshold, dev, cands)
-    res.sort(key=lambda r: (r[2] is None, r[2] or 0))
-    for idx, shape, ms, err in res:
-        print("%4d %-28s %s" % (idx, shape, ("%.3f ms" % ms) if ms else err), flush=True)
+    res.sort(key=lambda r: (r[1] is None, r[1] or 0))
+    for shape, ms, err in res:
+        print("%-28s %s" % (shape, ("%.3f ms" % ms) if ms else err), flush=True)
     best = res[0]
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     print("best", best, "SMs", sms)
-    if args.write and best[2]:
+    if args.write and best[1]:
         tab = load_table()
         ent = tab.setdefault(ladder_key(args.n, args.tmin, args.tmax, nms), {})
-        ent[str(sms)] = {"tile_override": best[0], "shape": list(best[1]), "ms": best[2],
-                         "side": args.side}
+        ent[str(sms)] = {"shape": list(best[0]), "ms": best[1], "side": args.side}
         with open(TABLE, "w") as f:
             json.dump(tab, f, indent=1, sort_keys=True)
 
