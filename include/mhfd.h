@@ -185,7 +185,11 @@ int mhfd_batch_uses_graph(mhfd_detector *det);
  * clamp, which passes gradient only strictly between lo and hi) and, if d_dw
  * is not NULL, d_dw[i] = grad_s * mean sigmoid of layer i.  The Gaussian
  * levels are recomputed on every call (nothing is kept between calls).
- * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA, OOM. */
+ * Without d_dimg only the forward runs, in the fused kernel (per-block FP64
+ * layer sums, reduced in a fixed order); with it, forward and adjoint run
+ * through full level planes.  Both are deterministic.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED (the LoG or
+ * periodic variants), CUDA, OOM, JIT. */
 int mhfd_soft_score(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H, int32_t W,
                     size_t pitch_bytes, const float *d_w, float tau, float temperature,
                     float grad_s, void *stream, float *d_S, float *d_mean_sig, float *d_dimg,
@@ -258,8 +262,10 @@ int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap);
  * fields as above).  Host only. */
 int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5);
 
-/* Compiles the fused kernel for the ladder and tile of `p` (store = 1: the
- * stack-storing variant of mhfd_debug_stack) into the on-disk kernel cache
+/* Compiles the fused kernel for the ladder and tile of `p` (store = 0: the
+ * detection kernel of params.nms; 1: the stack-storing variant of
+ * mhfd_debug_stack; 2: the soft-score forward of mhfd_soft_score) into the
+ * on-disk kernel cache
  * without using a GPU, so that a later mhfd_create_detector starts at once.
  * The cache directory is $MHFD_JIT_CACHE, else `_jit_cache` next to the
  * library.  Errors: INVALID_ARG, UNSUPPORTED, JIT. */

@@ -96,14 +96,15 @@ def build_lib(force=False):
     return LIB
 
 
-# ladders compiled ahead of time: (n, t_min, t_max, nms, store)
+# ladders compiled ahead of time: (n, t_min, t_max, nms, store); store 1 is
+# the stack-storing variant, 2 the soft-score forward
 STANDARD_VARIANTS = [
     (10, 1.0, 10.0, 0, 0), (10, 1.0, 10.0, 0, 1),     # 512^2 uint8 workload
     (10, 1.0, 10.0, 1, 0), (10, 1.0, 10.0, 1, 1),
     (16, 1.0, 12.0, 0, 0), (16, 1.0, 12.0, 0, 1),     # 4096^2 uint16 workload
-    (16, 1.0, 12.0, 1, 0),
+    (16, 1.0, 12.0, 1, 0), (16, 1.0, 12.0, 0, 2),
     (4, 1.0, 4.0, 0, 0), (4, 1.0, 4.0, 0, 1),         # small ladders of the tests
-    (4, 1.0, 4.0, 1, 0), (4, 1.0, 4.0, 1, 1),
+    (4, 1.0, 4.0, 1, 0), (4, 1.0, 4.0, 1, 1), (4, 1.0, 4.0, 0, 2),
 ]
 
 
@@ -133,8 +134,10 @@ def _tuned_variants():
         for best in ent.values():
             shape = best.get("shape")
             if shape and len(shape) == 5:
-                out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)),
-                            0 if m.group(4) == "paper" else 1, 0, tuple(int(v) for v in shape)))
+                nms = 0 if m.group(4) == "paper" else 1
+                for store in ((0, 1, 2) if nms == 0 else (0, 1)):
+                    out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)), nms,
+                                store, tuple(int(v) for v in shape)))
     return out
 
 

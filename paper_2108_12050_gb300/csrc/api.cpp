@@ -48,6 +48,7 @@ struct mhfd_detector {
     LadderKey lk;
     Variant *var = nullptr;
     Variant *var_store = nullptr;
+    Variant *var_soft = nullptr;  // soft-score forward (kernel mode 2)
     std::vector<uint64_t> params;  // by-value parameter block of the fused kernel
 
     // fixed device buffers
@@ -864,7 +865,8 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     make_taps(t, R, &lk.taps, &tapoff, &lk.tsc);
     TileConfig cfg;
     if ((rc = resolve_tile(R, *p, &cfg))) return rc;
-    return precompile_variant(lk, p->nms, store, cfg);
+    if (store == 2) return precompile_variant(lk, 2, 0, cfg);  // soft-score forward
+    return precompile_variant(lk, p->nms, store != 0, cfg);
 }
 
 
@@ -1043,15 +1045,54 @@ int mhfd_soft_score(mhfd_detector *d, const void *img, int32_t dtype, int32_t H,
     int rc = check_image(img, dtype, H, W, pitch);
     if (rc) return rc;
     DeviceGuard g(d->device);
-    if ((rc = ensure_image_capacity(d, H, W, true))) return rc;
+    if ((rc = ensure_image_capacity(d, H, W, d_dimg != nullptr))) return rc;
     constexpr int kMaxBlocks = 2048;
     if (!d->soft_part && (rc = dalloc(&d->soft_part, (size_t)kMaxBlocks * 64))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     rc = enqueue_stretch(img, dtype, H, W, (long long)pitch, clip_rank(d, H, W), d->sel, d->st, s);
     if (rc) return rc;
-    return enqueue_soft(img, dtype, H, W, (long long)pitch, d->st, (int)d->R.size(), d->R,
-                        d->d_taps, d->d_tsc, d_w, tau, temperature, grad_s, d->pL, d->pT, d->pI,
-                        d->soft_part, kMaxBlocks, d_S, d_mean_sig, d_dimg, d_dw, s);
+    if (d_dimg) {
+        // forward and adjoint through the plain level planes
+        return enqueue_soft(img, dtype, H, W, (long long)pitch, d->st, (int)d->R.size(), d->R,
+                            d->d_taps, d->d_tsc, d_w, tau, temperature, grad_s, d->pL, d->pT,
+                            d->pI, d->soft_part, kMaxBlocks, d_S, d_mean_sig, d_dimg, d_dw, s);
+    }
+    // forward only: the fused kernel accumulates the sigmoids per block
+    if (!d->var_soft && (rc = get_variant(d->lk, 2, 0, d->cfg, &d->var_soft))) return rc;
+    Variant *v = d->var_soft;
+    int tx, ty;
+    const int n_tiles = tiles_of(d, H, W, &tx, &ty);
+    int dev = 0, sms = 1;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    long long grid = (long long)sms * v->occupancy;
+    if (grid > n_tiles) grid = n_tiles;
+    if (grid > kMaxBlocks) grid = kMaxBlocks;
+    const int nd = (int)d->R.size() - 1;
+    MHFD_CUDA(cudaMemsetAsync(d->soft_part, 0, sizeof(double) * (size_t)grid * nd, s));
+    std::vector<unsigned long long> pbuf((v->param_bytes + 7) / 8 + 1, 0);
+    MhfdKHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.img = img;
+    h.st = d->st;
+    h.pitch = (long long)pitch;
+    h.plane = (long long)H * W;
+    h.H = H;
+    h.W = W;
+    h.dtype = dtype;
+    h.tiles_x = tx;
+    h.tiles_y = ty;
+    h.total_items = n_tiles;
+    h.soft_tau = tau;
+    h.soft_inv_t = 1.0f / temperature;
+    h.soft_part = d->soft_part;
+    std::memcpy(pbuf.data(), &h, sizeof(h));
+    void *args[] = {pbuf.data()};
+    const CUresult r = drv().launchKernel(v->fn, (unsigned)grid, 1, 1, (unsigned)v->cfg.nt, 1, 1,
+                                          (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
+    if (r != CUDA_SUCCESS) return fail(MHFD_ERR_CUDA, "cuLaunchKernel (soft forward)");
+    return enqueue_soft_finish(d->soft_part, (int)grid, nd, (long long)H * W, d_w, grad_s, d_S,
+                               d_mean_sig, d_dw, s);
 }
 
 int mhfd_result_ready(mhfd_detector *d) {

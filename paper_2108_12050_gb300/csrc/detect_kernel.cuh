@@ -49,7 +49,9 @@ constexpr int TX = TX2 - 2;       // output columns of a strip
 constexpr int TY = MHFD_TY2 - 2;  // output rows of a tile (candidate storage unit)
 constexpr int RB = MHFD_RB;
 constexpr int NT = MHFD_NT;
-constexpr int MODE = MHFD_MODE;  // 0: paper (argmax over scales + 3x3), 1: 3x3x3
+// 0: paper rule (argmax over scales + 3x3), 1: 3x3x3 rule, 2: soft-score
+// forward (per-layer sums of sigmoid((D - tau) / T), no maxima)
+constexpr int MODE = MHFD_MODE;
 constexpr bool STORE = (MHFD_STORE) != 0;
 
 // Kernel radius R_l of Gaussian level l and the level groups [GB(g), GB(g+1)).
@@ -126,7 +128,7 @@ constexpr int NTAPS = tapoff(NL);
 constexpr int VROW = vrow_max();
 constexpr int SMEM_IN = BROWS * WEXTP;
 constexpr int SMEM_V = RB * VROW;
-constexpr int SMEM_RING_F = MODE == 0 ? RING * TX2 : RING * NDOG * TX2;
+constexpr int SMEM_RING_F = MODE == 0 ? RING * TX2 : MODE == 1 ? RING * NDOG * TX2 : 0;
 constexpr int SMEM_RING_B = MODE == 0 ? ((RING * TX2 + 15) & ~15) : 0;
 constexpr int SMEM_BYTES = 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64;
 
@@ -141,10 +143,15 @@ struct KParams {
     MhfdKHeader h;
 };
 
+constexpr int NSOFT = MODE == 2 ? NDOG : 1;
+
 struct HState {
     float lp[4];  // L of the previous level
     float m[4];   // running max over scales
     int a[4];     // its first argmax
+    // soft-score forward: running sums over the march of sigmoid((D_i -
+    // tau) / T) at this item's interior output pixels, per layer
+    float soft[NSOFT];
 };
 
 __device__ __forceinline__ int reflect_idx(int i, int n) {
@@ -448,6 +455,13 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
                     st.m[u] = d[u];
                     st.a[u] = I;
                 }
+        } else if (MODE == 2) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cx.inter[u]) {
+                    const float z = fminf(fmaxf((d[u] - h.soft_tau) * h.soft_inv_t, -80.0f), 80.0f);
+                    st.soft[I] += __fdividef(1.0f, 1.0f + __expf(-z));
+                }
         } else {
             const float ninf = -__int_as_float(0x7f800000);
             float4 o;
@@ -701,6 +715,30 @@ struct Smem {
     int *scan;
 };
 
+// Adds this block's sums of every layer (FP64, fixed order) to its slot of
+// h.soft_part (zeroed before the launch; only this block writes it).
+__device__ __forceinline__ void soft_flush(const MhfdKHeader &h, const HState (&hs)[HI],
+                                           int *s_scan) {
+    constexpr int NW = NT / 32;
+    double *red = reinterpret_cast<double *>(s_scan);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < NSOFT; ++i) {
+        double v = 0.0;
+#pragma unroll
+        for (int it = 0; it < HI; ++it) v += (double)hs[it].soft[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NW; ++w) t += red[w];
+            h.soft_part[(long long)blockIdx.x * NSOFT + i] += t;
+        }
+        __syncthreads();
+    }
+}
+
 // One march down strip `tx` over its tiles [ta, tb): tile k's candidates go
 // to slot slot0 + k * tiles_x + tx.  `sp` carries the image of the job.
 __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &st, int tiles_x,
@@ -724,6 +762,10 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
     __syncthreads();
 
     HState hs[HI];
+#pragma unroll
+    for (int it = 0; it < HI; ++it)
+#pragma unroll
+        for (int i = 0; i < NSOFT; ++i) hs[it].soft[i] = 0.0f;
     int base = 0;       // input row held in window row 0
     int tile = 0;       // tile (relative to ta) now receiving candidates
     int total = 0;      // its candidates so far
@@ -736,7 +778,7 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
         // maxima of the rows whose lower neighbour is now known
         int ra = max(1, s * RB - 1);
         const int rb = min(m.Y, s * RB + RB - 2);
-        while (ra <= rb) {
+        while (MODE != 2 && ra <= rb) {
             const int tend = min(m.Y, (tile + 1) * TY);  // last row of the tile
             const int re = min(rb, tend);
             total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, ra, re,
@@ -760,6 +802,7 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
         }
         __syncthreads();
     }
+    if constexpr (MODE == 2) soft_flush(h, hs, sm.scan);
 }
 
 // Tiles [k0, k1) of an image in strip-major order (k -> strip k / tiles_y,

@@ -179,6 +179,11 @@ int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
 // ------------------------------------------------------------ soft score
 // Forward (and, with d_dimg, the adjoint) of the soft focus score on the
 // level planes L (n_levels planes of H*W, overwritten by the backward).
+// final reduction of per-block layer sums (fixed order) into S, the
+// per-layer means and optionally dS/dw
+int enqueue_soft_finish(const double *block_part, int nblocks, int n_layers, long long plane,
+                        const float *d_w, float grad_s, float *d_S, float *d_mean_sig, float *d_dw,
+                        cudaStream_t s);
 int enqueue_soft(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
                  int n_levels, const std::vector<int> &R, const float *d_taps, const float *d_tsc,
                  const float *d_w, float tau, float temp, float grad_s, float *scratch_L,

@@ -193,8 +193,9 @@ int smem_fixed(const std::vector<int> &R, int mode, const TileConfig &c) {
         for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) o += (c.tx2 + 2 * R[l] + 3) & ~3;
         vrow = o > vrow ? o : vrow;
     }
+    // mode 0: max/argmax ring, 1: response-stack ring, 2 (soft forward): none
     const int ring = c.rb + 2;
-    const int ring_f = mode == 0 ? ring * c.tx2 : ring * (nl - 1) * c.tx2;
+    const int ring_f = mode == 0 ? ring * c.tx2 : mode == 1 ? ring * (nl - 1) * c.tx2 : 0;
     const int ring_b = mode == 0 ? ((ring * c.tx2 + 15) & ~15) : 0;
     return 4 * (c.rb * vrow + ring_f) + ring_b + 4 * 64;
 }

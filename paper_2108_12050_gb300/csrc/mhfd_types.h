@@ -57,7 +57,10 @@ struct MhfdKHeader {
     int *queue;               // batch mode: next item counter (zeroed per launch)
     int n_jobs, total_items;  // batch mode: jobs, queue items (chunks)
     int chunk;                // batch mode: tiles per queue item
+    float soft_tau;           // soft-score forward: threshold of the sigmoid
+    float soft_inv_t;         //   and its inverse temperature
     int pad;
+    double *soft_part;        //   per-block, per-layer sums (zeroed before launch)
 };
 
 #endif  // MHFD_TYPES_H

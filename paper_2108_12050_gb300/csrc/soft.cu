@@ -173,6 +173,15 @@ __global__ void soft_mask(const char *img, int dtype, int H, int W, long long pi
 
 }  // namespace
 
+int enqueue_soft_finish(const double *block_part, int nblocks, int n_layers, long long plane,
+                        const float *d_w, float grad_s, float *d_S, float *d_mean_sig, float *d_dw,
+                        cudaStream_t s) {
+    soft_finish<<<1, 64, 0, s>>>(block_part, nblocks, n_layers, plane, d_w, grad_s, d_S,
+                                 d_mean_sig, d_dw);
+    MHFD_CUDA(cudaGetLastError());
+    return MHFD_OK;
+}
+
 int enqueue_soft(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
                  int n_levels, const std::vector<int> &R, const float *d_taps, const float *d_tsc,
                  const float *d_w, float tau, float temp, float grad_s, float *scratch_L,

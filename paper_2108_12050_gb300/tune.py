@@ -84,18 +84,21 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0):
     return out[:limit] if limit else out
 
 
-def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5), groups=(2, 3, 4)):
+def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6), groups=(2, 3, 4)):
     """Shapes off the menu's width grid (strip widths fitted to an image
-    width), three thread counts per (width, rows per step, groups), keeping
-    those that fit in shared memory."""
+    width).  Thread counts: enough for every horizontal item, and enough for
+    every halo'd column of the vertical pass in one round (plus one warp);
+    keeps those that fit in shared memory."""
     from . import _native
+    rmax = _rmax(n, t_min, t_max)
     out = []
     for tx2 in widths:
+        ncol = -(-(tx2 + 2 * rmax) // 32) * 32
         for rb in rbs:
             hitems = rb * tx2 // 4
-            nt0 = -(-hitems // 32) * 32
-            for nt in (nt0, nt0 + 32, nt0 + 64):
-                if nt > 1024:
+            nth = -(-hitems // 32) * 32
+            for nt in sorted({max(nth, ncol), max(nth, ncol) + 32}):
+                if nt > 1024 or hitems > nt:
                     continue
                 for ng in groups:
                     shape = (tx2, 18, rb, nt, ng)

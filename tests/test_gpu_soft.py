@@ -49,6 +49,36 @@ def test_soft_score_and_gradient_match_oracle(n, tmin, tmax, shape):
     det.close()
 
 
+@pytest.mark.parametrize("n,tmin,tmax,shape,dtype", [(4, 1.0, 4.0, (96, 80), "f32"),
+                                                     (16, 1.0, 12.0, (150, 130), "f32"),
+                                                     (16, 1.0, 12.0, (300, 700), "u16")])
+def test_fused_forward_matches_oracle_and_adjoint_path(n, tmin, tmax, shape, dtype):
+    """Forward-only calls run in the fused kernel; they agree with the oracle
+    and with the forward of the plain-plane path used with the adjoint."""
+    import paper_2108_12050_gb300 as mhfd
+    from paper_2108_12050_gb300 import soft
+    img, _ = _f32_tile(5, *shape)
+    if dtype == "u16":
+        img = np.clip(np.rint(img), 0, 4095).astype(np.uint16)
+    w = np.linspace(1.0, -0.5, n)
+    tau, T = 0.05, 0.01
+    det = mhfd.Detector(n, tmin, tmax, threshold=tau)
+    dev = torch.from_numpy(img.view(np.int16) if dtype == "u16" else img).cuda()
+    wt = torch.tensor(w, dtype=torch.float32)
+    S_f, ms_f, _, _ = soft.soft_score(det, dev, wt, tau, T)
+    S_p, ms_p, _, _ = soft.soft_score(det, dev, wt, tau, T, grad_s=1.0, want_grad=True)
+    lo, hi = oracle.stretch_bounds(img)
+    S_ref, ms_ref, _ = oracle.soft_score(img, n, tmin, tmax, w, tau=tau, T=T, lo=lo, hi=hi,
+                                         grad=False)
+    np.testing.assert_allclose(ms_f.cpu().numpy(), ms_ref, rtol=0, atol=1e-4)
+    np.testing.assert_allclose(ms_f.cpu().numpy(), ms_p.cpu().numpy(), rtol=0, atol=1e-4)
+    assert abs(float(S_f) - S_ref) <= 1e-4 * np.abs(w).sum()
+    # deterministic: a second call gives the same bits
+    S_f2, ms_f2, _, _ = soft.soft_score(det, dev, wt, tau, T)
+    assert torch.equal(ms_f, ms_f2) and float(S_f) == float(S_f2)
+    det.close()
+
+
 def test_autograd_wrapper():
     import paper_2108_12050_gb300 as mhfd
     from paper_2108_12050_gb300 import soft
