@@ -388,14 +388,15 @@ def bench_soft(mhfd, torch, stream, count=16):
     bwd, bwd_ms = timed(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    wf, bf, losses = soft.fit_weights(det, imgs, sds, tau=tau, T=temp, steps=200)
+    tm = {}
+    wf, bf, losses = soft.fit_weights(det, imgs, sds, tau=tau, T=temp, steps=200, timings=tm)
     torch.cuda.synchronize()
     fit_s = time.perf_counter() - t0
     det.close()
     return {"tiles": count, "side": 2048, "dtype": "f32", "unit": METRIC,
             "forward": fwd, "forward_ms_per_tile": fwd_ms,
             "forward_backward": bwd, "forward_backward_ms_per_tile": bwd_ms,
-            "fit": {"steps": 200, "optimizer": "Adam", "seconds": fit_s,
+            "fit": {"steps": 200, "optimizer": "Adam", "seconds": fit_s, **tm,
                     "mse_first": losses[0], "mse_last": losses[-1],
                     "target_var": float(np.var(sds))},
             "render_s": render_s}

@@ -231,9 +231,10 @@ std::vector<int> groups_for(int nl, int max_per_group) {
 }
 
 // relative instruction cost per output pixel (FMA-dominated model): the
-// vertical pass over each group's halo'd columns in rounds of nt threads,
-// the horizontal pass over the strip's columns in rounds of nt items, and
-// the window shifts
+// vertical pass over each group's halo'd columns (a group needing more than
+// one round of nt threads is charged for the idle thread slots of its last
+// round, which wait at the next barrier), the horizontal pass over the
+// strip's columns, and the window shifts
 double cost_model(const std::vector<int> &R, int mode, const TileConfig &c) {
     const int rmax = rmax_of(R);
     const double tx = c.tx2 - 2;
@@ -247,12 +248,11 @@ double cost_model(const std::vector<int> &R, int mode, const TileConfig &c) {
         }
         w += rg;  // folded sums of the group
         const int cols = c.tx2 + 2 * rg;
-        v += w * ((cols + c.nt - 1) / c.nt) * (double)c.nt / tx;
+        const double slots = cols <= c.nt ? cols : ((cols + c.nt - 1) / c.nt) * (double)c.nt;
+        v += w * slots / tx;
     }
     for (int r : R) h += 2 * r + 1;
-    const double h_items = c.rb * (c.tx2 / 4.0);
-    const double h_slots = ((int)((h_items + c.nt - 1) / c.nt)) * (double)c.nt;
-    const double h_eff = h * (c.tx2 / tx) * (h_slots / h_items);
+    const double h_eff = h * (c.tx2 / tx);
     const int brows = brows_for(R, mode, c);
     const int steps_per_shift = (brows - (c.rb + 2 * rmax)) / c.rb + 1;
     const double wext = c.tx2 + 2 * rmax;
@@ -293,25 +293,34 @@ std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode) {
 
 bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why) {
     const std::vector<TileConfig> menu = tile_menu(R, mode);
-    double best = 1e300;
-    bool found = false;
-    for (const TileConfig &c : menu) {
-        // balanced shapes: vertical-pass columns fit the block, every
-        // horizontal item has a thread
-        int rmax = 0;
-        for (int r : R) rmax = r > rmax ? r : rmax;
-        const int wext = c.tx2 + 2 * rmax;
-        if (c.nt < wext - 31 || c.nt > wext + 31) continue;
-        if (c.rb * (c.tx2 / 4) > c.nt) continue;
-        const double cost = cost_model(R, mode, c);
-        if (cost < best) {
-            best = cost;
-            *cfg = c;
-            found = true;
+    const int rmax = rmax_of(R);
+    // Preferred shapes (what the autotuner finds on GB300): four rows per
+    // step (one vertical part, enough rows to amortise a step's barriers and
+    // scans), one thread per halo'd column so that the vertical pass of every
+    // group is a single round, at most 512 threads (at least 128 registers
+    // each), every horizontal item with a thread.  Among them, and failing
+    // that among all balanced shapes, the cost model decides.
+    for (int pass = 0; pass < 2; ++pass) {
+        double best = 1e300;
+        bool found = false;
+        for (const TileConfig &c : menu) {
+            const int wext = c.tx2 + 2 * rmax;
+            const int ncol = (wext + 31) / 32 * 32;
+            if (c.rb * (c.tx2 / 4) > c.nt) continue;
+            if (pass == 0 && (c.rb != 4 || c.nt < ncol || c.nt > ncol + 32 || c.nt > 512))
+                continue;
+            if (pass == 1 && (c.nt < wext - 31 || c.nt > wext + 31)) continue;
+            const double cost = cost_model(R, mode, c);
+            if (cost < best) {
+                best = cost;
+                *cfg = c;
+                found = true;
+            }
         }
+        if (found) return true;
     }
-    if (!found && why) *why = "no tile configuration fits in shared memory for this ladder";
-    return found;
+    if (why) *why = "no tile configuration fits in shared memory for this ladder";
+    return false;
 }
 
 namespace {

@@ -70,7 +70,7 @@ def features(det, imgs, tau, T=0.01):
     return torch.stack([soft_score(det, im, ones, tau, T)[1] for im in imgs])
 
 
-def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0):
+def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0, timings=None):
     """Calibrate per-scale weights w and bias b so that S(I, w) + b regresses
     `targets` (e.g. the known defocus sigma_d) by Adam.
 
@@ -81,8 +81,13 @@ def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0):
     (mean sigmoids), so the optimiser works on standardised features:
     w = v / s and b = c - (m / s) . v with m, s the per-layer mean and spread
     over the calibration images, which leaves S(I, w) + b = sum_i v_i
-    (f_i - m_i) / s_i + c.  Returns (w, b, losses)."""
+    (f_i - m_i) / s_i + c.  Returns (w, b, losses); `timings`, if a dict,
+    receives the seconds spent on the features and on the optimiser."""
+    import time
+    t0 = time.perf_counter()
     f = features(det, imgs, tau, T).double()
+    torch.cuda.synchronize(f.device)
+    t1 = time.perf_counter()
     m = f.mean(0)
     sd = f.std(0) + 1e-6 if f.shape[0] > 1 else torch.ones_like(m)
     g = torch.Generator(device="cpu").manual_seed(seed)
@@ -102,4 +107,7 @@ def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0):
     with torch.no_grad():
         w = (v / sd).float()
         b = (c - torch.dot(m / sd, v)).float()
+    if timings is not None:
+        timings["features_s"] = t1 - t0
+        timings["optimizer_s"] = time.perf_counter() - t1
     return w.detach(), b.detach(), losses
