@@ -239,7 +239,7 @@ def main():
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(tiles) + 1)]
           for _ in range(args.steps)]
     kernel_ms = []
-    launches_per_tile = 16  # stretch 5, fused 1, gather 2, prune 4, output 4
+    launches_per_tile = 17  # stretch 5, fused 1, gather 2, prune 5, output 4 (ncu launch list)
     with ClockSampler(local) as clk:
         barrier()
         t_start = torch.cuda.Event(enable_timing=True)

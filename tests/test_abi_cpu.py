@@ -90,3 +90,30 @@ def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
     assert rc == 0
     files = os.listdir(tmp_path)
     assert any(f.endswith(".cubin") for f in files)
+
+
+def test_explicit_tile_shape(native):
+    kw = dict(n=16, t_min=1.0, t_max=12.0)
+    assert native.chosen_tile(tile_shape=(320, 18, 4, 448, 3), **kw) == (320, 18, 4, 448, 3)
+    # out of range: width not a multiple of 4, threads not a multiple of 32,
+    # too few rows per step, more groups than levels, more than two row
+    # quads per thread
+    for bad in ((322, 18, 4, 448, 3), (320, 18, 4, 450, 3), (320, 18, 1, 448, 3),
+                (320, 18, 4, 448, 18), (320, 18, 8, 128, 3)):
+        with pytest.raises(native.MhfdError) as e:
+            native.chosen_tile(tile_shape=bad, **kw)
+        assert e.value.code == -1, bad
+    # does not fit in shared memory for this ladder
+    with pytest.raises(native.MhfdError) as e:
+        native.chosen_tile(tile_shape=(1024, 18, 8, 1024, 1), **kw)
+    assert e.value.code == -2
+
+
+def test_heuristic_tile_is_one_vertical_round(native):
+    import math
+    for kw in (dict(n=16, t_min=1.0, t_max=12.0), dict(n=10, t_min=1.0, t_max=10.0),
+               dict(n=4, t_min=1.0, t_max=4.0)):
+        tx2, ty2, rb, nt, ng = native.chosen_tile(**kw)
+        dt = (kw["t_max"] - kw["t_min"]) / kw["n"]
+        rmax = max(math.ceil(4 * (kw["t_min"] + i * dt)) for i in range(kw["n"] + 1))
+        assert nt >= tx2 + 2 * rmax and rb * tx2 // 4 <= nt
