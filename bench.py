@@ -307,15 +307,20 @@ def main():
         pt_ = torch.empty(h.shape, dtype=torch.int16, pin_memory=True)
         pt_.numpy()[:] = h.view(np.int16)
         pinned.append(pt_.numpy().view(np.uint16))
+    # one detector and stream per tile of the step: the copy of one tile
+    # (pinned host memory, copy engine) overlaps the detection of another
+    streams = [torch.cuda.Stream() for _ in dets]
     res_bytes = 0
-    for h in pinned:
-        det.detect_host(h, stream)
+    for j, h in enumerate(pinned):
+        dets[j].detect_host(h, streams[j])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(3, min(args.steps, 10))
     for _ in range(e2e_steps):
-        for h in pinned:
-            r = det.detect_host(h, stream)
+        for j, h in enumerate(pinned):
+            dets[j].detect_host(h, streams[j], wait=False)
+        for j in range(len(pinned)):
+            r = dets[j].wait()
             res_bytes += 8 * 40 + 24 * r.n_blobs
     e2e_dt = time.perf_counter() - t0
     e2e = {"value": e2e_steps * px_step / e2e_dt / 1e6, "unit": METRIC,

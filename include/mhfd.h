@@ -205,6 +205,15 @@ int mhfd_result_ready(mhfd_detector *det);
 int mhfd_detect_host(mhfd_detector *det, const void *h_img, int32_t dtype, int32_t H, int32_t W,
                      size_t pitch_bytes, void *stream, mhfd_result *out);
 
+/* Asynchronous form of mhfd_detect_host: enqueues the copy of the host image
+ * into detector-owned device memory and the detection on `stream` and
+ * returns; read the results with mhfd_result_wait.  h_img must stay valid
+ * and unchanged until then; with pinned host memory the copy overlaps work
+ * already running on other streams (for example the detection of the
+ * previous image by another detector).  Same errors as mhfd_detect. */
+int mhfd_detect_host_async(mhfd_detector *det, const void *h_img, int32_t dtype, int32_t H,
+                           int32_t W, size_t pitch_bytes, void *stream);
+
 /* Same detection as mhfd_detect, computed by the unfused "plain" pipeline:
  * one blur kernel pair per Gaussian level writing every L_i to device
  * memory, then a DoG/argmax kernel, an NMS kernel and the same pruning.  It

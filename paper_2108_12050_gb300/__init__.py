@@ -234,14 +234,23 @@ class Detector:
         self.detect(img, stream)
         return self.wait()
 
-    def detect_host(self, img: np.ndarray, stream=None) -> DetectionResult:
-        """End to end from a host (numpy) image: copy in, detect, results out."""
+    def detect_host(self, img: np.ndarray, stream=None, wait=True):
+        """End to end from a host (numpy) image: copy in, detect, results out.
+        With ``wait=False`` the copy and the detection are only enqueued
+        (``img`` must stay alive and unchanged until ``wait()``); use pinned
+        host memory for the copy to overlap other streams' work."""
         img = np.ascontiguousarray(img)
         code = {np.dtype(np.uint8): _n.U8, np.dtype(np.uint16): _n.U16,
                 np.dtype(np.float32): _n.F32}.get(img.dtype)
         if code is None:
             raise TypeError("image must be uint8, uint16 or float32")
         H, W = img.shape
+        if not wait:
+            self._img_ref = img
+            _n.check(_n.lib().mhfd_detect_host_async(self._h, img.ctypes.data_as(ctypes.c_void_p),
+                                                     code, H, W, img.strides[0],
+                                                     _stream_handle(stream)))
+            return None
         r = _n.Result()
         _n.check(_n.lib().mhfd_detect_host(self._h, img.ctypes.data_as(ctypes.c_void_p), code,
                                            H, W, img.strides[0], _stream_handle(stream),

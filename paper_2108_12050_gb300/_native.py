@@ -29,7 +29,7 @@ EXPORTS = [
     "mhfd_default_params", "mhfd_create_detector", "mhfd_destroy_detector", "mhfd_detect",
     "mhfd_result_wait", "mhfd_detect_batch", "mhfd_result_wait_batch", "mhfd_batch_uses_graph",
     "mhfd_result_ready", "mhfd_soft_score",
-    "mhfd_detect_host", "mhfd_detect_plain", "mhfd_debug_stack",
+    "mhfd_detect_host", "mhfd_detect_host_async", "mhfd_detect_plain", "mhfd_debug_stack",
     "mhfd_prune", "mhfd_prune_noalloc", "mhfd_tile_configs", "mhfd_chosen_tile", "mhfd_precompile",
     "mhfd_last_timing", "mhfd_probe_ffma_peak", "mhfd_last_error", "mhfd_version",
 ]
@@ -108,6 +108,7 @@ def lib():
         L.mhfd_detect.argtypes = [P, P, I32, I32, I32, SZ, P]
         L.mhfd_result_wait.argtypes = [P, ctypes.POINTER(Result)]
         L.mhfd_detect_host.argtypes = [P, P, I32, I32, I32, SZ, P, ctypes.POINTER(Result)]
+        L.mhfd_detect_host_async.argtypes = [P, P, I32, I32, I32, SZ, P]
         L.mhfd_detect_batch.argtypes = [P, I32, P, P, P, P, P, P]
         L.mhfd_result_wait_batch.argtypes = [P, ctypes.POINTER(Result), I32]
         L.mhfd_batch_uses_graph.argtypes = [P]

@@ -756,22 +756,30 @@ int mhfd_result_wait(mhfd_detector *d, mhfd_result *out) {
     return out->status;
 }
 
-int mhfd_detect_host(mhfd_detector *d, const void *h_img, int32_t dtype, int32_t H, int32_t W,
-                     size_t pitch, void *stream, mhfd_result *out) {
-    if (!d || !out) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+int mhfd_detect_host_async(mhfd_detector *d, const void *h_img, int32_t dtype, int32_t H,
+                           int32_t W, size_t pitch, void *stream) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
     int rc = check_image(h_img, dtype, H, W, pitch);
     if (rc) return rc;
     DeviceGuard g(d->device);
     const size_t row = (size_t)W * elem_size(dtype);
     const size_t bytes = row * (size_t)H;
     if (bytes > d->img_copy_bytes) {
+        // the previous copy may still be in use by an earlier detection
+        if (d->pending && d->ev_done) MHFD_CUDA(cudaEventSynchronize(d->ev_done));
         if ((rc = dalloc(reinterpret_cast<char **>(&d->d_img_copy), bytes))) return rc;
         d->img_copy_bytes = bytes;
     }
     cudaStream_t s = (cudaStream_t)stream;
     MHFD_CUDA(cudaMemcpy2DAsync(d->d_img_copy, row, h_img, pitch, row, (size_t)H,
                                 cudaMemcpyHostToDevice, s));
-    rc = detect_impl(d, d->d_img_copy, dtype, H, W, row, s, false, nullptr, nullptr, nullptr);
+    return detect_impl(d, d->d_img_copy, dtype, H, W, row, s, false, nullptr, nullptr, nullptr);
+}
+
+int mhfd_detect_host(mhfd_detector *d, const void *h_img, int32_t dtype, int32_t H, int32_t W,
+                     size_t pitch, void *stream, mhfd_result *out) {
+    if (!d || !out) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    const int rc = mhfd_detect_host_async(d, h_img, dtype, H, W, pitch, stream);
     if (rc) return rc;
     return mhfd_result_wait(d, out);
 }

@@ -3,8 +3,9 @@
 // digits (1 pass for uint8, 2 for uint16, 4 for float32 keys), entirely on
 // the stream (no host round trip).  Each pass builds, per target, the digit
 // histogram of the pixels whose higher digits match the target's prefix,
-// with warp-aggregated shared-memory atomics; a one-block select kernel then
-// picks the digit that contains the remaining rank.
+// with warp-aggregated shared-memory atomics (one per distinct digit of a
+// warp); a one-block select kernel then picks the digit that contains the
+// remaining rank.
 #include "internal.h"
 
 namespace mhfd {
@@ -62,6 +63,16 @@ struct RunAcc {
     }
 };
 
+// Adds this lane's digit to the shared histogram h when `ok`, with one
+// atomic per distinct digit of the warp (lanes holding equal digits are
+// grouped; image digits are highly repetitive, so this removes the
+// same-address atomic contention that bounds a per-pixel scheme).
+__device__ __forceinline__ void warp_add(unsigned mask, bool ok, unsigned digit, unsigned *h) {
+    const unsigned key = ok ? digit : 0x100u;
+    const unsigned peers = __match_any_sync(mask, key);
+    if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[digit], __popc(peers));
+}
+
 // Histogram accumulation of one pass over rows [y0, H) step ystep of one
 // image into the block's shared histograms h[2][256].
 template <int DT, int BITS>
@@ -81,22 +92,31 @@ __device__ __forceinline__ void hist_rows(const char *img, int H, int W, long lo
         if (first || hi == p0) r0.add(digit, h[0]);
         if (!first && hi == p1) r1.add(digit, h[1]);
     };
+    // all lanes of a warp that reach a full 16-byte chunk take this branch
+    // together; the ragged end of a row goes through the per-thread runs
+    auto take_warp = [&](unsigned mask, unsigned key) {
+        const unsigned digit = (key >> shift) & 0xffu;
+        const unsigned hi = first ? 0u : (key >> (shift + 8));
+        warp_add(mask, first || hi == p0, digit, h[0]);
+        if (!first) warp_add(mask, hi == p1, digit, h[1]);
+    };
     for (int y = y0; y < H; y += ystep) {
         const char *row = img + (long long)y * pitch;
         for (int x0 = threadIdx.x * VEC; x0 < W; x0 += blockDim.x * VEC) {
             if (vec_ok && x0 + VEC <= W) {
+                const unsigned mask = __activemask();
                 const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + (long long)x0 * ES));
                 const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     if (DT == 0) {
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) take((w[e] >> (8 * b)) & 0xffu);
+                        for (int b = 0; b < 4; ++b) take_warp(mask, (w[e] >> (8 * b)) & 0xffu);
                     } else if (DT == 1) {
-                        take(w[e] & 0xffffu);
-                        take(w[e] >> 16);
+                        take_warp(mask, w[e] & 0xffffu);
+                        take_warp(mask, w[e] >> 16);
                     } else {
-                        take(key_f32(__uint_as_float(w[e])));
+                        take_warp(mask, key_f32(__uint_as_float(w[e])));
                     }
                 }
             } else {

@@ -84,11 +84,12 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0):
     return out[:limit] if limit else out
 
 
-def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6), groups=(2, 3, 4)):
+def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), groups=(2, 3, 4, 5)):
     """Shapes off the menu's width grid (strip widths fitted to an image
-    width).  Thread counts: enough for every horizontal item, and enough for
-    every halo'd column of the vertical pass in one round (plus one warp);
-    keeps those that fit in shared memory."""
+    width).  Thread counts: at least one per horizontal item and one per
+    halo'd column of the vertical pass (a single round), that count plus one
+    warp, and rounded up to whole groups of four warps (the four schedulers
+    of an SM); keeps those that fit in shared memory."""
     from . import _native
     rmax = _rmax(n, t_min, t_max)
     out = []
@@ -96,9 +97,9 @@ def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6), groups=(
         ncol = -(-(tx2 + 2 * rmax) // 32) * 32
         for rb in rbs:
             hitems = rb * tx2 // 4
-            nth = -(-hitems // 32) * 32
-            for nt in sorted({max(nth, ncol), max(nth, ncol) + 32}):
-                if nt > 1024 or hitems > nt:
+            base = max(-(-hitems // 32) * 32, ncol)
+            for nt in sorted({base, base + 32, -(-base // 128) * 128}):
+                if nt > 1024:
                     continue
                 for ng in groups:
                     shape = (tx2, 18, rb, nt, ng)
@@ -161,13 +162,17 @@ def main():
     ap.add_argument("--limit", type=int, default=0)
     ap.add_argument("--min-width", type=int, default=0, help="skip strips narrower than this")
     ap.add_argument("--widths", default="", help="extra strip widths off the menu, e.g. 312,344")
+    ap.add_argument("--rbs", default="2,3,4,5,6,8", help="rows per step of the extra shapes")
+    ap.add_argument("--groups", default="2,3,4,5", help="level groups of the extra shapes")
     ap.add_argument("--write", action="store_true", help="record the winner in tuned_tiles.json")
     args = ap.parse_args()
     nms = 0 if args.nms == "paper" else 1
     cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None, args.min_width)
     if args.widths:
         extra = width_candidates(args.n, args.tmin, args.tmax, nms,
-                                 [int(w) for w in args.widths.split(",")])
+                                 [int(w) for w in args.widths.split(",")],
+                                 rbs=[int(v) for v in args.rbs.split(",")],
+                                 groups=[int(v) for v in args.groups.split(",")])
         cands += [c for c in extra if c not in cands]
     t0 = time.time()
     comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands)

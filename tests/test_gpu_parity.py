@@ -262,6 +262,29 @@ def test_host_entry_point_matches_device_entry_point():
     assert np.array_equal(r_dev.blobs, r_host.blobs)
 
 
+def test_async_host_entry_point_on_several_streams():
+    """Enqueued host detections on separate detectors and streams (copies
+    overlapping other detections) give the results of the blocking call."""
+    import paper_2108_12050_gb300 as mhfd
+    imgs = [scene(90 + k, 300, 260, "u16", sigma_d=float(k)) for k in range(3)]
+    pinned = []
+    for im in imgs:
+        t = torch.empty(im.shape, dtype=torch.int16, pin_memory=True)
+        t.numpy()[:] = im.view(np.int16)
+        pinned.append(t.numpy().view(np.uint16))
+    dets = [mhfd.Detector(n=6, t_min=1.0, t_max=5.0, threshold=0.05) for _ in imgs]
+    want = [d.detect_host(im) for d, im in zip(dets, imgs)]
+    streams = [torch.cuda.Stream() for _ in imgs]
+    for _ in range(2):
+        for d, im, st in zip(dets, pinned, streams):
+            assert d.detect_host(im, st, wait=False) is None
+        for d, w in zip(dets, want):
+            r = d.wait()
+            assert r.n_blobs == w.n_blobs and np.array_equal(r.blobs, w.blobs)
+    for d in dets:
+        d.close()
+
+
 # -------------------------------------------------------------------- prune
 
 @pytest.mark.parametrize("seed,n,cluster,overlap", [(0, 3000, 0.0, 0.5), (1, 4000, 0.9, 0.5),
