@@ -2,10 +2,11 @@
 // smallest pixel values found exactly by an MSD radix select over 8-bit
 // digits (1 pass for uint8, 2 for uint16, 4 for float32 keys), entirely on
 // the stream (no host round trip).  Each pass builds, per target, the digit
-// histogram of the pixels whose higher digits match the target's prefix,
-// with warp-aggregated shared-memory atomics (one per distinct digit of a
-// warp); a one-block select kernel then picks the digit that contains the
-// remaining rank.
+// histogram of the pixels whose higher digits match the target's prefix in
+// shared memory (runs of equal digits counted in registers first; the
+// histogram replicated per lane group so that the few hot digits of an image
+// do not serialise the block's atomics); a one-block select kernel then
+// picks the digit that contains the remaining rank.
 #include "internal.h"
 
 namespace mhfd {
@@ -46,6 +47,14 @@ __device__ __forceinline__ unsigned load_key(const char *row, int x) {
 // load when the image is 16-byte aligned) and aggregates runs of equal
 // digits in registers before adding them to the block's shared histograms,
 // which are merged into the global histograms at the end.
+// shared histograms of one block: [target][replica][digit], a replica per
+// group of lanes (lane % kRep), rows padded to spread the replicas' banks
+constexpr int kRep = 8;
+constexpr int kRow = 257;
+struct HistSmem {
+    unsigned v[2][kRep][kRow];
+};
+
 struct RunAcc {
     unsigned cur = 0xffffffffu, n = 0;
     __device__ __forceinline__ void add(unsigned d, unsigned *h) {
@@ -63,22 +72,13 @@ struct RunAcc {
     }
 };
 
-// Adds this lane's digit to the shared histogram h when `ok`, with one
-// atomic per distinct digit of the warp (lanes holding equal digits are
-// grouped; image digits are highly repetitive, so this removes the
-// same-address atomic contention that bounds a per-pixel scheme).
-__device__ __forceinline__ void warp_add(unsigned mask, bool ok, unsigned digit, unsigned *h) {
-    const unsigned key = ok ? digit : 0x100u;
-    const unsigned peers = __match_any_sync(mask, key);
-    if (ok && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[digit], __popc(peers));
-}
-
 // Histogram accumulation of one pass over rows [y0, H) step ystep of one
-// image into the block's shared histograms h[2][256].
+// image into the block's shared histograms.
 template <int DT, int BITS>
 __device__ __forceinline__ void hist_rows(const char *img, int H, int W, long long pitch,
                                           int pass, const SelState *sel, int y0, int ystep,
-                                          unsigned (*h)[256]) {
+                                          HistSmem *hs) {
+    unsigned *h[2] = {hs->v[0][threadIdx.x % kRep], hs->v[1][threadIdx.x % kRep]};
     constexpr int ES = DT == 0 ? 1 : (DT == 1 ? 2 : 4);
     constexpr int VEC = 16 / ES;
     const int shift = BITS - 8 * (pass + 1);
@@ -92,31 +92,22 @@ __device__ __forceinline__ void hist_rows(const char *img, int H, int W, long lo
         if (first || hi == p0) r0.add(digit, h[0]);
         if (!first && hi == p1) r1.add(digit, h[1]);
     };
-    // all lanes of a warp that reach a full 16-byte chunk take this branch
-    // together; the ragged end of a row goes through the per-thread runs
-    auto take_warp = [&](unsigned mask, unsigned key) {
-        const unsigned digit = (key >> shift) & 0xffu;
-        const unsigned hi = first ? 0u : (key >> (shift + 8));
-        warp_add(mask, first || hi == p0, digit, h[0]);
-        if (!first) warp_add(mask, hi == p1, digit, h[1]);
-    };
     for (int y = y0; y < H; y += ystep) {
         const char *row = img + (long long)y * pitch;
         for (int x0 = threadIdx.x * VEC; x0 < W; x0 += blockDim.x * VEC) {
             if (vec_ok && x0 + VEC <= W) {
-                const unsigned mask = __activemask();
                 const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + (long long)x0 * ES));
                 const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     if (DT == 0) {
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) take_warp(mask, (w[e] >> (8 * b)) & 0xffu);
+                        for (int b = 0; b < 4; ++b) take((w[e] >> (8 * b)) & 0xffu);
                     } else if (DT == 1) {
-                        take_warp(mask, w[e] & 0xffffu);
-                        take_warp(mask, w[e] >> 16);
+                        take(w[e] & 0xffffu);
+                        take(w[e] >> 16);
                     } else {
-                        take_warp(mask, key_f32(__uint_as_float(w[e])));
+                        take(key_f32(__uint_as_float(w[e])));
                     }
                 }
             } else {
@@ -128,22 +119,29 @@ __device__ __forceinline__ void hist_rows(const char *img, int H, int W, long lo
     r1.flush(h[1]);
 }
 
-__device__ __forceinline__ void hist_flush(unsigned (*h)[256], SelState *sel) {
+__device__ __forceinline__ void hist_clear(HistSmem *hs) {
+    for (int i = threadIdx.x; i < 2 * kRep * kRow; i += blockDim.x) (&hs->v[0][0][0])[i] = 0;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void hist_flush(HistSmem *hs, SelState *sel) {
     __syncthreads();
     for (int i = threadIdx.x; i < 512; i += blockDim.x) {
-        const unsigned v = (&h[0][0])[i];
-        if (v) atomicAdd(&(&sel->hist[0][0])[i], v);
+        const int g = i >> 8, d = i & 255;
+        unsigned v = 0;
+#pragma unroll
+        for (int r = 0; r < kRep; ++r) v += hs->v[g][r][d];
+        if (v) atomicAdd(&sel->hist[g][d], v);
     }
 }
 
 template <int DT, int BITS>
 __global__ void __launch_bounds__(256) sel_hist(const char *img, int H, int W, long long pitch,
                                                 int pass, SelState *sel) {
-    __shared__ unsigned h[2][256];
-    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
-    hist_rows<DT, BITS>(img, H, W, pitch, pass, sel, blockIdx.x, gridDim.x, h);
-    hist_flush(h, sel);
+    __shared__ HistSmem hs;
+    hist_clear(&hs);
+    hist_rows<DT, BITS>(img, H, W, pitch, pass, sel, blockIdx.x, gridDim.x, &hs);
+    hist_flush(&hs, sel);
 }
 
 // Pick the digit holding each target's remaining rank; after the last pass
@@ -227,20 +225,19 @@ __global__ void bsel_init(const MhfdJob *jobs, SelState *sels, const long long *
 }
 
 __global__ void __launch_bounds__(256) bsel_hist(const MhfdJob *jobs, SelState *sels, int pass) {
-    __shared__ unsigned h[2][256];
+    __shared__ HistSmem hs;
     const MhfdJob job = jobs[blockIdx.y];
     if (pass >= passes_of(job.dtype) || (int)blockIdx.x >= job.H) return;
-    for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
-    __syncthreads();
+    hist_clear(&hs);
     SelState *sel = sels + blockIdx.y;
     const char *img = reinterpret_cast<const char *>(job.img);
     if (job.dtype == 0)
-        hist_rows<0, 8>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, h);
+        hist_rows<0, 8>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, &hs);
     else if (job.dtype == 1)
-        hist_rows<1, 16>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, h);
+        hist_rows<1, 16>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, &hs);
     else
-        hist_rows<2, 32>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, h);
-    hist_flush(h, sel);
+        hist_rows<2, 32>(img, job.H, job.W, job.pitch, pass, sel, blockIdx.x, gridDim.x, &hs);
+    hist_flush(&hs, sel);
 }
 
 __global__ void bsel_pick(const MhfdJob *jobs, SelState *sels, MhfdStretch *sts, int pass) {
