@@ -265,7 +265,6 @@ def main():
                 dets[j].detect(t, streams[j])
             for j in range(len(tiles)):
                 scores[j] = dets[j].wait().focus_score
-                kernel_ms.append(dets[j].last_timing()[0])
                 join = torch.cuda.Event()
                 join.record(streams[j])
                 stream.wait_event(join)
@@ -277,8 +276,11 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
 
-    # ---- latency per tile: the same detections one after another on one
-    # stream, CUDA events around each (K x 5 samples)
+    # ---- latency per tile and the fused kernel's own duration: the same
+    # detections one after another on one stream, CUDA events around each
+    # (K x 5 samples) and the library's events around the fused kernel (with
+    # concurrent streams an event pair would also time the queueing behind
+    # the other streams' kernels)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(tiles) + 1)]
           for _ in range(args.steps)]
     for k in range(args.steps):
@@ -288,6 +290,7 @@ def main():
             ev[k][j + 1].record(stream)
         for j in range(len(tiles)):
             dets[j].wait()
+            kernel_ms.append(dets[j].last_timing()[0])
     torch.cuda.synchronize()
     per_tile = [ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(args.steps)
                 for j in range(len(tiles))]
@@ -311,7 +314,9 @@ def main():
             "peak_note": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal; no FP32 figure in "
                          "MEASURED_PEAKS)", "probe_measured_peak": probe,
             "frac_of_probe": achieved / probe, "ops_per_px": algorithmic_ops_per_px(),
-            "kernel_ms_avg": k_avg}
+            "kernel_ms_avg": k_avg,
+            "kernel_timing": "CUDA events on the launching stream around each fused launch, "
+                             "%d launches of the single-stream latency loop" % len(kernel_ms)}
 
     # ---- plain (unfused) path on the same tiles
     plain = None
