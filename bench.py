@@ -154,7 +154,7 @@ def run_reference(args, rank, world):
     oracle.build()
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
-    img = synth.config2_tile(0.0)
+    img = synth.sweep_tile_4096_u16(0.0)
     side = int(os.environ.get("MHFD_REF_SIDE", "1024"))
     crops = [np.ascontiguousarray(img[y:y + side, x:x + side])
              for y in range(0, H, side) for x in range(0, W, side)]
@@ -224,7 +224,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # inputs: the sweep tiles, resident in HBM (uint16 bits held as int16)
-    host = [synth.config2_tile(sd) for sd in SIGMA_D]
+    host = [synth.sweep_tile_4096_u16(sd) for sd in SIGMA_D]
     tiles = [torch.from_numpy(h.view(np.int16)).cuda() for h in host]
     stream = torch.cuda.current_stream()
     # one detector per tile of the step, so that the five detections of a
@@ -400,7 +400,7 @@ def bench_soft(mhfd, torch, stream, count=16):
     import synth
     from paper_2108_12050_gb300 import soft
     t0 = time.perf_counter()
-    pairs = [synth.config4_tile(j) for j in range(count)]
+    pairs = [synth.soft_tile_f32(j) for j in range(count)]
     render_s = time.perf_counter() - t0
     imgs = [torch.from_numpy(p[0]).cuda() for p in pairs]
     sds = [p[1] for p in pairs]
@@ -449,11 +449,11 @@ def bench_batch(mhfd, torch, stream, count=256):
     persistent fused launch replayed from a CUDA graph; baselines are 256
     separate plain (unfused) launches and 256 separate fused launches."""
     import synth
-    specs = synth.config3_specs(count)
+    specs = synth.uneven_batch_specs(count)
     uniq = {}
     for seed, H, W, dt, sd in specs:
         if (H, W, dt) not in uniq:
-            uniq[(H, W, dt)] = synth.config3_tile(seed, H, W, dt, sd)
+            uniq[(H, W, dt)] = synth.uneven_batch_tile(seed, H, W, dt, sd)
     dev = {k: torch.from_numpy(v.view(np.int16) if v.dtype == np.uint16 else v).cuda()
            for k, v in uniq.items()}
     tiles = [dev[(H, W, dt)] for _, H, W, dt, _ in specs]
@@ -518,7 +518,7 @@ def _serve_tiles(torch):
     kinds = []
     sds = (0.0, 2.0, 4.0, 8.0)
     for j, side in enumerate((1024, 2048, 4096, 8192)):
-        base = synth.config2_tile(sds[j])
+        base = synth.sweep_tile_4096_u16(sds[j])
         img16 = base[:side, :side] if side <= 4096 else np.tile(base, (2, 2))
         img8 = np.clip(np.rint(img16.astype(np.float32) * (255.0 / 4095.0)), 0, 255).astype(np.uint8)
         for img in (img8, np.ascontiguousarray(img16)):
@@ -603,7 +603,7 @@ def profile_case(args):
     import synth
     import paper_2108_12050_gb300 as mhfd
     torch.cuda.set_device(0)
-    img = synth.config2_tile(0.0)[:args.side, :args.side].copy()
+    img = synth.sweep_tile_4096_u16(0.0)[:args.side, :args.side].copy()
     dev = torch.from_numpy(img.view(np.int16)).cuda()
     det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP, nms="paper")
     for _ in range(args.profile_case):

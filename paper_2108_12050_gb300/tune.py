@@ -184,7 +184,7 @@ def main():
     import torch
     sys.path.insert(0, os.path.dirname(PKG))
     import synth
-    img = synth.config2_tile(0.0)[:args.side, :args.side].copy()
+    img = synth.sweep_tile_4096_u16(0.0)[:args.side, :args.side].copy()
     dev = torch.from_numpy(img.view(np.int16)).cuda()
     res = measure(args.n, args.tmin, args.tmax, nms, args.threshold, dev, cands)
     res.sort(key=lambda r: (r[1] is None, r[1] or 0))

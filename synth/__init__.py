@@ -33,8 +33,8 @@ import numpy as np
 from scipy.special import erf
 
 __all__ = [
-    "SceneSpec", "make_scene", "config1_pair", "config2_tile", "config3_tile",
-    "config3_specs", "config4_tile", "random_candidates",
+    "SceneSpec", "make_scene", "pair512_u8", "sweep_tile_4096_u16", "uneven_batch_tile",
+    "uneven_batch_specs", "soft_tile_f32", "random_candidates",
 ]
 
 _SQRT2 = math.sqrt(2.0)
@@ -179,20 +179,20 @@ def make_scene(seed: int, spec: SceneSpec, *, return_truth: bool = False,
 # the five workloads (seeds, sizes and value distributions)
 # ----------------------------------------------------------------------------
 
-def config1_spec(sigma_d=0.0, H=512, W=512):
+def scene512_u8_spec(sigma_d=0.0, H=512, W=512):
     return SceneSpec(H=H, W=W, bg=128.0, noise_std=8.0, n_blobs=200, r_range=(2.0, 8.0),
                      amp=-60.0, n_lines=20, line_w=(3, 3), dtype="u8", vmax=255.0,
                      sigma_d=sigma_d)
 
 
-def config1_pair(seed=1, H=512, W=512, return_truth=False):
+def pair512_u8(seed=1, H=512, W=512, return_truth=False):
     """512x512 uint8 in-focus image A and the same scene defocused (sigma_d=3) B."""
-    a = make_scene(seed, config1_spec(0.0, H, W), return_truth=return_truth)
-    b = make_scene(seed, config1_spec(3.0, H, W), return_truth=False)
+    a = make_scene(seed, scene512_u8_spec(0.0, H, W), return_truth=return_truth)
+    b = make_scene(seed, scene512_u8_spec(3.0, H, W), return_truth=False)
     return a, b
 
 
-def config2_spec(sigma_d=0.0, H=4096, W=4096, dtype="u16"):
+def scene12bit_spec(sigma_d=0.0, H=4096, W=4096, dtype="u16"):
     scale = (H * W) / float(4096 * 4096)
     n_blobs = int(round(20000 * scale))
     n_lines = int(round(300 * scale))
@@ -229,42 +229,42 @@ def _cached(tag, fn):
     return img
 
 
-def config2_tile(sigma_d=0.0, seed=2, H=4096, W=4096, dtype="u16", cache=True):
+def sweep_tile_4096_u16(sigma_d=0.0, seed=2, H=4096, W=4096, dtype="u16", cache=True):
     """4096x4096 12-bit tile (uint16), mean 2000, noise 80, 20k blobs, 300 lines."""
-    spec = config2_spec(sigma_d, H, W, dtype)
+    spec = scene12bit_spec(sigma_d, H, W, dtype)
     if not cache:
         return make_scene(seed, spec)
     tag = "c2_s%d_%dx%d_%s_sd%g" % (seed, H, W, dtype, sigma_d)
     return _cached(tag, lambda: make_scene(seed, spec))
 
 
-_C3_SIZES = ((1024, 1024), (1536, 2048), (3072, 3072), (4096, 4096))
+_UNEVEN_SIZES = ((1024, 1024), (1536, 2048), (3072, 3072), (4096, 4096))
 
 
-def config3_specs(count=256, base_seed=3000):
+def uneven_batch_specs(count=256, base_seed=3000):
     """Per-tile (seed, H, W, dtype, sigma_d) of the uneven batch."""
     out = []
     for j in range(count):
         rng = np.random.default_rng([base_seed + j, 7])
-        H, W = _C3_SIZES[int(rng.integers(0, len(_C3_SIZES)))]
+        H, W = _UNEVEN_SIZES[int(rng.integers(0, len(_UNEVEN_SIZES)))]
         dtype = "u8" if rng.integers(0, 2) == 0 else "u16"
         sd = float(rng.uniform(0.0, 6.0))
         out.append((base_seed + j, H, W, dtype, sd))
     return out
 
 
-def config3_tile(seed, H, W, dtype, sigma_d):
-    base = config2_spec(sigma_d, H, W, dtype)
+def uneven_batch_tile(seed, H, W, dtype, sigma_d):
+    base = scene12bit_spec(sigma_d, H, W, dtype)
     n_blobs = int(round(1.2e-3 * H * W))
     spec = dataclasses.replace(base, n_blobs=n_blobs)
     return make_scene(seed, spec)
 
 
-def config4_tile(j, H=2048, W=2048, base_seed=4000):
-    """2048x2048 float32 tile of the config-2 scene (not quantised), known sigma_d."""
+def soft_tile_f32(j, H=2048, W=2048, base_seed=4000):
+    """2048x2048 float32 tile of the 12-bit scene (not quantised), known sigma_d."""
     rng = np.random.default_rng([base_seed + j, 9])
     sd = float(rng.uniform(0.0, 8.0))
-    spec = config2_spec(sd, H, W, "f32")
+    spec = scene12bit_spec(sd, H, W, "f32")
     return make_scene(base_seed + j, spec), sd
 
 

@@ -27,12 +27,12 @@ def cases():
 
 
 def main():
-    out = {"source": "FP64 oracle on synth.config1 scenes (seed, H, W given); "
+    out = {"source": "FP64 oracle on synth 512x512-style uint8 scenes (seed, H, W given); "
                      "ladder per §2.2, DoG per Eq. 2, NMS per Eq. 3",
            "cases": []}
     for name, seed, H, W, n, tmin, tmax, thr, ov, mode in cases():
         sd = 2.0 if "defocus" in name else 0.0
-        img = synth.make_scene(seed, synth.config1_spec(sd, H, W))
+        img = synth.make_scene(seed, synth.scene512_u8_spec(sd, H, W))
         r = oracle.detect(img, n, tmin, tmax, threshold=thr, overlap=ov, mode=mode)
         out["cases"].append(dict(
             name=name, seed=seed, H=H, W=W, sigma_d=sd, n=n, tmin=tmin, tmax=tmax,

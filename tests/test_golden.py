@@ -22,7 +22,7 @@ def _cases():
 
 @pytest.mark.parametrize("case", _cases(), ids=lambda c: c["name"])
 def test_oracle_matches_golden(case, oracle_mod):
-    img = synth.make_scene(case["seed"], synth.config1_spec(case["sigma_d"], case["H"], case["W"]))
+    img = synth.make_scene(case["seed"], synth.scene512_u8_spec(case["sigma_d"], case["H"], case["W"]))
     r = oracle.detect(img, case["n"], case["tmin"], case["tmax"], threshold=case["threshold"],
                       overlap=case["overlap"], mode=case["mode"])
     assert (r.lo, r.hi) == (case["lo"], case["hi"])

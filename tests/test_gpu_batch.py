@@ -23,7 +23,7 @@ def _batch_images():
     imgs = []
     for j, (H, W, dt) in enumerate([(300, 410, "u16"), (256, 256, "u8"), (517, 130, "u16"),
                                     (64, 900, "u8"), (401, 333, "u16"), (97, 97, "f32")]):
-        imgs.append(synth.make_scene(700 + j, synth.config2_spec(1.0 + j, H, W, dt)))
+        imgs.append(synth.make_scene(700 + j, synth.scene12bit_spec(1.0 + j, H, W, dt)))
     return imgs
 
 

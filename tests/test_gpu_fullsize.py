@@ -40,7 +40,7 @@ def _cuda():
 @pytest.fixture(scope="module")
 def full():
     import paper_2108_12050_gb300 as mhfd
-    img = synth.config2_tile(0.0)
+    img = synth.sweep_tile_4096_u16(0.0)
     dev = torch.from_numpy(img.view(np.int16)).cuda()
     det = mhfd.Detector(N, TMIN, TMAX, threshold=THR, overlap=OVERLAP, keep_candidates=True)
     res = det(dev)
@@ -137,7 +137,7 @@ def test_full_size_prune_and_score(full):
 def test_soft_score_full_size_2048_float32():
     import paper_2108_12050_gb300 as mhfd
     from paper_2108_12050_gb300 import soft
-    img, _ = synth.config4_tile(0)
+    img, _ = synth.soft_tile_f32(0)
     det = mhfd.Detector(N, TMIN, TMAX, threshold=THR)
     w = np.linspace(-0.5, 1.5, N)
     S, ms, _, _ = soft.soft_score(det, torch.from_numpy(img).cuda(),

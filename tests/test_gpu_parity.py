@@ -45,8 +45,8 @@ def to_dev(img):
 
 def scene(seed, H, W, dtype="u8", sigma_d=0.0):
     if dtype == "u8":
-        return synth.make_scene(seed, synth.config1_spec(sigma_d, H, W))
-    return synth.make_scene(seed, synth.config2_spec(sigma_d, H, W, dtype))
+        return synth.make_scene(seed, synth.scene512_u8_spec(sigma_d, H, W))
+    return synth.make_scene(seed, synth.scene12bit_spec(sigma_d, H, W, dtype))
 
 
 def ref_stack(img, n, tmin, tmax):
@@ -203,14 +203,14 @@ def _check_detection(img, n, tmin, tmax, thr, overlap, nms, response="dog",
 
 
 @pytest.mark.parametrize("which", ["A", "B"])
-def test_config1_512_uint8_end_to_end(which):
-    a, b = synth.config1_pair(seed=1)
+def test_pair_512_uint8_end_to_end(which):
+    a, b = synth.pair512_u8(seed=1)
     img = a if which == "A" else b
     _check_detection(img, 10, 1.0, 10.0, 0.1, 0.5, "paper")
 
 
-def test_config1_local26_end_to_end():
-    a, _ = synth.config1_pair(seed=1, H=256, W=300)
+def test_pair_512_uint8_local26_end_to_end():
+    a, _ = synth.pair512_u8(seed=1, H=256, W=300)
     _check_detection(a, 10, 1.0, 10.0, 0.1, 0.5, "local26")
 
 
@@ -224,7 +224,7 @@ def test_small_ladder_end_to_end(shape, dtype):
 
 @pytest.mark.parametrize("overlap", [0.0, 0.3, 1.0])
 def test_prune_overlap_settings(overlap):
-    a, _ = synth.config1_pair(seed=2, H=200, W=200)
+    a, _ = synth.pair512_u8(seed=2, H=200, W=200)
     _check_detection(a, 10, 1.0, 10.0, 0.1, overlap, "paper")
 
 
@@ -237,7 +237,7 @@ def test_constant_image_has_no_features():
 
 
 def test_overflow_reports_true_count():
-    a, _ = synth.config1_pair(seed=1)
+    a, _ = synth.pair512_u8(seed=1)
     full = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1)(to_dev(a))
     small = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1, max_candidates=100)
     res = small(to_dev(a))
@@ -255,7 +255,7 @@ def test_results_are_deterministic():
 
 
 def test_host_entry_point_matches_device_entry_point():
-    a, _ = synth.config1_pair(seed=3, H=200, W=180)
+    a, _ = synth.pair512_u8(seed=3, H=200, W=180)
     det = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1)
     r_dev = det(to_dev(a))
     r_host = det.detect_host(a)
@@ -306,7 +306,7 @@ def test_prune_bit_exact_on_identical_inputs(seed, n, cluster, overlap):
 # -------------------------------------------------------------- plain path
 
 def test_plain_path_matches_oracle():
-    a, _ = synth.config1_pair(seed=4, H=260, W=300)
+    a, _ = synth.pair512_u8(seed=4, H=260, W=300)
     det = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1, keep_candidates=True)
     det.detect_plain(to_dev(a))
     res = det.wait()
@@ -327,7 +327,7 @@ def test_plain_path_matches_oracle():
     ("dog", "reflect", "paper"), ("log", "reflect", "paper"), ("dog", "periodic", "paper"),
     ("log", "periodic", "paper"), ("log", "reflect", "local26"), ("dog", "periodic", "local26")])
 def test_variants_match_oracle(response, boundary, nms):
-    a, _ = synth.config1_pair(seed=6, H=200, W=270)
+    a, _ = synth.pair512_u8(seed=6, H=200, W=270)
     # the LoG response lacks the DoG's factor dt (0.9 here): threshold scaled
     thr = 0.1 / 0.9 if response == "log" else 0.1
     _check_detection(a, 10, 1.0, 10.0, thr, 0.5, nms, response=response, boundary=boundary,
@@ -360,7 +360,7 @@ def test_periodic_plain_commutes_with_circular_shift():
 
 def test_fused_entry_points_reject_variants():
     import paper_2108_12050_gb300 as mhfd
-    a, _ = synth.config1_pair(seed=6, H=64, W=64)
+    a, _ = synth.pair512_u8(seed=6, H=64, W=64)
     for kw in ({"response": "log"}, {"boundary": "periodic"}):
         det = detector(n=4, t_min=1.0, t_max=4.0, threshold=0.1, **kw)
         with pytest.raises(mhfd.MhfdError) as e:

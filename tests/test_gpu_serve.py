@@ -17,7 +17,7 @@ def _tiles():
     for j, (H, W, dt) in enumerate([(512, 512, "u16"), (300, 700, "u8"), (1024, 256, "u16"),
                                     (256, 256, "u8"), (640, 480, "f32"), (128, 900, "u16"),
                                     (700, 300, "u8"), (512, 384, "u16")]):
-        out.append(synth.make_scene(900 + j, synth.config2_spec(0.5 * j, H, W, dt)))
+        out.append(synth.make_scene(900 + j, synth.scene12bit_spec(0.5 * j, H, W, dt)))
     return out
 
 

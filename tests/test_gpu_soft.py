@@ -20,7 +20,7 @@ def _cuda():
 
 
 def _f32_tile(j, H, W):
-    img, sd = synth.config4_tile(j, H=H, W=W)
+    img, sd = synth.soft_tile_f32(j, H=H, W=W)
     return img, sd
 
 

@@ -184,7 +184,7 @@ def test_reflect_blur_equals_2d_direct_sum(shape):
 
 
 def test_dog_at_matches_separable_stack():
-    img = synth.config1_pair(seed=3, H=64, W=72)[0]
+    img = synth.pair512_u8(seed=3, H=64, W=72)[0]
     lo, hi = oracle.stretch_bounds(img)
     t = oracle.ladder(10, 1.0, 10.0)
     D = oracle.dog_stack(oracle.stretch(img, lo, hi), t)
@@ -405,7 +405,7 @@ def test_noise_free_blob_recovery():
 
 
 def test_defocus_lowers_the_feature_count():
-    a, b = synth.config1_pair(seed=1, H=256, W=256)
+    a, b = synth.pair512_u8(seed=1, H=256, W=256)
     ra = oracle.detect(a, 10, 1.0, 10.0, threshold=0.1, overlap=0.5)
     rb = oracle.detect(b, 10, 1.0, 10.0, threshold=0.1, overlap=0.5)
     assert rb.score < ra.score
@@ -444,7 +444,7 @@ def test_periodic_detection_commutes_with_circular_shift():
     # the blur wraps around; the 3x3 max-pool of Eq. 3 pads with -inf and
     # does not, so features on the outermost pixel ring are excluded
     H, W, dy, dx = 96, 128, 17, -30
-    img = synth.config1_pair(seed=5, H=H, W=W)[0]
+    img = synth.pair512_u8(seed=5, H=H, W=W)[0]
     r0 = oracle.detect(img, 4, 1.0, 4.0, threshold=0.1, overlap=1.0, boundary=oracle.PERIODIC)
     sh = np.roll(img, (dy, dx), axis=(0, 1))
     r1 = oracle.detect(sh, 4, 1.0, 4.0, threshold=0.1, overlap=1.0, boundary=oracle.PERIODIC)

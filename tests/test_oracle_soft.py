@@ -28,7 +28,7 @@ def test_blur_adjoint_dot_product(shape, t):
 
 
 def _crop():
-    img, _ = synth.config4_tile(0, H=256, W=256)
+    img, _ = synth.soft_tile_f32(0, H=256, W=256)
     return np.ascontiguousarray(img[40:104, 80:144])
 
 
