@@ -145,6 +145,30 @@ def cpu_baseline(img, side=2048, side1=1024):
                             "sample": "%dx%d crop, %.1f s" % (side1, side1, dt1)}}
 
 
+def rank_seed(rank):
+    """Scene seed of a replica's inputs: rank 0 renders the benchmark scene
+    (seed 2); other ranks render their own scenes, so replicas work on
+    disjoint inputs of the same statistics."""
+    return 2 + 1000 * int(rank)
+
+
+def max_over_ranks(ms, dist, device):
+    """Largest value of `ms` over all ranks (the slowest replica sets the
+    job's time); identity without a process group."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(px_per_rank_step, steps, world, total_ms):
+    """Whole-job throughput in Mpixel/s: the pixels all replicas processed
+    over the slowest replica's time."""
+    return world * steps * px_per_rank_step / (total_ms * 1e-3) / 1e6
+
+
 def run_reference(args, rank, world):
     """The oracle timed as the reference arm (rank 0 only)."""
     if rank != 0:
@@ -224,7 +248,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # inputs: the sweep tiles, resident in HBM (uint16 bits held as int16)
-    host = [synth.sweep_tile_4096_u16(sd) for sd in SIGMA_D]
+    host = [synth.sweep_tile_4096_u16(sd, seed=rank_seed(rank)) for sd in SIGMA_D]
     tiles = [torch.from_numpy(h.view(np.int16)).cuda() for h in host]
     stream = torch.cuda.current_stream()
     # one detector per tile of the step, so that the five detections of a
@@ -270,11 +294,7 @@ def main():
                 stream.wait_event(join)
         t_end.record(stream)
         barrier()
-    total_ms = t_start.elapsed_time(t_end)
-    if dist is not None:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dist, "cuda")
 
     # ---- latency per tile and the fused kernel's own duration: the same
     # detections one after another on one stream, CUDA events around each
@@ -295,7 +315,7 @@ def main():
     per_tile = [ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(args.steps)
                 for j in range(len(tiles))]
     px_step = len(tiles) * H * W
-    value = world * args.steps * px_step / (total_ms * 1e-3) / 1e6
+    value = whole_job_value(px_step, args.steps, world, total_ms)
 
     if rank != 0:
         if dist is not None:
