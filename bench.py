@@ -382,6 +382,8 @@ def main():
 
     cpu = None if args.no_cpu_baseline else cpu_baseline(host[0])
     batched = None if args.no_batch else bench_batch(mhfd, torch, stream)
+    sweep_batched = None if args.no_batch else bench_sweep_batch(mhfd, torch, stream, tiles,
+                                                                  args.steps)
     serving = None if args.no_serve else bench_serve(mhfd, torch)
     soft_sec = None if args.no_soft else bench_soft(mhfd, torch, stream, args.soft_tiles)
 
@@ -402,6 +404,7 @@ def main():
         "gpu_launches": launches_per_tile * len(tiles) * args.steps,
         "clocks": clk.summary(),
         "batched": batched,
+        "sweep_batched": sweep_batched,
         "serving": serving,
         "soft": soft_sec,
         "focus_scores": dict(zip([str(s) for s in SIGMA_D], scores)),
@@ -458,6 +461,32 @@ def bench_soft(mhfd, torch, stream, count=16):
                     "mse_first": losses[0], "mse_last": losses[-1],
                     "target_var": float(np.var(sds))},
             "render_s": render_s}
+
+
+def bench_sweep_batch(mhfd, torch, stream, tiles, steps):
+    """The benchmark's 5-tile step as one batch (batched stretch select, one
+    persistent fused launch over the five tiles, per-image post, replayed
+    from a CUDA graph), K steps, CUDA events on the launching stream."""
+    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP, nms="paper")
+    for _ in range(3):
+        det.detect_batch(tiles, stream)
+        outs = det.wait_batch()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        det.detect_batch(tiles, stream)
+        outs = det.wait_batch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    px = sum(t.numel() for t in tiles) * steps
+    graph = det.batch_uses_graph()
+    scores = [o.focus_score for o in outs]
+    det.close()
+    return {"value": px / (ms * 1e-3) / 1e6, "unit": METRIC, "ms_per_step": ms / steps,
+            "graph": graph, "focus_scores": scores}
 
 
 def bench_batch(mhfd, torch, stream, count=256):
