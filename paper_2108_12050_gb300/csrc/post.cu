@@ -67,26 +67,32 @@ __device__ __forceinline__ long long block_scan_incl(long long v, long long *sh,
     return ex + v;
 }
 
+// One block: each thread scans a contiguous chunk of tiles serially, one
+// block-wide scan joins the chunks.
 __global__ void __launch_bounds__(kScanThreads)
     gather_scan(const int *tile_count, int n_tiles, int cap_tile, long long cap, int *tile_off,
                 Counters *cnt) {
     __shared__ long long sh[32];
-    long long carry_s = 0, carry_t = 0;
-    for (int base = 0; base < n_tiles; base += blockDim.x) {
-        const int t = base + threadIdx.x;
-        const int c = t < n_tiles ? tile_count[t] : 0;
-        const long long st = c < cap_tile ? c : cap_tile;
-        long long tot_s, tot_t;
-        const long long inc = block_scan_incl(st, sh, &tot_s);
-        block_scan_incl((long long)c, sh, &tot_t);
-        if (t < n_tiles) tile_off[t] = (int)(carry_s + inc - st);
-        carry_s += tot_s;
-        carry_t += tot_t;
+    const int per = (n_tiles + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int beg = min(n_tiles, (int)threadIdx.x * per), end = min(n_tiles, beg + per);
+    long long loc_s = 0, loc_t = 0;
+    for (int t = beg; t < end; ++t) {
+        const int c = tile_count[t];
+        loc_s += c < cap_tile ? c : cap_tile;
+        loc_t += c;
+    }
+    long long tot_s, tot_t;
+    long long run = block_scan_excl_ll(loc_s, sh, &tot_s);
+    block_scan_excl_ll(loc_t, sh, &tot_t);
+    for (int t = beg; t < end; ++t) {
+        tile_off[t] = (int)run;
+        const int c = tile_count[t];
+        run += c < cap_tile ? c : cap_tile;
     }
     if (threadIdx.x == 0) {
-        cnt->n_true = (unsigned long long)carry_t;
-        cnt->n_stored = (unsigned long long)(carry_s < cap ? carry_s : cap);
-        cnt->overflow = (carry_t > (long long)cnt->n_stored) ? 1 : 0;
+        cnt->n_true = (unsigned long long)tot_t;
+        cnt->n_stored = (unsigned long long)(tot_s < cap ? tot_s : cap);
+        cnt->overflow = (tot_t > (long long)cnt->n_stored) ? 1 : 0;
         cnt->n_blobs = 0;
         cnt->timeout = 0;
         cnt->blob_base = 0;
@@ -116,22 +122,23 @@ __global__ void grid_count(const MhfdCand *cand, const Counters *cnt, int cs, in
     }
 }
 
+// Cell starts (exclusive scan of the counts) in one block, chunked like
+// gather_scan; the counts are reset to serve as fill cursors.
 __global__ void __launch_bounds__(kScanThreads)
     grid_scan(int *cell_cnt, int ncells, int *cell_start) {
     __shared__ long long sh[32];
-    long long carry = 0;
-    for (int base = 0; base < ncells; base += blockDim.x) {
-        const int c = base + threadIdx.x;
-        const long long v = c < ncells ? cell_cnt[c] : 0;
-        long long tot;
-        const long long inc = block_scan_incl(v, sh, &tot);
-        if (c < ncells) {
-            cell_start[c] = (int)(carry + inc - v);
-            cell_cnt[c] = 0;  // reused as the fill cursor
-        }
-        carry += tot;
+    const int per = (ncells + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int beg = min(ncells, (int)threadIdx.x * per), end = min(ncells, beg + per);
+    long long loc = 0;
+    for (int c = beg; c < end; ++c) loc += cell_cnt[c];
+    long long tot;
+    long long run = block_scan_excl_ll(loc, sh, &tot);
+    for (int c = beg; c < end; ++c) {
+        cell_start[c] = (int)run;
+        run += cell_cnt[c];
+        cell_cnt[c] = 0;  // reused as the fill cursor
     }
-    if (threadIdx.x == 0) cell_start[ncells] = (int)carry;
+    if (threadIdx.x == 0) cell_start[ncells] = (int)tot;
 }
 
 __global__ void grid_fill(const MhfdCand *cand, const Counters *cnt, int cs, int ncx,
@@ -186,32 +193,82 @@ __device__ __forceinline__ bool conflict_bit(const MhfdCand &b, const MhfdCand &
 // settle loop then rescans the cells instead.
 constexpr int kMaxNb = 16;
 
-__global__ void __launch_bounds__(256)
-    prune_neighbors(const MhfdCand *cand, const Counters *cnt, int cs, int ncx, int ncy,
-                    const int *cell_start, const int *items, ConflictTable ct, int W,
-                    int *nb_idx, int *nb_cnt, int *state) {
-    const long long n = (long long)cnt->n_stored;
-    for (long long jj = blockIdx.x * (long long)blockDim.x + threadIdx.x; jj < n;
-         jj += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)jj;
-        const MhfdCand a = cand[j];
-        const int cx = a.x / cs, cy = a.y / cs;
-        int found = 0;
-        for (int gy = max(0, cy - 1); gy <= min(ncy - 1, cy + 1); ++gy)
-            for (int gx = max(0, cx - 1); gx <= min(ncx - 1, cx + 1); ++gx) {
-                const int c = gy * ncx + gx;
-                for (int p = cell_start[c]; p < cell_start[c + 1]; ++p) {
+// One warp per grid cell: the candidates of the cell's 3x3 neighbourhood
+// are staged in shared memory once (index and record), then each lane takes
+// candidates of the centre cell and tests them against the staged list.  A
+// neighbourhood larger than the staging area falls back to reading the
+// records from global memory.
+constexpr int kCellWarps = 8;
+constexpr int kStage = 160;
+
+__device__ __forceinline__ void list_neighbors(int j, const MhfdCand &a, const MhfdCand *cand,
+                                               const int *items, int s0, int s1,
+                                               const ConflictTable &ct, int W, int *nb_idx,
+                                               int &found) {
+    for (int p = s0; p < s1; ++p) {
+        const int b = items[p];
+        if (b == j) continue;
+        const MhfdCand cb = cand[b];
+        if (!higher(cb, a, W)) continue;
+        if (!conflict_bit(cb, a, ct)) continue;
+        if (found < kMaxNb) nb_idx[(long long)j * kMaxNb + found] = b;
+        ++found;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kCellWarps)
+    prune_neighbors(const MhfdCand *cand, int cs, int ncx, int ncy, const int *cell_start,
+                    const int *items, ConflictTable ct, int W, int *nb_idx, int *nb_cnt,
+                    int *state) {
+    __shared__ MhfdCand s_c[kCellWarps][kStage];
+    __shared__ int s_i[kCellWarps][kStage];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncells = ncx * ncy;
+    for (int cell = blockIdx.x * kCellWarps + warp; cell < ncells;
+         cell += gridDim.x * kCellWarps) {
+        const int c0 = cell_start[cell], c1 = cell_start[cell + 1];
+        if (c0 == c1) continue;
+        const int cy = cell / ncx, cx = cell - cy * ncx;
+        const int y0 = max(0, cy - 1), y1 = min(ncy - 1, cy + 1);
+        const int x0 = max(0, cx - 1), x1 = min(ncx - 1, cx + 1);
+        int m = 0;
+        for (int gy = y0; gy <= y1; ++gy) {
+            // the three cells of a grid row are contiguous in `items`
+            const int s0 = cell_start[gy * ncx + x0], s1 = cell_start[gy * ncx + x1 + 1];
+            for (int p = s0 + lane; p < s1; p += 32) {
+                const int q = m + (p - s0);
+                if (q < kStage) {
                     const int b = items[p];
+                    s_i[warp][q] = b;
+                    s_c[warp][q] = cand[b];
+                }
+            }
+            m += s1 - s0;
+        }
+        __syncwarp();
+        for (int p = c0 + lane; p < c1; p += 32) {
+            const int j = items[p];
+            const MhfdCand a = cand[j];
+            int found = 0;
+            if (m <= kStage) {
+                for (int q = 0; q < m; ++q) {
+                    const int b = s_i[warp][q];
                     if (b == j) continue;
-                    const MhfdCand cb = cand[b];
+                    const MhfdCand cb = s_c[warp][q];
                     if (!higher(cb, a, W)) continue;
                     if (!conflict_bit(cb, a, ct)) continue;
                     if (found < kMaxNb) nb_idx[(long long)j * kMaxNb + found] = b;
                     ++found;
                 }
+            } else {
+                for (int gy = y0; gy <= y1; ++gy)
+                    list_neighbors(j, a, cand, items, cell_start[gy * ncx + x0],
+                                   cell_start[gy * ncx + x1 + 1], ct, W, nb_idx, found);
             }
-        nb_cnt[j] = found <= kMaxNb ? found : -1;
-        state[j] = found == 0 ? 1 : 0;
+            nb_cnt[j] = found <= kMaxNb ? found : -1;
+            state[j] = found == 0 ? 1 : 0;
+        }
+        __syncwarp();
     }
 }
 
@@ -546,9 +603,14 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
     grid_scan<<<1, kScanThreads, 0, s>>>(pb->cell_cnt, ncells, pb->cell_start);
     grid_fill<<<sms * 4, 256, 0, s>>>(cand, cnt, cs, ncx, pb->cell_start, pb->cell_cnt,
                                       pb->cell_items, pb->state);
-    prune_neighbors<<<sms * 8, 256, 0, s>>>(cand, cnt, cs, ncx, ncy, pb->cell_start,
-                                            pb->cell_items, ct, W, pb->nb_idx, pb->nb_cnt,
-                                            pb->state);
+    {
+        const int ncells_all = ncx * ncy;
+        int blocks = (ncells_all + kCellWarps - 1) / kCellWarps;
+        if (blocks > sms * 16) blocks = sms * 16;
+        prune_neighbors<<<blocks, 32 * kCellWarps, 0, s>>>(cand, cs, ncx, ncy, pb->cell_start,
+                                                           pb->cell_items, ct, W, pb->nb_idx,
+                                                           pb->nb_cnt, pb->state);
+    }
     MHFD_CUDA(cudaGetLastError());
     int per_sm = 0;
     MHFD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lfmis_kernel, 256, 0));
