@@ -122,23 +122,24 @@ __global__ void grid_count(const MhfdCand *cand, const Counters *cnt, int cs, in
     }
 }
 
-// Cell starts (exclusive scan of the counts) in one block, chunked like
-// gather_scan; the counts are reset to serve as fill cursors.
+// Cell starts (exclusive scan of the counts) in one block, a coalesced
+// pass of block scans; the counts are reset to serve as fill cursors.
 __global__ void __launch_bounds__(kScanThreads)
     grid_scan(int *cell_cnt, int ncells, int *cell_start) {
     __shared__ long long sh[32];
-    const int per = (ncells + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int beg = min(ncells, (int)threadIdx.x * per), end = min(ncells, beg + per);
-    long long loc = 0;
-    for (int c = beg; c < end; ++c) loc += cell_cnt[c];
-    long long tot;
-    long long run = block_scan_excl_ll(loc, sh, &tot);
-    for (int c = beg; c < end; ++c) {
-        cell_start[c] = (int)run;
-        run += cell_cnt[c];
-        cell_cnt[c] = 0;  // reused as the fill cursor
+    long long carry = 0;
+    for (int base = 0; base < ncells; base += blockDim.x) {
+        const int c = base + threadIdx.x;
+        const long long v = c < ncells ? cell_cnt[c] : 0;
+        long long tot;
+        const long long ex = block_scan_excl_ll(v, sh, &tot);
+        if (c < ncells) {
+            cell_start[c] = (int)(carry + ex);
+            cell_cnt[c] = 0;
+        }
+        carry += tot;
     }
-    if (threadIdx.x == 0) cell_start[ncells] = (int)tot;
+    if (threadIdx.x == 0) cell_start[ncells] = (int)carry;
 }
 
 __global__ void grid_fill(const MhfdCand *cand, const Counters *cnt, int cs, int ncx,
