@@ -90,8 +90,8 @@ typedef struct {
                                detection (read with mhfd_last_timing) */
     int32_t response;       /* mhfd_response; the fused entry points (detect,
                                batch, debug_stack, soft score) need DoG */
-    int32_t boundary;       /* mhfd_boundary; the fused entry points need
-                               reflect; mhfd_detect_plain supports all */
+    int32_t boundary;       /* mhfd_boundary; every entry point but the soft
+                               score (reflect only) supports both */
 } mhfd_params;
 
 /* A detected feature.  scale_idx is the 0-based DoG layer i-1; sigma = t_i,

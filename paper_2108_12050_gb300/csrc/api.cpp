@@ -336,10 +336,10 @@ int finish_pipeline(mhfd_detector *d, int n_tiles, int cap_tile, int H, int W, c
 }
 
 int fused_supported(const mhfd_detector *d) {
-    if (d->p.response != MHFD_RESPONSE_DOG || d->p.boundary != MHFD_BOUNDARY_REFLECT)
+    if (d->p.response != MHFD_RESPONSE_DOG)
         return fail(MHFD_ERR_UNSUPPORTED,
-                    "the fused kernel computes the DoG with the reflect boundary; use "
-                    "mhfd_detect_plain for the LoG response or the periodic boundary");
+                    "the fused kernel computes the DoG response; use mhfd_detect_plain for "
+                    "the LoG response");
     return MHFD_OK;
 }
 
@@ -622,6 +622,7 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
     d->lk.R = d->R;
     d->lk.taps = d->taps;
     d->lk.tsc = d->tsc;
+    d->lk.boundary = d->p.boundary;
     for (int i = 0; i < d->n; ++i) d->radius.push_back(std::sqrt(2.0) * d->t[i]);
     d->radius_max = d->radius[d->n - 1];
     if ((rc = resolve_tile(d->R, d->p, &d->cfg))) {
@@ -869,6 +870,7 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     if ((rc = build_ladder(*p, &t, &R))) return rc;
     LadderKey lk;
     lk.R = R;
+    lk.boundary = p->boundary;
     std::vector<int> tapoff;
     make_taps(t, R, &lk.taps, &tapoff, &lk.tsc);
     TileConfig cfg;
@@ -1050,6 +1052,8 @@ int mhfd_soft_score(mhfd_detector *d, const void *img, int32_t dtype, int32_t H,
     if (!(temperature > 0.0f) || !std::isfinite(tau))
         return fail(MHFD_ERR_INVALID_ARG, "temperature must be > 0 and tau finite");
     if (int rcs = fused_supported(d)) return rcs;
+    if (d->p.boundary != MHFD_BOUNDARY_REFLECT)
+        return fail(MHFD_ERR_UNSUPPORTED, "the soft score uses the reflect boundary");
     int rc = check_image(img, dtype, H, W, pitch);
     if (rc) return rc;
     DeviceGuard g(d->device);

@@ -10,8 +10,8 @@
 // of TY rows, the unit of candidate storage.  A CTA marches down a run of
 // consecutive tiles of one strip (a "chunk"), RB output rows per step:
 //   1. the input rows of the halo'd strip (RMAX+1 pixels of halo, reflect
-//      boundary "d c b a | a b c d | d c b a", histogram stretch of §3 applied
-//      on the fly) live in a sliding shared-memory window of BROWS rows; the
+//      boundary "d c b a | a b c d | d c b a" or periodic, histogram stretch
+//      of §3 applied on the fly) live in a sliding shared-memory window of BROWS rows; the
 //      RB rows the next step needs are fetched into registers at the start of
 //      a step and written after it (their latency hides behind the step), and
 //      every few steps the window is shifted back to the buffer's start;
@@ -154,12 +154,20 @@ struct HState {
     float soft[NSOFT];
 };
 
+// Image index of a position outside [0, n): reflect ("d c b a | a b c d |
+// d c b a", the default) or periodic (MHFD_BOUNDARY 1, the circular
+// convolution of the paper's Fourier formulation).
 __device__ __forceinline__ int reflect_idx(int i, int n) {
     if ((unsigned)i < (unsigned)n) return i;
-    const int p = 2 * n;
-    int m = i % p;
-    if (m < 0) m += p;
-    return m < n ? m : p - 1 - m;
+    if constexpr (MHFD_BOUNDARY == 1) {
+        const int m = i % n;
+        return m < 0 ? m + n : m;
+    } else {
+        const int p = 2 * n;
+        int m = i % p;
+        if (m < 0) m += p;
+        return m < n ? m : p - 1 - m;
+    }
 }
 
 // ---------------------------------------------------------------- 1. load

@@ -87,6 +87,7 @@ struct LadderKey {
     std::vector<int> R;
     std::vector<float> taps;
     std::vector<float> tsc;
+    int boundary = 0;  // mhfd_boundary of the blur
 };
 
 // Choose a tile configuration for the radii and mode (built-in heuristic).

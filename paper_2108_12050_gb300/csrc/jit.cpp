@@ -89,7 +89,8 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_RB " << c.rb << "\n"
       << "#define MHFD_NT " << c.nt << "\n"
       << "#define MHFD_MODE " << mode << "\n"
-      << "#define MHFD_STORE " << store << "\n";
+      << "#define MHFD_STORE " << store << "\n"
+      << "#define MHFD_BOUNDARY " << lk.boundary << "\n";
     return o.str() + kTypesSrc + kKernelSrc;
 }
 
