@@ -75,3 +75,14 @@ def test_score_is_linear_in_weights():
         S2, _, _ = oracle.soft_score(img, n, 1.0, 4.0, w2, tau=0.05, grad=False)
         assert abs((S2 - S) - 0.25 * ms[i]) < 1e-12
     assert np.all((ms > 0) & (ms < 1))
+
+
+@pytest.mark.parametrize("H,W,t", [(40, 50, 3.0), (20, 9, 4.0), (7, 5, 6.0)])
+def test_reflect_blur_is_self_adjoint(H, W, t):
+    """Symmetric taps with the half-sample symmetric (reflect) extension give
+    a symmetric operator, also when the kernel is wider than the image: the
+    adjoint written from the mirror families equals the blur itself."""
+    rng = np.random.default_rng(int(H * W))
+    y = rng.standard_normal((H, W))
+    g = oracle.kernel(t)
+    np.testing.assert_allclose(oracle.blur_adjoint(y, g), oracle.blur(y, g), rtol=0, atol=1e-13)
