@@ -92,26 +92,66 @@ __device__ __forceinline__ void hist_rows(const char *img, int H, int W, long lo
         if (first || hi == p0) r0.add(digit, h[0]);
         if (!first && hi == p1) r1.add(digit, h[1]);
     };
-    for (int y = y0; y < H; y += ystep) {
-        const char *row = img + (long long)y * pitch;
-        for (int x0 = threadIdx.x * VEC; x0 < W; x0 += blockDim.x * VEC) {
-            if (vec_ok && x0 + VEC <= W) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + (long long)x0 * ES));
-                const unsigned w[4] = {q.x, q.y, q.z, q.w};
+    auto take16 = [&](const uint4 &q) {
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (DT == 0) {
+        for (int e = 0; e < 4; ++e) {
+            if (DT == 0) {
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) take((w[e] >> (8 * b)) & 0xffu);
-                    } else if (DT == 1) {
-                        take(w[e] & 0xffffu);
-                        take(w[e] >> 16);
-                    } else {
-                        take(key_f32(__uint_as_float(w[e])));
-                    }
-                }
+                for (int b = 0; b < 4; ++b) take((w[e] >> (8 * b)) & 0xffu);
+            } else if (DT == 1) {
+                take(w[e] & 0xffffu);
+                take(w[e] >> 16);
             } else {
-                for (int x = x0; x < x0 + VEC && x < W; ++x) take(load_key<DT>(row, x));
+                take(key_f32(__uint_as_float(w[e])));
+            }
+        }
+    };
+    if (vec_ok && W % VEC == 0) {
+        // this thread's 16-byte chunks, row after row, with the loads of the
+        // next two chunks in flight while one is counted
+        const int xs = threadIdx.x * VEC, step = blockDim.x * VEC;
+        int y = y0, x = xs;
+        auto next = [&](int &yy, int &xx) {
+            xx += step;
+            if (xx >= W) {
+                xx = xs;
+                yy += ystep;
+            }
+        };
+        auto fetch = [&](int yy, int xx) {
+            return __ldg(reinterpret_cast<const uint4 *>(img + (long long)yy * pitch +
+                                                        (long long)xx * ES));
+        };
+        if (xs < W) {
+            int y1 = y, x1 = x;
+            next(y1, x1);
+            uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
+            if (y < H) q0 = fetch(y, x);
+            if (y1 < H) q1 = fetch(y1, x1);
+            while (y < H) {
+                int y2 = y1, x2 = x1;
+                next(y2, x2);
+                uint4 q2 = make_uint4(0, 0, 0, 0);
+                if (y2 < H) q2 = fetch(y2, x2);
+                take16(q0);
+                q0 = q1;
+                q1 = q2;
+                y = y1;
+                x = x1;
+                y1 = y2;
+                x1 = x2;
+            }
+        }
+    } else {
+        for (int y = y0; y < H; y += ystep) {
+            const char *row = img + (long long)y * pitch;
+            for (int x0 = threadIdx.x * VEC; x0 < W; x0 += blockDim.x * VEC) {
+                if (vec_ok && x0 + VEC <= W) {
+                    take16(__ldg(reinterpret_cast<const uint4 *>(row + (long long)x0 * ES)));
+                } else {
+                    for (int x = x0; x < x0 + VEC && x < W; ++x) take(load_key<DT>(row, x));
+                }
             }
         }
     }
