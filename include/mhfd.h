@@ -40,7 +40,8 @@ extern "C" {
 #define MHFD_OK 0
 #define MHFD_WARN_OVERFLOW 1        /* candidate list truncated; true count reported */
 #define MHFD_ERR_INVALID_ARG (-1)   /* bad size, pointer, ladder or parameter */
-#define MHFD_ERR_UNSUPPORTED (-2)   /* ladder too wide for the on-chip tile */
+#define MHFD_ERR_UNSUPPORTED (-2)   /* ladder too wide for the on-chip tile, or a
+                                       variant the entry point does not serve */
 #define MHFD_ERR_OOM (-3)           /* device or pinned allocation failed */
 #define MHFD_ERR_CUDA (-4)          /* a CUDA runtime/driver call failed */
 #define MHFD_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
