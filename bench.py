@@ -218,6 +218,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-tiles", type=int, default=256)
     ap.add_argument("--no-soft", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--soft-tiles", type=int, default=16,
                     help="2048^2 float32 tiles of the soft-score section (64 = full set)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
@@ -398,6 +399,7 @@ def main():
                                                                   args.steps)
     serving = None if args.no_serve else bench_serve(mhfd, torch)
     soft_sec = None if args.no_soft else bench_soft(mhfd, torch, stream, args.soft_tiles)
+    variants = None if args.no_variants else bench_variants(mhfd, torch, stream, tiles[0])
 
     per_tile.sort()
     p99 = per_tile[min(len(per_tile) - 1, int(math.ceil(0.99 * len(per_tile))) - 1)]
@@ -421,12 +423,50 @@ def main():
         "sweep_batched": sweep_batched,
         "serving": serving,
         "soft": soft_sec,
+        "variants": variants,
         "focus_scores": dict(zip([str(s) for s in SIGMA_D], scores)),
         "focus_monotone_drop": all(scores[j] > scores[j + 1] for j in range(len(scores) - 1)),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_variants(mhfd, torch, stream, tile, reps=5):
+    """The paper's variants on the in-focus 4096^2 tile: the periodic
+    boundary (fused kernel variant) and the explicit scale-normalised
+    Laplacian response (plain path, threshold divided by dt), each against
+    the default detection of the same path; CUDA events, median of `reps`."""
+    dt = (T_MAX - T_MIN) / N_LAYERS
+
+    def timed(det, plain):
+        ms = []
+        for r in range(reps + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if plain:
+                det.detect_plain(tile, stream)
+            else:
+                det.detect(tile, stream)
+            e1.record(stream)
+            res = det.wait()
+            if r:
+                ms.append(e0.elapsed_time(e1))
+        det.close()
+        med = statistics.median(ms)
+        return {"value": tile.numel() / (med * 1e-3) / 1e6, "unit": METRIC, "ms": med,
+                "focus_score": res.focus_score}
+
+    kw = dict(threshold=THR, overlap=OVERLAP, nms="paper")
+    return {
+        "fused_reflect": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), False),
+        "fused_periodic": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, boundary="periodic",
+                                              **kw), False),
+        "plain_dog": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), True),
+        "plain_log": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, response="log",
+                                         **dict(kw, threshold=THR / dt)), True),
+    }
 
 
 def bench_soft(mhfd, torch, stream, count=16):
