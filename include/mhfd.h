@@ -187,8 +187,10 @@ int mhfd_batch_uses_graph(mhfd_detector *det);
  * is not NULL, d_dw[i] = grad_s * mean sigmoid of layer i.  The Gaussian
  * levels are recomputed on every call (nothing is kept between calls).
  * Without d_dimg only the forward runs, in the fused kernel (per-block FP64
- * layer sums, reduced in a fixed order); with it, forward and adjoint run
- * through full level planes.  Both are deterministic.
+ * layer sums, reduced in a fixed order); with it, the fused kernel writes the
+ * D planes, and the adjoint blurs each level's gradient plane with that
+ * level's own kernel (the reflect blur is self-adjoint).  Both are
+ * deterministic.
  * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED (the LoG or
  * periodic variants), CUDA, OOM, JIT. */
 int mhfd_soft_score(mhfd_detector *det, const void *d_img, int32_t dtype, int32_t H, int32_t W,
@@ -274,8 +276,8 @@ int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5);
 
 /* Compiles the fused kernel for the ladder and tile of `p` (store = 0: the
  * detection kernel of params.nms; 1: the stack-storing variant of
- * mhfd_debug_stack; 2: the soft-score forward of mhfd_soft_score) into the
- * on-disk kernel cache
+ * mhfd_debug_stack; 2: the soft-score forward of mhfd_soft_score; 3: the
+ * single-level blurs of its adjoint) into the on-disk kernel cache
  * without using a GPU, so that a later mhfd_create_detector starts at once.
  * The cache directory is $MHFD_JIT_CACHE, else `_jit_cache` next to the
  * library.  Errors: INVALID_ARG, UNSUPPORTED, JIT. */

@@ -97,14 +97,15 @@ def build_lib(force=False):
 
 
 # ladders compiled ahead of time: (n, t_min, t_max, nms, store); store 1 is
-# the stack-storing variant, 2 the soft-score forward
+# the stack-storing variant, 2 the soft-score forward, 3 the soft-score
+# adjoint's single-level blurs
 STANDARD_VARIANTS = [
     (10, 1.0, 10.0, 0, 0), (10, 1.0, 10.0, 0, 1),     # 512^2 uint8 workload
     (10, 1.0, 10.0, 1, 0), (10, 1.0, 10.0, 1, 1),
     (16, 1.0, 12.0, 0, 0), (16, 1.0, 12.0, 0, 1),     # 4096^2 uint16 workload
-    (16, 1.0, 12.0, 1, 0), (16, 1.0, 12.0, 0, 2),
+    (16, 1.0, 12.0, 1, 0), (16, 1.0, 12.0, 0, 2), (16, 1.0, 12.0, 0, 3),
     (4, 1.0, 4.0, 0, 0), (4, 1.0, 4.0, 0, 1),         # small ladders of the tests
-    (4, 1.0, 4.0, 1, 0), (4, 1.0, 4.0, 1, 1), (4, 1.0, 4.0, 0, 2),
+    (4, 1.0, 4.0, 1, 0), (4, 1.0, 4.0, 1, 1), (4, 1.0, 4.0, 0, 2), (4, 1.0, 4.0, 0, 3),
 ]
 
 

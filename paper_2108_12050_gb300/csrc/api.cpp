@@ -49,6 +49,11 @@ struct mhfd_detector {
     Variant *var = nullptr;
     Variant *var_store = nullptr;
     Variant *var_soft = nullptr;  // soft-score forward (kernel mode 2)
+    // soft-score adjoint: one single-level blur kernel (mode 3) per level
+    std::vector<Variant *> var_level;
+    std::vector<TileConfig> level_cfg;
+    float *soft_D = nullptr;      // the n D planes of the adjoint's forward
+    size_t soft_D_px = 0;
     std::vector<uint64_t> params;  // by-value parameter block of the fused kernel
 
     // fixed device buffers
@@ -383,7 +388,8 @@ void release(mhfd_detector *d) {
                         d->d_tsc, d->d_tapoff, d->block_tmp, d->block_sum, d->cand, d->tile_count,
                         d->tile_off, d->stage, d->pb.cell_cnt, d->pb.cell_start, d->pb.cell_items,
                         d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->d_blobs, d->d_cands,
-                        d->soft_part, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy};
+                        d->soft_part, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy,
+                        d->soft_D};
     for (void *p : dev_ptrs)
         if (p) cudaFree(p);
     free_conflict_table(&d->ct);
@@ -564,6 +570,68 @@ int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long lo
                             d->block_sum, b.d_arena_n, b.arena_cap, s);
         if (rc) return rc;
     }
+    return MHFD_OK;
+}
+
+// The single-level ladder of level l (its radius and taps), compiled as a
+// plane blur (kernel mode 3) with its own tile shape.
+int level_variant(mhfd_detector *d, int l, Variant **out, TileConfig *cfg) {
+    const int nl = (int)d->R.size();
+    if ((int)d->var_level.size() != nl) {
+        d->var_level.assign(nl, nullptr);
+        d->level_cfg.assign(nl, TileConfig());
+    }
+    if (!d->var_level[l]) {
+        LadderKey lk;
+        lk.R = {d->R[l]};
+        lk.taps.assign(d->taps.begin() + d->tapoff[l], d->taps.begin() + d->tapoff[l] + d->R[l] + 1);
+        lk.tsc = {1.0f};
+        lk.boundary = d->p.boundary;
+        TileConfig c;
+        std::string why;
+        if (!choose_tile(lk.R, 3, &c, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+        int rc = get_variant(lk, 3, 0, c, &d->var_level[l]);
+        if (rc) return rc;
+        d->level_cfg[l] = c;
+    }
+    *out = d->var_level[l];
+    *cfg = d->level_cfg[l];
+    return MHFD_OK;
+}
+
+// out += B_l in (one level's separable blur of a float32 plane, H x W dense)
+int launch_level(mhfd_detector *d, int l, const float *in, float *out, int H, int W,
+                 cudaStream_t s) {
+    Variant *v;
+    TileConfig c;
+    int rc = level_variant(d, l, &v, &c);
+    if (rc) return rc;
+    const int tx = (W + c.tx2 - 3) / (c.tx2 - 2), ty = (H + c.ty2 - 3) / (c.ty2 - 2);
+    const long long n_tiles = (long long)tx * ty;
+    int dev = 0, sms = 1;
+    MHFD_CUDA(cudaGetDevice(&dev));
+    MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    long long grid = (long long)sms * v->occupancy;
+    if (grid > n_tiles) grid = n_tiles;
+    std::vector<unsigned long long> pbuf((v->param_bytes + 7) / 8 + 1, 0);
+    MhfdKHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.img = in;
+    h.st = d->st;
+    h.pitch = (long long)W * 4;
+    h.plane = (long long)H * W;
+    h.H = H;
+    h.W = W;
+    h.dtype = MHFD_F32;
+    h.tiles_x = tx;
+    h.tiles_y = ty;
+    h.total_items = (int)n_tiles;
+    h.stack_out = out;
+    std::memcpy(pbuf.data(), &h, sizeof(h));
+    void *args[] = {pbuf.data()};
+    const CUresult r = drv().launchKernel(v->fn, (unsigned)grid, 1, 1, (unsigned)c.nt, 1, 1,
+                                          (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
+    if (r != CUDA_SUCCESS) return fail(MHFD_ERR_CUDA, "cuLaunchKernel (level blur)");
     return MHFD_OK;
 }
 
@@ -876,6 +944,20 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     TileConfig cfg;
     if ((rc = resolve_tile(R, *p, &cfg))) return rc;
     if (store == 2) return precompile_variant(lk, 2, 0, cfg);  // soft-score forward
+    if (store == 3) {  // the soft-score adjoint's single-level blurs
+        for (size_t l = 0; l < R.size(); ++l) {
+            LadderKey l1;
+            l1.R = {R[l]};
+            l1.taps.assign(lk.taps.begin() + tapoff[l], lk.taps.begin() + tapoff[l] + R[l] + 1);
+            l1.tsc = {1.0f};
+            l1.boundary = p->boundary;
+            TileConfig c1;
+            std::string why;
+            if (!choose_tile(l1.R, 3, &c1, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+            if ((rc = precompile_variant(l1, 3, 0, c1))) return rc;
+        }
+        return MHFD_OK;
+    }
     return precompile_variant(lk, p->nms, store != 0, cfg);
 }
 
@@ -1064,10 +1146,28 @@ int mhfd_soft_score(mhfd_detector *d, const void *img, int32_t dtype, int32_t H,
     rc = enqueue_stretch(img, dtype, H, W, (long long)pitch, clip_rank(d, H, W), d->sel, d->st, s);
     if (rc) return rc;
     if (d_dimg) {
-        // forward and adjoint through the plain level planes
-        return enqueue_soft(img, dtype, H, W, (long long)pitch, d->st, (int)d->R.size(), d->R,
-                            d->d_taps, d->d_tsc, d_w, tau, temperature, grad_s, d->pL, d->pT,
-                            d->pI, d->soft_part, kMaxBlocks, d_S, d_mean_sig, d_dimg, d_dw, s);
+        // forward: the D planes from the stack-storing fused kernel; the
+        // per-layer means, S and the level gradients gL_l from them
+        const size_t px = (size_t)H * W;
+        const int nd = (int)d->R.size() - 1;
+        if (px > d->soft_D_px) {
+            if ((rc = dalloc(&d->soft_D, px * (size_t)nd))) return rc;
+            d->soft_D_px = px;
+        }
+        if (!d->var_store && (rc = get_variant(d->lk, d->p.nms, 1, d->cfg, &d->var_store)))
+            return rc;
+        if ((rc = launch_fused(d, d->var_store, img, dtype, H, W, pitch, s, d->soft_D, nullptr,
+                               nullptr)))
+            return rc;
+        if ((rc = enqueue_soft_stack(d->soft_D, (long long)px, nd, d->d_tsc, d_w, tau,
+                                     temperature, grad_s, d->soft_part, kMaxBlocks, d_S,
+                                     d_mean_sig, d_dw, d->pL, s)))
+            return rc;
+        // adjoint: the reflect blur is self-adjoint, so gI = sum_l B_l gL_l
+        MHFD_CUDA(cudaMemsetAsync(d->pI, 0, sizeof(float) * px, s));
+        for (int l = 0; l <= nd; ++l)
+            if ((rc = launch_level(d, l, d->pL + (size_t)l * px, d->pI, H, W, s))) return rc;
+        return enqueue_soft_mask(img, dtype, H, W, (long long)pitch, d->st, d->pI, d_dimg, s);
     }
     // forward only: the fused kernel accumulates the sigmoids per block
     if (!d->var_soft && (rc = get_variant(d->lk, 2, 0, d->cfg, &d->var_soft))) return rc;

@@ -50,7 +50,9 @@ constexpr int TY = MHFD_TY2 - 2;  // output rows of a tile (candidate storage un
 constexpr int RB = MHFD_RB;
 constexpr int NT = MHFD_NT;
 // 0: paper rule (argmax over scales + 3x3), 1: 3x3x3 rule, 2: soft-score
-// forward (per-layer sums of sigmoid((D - tau) / T), no maxima)
+// forward (per-layer sums of sigmoid((D - tau) / T), no maxima), 3: blur of
+// a float32 plane by the single level of the ladder, added into the output
+// plane (no stretch, no maxima; the soft-score adjoint runs one per level)
 constexpr int MODE = MHFD_MODE;
 constexpr bool STORE = (MHFD_STORE) != 0;
 
@@ -136,7 +138,7 @@ static_assert(TX2 % 4 == 0, "tile width must be a multiple of 4");
 static_assert(TY >= 1, "tile height");
 static_assert(BROWS >= WIN, "the input window must hold one step");
 static_assert(NT % 32 == 0 && NT <= 1024, "threads per block");
-static_assert(NL >= 2 && NL <= 64, "levels");
+static_assert((MODE == 3 ? NL == 1 : NL >= 2) && NL <= 64, "levels");
 static_assert(kGB(0) == 0 && kGB(NGROUPS) == NL, "level groups");
 
 struct KParams {
@@ -183,6 +185,7 @@ __device__ __forceinline__ unsigned raw_px(const char *row, int gx) {
 
 template <int DT>
 __device__ __forceinline__ float stretch_px(unsigned raw, const MhfdStretch &st) {
+    if constexpr (MODE == 3) return __uint_as_float(raw);  // a plane, taken as it is
     if (DT == 2) {
         float u = (__uint_as_float(raw) - st.lo) * st.inv;
         u = fminf(fmaxf(u, 0.0f), 1.0f);
@@ -440,7 +443,11 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
     float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     const float4 *w = reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q;
     HQuads<R, tapoff(L), NQ - 1>::run(h, w, a);
-    if (L == 0) {
+    if (MODE == 3) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (cx.inter[u]) h.stack_out[(long long)cx.gy * h.W + cx.gx0 + u] += a[u];
+    } else if (L == 0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             st.lp[u] = a[u];
@@ -786,7 +793,7 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
         // maxima of the rows whose lower neighbour is now known
         int ra = max(1, s * RB - 1);
         const int rb = min(m.Y, s * RB + RB - 2);
-        while (MODE != 2 && ra <= rb) {
+        while ((MODE == 0 || MODE == 1) && ra <= rb) {
             const int tend = min(m.Y, (tile + 1) * TY);  // last row of the tile
             const int re = min(rb, tend);
             total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, ra, re,

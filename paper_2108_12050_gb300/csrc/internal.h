@@ -164,6 +164,22 @@ int enqueue_pack(const int32_t *x, const int32_t *y, const int32_t *i, const flo
 int enqueue_keep(const int *state, const Counters *cnt, long long n, int prune_on, uint8_t *keep,
                  cudaStream_t s);
 
+// ------------------------------------------------------------ soft score
+// soft score from the D planes (n of them): per-layer means, S, dS/dw and the
+// level-gradient planes gL_l (n + 1 of them) of the adjoint
+int enqueue_soft_stack(const float *d_D, long long plane, int nd, const float *d_tsc,
+                       const float *d_w, float tau, float temp, float grad_s, double *block_part,
+                       int max_blocks, float *d_S, float *d_mean_sig, float *d_dw, float *d_gL,
+                       cudaStream_t s);
+// dimg = gI / (hi - lo) strictly inside (lo, hi), else 0
+int enqueue_soft_mask(const void *img, int dtype, int H, int W, long long pitch,
+                      const MhfdStretch *st, const float *d_gI, float *d_dimg, cudaStream_t s);
+// final reduction of per-block layer sums (fixed order) into S, the
+// per-layer means and optionally dS/dw
+int enqueue_soft_finish(const double *block_part, int nblocks, int n_layers, long long plane,
+                        const float *d_w, float grad_s, float *d_S, float *d_mean_sig, float *d_dw,
+                        cudaStream_t s);
+
 // ---------------------------------------------------------- plain path
 // I' (stretched, centred) and every Gaussian level L_l as full planes.
 int enqueue_stack(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
@@ -176,20 +192,6 @@ int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
                   float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
                   MhfdCand *stage, int cap_tile, int response, int boundary, int *n_tiles_out,
                   cudaStream_t s);
-
-// ------------------------------------------------------------ soft score
-// Forward (and, with d_dimg, the adjoint) of the soft focus score on the
-// level planes L (n_levels planes of H*W, overwritten by the backward).
-// final reduction of per-block layer sums (fixed order) into S, the
-// per-layer means and optionally dS/dw
-int enqueue_soft_finish(const double *block_part, int nblocks, int n_layers, long long plane,
-                        const float *d_w, float grad_s, float *d_S, float *d_mean_sig, float *d_dw,
-                        cudaStream_t s);
-int enqueue_soft(const void *img, int dtype, int H, int W, long long pitch, const MhfdStretch *st,
-                 int n_levels, const std::vector<int> &R, const float *d_taps, const float *d_tsc,
-                 const float *d_w, float tau, float temp, float grad_s, float *scratch_L,
-                 float *scratch_T, float *scratch_G, double *block_part, int max_blocks,
-                 float *d_S, float *d_mean_sig, float *d_dimg, float *d_dw, cudaStream_t s);
 
 // ------------------------------------------------------------- probe
 int probe_ffma(cudaStream_t s, double *ops_per_s);
