@@ -434,9 +434,9 @@ def main():
 
 def bench_variants(mhfd, torch, stream, tile, reps=5):
     """The paper's variants on the in-focus 4096^2 tile: the periodic
-    boundary (fused kernel variant) and the explicit scale-normalised
-    Laplacian response (plain path, threshold divided by dt), each against
-    the default detection of the same path; CUDA events, median of `reps`."""
+    boundary and the explicit scale-normalised Laplacian response (threshold
+    divided by dt), on the fused and the plain path, next to the default
+    detection; CUDA events, median of `reps`."""
     dt = (T_MAX - T_MIN) / N_LAYERS
 
     def timed(det, plain):
@@ -464,6 +464,8 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
         "fused_periodic": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, boundary="periodic",
                                               **kw), False),
         "plain_dog": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), True),
+        "fused_log": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, response="log",
+                                         **dict(kw, threshold=THR / dt)), False),
         "plain_log": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, response="log",
                                          **dict(kw, threshold=THR / dt)), True),
     }

@@ -50,7 +50,8 @@ extern "C" {
 typedef enum { MHFD_U8 = 0, MHFD_U16 = 1, MHFD_F32 = 2 } mhfd_dtype;
 typedef enum { MHFD_NMS_PAPER = 0, MHFD_NMS_LOCAL26 = 1 } mhfd_nms;
 /* Response: the DoG of Eq. 2, or the scale-normalised Laplacian t_i^2 grad^2 L
- * of §2.2 that the DoG approximates (5-point stencil on each level; it lacks
+ * of §2.2 that the DoG approximates (5-point stencil on each level t_1..t_n;
+ * the fused kernel folds the second differences into derived taps; it lacks
  * the DoG's factor dt, so thresholds scale by 1/dt). */
 typedef enum { MHFD_RESPONSE_DOG = 0, MHFD_RESPONSE_LOG = 1 } mhfd_response;
 /* Boundary of the blur: reflect, or periodic (the circular convolution of the
@@ -89,8 +90,8 @@ typedef struct {
                                when it does not fit in shared memory */
     int32_t timing;         /* 1: record CUDA events around the kernels of each
                                detection (read with mhfd_last_timing) */
-    int32_t response;       /* mhfd_response; the fused entry points (detect,
-                               batch, debug_stack, soft score) need DoG */
+    int32_t response;       /* mhfd_response; every entry point but the soft
+                               score (DoG only) supports both */
     int32_t boundary;       /* mhfd_boundary; every entry point but the soft
                                score (reflect only) supports both */
 } mhfd_params;

@@ -131,7 +131,7 @@ class Detector:
         if tile_override is None and tile_shape is None:
             # a measured tile shape for this ladder and GPU, if the autotuner
             # recorded one; otherwise the library's built-in choice
-            if sigmas is None and device >= 0:
+            if sigmas is None and device >= 0 and response in ("dog", 0):
                 from . import tune
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
                 tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate)

@@ -281,7 +281,7 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
     const int n_tiles = tiles_of(d, H, W, &tx, &ty);
     const size_t nl = d->R.size();
     (void)nl;
-    if ((size_t)v->param_bytes < sizeof(MhfdKHeader) || v->ntaps != (int)d->taps.size())
+    if ((size_t)v->param_bytes < sizeof(MhfdKHeader) || v->ntaps != (int)d->lk.taps.size())
         return fail(MHFD_ERR_JIT, "kernel parameter layout mismatch");
     d->params.assign((v->param_bytes + 7) / 8 + 1, 0);
     char *pb = reinterpret_cast<char *>(d->params.data());
@@ -340,19 +340,10 @@ int finish_pipeline(mhfd_detector *d, int n_tiles, int cap_tile, int H, int W, c
     return MHFD_OK;
 }
 
-int fused_supported(const mhfd_detector *d) {
-    if (d->p.response != MHFD_RESPONSE_DOG)
-        return fail(MHFD_ERR_UNSUPPORTED,
-                    "the fused kernel computes the DoG response; use mhfd_detect_plain for "
-                    "the LoG response");
-    return MHFD_OK;
-}
-
 int detect_impl(mhfd_detector *d, const void *img, int dtype, int H, int W, size_t pitch,
                 cudaStream_t s, bool store, float *d_D, float *d_M, int *d_A) {
     int rc = check_image(img, dtype, H, W, pitch);
     if (rc) return rc;
-    if ((rc = fused_supported(d))) return rc;
     DeviceGuard g(d->device);
     Variant *v = d->var;
     if (store) {
@@ -413,7 +404,45 @@ void release(mhfd_detector *d) {
     delete d;
 }
 
-int resolve_tile(const std::vector<int> &R, const mhfd_params &p, TileConfig *cfg) {
+// The fused kernel's ladder: all n + 1 levels for the DoG; for the LoG
+// response the first n levels (one layer each), their second-difference
+// taps and t^2 as the layer factors.  *mode gets the tile mode (the rule,
+// plus kModeLog for the LoG).
+void fused_ladder(const mhfd_params &p, const std::vector<double> &t, const std::vector<int> &R,
+                  LadderKey *lk, int *mode) {
+    std::vector<int> tapoff;
+    std::vector<float> taps, tsc;
+    make_taps(t, R, &taps, &tapoff, &tsc);
+    lk->boundary = p.boundary;
+    lk->response = p.response == MHFD_RESPONSE_LOG ? 1 : 0;
+    *mode = p.nms;
+    if (!lk->response) {
+        lk->R = R;
+        lk->taps = taps;
+        lk->tsc = tsc;
+        lk->taps2.clear();
+        return;
+    }
+    const int n = (int)R.size() - 1;
+    *mode = p.nms | kModeLog;
+    lk->R.assign(R.begin(), R.begin() + n);
+    lk->taps.assign(taps.begin(), taps.begin() + tapoff[n]);
+    lk->tsc.clear();
+    lk->taps2.clear();
+    for (int l = 0; l < n; ++l) {
+        lk->tsc.push_back((float)(t[l] * t[l]));
+        // g''_k = g_{k-1} - 2 g_k + g_{k+1} of the normalised FP64 taps
+        const int r = R[l];
+        std::vector<double> g(r + 3, 0.0);
+        double sum = 0.0;
+        for (int k = -r; k <= r; ++k) sum += std::exp(-((double)k * k) / (2.0 * t[l] * t[l]));
+        for (int k = 0; k <= r; ++k) g[k] = std::exp(-((double)k * k) / (2.0 * t[l] * t[l])) / sum;
+        auto ge = [&](int k) { return k < 0 ? g[-k] : (k <= r ? g[k] : 0.0); };
+        for (int k = 0; k <= r + 1; ++k) lk->taps2.push_back((float)(ge(k - 1) - 2.0 * ge(k) + ge(k + 1)));
+    }
+}
+
+int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, TileConfig *cfg) {
     std::string why;
     if (p.tile_shape[0] > 0) {
         const int *ts = p.tile_shape;
@@ -429,17 +458,17 @@ int resolve_tile(const std::vector<int> &R, const mhfd_params &p, TileConfig *cf
         cfg->nt = ts[3];
         cfg->gb.assign(ts[4] + 1, 0);
         for (int g = 0; g <= ts[4]; ++g) cfg->gb[g] = (int)((long long)nl * g / ts[4]);
-        if (smem_estimate(R, p.nms, *cfg) > kSmemLimitBytes)
+        if (smem_estimate(R, mode, *cfg) > kSmemLimitBytes)
             return fail(MHFD_ERR_UNSUPPORTED, "tile_shape exceeds shared memory for this ladder");
         return MHFD_OK;
     }
     if (p.tile_override > 0) {
-        const std::vector<TileConfig> menu = tile_menu(R, p.nms);
+        const std::vector<TileConfig> menu = tile_menu(R, mode);
         if (p.tile_override > (int)menu.size()) return fail(MHFD_ERR_INVALID_ARG, "tile_override out of range");
         *cfg = menu[p.tile_override - 1];
         return MHFD_OK;
     }
-    if (!choose_tile(R, p.nms, cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+    if (!choose_tile(R, mode, cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
     return MHFD_OK;
 }
 
@@ -687,13 +716,11 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
     DeviceGuard g(d->device);
     const int nl = d->n + 1;
     make_taps(d->t, d->R, &d->taps, &d->tapoff, &d->tsc);
-    d->lk.R = d->R;
-    d->lk.taps = d->taps;
-    d->lk.tsc = d->tsc;
-    d->lk.boundary = d->p.boundary;
+    int tile_mode = d->p.nms;
+    fused_ladder(d->p, d->t, d->R, &d->lk, &tile_mode);
     for (int i = 0; i < d->n; ++i) d->radius.push_back(std::sqrt(2.0) * d->t[i]);
     d->radius_max = d->radius[d->n - 1];
-    if ((rc = resolve_tile(d->R, d->p, &d->cfg))) {
+    if ((rc = resolve_tile(d->lk.R, tile_mode, d->p, &d->cfg))) {
         delete d;
         return rc;
     }
@@ -900,7 +927,10 @@ int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap) {
     std::vector<int> R;
     int rc = build_ladder(*p, &t, &R);
     if (rc) return rc;
-    const std::vector<TileConfig> menu = tile_menu(R, p->nms);
+    LadderKey lk;
+    int mode = p->nms;
+    fused_ladder(*p, t, R, &lk, &mode);
+    const std::vector<TileConfig> menu = tile_menu(lk.R, mode);
     if (desc) {
         for (int k = 0; k < (int)menu.size() && k < cap; ++k) {
             desc[5 * k + 0] = menu[k].tx2;
@@ -920,7 +950,10 @@ int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5) {
     int rc = build_ladder(*p, &t, &R);
     if (rc) return rc;
     TileConfig c;
-    if ((rc = resolve_tile(R, *p, &c))) return rc;
+    LadderKey lk;
+    int mode = p->nms;
+    fused_ladder(*p, t, R, &lk, &mode);
+    if ((rc = resolve_tile(lk.R, mode, *p, &c))) return rc;
     desc5[0] = c.tx2;
     desc5[1] = c.ty2;
     desc5[2] = c.rb;
@@ -937,18 +970,21 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     std::vector<int> R;
     if ((rc = build_ladder(*p, &t, &R))) return rc;
     LadderKey lk;
-    lk.R = R;
-    lk.boundary = p->boundary;
+    int mode = p->nms;
+    fused_ladder(*p, t, R, &lk, &mode);
     std::vector<int> tapoff;
-    make_taps(t, R, &lk.taps, &tapoff, &lk.tsc);
+    std::vector<float> taps_all, tsc_all;
+    make_taps(t, R, &taps_all, &tapoff, &tsc_all);
     TileConfig cfg;
-    if ((rc = resolve_tile(R, *p, &cfg))) return rc;
+    if ((rc = resolve_tile(lk.R, mode, *p, &cfg))) return rc;
+    if ((store == 2 || store == 3) && lk.response)
+        return fail(MHFD_ERR_UNSUPPORTED, "the soft score uses the DoG response");
     if (store == 2) return precompile_variant(lk, 2, 0, cfg);  // soft-score forward
     if (store == 3) {  // the soft-score adjoint's single-level blurs
         for (size_t l = 0; l < R.size(); ++l) {
             LadderKey l1;
             l1.R = {R[l]};
-            l1.taps.assign(lk.taps.begin() + tapoff[l], lk.taps.begin() + tapoff[l] + R[l] + 1);
+            l1.taps.assign(taps_all.begin() + tapoff[l], taps_all.begin() + tapoff[l] + R[l] + 1);
             l1.tsc = {1.0f};
             l1.boundary = p->boundary;
             TileConfig c1;
@@ -967,7 +1003,6 @@ int mhfd_detect_batch(mhfd_detector *d, int32_t n, const void *const *d_imgs,
                       const size_t *pitches, void *stream) {
     if (!d || n < 1 || !d_imgs || !dtypes || !Hs || !Ws || !pitches)
         return fail(MHFD_ERR_INVALID_ARG, "NULL argument or n < 1");
-    if (int rcs = fused_supported(d)) return rcs;
     DeviceGuard g(d->device);
     long long total_items = 0, total_px = 0;
     int max_passes = 1, max_h = 1, max_w = 1, max_rows = 1;
@@ -1133,9 +1168,9 @@ int mhfd_soft_score(mhfd_detector *d, const void *img, int32_t dtype, int32_t H,
     if (!d || !d_w || !d_S || !d_mean_sig) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
     if (!(temperature > 0.0f) || !std::isfinite(tau))
         return fail(MHFD_ERR_INVALID_ARG, "temperature must be > 0 and tau finite");
-    if (int rcs = fused_supported(d)) return rcs;
-    if (d->p.boundary != MHFD_BOUNDARY_REFLECT)
-        return fail(MHFD_ERR_UNSUPPORTED, "the soft score uses the reflect boundary");
+    if (d->p.response != MHFD_RESPONSE_DOG || d->p.boundary != MHFD_BOUNDARY_REFLECT)
+        return fail(MHFD_ERR_UNSUPPORTED,
+                    "the soft score uses the DoG response and the reflect boundary");
     int rc = check_image(img, dtype, H, W, pitch);
     if (rc) return rc;
     DeviceGuard g(d->device);

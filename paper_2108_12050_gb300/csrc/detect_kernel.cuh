@@ -42,7 +42,13 @@ namespace mk {
 #define MK_HD __host__ __device__
 
 constexpr int NL = MHFD_NL;
-constexpr int NDOG = NL - 1;
+// Response: 0 the DoG of Eq. 2 over NL levels (NL - 1 layers); 1 the
+// scale-normalised Laplacian t_l^2 grad^2 L_l of each of NL levels (NL
+// layers), with the 5-point second differences folded into derived taps:
+// dyy L = H (g'' (*)_y I) and dxx L = g'' (*)_x (V I), g''_k = g_{k-1} -
+// 2 g_k + g_{k+1} (radius R + 1), so both share the vertical folded sums.
+constexpr bool LOG = (MHFD_RESPONSE) == 1;
+constexpr int NDOG = LOG ? NL : NL - 1;  // response layers
 constexpr int NGROUPS = MHFD_NGROUPS;
 constexpr int TX2 = MHFD_TX2;
 constexpr int TX = TX2 - 2;       // output columns of a strip
@@ -76,14 +82,26 @@ MK_HD constexpr float kTsc(int l) {
     constexpr float a[] = {MHFD_TSC};
     return a[l];
 }
+// LoG: the second-difference taps g''_l[0..R_l+1] at tapoff2(l)
+MK_HD constexpr float kTap2(int i) {
+    constexpr float a[] = {MHFD_TAPS2};
+    return a[i];
+}
 template <int I>
 __device__ __forceinline__ float tap() {
     constexpr float v = kTap(I);
     return v;
 }
+template <int I>
+__device__ __forceinline__ float tap2() {
+    constexpr float v = kTap2(I);
+    return v;
+}
+// halo a level needs: its radius, one more for the second-difference taps
+MK_HD constexpr int kRH(int l) { return kR(l) + (LOG ? 1 : 0); }
 MK_HD constexpr int rmax_of() {
     int m = 0;
-    for (int l = 0; l < NL; ++l) m = kR(l) > m ? kR(l) : m;
+    for (int l = 0; l < NL; ++l) m = kRH(l) > m ? kRH(l) : m;
     return m;
 }
 constexpr int RMAX = rmax_of();
@@ -98,12 +116,19 @@ constexpr int HITEMS = RB * NQ4;
 constexpr int HI = (HITEMS + NT - 1) / NT;
 constexpr int NPARTS = (RB + 3) / 4;
 
-// padded width of the V row of level l (its outputs plus its own halo)
-MK_HD constexpr int extp(int l) { return (TX2 + 2 * kR(l) + 3) & ~3; }
+// padded width of the V row of level l (its outputs plus its own halo);
+// LoG levels hold two rows, V and g'' (*)_y I, side by side
+MK_HD constexpr int extp(int l) { return (TX2 + 2 * kRH(l) + 3) & ~3; }
+MK_HD constexpr int vwidth(int l) { return LOG ? 2 * extp(l) : extp(l); }
 // taps of level l start at tapoff(l) of the parameter block
 MK_HD constexpr int tapoff(int l) {
     int o = 0;
     for (int j = 0; j < l; ++j) o += kR(j) + 1;
+    return o;
+}
+MK_HD constexpr int tapoff2(int l) {
+    int o = 0;
+    for (int j = 0; j < l; ++j) o += kR(j) + 2;
     return o;
 }
 MK_HD constexpr int group_of(int l) {
@@ -114,14 +139,14 @@ MK_HD constexpr int group_of(int l) {
 // the V row of level l starts at voff(l) within its group's row
 MK_HD constexpr int voff(int l) {
     int o = 0;
-    for (int j = kGB(group_of(l)); j < l; ++j) o += extp(j);
+    for (int j = kGB(group_of(l)); j < l; ++j) o += vwidth(j);
     return o;
 }
 MK_HD constexpr int vrow_max() {
     int m = 0;
     for (int g = 0; g < NGROUPS; ++g) {
         int o = 0;
-        for (int j = kGB(g); j < kGB(g + 1); ++j) o += extp(j);
+        for (int j = kGB(g); j < kGB(g + 1); ++j) o += vwidth(j);
         m = o > m ? o : m;
     }
     return m;
@@ -138,7 +163,8 @@ static_assert(TX2 % 4 == 0, "tile width must be a multiple of 4");
 static_assert(TY >= 1, "tile height");
 static_assert(BROWS >= WIN, "the input window must hold one step");
 static_assert(NT % 32 == 0 && NT <= 1024, "threads per block");
-static_assert((MODE == 3 ? NL == 1 : NL >= 2) && NL <= 64, "levels");
+static_assert((MODE == 3 || LOG ? NL >= 1 : NL >= 2) && NL <= 64, "levels");
+static_assert(!LOG || MODE <= 1, "the LoG response is a detection mode");
 static_assert(kGB(0) == 0 && kGB(NGROUPS) == NL, "level groups");
 
 struct KParams {
@@ -305,43 +331,60 @@ __device__ __forceinline__ void shift_window(float *s_in, int from, int n) {
     }
 }
 
+// the largest halo radius among the levels of group g
+MK_HD constexpr int group_rmax(int g) {
+    int m = 0;
+    for (int l = kGB(g); l < kGB(g + 1); ++l) m = kRH(l) > m ? kRH(l) : m;
+    return m;
+}
+
 // Fold step K of the vertical pass for the levels L.. of group G: every
-// level whose radius reaches K takes tap K times the folded sum.
+// level whose radius reaches K takes tap K times the folded sum (and, for
+// the LoG, every level whose radius + 1 reaches K its second-difference
+// tap K into a2).
 template <int G, int K, int L>
-__device__ __forceinline__ void vlev(float sum, float *a) {
+__device__ __forceinline__ void vlev(float sum, float *a, float *a2) {
     constexpr int LB = kGB(G);
     constexpr int NG = kGB(G + 1) - LB;
     if constexpr (L < NG) {
         if constexpr (K <= kR(LB + L)) a[L] = fmaf(tap<tapoff(LB + L) + K>(), sum, a[L]);
-        vlev<G, K, L + 1>(sum, a);
+        if constexpr (LOG && K <= kR(LB + L) + 1)
+            a2[L] = fmaf(tap2<tapoff2(LB + L) + K>(), sum, a2[L]);
+        vlev<G, K, L + 1>(sum, a, a2);
     }
 }
 
 template <int G, int L>
-__device__ __forceinline__ void vinit(float x, float *a) {
+__device__ __forceinline__ void vinit(float x, float *a, float *a2) {
     constexpr int LB = kGB(G);
     constexpr int NG = kGB(G + 1) - LB;
     if constexpr (L < NG) {
         a[L] = tap<tapoff(LB + L)>() * x;
-        vinit<G, L + 1>(x, a);
+        if constexpr (LOG) a2[L] = tap2<tapoff2(LB + L)>() * x;
+        vinit<G, L + 1>(x, a, a2);
     }
 }
 
+template <int G>
+MK_HD constexpr int ng2() { return LOG ? kGB(G + 1) - kGB(G) : 1; }
+
 template <int G, int ROWS, int K>
-__device__ __forceinline__ void vstep(const float *colp, float (*acc)[kGB(G + 1) - kGB(G)]) {
-    if constexpr (K <= kR(kGB(G + 1) - 1)) {
+__device__ __forceinline__ void vstep(const float *colp, float (*acc)[kGB(G + 1) - kGB(G)],
+                                      float (*acc2)[ng2<G>()]) {
+    if constexpr (K <= group_rmax(G)) {
 #pragma unroll
         for (int j = 0; j < ROWS; ++j) {
             const float sum = colp[(j + K) * WEXTP] + colp[(j - K) * WEXTP];
-            vlev<G, K, 0>(sum, acc[j]);
+            vlev<G, K, 0>(sum, acc[j], acc2[j]);
         }
-        vstep<G, ROWS, K + 1>(colp, acc);
+        vstep<G, ROWS, K + 1>(colp, acc, acc2);
     }
 }
 
 // V_l(o0 + j, c) for the ROWS rows starting at step row o0 and every level l
-// of group G.  `win` is the window row of the step's first input row: step
-// row o sits at window row o + RMAX.
+// of group G (for the LoG also g''_l (*)_y I, stored after V_l).  `win` is
+// the window row of the step's first input row: step row o sits at window
+// row o + RMAX.
 template <int G, int ROWS>
 __device__ __forceinline__ void vcol(const float *__restrict__ win, float *__restrict__ s_v, int c,
                                      int o0) {
@@ -349,16 +392,21 @@ __device__ __forceinline__ void vcol(const float *__restrict__ win, float *__res
     constexpr int LE = kGB(G + 1);
     constexpr int NG = LE - LB;
     float acc[ROWS][NG];
+    float acc2[ROWS][ng2<G>()];
     const float *colp = win + (o0 + RMAX) * WEXTP + c;
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j) vinit<G, 0>(colp[j * WEXTP], acc[j]);
-    vstep<G, ROWS, 1>(colp, acc);
+    for (int j = 0; j < ROWS; ++j) vinit<G, 0>(colp[j * WEXTP], acc[j], acc2[j]);
+    vstep<G, ROWS, 1>(colp, acc, acc2);
 #pragma unroll
     for (int l = 0; l < NG; ++l) {
-        const int cc = c - (RMAX - kR(LB + l));
-        if (cc >= 0 && cc < TX2 + 2 * kR(LB + l)) {
+        const int cc = c - (RMAX - kRH(LB + l));
+        if (cc >= 0 && cc < TX2 + 2 * kRH(LB + l)) {
 #pragma unroll
-            for (int j = 0; j < ROWS; ++j) s_v[(o0 + j) * VROW + voff(LB + l) + cc] = acc[j][l];
+            for (int j = 0; j < ROWS; ++j) {
+                s_v[(o0 + j) * VROW + voff(LB + l) + cc] = acc[j][l];
+                if constexpr (LOG)
+                    s_v[(o0 + j) * VROW + voff(LB + l) + extp(LB + l) + cc] = acc2[j][l];
+            }
         }
     }
 }
@@ -376,13 +424,6 @@ struct VParts<G, NPARTS> {
     static __device__ __forceinline__ void run(const float *, float *, int) {}
 };
 
-// the columns group G needs: the strip plus the group's largest radius
-MK_HD constexpr int group_rmax(int g) {
-    int m = 0;
-    for (int l = kGB(g); l < kGB(g + 1); ++l) m = kR(l) > m ? kR(l) : m;
-    return m;
-}
-
 template <int G>
 __device__ __forceinline__ void vpass(const float *win, float *s_v) {
     constexpr int RG = group_rmax(G);
@@ -394,35 +435,42 @@ __device__ __forceinline__ void vpass(const float *win, float *s_v) {
 
 // ----------------------------------------------------- 3. horizontal pass
 
-// value number M of the window feeds output U with tap |M - U - R|
-template <int R, int TO, int M, int U>
+// value number M of the window (which starts OFF values before the first
+// output's) feeds output U with tap |M - U - R - OFF| of the Gaussian taps,
+// or of the second-difference taps when T2
+template <int R, int TO, int M, int U, int OFF, bool T2>
 __device__ __forceinline__ void hacc1(float v, float (&a)[4]) {
-    constexpr int k = M - U - R;
-    if constexpr (k >= -R && k <= R) a[U] = fmaf(tap<TO + (k < 0 ? -k : k)>(), v, a[U]);
+    constexpr int k = M - U - R - OFF;
+    if constexpr (k >= -R && k <= R) {
+        if constexpr (T2)
+            a[U] = fmaf(tap2<TO + (k < 0 ? -k : k)>(), v, a[U]);
+        else
+            a[U] = fmaf(tap<TO + (k < 0 ? -k : k)>(), v, a[U]);
+    }
 }
 
-template <int R, int TO, int M>
-__device__ __forceinline__ void hacc(const MhfdKHeader &, float v, float (&a)[4]) {
-    hacc1<R, TO, M, 0>(v, a);
-    hacc1<R, TO, M, 1>(v, a);
-    hacc1<R, TO, M, 2>(v, a);
-    hacc1<R, TO, M, 3>(v, a);
+template <int R, int TO, int M, int OFF, bool T2>
+__device__ __forceinline__ void hacc(float v, float (&a)[4]) {
+    hacc1<R, TO, M, 0, OFF, T2>(v, a);
+    hacc1<R, TO, M, 1, OFF, T2>(v, a);
+    hacc1<R, TO, M, 2, OFF, T2>(v, a);
+    hacc1<R, TO, M, 3, OFF, T2>(v, a);
 }
 
-template <int R, int TO, int M4>
+template <int R, int TO, int M4, int OFF, bool T2>
 struct HQuads {
-    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float4 *w, float (&a)[4]) {
+    static __device__ __forceinline__ void run(const float4 *w, float (&a)[4]) {
         const float4 v = w[M4];
-        hacc<R, TO, 4 * M4 + 0>(h, v.x, a);
-        hacc<R, TO, 4 * M4 + 1>(h, v.y, a);
-        hacc<R, TO, 4 * M4 + 2>(h, v.z, a);
-        hacc<R, TO, 4 * M4 + 3>(h, v.w, a);
-        HQuads<R, TO, M4 - 1>::run(h, w, a);
+        hacc<R, TO, 4 * M4 + 0, OFF, T2>(v.x, a);
+        hacc<R, TO, 4 * M4 + 1, OFF, T2>(v.y, a);
+        hacc<R, TO, 4 * M4 + 2, OFF, T2>(v.z, a);
+        hacc<R, TO, 4 * M4 + 3, OFF, T2>(v.w, a);
+        HQuads<R, TO, M4 - 1, OFF, T2>::run(w, a);
     }
 };
-template <int R, int TO>
-struct HQuads<R, TO, -1> {
-    static __device__ __forceinline__ void run(const MhfdKHeader &, const float4 *, float (&)[4]) {}
+template <int R, int TO, int OFF, bool T2>
+struct HQuads<R, TO, -1, OFF, T2> {
+    static __device__ __forceinline__ void run(const float4 *, float (&)[4]) {}
 };
 
 struct HCtx {
@@ -435,19 +483,34 @@ struct HCtx {
     bool inter[4];  // output inside the tile interior and the image (stored)
 };
 
+// The horizontal pass of level L for this item's four outputs, then its
+// response: the DoG of Eq. 2 with the previous level (kept in st.lp), or the
+// scale-normalised Laplacian of the level itself.
 template <int L>
 __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, const HCtx &cx,
                                        HState &st, float *s_ring) {
     constexpr int R = kR(L);
-    constexpr int NQ = (2 * R + 3) / 4 + 1;
     float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const float4 *w = reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q;
-    HQuads<R, tapoff(L), NQ - 1>::run(h, w, a);
+    if constexpr (LOG) {
+        // t^2 (g (*)_x (g'' (*)_y I) + g'' (*)_x (g (*)_y I)): the first row
+        // starts one column before its radius-R window, the second is read
+        // with radius R + 1
+        constexpr int NQA = (2 * R + 4) / 4 + 1;
+        constexpr int NQB = (2 * (R + 1) + 3) / 4 + 1;
+        HQuads<R, tapoff(L), NQA - 1, 1, false>::run(
+            reinterpret_cast<const float4 *>(vrow + voff(L) + extp(L)) + cx.q, a);
+        HQuads<R + 1, tapoff2(L), NQB - 1, 0, true>::run(
+            reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q, a);
+    } else {
+        constexpr int NQ = (2 * R + 3) / 4 + 1;
+        HQuads<R, tapoff(L), NQ - 1, 0, false>::run(
+            reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q, a);
+    }
     if (MODE == 3) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if (cx.inter[u]) h.stack_out[(long long)cx.gy * h.W + cx.gx0 + u] += a[u];
-    } else if (L == 0) {
+    } else if (!LOG && L == 0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             st.lp[u] = a[u];
@@ -455,13 +518,25 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
             st.a[u] = 0;
         }
     } else {
-        constexpr int I = (L > 0 ? L - 1 : 0);
-        constexpr float ts = kTsc(I);
+        constexpr int I = LOG ? L : (L > 0 ? L - 1 : 0);  // response layer
+        constexpr float ts = kTsc(I);                    // t_I, or t_I^2 for the LoG
         float d[4];
+        if constexpr (LOG) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            d[u] = ts * (a[u] - st.lp[u]);
-            st.lp[u] = a[u];
+            for (int u = 0; u < 4; ++u) d[u] = ts * a[u];
+            if (L == 0) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    st.m[u] = -__int_as_float(0x7f800000);
+                    st.a[u] = 0;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                d[u] = ts * (a[u] - st.lp[u]);
+                st.lp[u] = a[u];
+            }
         }
         if (MODE == 0) {
 #pragma unroll

@@ -88,6 +88,9 @@ struct LadderKey {
     std::vector<float> taps;
     std::vector<float> tsc;
     int boundary = 0;  // mhfd_boundary of the blur
+    int response = 0;  // mhfd_response: 1 = the LoG of each level (taps2: the
+                       // second-difference taps g''_l[0..R_l+1] per level)
+    std::vector<float> taps2;
 };
 
 // Choose a tile configuration for the radii and mode (built-in heuristic).
@@ -97,6 +100,9 @@ std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode);
 // opt-in shared memory per block (227 KB) less the kernel's static shared
 // variables (the batch loop's queue slot), which count against the same limit
 constexpr int kSmemLimitBytes = 232448 - 64;
+// added to a kernel mode in the tile and shared-memory helpers: the LoG
+// response (one more halo pixel, two V rows per level, a layer per level)
+constexpr int kModeLog = 4;
 int brows_for(const std::vector<int> &R, int mode, const TileConfig &c);
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c);
 // Compile (or fetch from cache) the fused kernel for this ladder/config.

@@ -76,6 +76,7 @@ std::string join_f(const std::vector<float> &v) {
 
 std::string make_source(const LadderKey &lk, int mode, int store, const TileConfig &c) {
     const std::vector<int> &R = lk.R;
+    const int smode = mode | (lk.response ? kModeLog : 0);
     std::ostringstream o;
     o << "#define MHFD_NL " << R.size() << "\n"
       << "#define MHFD_RLIST " << join(R) << "\n"
@@ -85,12 +86,14 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_GB " << join(c.gb) << "\n"
       << "#define MHFD_TX2 " << c.tx2 << "\n"
       << "#define MHFD_TY2 " << c.ty2 << "\n"
-      << "#define MHFD_BROWS " << brows_for(R, mode, c) << "\n"
+      << "#define MHFD_BROWS " << brows_for(R, smode, c) << "\n"
       << "#define MHFD_RB " << c.rb << "\n"
       << "#define MHFD_NT " << c.nt << "\n"
       << "#define MHFD_MODE " << mode << "\n"
       << "#define MHFD_STORE " << store << "\n"
-      << "#define MHFD_BOUNDARY " << lk.boundary << "\n";
+      << "#define MHFD_BOUNDARY " << lk.boundary << "\n"
+      << "#define MHFD_RESPONSE " << lk.response << "\n"
+      << "#define MHFD_TAPS2 " << (lk.response ? join_f(lk.taps2) : std::string("0.0f")) << "\n";
     return o.str() + kTypesSrc + kKernelSrc;
 }
 
@@ -179,30 +182,42 @@ const DrvApi &drv() {
 
 namespace {
 
+// `mode` is the kernel mode (0 paper rule, 1 26-neighbour rule, 2 soft
+// forward, 3 level blur) plus kModeLog for the LoG response, whose levels
+// need one more halo pixel and two V rows each, and whose layers are the
+// levels themselves (not their differences).
+bool is_log(int mode) { return (mode & kModeLog) != 0; }
+
 int rmax_of(const std::vector<int> &R) {
     int m = 0;
     for (int r : R) m = r > m ? r : m;
     return m;
 }
 
+int halo_of(const std::vector<int> &R, int mode) { return rmax_of(R) + (is_log(mode) ? 1 : 0); }
+
 // bytes of everything but the input window
 int smem_fixed(const std::vector<int> &R, int mode, const TileConfig &c) {
-    const int nl = (int)R.size();
+    const bool log = is_log(mode);
+    const int base = mode & 3;
+    const int layers = log ? (int)R.size() : (int)R.size() - 1;
     int vrow = 0;
     for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
         int o = 0;
-        for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) o += (c.tx2 + 2 * R[l] + 3) & ~3;
+        for (int l = c.gb[g]; l < c.gb[g + 1]; ++l)
+            o += (log ? 2 : 1) * ((c.tx2 + 2 * (R[l] + (log ? 1 : 0)) + 3) & ~3);
         vrow = o > vrow ? o : vrow;
     }
-    // mode 0: max/argmax ring, 1: response-stack ring, 2 (soft forward): none
+    // mode 0: max/argmax ring, 1: response-stack ring, 2 (soft forward) and
+    // 3 (level blur): none
     const int ring = c.rb + 2;
-    const int ring_f = mode == 0 ? ring * c.tx2 : mode == 1 ? ring * (nl - 1) * c.tx2 : 0;
-    const int ring_b = mode == 0 ? ((ring * c.tx2 + 15) & ~15) : 0;
+    const int ring_f = base == 0 ? ring * c.tx2 : base == 1 ? ring * layers * c.tx2 : 0;
+    const int ring_b = base == 0 ? ((ring * c.tx2 + 15) & ~15) : 0;
     return 4 * (c.rb * vrow + ring_f) + ring_b + 4 * 64;
 }
 
-int wextp_of(const std::vector<int> &R, const TileConfig &c) {
-    return (c.tx2 + 2 * rmax_of(R) + 3) & ~3;
+int wextp_of(const std::vector<int> &R, int mode, const TileConfig &c) {
+    return (c.tx2 + 2 * halo_of(R, mode) + 3) & ~3;
 }
 
 }  // namespace
@@ -210,8 +225,8 @@ int wextp_of(const std::vector<int> &R, const TileConfig &c) {
 // Input window rows: one step's rows (rb + 2 rmax) plus up to four steps of
 // slack (the window shifts back once the slack is used up), as many as fit.
 int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
-    const int win = c.rb + 2 * rmax_of(R);
-    const int row_bytes = 4 * wextp_of(R, c);
+    const int win = c.rb + 2 * halo_of(R, mode);
+    const int row_bytes = 4 * wextp_of(R, mode, c);
     const int room = (kSmemLimit - smem_fixed(R, mode, c)) / row_bytes;
     int b = win + 4 * c.rb;
     if (b > room) b = room;
@@ -219,7 +234,7 @@ int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
 }
 
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
-    return smem_fixed(R, mode, c) + 4 * brows_for(R, mode, c) * wextp_of(R, c);
+    return smem_fixed(R, mode, c) + 4 * brows_for(R, mode, c) * wextp_of(R, mode, c);
 }
 
 namespace {
@@ -237,7 +252,7 @@ std::vector<int> groups_for(int nl, int max_per_group) {
 // round, which wait at the next barrier), the horizontal pass over the
 // strip's columns, and the window shifts
 double cost_model(const std::vector<int> &R, int mode, const TileConfig &c) {
-    const int rmax = rmax_of(R);
+    const int rmax = halo_of(R, mode);
     const double tx = c.tx2 - 2;
     double v = 0, h = 0;
     for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
@@ -266,7 +281,7 @@ double cost_model(const std::vector<int> &R, int mode, const TileConfig &c) {
 std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode) {
     std::vector<TileConfig> out;
     const int nl = (int)R.size();
-    const int rmax = rmax_of(R);
+    const int rmax = halo_of(R, mode);
     const int widths[] = {64, 96, 128, 160, 192, 224, 256, 288, 320};
     const int gmax[] = {6, 8, 10, 12};
     for (int tx2 : widths) {
@@ -294,7 +309,7 @@ std::vector<TileConfig> tile_menu(const std::vector<int> &R, int mode) {
 
 bool choose_tile(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why) {
     const std::vector<TileConfig> menu = tile_menu(R, mode);
-    const int rmax = rmax_of(R);
+    const int rmax = halo_of(R, mode);
     // Preferred shapes (what the autotuner finds on GB300): four rows per
     // step (one vertical part, enough rows to amortise a step's barriers and
     // scans), one thread per halo'd column so that the vertical pass of every
@@ -338,7 +353,7 @@ std::string source_hash(const std::string &src) {
 }  // namespace
 
 int precompile_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg) {
-    if (smem_estimate(lk.R, mode, cfg) > kSmemLimit)
+    if (smem_estimate(lk.R, mode | (lk.response ? kModeLog : 0), cfg) > kSmemLimit)
         return fail(MHFD_ERR_UNSUPPORTED, "tile configuration exceeds shared memory");
     const std::string src = make_source(lk, mode, store, cfg);
     const std::string path = cache_dir() + "/" + source_hash(src) + ".cubin";
@@ -366,7 +381,7 @@ int get_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg,
             return MHFD_OK;
         }
     }
-    if (smem_estimate(R, mode, cfg) > kSmemLimit)
+    if (smem_estimate(R, mode | (lk.response ? kModeLog : 0), cfg) > kSmemLimit)
         return fail(MHFD_ERR_UNSUPPORTED, "tile configuration exceeds shared memory");
     const std::string path = cache_dir() + "/" + hbuf + ".cubin";
     std::string cubin;

@@ -327,7 +327,9 @@ def test_plain_path_matches_oracle():
     ("dog", "reflect", "paper", True), ("log", "reflect", "paper", True),
     ("dog", "periodic", "paper", True), ("log", "periodic", "paper", True),
     ("log", "reflect", "local26", True), ("dog", "periodic", "local26", True),
-    ("dog", "periodic", "paper", False), ("dog", "periodic", "local26", False)])
+    ("dog", "periodic", "paper", False), ("dog", "periodic", "local26", False),
+    ("log", "reflect", "paper", False), ("log", "periodic", "paper", False),
+    ("log", "reflect", "local26", False)])
 def test_variants_match_oracle(response, boundary, nms, plain):
     a, _ = synth.pair512_u8(seed=6, H=200, W=270)
     # the LoG response lacks the DoG's factor dt (0.9 here): threshold scaled
@@ -373,10 +375,34 @@ def test_periodic_plain_commutes_with_circular_shift():
     assert not diff, diff[:10]
 
 
-def test_fused_entry_points_reject_the_log_response():
+@pytest.mark.parametrize("boundary,shape", [("reflect", (150, 230)), ("periodic", (70, 45))])
+def test_fused_log_stack_within_tolerance(boundary, shape):
+    """The fused kernel's scale-normalised Laplacian (second differences
+    folded into derived taps) against the oracle's 5-point stencil on its
+    FP64 levels, including an image narrower than the largest kernel."""
+    img = scene(71, shape[0], shape[1], "u16")
+    n, tmin, tmax = 10, 1.0, 10.0
+    det = detector(n=n, t_min=tmin, t_max=tmax, threshold=0.1, response="log",
+                   boundary=boundary)
+    D, _, _, _ = det.debug_stack(to_dev(img), want=("D",))
+    lo, hi = oracle.stretch_bounds(img)
+    t = oracle.ladder(n, tmin, tmax)
+    Ip = oracle.stretch(img, lo, hi)
+    bnd = oracle.PERIODIC if boundary == "periodic" else oracle.REFLECT
+    D_ref = oracle.log_stack(Ip, t, boundary=bnd)
+    R = [oracle.kernel_radius(ti) for ti in t[:n]]
+    eps = log_eps(D_ref, t, R, float(np.abs(Ip).max()))
+    D = D.cpu().numpy().astype(np.float64)
+    for i in range(n):
+        err = np.abs(D[i] - D_ref[i]).max()
+        assert err <= eps[i], (boundary, i, err, eps[i])
+
+
+def test_soft_score_rejects_the_log_response():
     import paper_2108_12050_gb300 as mhfd
+    from paper_2108_12050_gb300 import soft
     a, _ = synth.pair512_u8(seed=6, H=64, W=64)
     det = detector(n=4, t_min=1.0, t_max=4.0, threshold=0.1, response="log")
     with pytest.raises(mhfd.MhfdError) as e:
-        det(to_dev(a))
+        soft.soft_score(det, to_dev(a.astype(np.float32)), torch.ones(4), 0.1)
     assert e.value.code == -2
