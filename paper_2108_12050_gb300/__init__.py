@@ -131,10 +131,11 @@ class Detector:
         if tile_override is None and tile_shape is None:
             # a measured tile shape for this ladder and GPU, if the autotuner
             # recorded one; otherwise the library's built-in choice
-            if sigmas is None and device >= 0 and response in ("dog", 0):
+            if sigmas is None and device >= 0:
                 from . import tune
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
-                tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate)
+                tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate,
+                                         "log" if response in ("log", 1) else "dog")
         tile_override = tile_override or 0
         self.n = int(n)
         self.device = device

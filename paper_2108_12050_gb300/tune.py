@@ -25,9 +25,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(PKG, "tuned_tiles.json")
 
 
-def ladder_key(n, t_min, t_max, nms, truncate=4.0):
-    return "n%d_t%g-%g_%s_tr%g" % (n, t_min, t_max, "paper" if nms in (0, "paper") else "local26",
-                                   truncate)
+def ladder_key(n, t_min, t_max, nms, truncate=4.0, response="dog"):
+    key = "n%d_t%g-%g_%s_tr%g" % (n, t_min, t_max,
+                                  "paper" if nms in (0, "paper") else "local26", truncate)
+    return key if response in ("dog", 0) else key + "_log"
 
 
 def load_table():
@@ -38,10 +39,10 @@ def load_table():
         return {}
 
 
-def lookup(n, t_min, t_max, nms, sms, truncate=4.0):
+def lookup(n, t_min, t_max, nms, sms, truncate=4.0, response="dog"):
     """Tuned tile shape (the five-field tile_shape of the parameters) for this
-    ladder and SM count, or None (the library's built-in choice is used)."""
-    ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate))
+    ladder, response and SM count, or None (the built-in choice is used)."""
+    ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate, response))
     if not ent:
         return None
     best = ent.get(str(sms)) or ent.get("any")
@@ -59,12 +60,12 @@ def _rmax(n, t_min, t_max, truncate=4.0):
     return max(int(math.ceil(truncate * (t_min + i * dt))) for i in range(n + 1))
 
 
-def candidates(n, t_min, t_max, nms, limit=None, min_width=0):
+def candidates(n, t_min, t_max, nms, limit=None, min_width=0, response="dog"):
     """Balanced shapes of the built-in menu: every horizontal item has a
     thread and the vertical pass keeps most threads busy."""
     from . import _native
-    menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms)
-    rmax = _rmax(n, t_min, t_max)
+    menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms, response=response)
+    rmax = _rmax(n, t_min, t_max) + (0 if response in ("dog", 0) else 1)
     seen, out = set(), []
     for (tx2, ty2, rb, nt, ng) in menu:
         if tx2 < min_width:
@@ -84,14 +85,15 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0):
     return out[:limit] if limit else out
 
 
-def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), groups=(2, 3, 4, 5)):
+def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), groups=(2, 3, 4, 5),
+                     response="dog"):
     """Shapes off the menu's width grid (strip widths fitted to an image
     width).  Thread counts: at least one per horizontal item and one per
     halo'd column of the vertical pass (a single round), that count plus one
     warp, and rounded up to whole groups of four warps (the four schedulers
     of an SM); keeps those that fit in shared memory."""
     from . import _native
-    rmax = _rmax(n, t_min, t_max)
+    rmax = _rmax(n, t_min, t_max) + (0 if response in ("dog", 0) else 1)
     out = []
     for tx2 in widths:
         ncol = -(-(tx2 + 2 * rmax) // 32) * 32
@@ -105,7 +107,7 @@ def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), group
                     shape = (tx2, 18, rb, nt, ng)
                     try:
                         _native.chosen_tile(n=n, t_min=t_min, t_max=t_max, nms=nms,
-                                            tile_shape=shape)
+                                            tile_shape=shape, response=response)
                     except Exception:
                         continue
                     out.append(shape)
@@ -113,31 +115,32 @@ def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), group
 
 
 def _compile_one(args):
-    n, t_min, t_max, nms, shape = args
+    n, t_min, t_max, nms, shape, response = args
     sys.path.insert(0, os.path.dirname(PKG))
     from paper_2108_12050_gb300 import _native
     t0 = time.time()
     try:
-        _native.precompile(n=n, t_min=t_min, t_max=t_max, nms=nms, tile_shape=shape)
+        _native.precompile(n=n, t_min=t_min, t_max=t_max, nms=nms, tile_shape=shape,
+                           response=response)
         return shape, time.time() - t0, None
     except Exception as e:  # a shape the compiler rejects is skipped
         return shape, time.time() - t0, str(e)
 
 
-def precompile_all(n, t_min, t_max, nms, cands, workers=None):
+def precompile_all(n, t_min, t_max, nms, cands, workers=None, response="dog"):
     ctx = mp.get_context("spawn")
     workers = workers or (os.cpu_count() or 4)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
-        return list(ex.map(_compile_one, [(n, t_min, t_max, nms, c) for c in cands]))
+        return list(ex.map(_compile_one, [(n, t_min, t_max, nms, c, response) for c in cands]))
 
 
-def measure(n, t_min, t_max, nms, threshold, img_dev, cands, reps=5):
+def measure(n, t_min, t_max, nms, threshold, img_dev, cands, reps=5, response="dog"):
     import paper_2108_12050_gb300 as mhfd
     res = []
     for shape in cands:
         try:
             det = mhfd.Detector(n, t_min, t_max, threshold=threshold, nms=nms, tile_shape=shape,
-                                timing=True)
+                                timing=True, response=response)
         except Exception as e:
             res.append((shape, None, str(e)))
             continue
@@ -164,18 +167,21 @@ def main():
     ap.add_argument("--widths", default="", help="extra strip widths off the menu, e.g. 312,344")
     ap.add_argument("--rbs", default="2,3,4,5,6,8", help="rows per step of the extra shapes")
     ap.add_argument("--groups", default="2,3,4,5", help="level groups of the extra shapes")
+    ap.add_argument("--response", default="dog", choices=["dog", "log"])
     ap.add_argument("--write", action="store_true", help="record the winner in tuned_tiles.json")
     args = ap.parse_args()
     nms = 0 if args.nms == "paper" else 1
-    cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None, args.min_width)
+    cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None, args.min_width,
+                       args.response)
     if args.widths:
         extra = width_candidates(args.n, args.tmin, args.tmax, nms,
                                  [int(w) for w in args.widths.split(",")],
                                  rbs=[int(v) for v in args.rbs.split(",")],
-                                 groups=[int(v) for v in args.groups.split(",")])
+                                 groups=[int(v) for v in args.groups.split(",")],
+                                 response=args.response)
         cands += [c for c in extra if c not in cands]
     t0 = time.time()
-    comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands)
+    comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands, response=args.response)
     print("compiled %d shapes in %.1f s" % (len(comp), time.time() - t0), flush=True)
     bad = {tuple(c) for c, _, e in comp if e}
     cands = [c for c in cands if tuple(c) not in bad]
@@ -186,7 +192,8 @@ def main():
     import synth
     img = synth.sweep_tile_4096_u16(0.0)[:args.side, :args.side].copy()
     dev = torch.from_numpy(img.view(np.int16)).cuda()
-    res = measure(args.n, args.tmin, args.tmax, nms, args.threshold, dev, cands)
+    res = measure(args.n, args.tmin, args.tmax, nms, args.threshold, dev, cands,
+                  response=args.response)
     res.sort(key=lambda r: (r[1] is None, r[1] or 0))
     for shape, ms, err in res:
         print("%-28s %s" % (shape, ("%.3f ms" % ms) if ms else err), flush=True)
@@ -195,7 +202,8 @@ def main():
     print("best", best, "SMs", sms)
     if args.write and best[1]:
         tab = load_table()
-        ent = tab.setdefault(ladder_key(args.n, args.tmin, args.tmax, nms), {})
+        ent = tab.setdefault(ladder_key(args.n, args.tmin, args.tmax, nms,
+                                        response=args.response), {})
         ent[str(sms)] = {"shape": list(best[0]), "ms": best[1], "side": args.side}
         with open(TABLE, "w") as f:
             json.dump(tab, f, indent=1, sort_keys=True)
