@@ -117,3 +117,21 @@ def test_heuristic_tile_is_one_vertical_round(native):
         dt = (kw["t_max"] - kw["t_min"]) / kw["n"]
         rmax = max(math.ceil(4 * (kw["t_min"] + i * dt)) for i in range(kw["n"] + 1))
         assert nt >= tx2 + 2 * rmax and rb * tx2 // 4 <= nt
+
+
+def test_tuned_shapes_are_valid_for_their_ladders(native):
+    """Every shape the autotuner recorded is accepted for its ladder and
+    response (fits shared memory, passes the range checks)."""
+    import json
+    import re
+    path = os.path.join(os.path.dirname(native.__file__), "tuned_tiles.json")
+    tab = json.load(open(path))
+    assert tab
+    for key, ent in tab.items():
+        m = re.match(r"n(\d+)_t([0-9.e+-]+)-([0-9.e+-]+)_(paper|local26)_tr4(_log)?$", key)
+        assert m, key
+        kw = dict(n=int(m.group(1)), t_min=float(m.group(2)), t_max=float(m.group(3)),
+                  nms=m.group(4), response="log" if m.group(5) else "dog")
+        for best in ent.values():
+            shape = tuple(best["shape"])
+            assert native.chosen_tile(tile_shape=shape, **kw) == shape
