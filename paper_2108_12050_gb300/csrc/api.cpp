@@ -62,7 +62,6 @@ struct mhfd_detector {
     Counters *cnt = nullptr;
     double *d_radius = nullptr;
     float *d_sigma = nullptr, *d_radius_f = nullptr, *d_taps = nullptr, *d_tsc = nullptr;
-    int *d_tapoff = nullptr;
     int *block_tmp = nullptr;
     double *block_sum = nullptr;
     double *soft_part = nullptr;   // per-block layer sums of the soft score
@@ -279,8 +278,6 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
                  size_t pitch, cudaStream_t s, float *d_D, float *d_M, int *d_A) {
     int tx, ty;
     const int n_tiles = tiles_of(d, H, W, &tx, &ty);
-    const size_t nl = d->R.size();
-    (void)nl;
     if ((size_t)v->param_bytes < sizeof(MhfdKHeader) || v->ntaps != (int)d->lk.taps.size())
         return fail(MHFD_ERR_JIT, "kernel parameter layout mismatch");
     d->params.assign((v->param_bytes + 7) / 8 + 1, 0);
@@ -376,7 +373,7 @@ void release(mhfd_detector *d) {
     DeviceGuard g(d->device);
     if (d->pending && d->ev_done) cudaEventSynchronize(d->ev_done);
     void *dev_ptrs[] = {d->sel, d->st, d->cnt, d->d_radius, d->d_sigma, d->d_radius_f, d->d_taps,
-                        d->d_tsc, d->d_tapoff, d->block_tmp, d->block_sum, d->cand, d->tile_count,
+                        d->d_tsc, d->block_tmp, d->block_sum, d->cand, d->tile_count,
                         d->tile_off, d->stage, d->pb.cell_cnt, d->pb.cell_start, d->pb.cell_items,
                         d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->d_blobs, d->d_cands,
                         d->soft_part, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy,
@@ -744,7 +741,7 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
     if ((rc = dalloc(&d->sel, 1)) || (rc = dalloc(&d->st, 1)) || (rc = dalloc(&d->cnt, 1)) ||
         (rc = dalloc(&d->d_radius, 64)) || (rc = dalloc(&d->d_sigma, 64)) ||
         (rc = dalloc(&d->d_radius_f, 64)) || (rc = dalloc(&d->d_taps, d->taps.size())) ||
-        (rc = dalloc(&d->d_tsc, nl)) || (rc = dalloc(&d->d_tapoff, nl + 1)) ||
+        (rc = dalloc(&d->d_tsc, nl)) ||
         (rc = dalloc(&d->block_tmp, 256 + 64)) || (rc = dalloc(&d->block_sum, 256 + 1)) ||
         (rc = dalloc(&d->cand, (size_t)d->cap)) || (rc = dalloc(&d->pb.cell_items, (size_t)d->cap)) ||
         (rc = dalloc(&d->pb.state, (size_t)d->cap)) ||
@@ -759,8 +756,7 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
         cudaMemcpy(d->d_sigma, sig.data(), 64 * sizeof(float), cudaMemcpyHostToDevice) ||
         cudaMemcpy(d->d_radius_f, radf.data(), 64 * sizeof(float), cudaMemcpyHostToDevice) ||
         cudaMemcpy(d->d_taps, d->taps.data(), d->taps.size() * sizeof(float), cudaMemcpyHostToDevice) ||
-        cudaMemcpy(d->d_tsc, d->tsc.data(), nl * sizeof(float), cudaMemcpyHostToDevice) ||
-        cudaMemcpy(d->d_tapoff, d->tapoff.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice)) {
+        cudaMemcpy(d->d_tsc, d->tsc.data(), nl * sizeof(float), cudaMemcpyHostToDevice)) {
         release(d);
         return fail(MHFD_ERR_CUDA, "uploading ladder tables failed");
     }
@@ -896,7 +892,7 @@ int mhfd_detect_plain(mhfd_detector *d, const void *img, int32_t dtype, int32_t 
     const int cap_tile = d->p.nms == MHFD_NMS_PAPER ? 256 : 1024;
     int n_tiles = 0;
     rc = enqueue_plain(img, dtype, H, W, (long long)pitch, d->st, (int)d->R.size(), d->R,
-                       d->d_taps, d->d_tapoff, d->d_tsc, d->p.nms, d->p.threshold, d->pI, d->pT,
+                       d->d_taps, d->d_tsc, d->p.nms, d->p.threshold, d->pI, d->pT,
                        d->pL, d->pM, d->pA, d->pD, d->tile_count, d->stage, cap_tile,
                        d->p.response, d->p.boundary, &n_tiles, s);
     if (rc) return rc;

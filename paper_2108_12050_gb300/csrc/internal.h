@@ -193,7 +193,7 @@ int enqueue_stack(const void *img, int dtype, int H, int W, long long pitch, con
                   float *scratch_T, float *scratch_L, cudaStream_t s, int boundary = 0);
 int enqueue_plain(const void *img, int dtype, int H, int W, long long pitch,
                   const MhfdStretch *st, int n_levels, const std::vector<int> &R,
-                  const float *d_taps, const int *d_tapoff, const float *d_tsc, int mode,
+                  const float *d_taps, const float *d_tsc, int mode,
                   float thr, float *scratch_I, float *scratch_T, float *scratch_L,
                   float *scratch_M, int *scratch_A, float *scratch_D, int *tile_count,
                   MhfdCand *stage, int cap_tile, int response, int boundary, int *n_tiles_out,
