@@ -54,6 +54,31 @@ def test_batch_equals_single_detections():
     det.close()
 
 
+@pytest.mark.parametrize("kw", [{"response": "log", "threshold": 0.05 / 0.6875},
+                                {"boundary": "periodic"},
+                                {"nms": "local26", "boundary": "periodic"}])
+def test_batch_equals_single_detections_for_variants(kw):
+    """The same identity for the compiled variants (LoG response, periodic
+    boundary, 26-neighbour rule)."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2108_12050_gb300 as mhfd
+    torch.cuda.set_device(0)
+    imgs = _batch_images()[:4]
+    devs = [_dev(i) for i in imgs]
+    params = dict(threshold=0.05, overlap=0.5)
+    params.update(kw)
+    det = mhfd.Detector(16, 1.0, 12.0, **params)
+    singles = [det(d) for d in devs]
+    for rep in range(2):
+        det.detect_batch(devs)
+        outs = det.wait_batch()
+        for s, o in zip(singles, outs):
+            assert o.n_blobs == s.n_blobs and o.n_candidates_true == s.n_candidates_true
+            assert np.array_equal(o.blobs, s.blobs)
+    det.close()
+
+
 def test_batch_reports_graph_use():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")

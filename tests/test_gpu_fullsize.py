@@ -134,6 +134,36 @@ def test_full_size_prune_and_score(full):
     assert np.array_equal(res.per_scale, per_scale)
 
 
+def test_maximum_size_8192_uint8_sampled_against_oracle():
+    """The largest tiles the service takes (8192^2, uint8): stretch bounds
+    bit-exact, sampled candidates' responses and scales against the oracle,
+    counts consistent, and the prune of the GPU's list equal to the
+    oracle's."""
+    import paper_2108_12050_gb300 as mhfd
+    img = synth.sweep_tile_4096_u16(0.0, seed=8192, H=8192, W=8192, dtype="u8")
+    det = mhfd.Detector(N, TMIN, TMAX, threshold=THR, overlap=OVERLAP, keep_candidates=True)
+    res = det(torch.from_numpy(img).cuda())
+    det.close()
+    lo, hi = oracle.stretch_bounds(img)
+    assert (res.lo, res.hi) == (lo, hi)
+    cands = res.candidates
+    assert res.n_candidates == res.n_candidates_true == len(cands) > 10000
+    rng = np.random.default_rng(13)
+    pick = rng.choice(len(cands), 200, replace=False)
+    t = oracle.ladder(N, TMIN, TMAX)
+    D = oracle.dog_at(img, lo, hi, t, cands["x"][pick].astype(int), cands["y"][pick].astype(int))
+    eps_i = 1e-4 * np.abs(D).max(axis=0)
+    for k, j in enumerate(pick):
+        i = int(cands["scale_idx"][j])
+        assert abs(float(cands["response"][j]) - D[k, i]) <= eps_i[i], (k, i)
+        srt = np.sort(D[k])
+        assert i == int(D[k].argmax()) or srt[-1] - srt[-2] <= eps_i.max()
+    radius = math.sqrt(2.0) * t[:N]
+    keep = oracle.prune(cands["x"], cands["y"], cands["scale_idx"],
+                        cands["response"].astype(np.float64), radius, OVERLAP, img.shape[1])
+    assert res.n_blobs == res.focus_score == int(keep.sum())
+
+
 def test_soft_score_full_size_2048_float32():
     import paper_2108_12050_gb300 as mhfd
     from paper_2108_12050_gb300 import soft
