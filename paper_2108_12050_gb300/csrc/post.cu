@@ -122,22 +122,46 @@ __global__ void grid_count(const MhfdCand *cand, const Counters *cnt, int cs, in
     }
 }
 
-// Cell starts (exclusive scan of the counts) in one block, a coalesced
-// pass of block scans; the counts are reset to serve as fill cursors.
+// Cell starts (exclusive scan of the counts) in one block: rounds of
+// kCellChunk cells are staged in shared memory with coalesced accesses, each
+// thread scans a contiguous run of kCellChunk / kScanThreads cells serially
+// (the index padded by one word per 32 so that the runs do not share banks)
+// and one block scan joins the runs.  The counts are reset to serve as fill
+// cursors.
+constexpr int kCellChunk = 8192;
+__device__ __forceinline__ int cell_pad(int i) { return i + (i >> 5); }
+
 __global__ void __launch_bounds__(kScanThreads)
     grid_scan(int *cell_cnt, int ncells, int *cell_start) {
+    __shared__ int sc[kCellChunk + kCellChunk / 32];
     __shared__ long long sh[32];
+    constexpr int per = kCellChunk / kScanThreads;
     long long carry = 0;
-    for (int base = 0; base < ncells; base += blockDim.x) {
-        const int c = base + threadIdx.x;
-        const long long v = c < ncells ? cell_cnt[c] : 0;
+    for (int base = 0; base < ncells; base += kCellChunk) {
+        const int n = min(kCellChunk, ncells - base);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sc[cell_pad(i)] = cell_cnt[base + i];
+        __syncthreads();
+        const int beg = threadIdx.x * per;
+        long long loc = 0;
+#pragma unroll
+        for (int k = 0; k < per; ++k)
+            if (beg + k < n) loc += sc[cell_pad(beg + k)];
         long long tot;
-        const long long ex = block_scan_excl_ll(v, sh, &tot);
-        if (c < ncells) {
-            cell_start[c] = (int)(carry + ex);
-            cell_cnt[c] = 0;
+        long long run = carry + block_scan_excl_ll(loc, sh, &tot);
+#pragma unroll
+        for (int k = 0; k < per; ++k)
+            if (beg + k < n) {
+                const int v = sc[cell_pad(beg + k)];
+                sc[cell_pad(beg + k)] = (int)run;
+                run += v;
+            }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            cell_start[base + i] = sc[cell_pad(i)];
+            cell_cnt[base + i] = 0;  // reused as the fill cursor
         }
         carry += tot;
+        __syncthreads();
     }
     if (threadIdx.x == 0) cell_start[ncells] = (int)carry;
 }
