@@ -74,16 +74,16 @@ struct RunAcc {
 
 // Histogram accumulation of one pass over rows [y0, H) step ystep of one
 // image into the block's shared histograms.
-template <int DT, int BITS>
-__device__ __forceinline__ void hist_rows(const char *img, int H, int W, long long pitch,
-                                          int pass, const SelState *sel, int y0, int ystep,
-                                          HistSmem *hs) {
+template <int DT, int BITS, bool FIRST>
+__device__ __forceinline__ void hist_rows_p(const char *img, int H, int W, long long pitch,
+                                            int pass, const SelState *sel, int y0, int ystep,
+                                            HistSmem *hs) {
     unsigned *h[2] = {hs->v[0][threadIdx.x % kRep], hs->v[1][threadIdx.x % kRep]};
     constexpr int ES = DT == 0 ? 1 : (DT == 1 ? 2 : 4);
     constexpr int VEC = 16 / ES;
-    const int shift = BITS - 8 * (pass + 1);
+    constexpr bool first = FIRST;  // the first pass counts every pixel for both targets
+    const int shift = FIRST ? BITS - 8 : BITS - 8 * (pass + 1);
     const unsigned p0 = sel->prefix[0], p1 = sel->prefix[1];
-    const bool first = (pass == 0);
     const bool vec_ok = ((reinterpret_cast<unsigned long long>(img) | (unsigned long long)pitch) & 15ull) == 0;
     RunAcc r0, r1;
     auto take = [&](unsigned key) {
@@ -157,6 +157,16 @@ __device__ __forceinline__ void hist_rows(const char *img, int H, int W, long lo
     }
     r0.flush(h[0]);
     r1.flush(h[1]);
+}
+
+template <int DT, int BITS>
+__device__ __forceinline__ void hist_rows(const char *img, int H, int W, long long pitch,
+                                          int pass, const SelState *sel, int y0, int ystep,
+                                          HistSmem *hs) {
+    if (pass == 0)
+        hist_rows_p<DT, BITS, true>(img, H, W, pitch, pass, sel, y0, ystep, hs);
+    else
+        hist_rows_p<DT, BITS, false>(img, H, W, pitch, pass, sel, y0, ystep, hs);
 }
 
 __device__ __forceinline__ void hist_clear(HistSmem *hs) {
