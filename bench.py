@@ -434,9 +434,10 @@ def main():
 
 def bench_variants(mhfd, torch, stream, tile, reps=5):
     """The paper's variants on the in-focus 4096^2 tile: the periodic
-    boundary and the explicit scale-normalised Laplacian response (threshold
-    divided by dt), on the fused and the plain path, next to the default
-    detection; CUDA events, median of `reps`."""
+    boundary, the explicit scale-normalised Laplacian response (threshold
+    divided by dt) and the 3x3x3 scale-space maxima, on the fused and the
+    plain path, next to the default detection; CUDA events, median of
+    `reps`."""
     dt = (T_MAX - T_MIN) / N_LAYERS
 
     def timed(det, plain):
@@ -463,7 +464,11 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
         "fused_reflect": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), False),
         "fused_periodic": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, boundary="periodic",
                                               **kw), False),
+        "fused_local26": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX,
+                                             **dict(kw, nms="local26")), False),
         "plain_dog": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), True),
+        "plain_local26": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX,
+                                             **dict(kw, nms="local26")), True),
         "fused_log": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, response="log",
                                          **dict(kw, threshold=THR / dt)), False),
         "plain_log": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, response="log",
