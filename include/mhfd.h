@@ -266,8 +266,9 @@ int mhfd_prune_noalloc(const double *radius, int32_t n_levels, float overlap, co
 
 /* Tile configurations the fused kernel can be specialised with for the
  * ladder of `p` (autotuner menu): returns their count; if `desc` is not NULL
- * writes up to `cap` rows of five int32 (tile width and height including the
- * one-pixel NMS border, rows per step, threads per block, level groups).
+ * writes up to `cap` rows of five int32 (strip width and tile height, both
+ * including the one-pixel NMS border, rows per step, threads per block,
+ * level groups).
  * Row k is selected by params.tile_override = k + 1.  Host only. */
 int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap);
 
