@@ -156,7 +156,20 @@ constexpr int VROW = vrow_max();
 constexpr int SMEM_IN = BROWS * WEXTP;
 constexpr int SMEM_V = RB * VROW;
 constexpr int SMEM_RING_F = MODE == 0 ? RING * TX2 : MODE == 1 ? RING * NDOG * TX2 : 0;
-constexpr int SMEM_RING_B = MODE == 0 ? ((RING * TX2 + 15) & ~15) : 0;
+// per-pixel side data of the ring rows: the argmax (paper rule) or the mask
+// of layers above the threshold (26-neighbour rule)
+template <bool WIDE>
+struct MaskT {
+    using T = unsigned;
+};
+template <>
+struct MaskT<true> {
+    using T = unsigned long long;
+};
+using LMask = MaskT<(NDOG > 32)>::T;
+constexpr int SMEM_RING_B = MODE == 0   ? ((RING * TX2 + 15) & ~15)
+                            : MODE == 1 ? ((RING * TX2 * (int)sizeof(LMask) + 15) & ~15)
+                                        : 0;
 constexpr int SMEM_BYTES = 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64;
 
 static_assert(TX2 % 4 == 0, "tile width must be a multiple of 4");
@@ -177,6 +190,7 @@ struct HState {
     float lp[4];  // L of the previous level
     float m[4];   // running max over scales
     int a[4];     // its first argmax
+    LMask mk[4];  // 26-neighbour rule: layers whose response is above the threshold
     // soft-score forward: running sums over the march of sigmoid((D_i -
     // tau) / T) at this item's interior output pixels, per layer
     float soft[NSOFT];
@@ -516,6 +530,7 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
             st.lp[u] = a[u];
             st.m[u] = -__int_as_float(0x7f800000);
             st.a[u] = 0;
+            st.mk[u] = 0;
         }
     } else {
         constexpr int I = LOG ? L : (L > 0 ? L - 1 : 0);  // response layer
@@ -529,6 +544,7 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
                 for (int u = 0; u < 4; ++u) {
                     st.m[u] = -__int_as_float(0x7f800000);
                     st.a[u] = 0;
+                    st.mk[u] = 0;
                 }
             }
         } else {
@@ -560,6 +576,9 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
             o.z = cx.inb[2] ? d[2] : ninf;
             o.w = cx.inb[3] ? d[3] : ninf;
             reinterpret_cast<float4 *>(s_ring + (cx.slot * NDOG + I) * TX2)[cx.q] = o;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cx.inb[u] && d[u] > h.thr) st.mk[u] |= LMask(1) << I;
         }
         if (STORE) {
 #pragma unroll
@@ -646,6 +665,11 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
                             if (h.arg_out) h.arg_out[o2] = hs[it].a[u];
                         }
                 }
+            }
+            if (G == NGROUPS - 1 && MODE == 1) {
+                LMask *mrow = reinterpret_cast<LMask *>(s_arg) + cx.slot * TX2 + 4 * cx.q;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) mrow[u] = hs[it].mk[u];
             }
         }
     }
@@ -734,57 +758,64 @@ __device__ __forceinline__ bool cand_26(const float *s_ring, int r, int c, int l
 }
 
 // Candidates of chunk rows [ra, rb] (all in one tile) appended after `total`
-// candidates of that tile's slots; returns the tile's new count.
+// candidates of that tile's slots; returns the tile's new count.  Items are
+// the pixels of the rows in row-major order; under the 26-neighbour rule a
+// pixel's layers above the threshold (its mask) are tested in ascending
+// order, so candidates come out ordered by row, column, layer.
 __device__ __forceinline__ int nms_rows(const MhfdKHeader &h, const March &m,
                                         const float *s_ring, const unsigned char *s_arg,
                                         int *s_scan, int ra, int rb, long long slot, int total) {
     const int nrows = rb - ra + 1;
-    const int per = (MODE == 0) ? TX : TX * NDOG;
-    const int items = nrows * per;
+    const int items = nrows * TX;
     const int ch = (items + NT - 1) / NT;
     const int beg = min(items, (int)threadIdx.x * ch);
     const int end = min(items, beg + ch);
     const float thr = h.thr;
+    const LMask *s_mask = reinterpret_cast<const LMask *>(s_arg);
     int cnt = 0;
     for (int it = beg; it < end; ++it) {
-        const int r = ra + it / per;
-        const int rem = it - (it / per) * per;
+        const int r = ra + it / TX;
+        const int c = 1 + (it - (it / TX) * TX);
         float v;
         if (MODE == 0) {
-            cnt += cand_paper(s_ring, r, 1 + rem, thr, &v) ? 1 : 0;
+            cnt += cand_paper(s_ring, r, c, thr, &v) ? 1 : 0;
         } else {
-            cnt += cand_26(s_ring, r, 1 + rem / NDOG, rem % NDOG, thr, &v) ? 1 : 0;
+            LMask mk = s_mask[(r % RING) * TX2 + c];
+            while (mk) {
+                const int l = NDOG > 32 ? __ffsll((long long)mk) - 1 : __ffs((int)mk) - 1;
+                mk &= mk - 1;
+                cnt += cand_26(s_ring, r, c, l, thr, &v) ? 1 : 0;
+            }
         }
     }
     int sum;
     int pos = total + block_excl_scan(cnt, s_scan, &sum);
     if (cnt) {
         MhfdCand *dst = h.stage + slot * h.cap_tile;
-        for (int it = beg; it < end; ++it) {
-            const int r = ra + it / per;
-            const int rem = it - (it / per) * per;
-            float v;
-            bool ok;
-            int c, l;
-            if (MODE == 0) {
-                c = 1 + rem;
-                ok = cand_paper(s_ring, r, c, thr, &v);
-                l = s_arg[(r % RING) * TX2 + c];
-            } else {
-                c = 1 + rem / NDOG;
-                l = rem % NDOG;
-                ok = cand_26(s_ring, r, c, l, thr, &v);
+        auto put = [&](int r, int c, int l, float v) {
+            if (pos < h.cap_tile) {
+                MhfdCand cd;
+                cd.x = m.x0 - 1 + c;
+                cd.y = m.yb + r;
+                cd.i = l;
+                cd.resp = v;
+                dst[pos] = cd;
             }
-            if (ok) {
-                if (pos < h.cap_tile) {
-                    MhfdCand cd;
-                    cd.x = m.x0 - 1 + c;
-                    cd.y = m.yb + r;
-                    cd.i = l;
-                    cd.resp = v;
-                    dst[pos] = cd;
+            ++pos;
+        };
+        for (int it = beg; it < end; ++it) {
+            const int r = ra + it / TX;
+            const int c = 1 + (it - (it / TX) * TX);
+            float v;
+            if (MODE == 0) {
+                if (cand_paper(s_ring, r, c, thr, &v)) put(r, c, s_arg[(r % RING) * TX2 + c], v);
+            } else {
+                LMask mk = s_mask[(r % RING) * TX2 + c];
+                while (mk) {
+                    const int l = NDOG > 32 ? __ffsll((long long)mk) - 1 : __ffs((int)mk) - 1;
+                    mk &= mk - 1;
+                    if (cand_26(s_ring, r, c, l, thr, &v)) put(r, c, l, v);
                 }
-                ++pos;
             }
         }
     }

@@ -212,7 +212,10 @@ int smem_fixed(const std::vector<int> &R, int mode, const TileConfig &c) {
     // 3 (level blur): none
     const int ring = c.rb + 2;
     const int ring_f = base == 0 ? ring * c.tx2 : base == 1 ? ring * layers * c.tx2 : 0;
-    const int ring_b = base == 0 ? ((ring * c.tx2 + 15) & ~15) : 0;
+    const int mask_bytes = layers > 32 ? 8 : 4;
+    const int ring_b = base == 0   ? ((ring * c.tx2 + 15) & ~15)
+                       : base == 1 ? ((ring * c.tx2 * mask_bytes + 15) & ~15)
+                                   : 0;
     return 4 * (c.rb * vrow + ring_f) + ring_b + 4 * 64;
 }
 
