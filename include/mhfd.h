@@ -94,6 +94,17 @@ typedef struct {
                                score (DoG only) supports both */
     int32_t boundary;       /* mhfd_boundary; every entry point but the soft
                                score (reflect only) supports both */
+    int32_t tensor_cores;   /* 1: the fused kernel's vertical blur runs on the
+                               tensor cores (tcgen05, fp16 operands that hold
+                               the window exactly and the taps as two parts,
+                               f32 accumulation) for DoG detection of uint8
+                               images and of uint16 images whose stretch range
+                               hi - lo is at most 4095; other images and modes
+                               take the FFMA kernel (same results within the
+                               FP32 tolerance).  tile_shape / tile_override
+                               then describe the tensor-core kernel (four rows
+                               per step, threads a multiple of 128).  0: FFMA
+                               only.  Default 0 */
 } mhfd_params;
 
 /* A detected feature.  scale_idx is the 0-based DoG layer i-1; sigma = t_i,
@@ -171,6 +182,10 @@ int mhfd_detect_batch(mhfd_detector *det, int32_t n, const void *const *d_imgs,
  * next batch; candidate lists are not kept for batches.  Returns MHFD_OK,
  * MHFD_WARN_OVERFLOW if any image overflowed, or an error. */
 int mhfd_result_wait_batch(mhfd_detector *det, mhfd_result *outs, int32_t n);
+
+/* 1 if the detector runs the tensor-core vertical pass (params.tensor_cores
+ * and a DoG detection mode), 0 if not, negative on error.  Host only. */
+int mhfd_uses_tensor_cores(mhfd_detector *det);
 
 /* 1 if the last batch ran from a captured CUDA graph, 0 if its kernels were
  * launched directly. */

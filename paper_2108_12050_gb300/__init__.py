@@ -118,13 +118,16 @@ class Detector:
     maximum rule (``"paper"``: argmax over scales then 3x3 max-pool;
     ``"local26"``: 3x3x3 scale-space maxima), the kernel truncation and the
     stretch saturation fraction.  ``sigmas`` gives an explicit ladder of
-    ``n+1`` scales instead.
+    ``n+1`` scales instead.  ``tensor_cores=True`` runs the vertical blur of
+    the fused kernel on the tensor cores (DoG detection of uint8 images and
+    of uint16 images whose stretch range is at most 4095; the FFMA kernel
+    takes everything else).
     """
 
     def __init__(self, n=10, t_min=1.0, t_max=10.0, *, sigmas=None, threshold=0.1, overlap=0.5,
                  nms="paper", truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
                  device=None, keep_candidates=False, tile_override=None, tile_shape=None,
-                 timing=False, response="dog", boundary="reflect"):
+                 timing=False, response="dog", boundary="reflect", tensor_cores=False):
         import torch
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
@@ -135,7 +138,8 @@ class Detector:
                 from . import tune
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
                 tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate,
-                                         "log" if response in ("log", 1) else "dog")
+                                         "log" if response in ("log", 1) else "dog",
+                                         tensor_cores=bool(tensor_cores))
         tile_override = tile_override or 0
         self.n = int(n)
         self.device = device
@@ -145,11 +149,16 @@ class Detector:
                                  max_candidates=max_candidates, device=device,
                                  keep_candidates=keep_candidates, tile_override=tile_override,
                                  tile_shape=tile_shape, timing=timing, response=response,
-                                 boundary=boundary)
+                                 boundary=boundary, tensor_cores=tensor_cores)
         h = ctypes.c_void_p()
         _n.check(_n.lib().mhfd_create_detector(ctypes.byref(self._p), ctypes.byref(h)))
         self._h = h
         self._img_ref = None
+
+    @property
+    def uses_tensor_cores(self):
+        """Whether the fused kernel's vertical pass runs on the tensor cores."""
+        return bool(_n.lib().mhfd_uses_tensor_cores(self._h))
 
     # --------------------------------------------------------------- core
     def close(self):

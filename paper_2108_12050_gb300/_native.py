@@ -28,6 +28,7 @@ NMS_PAPER, NMS_LOCAL26 = 0, 1
 EXPORTS = [
     "mhfd_default_params", "mhfd_create_detector", "mhfd_destroy_detector", "mhfd_detect",
     "mhfd_result_wait", "mhfd_detect_batch", "mhfd_result_wait_batch", "mhfd_batch_uses_graph",
+    "mhfd_uses_tensor_cores",
     "mhfd_result_ready", "mhfd_soft_score",
     "mhfd_detect_host", "mhfd_detect_host_async", "mhfd_detect_plain", "mhfd_debug_stack",
     "mhfd_prune", "mhfd_prune_noalloc", "mhfd_tile_configs", "mhfd_chosen_tile", "mhfd_precompile",
@@ -60,6 +61,7 @@ class Params(ctypes.Structure):
         ("timing", ctypes.c_int32),
         ("response", ctypes.c_int32),
         ("boundary", ctypes.c_int32),
+        ("tensor_cores", ctypes.c_int32),
     ]
 
 
@@ -112,6 +114,7 @@ def lib():
         L.mhfd_detect_batch.argtypes = [P, I32, P, P, P, P, P, P]
         L.mhfd_result_wait_batch.argtypes = [P, ctypes.POINTER(Result), I32]
         L.mhfd_batch_uses_graph.argtypes = [P]
+        L.mhfd_uses_tensor_cores.argtypes = [P]
         L.mhfd_result_ready.argtypes = [P]
         L.mhfd_soft_score.argtypes = [P, P, I32, I32, I32, SZ, P, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_float, P, P, P, P, P]
@@ -145,7 +148,7 @@ def check(rc, allow_overflow=True):
 def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap=0.5,
                 nms=NMS_PAPER, truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
                 device=-1, keep_candidates=False, tile_override=0, tile_shape=None, timing=False,
-                response=0, boundary=0):
+                response=0, boundary=0, tensor_cores=False):
     p = Params()
     lib().mhfd_default_params(ctypes.byref(p))
     p.n = int(n)
@@ -177,6 +180,7 @@ def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap
         boundary = {"reflect": 0, "periodic": 1}[boundary]
     p.response = int(response)
     p.boundary = int(boundary)
+    p.tensor_cores = 1 if tensor_cores else 0
     p._keepalive = keep
     return p
 

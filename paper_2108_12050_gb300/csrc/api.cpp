@@ -44,10 +44,16 @@ struct mhfd_detector {
     std::vector<float> tsc;      // t_l as f32 (DoG factor)
     std::vector<double> radius;  // blob radius per DoG layer, sqrt(2) t_i
     double radius_max = 0.0;
-    TileConfig cfg;
+    TileConfig cfg;              // FFMA kernel (the tile grid both kernels share)
     LadderKey lk;
     Variant *var = nullptr;
     Variant *var_store = nullptr;
+    // tensor-core vertical pass (params.tensor_cores): same tile grid as cfg;
+    // takes uint8 and narrow-range uint16 images, the FFMA kernel the rest
+    bool use_tc = false;
+    TileConfig cfg_tc;
+    Variant *var_tc = nullptr;
+    Variant *var_tc_store = nullptr;
     Variant *var_soft = nullptr;  // soft-score forward (kernel mode 2)
     // soft-score adjoint: one single-level blur kernel (mode 3) per level
     std::vector<Variant *> var_level;
@@ -199,6 +205,8 @@ int validate_params(const mhfd_params &p) {
         return fail(MHFD_ERR_INVALID_ARG, "response must be MHFD_RESPONSE_DOG or MHFD_RESPONSE_LOG");
     if (p.boundary != MHFD_BOUNDARY_REFLECT && p.boundary != MHFD_BOUNDARY_PERIODIC)
         return fail(MHFD_ERR_INVALID_ARG, "boundary must be reflect or periodic");
+    if (p.tensor_cores != 0 && p.tensor_cores != 1)
+        return fail(MHFD_ERR_INVALID_ARG, "tensor_cores must be 0 or 1");
     return MHFD_OK;
 }
 
@@ -275,7 +283,7 @@ long long clip_rank(const mhfd_detector *d, int H, int W) {
 
 // fill and launch the fused kernel
 int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H, int W,
-                 size_t pitch, cudaStream_t s, float *d_D, float *d_M, int *d_A) {
+                 size_t pitch, cudaStream_t s, float *d_D, float *d_M, int *d_A, int gate = 0) {
     int tx, ty;
     const int n_tiles = tiles_of(d, H, W, &tx, &ty);
     if ((size_t)v->param_bytes < sizeof(MhfdKHeader) || v->ntaps != (int)d->lk.taps.size())
@@ -301,6 +309,8 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
     h.total_items = n_tiles;
     h.cap_tile = d->cap_tile;
     h.thr = d->p.threshold;
+    h.gate = gate;
+    h.flag = &d->cnt->ktimeout;
     std::memcpy(pb, &h, sizeof(h));
     void *args[] = {pb};
     // one resident wave: every block marches down an equal share of tiles
@@ -342,13 +352,18 @@ int detect_impl(mhfd_detector *d, const void *img, int dtype, int H, int W, size
     int rc = check_image(img, dtype, H, W, pitch);
     if (rc) return rc;
     DeviceGuard g(d->device);
-    Variant *v = d->var;
+    Variant *v = d->var, *vt = d->var_tc;
     if (store) {
         if (!d->var_store) {
             rc = get_variant(d->lk, d->p.nms, 1, d->cfg, &d->var_store);
             if (rc) return rc;
         }
         v = d->var_store;
+        if (d->use_tc && !d->var_tc_store) {
+            rc = get_variant(d->lk, d->p.nms, 1, d->cfg_tc, &d->var_tc_store);
+            if (rc) return rc;
+        }
+        vt = d->var_tc_store;
     }
     if ((rc = ensure_image_capacity(d, H, W, false))) return rc;
     d->timed = d->p.timing != 0;
@@ -356,7 +371,18 @@ int detect_impl(mhfd_detector *d, const void *img, int dtype, int H, int W, size
     rc = enqueue_stretch(img, dtype, H, W, (long long)pitch, clip_rank(d, H, W), d->sel, d->st, s);
     if (rc) return rc;
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k0, s));
-    if ((rc = launch_fused(d, v, img, dtype, H, W, pitch, s, d_D, d_M, d_A))) return rc;
+    if (d->use_tc && dtype != MHFD_F32) {
+        // uint8 always fits the tensor-core pass; a uint16 image does when
+        // its stretch range does (decided on the device: both kernels are
+        // launched, gated, and one of them returns at once)
+        const bool gated = dtype == MHFD_U16;
+        if ((rc = launch_fused(d, vt, img, dtype, H, W, pitch, s, d_D, d_M, d_A, gated ? 1 : 0)))
+            return rc;
+        if (gated && (rc = launch_fused(d, v, img, dtype, H, W, pitch, s, d_D, d_M, d_A, 2)))
+            return rc;
+    } else if ((rc = launch_fused(d, v, img, dtype, H, W, pitch, s, d_D, d_M, d_A))) {
+        return rc;
+    }
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k1, s));
     int tx, ty;
     const int n_tiles = tiles_of(d, H, W, &tx, &ty);
@@ -439,8 +465,37 @@ void fused_ladder(const mhfd_params &p, const std::vector<double> &t, const std:
     }
 }
 
-int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, TileConfig *cfg) {
+int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, TileConfig *cfg,
+                 bool tc = false) {
     std::string why;
+    if (tc) {
+        if (p.tile_shape[0] > 0) {
+            const int *ts = p.tile_shape;
+            const int nl = (int)R.size();
+            if (ts[0] % 4 || ts[0] < 8 || ts[0] > 2048 || ts[1] < 3 || ts[1] > 4096 ||
+                ts[4] < 1 || ts[4] > nl)
+                return fail(MHFD_ERR_INVALID_ARG, "tile_shape out of range");
+            cfg->tx2 = ts[0];
+            cfg->ty2 = ts[1];
+            cfg->rb = ts[2];
+            cfg->nt = ts[3];
+            cfg->gb.assign(ts[4] + 1, 0);
+            for (int g = 0; g <= ts[4]; ++g) cfg->gb[g] = (int)((long long)nl * g / ts[4]);
+            cfg->tc = 1;
+            if (!tc_shape_ok(R, mode, *cfg, &why))
+                return fail(MHFD_ERR_UNSUPPORTED, "tile_shape (tensor cores): " + why);
+            return MHFD_OK;
+        }
+        if (p.tile_override > 0) {
+            const std::vector<TileConfig> menu = tile_menu_tc(R, mode);
+            if (p.tile_override > (int)menu.size())
+                return fail(MHFD_ERR_INVALID_ARG, "tile_override out of range");
+            *cfg = menu[p.tile_override - 1];
+            return MHFD_OK;
+        }
+        if (!choose_tile_tc(R, mode, cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+        return MHFD_OK;
+    }
     if (p.tile_shape[0] > 0) {
         const int *ts = p.tile_shape;
         const int nl = (int)R.size();
@@ -685,6 +740,7 @@ void mhfd_default_params(mhfd_params *p) {
     p->timing = 0;
     p->response = MHFD_RESPONSE_DOG;
     p->boundary = MHFD_BOUNDARY_REFLECT;
+    p->tensor_cores = 0;
 }
 
 const char *mhfd_last_error(void) { return mhfd::t_err.c_str(); }
@@ -717,7 +773,20 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
     fused_ladder(d->p, d->t, d->R, &d->lk, &tile_mode);
     for (int i = 0; i < d->n; ++i) d->radius.push_back(std::sqrt(2.0) * d->t[i]);
     d->radius_max = d->radius[d->n - 1];
-    if ((rc = resolve_tile(d->lk.R, tile_mode, d->p, &d->cfg))) {
+    d->use_tc = d->p.tensor_cores != 0 && tc_mode_ok(tile_mode);
+    if (d->use_tc) {
+        // the tensor-core kernel's shape (tile_shape / tile_override refer to
+        // it), and an FFMA companion on the same tile grid
+        if ((rc = resolve_tile(d->lk.R, tile_mode, d->p, &d->cfg_tc, true))) {
+            delete d;
+            return rc;
+        }
+        if (!companion_tile(d->lk.R, tile_mode, d->cfg_tc, &d->cfg)) {
+            delete d;
+            return fail(MHFD_ERR_UNSUPPORTED,
+                        "no FFMA tile shape shares the tensor-core kernel's strip width");
+        }
+    } else if ((rc = resolve_tile(d->lk.R, tile_mode, d->p, &d->cfg))) {
         delete d;
         return rc;
     }
@@ -727,7 +796,8 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
     const int TXY = (d->cfg.tx2 - 2) * (d->cfg.ty2 - 2);
     d->cap_tile = d->p.nms == MHFD_NMS_PAPER ? (TXY + 7) / 8 : (TXY + 1) / 2;
     d->cap = d->p.max_candidates;
-    if ((rc = get_variant(d->lk, d->p.nms, 0, d->cfg, &d->var))) {
+    if ((rc = get_variant(d->lk, d->p.nms, 0, d->cfg, &d->var)) ||
+        (d->use_tc && (rc = get_variant(d->lk, d->p.nms, 0, d->cfg_tc, &d->var_tc)))) {
         delete d;
         return rc;
     }
@@ -752,7 +822,8 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
         release(d);
         return rc;
     }
-    if (cudaMemcpy(d->d_radius, rad.data(), 64 * sizeof(double), cudaMemcpyHostToDevice) ||
+    if (cudaMemset(d->cnt, 0, sizeof(Counters)) ||
+        cudaMemcpy(d->d_radius, rad.data(), 64 * sizeof(double), cudaMemcpyHostToDevice) ||
         cudaMemcpy(d->d_sigma, sig.data(), 64 * sizeof(float), cudaMemcpyHostToDevice) ||
         cudaMemcpy(d->d_radius_f, radf.data(), 64 * sizeof(float), cudaMemcpyHostToDevice) ||
         cudaMemcpy(d->d_taps, d->taps.data(), d->taps.size() * sizeof(float), cudaMemcpyHostToDevice) ||
@@ -842,7 +913,8 @@ int mhfd_result_wait(mhfd_detector *d, mhfd_result *out) {
     out->hi = h.hi;
     if (h.c.timeout) {
         out->status = MHFD_ERR_TIMEOUT;
-        return fail(MHFD_ERR_TIMEOUT, "overlap prune did not settle within its wait limit");
+        return fail(MHFD_ERR_TIMEOUT,
+                    "a bounded device wait gave up (fused kernel or overlap prune)");
     }
     out->status = h.c.overflow ? MHFD_WARN_OVERFLOW : MHFD_OK;
     return out->status;
@@ -926,7 +998,8 @@ int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap) {
     LadderKey lk;
     int mode = p->nms;
     fused_ladder(*p, t, R, &lk, &mode);
-    const std::vector<TileConfig> menu = tile_menu(lk.R, mode);
+    const std::vector<TileConfig> menu =
+        p->tensor_cores ? tile_menu_tc(lk.R, mode) : tile_menu(lk.R, mode);
     if (desc) {
         for (int k = 0; k < (int)menu.size() && k < cap; ++k) {
             desc[5 * k + 0] = menu[k].tx2;
@@ -949,7 +1022,7 @@ int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5) {
     LadderKey lk;
     int mode = p->nms;
     fused_ladder(*p, t, R, &lk, &mode);
-    if ((rc = resolve_tile(lk.R, mode, *p, &c))) return rc;
+    if ((rc = resolve_tile(lk.R, mode, *p, &c, p->tensor_cores && tc_mode_ok(mode)))) return rc;
     desc5[0] = c.tx2;
     desc5[1] = c.ty2;
     desc5[2] = c.rb;
@@ -972,6 +1045,16 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     std::vector<float> taps_all, tsc_all;
     make_taps(t, R, &taps_all, &tapoff, &tsc_all);
     TileConfig cfg;
+    if (p->tensor_cores && tc_mode_ok(mode) && (store == 0 || store == 1)) {
+        // the tensor-core kernel and its FFMA companion
+        TileConfig ct;
+        if ((rc = resolve_tile(lk.R, mode, *p, &ct, true))) return rc;
+        if (!companion_tile(lk.R, mode, ct, &cfg))
+            return fail(MHFD_ERR_UNSUPPORTED,
+                        "no FFMA tile shape shares the tensor-core kernel's strip width");
+        if ((rc = precompile_variant(lk, p->nms, store != 0, ct))) return rc;
+        return precompile_variant(lk, p->nms, store != 0, cfg);
+    }
     if ((rc = resolve_tile(lk.R, mode, *p, &cfg))) return rc;
     if ((store == 2 || store == 3) && lk.response)
         return fail(MHFD_ERR_UNSUPPORTED, "the soft score uses the DoG response");
@@ -1246,6 +1329,11 @@ int mhfd_result_ready(mhfd_detector *d) {
     if (e == cudaSuccess) return 1;
     if (e == cudaErrorNotReady) return 0;
     return cuda_fail(e, "cudaEventQuery");
+}
+
+int mhfd_uses_tensor_cores(mhfd_detector *d) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    return d->use_tc ? 1 : 0;
 }
 
 int mhfd_batch_uses_graph(mhfd_detector *d) {

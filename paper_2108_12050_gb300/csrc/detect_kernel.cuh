@@ -61,6 +61,12 @@ constexpr int NT = MHFD_NT;
 // plane (no stretch, no maxima; the soft-score adjoint runs one per level)
 constexpr int MODE = MHFD_MODE;
 constexpr bool STORE = (MHFD_STORE) != 0;
+// Vertical pass on the tensor cores (tcgen05, see "tensor-core vertical
+// pass" below) instead of FFMA; detection modes, DoG, integer images.
+#ifndef MHFD_VTC
+#define MHFD_VTC 0
+#endif
+constexpr bool TC = (MHFD_VTC) != 0;
 
 // Kernel radius R_l of Gaussian level l and the level groups [GB(g), GB(g+1)).
 MK_HD constexpr int kR(int l) {
@@ -105,6 +111,12 @@ MK_HD constexpr int rmax_of() {
     return m;
 }
 constexpr int RMAX = rmax_of();
+// the largest halo radius among the levels of group g
+MK_HD constexpr int group_rmax(int g) {
+    int m = 0;
+    for (int l = kGB(g); l < kGB(g + 1); ++l) m = kRH(l) > m ? kRH(l) : m;
+    return m;
+}
 constexpr int WEXT = TX2 + 2 * RMAX;           // columns of the halo'd strip
 constexpr int WEXTP = (WEXT + 3) & ~3;
 constexpr int WIN = RB + 2 * RMAX;             // input rows one step reads
@@ -153,7 +165,22 @@ MK_HD constexpr int vrow_max() {
 }
 constexpr int NTAPS = tapoff(NL);
 constexpr int VROW = vrow_max();
-constexpr int SMEM_IN = BROWS * WEXTP;
+
+// Tensor-core vertical pass geometry.  The window holds the centred integer
+// pixels x = clamp(v, lo, hi) - c0 as fp16 (exact while |x| <= 2048) in the
+// canonical no-swizzle MN-major operand layout of tcgen05: column group cg
+// (8 columns, 16 bytes per row) at cg * TC_GSTR, row r at + 16 r.  M tiles
+// of 128 window columns; per level group G a K range of RB + 2 RG window
+// rows (padded to 16) and N = (levels of G) x RB accumulator columns (padded
+// to 16): one B matrix per group and tap part (hi, lo).
+constexpr int TC_NMT = (WEXT + 127) / 128;
+constexpr int TC_WT = 128 * TC_NMT;
+constexpr int TC_CG = TC_WT / 8;
+constexpr int TC_CGL = (WEXT + 7) / 8;  // column groups holding image columns
+constexpr int TC_GSTR = ((16 * BROWS + 127) / 128) * 128 + 32;  // 4 groups cover the 32 banks
+constexpr int TC_WIN_BYTES = TC ? TC_CG * TC_GSTR : 0;
+constexpr float TC_S = 1024.0f;  // tap scale: keeps the lo parts of small taps normal in fp16
+constexpr int SMEM_IN = TC ? 0 : BROWS * WEXTP;
 constexpr int SMEM_V = RB * VROW;
 constexpr int SMEM_RING_F = MODE == 0 ? RING * TX2 : MODE == 1 ? RING * NDOG * TX2 : 0;
 // per-pixel side data of the ring rows: the argmax (paper rule) or the mask
@@ -170,7 +197,30 @@ using LMask = MaskT<(NDOG > 32)>::T;
 constexpr int SMEM_RING_B = MODE == 0   ? ((RING * TX2 + 15) & ~15)
                             : MODE == 1 ? ((RING * TX2 * (int)sizeof(LMask) + 15) & ~15)
                                         : 0;
-constexpr int SMEM_BYTES = 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64;
+MK_HD constexpr int tc_kgp(int g) { return (RB + 2 * group_rmax(g) + 15) & ~15; }
+MK_HD constexpr int tc_ngp(int g) { return ((kGB(g + 1) - kGB(g)) * RB + 15) & ~15; }
+MK_HD constexpr int tc_colg(int g) {
+    int o = 0;
+    for (int j = 0; j < g; ++j) o += tc_ngp(j);
+    return o;
+}
+// bytes of group g's B matrices (hi part then lo part) from the table start
+MK_HD constexpr int tc_boff(int g) {
+    int o = 0;
+    for (int j = 0; j < g; ++j) o += 2 * 2 * tc_kgp(j) * tc_ngp(j);
+    return o;
+}
+constexpr int TC_NCT = tc_colg(NGROUPS);  // TMEM columns per M tile
+constexpr int TC_B_BYTES = TC ? tc_boff(NGROUPS) : 0;
+MK_HD constexpr int tc_tcols() {
+    int c = 32;
+    while (c < TC_NMT * TC_NCT) c *= 2;
+    return c;
+}
+constexpr int TC_TCOLS = tc_tcols();
+constexpr int TC_CTRL = TC ? 128 : 0;  // mbarriers (one per group) and the TMEM address
+constexpr int SMEM_BYTES =
+    TC_WIN_BYTES + TC_B_BYTES + 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64 + TC_CTRL;
 
 static_assert(TX2 % 4 == 0, "tile width must be a multiple of 4");
 static_assert(TY >= 1, "tile height");
@@ -179,6 +229,10 @@ static_assert(NT % 32 == 0 && NT <= 1024, "threads per block");
 static_assert((MODE == 3 || LOG ? NL >= 1 : NL >= 2) && NL <= 64, "levels");
 static_assert(!LOG || MODE <= 1, "the LoG response is a detection mode");
 static_assert(kGB(0) == 0 && kGB(NGROUPS) == NL, "level groups");
+static_assert(!TC || (MODE <= 1 && !LOG && RB == 4 && NT % 128 == 0), "tensor-core vertical pass");
+static_assert(!TC || TC_NMT * TC_NCT <= 512, "tensor memory columns");
+static_assert(!TC || BROWS >= WIN + 2 * RB + 16, "window rows of the tensor-core pass");
+static_assert(!TC || NGROUPS <= 12, "one mbarrier per group in the control block");
 
 struct KParams {
     MhfdKHeader h;
@@ -345,11 +399,316 @@ __device__ __forceinline__ void shift_window(float *s_in, int from, int n) {
     }
 }
 
-// the largest halo radius among the levels of group g
-MK_HD constexpr int group_rmax(int g) {
-    int m = 0;
-    for (int l = kGB(g); l < kGB(g + 1); ++l) m = kRH(l) > m ? kRH(l) : m;
-    return m;
+
+// ----------------------------------------- tensor-core vertical pass (TC)
+//
+// V_l(y0 + j, c) = sum_k g_l[k - j - RG] x(y0 + RMAX - RG + k, c) for the
+// levels l of group G is the product of the window (M = columns, K = rows,
+// MN-major) with a banded tap matrix B_G (K x N, N = (level, row j)), built
+// once per block: taps scaled by TC_S and split into fp16 hi and lo parts,
+// so that the two products add up to the f32 tap to about 2^-22 while the
+// window values are exact.  One elected thread issues the MMAs
+// (tcgen05.mma, kind::f16, f32 accumulators in tensor memory) for the next
+// step of a group as soon as this step's results of the group have been
+// read out, so they run under the horizontal passes; the block reads each
+// group's accumulators back with tcgen05.ld (lane = column), applies the
+// stretch affine (acc / TC_S) inv + (c0 - lo) inv + off and writes the V rows
+// the horizontal pass reads.  All waits are bounded: a wait that gives up
+// sets h.flag and the block carries on (the results are then reported as
+// unreliable by the host).
+
+__device__ const float mk_taps_rt[NTAPS] = {MHFD_TAPS};
+struct TcTab {
+    int r[NL];
+    int off[NL];
+};
+MK_HD constexpr TcTab tc_tab() {
+    TcTab t{};
+    for (int l = 0; l < NL; ++l) {
+        t.r[l] = kR(l);
+        t.off[l] = tapoff(l);
+    }
+    return t;
+}
+__device__ const TcTab mk_tctab = tc_tab();
+
+__device__ __forceinline__ unsigned short f2h_rn(float f) {
+    unsigned short h;
+    asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return h;
+}
+__device__ __forceinline__ float h2f(unsigned short h) {
+    float f;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+    return f;
+}
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// stretch of one image for the tensor-core pass
+struct TcStretch {
+    int lo, hi, c0;
+    float a, b;  // V = a * acc + b
+};
+__device__ __forceinline__ TcStretch tc_stretch(const MhfdStretch &st) {
+    TcStretch t;
+    t.lo = st.lo_i;
+    t.hi = st.hi_i;
+    t.c0 = (st.lo_i + st.hi_i) >> 1;
+    t.a = st.inv * (1.0f / TC_S);
+    t.b = fmaf((float)(t.c0 - st.lo_i), st.inv, st.off);
+    return t;
+}
+// uint8, or uint16 whose stretch range keeps |x| <= 2048
+__device__ __forceinline__ bool tc_narrow(int dtype, const MhfdStretch &st) {
+    return dtype == 0 || (dtype == 1 && st.hi_i - st.lo_i <= 4095);
+}
+__device__ __forceinline__ unsigned short tc_px(unsigned raw, const TcStretch &ts) {
+    const int v = min(max((int)raw, ts.lo), ts.hi) - ts.c0;
+    return f2h_rn((float)v);
+}
+__device__ __forceinline__ void tc_put(unsigned char *win, int row, int c, unsigned short v) {
+    *reinterpret_cast<unsigned short *>(win + (c >> 3) * TC_GSTR + row * 16 + (c & 7) * 2) = v;
+}
+
+// Input rows [r0, r1) into window rows [r0, r1) (the start of a march).
+template <int DT>
+__device__ __forceinline__ void tc_load_rows_t(const Strip &sp, const TcStretch &ts,
+                                               unsigned char *win, int r0, int r1) {
+    constexpr int LB = 16;
+    for (int c = threadIdx.x; c < WEXT; c += NT) {
+        const int gx = reflect_idx(sp.xin + c, sp.W);
+#pragma unroll 1
+        for (int r = r0; r < r1; r += LB) {
+            unsigned v[LB];
+#pragma unroll
+            for (int e = 0; e < LB; ++e)
+                if (r + e < r1)
+                    v[e] = raw_px<DT>(sp.img + (long long)reflect_idx(sp.yin + r + e, sp.H) * sp.pitch,
+                                      gx);
+#pragma unroll
+            for (int e = 0; e < LB; ++e)
+                if (r + e < r1) tc_put(win, r + e, c, tc_px(v[e], ts));
+        }
+    }
+}
+__device__ __forceinline__ void tc_load_rows(const Strip &sp, const TcStretch &ts,
+                                             unsigned char *win, int r0, int r1) {
+    if (sp.dtype == 0)
+        tc_load_rows_t<0>(sp, ts, win, r0, r1);
+    else
+        tc_load_rows_t<1>(sp, ts, win, r0, r1);
+}
+
+// Move window rows [from, from + n) to [0, n): one thread per column group
+// walks its rows upwards, eight at a time (read before written).
+__device__ __forceinline__ void tc_shift(unsigned char *win, int from, int n) {
+    for (int cg = threadIdx.x; cg < TC_CGL; cg += NT) {
+        uint4 *col = reinterpret_cast<uint4 *>(win + cg * TC_GSTR);
+#pragma unroll 1
+        for (int r = 0; r < n; r += 8) {
+            uint4 v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (r + e < n) v[e] = col[from + r + e];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (r + e < n) col[r + e] = v[e];
+        }
+    }
+}
+
+// Zero the window (rows and columns the MMAs read but no image row fills
+// must hold finite values) and build the B matrices: K-major, core matrices
+// of 8 N-rows x 8 K-values (128 bytes), K-adjacent core matrices 128 bytes
+// apart, N-adjacent ones (kgp / 8) * 128 bytes apart.
+__device__ __forceinline__ void tc_setup_smem(unsigned char *win, unsigned char *btab) {
+    for (int i = threadIdx.x; i < TC_WIN_BYTES / 16; i += NT)
+        reinterpret_cast<uint4 *>(win)[i] = make_uint4(0u, 0u, 0u, 0u);
+    unsigned short *hb = reinterpret_cast<unsigned short *>(btab);
+    for (int g = 0; g < NGROUPS; ++g) {
+        const int kgp = tc_kgp(g), ngp = tc_ngp(g), rg = group_rmax(g);
+        const int lb = kGB(g), ng = kGB(g + 1) - lb;
+        const int part = kgp * ngp;
+        unsigned short *p0 = hb + tc_boff(g) / 2;
+        for (int q = threadIdx.x; q < part; q += NT) {
+            const int blk = q >> 6, e = q & 63;
+            const int n = (blk / (kgp / 8)) * 8 + (e >> 3);
+            const int k = (blk % (kgp / 8)) * 8 + (e & 7);
+            const int li = n / RB, j = n - li * RB;
+            float v = 0.0f;
+            if (li < ng) {
+                const int l = lb + li;
+                int d = k - j - rg;
+                d = d < 0 ? -d : d;
+                if (d <= mk_tctab.r[l]) v = mk_taps_rt[mk_tctab.off[l] + d] * TC_S;
+            }
+            const unsigned short hi = f2h_rn(v);
+            p0[q] = hi;
+            p0[part + q] = f2h_rn(v - h2f(hi));
+        }
+    }
+}
+
+// shared-memory matrix descriptor: no swizzle, start / leading (K) / stride
+// (M or N) byte offsets in 16-byte units, descriptor version 1
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) |
+           ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: f32 accumulator, f16 A and B, A
+// MN-major, B K-major, N >> 3 and M >> 4
+MK_HD constexpr unsigned tc_idesc(int n) {
+    return (1u << 4) | (1u << 15) | ((unsigned)(n >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+}
+
+// The thread that issues the MMAs: lane 0 of the first warp without a
+// horizontal item when there is one (its issue then runs beside the
+// horizontal passes of the other warps), else thread 0.
+constexpr int TC_ISSUER = ((HITEMS + 31) / 32) * 32 < NT ? ((HITEMS + 31) / 32) * 32 : 0;
+
+struct TcState {
+    unsigned tmem;   // tensor-memory base (lane 0, first column)
+    unsigned win;    // shared addresses of the window, the B table, the mbarriers
+    unsigned btab;
+    unsigned bar;
+    unsigned ph;     // expected phase parity per group (bit G)
+    bool issuer;
+};
+
+// The MMAs of group G for the step whose first input row is window row row0.
+template <int G>
+__device__ __forceinline__ void tc_issue(const TcState &tc, int row0) {
+    constexpr int NK = tc_kgp(G) / 16;
+    constexpr unsigned IDESC = tc_idesc(tc_ngp(G));
+    constexpr unsigned PART = 2u * tc_kgp(G) * tc_ngp(G);
+    const unsigned long long a0 =
+        tc_desc(tc.win + (unsigned)(row0 + RMAX - group_rmax(G)) * 16u, 128u, (unsigned)TC_GSTR);
+    const unsigned long long b0 =
+        tc_desc(tc.btab + (unsigned)tc_boff(G), 128u, (unsigned)(tc_kgp(G) / 8) * 128u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+    for (int t = 0; t < TC_NMT; ++t) {
+        const unsigned d = tc.tmem + (unsigned)(t * TC_NCT + tc_colg(G));
+        const unsigned long long at = a0 + (unsigned long long)((t * 16 * TC_GSTR) >> 4);
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const unsigned long long a = at + (unsigned long long)(kk * 16);
+                const unsigned long long b = b0 + (unsigned long long)((p * PART + kk * 256) >> 4);
+                const unsigned acc = (kk | p) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(d),
+                    "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+                    : "memory");
+            }
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     tc.bar + 8u * G)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool tc_try(unsigned bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait (at most about 0.2 s) for the MMAs of group G to complete.
+__device__ __forceinline__ void tc_wait(const MhfdKHeader &h, const TcState &tc, int g) {
+    const unsigned bar = tc.bar + 8u * g, par = (tc.ph >> g) & 1u;
+    if (tc_try(bar, par)) return;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+#pragma unroll 1
+        for (int i = 0; i < 256; ++i)
+            if (tc_try(bar, par)) return;
+        if (gtimer() - t0 > 200000000ull) break;
+    }
+    if (h.flag) atomicExch(h.flag, 1);
+}
+
+__device__ __forceinline__ void tc_ld4(unsigned addr, unsigned (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+
+// the RB prefetched rows into window rows [prow, prow + RB)
+__device__ __forceinline__ void tc_store_prefetch(const Prefetch &pf, const TcStretch &ts,
+                                                  unsigned char *win, int prow) {
+#pragma unroll
+    for (int k = 0; k < NT_COLS; ++k) {
+        const int c = threadIdx.x + k * NT;
+        if (c < WEXT) {
+#pragma unroll
+            for (int e = 0; e < RB; ++e) tc_put(win, prow + e, c, tc_px(pf.v[k][e], ts));
+        }
+    }
+}
+
+// the loaded registers are only read after tcgen05.wait::ld: this empty
+// statement (ordered after the wait like every volatile asm) redefines them
+__device__ __forceinline__ void tc_regs_ready(unsigned (&r)[4]) {
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
+}
+
+template <int G, int LI>
+__device__ __forceinline__ void tc_ld_levels(unsigned taddr, unsigned (*r)[4]) {
+    if constexpr (LI < kGB(G + 1) - kGB(G)) {
+        tc_ld4(taddr + (unsigned)(LI * RB), r[LI]);
+        tc_ld_levels<G, LI + 1>(taddr, r);
+    }
+}
+template <int G, int LI>
+__device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (*r)[4], int c,
+                                             const TcStretch &ts) {
+    if constexpr (LI < kGB(G + 1) - kGB(G)) {
+        constexpr int L = kGB(G) + LI;
+        tc_regs_ready(r[LI]);
+        const int cc = c - (RMAX - kR(L));
+        if (cc >= 0 && cc < TX2 + 2 * kR(L)) {
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+                s_v[j * VROW + voff(L) + cc] = fmaf(__uint_as_float(r[LI][j]), ts.a, ts.b);
+        }
+        tc_st_levels<G, LI + 1>(s_v, r, c, ts);
+    }
+}
+
+// Read group G's accumulators and write the V rows of its levels: warp w
+// reads tensor-memory lanes 32 (w % 4) .. + 31 (window columns 128 t + lane)
+// of the M tiles t = w / 4, w / 4 + NT / 128, ...
+template <int G>
+__device__ __forceinline__ void tc_read(const TcState &tc, float *s_v, const TcStretch &ts) {
+    constexpr int NG = kGB(G + 1) - kGB(G);
+    constexpr int NWG = NT / 128;
+    const int warp = threadIdx.x >> 5, q = warp & 3;
+    const int c0 = 32 * q + (threadIdx.x & 31);
+#pragma unroll 1
+    for (int t = warp >> 2; t < TC_NMT; t += NWG) {
+        const unsigned taddr =
+            tc.tmem + ((unsigned)(32 * q) << 16) + (unsigned)(t * TC_NCT + tc_colg(G));
+        unsigned r[NG][4];
+        tc_ld_levels<G, 0>(taddr, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        tc_st_levels<G, 0>(s_v, r, 128 * t + c0, ts);
+    }
 }
 
 // Fold step K of the vertical pass for the levels L.. of group G: every
@@ -767,7 +1126,10 @@ __device__ __forceinline__ int nms_rows(const MhfdKHeader &h, const March &m,
                                         int *s_scan, int ra, int rb, long long slot, int total) {
     const int nrows = rb - ra + 1;
     const int items = nrows * TX;
-    const int ch = (items + NT - 1) / NT;
+    // contiguous runs of pixels per thread (candidates come out in row-major
+    // order after one scan); an odd run length keeps the lanes' ring reads
+    // in distinct banks
+    const int ch = ((items + NT - 1) / NT) | 1;
     const int beg = min(items, (int)threadIdx.x * ch);
     const int end = min(items, beg + ch);
     const float thr = h.thr;
@@ -834,6 +1196,7 @@ struct Smem {
     float *in, *v, *ring;
     unsigned char *arg;
     int *scan;
+    unsigned char *win, *btab, *ctrl;  // tensor-core pass: window, B matrices, mbarriers
 };
 
 // Adds this block's sums of every layer (FP64, fixed order) to its slot of
@@ -926,45 +1289,133 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
     if constexpr (MODE == 2) soft_flush(h, hs, sm.scan);
 }
 
+// Tensor-core march: the vertical pass of each group comes from the MMAs
+// issued one step earlier; the rows of step s + 2 are fetched during step s
+// and stored at its end, so the MMAs of step s + 1 (issued during step s)
+// find their rows in the window.
+template <int G>
+struct GroupsTC {
+    static __device__ __forceinline__ void run(const MhfdKHeader &h, const March &m, TcState &tc,
+                                               const TcStretch &ts, const Smem &sm,
+                                               HState (&hs)[HI], int s, int nsteps, int base) {
+        if constexpr (G < NGROUPS) {
+            tc_wait(h, tc, G);
+            tc.ph ^= 1u << G;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc_read<G>(tc, sm.v, ts);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tc.issuer && s + 1 < nsteps) tc_issue<G>(tc, (s + 1) * RB - base);
+            hpass<G>(h, m, sm.v, sm.ring, sm.arg, hs, s);
+            __syncthreads();
+            GroupsTC<G + 1>::run(h, m, tc, ts, sm, hs, s, nsteps, base);
+        }
+    }
+};
+
+template <int G>
+__device__ __forceinline__ void tc_issue_all(const TcState &tc, int row0) {
+    if constexpr (G < NGROUPS) {
+        tc_issue<G>(tc, row0);
+        tc_issue_all<G + 1>(tc, row0);
+    }
+}
+
+__device__ __forceinline__ void tc_wait_all(const MhfdKHeader &h, const TcState &tc) {
+    for (int g = 0; g < NGROUPS; ++g) tc_wait(h, tc, g);
+}
+
+__device__ __forceinline__ void march_tc(const MhfdKHeader &h, const MhfdStretch &st,
+                                         int tiles_x, int tx, int ta, int tb, long long slot0,
+                                         const Smem &sm, TcState &tc) {
+    March m;
+    m.x0 = tx * TX;
+    m.yb = ta * TY - 1;
+    m.Y = min((tb - ta) * TY, h.H - ta * TY);
+    Strip sp;
+    sp.img = reinterpret_cast<const char *>(h.img);
+    sp.pitch = h.pitch;
+    sp.H = h.H;
+    sp.W = h.W;
+    sp.dtype = h.dtype;
+    sp.xin = m.x0 - 1 - RMAX;
+    sp.yin = m.yb - RMAX;
+    const int nsteps = (m.Y + 2 + RB - 1) / RB;
+    const TcStretch ts = tc_stretch(st);
+
+    __syncthreads();  // the previous march's last reads of shared memory
+    tc_load_rows(sp, ts, sm.win, 0, WIN + RB);  // the rows of steps 0 and 1
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tc.issuer) tc_issue_all<0>(tc, 0);
+
+    HState hs[HI];
+#pragma unroll
+    for (int it = 0; it < HI; ++it)
+#pragma unroll
+        for (int i = 0; i < NSOFT; ++i) hs[it].soft[i] = 0.0f;
+    int base = 0;       // input row held in window row 0
+    int tile = 0;       // tile (relative to ta) now receiving candidates
+    int total = 0;      // its candidates so far
+#pragma unroll 1
+    for (int s = 0; s < nsteps; ++s) {
+        const bool more2 = s + 2 < nsteps;
+        Prefetch pf;
+        if (more2) pf.issue(sp, (s + 1) * RB + WIN);  // the new rows of step s + 2
+        GroupsTC<0>::run(h, m, tc, ts, sm, hs, s, nsteps, base);
+        int ra = max(1, s * RB - 1);
+        const int rb = min(m.Y, s * RB + RB - 2);
+        while (ra <= rb) {
+            const int tend = min(m.Y, (tile + 1) * TY);
+            const int re = min(rb, tend);
+            total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, ra, re,
+                             slot0 + (long long)(ta + tile) * tiles_x + tx, total);
+            if (re == tend) {
+                if (threadIdx.x == 0)
+                    h.tile_count[slot0 + (long long)(ta + tile) * tiles_x + tx] = total;
+                ++tile;
+                total = 0;
+            }
+            ra = re + 1;
+        }
+        if (more2) {
+            // the window must hold rows [(s+1) RB, (s+2) RB + WIN) and the
+            // 16 rows past them that padded K ranges read
+            if ((s + 2) * RB + WIN + 16 - base > BROWS) {
+                tc_wait_all(h, tc);  // the MMAs of step s + 1 read the window
+                tc_shift(sm.win, (s + 1) * RB - base, WIN);
+                base = (s + 1) * RB;
+                __syncthreads();
+            }
+            tc_store_prefetch(pf, ts, sm.win, (s + 1) * RB + WIN - base);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+    }
+}
+
 // Tiles [k0, k1) of an image in strip-major order (k -> strip k / tiles_y,
 // tile row k % tiles_y), as one march per strip touched.
 __device__ __forceinline__ void run_range(const MhfdKHeader &h, long long k0, long long k1,
                                           int tiles_x, int tiles_y, long long slot0,
-                                          const Smem &sm) {
+                                          const Smem &sm, TcState &tc) {
     const MhfdStretch st = *h.st;
     long long k = k0;
     while (k < k1) {
         const int tx = (int)(k / tiles_y);
         const int ta = (int)(k - (long long)tx * tiles_y);
         const int tb = (int)min((long long)tiles_y, ta + (k1 - k));
-        march(h, st, tiles_x, tx, ta, tb, slot0, sm);
+        if constexpr (TC)
+            march_tc(h, st, tiles_x, tx, ta, tb, slot0, sm, tc);
+        else
+            march(h, st, tiles_x, tx, ta, tb, slot0, sm);
         k += tb - ta;
     }
 }
 
-}  // namespace mk
-
-extern "C" __global__ void __launch_bounds__(mk::NT, 1)
-    mhfd_fused_detect(const __grid_constant__ mk::KParams p) {
-    using namespace mk;
-    extern __shared__ __align__(16) float smem[];
-    Smem sm;
-    sm.in = smem;
-    sm.v = smem + SMEM_IN;
-    sm.ring = sm.v + SMEM_V;
-    sm.arg = reinterpret_cast<unsigned char *>(sm.ring + SMEM_RING_F);
-    sm.scan = reinterpret_cast<int *>(sm.arg + SMEM_RING_B);
-
-    if (p.h.jobs == nullptr) {
-        // one image: block b takes an equal share of its tiles
-        const long long T = (long long)p.h.tiles_x * p.h.tiles_y;
-        const long long k0 = T * blockIdx.x / gridDim.x;
-        const long long k1 = T * (blockIdx.x + 1) / gridDim.x;
-        run_range(p.h, k0, k1, p.h.tiles_x, p.h.tiles_y, 0, sm);
-        return;
-    }
-    // batch: persistent blocks take chunks of `chunk` tiles from the queue
-    // (no waits); chunk -> (job, tiles) through chunk_base
+// batch: persistent blocks take chunks of `chunk` tiles from the queue
+// (no waits); chunk -> (job, tiles) through chunk_base
+__device__ __forceinline__ void batch_loop(const KParams &p, const Smem &sm, TcState &tc) {
     __shared__ int s_item;
 #pragma unroll 1
     for (;;) {
@@ -992,6 +1443,87 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
         const long long n_tiles = (long long)job.tiles_x * job.tiles_y;
         const long long k0 = (long long)(item - job.chunk_base) * p.h.chunk;
         const long long k1 = min(n_tiles, k0 + p.h.chunk);
-        run_range(h, k0, k1, job.tiles_x, job.tiles_y, job.tile_base, sm);
+        run_range(h, k0, k1, job.tiles_x, job.tiles_y, job.tile_base, sm, tc);
     }
 }
+
+}  // namespace mk
+
+extern "C" __global__ void __launch_bounds__(mk::NT, 1)
+    mhfd_fused_detect(const __grid_constant__ mk::KParams p) {
+    using namespace mk;
+    extern __shared__ __align__(16) float smem[];
+    Smem sm;
+    if constexpr (TC) {
+        sm.win = reinterpret_cast<unsigned char *>(smem);
+        sm.btab = sm.win + TC_WIN_BYTES;
+        sm.in = nullptr;
+        sm.v = reinterpret_cast<float *>(sm.btab + TC_B_BYTES);
+    } else {
+        sm.win = sm.btab = nullptr;
+        sm.in = smem;
+        sm.v = smem + SMEM_IN;
+    }
+    sm.ring = sm.v + SMEM_V;
+    sm.arg = reinterpret_cast<unsigned char *>(sm.ring + SMEM_RING_F);
+    sm.scan = reinterpret_cast<int *>(sm.arg + SMEM_RING_B);
+    sm.ctrl = reinterpret_cast<unsigned char *>(sm.scan) + 4 * 64;
+
+    // single image with a gate: the tensor-core kernel takes narrow stretch
+    // ranges, its FFMA companion the rest (both launched, one works)
+    if (p.h.jobs == nullptr && p.h.gate != 0) {
+        const bool narrow = tc_narrow(p.h.dtype, *p.h.st);
+        if ((p.h.gate == 1) != narrow) return;
+    }
+    TcState tc{};
+    if constexpr (TC) {
+        if (p.h.dtype == 2) {  // float images never reach this kernel
+            if (threadIdx.x == 0 && p.h.flag) atomicExch(p.h.flag, 1);
+            return;
+        }
+        tc_setup_smem(sm.win, sm.btab);
+        unsigned *tslot = reinterpret_cast<unsigned *>(sm.ctrl + 96);
+        if (threadIdx.x == 0) {
+            for (int g = 0; g < NGROUPS; ++g)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(sm.ctrl + 8 * g))
+                             : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (threadIdx.x < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_addr(tslot)),
+                         "r"((unsigned)TC_TCOLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc.tmem = *tslot;
+        tc.win = smem_addr(sm.win);
+        tc.btab = smem_addr(sm.btab);
+        tc.bar = smem_addr(sm.ctrl);
+        tc.ph = 0;
+        tc.issuer = threadIdx.x == TC_ISSUER;
+    }
+
+    if (p.h.jobs == nullptr) {
+        // one image: block b takes an equal share of its tiles
+        const long long T = (long long)p.h.tiles_x * p.h.tiles_y;
+        const long long k0 = T * blockIdx.x / gridDim.x;
+        const long long k1 = T * (blockIdx.x + 1) / gridDim.x;
+        run_range(p.h, k0, k1, p.h.tiles_x, p.h.tiles_y, 0, sm, tc);
+    } else {
+        batch_loop(p, sm, tc);
+    }
+    if constexpr (TC) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x < 32)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem),
+                         "r"((unsigned)TC_TCOLS)
+                         : "memory");
+    }
+}
+

@@ -68,6 +68,7 @@ int enqueue_stretch_batch(const MhfdJob *d_jobs, int n_jobs, int max_passes, int
 struct TileConfig {
     int tx2, ty2, rb, nt;
     std::vector<int> gb;   // level-group boundaries
+    int tc = 0;            // 1: vertical pass on the tensor cores (tcgen05)
 };
 
 struct Variant {
@@ -105,6 +106,16 @@ constexpr int kSmemLimitBytes = 232448 - 64;
 constexpr int kModeLog = 4;
 int brows_for(const std::vector<int> &R, int mode, const TileConfig &c);
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c);
+// Whether the tensor-core vertical pass can take this ladder and mode at all
+// (detection rules, DoG response) and whether a shape is valid for it (four
+// rows per step, whole warpgroups, tensor-memory columns, shared memory).
+bool tc_mode_ok(int mode);
+bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why);
+std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode);
+bool choose_tile_tc(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why);
+// The FFMA kernel's shape on a tensor-core shape's tile grid (the kernel
+// that takes the images the tensor-core pass cannot hold exactly).
+bool companion_tile(const std::vector<int> &R, int mode, const TileConfig &tc, TileConfig *cfg);
 // Compile (or fetch from cache) the fused kernel for this ladder/config.
 int get_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg, Variant **out);
 // Compile into the on-disk cache only (no GPU needed).
@@ -117,6 +128,8 @@ struct Counters {
     unsigned long long n_blobs;     // survivors
     int overflow;
     int timeout;
+    int ktimeout;                   // set by a fused kernel whose bounded wait gave up;
+                                    // moved into `timeout` (and cleared) by the gather
     unsigned long long blob_base;   // first slot of this image's blobs in the output list
 };
 

@@ -88,6 +88,7 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_TY2 " << c.ty2 << "\n"
       << "#define MHFD_BROWS " << brows_for(R, smode, c) << "\n"
       << "#define MHFD_RB " << c.rb << "\n"
+      << "#define MHFD_VTC " << c.tc << "\n"
       << "#define MHFD_NT " << c.nt << "\n"
       << "#define MHFD_MODE " << mode << "\n"
       << "#define MHFD_STORE " << store << "\n"
@@ -119,6 +120,15 @@ void write_file_atomic(const std::string &path, const std::string &data) {
 }
 
 int compile_cubin(const std::string &src, std::string *cubin) {
+    // MHFD_JIT_DUMP=<dir>: also write each compiled source there (to inspect
+    // register use with nvcc -Xptxas -v)
+    if (const char *dump = std::getenv("MHFD_JIT_DUMP")) {
+        if (*dump) {
+            char name[64];
+            std::snprintf(name, sizeof(name), "/mhfd_%016llx.cu", fnv1a(src));
+            write_file_atomic(std::string(dump) + name, src);
+        }
+    }
     nvrtcProgram prog;
     nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "mhfd_fused.cu", 0, nullptr, nullptr);
     if (r != NVRTC_SUCCESS) return fail(MHFD_ERR_JIT, std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r));
@@ -225,9 +235,64 @@ int wextp_of(const std::vector<int> &R, int mode, const TileConfig &c) {
 
 }  // namespace
 
+namespace {
+
+// Tensor-core variant: the fp16 window (column groups of 8 columns, 16 bytes
+// a row, groups padded so that four cover the 32 banks), the tap matrices
+// (hi and lo parts per level group), the mbarrier / tensor-memory block.
+int tc_window_bytes(const std::vector<int> &R, int mode, const TileConfig &c, int brows) {
+    const int wext = c.tx2 + 2 * halo_of(R, mode);
+    const int nmt = (wext + 127) / 128;
+    const int gstr = ((16 * brows + 127) / 128) * 128 + 32;
+    return nmt * 16 * gstr;
+}
+
+void tc_group_dims(const std::vector<int> &R, const TileConfig &c, int g, int *kgp, int *ngp) {
+    int rg = 0;
+    for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) rg = R[l] > rg ? R[l] : rg;
+    *kgp = (c.rb + 2 * rg + 15) & ~15;
+    *ngp = ((c.gb[g + 1] - c.gb[g]) * c.rb + 15) & ~15;
+}
+
+int tc_b_bytes(const std::vector<int> &R, const TileConfig &c) {
+    int o = 0;
+    for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
+        int kgp, ngp;
+        tc_group_dims(R, c, (int)g, &kgp, &ngp);
+        o += 4 * kgp * ngp;
+    }
+    return o;
+}
+
+int tc_tmem_cols(const std::vector<int> &R, int mode, const TileConfig &c) {
+    const int wext = c.tx2 + 2 * halo_of(R, mode);
+    int nct = 0;
+    for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
+        int kgp, ngp;
+        tc_group_dims(R, c, (int)g, &kgp, &ngp);
+        nct += ngp;
+    }
+    return ((wext + 127) / 128) * nct;
+}
+
+int tc_min_rows(const std::vector<int> &R, int mode, const TileConfig &c) {
+    return c.rb + 2 * halo_of(R, mode) + 2 * c.rb + 16;
+}
+
+}  // namespace
+
 // Input window rows: one step's rows (rb + 2 rmax) plus up to four steps of
 // slack (the window shifts back once the slack is used up), as many as fit.
+// The tensor-core variant also holds the rows of the step after next and 16
+// rows of K padding, and takes up to six steps of slack.
 int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
+    if (c.tc) {
+        const int lo = tc_min_rows(R, mode, c);
+        const int fixed = smem_fixed(R, mode, c) + tc_b_bytes(R, c) + 128;
+        int b = lo + 6 * c.rb;
+        while (b > lo && fixed + tc_window_bytes(R, mode, c, b) > kSmemLimit) --b;
+        return b;
+    }
     const int win = c.rb + 2 * halo_of(R, mode);
     const int row_bytes = 4 * wextp_of(R, mode, c);
     const int room = (kSmemLimit - smem_fixed(R, mode, c)) / row_bytes;
@@ -237,7 +302,117 @@ int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
 }
 
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
+    if (c.tc)
+        return smem_fixed(R, mode, c) + tc_b_bytes(R, c) + 128 +
+               tc_window_bytes(R, mode, c, brows_for(R, mode, c));
     return smem_fixed(R, mode, c) + 4 * brows_for(R, mode, c) * wextp_of(R, mode, c);
+}
+
+namespace {
+double cost_model(const std::vector<int> &R, int mode, const TileConfig &c);
+}
+
+bool tc_mode_ok(int mode) { return (mode & kModeLog) == 0 && (mode & 3) <= 1; }
+
+bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why) {
+    auto no = [&](const char *m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (!tc_mode_ok(mode)) return no("the tensor-core pass takes the DoG detection modes only");
+    if (c.rb != 4) return no("the tensor-core pass takes four rows per step");
+    if (c.nt % 128 || c.nt < 128 || c.nt > 1024) return no("threads: whole warpgroups");
+    if (c.rb * (c.tx2 / 4) > 2 * c.nt) return no("more than two row quads per thread");
+    if (c.gb.size() - 1 > 12) return no("at most 12 level groups");
+    if (tc_tmem_cols(R, mode, c) > 512) return no("tensor memory holds 512 columns");
+    if (brows_for(R, mode, c) < tc_min_rows(R, mode, c) ||
+        smem_estimate(R, mode, c) > kSmemLimit)
+        return no("does not fit in shared memory");
+    return true;
+}
+
+std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode) {
+    std::vector<TileConfig> out;
+    if (!tc_mode_ok(mode)) return out;
+    const int nl = (int)R.size();
+    const int widths[] = {96, 128, 192, 224, 256, 320, 352, 384, 448, 480, 512};
+    for (int tx2 : widths)
+        for (int nt = 128; nt <= 512; nt += 128) {
+            if (tx2 > 2 * nt || tx2 <= nt - 128) continue;  // items per thread 1..2, no idle warpgroup
+            for (int ng = 1; ng <= 6 && ng <= nl; ++ng) {
+                TileConfig c;
+                c.tx2 = tx2;
+                c.ty2 = 2 + 16;
+                c.rb = 4;
+                c.nt = nt;
+                c.gb.assign(ng + 1, 0);
+                for (int g = 0; g <= ng; ++g) c.gb[g] = (int)((long long)nl * g / ng);
+                c.tc = 1;
+                if (tc_shape_ok(R, mode, c, nullptr)) out.push_back(c);
+            }
+        }
+    return out;
+}
+
+// The FFMA kernel sharing a tensor-core shape's tile grid (strip width and
+// tile height): four (else two) rows per step, a thread per halo'd column
+// and per horizontal item, the fewest level groups that fit, then the cost
+// model.
+bool companion_tile(const std::vector<int> &R, int mode, const TileConfig &tc, TileConfig *cfg) {
+    const int nl = (int)R.size();
+    const int wext = tc.tx2 + 2 * halo_of(R, mode);
+    bool found = false;
+    double best = 0.0;
+    for (int rb : {4, 2}) {
+        const int items = rb * (tc.tx2 / 4);
+        int nt = wext > items ? wext : items;
+        nt = (nt + 31) / 32 * 32;
+        if (nt > 1024) nt = ((items + 31) / 32) * 32;
+        for (int ng = 1; ng <= 12 && ng <= nl; ++ng) {
+            TileConfig c;
+            c.tx2 = tc.tx2;
+            c.ty2 = tc.ty2;
+            c.rb = rb;
+            c.nt = nt;
+            c.gb.assign(ng + 1, 0);
+            for (int g = 0; g <= ng; ++g) c.gb[g] = (int)((long long)nl * g / ng);
+            if (smem_estimate(R, mode, c) > kSmemLimit) continue;
+            const double cost = cost_model(R, mode, c);
+            if (!found || cost < best) {
+                best = cost;
+                *cfg = c;
+                found = true;
+            }
+        }
+        if (found) return true;
+    }
+    return false;
+}
+
+// Widest strip whose horizontal items leave exactly one warp free for the
+// MMA issue (tx2 = threads - 32, one item per thread: the four schedulers
+// then hold equal work), fewest groups.
+bool choose_tile_tc(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why) {
+    const std::vector<TileConfig> menu = tile_menu_tc(R, mode);
+    bool found = false;
+    TileConfig comp;
+    for (const TileConfig &c : menu) {
+        if (c.tx2 != c.nt - 32 || !companion_tile(R, mode, c, &comp)) continue;
+        if (!found || c.tx2 > cfg->tx2 ||
+            (c.tx2 == cfg->tx2 && c.gb.size() < cfg->gb.size())) {
+            *cfg = c;
+            found = true;
+        }
+    }
+    for (const TileConfig &c : menu) {
+        if (found) break;
+        if (companion_tile(R, mode, c, &comp)) {
+            *cfg = c;
+            found = true;
+        }
+    }
+    if (!found && why) *why = "no tensor-core tile configuration fits for this ladder";
+    return found;
 }
 
 namespace {

@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kScanThreads)
         cnt->n_stored = (unsigned long long)(tot_s < cap ? tot_s : cap);
         cnt->overflow = (tot_t > (long long)cnt->n_stored) ? 1 : 0;
         cnt->n_blobs = 0;
-        cnt->timeout = 0;
+        cnt->timeout = cnt->ktimeout;
+        cnt->ktimeout = 0;
         cnt->blob_base = 0;
     }
 }

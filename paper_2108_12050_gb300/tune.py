@@ -25,10 +25,12 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(PKG, "tuned_tiles.json")
 
 
-def ladder_key(n, t_min, t_max, nms, truncate=4.0, response="dog"):
+def ladder_key(n, t_min, t_max, nms, truncate=4.0, response="dog", tensor_cores=False):
     key = "n%d_t%g-%g_%s_tr%g" % (n, t_min, t_max,
                                   "paper" if nms in (0, "paper") else "local26", truncate)
-    return key if response in ("dog", 0) else key + "_log"
+    if response not in ("dog", 0):
+        key += "_log"
+    return key + "_tc" if tensor_cores else key
 
 
 def load_table():
@@ -39,10 +41,11 @@ def load_table():
         return {}
 
 
-def lookup(n, t_min, t_max, nms, sms, truncate=4.0, response="dog"):
+def lookup(n, t_min, t_max, nms, sms, truncate=4.0, response="dog", tensor_cores=False):
     """Tuned tile shape (the five-field tile_shape of the parameters) for this
-    ladder, response and SM count, or None (the built-in choice is used)."""
-    ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate, response))
+    ladder, response, kernel kind and SM count, or None (the built-in choice
+    is used)."""
+    ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate, response, tensor_cores))
     if not ent:
         return None
     best = ent.get(str(sms)) or ent.get("any")
@@ -115,32 +118,35 @@ def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), group
 
 
 def _compile_one(args):
-    n, t_min, t_max, nms, shape, response = args
+    n, t_min, t_max, nms, shape, response, tc = args
     sys.path.insert(0, os.path.dirname(PKG))
     from paper_2108_12050_gb300 import _native
     t0 = time.time()
     try:
         _native.precompile(n=n, t_min=t_min, t_max=t_max, nms=nms, tile_shape=shape,
-                           response=response)
+                           response=response, tensor_cores=tc)
         return shape, time.time() - t0, None
     except Exception as e:  # a shape the compiler rejects is skipped
         return shape, time.time() - t0, str(e)
 
 
-def precompile_all(n, t_min, t_max, nms, cands, workers=None, response="dog"):
+def precompile_all(n, t_min, t_max, nms, cands, workers=None, response="dog",
+                   tensor_cores=False):
     ctx = mp.get_context("spawn")
     workers = workers or (os.cpu_count() or 4)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
-        return list(ex.map(_compile_one, [(n, t_min, t_max, nms, c, response) for c in cands]))
+        return list(ex.map(_compile_one, [(n, t_min, t_max, nms, c, response, tensor_cores)
+                                          for c in cands]))
 
 
-def measure(n, t_min, t_max, nms, threshold, img_dev, cands, reps=5, response="dog"):
+def measure(n, t_min, t_max, nms, threshold, img_dev, cands, reps=5, response="dog",
+            tensor_cores=False):
     import paper_2108_12050_gb300 as mhfd
     res = []
     for shape in cands:
         try:
             det = mhfd.Detector(n, t_min, t_max, threshold=threshold, nms=nms, tile_shape=shape,
-                                timing=True, response=response)
+                                timing=True, response=response, tensor_cores=tensor_cores)
         except Exception as e:
             res.append((shape, None, str(e)))
             continue
@@ -168,12 +174,22 @@ def main():
     ap.add_argument("--rbs", default="2,3,4,5,6,8", help="rows per step of the extra shapes")
     ap.add_argument("--groups", default="2,3,4,5", help="level groups of the extra shapes")
     ap.add_argument("--response", default="dog", choices=["dog", "log"])
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="tune the tensor-core kernel (its own shape menu)")
     ap.add_argument("--write", action="store_true", help="record the winner in tuned_tiles.json")
     args = ap.parse_args()
     nms = 0 if args.nms == "paper" else 1
-    cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None, args.min_width,
-                       args.response)
-    if args.widths:
+    if args.tensor_cores:
+        from . import _native
+        cands = [c for c in _native.tile_configs(n=args.n, t_min=args.tmin, t_max=args.tmax,
+                                                 nms=nms, tensor_cores=True)
+                 if c[0] >= args.min_width]
+        if args.limit:
+            cands = cands[:args.limit]
+    else:
+        cands = candidates(args.n, args.tmin, args.tmax, nms, args.limit or None,
+                           args.min_width, args.response)
+    if args.widths and not args.tensor_cores:
         extra = width_candidates(args.n, args.tmin, args.tmax, nms,
                                  [int(w) for w in args.widths.split(",")],
                                  rbs=[int(v) for v in args.rbs.split(",")],
@@ -181,7 +197,8 @@ def main():
                                  response=args.response)
         cands += [c for c in extra if c not in cands]
     t0 = time.time()
-    comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands, response=args.response)
+    comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands, response=args.response,
+                          tensor_cores=args.tensor_cores)
     print("compiled %d shapes in %.1f s" % (len(comp), time.time() - t0), flush=True)
     bad = {tuple(c) for c, _, e in comp if e}
     cands = [c for c in cands if tuple(c) not in bad]
@@ -193,7 +210,7 @@ def main():
     img = synth.sweep_tile_4096_u16(0.0)[:args.side, :args.side].copy()
     dev = torch.from_numpy(img.view(np.int16)).cuda()
     res = measure(args.n, args.tmin, args.tmax, nms, args.threshold, dev, cands,
-                  response=args.response)
+                  response=args.response, tensor_cores=args.tensor_cores)
     res.sort(key=lambda r: (r[1] is None, r[1] or 0))
     for shape, ms, err in res:
         print("%-28s %s" % (shape, ("%.3f ms" % ms) if ms else err), flush=True)
@@ -203,7 +220,8 @@ def main():
     if args.write and best[1]:
         tab = load_table()
         ent = tab.setdefault(ladder_key(args.n, args.tmin, args.tmax, nms,
-                                        response=args.response), {})
+                                        response=args.response,
+                                        tensor_cores=args.tensor_cores), {})
         ent[str(sms)] = {"shape": list(best[0]), "ms": best[1], "side": args.side}
         with open(TABLE, "w") as f:
             json.dump(tab, f, indent=1, sort_keys=True)
