@@ -11,8 +11,8 @@ larger than L2, so consecutive steps do not hit in L2.
 
 Prints ONE JSON line.  `value` is whole-job Mpixel/s (all ranks); extra keys
 give p50/p99 ms per tile, the unfused plain path on the same tiles, the
-roofline of the fused kernel (FP32 FFMA issue bound), the FP64 CPU oracle on a
-bounded sample, the end-to-end rate through the host-buffer entry point, the
+roofline of the fused kernel (FP32 bound; its vertical pass runs on the tensor
+cores), the FP64 CPU oracle on a bounded sample, the end-to-end rate through the host-buffer entry point, the
 SM clocks sampled during the timed region and the focus scores of the sweep.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -53,6 +53,14 @@ def algorithmic_ops_per_px():
     one max/argmax op per layer, and the 3x3 comparison."""
     _, R = ladder_radii()
     return sum(2 * (2 * r + 1) for r in R) + 2 * N_LAYERS + 8
+
+
+def ffma_side_ops_per_px():
+    """The part of algorithmic_ops_per_px() the tensor-core kernel leaves on
+    the FP32 pipe: the horizontal pass (2R+1 per level), the DoG, the
+    max/argmax and the 3x3 comparison (the vertical pass runs as MMAs)."""
+    _, R = ladder_radii()
+    return sum(2 * r + 1 for r in R) + 2 * N_LAYERS + 8
 
 
 def nominal_alu_peak():
@@ -276,7 +284,10 @@ def main():
     # fused kernel; CUDA events on the launching stream bracket the region.
     streams = [torch.cuda.Stream() for _ in tiles]
     kernel_ms = []
-    launches_per_tile = 17  # stretch 5, fused 1, gather 2, prune 5, output 4 (ncu launch list)
+    # stretch 5, fused 1 (+ 1: the gated FFMA companion of the tensor-core
+    # kernel, which returns at once for these tiles), gather 2, prune 5,
+    # output 4 (ncu launch list)
+    launches_per_tile = 17 + (1 if dets[0].uses_tensor_cores else 0)
     with ClockSampler(local) as clk:
         barrier()
         t_start = torch.cuda.Event(enable_timing=True)
@@ -335,21 +346,33 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- roofline of the fused kernel (FP32 FFMA issue bound)
+    # ---- roofline of the fused kernel: the algorithm's FP32 work per pixel
+    # (both separable passes, DoG, maxima) over the FP32 FFMA peak.  With the
+    # tensor-core kernel the vertical pass runs as MMAs, so the FP32 pipe
+    # carries only the rest ("ffma_side"), and frac may exceed what an
+    # FFMA-only kernel could reach
     ops = algorithmic_ops_per_px() * H * W
     k_avg = statistics.mean(kernel_ms)
     achieved = ops / (k_avg * 1e-3) / 1e12
     peak = nominal_alu_peak() / 1e12
     probe = mhfd.probe_ffma_peak() / 1e12
     traffic = profiled_traffic()
+    tc = dets[0].uses_tensor_cores
+    side = ffma_side_ops_per_px() * H * W / (k_avg * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 FFMA)",
             "frac": achieved / peak, "traffic": traffic,
             "peak_note": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal; no FP32 figure in "
                          "MEASURED_PEAKS)", "probe_measured_peak": probe,
             "frac_of_probe": achieved / probe, "ops_per_px": algorithmic_ops_per_px(),
+            "vertical_pass": "tensor cores (tcgen05 MMA, fp16 parts, f32 accumulate)" if tc
+                             else "FP32 FFMA",
+            "ffma_side": {"ops_per_px": ffma_side_ops_per_px(), "achieved": side,
+                          "frac": side / peak} if tc else None,
             "kernel_ms_avg": k_avg,
-            "kernel_timing": "CUDA events on the launching stream around each fused launch, "
-                             "%d launches of the single-stream latency loop" % len(kernel_ms)}
+            "kernel_timing": "CUDA events on the launching stream around each fused launch "
+                             "(with the tensor-core kernel also its gated FFMA companion, "
+                             "which returns at once for these tiles), %d launches of the "
+                             "single-stream latency loop" % len(kernel_ms)}
 
     # ---- plain (unfused) path on the same tiles
     plain = None
@@ -462,6 +485,8 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
     kw = dict(threshold=THR, overlap=OVERLAP, nms="paper")
     return {
         "fused_reflect": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), False),
+        "fused_reflect_ffma": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, tensor_cores=False,
+                                                  **kw), False),
         "fused_periodic": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, boundary="periodic",
                                               **kw), False),
         "fused_local26": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX,
@@ -700,10 +725,11 @@ def tile_used(mhfd):
     import torch
     from paper_2108_12050_gb300 import tune
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    tuned = tune.lookup(N_LAYERS, T_MIN, T_MAX, "paper", sms)
-    shape = tuned or mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX)
+    tuned = tune.lookup(N_LAYERS, T_MIN, T_MAX, "paper", sms, tensor_cores=True)
+    shape = tuned or mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX, tensor_cores=True)
     return {"width": shape[0], "height": shape[1], "rows_per_step": shape[2],
             "threads": shape[3], "level_groups": shape[4],
+            "vertical_pass": "tensor cores",
             "source": "autotuned" if tuned else "heuristic"}
 
 

@@ -103,8 +103,9 @@ typedef struct {
                                take the FFMA kernel (same results within the
                                FP32 tolerance).  tile_shape / tile_override
                                then describe the tensor-core kernel (four rows
-                               per step, threads a multiple of 128).  0: FFMA
-                               only.  Default 0 */
+                               per step, at least 128 threads).  The paper
+                               rule with the DoG response only; 0: FFMA
+                               only.  Default 1 */
 } mhfd_params;
 
 /* A detected feature.  scale_idx is the 0-based DoG layer i-1; sigma = t_i,

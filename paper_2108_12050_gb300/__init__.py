@@ -118,16 +118,17 @@ class Detector:
     maximum rule (``"paper"``: argmax over scales then 3x3 max-pool;
     ``"local26"``: 3x3x3 scale-space maxima), the kernel truncation and the
     stretch saturation fraction.  ``sigmas`` gives an explicit ladder of
-    ``n+1`` scales instead.  ``tensor_cores=True`` runs the vertical blur of
-    the fused kernel on the tensor cores (DoG detection of uint8 images and
-    of uint16 images whose stretch range is at most 4095; the FFMA kernel
-    takes everything else).
+    ``n+1`` scales instead.  ``tensor_cores`` (default) runs the vertical
+    blur of the fused kernel on the tensor cores for the paper rule with the
+    DoG response on uint8 images and on uint16 images whose stretch range is
+    at most 4095; the FFMA kernel takes everything else (``False``: FFMA
+    only).
     """
 
     def __init__(self, n=10, t_min=1.0, t_max=10.0, *, sigmas=None, threshold=0.1, overlap=0.5,
                  nms="paper", truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
                  device=None, keep_candidates=False, tile_override=None, tile_shape=None,
-                 timing=False, response="dog", boundary="reflect", tensor_cores=False):
+                 timing=False, response="dog", boundary="reflect", tensor_cores=True):
         import torch
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
@@ -137,9 +138,10 @@ class Detector:
             if sigmas is None and device >= 0:
                 from . import tune
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
+                is_log = response in ("log", 1)
+                tc = bool(tensor_cores) and nms in ("paper", 0) and not is_log
                 tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate,
-                                         "log" if response in ("log", 1) else "dog",
-                                         tensor_cores=bool(tensor_cores))
+                                         "log" if is_log else "dog", tensor_cores=tc)
         tile_override = tile_override or 0
         self.n = int(n)
         self.device = device

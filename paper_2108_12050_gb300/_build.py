@@ -113,10 +113,11 @@ def _precompile_one(args):
     n, tmin, tmax, nms, store = args[:5]
     shape = args[5] if len(args) > 5 else None
     response = args[6] if len(args) > 6 else "dog"
+    tc = args[7] if len(args) > 7 else True
     sys.path.insert(0, os.path.dirname(PKG))
     from paper_2108_12050_gb300 import _native
     return _native.precompile(n=n, t_min=tmin, t_max=tmax, nms=nms, store=store,
-                              tile_shape=shape, response=response)
+                              tile_shape=shape, response=response, tensor_cores=tc)
 
 
 def _tuned_variants():
@@ -130,7 +131,7 @@ def _tuned_variants():
     except Exception:
         return out
     for key, ent in tab.items():
-        m = re.match(r"n(\d+)_t([0-9.e+-]+)-([0-9.e+-]+)_(paper|local26)_tr4(_log)?$", key)
+        m = re.match(r"n(\d+)_t([0-9.e+-]+)-([0-9.e+-]+)_(paper|local26)_tr4(_log)?(_tc)?$", key)
         if not m:
             continue
         for best in ent.values():
@@ -138,10 +139,15 @@ def _tuned_variants():
             if shape and len(shape) == 5:
                 nms = 0 if m.group(4) == "paper" else 1
                 log = m.group(5) is not None
+                tc = m.group(6) is not None
+                # an FFMA shape of the paper rule serves detectors built with
+                # tensor_cores=False; a tensor-core shape, with its companion
+                # (which the soft score also uses), the default ones
                 stores = (0, 1) if (nms == 1 or log) else (0, 1, 2)
                 for store in stores:
                     out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)), nms,
-                                store, tuple(int(v) for v in shape), "log" if log else "dog"))
+                                store, tuple(int(v) for v in shape), "log" if log else "dog",
+                                tc))
     return out
 
 

@@ -148,7 +148,7 @@ def check(rc, allow_overflow=True):
 def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap=0.5,
                 nms=NMS_PAPER, truncate=4.0, clip_frac=0.00175, max_candidates=1 << 20,
                 device=-1, keep_candidates=False, tile_override=0, tile_shape=None, timing=False,
-                response=0, boundary=0, tensor_cores=False):
+                response=0, boundary=0, tensor_cores=True):
     p = Params()
     lib().mhfd_default_params(ctypes.byref(p))
     p.n = int(n)

@@ -61,6 +61,7 @@ struct mhfd_detector {
     float *soft_D = nullptr;      // the n D planes of the adjoint's forward
     size_t soft_D_px = 0;
     std::vector<uint64_t> params;  // by-value parameter block of the fused kernel
+    std::vector<uint64_t> params2; // that of the second (gated) batch launch
 
     // fixed device buffers
     SelState *sel = nullptr;
@@ -552,7 +553,7 @@ int batch_reserve(mhfd_detector *d, int n, long long total_items, long long tota
         b.exec = nullptr;
         b.key.clear();
     }
-    if (!b.d_queue && ((rc = dalloc(&b.d_queue, 1)) || (rc = dalloc(&b.d_arena_n, 1)))) return rc;
+    if (!b.d_queue && ((rc = dalloc(&b.d_queue, 2)) || (rc = dalloc(&b.d_arena_n, 1)))) return rc;
     const unsigned long long want = (unsigned long long)(total_px / 32) > (unsigned long long)d->cap
                                         ? (unsigned long long)(total_px / 32)
                                         : (unsigned long long)d->cap;
@@ -606,35 +607,43 @@ int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long lo
     MHFD_CUDA(cudaMemcpyAsync(b.d_jobs, b.h_jobs, sizeof(MhfdJob) * n, cudaMemcpyHostToDevice, s));
     MHFD_CUDA(cudaMemcpyAsync(b.d_ranks, b.h_ranks, sizeof(long long) * n, cudaMemcpyHostToDevice, s));
     MHFD_CUDA(cudaMemsetAsync(b.d_arena_n, 0, sizeof(unsigned long long), s));
-    MHFD_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int), s));
+    MHFD_CUDA(cudaMemsetAsync(b.d_queue, 0, 2 * sizeof(int), s));
     int rc = enqueue_stretch_batch(b.d_jobs, n, max_passes, max_rows, b.d_ranks, b.d_sels,
                                    b.d_sts, s);
     if (rc) return rc;
-    // one persistent launch over every tile of every image
-    Variant *v = d->var;
+    // one persistent launch over every tile of every image; with the
+    // tensor-core pass, two gated launches (each takes its images' chunks
+    // from its own queue and skips the rest)
     int dev = 0, sms = 1;
     MHFD_CUDA(cudaGetDevice(&dev));
     MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    d->params.assign((v->param_bytes + 7) / 8 + 1, 0);
-    MhfdKHeader h;
-    std::memset(&h, 0, sizeof(h));
-    h.stage = d->stage;
-    h.tile_count = d->tile_count;
-    h.cap_tile = d->cap_tile;
-    h.thr = d->p.threshold;
-    h.jobs = b.d_jobs;
-    h.queue = b.d_queue;
-    h.n_jobs = n;
-    h.total_items = (int)total_chunks;
-    h.chunk = batch_chunk(d);
-    std::memcpy(d->params.data(), &h, sizeof(h));
-    void *args[] = {d->params.data()};
-    const long long wave = (long long)sms * v->occupancy;
-    const unsigned grid = (unsigned)(total_chunks < wave ? total_chunks : wave);
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k0, s));
-    const CUresult r = drv().launchKernel(v->fn, grid, 1, 1, (unsigned)v->cfg.nt, 1, 1,
-                                          (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
-    if (r != CUDA_SUCCESS) return fail(MHFD_ERR_CUDA, "cuLaunchKernel (batch)");
+    const int nl = d->use_tc ? 2 : 1;
+    for (int k = 0; k < nl; ++k) {
+        Variant *v = (d->use_tc && k == 0) ? d->var_tc : d->var;
+        std::vector<uint64_t> &pv = k == 0 ? d->params : d->params2;
+        pv.assign((v->param_bytes + 7) / 8 + 1, 0);
+        MhfdKHeader h;
+        std::memset(&h, 0, sizeof(h));
+        h.stage = d->stage;
+        h.tile_count = d->tile_count;
+        h.cap_tile = d->cap_tile;
+        h.thr = d->p.threshold;
+        h.jobs = b.d_jobs;
+        h.queue = b.d_queue + k;
+        h.n_jobs = n;
+        h.total_items = (int)total_chunks;
+        h.chunk = batch_chunk(d);
+        h.gate = d->use_tc ? (k == 0 ? 1 : 2) : 0;
+        h.flag = &d->cnt->ktimeout;
+        std::memcpy(pv.data(), &h, sizeof(h));
+        void *args[] = {pv.data()};
+        const long long wave = (long long)sms * v->occupancy;
+        const unsigned grid = (unsigned)(total_chunks < wave ? total_chunks : wave);
+        const CUresult r = drv().launchKernel(v->fn, grid, 1, 1, (unsigned)v->cfg.nt, 1, 1,
+                                              (unsigned)v->smem_bytes, (CUstream)s, args, nullptr);
+        if (r != CUDA_SUCCESS) return fail(MHFD_ERR_CUDA, "cuLaunchKernel (batch)");
+    }
     if (d->timed) MHFD_CUDA(cudaEventRecord(d->ev_k1, s));
     // per image: gather its tiles, prune, compact into the shared blob arena
     for (int j = 0; j < n; ++j) {
@@ -740,7 +749,7 @@ void mhfd_default_params(mhfd_params *p) {
     p->timing = 0;
     p->response = MHFD_RESPONSE_DOG;
     p->boundary = MHFD_BOUNDARY_REFLECT;
-    p->tensor_cores = 0;
+    p->tensor_cores = 1;
 }
 
 const char *mhfd_last_error(void) { return mhfd::t_err.c_str(); }
@@ -1044,18 +1053,19 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     std::vector<int> tapoff;
     std::vector<float> taps_all, tsc_all;
     make_taps(t, R, &taps_all, &tapoff, &tsc_all);
-    TileConfig cfg;
-    if (p->tensor_cores && tc_mode_ok(mode) && (store == 0 || store == 1)) {
-        // the tensor-core kernel and its FFMA companion
-        TileConfig ct;
+    // the shapes a detector with these parameters uses: the tensor-core
+    // kernel and its FFMA companion (which the soft score also runs), or the
+    // FFMA kernel alone
+    TileConfig cfg, ct;
+    const bool use_tc = p->tensor_cores && tc_mode_ok(mode);
+    if (use_tc) {
         if ((rc = resolve_tile(lk.R, mode, *p, &ct, true))) return rc;
         if (!companion_tile(lk.R, mode, ct, &cfg))
             return fail(MHFD_ERR_UNSUPPORTED,
                         "no FFMA tile shape shares the tensor-core kernel's strip width");
-        if ((rc = precompile_variant(lk, p->nms, store != 0, ct))) return rc;
-        return precompile_variant(lk, p->nms, store != 0, cfg);
+    } else if ((rc = resolve_tile(lk.R, mode, *p, &cfg))) {
+        return rc;
     }
-    if ((rc = resolve_tile(lk.R, mode, *p, &cfg))) return rc;
     if ((store == 2 || store == 3) && lk.response)
         return fail(MHFD_ERR_UNSUPPORTED, "the soft score uses the DoG response");
     if (store == 2) return precompile_variant(lk, 2, 0, cfg);  // soft-score forward
@@ -1073,6 +1083,7 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
         }
         return MHFD_OK;
     }
+    if (use_tc && (rc = precompile_variant(lk, p->nms, store != 0, ct))) return rc;
     return precompile_variant(lk, p->nms, store != 0, cfg);
 }
 

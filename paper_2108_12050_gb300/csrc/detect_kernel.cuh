@@ -1430,6 +1430,9 @@ __device__ __forceinline__ void batch_loop(const KParams &p, const Smem &sm, TcS
             if (p.h.jobs[mid].chunk_base <= item) lo = mid; else hi = mid - 1;
         }
         const MhfdJob job = p.h.jobs[lo];
+        // gated batches: the tensor-core launch takes the images whose
+        // stretch range it holds exactly, the FFMA launch the others
+        if (p.h.gate != 0 && (p.h.gate == 1) != tc_narrow(job.dtype, *job.st)) continue;
         MhfdKHeader h = p.h;
         h.img = job.img;
         h.st = job.st;
@@ -1470,7 +1473,8 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
     sm.ctrl = reinterpret_cast<unsigned char *>(sm.scan) + 4 * 64;
 
     // single image with a gate: the tensor-core kernel takes narrow stretch
-    // ranges, its FFMA companion the rest (both launched, one works)
+    // ranges, its FFMA companion the rest (both launched, one works); a batch
+    // applies the gate per image
     if (p.h.jobs == nullptr && p.h.gate != 0) {
         const bool narrow = tc_narrow(p.h.dtype, *p.h.st);
         if ((p.h.gate == 1) != narrow) return;

@@ -312,7 +312,9 @@ namespace {
 double cost_model(const std::vector<int> &R, int mode, const TileConfig &c);
 }
 
-bool tc_mode_ok(int mode) { return (mode & kModeLog) == 0 && (mode & 3) <= 1; }
+// the paper rule with the DoG response (the 26-neighbour rule's ring of all
+// layers leaves too little shared memory for a useful tensor-core strip)
+bool tc_mode_ok(int mode) { return mode == 0; }
 
 bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why) {
     auto no = [&](const char *m) {

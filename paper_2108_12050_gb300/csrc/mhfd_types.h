@@ -59,11 +59,11 @@ struct MhfdKHeader {
     int chunk;                // batch mode: tiles per queue item
     float soft_tau;           // soft-score forward: threshold of the sigmoid
     float soft_inv_t;         //   and its inverse temperature
-    int gate;                 // single image: 0 always run; 1 only when the
+    int gate;                 // 0 always run; 1 only for an image whose
                               // stretch range is narrow (uint8, or uint16 with
                               // hi - lo <= 4095: the range the tensor-core
                               // vertical pass holds exactly in fp16); 2 only
-                              // when it is not
+                              // for the others (per image in a batch)
     double *soft_part;        //   per-block, per-layer sums (zeroed before launch)
     int *flag;                // set to 1 when a bounded wait gives up (or null)
 };

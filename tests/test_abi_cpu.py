@@ -76,6 +76,7 @@ def test_null_arguments(native):
 def test_tile_menu_fits_shared_memory(native):
     for kw in (dict(n=10, t_min=1, t_max=10), dict(n=16, t_min=1, t_max=12),
                dict(n=16, t_min=1, t_max=12, nms=1)):
+        kw["tensor_cores"] = False
         menu = native.tile_configs(**kw)
         assert len(menu) > 10
         for tx2, ty2, rb, nt, ng in menu:
@@ -92,8 +93,39 @@ def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
     assert any(f.endswith(".cubin") for f in files)
 
 
+def test_tensor_core_tile_menu(native):
+    """The tensor-core kernel's shapes: four rows per step, whole warps, at
+    least one warpgroup; the built-in choice leaves exactly one warp free of
+    horizontal items (the MMA issuer) and is on the menu."""
+    for kw in (dict(n=10, t_min=1, t_max=10), dict(n=16, t_min=1, t_max=12)):
+        menu = native.tile_configs(tensor_cores=True, **kw)
+        assert len(menu) > 10
+        for tx2, ty2, rb, nt, ng in menu:
+            assert rb == 4 and nt % 32 == 0 and nt >= 128 and tx2 <= 2 * nt
+        chosen = native.chosen_tile(tensor_cores=True, **kw)
+        assert chosen in menu and chosen[0] == chosen[3] - 32
+    # the 26-neighbour rule and the LoG response take the FFMA kernel: the
+    # flag changes nothing for them
+    for kw in (dict(n=16, t_min=1, t_max=12, nms=1), dict(n=16, t_min=1, t_max=12, response=1)):
+        assert native.chosen_tile(tensor_cores=True, **kw) == native.chosen_tile(
+            tensor_cores=False, **kw)
+
+
+def test_explicit_tensor_core_tile_shape(native):
+    kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=True)
+    assert native.chosen_tile(tile_shape=(352, 18, 4, 384, 3), **kw) == (352, 18, 4, 384, 3)
+    # rows per step other than 4, threads below a warpgroup: unsupported
+    for bad in ((352, 18, 8, 384, 3), (96, 18, 4, 96, 1)):
+        with pytest.raises(native.MhfdError) as e:
+            native.chosen_tile(tile_shape=bad, **kw)
+        assert e.value.code == -2, bad
+    with pytest.raises(native.MhfdError) as e:
+        native.chosen_tile(tile_shape=(350, 18, 4, 384, 3), **kw)
+    assert e.value.code == -1
+
+
 def test_explicit_tile_shape(native):
-    kw = dict(n=16, t_min=1.0, t_max=12.0)
+    kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=False)
     assert native.chosen_tile(tile_shape=(320, 18, 4, 448, 3), **kw) == (320, 18, 4, 448, 3)
     # out of range: width not a multiple of 4, threads not a multiple of 32,
     # too few rows per step, more groups than levels, more than two row
@@ -113,7 +145,7 @@ def test_heuristic_tile_is_one_vertical_round(native):
     import math
     for kw in (dict(n=16, t_min=1.0, t_max=12.0), dict(n=10, t_min=1.0, t_max=10.0),
                dict(n=4, t_min=1.0, t_max=4.0)):
-        tx2, ty2, rb, nt, ng = native.chosen_tile(**kw)
+        tx2, ty2, rb, nt, ng = native.chosen_tile(tensor_cores=False, **kw)
         dt = (kw["t_max"] - kw["t_min"]) / kw["n"]
         rmax = max(math.ceil(4 * (kw["t_min"] + i * dt)) for i in range(kw["n"] + 1))
         assert nt >= tx2 + 2 * rmax and rb * tx2 // 4 <= nt
@@ -128,10 +160,11 @@ def test_tuned_shapes_are_valid_for_their_ladders(native):
     tab = json.load(open(path))
     assert tab
     for key, ent in tab.items():
-        m = re.match(r"n(\d+)_t([0-9.e+-]+)-([0-9.e+-]+)_(paper|local26)_tr4(_log)?$", key)
+        m = re.match(r"n(\d+)_t([0-9.e+-]+)-([0-9.e+-]+)_(paper|local26)_tr4(_log)?(_tc)?$", key)
         assert m, key
         kw = dict(n=int(m.group(1)), t_min=float(m.group(2)), t_max=float(m.group(3)),
-                  nms=m.group(4), response="log" if m.group(5) else "dog")
+                  nms=m.group(4), response="log" if m.group(5) else "dog",
+                  tensor_cores=m.group(6) is not None)
         for best in ent.values():
             shape = tuple(best["shape"])
             assert native.chosen_tile(tile_shape=shape, **kw) == shape

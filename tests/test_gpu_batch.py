@@ -1,8 +1,12 @@
-"""Batched detection (one persistent launch, CUDA graph) vs single detections.
+"""Batched detection (persistent launches, CUDA graph) vs single detections.
 
 Each image's result in a batch of uneven sizes and mixed dtypes must be
 bit-identical to detecting it alone (the fused kernel is deterministic per
-tile and the per-image post-processing runs in the same order)."""
+tile and the per-image post-processing runs in the same order).  With the
+tensor-core pass a batch runs two gated persistent launches: the
+tensor-core kernel takes the images whose stretch range it holds exactly,
+the FFMA kernel the others (float images, wide uint16 ranges) - the same
+kernel each image gets alone."""
 import numpy as np
 import pytest
 
@@ -24,17 +28,22 @@ def _batch_images():
     for j, (H, W, dt) in enumerate([(300, 410, "u16"), (256, 256, "u8"), (517, 130, "u16"),
                                     (64, 900, "u8"), (401, 333, "u16"), (97, 97, "f32")]):
         imgs.append(synth.make_scene(700 + j, synth.scene12bit_spec(1.0 + j, H, W, dt)))
+    # a uint16 image whose stretch range exceeds 4095 (FFMA kernel)
+    wide = synth.make_scene(720, synth.scene12bit_spec(0.0, 200, 240, "u16"))
+    imgs.insert(3, (wide.astype(np.uint32) * 9).clip(0, 65535).astype(np.uint16))
     return imgs
 
 
-def test_batch_equals_single_detections():
+@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
+def test_batch_equals_single_detections(tc):
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     import paper_2108_12050_gb300 as mhfd
     torch.cuda.set_device(0)
     imgs = _batch_images()
     devs = [_dev(i) for i in imgs]
-    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5)
+    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5, tensor_cores=tc)
+    assert det.uses_tensor_cores == tc
     singles = [det(d) for d in devs]
     for rep in range(3):          # capture, then replays of the graph
         det.detect_batch(devs)

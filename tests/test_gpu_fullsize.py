@@ -37,12 +37,16 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=[True, False], ids=["tc", "ffma"])
+def full(request):
+    """The benchmark's tile through the tensor-core kernel (the default) and
+    through the FFMA kernel."""
     import paper_2108_12050_gb300 as mhfd
     img = synth.sweep_tile_4096_u16(0.0)
     dev = torch.from_numpy(img.view(np.int16)).cuda()
-    det = mhfd.Detector(N, TMIN, TMAX, threshold=THR, overlap=OVERLAP, keep_candidates=True)
+    det = mhfd.Detector(N, TMIN, TMAX, threshold=THR, overlap=OVERLAP, keep_candidates=True,
+                        tensor_cores=request.param)
+    assert det.uses_tensor_cores == request.param
     res = det(dev)
     yield img, res
     det.close()

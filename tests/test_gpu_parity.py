@@ -2,7 +2,8 @@
 
 Sizes span several fused-kernel tiles and ragged tails; edge cases cover
 1-pixel-wide images, images narrower than the kernel radius, pitched rows,
-all three dtypes and a constant image."""
+all three dtypes and a constant image.  The paper rule runs on both fused
+kernels: the tensor-core vertical pass (the default) and the FFMA one."""
 import math
 import zlib
 
@@ -88,11 +89,12 @@ STACK_CASES = [
 ]
 
 
+@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
 @pytest.mark.parametrize("case", STACK_CASES, ids=lambda c: c[0])
-def test_response_stack_within_tolerance(case):
+def test_response_stack_within_tolerance(case, tc):
     name, seed, H, W, dtype, n, tmin, tmax = case
     img = scene(seed, H, W, dtype)
-    det = detector(n=n, t_min=tmin, t_max=tmax, threshold=0.1)
+    det = detector(n=n, t_min=tmin, t_max=tmax, threshold=0.1, tensor_cores=tc)
     D, M, A, res = det.debug_stack(to_dev(img))
     D_ref, (lo, hi), t = ref_stack(img, n, tmin, tmax)
     assert (res.lo, res.hi) == (np.float32(lo), np.float32(hi))
@@ -140,9 +142,10 @@ def _variant_stack(img, n, tmin, tmax, response, boundary):
 
 
 def _check_detection(img, n, tmin, tmax, thr, overlap, nms, response="dog",
-                     boundary="reflect", plain=False):
+                     boundary="reflect", plain=False, tc=True):
     det = detector(n=n, t_min=tmin, t_max=tmax, threshold=thr, overlap=overlap, nms=nms,
-                   keep_candidates=True, response=response, boundary=boundary)
+                   keep_candidates=True, response=response, boundary=boundary,
+                   tensor_cores=tc)
     if plain:
         det.detect_plain(to_dev(img))
         res = det.wait()
@@ -202,11 +205,12 @@ def _check_detection(img, n, tmin, tmax, thr, overlap, nms, response="dog",
     return res, ref
 
 
+@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
 @pytest.mark.parametrize("which", ["A", "B"])
-def test_pair_512_uint8_end_to_end(which):
+def test_pair_512_uint8_end_to_end(which, tc):
     a, b = synth.pair512_u8(seed=1)
     img = a if which == "A" else b
-    _check_detection(img, 10, 1.0, 10.0, 0.1, 0.5, "paper")
+    _check_detection(img, 10, 1.0, 10.0, 0.1, 0.5, "paper", tc=tc)
 
 
 def test_pair_512_uint8_local26_end_to_end():
@@ -219,7 +223,40 @@ def test_pair_512_uint8_local26_end_to_end():
 def test_small_ladder_end_to_end(shape, dtype):
     img = scene(40 + shape[0], shape[0], shape[1], dtype)
     _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "paper")
+    _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "paper", tc=False)
     _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "local26")
+
+
+# ------------------------------------------------ tensor-core vertical pass
+
+def test_tensor_core_pass_is_used_where_it_applies():
+    assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1).uses_tensor_cores
+    assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
+                        tensor_cores=False).uses_tensor_cores
+    assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
+                        nms="local26").uses_tensor_cores
+    assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9,
+                        response="log").uses_tensor_cores
+
+
+@pytest.mark.parametrize("scale,kernel", [(1, "tensor cores"), (9, "FFMA companion")])
+def test_uint16_stretch_range_decides_the_kernel(scale, kernel):
+    """A uint16 image whose stretch range exceeds 4095 cannot be held exactly
+    as fp16 integers: the FFMA companion takes it (gated on the device).
+    Both ranges match the oracle's stack, and the two kernels agree on the
+    same image within the stack tolerance."""
+    base = scene(45, 180, 260, "u16")
+    img = (base.astype(np.uint32) * scale).clip(0, 65535).astype(np.uint16)
+    lo, hi = oracle.stretch_bounds(img)
+    assert (hi - lo > 4095) == (scale > 1)
+    det = detector(n=6, t_min=1.0, t_max=5.0, threshold=0.05)
+    D, _, _, res = det.debug_stack(to_dev(img))
+    D_ref, _, _ = ref_stack(img, 6, 1.0, 5.0)
+    assert_stack_close(D.cpu().numpy(), D_ref, kernel)
+    D2, _, _, _ = detector(n=6, t_min=1.0, t_max=5.0, threshold=0.05,
+                           tensor_cores=False).debug_stack(to_dev(img))
+    assert_stack_close(D.cpu().numpy(), D2.cpu().numpy().astype(np.float64), kernel + " vs FFMA")
+    _check_detection(img, 6, 1.0, 5.0, 0.05, 0.5, "paper")
 
 
 @pytest.mark.parametrize("overlap", [0.0, 0.3, 1.0])
@@ -323,19 +360,21 @@ def test_plain_path_matches_oracle():
 
 # -------------------------------------------------- variants (plain path)
 
-@pytest.mark.parametrize("response,boundary,nms,plain", [
+@pytest.mark.parametrize("response,boundary,nms,plain,tc", [
+    ("dog", "periodic", "paper", False, False), ("dog", "reflect", "paper", False, False)] + [
+    p + (True,) for p in [
     ("dog", "reflect", "paper", True), ("log", "reflect", "paper", True),
     ("dog", "periodic", "paper", True), ("log", "periodic", "paper", True),
     ("log", "reflect", "local26", True), ("dog", "periodic", "local26", True),
     ("dog", "periodic", "paper", False), ("dog", "periodic", "local26", False),
     ("log", "reflect", "paper", False), ("log", "periodic", "paper", False),
-    ("log", "reflect", "local26", False)])
-def test_variants_match_oracle(response, boundary, nms, plain):
+    ("log", "reflect", "local26", False)]])
+def test_variants_match_oracle(response, boundary, nms, plain, tc):
     a, _ = synth.pair512_u8(seed=6, H=200, W=270)
     # the LoG response lacks the DoG's factor dt (0.9 here): threshold scaled
     thr = 0.1 / 0.9 if response == "log" else 0.1
     _check_detection(a, 10, 1.0, 10.0, thr, 0.5, nms, response=response, boundary=boundary,
-                     plain=plain)
+                     plain=plain, tc=tc)
 
 
 def test_fused_periodic_stack_within_tolerance():
