@@ -1055,32 +1055,34 @@ struct Groups<NGROUPS> {
 
 // ------------------------------------------------------ 4-5. NMS, compaction
 
-// exclusive block scan of one int per thread; *sum receives the total
-__device__ __forceinline__ int block_excl_scan(int v, int *s_scan, int *sum) {
+// exclusive block scan of one int per thread; *sum receives the total.
+// One barrier: the warps' totals go to one of two halves of s_scan
+// (alternating with `par`), and every thread adds up the totals itself; the
+// barrier of the next scan separates this scan's reads from the writes of
+// the scan after it into the same half.
+__device__ __forceinline__ int block_excl_scan(int v, int *s_scan, int *sum, int &par) {
     constexpr int NW = NT / 32;
+    static_assert(NW <= 32, "two halves of 32 warp totals");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int *buf = s_scan + 32 * par;
+    par ^= 1;
     int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) s_scan[warp] = x;
+    if (lane == 31) buf[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        int w = lane < NW ? s_scan[lane] : 0;
+    int before = 0, total = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < NW) s_scan[lane] = w;
+    for (int w = 0; w < NW; ++w) {
+        const int t = buf[w];
+        before += w < warp ? t : 0;
+        total += t;
     }
-    __syncthreads();
-    const int excl = (warp > 0 ? s_scan[warp - 1] : 0) + x - v;
-    *sum = s_scan[NW - 1];
-    __syncthreads();
-    return excl;
+    *sum = total;
+    return before + x - v;
 }
 
 // paper rule: M > thr and M >= every 8-neighbour (out-of-image = -inf)
@@ -1123,7 +1125,8 @@ __device__ __forceinline__ bool cand_26(const float *s_ring, int r, int c, int l
 // order, so candidates come out ordered by row, column, layer.
 __device__ __forceinline__ int nms_rows(const MhfdKHeader &h, const March &m,
                                         const float *s_ring, const unsigned char *s_arg,
-                                        int *s_scan, int ra, int rb, long long slot, int total) {
+                                        int *s_scan, int &par, int ra, int rb, long long slot,
+                                        int total) {
     const int nrows = rb - ra + 1;
     const int items = nrows * TX;
     // contiguous runs of pixels per thread (candidates come out in row-major
@@ -1151,7 +1154,7 @@ __device__ __forceinline__ int nms_rows(const MhfdKHeader &h, const March &m,
         }
     }
     int sum;
-    int pos = total + block_excl_scan(cnt, s_scan, &sum);
+    int pos = total + block_excl_scan(cnt, s_scan, &sum, par);
     if (cnt) {
         MhfdCand *dst = h.stage + slot * h.cap_tile;
         auto put = [&](int r, int c, int l, float v) {
@@ -1253,6 +1256,7 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
     int base = 0;       // input row held in window row 0
     int tile = 0;       // tile (relative to ta) now receiving candidates
     int total = 0;      // its candidates so far
+    int par = 0;        // half of the scan buffer the next block scan uses
 #pragma unroll 1
     for (int s = 0; s < nsteps; ++s) {
         const bool more = s + 1 < nsteps;
@@ -1265,7 +1269,7 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
         while ((MODE == 0 || MODE == 1) && ra <= rb) {
             const int tend = min(m.Y, (tile + 1) * TY);  // last row of the tile
             const int re = min(rb, tend);
-            total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, ra, re,
+            total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, par, ra, re,
                              slot0 + (long long)(ta + tile) * tiles_x + tx, total);
             if (re == tend) {
                 if (threadIdx.x == 0)
@@ -1357,6 +1361,7 @@ __device__ __forceinline__ void march_tc(const MhfdKHeader &h, const MhfdStretch
     int base = 0;       // input row held in window row 0
     int tile = 0;       // tile (relative to ta) now receiving candidates
     int total = 0;      // its candidates so far
+    int par = 0;        // half of the scan buffer the next block scan uses
 #pragma unroll 1
     for (int s = 0; s < nsteps; ++s) {
         const bool more2 = s + 2 < nsteps;
@@ -1368,7 +1373,7 @@ __device__ __forceinline__ void march_tc(const MhfdKHeader &h, const MhfdStretch
         while (ra <= rb) {
             const int tend = min(m.Y, (tile + 1) * TY);
             const int re = min(rb, tend);
-            total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, ra, re,
+            total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, par, ra, re,
                              slot0 + (long long)(ta + tile) * tiles_x + tx, total);
             if (re == tend) {
                 if (threadIdx.x == 0)
