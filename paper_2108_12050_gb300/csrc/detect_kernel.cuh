@@ -125,7 +125,10 @@ constexpr int NT_COLS = (WEXT + MHFD_NT - 1) / MHFD_NT;  // input columns per th
 constexpr int RING = RB + 2;
 constexpr int NQ4 = TX2 / 4;
 constexpr int HITEMS = RB * NQ4;
-constexpr int HI = (HITEMS + NT - 1) / NT;
+// threads that take horizontal items: with the tensor-core pass and a
+// block of whole warpgroups plus one warp, that last warp only issues MMAs
+constexpr int NTW = (TC && NT % 128 == 32) ? NT - 32 : NT;
+constexpr int HI = (HITEMS + NTW - 1) / NTW;
 constexpr int NPARTS = (RB + 3) / 4;
 
 // padded width of the V row of level l (its outputs plus its own halo);
@@ -229,7 +232,8 @@ static_assert(NT % 32 == 0 && NT <= 1024, "threads per block");
 static_assert((MODE == 3 || LOG ? NL >= 1 : NL >= 2) && NL <= 64, "levels");
 static_assert(!LOG || MODE <= 1, "the LoG response is a detection mode");
 static_assert(kGB(0) == 0 && kGB(NGROUPS) == NL, "level groups");
-static_assert(!TC || (MODE <= 1 && !LOG && RB == 4 && NT % 128 == 0), "tensor-core vertical pass");
+static_assert(!TC || (MODE <= 1 && !LOG && (RB == 4 || RB == 8) && NT >= 128),
+              "tensor-core vertical pass");
 static_assert(!TC || TC_NMT * TC_NCT <= 512, "tensor memory columns");
 static_assert(!TC || BROWS >= WIN + 2 * RB + 16, "window rows of the tensor-core pass");
 static_assert(!TC || NGROUPS <= 12, "one mbarrier per group in the control block");
@@ -567,7 +571,9 @@ MK_HD constexpr unsigned tc_idesc(int n) {
 // The thread that issues the MMAs: lane 0 of the first warp without a
 // horizontal item when there is one (its issue then runs beside the
 // horizontal passes of the other warps), else thread 0.
-constexpr int TC_ISSUER = ((HITEMS + 31) / 32) * 32 < NT ? ((HITEMS + 31) / 32) * 32 : 0;
+constexpr int TC_ISSUER = NTW < NT                               ? NTW
+                          : ((HITEMS + 31) / 32) * 32 < NT ? ((HITEMS + 31) / 32) * 32
+                                                           : 0;
 
 struct TcState {
     unsigned tmem;   // tensor-memory base (lane 0, first column)
@@ -642,11 +648,22 @@ __device__ __forceinline__ void tc_wait(const MhfdKHeader &h, const TcState &tc,
     if (h.flag) atomicExch(h.flag, 1);
 }
 
-__device__ __forceinline__ void tc_ld4(unsigned addr, unsigned (&r)[4]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr)
-                 : "memory");
+// the RB accumulator columns of one level (rows j = 0 .. RB-1) of this
+// warp's 32 lanes
+__device__ __forceinline__ void tc_ld_rows(unsigned addr, unsigned (&r)[RB]) {
+    if constexpr (RB == 4) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                     : "r"(addr)
+                     : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7])
+            : "r"(addr)
+            : "memory");
+    }
 }
 
 // the RB prefetched rows into window rows [prow, prow + RB)
@@ -664,19 +681,21 @@ __device__ __forceinline__ void tc_store_prefetch(const Prefetch &pf, const TcSt
 
 // the loaded registers are only read after tcgen05.wait::ld: this empty
 // statement (ordered after the wait like every volatile asm) redefines them
-__device__ __forceinline__ void tc_regs_ready(unsigned (&r)[4]) {
-    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
+__device__ __forceinline__ void tc_regs_ready(unsigned (&r)[RB]) {
+#pragma unroll
+    for (int j = 0; j < RB; j += 4)
+        asm volatile("" : "+r"(r[j]), "+r"(r[j + 1]), "+r"(r[j + 2]), "+r"(r[j + 3]));
 }
 
 template <int G, int LI>
-__device__ __forceinline__ void tc_ld_levels(unsigned taddr, unsigned (*r)[4]) {
+__device__ __forceinline__ void tc_ld_levels(unsigned taddr, unsigned (*r)[RB]) {
     if constexpr (LI < kGB(G + 1) - kGB(G)) {
-        tc_ld4(taddr + (unsigned)(LI * RB), r[LI]);
+        tc_ld_rows(taddr + (unsigned)(LI * RB), r[LI]);
         tc_ld_levels<G, LI + 1>(taddr, r);
     }
 }
 template <int G, int LI>
-__device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (*r)[4], int c,
+__device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (*r)[RB], int c,
                                              const TcStretch &ts) {
     if constexpr (LI < kGB(G + 1) - kGB(G)) {
         constexpr int L = kGB(G) + LI;
@@ -697,14 +716,15 @@ __device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (
 template <int G>
 __device__ __forceinline__ void tc_read(const TcState &tc, float *s_v, const TcStretch &ts) {
     constexpr int NG = kGB(G + 1) - kGB(G);
-    constexpr int NWG = NT / 128;
+    constexpr int NWG = NT / 128;  // a last partial warpgroup does not read
     const int warp = threadIdx.x >> 5, q = warp & 3;
+    if ((warp >> 2) >= NWG) return;
     const int c0 = 32 * q + (threadIdx.x & 31);
 #pragma unroll 1
     for (int t = warp >> 2; t < TC_NMT; t += NWG) {
         const unsigned taddr =
             tc.tmem + ((unsigned)(32 * q) << 16) + (unsigned)(t * TC_NCT + tc_colg(G));
-        unsigned r[NG][4];
+        unsigned r[NG][RB];
         tc_ld_levels<G, 0>(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         tc_st_levels<G, 0>(s_v, r, 128 * t + c0, ts);
@@ -996,7 +1016,7 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
                                       int s) {
 #pragma unroll
     for (int it = 0; it < HI; ++it) {
-        const int item = threadIdx.x + it * NT;
+        const int item = threadIdx.x < NTW ? threadIdx.x + it * NTW : HITEMS;
         if (item < HITEMS) {
             const HCtx cx = make_ctx(h, m, item, s);
             const float *vrow = s_v + (cx.r - s * RB) * VROW;

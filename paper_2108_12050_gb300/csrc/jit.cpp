@@ -322,8 +322,8 @@ bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::
         return false;
     };
     if (!tc_mode_ok(mode)) return no("the tensor-core pass takes the DoG detection modes only");
-    if (c.rb != 4) return no("the tensor-core pass takes four rows per step");
-    if (c.nt % 128 || c.nt < 128 || c.nt > 1024) return no("threads: whole warpgroups");
+    if (c.rb != 4 && c.rb != 8) return no("the tensor-core pass takes four or eight rows per step");
+    if (c.nt % 32 || c.nt < 128 || c.nt > 1024) return no("threads: whole warps, at least one warpgroup");
     if (c.rb * (c.tx2 / 4) > 2 * c.nt) return no("more than two row quads per thread");
     if (c.gb.size() - 1 > 12) return no("at most 12 level groups");
     if (tc_tmem_cols(R, mode, c) > 512) return no("tensor memory holds 512 columns");
@@ -337,15 +337,20 @@ std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode) {
     std::vector<TileConfig> out;
     if (!tc_mode_ok(mode)) return out;
     const int nl = (int)R.size();
-    const int widths[] = {96, 128, 192, 224, 256, 320, 352, 384, 448, 480, 512};
+    const int widths[] = {96, 128, 192, 224, 256, 288, 320, 352, 384, 448, 480, 512};
+    const int threads[] = {128, 160, 256, 288, 384, 416, 512};
+    // four rows per step (eight rows run, through tile_shape, at about twice
+    // the time on GB300: two items a thread on two warps per scheduler)
+    for (int rb : {4})
     for (int tx2 : widths)
-        for (int nt = 128; nt <= 512; nt += 128) {
-            if (tx2 > 2 * nt || tx2 <= nt - 128) continue;  // items per thread 1..2, no idle warpgroup
+        for (int nt : threads) {
+            const int items = rb * (tx2 / 4);
+            if (items > 2 * nt || items <= nt - 128) continue;  // 1..2 items a thread, no idle warpgroup
             for (int ng = 1; ng <= 6 && ng <= nl; ++ng) {
                 TileConfig c;
                 c.tx2 = tx2;
                 c.ty2 = 2 + 16;
-                c.rb = 4;
+                c.rb = rb;
                 c.nt = nt;
                 c.gb.assign(ng + 1, 0);
                 for (int g = 0; g <= ng; ++g) c.gb[g] = (int)((long long)nl * g / ng);
@@ -399,7 +404,9 @@ bool choose_tile_tc(const std::vector<int> &R, int mode, TileConfig *cfg, std::s
     bool found = false;
     TileConfig comp;
     for (const TileConfig &c : menu) {
-        if (c.tx2 != c.nt - 32 || !companion_tile(R, mode, c, &comp)) continue;
+        if (c.rb != 4 || c.tx2 != c.nt - 32 || c.nt * 168 > 65536 ||
+            !companion_tile(R, mode, c, &comp))
+            continue;
         if (!found || c.tx2 > cfg->tx2 ||
             (c.tx2 == cfg->tx2 && c.gb.size() < cfg->gb.size())) {
             *cfg = c;

@@ -94,14 +94,15 @@ def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
 
 
 def test_tensor_core_tile_menu(native):
-    """The tensor-core kernel's shapes: four rows per step, whole warps, at
-    least one warpgroup; the built-in choice leaves exactly one warp free of
+    """The tensor-core kernel's shapes: four or eight rows per step, whole
+    warps, at least one warpgroup, one or two horizontal items per thread;
+    the built-in choice (four rows) leaves exactly one warp free of
     horizontal items (the MMA issuer) and is on the menu."""
     for kw in (dict(n=10, t_min=1, t_max=10), dict(n=16, t_min=1, t_max=12)):
         menu = native.tile_configs(tensor_cores=True, **kw)
         assert len(menu) > 10
         for tx2, ty2, rb, nt, ng in menu:
-            assert rb == 4 and nt % 32 == 0 and nt >= 128 and tx2 <= 2 * nt
+            assert rb in (4, 8) and nt % 32 == 0 and nt >= 128 and rb * tx2 // 4 <= 2 * nt
         chosen = native.chosen_tile(tensor_cores=True, **kw)
         assert chosen in menu and chosen[0] == chosen[3] - 32
     # the 26-neighbour rule and the LoG response take the FFMA kernel: the
@@ -114,8 +115,8 @@ def test_tensor_core_tile_menu(native):
 def test_explicit_tensor_core_tile_shape(native):
     kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=True)
     assert native.chosen_tile(tile_shape=(352, 18, 4, 384, 3), **kw) == (352, 18, 4, 384, 3)
-    # rows per step other than 4, threads below a warpgroup: unsupported
-    for bad in ((352, 18, 8, 384, 3), (96, 18, 4, 96, 1)):
+    # rows per step other than 4 or 8, threads below a warpgroup: unsupported
+    for bad in ((352, 18, 6, 384, 3), (96, 18, 4, 96, 1)):
         with pytest.raises(native.MhfdError) as e:
             native.chosen_tile(tile_shape=bad, **kw)
         assert e.value.code == -2, bad
