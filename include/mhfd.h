@@ -97,14 +97,14 @@ typedef struct {
     int32_t tensor_cores;   /* 1: the fused kernel's vertical blur runs on the
                                tensor cores (tcgen05, fp16 operands that hold
                                the window exactly and the taps as two parts,
-                               f32 accumulation) for DoG detection of uint8
+                               f32 accumulation) for detection of uint8
                                images and of uint16 images whose stretch range
                                hi - lo is at most 4095; other images and modes
                                take the FFMA kernel (same results within the
                                FP32 tolerance).  tile_shape / tile_override
                                then describe the tensor-core kernel (four rows
                                per step, at least 128 threads).  The paper
-                               rule with the DoG response only; 0: FFMA
+                               rule (DoG or LoG response) only; 0: FFMA
                                only.  Default 1 */
 } mhfd_params;
 

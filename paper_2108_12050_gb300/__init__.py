@@ -119,9 +119,9 @@ class Detector:
     ``"local26"``: 3x3x3 scale-space maxima), the kernel truncation and the
     stretch saturation fraction.  ``sigmas`` gives an explicit ladder of
     ``n+1`` scales instead.  ``tensor_cores`` (default) runs the vertical
-    blur of the fused kernel on the tensor cores for the paper rule with the
-    DoG response on uint8 images and on uint16 images whose stretch range is
-    at most 4095; the FFMA kernel takes everything else (``False``: FFMA
+    blur of the fused kernel on the tensor cores for the paper rule (DoG or
+    LoG response) on uint8 images and on uint16 images whose stretch range
+    is at most 4095; the FFMA kernel takes everything else (``False``: FFMA
     only).
     """
 
@@ -139,7 +139,7 @@ class Detector:
                 from . import tune
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
                 is_log = response in ("log", 1)
-                tc = bool(tensor_cores) and nms in ("paper", 0) and not is_log
+                tc = bool(tensor_cores) and nms in ("paper", 0)
                 tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate,
                                          "log" if is_log else "dog", tensor_cores=tc)
         tile_override = tile_override or 0

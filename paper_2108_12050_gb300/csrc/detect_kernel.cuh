@@ -201,7 +201,10 @@ constexpr int SMEM_RING_B = MODE == 0   ? ((RING * TX2 + 15) & ~15)
                             : MODE == 1 ? ((RING * TX2 * (int)sizeof(LMask) + 15) & ~15)
                                         : 0;
 MK_HD constexpr int tc_kgp(int g) { return (RB + 2 * group_rmax(g) + 15) & ~15; }
-MK_HD constexpr int tc_ngp(int g) { return ((kGB(g + 1) - kGB(g)) * RB + 15) & ~15; }
+// accumulator columns per level: RB rows, twice for the LoG (g and g'' rows)
+constexpr int TC_P = LOG ? 2 : 1;
+constexpr int TC_RC = RB * TC_P;
+MK_HD constexpr int tc_ngp(int g) { return ((kGB(g + 1) - kGB(g)) * TC_RC + 15) & ~15; }
 MK_HD constexpr int tc_colg(int g) {
     int o = 0;
     for (int j = 0; j < g; ++j) o += tc_ngp(j);
@@ -232,7 +235,7 @@ static_assert(NT % 32 == 0 && NT <= 1024, "threads per block");
 static_assert((MODE == 3 || LOG ? NL >= 1 : NL >= 2) && NL <= 64, "levels");
 static_assert(!LOG || MODE <= 1, "the LoG response is a detection mode");
 static_assert(kGB(0) == 0 && kGB(NGROUPS) == NL, "level groups");
-static_assert(!TC || (MODE <= 1 && !LOG && (RB == 4 || RB == 8) && NT >= 128),
+static_assert(!TC || ((MODE == 0 || (MODE == 1 && !LOG)) && (RB == 4 || RB == 8) && NT >= 128),
               "tensor-core vertical pass");
 static_assert(!TC || TC_NMT * TC_NCT <= 512, "tensor memory columns");
 static_assert(!TC || BROWS >= WIN + 2 * RB + 16, "window rows of the tensor-core pass");
@@ -422,15 +425,18 @@ __device__ __forceinline__ void shift_window(float *s_in, int from, int n) {
 // unreliable by the host).
 
 __device__ const float mk_taps_rt[NTAPS] = {MHFD_TAPS};
+__device__ const float mk_taps2_rt[] = {MHFD_TAPS2};
 struct TcTab {
     int r[NL];
     int off[NL];
+    int off2[NL];
 };
 MK_HD constexpr TcTab tc_tab() {
     TcTab t{};
     for (int l = 0; l < NL; ++l) {
         t.r[l] = kR(l);
         t.off[l] = tapoff(l);
+        t.off2[l] = tapoff2(l);
     }
     return t;
 }
@@ -540,13 +546,17 @@ __device__ __forceinline__ void tc_setup_smem(unsigned char *win, unsigned char 
             const int blk = q >> 6, e = q & 63;
             const int n = (blk / (kgp / 8)) * 8 + (e >> 3);
             const int k = (blk % (kgp / 8)) * 8 + (e & 7);
-            const int li = n / RB, j = n - li * RB;
+            // column n = level li x TC_RC + part x RB + row j (part 1: the
+            // LoG's second-difference taps, radius R + 1)
+            const int li = n / TC_RC, rem = n - li * TC_RC;
+            const int part2 = rem / RB, j = rem - part2 * RB;
             float v = 0.0f;
             if (li < ng) {
                 const int l = lb + li;
                 int d = k - j - rg;
                 d = d < 0 ? -d : d;
-                if (d <= mk_tctab.r[l]) v = mk_taps_rt[mk_tctab.off[l] + d] * TC_S;
+                if (!part2 && d <= mk_tctab.r[l]) v = mk_taps_rt[mk_tctab.off[l] + d] * TC_S;
+                if (part2 && d <= mk_tctab.r[l] + 1) v = mk_taps2_rt[mk_tctab.off2[l] + d] * TC_S;
             }
             const unsigned short hi = f2h_rn(v);
             p0[q] = hi;
@@ -648,22 +658,27 @@ __device__ __forceinline__ void tc_wait(const MhfdKHeader &h, const TcState &tc,
     if (h.flag) atomicExch(h.flag, 1);
 }
 
-// the RB accumulator columns of one level (rows j = 0 .. RB-1) of this
-// warp's 32 lanes
-__device__ __forceinline__ void tc_ld_rows(unsigned addr, unsigned (&r)[RB]) {
-    if constexpr (RB == 4) {
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                     : "r"(addr)
-                     : "memory");
-    } else {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-              "=r"(r[6]), "=r"(r[7])
-            : "r"(addr)
-            : "memory");
-    }
+// four / eight accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_ld4(unsigned addr, unsigned *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_ld8(unsigned addr, unsigned *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(addr)
+        : "memory");
+}
+// the TC_RC accumulator columns of one level (rows j = 0 .. RB-1, then for
+// the LoG the second-difference rows)
+__device__ __forceinline__ void tc_ld_rows(unsigned addr, unsigned (&r)[TC_RC]) {
+#pragma unroll
+    for (int c = 0; c + 8 <= TC_RC; c += 8) tc_ld8(addr + (unsigned)c, r + c);
+    if constexpr (TC_RC % 8 == 4) tc_ld4(addr + (unsigned)(TC_RC - 4), r + TC_RC - 4);
 }
 
 // the RB prefetched rows into window rows [prow, prow + RB)
@@ -681,30 +696,37 @@ __device__ __forceinline__ void tc_store_prefetch(const Prefetch &pf, const TcSt
 
 // the loaded registers are only read after tcgen05.wait::ld: this empty
 // statement (ordered after the wait like every volatile asm) redefines them
-__device__ __forceinline__ void tc_regs_ready(unsigned (&r)[RB]) {
+__device__ __forceinline__ void tc_regs_ready(unsigned (&r)[TC_RC]) {
 #pragma unroll
-    for (int j = 0; j < RB; j += 4)
+    for (int j = 0; j < TC_RC; j += 4)
         asm volatile("" : "+r"(r[j]), "+r"(r[j + 1]), "+r"(r[j + 2]), "+r"(r[j + 3]));
 }
 
 template <int G, int LI>
-__device__ __forceinline__ void tc_ld_levels(unsigned taddr, unsigned (*r)[RB]) {
+__device__ __forceinline__ void tc_ld_levels(unsigned taddr, unsigned (*r)[TC_RC]) {
     if constexpr (LI < kGB(G + 1) - kGB(G)) {
-        tc_ld_rows(taddr + (unsigned)(LI * RB), r[LI]);
+        tc_ld_rows(taddr + (unsigned)(LI * TC_RC), r[LI]);
         tc_ld_levels<G, LI + 1>(taddr, r);
     }
 }
 template <int G, int LI>
-__device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (*r)[RB], int c,
+__device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (*r)[TC_RC], int c,
                                              const TcStretch &ts) {
     if constexpr (LI < kGB(G + 1) - kGB(G)) {
         constexpr int L = kGB(G) + LI;
         tc_regs_ready(r[LI]);
-        const int cc = c - (RMAX - kR(L));
-        if (cc >= 0 && cc < TX2 + 2 * kR(L)) {
+        const int cc = c - (RMAX - kRH(L));
+        if (cc >= 0 && cc < TX2 + 2 * kRH(L)) {
 #pragma unroll
             for (int j = 0; j < RB; ++j)
                 s_v[j * VROW + voff(L) + cc] = fmaf(__uint_as_float(r[LI][j]), ts.a, ts.b);
+            // the LoG's g'' (*)_y I row beside it: its taps sum to zero, so
+            // the stretch offset drops out
+            if constexpr (LOG) {
+#pragma unroll
+                for (int j = 0; j < RB; ++j)
+                    s_v[j * VROW + voff(L) + extp(L) + cc] = __uint_as_float(r[LI][RB + j]) * ts.a;
+            }
         }
         tc_st_levels<G, LI + 1>(s_v, r, c, ts);
     }
@@ -724,7 +746,7 @@ __device__ __forceinline__ void tc_read(const TcState &tc, float *s_v, const TcS
     for (int t = warp >> 2; t < TC_NMT; t += NWG) {
         const unsigned taddr =
             tc.tmem + ((unsigned)(32 * q) << 16) + (unsigned)(t * TC_NCT + tc_colg(G));
-        unsigned r[NG][RB];
+        unsigned r[NG][TC_RC];
         tc_ld_levels<G, 0>(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         tc_st_levels<G, 0>(s_v, r, 128 * t + c0, ts);

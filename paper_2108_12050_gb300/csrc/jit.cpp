@@ -247,18 +247,23 @@ int tc_window_bytes(const std::vector<int> &R, int mode, const TileConfig &c, in
     return nmt * 16 * gstr;
 }
 
-void tc_group_dims(const std::vector<int> &R, const TileConfig &c, int g, int *kgp, int *ngp) {
+// K rows and N columns of group g's MMAs: the group's largest halo (R, or
+// R + 1 for the LoG's second-difference taps) on both sides of the step's
+// rows; rows x levels, twice for the LoG (g and g'' rows), padded to 16
+void tc_group_dims(const std::vector<int> &R, int mode, const TileConfig &c, int g, int *kgp,
+                   int *ngp) {
+    const int extra = is_log(mode) ? 1 : 0;
     int rg = 0;
-    for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) rg = R[l] > rg ? R[l] : rg;
+    for (int l = c.gb[g]; l < c.gb[g + 1]; ++l) rg = R[l] + extra > rg ? R[l] + extra : rg;
     *kgp = (c.rb + 2 * rg + 15) & ~15;
-    *ngp = ((c.gb[g + 1] - c.gb[g]) * c.rb + 15) & ~15;
+    *ngp = ((c.gb[g + 1] - c.gb[g]) * c.rb * (1 + extra) + 15) & ~15;
 }
 
-int tc_b_bytes(const std::vector<int> &R, const TileConfig &c) {
+int tc_b_bytes(const std::vector<int> &R, int mode, const TileConfig &c) {
     int o = 0;
     for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
         int kgp, ngp;
-        tc_group_dims(R, c, (int)g, &kgp, &ngp);
+        tc_group_dims(R, mode, c, (int)g, &kgp, &ngp);
         o += 4 * kgp * ngp;
     }
     return o;
@@ -269,7 +274,7 @@ int tc_tmem_cols(const std::vector<int> &R, int mode, const TileConfig &c) {
     int nct = 0;
     for (size_t g = 0; g + 1 < c.gb.size(); ++g) {
         int kgp, ngp;
-        tc_group_dims(R, c, (int)g, &kgp, &ngp);
+        tc_group_dims(R, mode, c, (int)g, &kgp, &ngp);
         nct += ngp;
     }
     return ((wext + 127) / 128) * nct;
@@ -288,7 +293,7 @@ int tc_min_rows(const std::vector<int> &R, int mode, const TileConfig &c) {
 int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
     if (c.tc) {
         const int lo = tc_min_rows(R, mode, c);
-        const int fixed = smem_fixed(R, mode, c) + tc_b_bytes(R, c) + 128;
+        const int fixed = smem_fixed(R, mode, c) + tc_b_bytes(R, mode, c) + 128;
         int b = lo + 6 * c.rb;
         while (b > lo && fixed + tc_window_bytes(R, mode, c, b) > kSmemLimit) --b;
         return b;
@@ -303,7 +308,7 @@ int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
 
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
     if (c.tc)
-        return smem_fixed(R, mode, c) + tc_b_bytes(R, c) + 128 +
+        return smem_fixed(R, mode, c) + tc_b_bytes(R, mode, c) + 128 +
                tc_window_bytes(R, mode, c, brows_for(R, mode, c));
     return smem_fixed(R, mode, c) + 4 * brows_for(R, mode, c) * wextp_of(R, mode, c);
 }
@@ -312,9 +317,9 @@ namespace {
 double cost_model(const std::vector<int> &R, int mode, const TileConfig &c);
 }
 
-// the paper rule with the DoG response (the 26-neighbour rule's ring of all
+// the paper rule, DoG or LoG response (the 26-neighbour rule's ring of all
 // layers leaves too little shared memory for a useful tensor-core strip)
-bool tc_mode_ok(int mode) { return mode == 0; }
+bool tc_mode_ok(int mode) { return (mode & 3) == 0; }
 
 bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why) {
     auto no = [&](const char *m) {

@@ -235,8 +235,10 @@ def test_tensor_core_pass_is_used_where_it_applies():
                         tensor_cores=False).uses_tensor_cores
     assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
                         nms="local26").uses_tensor_cores
-    assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9,
-                        response="log").uses_tensor_cores
+    assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9,
+                    response="log").uses_tensor_cores
+    assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9, response="log",
+                        tensor_cores=False).uses_tensor_cores
 
 
 @pytest.mark.parametrize("scale,kernel", [(1, "tensor cores"), (9, "FFMA companion")])
@@ -361,7 +363,8 @@ def test_plain_path_matches_oracle():
 # -------------------------------------------------- variants (plain path)
 
 @pytest.mark.parametrize("response,boundary,nms,plain,tc", [
-    ("dog", "periodic", "paper", False, False), ("dog", "reflect", "paper", False, False)] + [
+    ("dog", "periodic", "paper", False, False), ("dog", "reflect", "paper", False, False),
+    ("log", "reflect", "paper", False, False), ("log", "periodic", "paper", False, False)] + [
     p + (True,) for p in [
     ("dog", "reflect", "paper", True), ("log", "reflect", "paper", True),
     ("dog", "periodic", "paper", True), ("log", "periodic", "paper", True),
@@ -414,15 +417,19 @@ def test_periodic_plain_commutes_with_circular_shift():
     assert not diff, diff[:10]
 
 
+@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
 @pytest.mark.parametrize("boundary,shape", [("reflect", (150, 230)), ("periodic", (70, 45))])
-def test_fused_log_stack_within_tolerance(boundary, shape):
+def test_fused_log_stack_within_tolerance(boundary, shape, tc):
     """The fused kernel's scale-normalised Laplacian (second differences
     folded into derived taps) against the oracle's 5-point stencil on its
-    FP64 levels, including an image narrower than the largest kernel."""
+    FP64 levels, including an image narrower than the largest kernel; on the
+    tensor-core kernel (g and g'' vertical rows from the MMAs) and the FFMA
+    one."""
     img = scene(71, shape[0], shape[1], "u16")
     n, tmin, tmax = 10, 1.0, 10.0
     det = detector(n=n, t_min=tmin, t_max=tmax, threshold=0.1, response="log",
-                   boundary=boundary)
+                   boundary=boundary, tensor_cores=tc)
+    assert det.uses_tensor_cores == tc
     D, _, _, _ = det.debug_stack(to_dev(img), want=("D",))
     lo, hi = oracle.stretch_bounds(img)
     t = oracle.ladder(n, tmin, tmax)
