@@ -105,12 +105,13 @@ def test_tensor_core_tile_menu(native):
             assert rb in (4, 8) and nt % 32 == 0 and nt >= 128 and rb * tx2 // 4 <= 2 * nt
         chosen = native.chosen_tile(tensor_cores=True, **kw)
         assert chosen in menu and chosen[0] == chosen[3] - 32
-    # the 26-neighbour rule takes the FFMA kernel: the flag changes nothing
-    # for it; the LoG response has tensor-core shapes of its own
+    # the LoG response has tensor-core shapes of its own; the 26-neighbour
+    # rule takes the FFMA kernel (the flag changes nothing for it)
+    assert native.tile_configs(tensor_cores=True, n=16, t_min=1, t_max=12, response=1)
     kw = dict(n=16, t_min=1, t_max=12, nms=1)
+    assert not native.tile_configs(tensor_cores=True, **kw)
     assert native.chosen_tile(tensor_cores=True, **kw) == native.chosen_tile(
         tensor_cores=False, **kw)
-    assert native.tile_configs(tensor_cores=True, n=16, t_min=1, t_max=12, response=1)
 
 
 def test_explicit_tensor_core_tile_shape(native):
