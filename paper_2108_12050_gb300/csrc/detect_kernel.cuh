@@ -644,7 +644,9 @@ __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait (at most about 0.2 s) for the MMAs of group G to complete.
+// Wait for the MMAs of group G to complete, at most 2 s of global time (as
+// the prune's settle loop; far beyond any MMA batch, and long enough that a
+// block preempted by time slicing does not give up early).
 __device__ __forceinline__ void tc_wait(const MhfdKHeader &h, const TcState &tc, int g) {
     const unsigned bar = tc.bar + 8u * g, par = (tc.ph >> g) & 1u;
     if (tc_try(bar, par)) return;
@@ -653,7 +655,7 @@ __device__ __forceinline__ void tc_wait(const MhfdKHeader &h, const TcState &tc,
 #pragma unroll 1
         for (int i = 0; i < 256; ++i)
             if (tc_try(bar, par)) return;
-        if (gtimer() - t0 > 200000000ull) break;
+        if (gtimer() - t0 > 2000000000ull) break;
     }
     if (h.flag) atomicExch(h.flag, 1);
 }
