@@ -19,7 +19,10 @@
 //      V_l = g_l (*)_y I' for every column of the group's halo'd width: each
 //      thread owns a column, forms the folded sums I'(y+k) + I'(y-k) once and
 //      feeds them to all levels of the group (taps are symmetric, §2.2), for
-//      up to four rows at a time;
+//      up to four rows at a time; or (MHFD_VTC, "tensor-core vertical pass"
+//      below) the window holds exact fp16 integers and the vertical pass is
+//      a product with banded tap matrices on the tensor cores (tcgen05),
+//      issued a step ahead and read back from tensor memory;
 //   3. a horizontal pass computes L_l = g_l (*)_x V_l for four adjacent
 //      outputs per thread from float4 shared-memory reads and forms the DoG
 //      of Eq. 2, D_{l-1} = t_{l-1} (L_l - L_{l-1}), in registers;
@@ -1439,7 +1442,10 @@ __device__ __forceinline__ void march_tc(const MhfdKHeader &h, const MhfdStretch
             tc_store_prefetch(pf, ts, sm.win, (s + 1) * RB + WIN - base);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        __syncthreads();
+        // no barrier here: the rows just stored are first read by MMAs issued
+        // after the next step's first readout barrier; the V rows, the ring
+        // and the scan buffer are each guarded by an earlier barrier (the
+        // last group's, and the next scan's)
     }
 }
 
