@@ -17,6 +17,8 @@
 // * output: kept candidates are compacted in list order (per-block counts,
 //   a one-block scan, ordered writes) straight into pinned host memory
 //   mapped into the device address space.
+#include <cstdlib>
+
 #include "internal.h"
 #include "prune_common.cuh"
 
@@ -644,6 +646,11 @@ int enqueue_prune(const MhfdCand *cand, const Counters *cnt_c, long long cap, in
     const int grid = sms * (per_sm < 4 ? per_sm : 4);
     long long max_sweeps = 1ll << 24;
     unsigned long long max_ns = 2000000000ull;  // 2 s of device time
+    // MHFD_PRUNE_MAX_SWEEPS: a smaller bound on the settle loop, for tests of
+    // the timeout report (0 gives up before the first sweep)
+    if (const char *e = std::getenv("MHFD_PRUNE_MAX_SWEEPS")) {
+        if (*e) max_sweeps = std::atoll(e) < 0 ? 0 : std::atoll(e);
+    }
     ConflictTable ctv = ct;
     void *args[] = {(void *)&cand, (void *)&cnt, (void *)&cs, (void *)&ncx, (void *)&ncy,
                     (void *)&pb->cell_start, (void *)&pb->cell_items, (void *)&ctv, (void *)&W,

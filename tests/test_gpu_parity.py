@@ -326,6 +326,25 @@ def test_async_host_entry_point_on_several_streams():
 
 # -------------------------------------------------------------------- prune
 
+def test_settle_wait_limit_reports_timeout_and_detector_recovers(monkeypatch):
+    """The prune's settle loop is bounded; when the bound runs out (here set
+    to zero sweeps, so it gives up before the first) the detection reports
+    MHFD_ERR_TIMEOUT, and the next detection on the same detector, with the
+    default bound, gives the usual result (the context stays usable)."""
+    import paper_2108_12050_gb300 as mhfd
+    a, _ = synth.pair512_u8(seed=2, H=200, W=200)
+    det = detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1, overlap=0.5)
+    want = det(to_dev(a))
+    assert want.n_candidates > 0
+    monkeypatch.setenv("MHFD_PRUNE_MAX_SWEEPS", "0")
+    with pytest.raises(mhfd.MhfdError) as e:
+        det(to_dev(a))
+    assert e.value.code == -5
+    monkeypatch.delenv("MHFD_PRUNE_MAX_SWEEPS")
+    again = det(to_dev(a))
+    assert again.n_blobs == want.n_blobs and np.array_equal(again.blobs, want.blobs)
+
+
 @pytest.mark.parametrize("seed,n,cluster,overlap", [(0, 3000, 0.0, 0.5), (1, 4000, 0.9, 0.5),
                                                     (2, 2500, 0.95, 0.1), (3, 1, 0.0, 0.5),
                                                     (4, 5000, 0.8, 0.0)])
