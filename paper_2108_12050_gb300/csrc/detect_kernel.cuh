@@ -421,9 +421,11 @@ __device__ __forceinline__ void shift_window(float *s_in, int from, int n) {
 // (tcgen05.mma, kind::f16, f32 accumulators in tensor memory) for the next
 // step of a group as soon as this step's results of the group have been
 // read out, so they run under the horizontal passes; the block reads each
-// group's accumulators back with tcgen05.ld (lane = column), applies the
-// stretch affine (acc / TC_S) inv + (c0 - lo) inv + off and writes the V rows
-// the horizontal pass reads.  All waits are bounded: a wait that gives up
+// group's accumulators back with tcgen05.ld (lane = column) and writes them
+// unscaled as the V rows the horizontal pass reads: the stretch affine
+// (acc / TC_S) inv + (c0 - lo) inv + off is a scale, applied to the response,
+// plus an offset that the DoG difference and the zero-sum second-difference
+// taps remove.  All waits are bounded: a wait that gives up
 // sets h.flag and the block carries on (the results are then reported as
 // unreliable by the host).
 
@@ -462,7 +464,7 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
 // stretch of one image for the tensor-core pass
 struct TcStretch {
     int lo, hi, c0;
-    float a, b;  // V = a * acc + b
+    float a;  // stretched units per unit of the MMA sums
 };
 __device__ __forceinline__ TcStretch tc_stretch(const MhfdStretch &st) {
     TcStretch t;
@@ -470,7 +472,6 @@ __device__ __forceinline__ TcStretch tc_stretch(const MhfdStretch &st) {
     t.hi = st.hi_i;
     t.c0 = (st.lo_i + st.hi_i) >> 1;
     t.a = st.inv * (1.0f / TC_S);
-    t.b = fmaf((float)(t.c0 - st.lo_i), st.inv, st.off);
     return t;
 }
 // uint8, or uint16 whose stretch range keeps |x| <= 2048
@@ -722,15 +723,15 @@ __device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (
         tc_regs_ready(r[LI]);
         const int cc = c - (RMAX - kRH(L));
         if (cc >= 0 && cc < TX2 + 2 * kRH(L)) {
+            // the raw MMA sums (the horizontal pass applies the scale)
 #pragma unroll
             for (int j = 0; j < RB; ++j)
-                s_v[j * VROW + voff(L) + cc] = fmaf(__uint_as_float(r[LI][j]), ts.a, ts.b);
-            // the LoG's g'' (*)_y I row beside it: its taps sum to zero, so
-            // the stretch offset drops out
+                s_v[j * VROW + voff(L) + cc] = __uint_as_float(r[LI][j]);
+            // the LoG's g'' (*)_y I row beside it
             if constexpr (LOG) {
 #pragma unroll
                 for (int j = 0; j < RB; ++j)
-                    s_v[j * VROW + voff(L) + extp(L) + cc] = __uint_as_float(r[LI][RB + j]) * ts.a;
+                    s_v[j * VROW + voff(L) + extp(L) + cc] = __uint_as_float(r[LI][RB + j]);
             }
         }
         tc_st_levels<G, LI + 1>(s_v, r, c, ts);
@@ -905,10 +906,13 @@ struct HCtx {
 
 // The horizontal pass of level L for this item's four outputs, then its
 // response: the DoG of Eq. 2 with the previous level (kept in st.lp), or the
-// scale-normalised Laplacian of the level itself.
+// scale-normalised Laplacian of the level itself.  `vs` scales the V rows to
+// stretched units (1 for the FFMA kernel; the tensor-core kernel keeps the
+// raw MMA sums, whose offset drops out of the DoG and the LoG because the
+// taps sum to 1 and the second-difference taps to 0).
 template <int L>
 __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, const HCtx &cx,
-                                       HState &st, float *s_ring) {
+                                       HState &st, float *s_ring, float vs) {
     constexpr int R = kR(L);
     float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if constexpr (LOG) {
@@ -941,10 +945,11 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
     } else {
         constexpr int I = LOG ? L : (L > 0 ? L - 1 : 0);  // response layer
         constexpr float ts = kTsc(I);                    // t_I, or t_I^2 for the LoG
+        const float tsv = ts * vs;
         float d[4];
         if constexpr (LOG) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) d[u] = ts * a[u];
+            for (int u = 0; u < 4; ++u) d[u] = tsv * a[u];
             if (L == 0) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -956,7 +961,7 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
         } else {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                d[u] = ts * (a[u] - st.lp[u]);
+                d[u] = tsv * (a[u] - st.lp[u]);
                 st.lp[u] = a[u];
             }
         }
@@ -999,15 +1004,16 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
 template <int L, int LE>
 struct HLevels {
     static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *vrow,
-                                               const HCtx &cx, HState &st, float *s_ring) {
-        hlevel<L>(h, vrow, cx, st, s_ring);
-        HLevels<L + 1, LE>::run(h, vrow, cx, st, s_ring);
+                                               const HCtx &cx, HState &st, float *s_ring,
+                                               float vs) {
+        hlevel<L>(h, vrow, cx, st, s_ring, vs);
+        HLevels<L + 1, LE>::run(h, vrow, cx, st, s_ring, vs);
     }
 };
 template <int LE>
 struct HLevels<LE, LE> {
     static __device__ __forceinline__ void run(const MhfdKHeader &, const float *, const HCtx &,
-                                               HState &, float *) {}
+                                               HState &, float *, float) {}
 };
 
 // Chunk geometry: chunk row r is image row yb + r; rows 1..Y are output
@@ -1040,14 +1046,14 @@ __device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, const March &m, i
 template <int G>
 __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, const float *s_v,
                                       float *s_ring, unsigned char *s_arg, HState (&hs)[HI],
-                                      int s) {
+                                      int s, float vs = 1.0f) {
 #pragma unroll
     for (int it = 0; it < HI; ++it) {
         const int item = threadIdx.x < NTW ? threadIdx.x + it * NTW : HITEMS;
         if (item < HITEMS) {
             const HCtx cx = make_ctx(h, m, item, s);
             const float *vrow = s_v + (cx.r - s * RB) * VROW;
-            HLevels<kGB(G), kGB(G + 1)>::run(h, vrow, cx, hs[it], s_ring);
+            HLevels<kGB(G), kGB(G + 1)>::run(h, vrow, cx, hs[it], s_ring, vs);
             if (G == NGROUPS - 1 && MODE == 0) {
                 const float ninf = -__int_as_float(0x7f800000);
                 float4 o;
@@ -1357,7 +1363,7 @@ struct GroupsTC {
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             if (tc.issuer && s + 1 < nsteps) tc_issue<G>(tc, (s + 1) * RB - base);
-            hpass<G>(h, m, sm.v, sm.ring, sm.arg, hs, s);
+            hpass<G>(h, m, sm.v, sm.ring, sm.arg, hs, s, ts.a);
             __syncthreads();
             GroupsTC<G + 1>::run(h, m, tc, ts, sm, hs, s, nsteps, base);
         }
