@@ -70,6 +70,10 @@ constexpr bool STORE = (MHFD_STORE) != 0;
 #define MHFD_VTC 0
 #endif
 constexpr bool TC = (MHFD_VTC) != 0;
+// horizontal pass on packed two-lane FMAs: measured faster for the
+// tensor-core LoG kernel (2.79 -> 2.61 ms on a 4096^2 tile), slower for the
+// DoG kernels (1.00 -> 1.16 ms tensor-core, 1.51 -> 1.60 ms FFMA)
+constexpr bool HPACK = TC && LOG;
 
 // Kernel radius R_l of Gaussian level l and the level groups [GB(g), GB(g+1)).
 MK_HD constexpr int kR(int l) {
@@ -894,6 +898,57 @@ struct HQuads<R, TO, -1, OFF, T2> {
     static __device__ __forceinline__ void run(const float4 *, float (&)[4]) {}
 };
 
+// The same sums with packed two-lane FMAs (sm_100 and later): outputs
+// (0, 1) and (2, 3) of the item form two lane pairs, and the window values
+// M, M + 1 feed both lanes of a pair with one tap, |M - R - OFF| for the
+// first and |M - 2 - R - OFF| for the second.  Pairs at even M are halves of
+// the loaded float4s; pairs at odd M straddle them.
+template <int R, int TO, int M, int OFF, bool T2>
+__device__ __forceinline__ void hpk(float2 v, float2 (&a)[2]) {
+    constexpr int k0 = M - R - OFF, k1 = M - 2 - R - OFF;
+    constexpr int a0 = k0 < 0 ? -k0 : k0, a1 = k1 < 0 ? -k1 : k1;
+    if constexpr (a0 <= R) {
+        constexpr float t = T2 ? kTap2(TO + a0) : kTap(TO + a0);
+        a[0] = __ffma2_rn(make_float2(t, t), v, a[0]);
+    }
+    if constexpr (a1 <= R) {
+        constexpr float t = T2 ? kTap2(TO + a1) : kTap(TO + a1);
+        a[1] = __ffma2_rn(make_float2(t, t), v, a[1]);
+    }
+}
+
+template <int R, int TO, int NQ, int OFF, bool T2, int I>
+struct HQuadsP {
+    static __device__ __forceinline__ void run(const float4 *w, float2 (&a)[2], float prevw) {
+        const float4 v = w[I];
+        if constexpr (I > 0) hpk<R, TO, 4 * I - 1, OFF, T2>(make_float2(prevw, v.x), a);
+        hpk<R, TO, 4 * I, OFF, T2>(make_float2(v.x, v.y), a);
+        hpk<R, TO, 4 * I + 1, OFF, T2>(make_float2(v.y, v.z), a);
+        hpk<R, TO, 4 * I + 2, OFF, T2>(make_float2(v.z, v.w), a);
+        HQuadsP<R, TO, NQ, OFF, T2, I + 1>::run(w, a, v.w);
+    }
+};
+template <int R, int TO, int NQ, int OFF, bool T2>
+struct HQuadsP<R, TO, NQ, OFF, T2, NQ> {
+    // the pair at 4 NQ - 1 would need the next float4: it feeds no output
+    static_assert(4 * NQ - 1 > 2 * R + 2 + OFF, "window of the packed horizontal pass");
+    static __device__ __forceinline__ void run(const float4 *, float2 (&)[2], float) {}
+};
+
+template <int R, int TO, int NQ, int OFF, bool T2>
+__device__ __forceinline__ void hquads(const float4 *w, float (&a)[4]) {
+    if constexpr (HPACK) {
+        float2 p[2] = {make_float2(a[0], a[1]), make_float2(a[2], a[3])};
+        HQuadsP<R, TO, NQ, OFF, T2, 0>::run(w, p, 0.0f);
+        a[0] = p[0].x;
+        a[1] = p[0].y;
+        a[2] = p[1].x;
+        a[3] = p[1].y;
+    } else {
+        HQuads<R, TO, NQ - 1, OFF, T2>::run(w, a);
+    }
+}
+
 struct HCtx {
     int r;        // tile row of this item
     int q;        // float4 chunk (outputs 4q .. 4q+3)
@@ -921,13 +976,13 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
         // with radius R + 1
         constexpr int NQA = (2 * R + 4) / 4 + 1;
         constexpr int NQB = (2 * (R + 1) + 3) / 4 + 1;
-        HQuads<R, tapoff(L), NQA - 1, 1, false>::run(
+        hquads<R, tapoff(L), NQA, 1, false>(
             reinterpret_cast<const float4 *>(vrow + voff(L) + extp(L)) + cx.q, a);
-        HQuads<R + 1, tapoff2(L), NQB - 1, 0, true>::run(
+        hquads<R + 1, tapoff2(L), NQB, 0, true>(
             reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q, a);
     } else {
         constexpr int NQ = (2 * R + 3) / 4 + 1;
-        HQuads<R, tapoff(L), NQ - 1, 0, false>::run(
+        hquads<R, tapoff(L), NQ, 0, false>(
             reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q, a);
     }
     if (MODE == 3) {
