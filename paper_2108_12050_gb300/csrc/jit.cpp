@@ -95,7 +95,12 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_BOUNDARY " << lk.boundary << "\n"
       << "#define MHFD_RESPONSE " << lk.response << "\n"
       << "#define MHFD_TAPS2 " << (lk.response ? join_f(lk.taps2) : std::string("0.0f")) << "\n";
-    return o.str() + kTypesSrc + kKernelSrc;
+    // the kernel's own shared-memory layout must be the one the host sized
+    // and chose the tile by: a compile error otherwise
+    const std::string check = "\nstatic_assert(mk::SMEM_BYTES == " +
+                              std::to_string(smem_estimate(R, smode, c)) +
+                              ", \"kernel shared-memory layout differs from the host estimate\");\n";
+    return o.str() + kTypesSrc + kKernelSrc + check;
 }
 
 const char *kOpts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};

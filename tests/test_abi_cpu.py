@@ -171,3 +171,41 @@ def test_tuned_shapes_are_valid_for_their_ladders(native):
         for best in ent.values():
             shape = tuple(best["shape"])
             assert native.chosen_tile(tile_shape=shape, **kw) == shape
+
+
+def test_kernel_layout_matches_host_shared_memory_estimate(native, tmp_path, monkeypatch):
+    """The host sizes and chooses a tile by its shared-memory estimate; every
+    generated kernel source asserts at compile time that its own layout
+    (input window, V rows, ring, tap matrices, control block) takes exactly
+    that many bytes.  Compiling (NVRTC, no GPU) a spread of variants and
+    menu shapes therefore checks the two layouts against each other."""
+    monkeypatch.setenv("MHFD_JIT_CACHE", str(tmp_path))
+    small = dict(n=4, t_min=1.0, t_max=4.0)
+    cases = [
+        (dict(tensor_cores=True, **small), 0),                     # paper rule, tensor cores
+        (dict(tensor_cores=True, response="log", **small), 0),     # LoG on tensor cores
+        (dict(tensor_cores=False, nms="local26", **small), 0),     # 26-neighbour rule
+        (dict(tensor_cores=False, boundary="periodic", **small), 1),  # stack-storing variant
+        (dict(tensor_cores=False, **small), 2),                    # soft-score forward
+        (dict(tensor_cores=False, **small), 3),                    # level blur of the adjoint
+    ]
+    # first and last shapes of the tensor-core menu of the n = 16 ladder
+    full = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=True)
+    menu = native.tile_configs(**full)
+    for shape in (menu[0], menu[-1]):
+        cases.append((dict(tile_shape=shape, **full), 0))
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=min(len(cases), os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        rcs = list(ex.map(_precompile_case, cases))
+    assert rcs == [0] * len(cases), list(zip(cases, rcs))
+
+
+def _precompile_case(case):
+    kw, store = case
+    from paper_2108_12050_gb300 import _native
+    try:
+        return _native.precompile(store=store, **kw)
+    except _native.MhfdError as e:
+        return str(e)
