@@ -56,6 +56,25 @@ def footprint(shape, dtype) -> int:
     return H * W * (np.dtype(dtype).itemsize + _SCRATCH_BYTES_PER_PX)
 
 
+def plan_admission(free, need, resident, used, budget, fixed=_FIXED_BYTES):
+    """Admission step for the request at the head of the queue.
+
+    `free` lists the free slots, `need[k]` the bytes slot k would have to
+    grow by to serve the request, `resident[k]` its resident bytes, `used`
+    the bytes charged over all slots.  Returns ("admit", k) for the free slot
+    needing the least growth that keeps `used` within `budget` (ties: the
+    first in `free`); else ("reset", j) for the free slot with the most
+    scratch grown beyond `fixed` (giving it back may make room); else
+    ("wait", None) until a running detection completes."""
+    for k in sorted(free, key=lambda k: need[k]):
+        if used + need[k] <= budget:
+            return "admit", k
+    grown = [j for j in free if resident[j] > fixed]
+    if grown:
+        return "reset", max(grown, key=lambda j: resident[j])
+    return "wait", None
+
+
 class Server:
     """Slots x streams detection service with HBM-budget admission."""
 
@@ -157,18 +176,15 @@ class Server:
                 while self.queue:
                     req = self.queue[0]
                     free = [k for k, s in enumerate(self.slots) if s["req"] is None]
-                    # prefer a slot whose resident state already fits the tile
-                    free.sort(key=lambda k: self._need(self.slots[k], req))
-                    k = next((k for k in free
-                              if self.used + self._need(self.slots[k], req) <= self.budget),
-                             None)
-                    if k is None:
-                        # free slots hold scratch grown for earlier, larger
-                        # tiles: release the biggest and retry
-                        grown = [j for j in free if self.slots[j]["resident"] > _FIXED_BYTES]
-                        if not grown:
-                            break
-                        self._reset(max(grown, key=lambda j: self.slots[j]["resident"]))
+                    # prefer a slot whose resident state already fits the
+                    # tile; else release the biggest grown scratch and retry
+                    act, k = plan_admission(
+                        free, {j: self._need(self.slots[j], req) for j in free},
+                        {j: self.slots[j]["resident"] for j in free}, self.used, self.budget)
+                    if act == "wait":
+                        break
+                    if act == "reset":
+                        self._reset(k)
                         continue
                     self.queue.popleft()
                     self._admit(k, req)
