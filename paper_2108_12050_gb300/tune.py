@@ -64,10 +64,11 @@ def _rmax(n, t_min, t_max, truncate=4.0):
 
 
 def candidates(n, t_min, t_max, nms, limit=None, min_width=0, response="dog"):
-    """Balanced shapes of the built-in menu: every horizontal item has a
-    thread and the vertical pass keeps most threads busy."""
+    """Balanced shapes of the FFMA kernel's built-in menu: every horizontal
+    item has a thread and the vertical pass keeps most threads busy."""
     from . import _native
-    menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms, response=response)
+    menu = _native.tile_configs(n=n, t_min=t_min, t_max=t_max, nms=nms, response=response,
+                                tensor_cores=False)
     rmax = _rmax(n, t_min, t_max) + (0 if response in ("dog", 0) else 1)
     seen, out = set(), []
     for (tx2, ty2, rb, nt, ng) in menu:
@@ -90,8 +91,8 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0, response="dog"):
 
 def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), groups=(2, 3, 4, 5),
                      response="dog"):
-    """Shapes off the menu's width grid (strip widths fitted to an image
-    width).  Thread counts: at least one per horizontal item and one per
+    """FFMA-kernel shapes off the menu's width grid (strip widths fitted to
+    an image width).  Thread counts: at least one per horizontal item and one per
     halo'd column of the vertical pass (a single round), that count plus one
     warp, and rounded up to whole groups of four warps (the four schedulers
     of an SM); keeps those that fit in shared memory."""
@@ -110,7 +111,8 @@ def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), group
                     shape = (tx2, 18, rb, nt, ng)
                     try:
                         _native.chosen_tile(n=n, t_min=t_min, t_max=t_max, nms=nms,
-                                            tile_shape=shape, response=response)
+                                            tile_shape=shape, response=response,
+                                            tensor_cores=False)
                     except Exception:
                         continue
                     out.append(shape)
@@ -182,7 +184,8 @@ def main():
     if args.tensor_cores:
         from . import _native
         cands = [c for c in _native.tile_configs(n=args.n, t_min=args.tmin, t_max=args.tmax,
-                                                 nms=nms, tensor_cores=True)
+                                                 nms=nms, response=args.response,
+                                                 tensor_cores=True)
                  if c[0] >= args.min_width]
         if args.limit:
             cands = cands[:args.limit]
