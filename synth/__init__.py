@@ -207,7 +207,10 @@ def scene12bit_spec(sigma_d=0.0, H=4096, W=4096, dtype="u16"):
 
 
 def _cache_path(tag):
-    root = os.environ.get("MHFD_SYNTH_CACHE", "/tmp/mhfd_synth_cache")
+    """Rendered large tiles are kept (MHFD_SYNTH_CACHE, else `.synth_cache`
+    at the repository root, which version control and copies skip)."""
+    root = os.environ.get("MHFD_SYNTH_CACHE") or os.path.join(
+        os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".synth_cache")
     return os.path.join(root, tag + ".npy")
 
 
