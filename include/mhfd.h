@@ -185,7 +185,8 @@ int mhfd_detect_batch(mhfd_detector *det, int32_t n, const void *const *d_imgs,
 int mhfd_result_wait_batch(mhfd_detector *det, mhfd_result *outs, int32_t n);
 
 /* 1 if the detector runs the tensor-core vertical pass (params.tensor_cores
- * and a DoG detection mode), 0 if not, negative on error.  Host only. */
+ * and the paper rule, DoG or LoG response), 0 if not, negative on error.
+ * Host only. */
 int mhfd_uses_tensor_cores(mhfd_detector *det);
 
 /* 1 if the last batch ran from a captured CUDA graph, 0 if its kernels were
