@@ -183,6 +183,36 @@ def test_reflect_blur_equals_2d_direct_sum(shape):
     np.testing.assert_allclose(oracle.blur(I, g), ref, rtol=0, atol=1e-14)
 
 
+@pytest.mark.parametrize("boundary,pad", [(oracle.REFLECT, "symmetric"),
+                                          (oracle.PERIODIC, "wrap")])
+def test_log_stencil_equals_separable_second_difference_taps(boundary, pad):
+    # the 5-point Laplacian of L = g (*)_x g (*)_y I, with L extended through
+    # the blur's boundary, equals the sum of the two separable blurs with one
+    # factor replaced by its second difference g''[k] = g[k-1] - 2 g[k] + g[k+1]
+    # (radius R + 1): the formulation the fused LoG kernel computes.  Numpy
+    # padding and explicit window sums, independent of the oracle's loops.
+    rng = np.random.default_rng(21)
+    I = rng.uniform(-0.5, 0.5, (23, 17))
+    t = oracle.ladder(3, 1.0, 2.5)
+    D = oracle.log_stack(I, t, boundary=boundary)
+
+    def conv(img, taps, axis):
+        K = (taps.size - 1) // 2
+        widths = [(K, K) if a == axis else (0, 0) for a in range(2)]
+        P = np.pad(img, widths, mode=pad)
+        n = img.shape[axis]
+        return sum(taps[j] * np.take(P, np.arange(j, j + n), axis=axis)
+                   for j in range(taps.size))
+
+    for i, ti in enumerate(t[:3]):
+        g = oracle.kernel(float(ti))
+        ge = np.concatenate(([0.0, 0.0], g, [0.0, 0.0]))
+        d2 = ge[:-2] - 2 * ge[1:-1] + ge[2:]             # g''[-R-1..R+1]
+        g1 = np.concatenate(([0.0], g, [0.0]))           # g on the same support
+        ref = ti * ti * (conv(conv(I, g1, 0), d2, 1) + conv(conv(I, d2, 0), g1, 1))
+        np.testing.assert_allclose(D[i], ref, rtol=0, atol=1e-13)
+
+
 def test_dog_at_matches_separable_stack():
     img = synth.pair512_u8(seed=3, H=64, W=72)[0]
     lo, hi = oracle.stretch_bounds(img)
