@@ -68,3 +68,24 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = argparse.Namespace(steps=1, warmup=3)
     bench.run_reference(args, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(capsys, monkeypatch):
+    """Rank 0 prints one JSON line with the base contract's keys, the oracle
+    as the reference implementation, and zero host-device bytes."""
+    import argparse
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("MHFD_REF_SIDE", "128")
+    bench.run_reference(argparse.Namespace(steps=2, warmup=1), rank=0, world=1)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == d["unit"] == bench.METRIC
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2
+    assert d["n_gpus"] == 1 and d["config"]["workload"] == bench.WORKLOAD
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": bench.METRIC, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
