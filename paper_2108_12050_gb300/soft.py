@@ -81,33 +81,44 @@ def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0, tim
     (mean sigmoids), so the optimiser works on standardised features:
     w = v / s and b = c - (m / s) . v with m, s the per-layer mean and spread
     over the calibration images, which leaves S(I, w) + b = sum_i v_i
-    (f_i - m_i) / s_i + c.  Returns (w, b, losses); `timings`, if a dict,
-    receives the seconds spent on the features and on the optimiser."""
+    (f_i - m_i) / s_i + c.  The 17-parameter least-squares loss and its
+    gradient are written out and Adam (default moments 0.9 / 0.999, eps 1e-8,
+    bias-corrected) runs on the host in float64.  Returns (w, b, losses);
+    `timings`, if a dict, receives the seconds spent on the features and on
+    the optimiser."""
     import time
+    import numpy as np
     t0 = time.perf_counter()
-    f = features(det, imgs, tau, T).double()
-    torch.cuda.synchronize(f.device)
+    dev = imgs[0].device
+    f = features(det, imgs, tau, T).double().cpu().numpy()
     t1 = time.perf_counter()
+    y = np.asarray(targets, dtype=np.float64)
+    N = f.shape[0]
     m = f.mean(0)
-    sd = f.std(0) + 1e-6 if f.shape[0] > 1 else torch.ones_like(m)
+    sd = f.std(0, ddof=1) + 1e-6 if N > 1 else np.ones_like(m)
+    fz = (f - m) / sd
     g = torch.Generator(device="cpu").manual_seed(seed)
-    y = torch.as_tensor(targets, dtype=torch.float64, device=f.device)
-    v = (0.1 * torch.randn(det.n, generator=g, dtype=torch.float64)).to(f.device)
-    v.requires_grad_(True)
-    c = y.mean().reshape(1).clone().requires_grad_(True)
-    opt = torch.optim.Adam([v, c], lr=lr)
+    v = 0.1 * torch.randn(det.n, generator=g, dtype=torch.float64).numpy()
+    c = float(y.mean())
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    mv, sv = np.zeros_like(v), np.zeros_like(v)
+    mc = sc = 0.0
     losses = []
-    for _ in range(steps):
-        opt.zero_grad()
-        pred = f @ (v / sd) + (c - torch.dot(m / sd, v))
-        loss = torch.mean((pred - y) ** 2)
-        loss.backward()
-        opt.step()
-        losses.append(float(loss.detach()))
-    with torch.no_grad():
-        w = (v / sd).float()
-        b = (c - torch.dot(m / sd, v)).float()
+    for k in range(1, steps + 1):
+        r = fz @ v + c - y
+        losses.append(float(np.mean(r * r)))
+        gv = (2.0 / N) * (fz.T @ r)
+        gc = (2.0 / N) * float(r.sum())
+        mv = b1 * mv + (1 - b1) * gv
+        sv = b2 * sv + (1 - b2) * gv * gv
+        mc = b1 * mc + (1 - b1) * gc
+        sc = b2 * sc + (1 - b2) * gc * gc
+        h1, h2 = 1 - b1 ** k, 1 - b2 ** k
+        v = v - lr * (mv / h1) / (np.sqrt(sv / h2) + eps)
+        c = c - lr * (mc / h1) / (np.sqrt(sc / h2) + eps)
+    w = torch.as_tensor(v / sd, dtype=torch.float32, device=dev)
+    b = torch.tensor(c - float(np.dot(m / sd, v)), dtype=torch.float32, device=dev)
     if timings is not None:
         timings["features_s"] = t1 - t0
         timings["optimizer_s"] = time.perf_counter() - t1
-    return w.detach(), b.detach(), losses
+    return w, b, losses
