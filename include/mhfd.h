@@ -273,10 +273,17 @@ int mhfd_prune(mhfd_detector *det, const int32_t *d_x, const int32_t *d_y, const
  * outside the image or the ladder are clamped into it).  Limits: n_cand <=
  * 65536 and ceil(W/c)*ceil(H/c) <= 65536 with c = ceil(2 max(radius)) + 1;
  * larger calls return MHFD_ERR_INVALID_ARG and do nothing.  Asynchronous on
- * `stream`.  All calls share the one array (each clears what must start at
- * zero), so calls whose work overlaps on the GPU race: serialise them.  The
- * first call on a device looks up the array's device address with that
- * device current; make it before any stream capture. */
+ * `stream`.  d_keep receives 1 (kept), 0 (dropped) or 2 (unresolved): the
+ * settle loop's wait is bounded (2^24 sweeps or 2 s of device time; the
+ * environment variable MHFD_PRUNE_MAX_SWEEPS sets a smaller sweep bound),
+ * and when the bound runs out the candidates it has not settled get 2 - the
+ * result is then incomplete (the detector's prune reports the same event as
+ * MHFD_ERR_TIMEOUT).  All calls share the one array (each clears what must
+ * start at zero), so calls whose work overlaps on the GPU race: serialise
+ * them.  The first call on a device looks up the array's device address
+ * with that device current (and `stream` must belong to that device); make
+ * it before any stream capture.  The address is kept for the life of the
+ * process: cudaDeviceReset after the first call is not supported. */
 int mhfd_prune_noalloc(const double *radius, int32_t n_levels, float overlap, const int32_t *d_x,
                        const int32_t *d_y, const int32_t *d_i, const float *d_resp,
                        int64_t n_cand, int32_t H, int32_t W, uint8_t *d_keep, void *stream);

@@ -15,7 +15,10 @@ Every function cites the passage of the paper it follows:
 * ``nms_paper``: Eq. 3 (argmax over scales, then 3x3 max-pool comparison);
 * ``nms_local26``: 3x3x3 scale-space maxima;
 * ``lens_overlap`` / ``prune``: greedy overlap pruning (not in the paper);
-* ``detect``: Algorithm 1 end to end plus threshold and prune.
+* ``detect``: Algorithm 1 end to end plus threshold and prune, with the
+  per-image statistics: the count |C| (the DOF of Algorithm 1), the count
+  per scale and the mean response of the kept features;
+* ``detect_from_stack``: the same steps after the stack, on a given stack.
 """
 from __future__ import annotations
 
@@ -77,6 +80,7 @@ def _load():
         lib.oracle_nms_local26.restype = i64
         lib.oracle_lens_overlap.argtypes = [dbl, dbl, dbl]
         lib.oracle_lens_overlap.restype = dbl
+        lib.oracle_lens_overlap_many.argtypes = [P, P, P, i64, P]
         lib.oracle_prune.argtypes = [P, P, P, P, i64, P, i32, dbl, i64, P]
         lib.oracle_prune.restype = i64
         lib.oracle_dog_at.argtypes = [P, i32, i64, i64, i64, dbl, dbl, P, i32, dbl, i64, i64, P]
@@ -217,6 +221,16 @@ def lens_overlap(r1, r2, d):
     return float(_load().oracle_lens_overlap(float(r1), float(r2), float(d)))
 
 
+def lens_overlap_many(r1, r2, d):
+    """``lens_overlap`` elementwise over equal-length arrays."""
+    r1 = np.ascontiguousarray(r1, np.float64); r2 = np.ascontiguousarray(r2, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    out = np.empty(d.size, np.float64)
+    if d.size:
+        _load().oracle_lens_overlap_many(_ptr(r1), _ptr(r2), _ptr(d), d.size, _ptr(out))
+    return out
+
+
 def prune(x, y, i, resp, radius, overlap, W):
     """Greedy overlap prune; returns a uint8 keep mask."""
     x = np.ascontiguousarray(x, np.int32); y = np.ascontiguousarray(y, np.int32)
@@ -297,7 +311,29 @@ def detect(img, n, tmin, tmax, *, threshold, overlap=0.5, mode=MODE_PAPER, trunc
     m = min(cnt, cap)
     keep = keep[:m].astype(bool)
     t = ladder(n, tmin, tmax)
-    per_scale = np.bincount(i[:m][keep], minlength=n)
-    return OracleResult(x=x[:m].copy(), y=y[:m].copy(), i=i[:m].copy(), resp=r[:m].copy(),
-                        keep=keep, n_candidates=int(cnt), score=int(nk.value),
-                        per_scale=per_scale, lo=lo.value, hi=hi.value, t=t)
+    return _result(x[:m].copy(), y[:m].copy(), i[:m].copy(), r[:m].copy(), keep, int(cnt),
+                   int(nk.value), n, t, lo=lo.value, hi=hi.value)
+
+
+def _result(x, y, i, resp, keep, n_candidates, score, n, t, **extra):
+    """Per-image statistics of a detection: the kept count |C|, the count per
+    scale and the mean response of the kept features (0 when none is kept)."""
+    per_scale = np.bincount(i[keep], minlength=n)[:n]
+    mean_response = float(resp[keep].mean()) if keep.any() else 0.0
+    return OracleResult(x=x, y=y, i=i, resp=resp, keep=keep, n_candidates=n_candidates,
+                        score=score, per_scale=per_scale, mean_response=mean_response, t=t,
+                        **extra)
+
+
+def detect_from_stack(D, t, threshold, overlap=0.5, mode=MODE_PAPER):
+    """The steps of ``detect`` after the response stack (Eq. 3 maxima above the
+    threshold, then the greedy prune over radii sqrt(2) t_i) on a given stack
+    ``D`` of shape (n, H, W) over the ladder ``t``."""
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    n, H, W = D.shape
+    t = np.asarray(t, np.float64)
+    f = nms_paper if mode == MODE_PAPER else nms_local26
+    x, y, i, r, cnt = f(D, threshold)
+    radius = np.sqrt(2.0) * t[:n]
+    keep = prune(x, y, i, r, radius, overlap, W).astype(bool)
+    return _result(x, y, i, r, keep, cnt, int(keep.sum()), n, t)

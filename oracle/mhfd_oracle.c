@@ -299,6 +299,12 @@ double oracle_lens_overlap(double r1, double r2, double d) {
     return area / (M_PI * rmin * rmin);
 }
 
+/* oracle_lens_overlap over m (r1, r2, d) triples (for checks over many pairs). */
+void oracle_lens_overlap_many(const double *r1, const double *r2, const double *d, int64_t m,
+                              double *out) {
+    for (int64_t j = 0; j < m; ++j) out[j] = oracle_lens_overlap(r1[j], r2[j], d[j]);
+}
+
 /* priority order of the greedy prune */
 typedef struct {
     int32_t x, y, i;

@@ -18,8 +18,14 @@
 // example on two streams) race on the array and must be serialised by the
 // caller.  The first call on a device looks up the array's device address
 // (cudaGetSymbolAddress) with that device current; make that first call
-// before any stream capture.
+// before any stream capture.  The address is kept for the process's life, so
+// cudaDeviceReset after the first call is not supported.
+//
+// The settle loop's wait is bounded (2^24 sweeps or 2 s of device time, or
+// MHFD_PRUNE_MAX_SWEEPS sweeps); candidates it leaves unresolved when the
+// bound runs out get keep = 2, so the caller sees an incomplete result.
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -216,9 +222,13 @@ __global__ void __launch_bounds__(256)
     if (pending) atomicExch(&s.flags[0], 1);
 }
 
+// keep: 1 kept, 0 dropped, 2 left unresolved by a settle loop that gave up
+// (state 0 survives the loop only when its bound ran out)
 __global__ void na_keep(int n, Scratch s, uint8_t *keep) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        keep[j] = s.state[j] == 1 ? 1 : 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int st = s.state[j];
+        keep[j] = st == 1 ? 1 : (st == 0 ? 2 : 0);
+    }
 }
 
 std::mutex g_na_mu;
@@ -301,6 +311,11 @@ extern "C" int mhfd_prune_noalloc(const double *radius, int32_t n_levels, float 
     const int cgrid = sms * (per_sm < 4 ? per_sm : 4);
     long long max_sweeps = 1ll << 24;
     unsigned long long max_ns = 2000000000ull;
+    // MHFD_PRUNE_MAX_SWEEPS: a smaller bound on the settle loop, as for the
+    // detector's prune (0 gives up before the first sweep)
+    if (const char *e = std::getenv("MHFD_PRUNE_MAX_SWEEPS")) {
+        if (*e) max_sweeps = std::atoll(e) < 0 ? 0 : std::atoll(e);
+    }
     Scratch scv = sc;
     Radii radv = rad;
     double ovv = ov;

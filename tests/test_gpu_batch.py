@@ -1,8 +1,12 @@
-"""Batched detection (persistent launches, CUDA graph) vs single detections.
+"""Batched detection (persistent launches, CUDA graph) vs the oracle and vs
+single detections.
 
-Each image's result in a batch of uneven sizes and mixed dtypes must be
+Each image's detection alone is held to the FP64 oracle (candidates, kept
+set, counts, mean response, under the ambiguity rules of ``parity_util``),
+and its result in a batch of uneven sizes and mixed dtypes must be
 bit-identical to detecting it alone (the fused kernel is deterministic per
-tile and the per-image post-processing runs in the same order).  With the
+tile and the per-image post-processing runs in the same order), so every
+batched result is held to the oracle too.  With the
 tensor-core pass a batch runs two gated persistent launches: the
 tensor-core kernel takes the images whose stretch range it holds exactly,
 the FFMA kernel the others (float images, wide uint16 ranges) - the same
@@ -11,6 +15,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity_util import check_detection, oracle_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -21,6 +26,24 @@ def _dev(img):
     if img.dtype == np.uint16:
         return torch.from_numpy(img.view(np.int16)).cuda()
     return torch.from_numpy(img).cuda()
+
+
+def _held_to_oracle(img, res, **kw):
+    """The detection of ``img`` alone (candidates kept) against the oracle."""
+    p = dict(thr=0.05, nms="paper", response="dog", boundary="reflect")
+    p.update(kw)
+    ref, D, tol, t, _ = oracle_reference(img, 16, 1.0, 12.0, p["thr"], 0.5, p["nms"],
+                                         p["response"], p["boundary"])
+    assert (res.lo, res.hi) == (np.float32(ref.lo), np.float32(ref.hi))
+    check_detection(res, ref, D, tol, p["thr"], 0.5, p["nms"], t)
+
+
+def _same(o, s):
+    assert (o.lo, o.hi) == (s.lo, s.hi)
+    assert o.n_blobs == s.n_blobs and o.n_candidates_true == s.n_candidates_true
+    assert np.array_equal(o.blobs, s.blobs)
+    assert np.array_equal(o.per_scale, s.per_scale)
+    assert o.mean_response == s.mean_response
 
 
 def _batch_images():
@@ -42,18 +65,18 @@ def test_batch_equals_single_detections(tc):
     torch.cuda.set_device(0)
     imgs = _batch_images()
     devs = [_dev(i) for i in imgs]
-    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5, tensor_cores=tc)
+    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5, tensor_cores=tc,
+                        keep_candidates=True)
     assert det.uses_tensor_cores == tc
     singles = [det(d) for d in devs]
+    for img, s in zip(imgs, singles):
+        _held_to_oracle(img, s)
     for rep in range(3):          # capture, then replays of the graph
         det.detect_batch(devs)
         outs = det.wait_batch()
         assert len(outs) == len(imgs)
         for s, o in zip(singles, outs):
-            assert (o.lo, o.hi) == (s.lo, s.hi)
-            assert o.n_blobs == s.n_blobs and o.n_candidates_true == s.n_candidates_true
-            assert np.array_equal(o.blobs, s.blobs)
-            assert np.array_equal(o.per_scale, s.per_scale)
+            _same(o, s)
     # new image contents with the same shapes replay the graph
     devs2 = [d.flip(0).contiguous() for d in devs]
     det.detect_batch(devs2)
@@ -77,26 +100,40 @@ def test_batch_equals_single_detections_for_variants(kw):
     devs = [_dev(i) for i in imgs]
     params = dict(threshold=0.05, overlap=0.5)
     params.update(kw)
-    det = mhfd.Detector(16, 1.0, 12.0, **params)
+    det = mhfd.Detector(16, 1.0, 12.0, keep_candidates=True, **params)
     singles = [det(d) for d in devs]
+    for img, s in zip(imgs, singles):
+        _held_to_oracle(img, s, thr=params["threshold"], nms=params.get("nms", "paper"),
+                        response=params.get("response", "dog"),
+                        boundary=params.get("boundary", "reflect"))
     for rep in range(2):
         det.detect_batch(devs)
         outs = det.wait_batch()
         for s, o in zip(singles, outs):
-            assert o.n_blobs == s.n_blobs and o.n_candidates_true == s.n_candidates_true
-            assert np.array_equal(o.blobs, s.blobs)
+            _same(o, s)
     det.close()
 
 
-def test_batch_reports_graph_use():
+def test_batch_is_replayed_from_a_graph_and_matches_direct_launches():
+    """Where capture is permitted (a detector without per-kernel timing) the
+    batch is captured once and replayed as a CUDA graph; a detector with
+    timing events runs the same batch as direct launches.  Both give the
+    same bits."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     import paper_2108_12050_gb300 as mhfd
-    imgs = _batch_images()[:3]
-    det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5)
-    det.detect_batch([_dev(i) for i in imgs])
-    det.wait_batch()
-    # informative: the batch runs either from a captured graph or, where the
-    # capture is refused, from direct launches with identical results
-    assert det.batch_uses_graph() in (True, False)
-    det.close()
+    imgs = _batch_images()[:5]
+    devs = [_dev(i) for i in imgs]
+    graphed = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5)
+    direct = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5, timing=True)
+    for rep in range(2):
+        graphed.detect_batch(devs)
+        g = graphed.wait_batch()
+        assert graphed.batch_uses_graph()
+        direct.detect_batch(devs)
+        d = direct.wait_batch()
+        assert not direct.batch_uses_graph()
+        for a, b in zip(g, d):
+            _same(a, b)
+    graphed.close()
+    direct.close()

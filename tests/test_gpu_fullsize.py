@@ -1,33 +1,44 @@
-"""Full-size parity in the launch configuration the benchmark times: one
-4096x4096 uint16 tile of the sweep, n = 16 scales (t = 1..12), tau = 0.05,
-overlap 0.5, the autotuned tile shape.  The FP64 oracle cannot build the
-whole 17-level stack at this size within a test, so it is asked one pixel at
-a time (Eq. 2 straight from the raw image, `oracle.dog_at`):
+"""Full-size parity in the launch configuration the benchmark times: the
+4096x4096 uint16 tile of the defocus sweep, n = 16 scales (t = 1..12),
+tau = 0.05, overlap 0.5, the autotuned tile shape.
 
-* stretch bounds bit-exact (whole-image order statistics);
-* a sample of candidates: response within tolerance of the oracle's D at the
-  candidate's scale, that scale the first argmax, above the threshold and a
-  maximum of its 3x3 neighbourhood under the paper rule (each up to the
-  ambiguity rules);
-* a sample of other pixels: none is an unambiguous maximum by the oracle;
-* the prune of the GPU's own candidate list equals the oracle's prune of the
-  same list bit for bit, and the counts and focus score follow from it.
+The FP64 oracle builds the whole 17-level stack of the tile (about 2 GB of
+FP64, a few seconds on the host's cores with its OpenMP loops) and the
+detection from it, and every GPU path is held to it element by element:
 
-The soft focus score is checked at its full size (2048x2048 float32) too.
+* the response stack of the stack-storing variant of both fused kernels
+  (tensor-core vertical pass, FFMA) within 1e-4 ||D_ref,i||_inf per layer;
+* the whole candidate set (x, y, scale) of the fused kernels and of the
+  plain path, the kept set after the prune, the counts per scale, the focus
+  score and the mean response, up to the ambiguity rules of
+  ``parity_util`` with per-layer tolerances;
+* at sigma_d = 0 (dense maxima) and sigma_d = 4 (sparse, flat maxima), and
+  for the scale-normalised Laplacian response at sigma_d = 0.
+
+Each check prints one ``FULLSIZE {...}`` line with its counts (run with
+``-s`` to see them).  The 8192^2 uint8 tile (the largest the service
+takes) is checked on a sample of its candidates; the soft focus score at
+its full size (2048^2 float32).
 """
+import json
 import math
+import os
+import time
 
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from parity_util import (ambiguous_paper, assert_stack_close, check_detection, log_eps,
+                         oracle_reference, stack_rel_err)
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
 N, TMIN, TMAX, THR, OVERLAP = 16, 1.0, 12.0, 0.05, 0.5
+DT = (TMAX - TMIN) / N
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,114 +46,85 @@ def _cuda():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     torch.cuda.set_device(0)
+    oracle.set_threads(os.cpu_count() or 1)
 
 
-@pytest.fixture(scope="module", params=[True, False], ids=["tc", "ffma"])
-def full(request):
-    """The benchmark's tile through the tensor-core kernel (the default) and
-    through the FFMA kernel."""
+@pytest.fixture(scope="module", params=[("dog", 0.0), ("dog", 4.0), ("log", 0.0)],
+                ids=["dog-sd0", "dog-sd4", "log-sd0"])
+def reference(request):
+    """The tile and the oracle's stack and detection of it (one at a time:
+    each stack is 2.1 GB of FP64)."""
+    response, sigma_d = request.param
+    img = synth.sweep_tile_4096_u16(sigma_d)
+    # the Laplacian lacks the DoG's factor dt: threshold scaled to match
+    thr = THR / DT if response == "log" else THR
+    t0 = time.time()
+    ref, D, tol, t, Ip = oracle_reference(img, N, TMIN, TMAX, thr, OVERLAP, "paper", response)
+    secs = time.time() - t0
+    amb = ambiguous_paper(D, thr, tol)
+    yield dict(img=img, ref=ref, D=D, tol=tol, t=t, Ip=Ip, thr=thr, amb=amb,
+               response=response, sigma_d=sigma_d, oracle_s=secs)
+    del D, amb
+
+
+def _detector(response, tc, thr):
     import paper_2108_12050_gb300 as mhfd
-    img = synth.sweep_tile_4096_u16(0.0)
+    return mhfd.Detector(N, TMIN, TMAX, threshold=thr, overlap=OVERLAP, keep_candidates=True,
+                         tensor_cores=tc, response=response)
+
+
+@pytest.mark.parametrize("path", ["tc", "ffma", "plain"])
+def test_full_tile_detection_against_oracle(reference, path):
+    r = reference
+    img, ref, D_ref, t, thr = r["img"], r["ref"], r["D"], r["t"], r["thr"]
+    det = _detector(r["response"], path == "tc", thr)
+    assert det.uses_tensor_cores == (path == "tc")
     dev = torch.from_numpy(img.view(np.int16)).cuda()
-    det = mhfd.Detector(N, TMIN, TMAX, threshold=THR, overlap=OVERLAP, keep_candidates=True,
-                        tensor_cores=request.param)
-    assert det.uses_tensor_cores == request.param
-    res = det(dev)
-    yield img, res
+    if path == "plain":
+        det.detect_plain(dev)
+        res = det.wait()
+    else:
+        res = det(dev)
     det.close()
+    assert (res.lo, res.hi) == (ref.lo, ref.hi)
+    assert res.n_candidates == res.n_candidates_true > 10000
+    tol, amb = r["tol"], r["amb"]
+    if r["response"] == "log" and path == "plain":
+        # the plain path's 5-point stencil: its derived, wider tolerance
+        R = [oracle.kernel_radius(ti) for ti in t[:N]]
+        tol = log_eps(D_ref, t, R, float(np.abs(r["Ip"]).max()))
+        amb = None
+    stats = check_detection(res, ref, D_ref, tol, thr, OVERLAP, "paper", t, amb_maps=amb)
+    stats.update(path=path, response=r["response"], sigma_d=r["sigma_d"],
+                 score_gpu=res.n_blobs, score_ref=ref.score,
+                 mean_response_gpu=res.mean_response, mean_response_ref=ref.mean_response,
+                 oracle_s=round(r["oracle_s"], 1))
+    print("FULLSIZE " + json.dumps(stats))
 
 
-def _neighbourhood(xs, ys, H, W):
-    """The 3x3 windows of the given pixels clipped to the image: flat lists
-    of (x, y) and, per pixel, the slice of its window in those lists."""
-    px, py, sl = [], [], []
-    for x, y in zip(xs, ys):
-        s0 = len(px)
-        for dy in (-1, 0, 1):
-            for dx in (-1, 0, 1):
-                xx, yy = x + dx, y + dy
-                if 0 <= xx < W and 0 <= yy < H:
-                    px.append(xx)
-                    py.append(yy)
-        sl.append((s0, len(px)))
-    return np.array(px), np.array(py), sl
-
-
-def test_full_size_detection_sampled_against_oracle(full):
-    img, res = full
-    H, W = img.shape
-    lo, hi = oracle.stretch_bounds(img)
-    assert (res.lo, res.hi) == (lo, hi)
-    cands = res.candidates
-    assert res.n_candidates == res.n_candidates_true == len(cands) > 10000
-    t = oracle.ladder(N, TMIN, TMAX)
-    rng = np.random.default_rng(11)
-    pick = rng.choice(len(cands), 300, replace=False)
-    cx, cy = cands["x"][pick].astype(int), cands["y"][pick].astype(int)
-    rx = rng.integers(0, W, 300)
-    ry = rng.integers(0, H, 300)
-    px, py, sl = _neighbourhood(np.concatenate([cx, rx]), np.concatenate([cy, ry]), H, W)
-    D = oracle.dog_at(img, lo, hi, t, px, py)              # (pixels, n)
-    # per-layer tolerance 1e-4 ||D_i||: the sample holds 300 maxima and their
-    # neighbourhoods, so its per-layer maximum stands in for the image's
-    # (a smaller scale makes the checks stricter, never looser)
-    eps_i = 1e-4 * np.abs(D).max(axis=0)
-    eps = float(eps_i.max())
-    M = D.max(axis=1)
-    arg = D.argmax(axis=1)
-    cset = {(int(x), int(y)) for x, y in zip(cands["x"], cands["y"])}
-    bad = []
-    for k in range(len(pick)):
-        s0, s1 = sl[k]
-        c = np.where((px[s0:s1] == cx[k]) & (py[s0:s1] == cy[k]))[0][0] + s0
-        i = int(cands["scale_idx"][pick[k]])
-        d_ref = D[c]
-        if abs(float(cands["response"][pick[k]]) - d_ref[i]) > eps_i[i]:
-            bad.append(("response", cx[k], cy[k], i))
-        srt = np.sort(d_ref)
-        if i != arg[c] and not (srt[-1] - srt[-2] <= eps):
-            bad.append(("argmax", cx[k], cy[k], i, int(arg[c])))
-        if not M[c] > THR - eps:
-            bad.append(("threshold", cx[k], cy[k]))
-        others = [M[j] for j in range(s0, s1) if j != c]
-        if others and max(others) > M[c] + eps:
-            bad.append(("not a maximum", cx[k], cy[k]))
-    assert not bad, bad[:10]
-    # sampled pixels that are not candidates are not clear maxima
-    for k in range(len(rx)):
-        s0, s1 = sl[len(pick) + k]
-        x, y = int(rx[k]), int(ry[k])
-        if (x, y) in cset:
-            continue
-        c = np.where((px[s0:s1] == x) & (py[s0:s1] == y))[0][0] + s0
-        others = [M[j] for j in range(s0, s1) if j != c]
-        clear = M[c] > THR + eps and (not others or max(others) < M[c] - eps)
-        assert not clear, (x, y, M[c], max(others) if others else None)
-
-
-def test_full_size_prune_and_score(full):
-    img, res = full
-    H, W = img.shape
-    cands = res.candidates
-    t = oracle.ladder(N, TMIN, TMAX)
-    radius = math.sqrt(2.0) * t[:N]
-    keep = oracle.prune(cands["x"], cands["y"], cands["scale_idx"],
-                        cands["response"].astype(np.float64), radius, OVERLAP, W)
-    kept_ref = {(int(a), int(b), int(c)) for a, b, c, k in
-                zip(cands["x"], cands["y"], cands["scale_idx"], keep) if k}
-    kept_gpu = {(int(a), int(b), int(c)) for a, b, c in
-                zip(res.blobs["x"], res.blobs["y"], res.blobs["scale_idx"])}
-    assert kept_gpu == kept_ref
-    assert res.n_blobs == res.focus_score == int(keep.sum())
-    per_scale = np.bincount(res.blobs["scale_idx"], minlength=N)[:N]
-    assert np.array_equal(res.per_scale, per_scale)
+@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
+def test_full_tile_stack_within_tolerance(reference, tc):
+    r = reference
+    if r["sigma_d"] != 0.0:
+        pytest.skip("stack compared on the in-focus tile")
+    det = _detector(r["response"], tc, r["thr"])
+    dev = torch.from_numpy(r["img"].view(np.int16)).cuda()
+    D, _, _, res = det.debug_stack(dev, want=("D",))
+    det.close()
+    assert (res.lo, res.hi) == (r["ref"].lo, r["ref"].hi)
+    Dh = D.cpu().numpy()
+    del D
+    rel = stack_rel_err(Dh, r["D"])
+    print("FULLSIZE " + json.dumps({"stack": r["response"], "tc": tc,
+                                    "max_rel_err_per_layer": [float("%.3g" % v) for v in rel]}))
+    assert_stack_close(Dh, r["D"], "%s tc=%s" % (r["response"], tc))
 
 
 def test_maximum_size_8192_uint8_sampled_against_oracle():
     """The largest tiles the service takes (8192^2, uint8): stretch bounds
-    bit-exact, sampled candidates' responses and scales against the oracle,
-    counts consistent, and the prune of the GPU's list equal to the
-    oracle's."""
+    bit-exact, sampled candidates' responses and scales against the oracle
+    (Eq. 2 at single pixels), counts consistent, and the prune of the GPU's
+    list equal to the oracle's."""
     import paper_2108_12050_gb300 as mhfd
     img = synth.sweep_tile_4096_u16(0.0, seed=8192, H=8192, W=8192, dtype="u8")
     det = mhfd.Detector(N, TMIN, TMAX, threshold=THR, overlap=OVERLAP, keep_candidates=True)

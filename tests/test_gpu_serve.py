@@ -1,9 +1,12 @@
-"""Continuous-batching server: each result equals the tile detected alone,
-requests overlap on the device, and the HBM budget gates admission."""
+"""Continuous-batching server: each tile detected alone is held to the FP64
+oracle (ambiguity rules of ``parity_util``), each served result equals the
+tile detected alone bit for bit, requests overlap on the device, and the
+HBM budget gates admission."""
 import numpy as np
 import pytest
 
 import synth
+from parity_util import check_detection, oracle_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -21,13 +24,18 @@ def _tiles():
     return out
 
 
-def _alone(tiles):
+def _alone(tiles, against_oracle=False):
     import paper_2108_12050_gb300 as mhfd
-    det = mhfd.Detector(**PARAMS)
+    det = mhfd.Detector(keep_candidates=True, **PARAMS)
     res = []
     for t in tiles:
         dev = torch.from_numpy(t.view(np.int16) if t.dtype == np.uint16 else t).cuda()
-        res.append(det(dev))
+        r = det(dev)
+        if against_oracle:
+            ref, D, tol, lad, _ = oracle_reference(t, 16, 1.0, 12.0, 0.05, 0.5)
+            assert (r.lo, r.hi) == (np.float32(ref.lo), np.float32(ref.hi))
+            check_detection(r, ref, D, tol, 0.05, 0.5, "paper", lad)
+        res.append(r)
     det.close()
     return res
 
@@ -38,7 +46,7 @@ def test_results_in_the_mix_equal_results_alone():
     from paper_2108_12050_gb300 import serve
     torch.cuda.set_device(0)
     tiles = _tiles() * 3
-    ref = _alone(tiles[:8])
+    ref = _alone(tiles[:8], against_oracle=True)
     srv = serve.Server(n_slots=4, hbm_budget=8 << 30, **PARAMS)
     futs = [srv.submit(t) for t in tiles]
     got = [f.result(timeout=120) for f in futs]
@@ -47,8 +55,10 @@ def test_results_in_the_mix_equal_results_alone():
     for j, r in enumerate(got):
         want = ref[j % 8]
         assert (r.lo, r.hi) == (want.lo, want.hi)
-        assert r.n_blobs == want.n_blobs
+        assert r.n_blobs == want.n_blobs and r.n_candidates_true == want.n_candidates_true
         assert np.array_equal(r.blobs, want.blobs)
+        assert np.array_equal(r.per_scale, want.per_scale)
+        assert r.mean_response == want.mean_response
     assert stats["completed"] == len(tiles)
     assert stats["peak_in_flight"] > 1          # requests overlapped on the device
 

@@ -493,3 +493,58 @@ def test_periodic_detection_commutes_with_circular_shift():
         if inner(x, y) and inner(x0, y0):
             b.add((x, y, i))
     assert a == b and len(a) > 10
+
+
+# ------------------------------------------------- per-image statistics (a9)
+
+def test_mean_response_of_identical_blobs_is_the_closed_form_peak():
+    # Six identical noise-free dark Gaussian blobs at integer centres, far
+    # apart, on a flat float image.  With no saturation (clip 0) the stretch
+    # is affine, mapping the background to 1 and each blob's centre to 0, so
+    # every blob has amplitude -1 after stretching.  Each is kept once, at
+    # the scale maximising the closed-form DoG of its centre, and the mean
+    # response of the kept features is that peak value.
+    N, s = 360, 3.0
+    cs = [(60, 60), (180, 60), (300, 60), (60, 240), (180, 240), (300, 240)]
+    img = np.full((N, N), 180.0)
+    y, x = np.mgrid[0:N, 0:N]
+    for cx, cy in cs:
+        img += -100.0 * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * s * s))
+    r = oracle.detect(img.astype(np.float32), 10, 1.0, 10.0, threshold=0.1, overlap=0.5,
+                      clip=0.0)
+    assert r.score == len(cs)
+    t = r.t
+    want = _dog_closed_form(t, s, -1.0)
+    v = t * t * s * s / (t * t + s * s)
+    alias = 4.0 * t[:-1] * np.exp(-2 * math.pi ** 2 * np.minimum(v[:-1], v[1:]))
+    # float32 rounding of the image (relative 6e-8 of 180 over a range of 100)
+    assert abs(r.mean_response - want.max()) <= 1e-3 + alias.max() + 1e-6
+    assert set(r.i[r.keep].tolist()) == {int(np.argmax(want))}
+    assert r.per_scale.sum() == r.score
+
+
+def test_mean_response_is_zero_without_features():
+    r = oracle.detect(np.full((40, 50), 9, np.uint8), 4, 1.0, 4.0, threshold=0.1)
+    assert r.score == 0 and r.mean_response == 0.0
+
+
+def test_detect_from_stack_equals_detect():
+    a, _ = synth.pair512_u8(seed=3, H=150, W=170)
+    for mode in (oracle.MODE_PAPER, oracle.MODE_LOCAL26):
+        want = oracle.detect(a, 6, 1.0, 5.0, threshold=0.05, overlap=0.3, mode=mode)
+        lo, hi = oracle.stretch_bounds(a)
+        t = oracle.ladder(6, 1.0, 5.0)
+        D = oracle.dog_stack(oracle.stretch(a, lo, hi), t)
+        got = oracle.detect_from_stack(D, t, 0.05, 0.3, mode=mode)
+        for k in ("x", "y", "i", "resp", "keep"):
+            assert np.array_equal(got[k], want[k]), k
+        assert got.score == want.score and got.mean_response == want.mean_response
+
+
+def test_lens_overlap_many_equals_the_scalar_form():
+    rng = np.random.default_rng(9)
+    r1, r2 = rng.uniform(0.5, 5, 200), rng.uniform(0.5, 5, 200)
+    d = rng.uniform(0, 11, 200)
+    got = oracle.lens_overlap_many(r1, r2, d)
+    want = [oracle.lens_overlap(a, b, c) for a, b, c in zip(r1, r2, d)]
+    assert np.array_equal(got, np.array(want))
