@@ -36,9 +36,13 @@ N_LAYERS, T_MIN, T_MAX, THR, OVERLAP = 16, 1.0, 12.0, 0.05, 0.5
 SIGMA_D = (0.0, 1.0, 2.0, 4.0, 8.0)
 H = W = 4096
 METRIC = "Mpixel/s"
-WORKLOAD = ("4096x4096 uint16 SEM-like tiles, defocus sweep sigma_d in {0,1,2,4,8} (one "
-            "step = 5 tiles), n=16 scales t=1..12, FP32, threshold 0.05, overlap prune 0.5, "
-            "paper argmax + 3x3 max-pool rule")
+WORKLOAD = ("4096^2 u16 SEM-like tiles, sigma_d sweep {0,1,2,4,8} (5 tiles/step), n=16 "
+            "t=1..12, FP32, tau 0.05, overlap 0.5, Eq. 3 rule")
+
+
+def r4(x):
+    """x to four significant digits (keeps the result line short)."""
+    return float("%.4g" % x) if x is not None else None
 
 
 def ladder_radii():
@@ -61,6 +65,23 @@ def ffma_side_ops_per_px():
     max/argmax and the 3x3 comparison (the vertical pass runs as MMAs)."""
     _, R = ladder_radii()
     return sum(2 * r + 1 for r in R) + 2 * N_LAYERS + 8
+
+
+def variant_ops_per_px(variant):
+    """FP32 work per pixel of a detection variant, as each computes it:
+    * "dog" (both boundaries): algorithmic_ops_per_px();
+    * "log": per level t_1..t_n the derived-tap Laplacian, vertical g and
+      g'' (2R+1 and 2R+3 taps) and horizontal g'' on the first and g on the
+      second row, 8R+8, plus the response, max/argmax and 3x3 comparison;
+    * "local26": the DoG stack plus one threshold test per (pixel, layer);
+      the 26-neighbour comparisons of the few items above the threshold are
+      data-dependent and not counted."""
+    _, R = ladder_radii()
+    if variant == "log":
+        return sum(8 * r + 8 for r in R[:N_LAYERS]) + 2 * N_LAYERS + 8
+    if variant == "local26":
+        return sum(2 * (2 * r + 1) for r in R) + 2 * N_LAYERS
+    return algorithmic_ops_per_px()
 
 
 def nominal_alu_peak():
@@ -147,8 +168,7 @@ def cpu_baseline(img, side=2048, side1=1024):
     oracle.set_threads(threads)
     return {"value": crop.size / dt / 1e6, "unit": METRIC, "cores": cores,
             "kind": "oracle",
-            "sample": "%dx%d crop of the sigma_d=0 tile, full method (stretch, 17-level "
-                      "stack, DoG, NMS, prune), %.1f s" % (side, side, dt),
+            "sample": "%d^2 crop of the sd=0 tile, whole method, %.1f s" % (side, dt),
             "single_core": {"value": crop1.size / dt1 / 1e6, "unit": METRIC, "cores": 1,
                             "sample": "%dx%d crop, %.1f s" % (side1, side1, dt1)}}
 
@@ -227,7 +247,7 @@ def main():
     ap.add_argument("--batch-tiles", type=int, default=256)
     ap.add_argument("--no-soft", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--soft-tiles", type=int, default=16,
+    ap.add_argument("--soft-tiles", type=int, default=64,
                     help="2048^2 float32 tiles of the soft-score section (64 = full set)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run R detections of the sigma_d=0 tile (for ncu captures)")
@@ -426,29 +446,56 @@ def main():
 
     per_tile.sort()
     p99 = per_tile[min(len(per_tile) - 1, int(math.ceil(0.99 * len(per_tile))) - 1)]
+    # the long sections go on a detail line printed first; the headline line
+    # comes last and stays short
+    detail = {"plain": plain, "roofline": roof, "cpu_baseline": cpu, "batched": batched,
+              "sweep_batched": sweep_batched, "serving": serving, "soft": soft_sec,
+              "variants": variants, "latency_samples": len(per_tile),
+              "median_ms_paper_protocol": statistics.median(paper_ms),
+              "clocks": clk.summary()}
+    print("# detail " + json.dumps(detail), flush=True)
+    summary = {}
+    if batched:
+        summary["batch256"] = {"tiles_s": r4(batched["tiles_per_s"]),
+                               "vs_plain": r4(batched["speedup_vs_plain"])}
+    if serving:
+        summary["serve"] = {"tiles_s": [r4(v["tiles_per_s"]) for v in serving["rates"].values()],
+                            "p99_ms": [r4(v["p99_ms"]) for v in serving["rates"].values()],
+                            "plain_tiles_s": [r4(v["tiles_per_s"]) for v in
+                                              serving["sequential_plain"].values()]}
+    if soft_sec:
+        f = soft_sec["fit"]
+        summary["soft_heldout"] = {"mse": r4(f["held_out_mse"]),
+                                   "var": r4(f["held_out_target_var"]),
+                                   "spearman": r4(f["held_out_spearman"])}
+    if variants:
+        summary["variant_frac"] = {k[6:]: r4(v["roofline"]["frac"]) for k, v in variants.items()
+                                   if "roofline" in v}
     line = {
-        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": METRIC, "value": r4(value), "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r4(total_ms / args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (5 x 32 MiB tiles per step)",
-                   "tile": tile_used(mhfd),
+        "config": {"workload": WORKLOAD, "l2": "inputs > L2 (5 x 32 MiB per step)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "p50_ms_per_tile": statistics.median(per_tile), "p99_ms_per_tile": p99,
-        "latency_samples": len(per_tile),
-        "median_ms_paper_protocol": statistics.median(paper_ms),
-        "plain": plain,
-        "fused_vs_plain": (value / world / plain["value"]) if plain else None,
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "p50_ms_per_tile": r4(statistics.median(per_tile)), "p99_ms_per_tile": r4(p99),
+        "plain": {"value": r4(plain["value"]), "p50_ms_per_tile": r4(plain["p50_ms_per_tile"])}
+                 if plain else None,
+        "fused_vs_plain": r4(value / world / plain["value"]) if plain else None,
+        "roofline": {"bound": "alu", "achieved": r4(achieved), "peak": r4(peak),
+                     "unit": "Tops/s (FP32 FFMA)", "frac": r4(achieved / peak),
+                     "traffic": traffic, "kernel_ms_avg": r4(k_avg),
+                     "frac_of_probe": r4(achieved / probe),
+                     "ffma_side_frac": r4(side / peak) if tc else None},
+        "cpu_baseline": {k: r4(v) if isinstance(v, float) else v for k, v in cpu.items()
+                         if k != "single_core"} if cpu else None,
+        "e2e": {k: r4(v) if isinstance(v, float) else v
+                                     for k, v in e2e.items()},
         "gpu_launches": launches_per_tile * len(tiles) * args.steps,
-        "clocks": clk.summary(),
-        "batched": batched,
-        "sweep_batched": sweep_batched,
-        "serving": serving,
-        "soft": soft_sec,
-        "variants": variants,
-        "focus_scores": dict(zip([str(s) for s in SIGMA_D], scores)),
+        "clocks": {k: v for k, v in clk.summary().items() if k != "samples"},
+        "focus_scores": [int(x) for x in scores],
         "focus_monotone_drop": all(scores[j] > scores[j + 1] for j in range(len(scores) - 1)),
+        "summary": summary,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -463,7 +510,7 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
     `reps`."""
     dt = (T_MAX - T_MIN) / N_LAYERS
 
-    def timed(det, plain):
+    def timed(det, plain, variant="dog"):
         ms = []
         for r in range(reps + 1):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -479,8 +526,13 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
                 ms.append(e0.elapsed_time(e1))
         det.close()
         med = statistics.median(ms)
-        return {"value": tile.numel() / (med * 1e-3) / 1e6, "unit": METRIC, "ms": med,
-                "focus_score": res.focus_score}
+        out = {"value": tile.numel() / (med * 1e-3) / 1e6, "unit": METRIC, "ms": med,
+               "focus_score": res.focus_score}
+        if not plain:
+            ops = variant_ops_per_px(variant)
+            out["roofline"] = {"ops_per_px": ops,
+                               "frac": ops * tile.numel() / (med * 1e-3) / nominal_alu_peak()}
+        return out
 
     kw = dict(threshold=THR, overlap=OVERLAP, nms="paper")
     return {
@@ -490,26 +542,29 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
         "fused_periodic": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, boundary="periodic",
                                               **kw), False),
         "fused_local26": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX,
-                                             **dict(kw, nms="local26")), False),
+                                             **dict(kw, nms="local26")), False, "local26"),
         "plain_dog": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), True),
         "plain_local26": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX,
                                              **dict(kw, nms="local26")), True),
         "fused_log": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, response="log",
-                                         **dict(kw, threshold=THR / dt)), False),
+                                         **dict(kw, threshold=THR / dt)), False, "log"),
         "plain_log": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, response="log",
                                          **dict(kw, threshold=THR / dt)), True),
     }
 
 
-def bench_soft(mhfd, torch, stream, count=16):
-    """Differentiable soft focus score on 2048^2 float32 tiles of the 12-bit
-    scene (not quantised) with known sigma_d ~ U[0, 8]: forward and
+def bench_soft(mhfd, torch, stream, count=64, held_out=16):
+    """Differentiable soft focus score on `count` 2048^2 float32 tiles of the
+    12-bit scene (not quantised) with known sigma_d ~ U[0, 8]: forward and
     forward+adjoint throughput of the CUDA kernels, and the 200-step Adam
-    calibration of the 16 per-scale weights against sigma_d."""
+    calibration of the 16 per-scale weights against sigma_d on the first
+    count - held_out tiles, evaluated on the last held_out tiles (mean
+    squared error against the targets' variance, Spearman rank
+    correlation)."""
     import synth
     from paper_2108_12050_gb300 import soft
     t0 = time.perf_counter()
-    pairs = [synth.soft_tile_f32(j) for j in range(count)]
+    pairs = synth.render_parallel("soft_tile_f32_cached", [(j,) for j in range(count)])
     render_s = time.perf_counter() - t0
     imgs = [torch.from_numpy(p[0]).cuda() for p in pairs]
     sds = [p[1] for p in pairs]
@@ -534,18 +589,24 @@ def bench_soft(mhfd, torch, stream, count=16):
     fwd, fwd_ms = timed(False)
     bwd, bwd_ms = timed(True)
     torch.cuda.synchronize()
+    ntr = count - held_out
     t0 = time.perf_counter()
     tm = {}
-    wf, bf, losses = soft.fit_weights(det, imgs, sds, tau=tau, T=temp, steps=200, timings=tm)
+    wf, bf, losses = soft.fit_weights(det, imgs[:ntr], sds[:ntr], tau=tau, T=temp, steps=200,
+                                      timings=tm)
     torch.cuda.synchronize()
     fit_s = time.perf_counter() - t0
+    _, mse_ho, rho = soft.evaluate(det, imgs[ntr:], sds[ntr:], wf, bf, tau, temp)
     det.close()
     return {"tiles": count, "side": 2048, "dtype": "f32", "unit": METRIC,
             "forward": fwd, "forward_ms_per_tile": fwd_ms,
             "forward_backward": bwd, "forward_backward_ms_per_tile": bwd_ms,
             "fit": {"steps": 200, "optimizer": "Adam", "seconds": fit_s, **tm,
-                    "mse_first": losses[0], "mse_last": losses[-1],
-                    "target_var": float(np.var(sds))},
+                    "train_tiles": ntr, "held_out_tiles": held_out,
+                    "train_mse_first": losses[0], "train_mse_last": losses[-1],
+                    "train_target_var": float(np.var(sds[:ntr])),
+                    "held_out_mse": mse_ho, "held_out_target_var": float(np.var(sds[ntr:])),
+                    "held_out_spearman": rho},
             "render_s": render_s}
 
 
@@ -576,22 +637,20 @@ def bench_sweep_batch(mhfd, torch, stream, tiles, steps):
 
 
 def bench_batch(mhfd, torch, stream, count=256):
-    """Uneven batch: `count` tiles with sizes drawn from {1024^2, 2048x1536,
-    3072^2, 4096^2} and mixed uint8/uint16 (the 12-bit scene, blob density
-    1.2e-3 /px, sigma_d ~ U[0, 6]).  One tile is rendered per (size, dtype)
-    and reused for every tile of that kind (rendering 256 distinct scenes
-    would take minutes; every tile is still processed).  The batch runs as one
+    """Uneven batch: `count` distinct scenes (seeds 3000 + j) with sizes drawn
+    from {1024^2, 2048x1536, 3072^2, 4096^2}, mixed uint8/uint16 (the 12-bit
+    scene, blob density 1.2e-3 /px, per-tile sigma_d ~ U[0, 6]), rendered
+    once in worker processes into the tile cache.  The batch runs as one
     persistent fused launch replayed from a CUDA graph; baselines are 256
     separate plain (unfused) launches and 256 separate fused launches."""
     import synth
     specs = synth.uneven_batch_specs(count)
-    uniq = {}
-    for seed, H, W, dt, sd in specs:
-        if (H, W, dt) not in uniq:
-            uniq[(H, W, dt)] = synth.uneven_batch_tile(seed, H, W, dt, sd)
-    dev = {k: torch.from_numpy(v.view(np.int16) if v.dtype == np.uint16 else v).cuda()
-           for k, v in uniq.items()}
-    tiles = [dev[(H, W, dt)] for _, H, W, dt, _ in specs]
+    t0 = time.perf_counter()
+    host = synth.render_parallel("uneven_batch_tile_cached", specs)
+    render_s = time.perf_counter() - t0
+    tiles = [torch.from_numpy(v.view(np.int16) if v.dtype == np.uint16 else v).cuda()
+             for v in host]
+    del host
     px = sum(H * W for _, H, W, _, _ in specs)
     det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP, nms="paper")
     det.detect_batch(tiles, stream)            # capture
@@ -607,9 +666,7 @@ def bench_batch(mhfd, torch, stream, count=256):
         times.append(e0.elapsed_time(e1))
     graph = det.batch_uses_graph()
     # identical per tile to a single detection
-    ref = {k: det(t) for k, t in dev.items()}
-    same = all(np.array_equal(o.blobs, ref[(H, W, dt)].blobs)
-               for o, (_, H, W, dt, _) in zip(outs, specs))
+    same = all(np.array_equal(o.blobs, det(t).blobs) for o, t in zip(outs, tiles))
 
     def per_tile(fn):
         torch.cuda.synchronize()
@@ -642,7 +699,9 @@ def bench_batch(mhfd, torch, stream, count=256):
             "fused_per_tile_launches": {"tiles_per_s": count / (ms_fused * 1e-3),
                                         "ms": ms_fused},
             "speedup_vs_plain": ms_plain / ms_b, "speedup_vs_fused_single": ms_fused / ms_b,
-            "inputs": "one rendered tile per (size, dtype), reused across the 256 tiles"}
+            "inputs": "%d distinct scenes (seeds 3000+j), %.1f GB on the device" % (
+                count, sum(t.numel() * t.element_size() for t in tiles) / 1e9),
+            "render_s": render_s}
 
 
 def _serve_tiles(torch):
@@ -664,44 +723,14 @@ def _serve_tiles(torch):
     return kinds
 
 
-def bench_serve(mhfd, torch, rates=(100, 500, 2000), duration=1.0, n_slots=8,
-                budget=40 << 30):
-    """Poisson arrivals of tiles (side uniform in {1024, 2048, 4096, 8192},
-    uint8 or uint16) into the continuous-batching server under a 40 GB HBM
-    budget; p50/p99 latency (arrival to result on the host) and tiles/s.
-    Baseline: the same arrival stream served sequentially, one unfused plain
-    launch per tile (at the lowest rate; the plain path cannot keep up with
-    the others)."""
-    from paper_2108_12050_gb300 import serve
-    kinds = _serve_tiles(torch)
-    out = {"slots": n_slots, "budget_gb": budget / 2**30, "rates": {}}
-    srv = serve.Server(n_slots=n_slots, hbm_budget=budget, n=N_LAYERS, t_min=T_MIN,
-                       t_max=T_MAX, threshold=THR, overlap=OVERLAP)
-    for f in [srv.submit(k) for k in kinds]:   # warm every slot size
-        f.result()
-    for rate in rates:
-        arr = serve.poisson_arrivals(rate, duration, seed=5)
-        pick = np.random.default_rng([5, rate]).integers(0, len(kinds), len(arr))
-        tiles = [kinds[k] for k in pick]
-        res, wall = serve.run_open_loop(srv, tiles, arr)
-        lat = np.array([r.latency_ms for r in res])
-        px = sum(t.size for t in tiles)
-        out["rates"][str(rate)] = {
-            "requests": len(tiles), "tiles_per_s": len(tiles) / wall,
-            "mpixel_per_s": px / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall}
-    out["peak_in_flight"] = srv.stats["peak_in_flight"]
-    out["peak_budget_gb"] = srv.stats["peak_bytes"] / 2**30
-    srv.close()
-    # sequential plain per-tile launches on the lowest-rate stream
-    rate = rates[0]
-    arr = serve.poisson_arrivals(rate, duration, seed=5)
-    pick = np.random.default_rng([5, rate]).integers(0, len(kinds), len(arr))
+def _sequential_plain(mhfd, torch, kinds, pick, arrivals):
+    """The arrival stream served one request at a time by the unfused plain
+    path (copy in, detect, read the result); latencies from arrival."""
     det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP)
     buf = torch.empty(max(k.nbytes for k in kinds), dtype=torch.uint8, device="cuda")
     lat = []
     t0 = time.perf_counter()
-    for k, ta in zip(pick, arr):
+    for k, ta in zip(pick, arrivals):
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
@@ -714,9 +743,69 @@ def bench_serve(mhfd, torch, rates=(100, 500, 2000), duration=1.0, n_slots=8,
         lat.append(1e3 * (time.perf_counter() - t0 - ta))
     wall = time.perf_counter() - t0
     det.close()
-    out["sequential_plain"] = {"rate": rate, "requests": len(lat), "tiles_per_s": len(lat) / wall,
-                               "p50_ms": float(np.percentile(lat, 50)),
-                               "p99_ms": float(np.percentile(lat, 99))}
+    return {"requests": len(lat), "tiles_per_s": len(lat) / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+
+def bench_serve(mhfd, torch, rates=(100, 500, 2000), duration=1.0, n_slots=8,
+                budget=40 << 30, plain_requests=100):
+    """Poisson arrivals of tiles (side uniform in {1024, 2048, 4096, 8192},
+    uint8 or uint16) into the continuous-batching server under a 40 GB HBM
+    budget; p50/p99 latency (arrival to result on the host) and tiles/s.
+    Baseline: the first `plain_requests` arrivals of each rate's stream served
+    sequentially, one unfused plain launch per tile.  A second run holds
+    8192^2 uint16 tiles arriving at 500/s to a budget that admits three of
+    them at once (with 8 slots), so that the budget, not the slots, limits
+    concurrency."""
+    from paper_2108_12050_gb300 import serve
+    kinds = _serve_tiles(torch)
+    out = {"slots": n_slots, "budget_gb": budget / 2**30, "rates": {}}
+    srv = serve.Server(n_slots=n_slots, hbm_budget=budget, n=N_LAYERS, t_min=T_MIN,
+                       t_max=T_MAX, threshold=THR, overlap=OVERLAP)
+    for f in [srv.submit(k) for k in kinds]:   # warm every slot size
+        f.result()
+    streams = {}
+    for rate in rates:
+        arr = serve.poisson_arrivals(rate, duration, seed=5)
+        pick = np.random.default_rng([5, rate]).integers(0, len(kinds), len(arr))
+        streams[rate] = (arr, pick)
+        tiles = [kinds[k] for k in pick]
+        res, wall = serve.run_open_loop(srv, tiles, arr)
+        lat = np.array([r.latency_ms for r in res])
+        px = sum(t.size for t in tiles)
+        out["rates"][str(rate)] = {
+            "requests": len(tiles), "tiles_per_s": len(tiles) / wall,
+            "mpixel_per_s": px / wall / 1e6, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall}
+    out["peak_in_flight"] = srv.stats["peak_in_flight"]
+    out["peak_budget_gb"] = srv.stats["peak_bytes"] / 2**30
+    out["slot_fixed_mb"] = srv.fixed / 2**20
+    srv.close()
+    out["sequential_plain"] = {}
+    for rate in rates:
+        arr, pick = streams[rate]
+        r = _sequential_plain(mhfd, torch, kinds, pick[:plain_requests], arr[:plain_requests])
+        out["sequential_plain"][str(rate)] = r
+    # the budget binds: 8192^2 uint16 tiles, room for three at once
+    big = [k for k in kinds if k.shape == (8192, 8192) and k.dtype == np.uint16][0]
+    probe = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP)
+    fixed, scratch = probe.device_bytes(*big.shape)
+    probe.close()
+    need = serve.image_bytes(big.shape, big.dtype) + scratch
+    tight = n_slots * fixed + 3 * need + need // 2
+    srv = serve.Server(n_slots=n_slots, hbm_budget=tight, n=N_LAYERS, t_min=T_MIN, t_max=T_MAX,
+                       threshold=THR, overlap=OVERLAP)
+    arr = serve.poisson_arrivals(500, 0.4, seed=6)
+    res, wall = serve.run_open_loop(srv, [big] * len(arr), arr)
+    lat = np.array([r.latency_ms for r in res])
+    out["budget_bound"] = {
+        "tile": "8192x8192 u16", "rate": 500, "requests": len(arr),
+        "budget_gb": tight / 2**30, "per_tile_gb": need / 2**30,
+        "peak_budget_gb": srv.stats["peak_bytes"] / 2**30,
+        "peak_in_flight": srv.stats["peak_in_flight"],
+        "tiles_per_s": len(arr) / wall, "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99))}
+    srv.close()
     return out
 
 

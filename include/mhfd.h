@@ -288,6 +288,19 @@ int mhfd_prune_noalloc(const double *radius, int32_t n_levels, float overlap, co
                        const int32_t *d_y, const int32_t *d_i, const float *d_resp,
                        int64_t n_cand, int32_t H, int32_t W, uint8_t *d_keep, void *stream);
 
+/* Device memory of a detector, for callers that budget HBM (the serving
+ * loop admits requests by it; not in the paper).  *fixed_bytes receives the
+ * bytes mhfd_create_detector allocated (candidate list and prune buffers
+ * sized by params.max_candidates, ladder tables); *image_bytes the bytes a
+ * fused detection (mhfd_detect) of an H x W image adds: tile counters,
+ * candidate staging (about 2 B per pixel) and the prune grid.  Those grow to
+ * the largest image detected and stay until mhfd_destroy_detector.  The
+ * image itself is the caller's; H = W = 0 gives *image_bytes = 0.  The plain
+ * path, batches, the soft score and mhfd_detect_host allocate more.  Host
+ * only.  Errors: INVALID_ARG. */
+int mhfd_device_bytes(mhfd_detector *det, int32_t H, int32_t W, int64_t *fixed_bytes,
+                      int64_t *image_bytes);
+
 /* Tile configurations the fused kernel can be specialised with for the
  * ladder of `p` (autotuner menu): returns their count; if `desc` is not NULL
  * writes up to `cap` rows of five int32 (strip width and tile height, both

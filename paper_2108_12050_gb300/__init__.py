@@ -157,6 +157,14 @@ class Detector:
         self._h = h
         self._img_ref = None
 
+    def device_bytes(self, H=0, W=0):
+        """(bytes the detector holds on the device, bytes a fused detection of
+        an H x W image adds) as the library allocates them."""
+        f, i = ctypes.c_int64(), ctypes.c_int64()
+        _n.check(_n.lib().mhfd_device_bytes(self._h, int(H), int(W), ctypes.byref(f),
+                                            ctypes.byref(i)))
+        return f.value, i.value
+
     @property
     def uses_tensor_cores(self):
         """Whether the fused kernel's vertical pass runs on the tensor cores."""

@@ -227,14 +227,32 @@ int tiles_of(const mhfd_detector *d, int H, int W, int *tx, int *ty) {
     return (*tx) * (*ty);
 }
 
-int ensure_image_capacity(mhfd_detector *d, int H, int W, bool plain) {
+// Entries of the per-image buffers a detection of an H x W image needs: tile
+// counters, candidate staging slots and prune grid cells.  The fused kernel
+// stages cap_tile candidates per tile (about 2 B per image pixel); the plain
+// path's 16 x 16 tiles stage more (256 or 1024 per tile) and are sized only
+// when that path runs.
+void image_needs(const mhfd_detector *d, int H, int W, bool plain, size_t *tiles, size_t *stage,
+                 size_t *cells) {
     int tx, ty;
     const size_t n_tiles_fused = (size_t)tiles_of(d, H, W, &tx, &ty);
-    const size_t n_tiles_plain = (size_t)((W + 15) / 16) * ((H + 15) / 16);
-    const size_t cap_tile_plain = d->p.nms == MHFD_NMS_PAPER ? 256 : 1024;
-    const size_t need_tiles = n_tiles_fused > n_tiles_plain ? n_tiles_fused : n_tiles_plain;
+    size_t need_tiles = n_tiles_fused;
     size_t need_stage = n_tiles_fused * (size_t)d->cap_tile;
-    if (n_tiles_plain * cap_tile_plain > need_stage) need_stage = n_tiles_plain * cap_tile_plain;
+    if (plain) {
+        const size_t n_tiles_plain = (size_t)((W + 15) / 16) * ((H + 15) / 16);
+        const size_t cap_tile_plain = d->p.nms == MHFD_NMS_PAPER ? 256 : 1024;
+        if (n_tiles_plain > need_tiles) need_tiles = n_tiles_plain;
+        if (n_tiles_plain * cap_tile_plain > need_stage) need_stage = n_tiles_plain * cap_tile_plain;
+    }
+    const int cs = (int)std::ceil(2.0 * d->radius_max) + 1;
+    *tiles = need_tiles;
+    *stage = need_stage;
+    *cells = (size_t)((W + cs - 1) / cs) * ((H + cs - 1) / cs) + 1;
+}
+
+int ensure_image_capacity(mhfd_detector *d, int H, int W, bool plain) {
+    size_t need_tiles, need_stage, ncells;
+    image_needs(d, H, W, plain, &need_tiles, &need_stage, &ncells);
     int rc;
     if (need_tiles > d->tiles_cap) {
         if ((rc = dalloc(&d->tile_count, need_tiles)) || (rc = dalloc(&d->tile_off, need_tiles))) return rc;
@@ -244,8 +262,6 @@ int ensure_image_capacity(mhfd_detector *d, int H, int W, bool plain) {
         if ((rc = dalloc(&d->stage, need_stage))) return rc;
         d->stage_cap = need_stage;
     }
-    const int cs = (int)std::ceil(2.0 * d->radius_max) + 1;
-    const size_t ncells = (size_t)((W + cs - 1) / cs) * ((H + cs - 1) / cs) + 1;
     if (ncells > d->pb.ncells_cap) {
         if ((rc = dalloc(&d->pb.cell_cnt, ncells)) || (rc = dalloc(&d->pb.cell_start, ncells)))
             return rc;
@@ -1340,6 +1356,30 @@ int mhfd_result_ready(mhfd_detector *d) {
     if (e == cudaSuccess) return 1;
     if (e == cudaErrorNotReady) return 0;
     return cuda_fail(e, "cudaEventQuery");
+}
+
+int mhfd_device_bytes(mhfd_detector *d, int32_t H, int32_t W, int64_t *fixed_bytes,
+                      int64_t *image_bytes) {
+    if (!d || !fixed_bytes || !image_bytes) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+    if (H < 0 || W < 0) return fail(MHFD_ERR_INVALID_ARG, "H and W must be >= 0");
+    const size_t nl = d->R.size();
+    const size_t cap = (size_t)d->cap;
+    size_t fixed = sizeof(SelState) + sizeof(MhfdStretch) + sizeof(Counters) +
+                   64 * (sizeof(double) + 2 * sizeof(float)) + d->taps.size() * sizeof(float) +
+                   nl * sizeof(float) + (256 + 64) * sizeof(int) + (256 + 1) * sizeof(double);
+    // candidate list, prune grid items, states, 16 neighbours, counts, blob list
+    fixed += cap * (sizeof(MhfdCand) + 3 * sizeof(int) + 16 * sizeof(int) + sizeof(mhfd_blob));
+    if (d->p.keep_candidates) fixed += cap * sizeof(mhfd_blob);
+    fixed += d->ct.bytes;
+    *fixed_bytes = (int64_t)fixed;
+    *image_bytes = 0;
+    if (H > 0 && W > 0) {
+        size_t tiles, stage, cells;
+        image_needs(d, H, W, false, &tiles, &stage, &cells);
+        *image_bytes = (int64_t)(2 * tiles * sizeof(int) + stage * sizeof(MhfdCand) +
+                                 2 * cells * sizeof(int));
+    }
+    return MHFD_OK;
 }
 
 int mhfd_uses_tensor_cores(mhfd_detector *d) {

@@ -157,6 +157,7 @@ struct ConflictTable {
     const int *lim = nullptr;   // nl*nl: first d2 with zero overlap (0: pair unused)
     const int *off = nullptr;   // nl*nl: word offset of the pair's bitset
     const unsigned *tab = nullptr;
+    size_t bytes = 0;           // device bytes of lim, off and tab
 };
 int build_conflict_table(const double *d_radius, const std::vector<double> &radius,
                          double overlap, ConflictTable *ct);

@@ -594,6 +594,7 @@ int build_conflict_table(const double *d_radius, const std::vector<double> &radi
     ct->lim = d_lim;
     ct->off = d_off;
     ct->tab = d_tab;
+    ct->bytes = sizeof(int) * 2 * nl * nl + sizeof(unsigned) * (words > 0 ? words : 1);
     MHFD_CUDA(cudaMemcpy(d_lim, lim.data(), sizeof(int) * nl * nl, cudaMemcpyHostToDevice));
     MHFD_CUDA(cudaMemcpy(d_off, off.data(), sizeof(int) * nl * nl, cudaMemcpyHostToDevice));
     conflict_table_kernel<<<dim3(8, nl * nl), 128>>>(d_radius, nl, d_lim, d_off, overlap, d_tab);

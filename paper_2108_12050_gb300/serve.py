@@ -10,7 +10,8 @@ loop is in-process and GPU-resident:
 * requests (host tiles of any size, uint8/uint16/float32) arrive at any time
   and queue; a request is admitted into a free slot as soon as the HBM budget
   allows its footprint (the slot's resident scratch grows to the largest tile
-  it has served; the image buffer and per-pixel candidate slots are charged);
+  it has served; the detector's fixed state, the image buffer and the
+  per-image scratch are charged at the sizes the library reports);
 * an admitted request's host-to-device copy and detection are enqueued
   asynchronously on its slot's stream, so requests admitted while others are
   still on the GPU overlap with them on the device (continuous batching, not
@@ -35,10 +36,6 @@ import numpy as np
 
 from . import Detector
 
-# bytes a detection charges against the budget per pixel, besides the image:
-# candidate slots (1 per 8 px x 16 B = 2 B/px) + tile counts/offsets + margin
-_SCRATCH_BYTES_PER_PX = 3
-_FIXED_BYTES = 96 << 20          # per-slot lists sized by max_candidates, tables
 
 
 @dataclasses.dataclass
@@ -46,17 +43,18 @@ class _Req:
     img: np.ndarray
     future: cf.Future
     t_arrive: float
+    host: object = None           # pinned host bytes of img (torch uint8)
     slot: int = -1
     t_admit: float = 0.0
 
 
-def footprint(shape, dtype) -> int:
-    """Device bytes a request of this size needs beyond the fixed slot state."""
+def image_bytes(shape, dtype) -> int:
+    """Bytes of a tile's device copy."""
     H, W = shape
-    return H * W * (np.dtype(dtype).itemsize + _SCRATCH_BYTES_PER_PX)
+    return H * W * np.dtype(dtype).itemsize
 
 
-def plan_admission(free, need, resident, used, budget, fixed=_FIXED_BYTES):
+def plan_admission(free, need, resident, used, budget, fixed):
     """Admission step for the request at the head of the queue.
 
     `free` lists the free slots, `need[k]` the bytes slot k would have to
@@ -91,9 +89,12 @@ class Server:
                 "det": Detector(device=device, **detector_params),
                 "stream": torch.cuda.Stream(device=device),
                 "buf": None,          # device image buffer (grows)
-                "resident": _FIXED_BYTES,
                 "req": None,
             })
+        # what every slot's detector holds, as the library allocates it
+        self.fixed = self.slots[0]["det"].device_bytes()[0]
+        for slot in self.slots:
+            slot["resident"] = self.fixed
         self.used = sum(s["resident"] for s in self.slots)
         if self.used > self.budget:
             raise ValueError("budget smaller than the slots' fixed state")
@@ -107,16 +108,24 @@ class Server:
 
     # -------------------------------------------------------------- client
     def submit(self, img: np.ndarray) -> cf.Future:
+        """Queue a host tile; returns a future of its DetectionResult.  A
+        pageable (not pinned) image is first copied into pinned memory here,
+        on the caller's thread, so that the server thread only enqueues
+        asynchronous copies and never stalls other requests on host work."""
+        t_arrive = time.perf_counter()
         fut = cf.Future()
         if img.ndim != 2 or img.dtype not in (np.uint8, np.uint16, np.float32):
             fut.set_exception(TypeError("2-D uint8/uint16/float32 image expected"))
             return fut
-        fixed_all = _FIXED_BYTES * len(self.slots)
-        if fixed_all + footprint(img.shape, img.dtype) > self.budget:
+        fixed_all = self.fixed * len(self.slots)
+        if fixed_all + self.footprint(img.shape, img.dtype) > self.budget:
             fut.set_exception(ValueError("tile does not fit the HBM budget"))
             return fut
+        host = self.torch.from_numpy(np.ascontiguousarray(img).reshape(-1).view(np.uint8))
+        if not host.is_pinned():
+            host = host.pin_memory()
         with self.cv:
-            self.queue.append(_Req(img=img, future=fut, t_arrive=time.perf_counter()))
+            self.queue.append(_Req(img=img, future=fut, t_arrive=t_arrive, host=host))
             self.cv.notify()
         return fut
 
@@ -128,9 +137,16 @@ class Server:
         for s in self.slots:
             s["det"].close()
 
+    def footprint(self, shape, dtype) -> int:
+        """Device bytes a request of this size needs beyond the fixed slot
+        state: the tile's device copy and the detector's per-image scratch
+        (tile counters, candidate staging, prune grid), as the library
+        reports them."""
+        return image_bytes(shape, dtype) + self.slots[0]["det"].device_bytes(*shape)[1]
+
     # ----------------------------------------------------------- internals
     def _need(self, slot, req) -> int:
-        want = _FIXED_BYTES + footprint(req.img.shape, req.img.dtype)
+        want = self.fixed + self.footprint(req.img.shape, req.img.dtype)
         return max(0, want - slot["resident"])
 
     def _reset(self, k):
@@ -139,8 +155,8 @@ class Server:
         slot["det"].close()
         slot["det"] = Detector(device=self.device, **self.params)
         slot["buf"] = None
-        self.used -= slot["resident"] - _FIXED_BYTES
-        slot["resident"] = _FIXED_BYTES
+        self.used -= slot["resident"] - self.fixed
+        slot["resident"] = self.fixed
 
     def _admit(self, k, req):
         torch = self.torch
@@ -152,9 +168,7 @@ class Server:
         nbytes = img.nbytes
         if slot["buf"] is None or slot["buf"].numel() < nbytes:
             slot["buf"] = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-        host = torch.from_numpy(img.reshape(-1).view(np.uint8))
-        if not host.is_pinned():
-            host = host.pin_memory()
+        host = req.host
         tdtype = {np.dtype(np.uint8): torch.uint8, np.dtype(np.uint16): torch.int16,
                   np.dtype(np.float32): torch.float32}[img.dtype]
         with torch.cuda.stream(slot["stream"]):
@@ -180,7 +194,8 @@ class Server:
                     # tile; else release the biggest grown scratch and retry
                     act, k = plan_admission(
                         free, {j: self._need(self.slots[j], req) for j in free},
-                        {j: self.slots[j]["resident"] for j in free}, self.used, self.budget)
+                        {j: self.slots[j]["resident"] for j in free}, self.used, self.budget,
+                        self.fixed)
                     if act == "wait":
                         break
                     if act == "reset":

@@ -122,3 +122,24 @@ def fit_weights(det, imgs, targets, tau, T=0.01, steps=200, lr=0.05, seed=0, tim
         timings["features_s"] = t1 - t0
         timings["optimizer_s"] = time.perf_counter() - t1
     return w, b, losses
+
+
+def evaluate(det, imgs, targets, w, b, tau, T=0.01):
+    """Predictions S(I, w) + b of the calibrated score on `imgs` (CUDA
+    forward) and their agreement with `targets`: returns (predictions, mean
+    squared error, Spearman rank correlation)."""
+    import numpy as np
+    pred = np.array([float(soft_score(det, im, w, tau, T)[0]) for im in imgs]) + float(b)
+    y = np.asarray(targets, dtype=np.float64)
+    mse = float(np.mean((pred - y) ** 2))
+
+    def ranks(a):
+        r = np.empty(len(a))
+        r[np.argsort(a, kind="stable")] = np.arange(len(a))
+        return r
+
+    rp, ry = ranks(pred), ranks(y)
+    rp -= rp.mean()
+    ry -= ry.mean()
+    den = float(np.sqrt((rp * rp).sum() * (ry * ry).sum()))
+    return pred, mse, float((rp * ry).sum() / den) if den > 0 else 0.0

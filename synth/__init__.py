@@ -294,3 +294,53 @@ def random_candidates(seed, n, H, W, n_levels, *, cluster=0.0):
     # tie-break order
     resp = (np.round(rng.uniform(0.05, 1.0, x.size) * 64.0) / 64.0).astype(np.float32)
     return x, y, i, resp
+
+
+def uneven_batch_tile_cached(seed, H, W, dtype, sigma_d):
+    """``uneven_batch_tile`` kept in the tile cache."""
+    tag = "c3_s%d_%dx%d_%s_sd%.9g" % (seed, H, W, dtype, sigma_d)
+    return _cached(tag, lambda: uneven_batch_tile(seed, H, W, dtype, sigma_d))
+
+
+def soft_tile_f32_cached(j, H=2048, W=2048, base_seed=4000):
+    """``soft_tile_f32`` with the image kept in the tile cache."""
+    rng = np.random.default_rng([base_seed + j, 9])
+    sd = float(rng.uniform(0.0, 8.0))
+    tag = "c4_s%d_%dx%d_f32" % (base_seed + j, H, W)
+    return _cached(tag, lambda: soft_tile_f32(j, H, W, base_seed)[0]), sd
+
+
+def _render_one(job):
+    name, args = job
+    globals()[name](*args)
+    return 0
+
+
+def render_parallel(name, arglist, workers=None):
+    """Fills the tile cache for ``name(*args)`` over ``arglist`` (one of the
+    ``*_cached`` renderers) in worker processes started with ``spawn``, then
+    returns the results in order, loaded from the cache."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+    todo = [(name, tuple(a)) for a in arglist]
+    todo = [j for j in todo if not _is_cached(j)]
+    workers = min(workers or min(16, os.cpu_count() or 1), len(todo))
+    if workers > 1:
+        # a worker that dies raises BrokenProcessPool here instead of hanging
+        with ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+            list(ex.map(_render_one, todo))
+    return [globals()[name](*a) for a in arglist]
+
+
+def _is_cached(job):
+    name, args = job
+    if name == "uneven_batch_tile_cached":
+        seed, H, W, dtype, sd = args
+        tag = "c3_s%d_%dx%d_%s_sd%.9g" % (seed, H, W, dtype, sd)
+    elif name == "soft_tile_f32_cached":
+        j = args[0]
+        H, W, base = (list(args[1:]) + [2048, 2048, 4000][len(args) - 1:])[:3]
+        tag = "c4_s%d_%dx%d_f32" % (base + j, H, W)
+    else:
+        return False
+    return os.path.exists(_cache_path(tag))

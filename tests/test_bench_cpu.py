@@ -40,3 +40,21 @@ def test_algorithmic_operation_count(bench):
 def test_nominal_fp32_peak(bench):
     # 152 SMs x 128 FP32 lanes x 2.07 GHz maximum SM clock
     assert abs(bench.nominal_alu_peak() - 40.27392e12) < 1e6
+
+
+def test_variant_operation_counts(bench):
+    import oracle
+    t = oracle.ladder(16, 1.0, 12.0)
+    R = [oracle.kernel_radius(x) for x in t]
+    assert bench.variant_ops_per_px("dog") == 1866
+    # the derived-tap Laplacian on levels t_1..t_n: vertical g (2R+1) and
+    # g'' (2R+3), horizontal g'' and g on them (2R+3, 2R+1)
+    assert bench.variant_ops_per_px("log") == sum(8 * r + 8 for r in R[:16]) + 2 * 16 + 8
+    # the DoG stack and one threshold test per (pixel, layer)
+    assert bench.variant_ops_per_px("local26") == 2 * sum(2 * r + 1 for r in R) + 2 * 16
+
+
+def test_r4_keeps_four_significant_digits(bench):
+    assert bench.r4(14643.263544) == 14640.0
+    assert bench.r4(0.0009999840015) == 0.001
+    assert bench.r4(None) is None

@@ -67,14 +67,51 @@ def test_budget_limits_concurrency():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     from paper_2108_12050_gb300 import serve
+    import paper_2108_12050_gb300 as mhfd
     tiles = _tiles()[:4]
     ref = _alone(tiles)
     # room for the slots' fixed state plus exactly one 1024x256 uint16 tile
-    budget = 4 * serve._FIXED_BYTES + serve.footprint((1024, 256), np.uint16)
+    probe = mhfd.Detector(**PARAMS)
+    fixed, scratch = probe.device_bytes(1024, 256)
+    probe.close()
+    budget = 4 * fixed + serve.image_bytes((1024, 256), np.uint16) + scratch
     srv = serve.Server(n_slots=4, hbm_budget=budget, **PARAMS)
+    assert srv.fixed == fixed
     got = [f.result(timeout=120) for f in [srv.submit(t) for t in tiles]]
     stats = dict(srv.stats)
     srv.close()
     assert stats["peak_bytes"] <= budget
     for r, want in zip(got, ref):
         assert np.array_equal(r.blobs, want.blobs)
+
+
+def test_reported_device_bytes_match_the_allocations():
+    """What the library reports (and the server charges) against what the
+    device actually lost, read with cudaMemGetInfo: the detector's fixed
+    state at creation, and the per-image scratch of a first detection of an
+    8192 x 8192 uint8 tile.  The driver rounds allocations up to its page
+    size, so each side may differ by a few pages per allocation."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2108_12050_gb300 as mhfd
+    torch.cuda.set_device(0)
+    warm = mhfd.Detector(**PARAMS)          # loads the compiled kernels once
+    warm.close()
+    img = torch.zeros((8192, 8192), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    det = mhfd.Detector(**PARAMS)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    fixed, scratch = det.device_bytes(8192, 8192)
+    det(img)
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    det.close()
+    got_fixed, got_scratch = free0 - free1, free1 - free2
+    print("device bytes: fixed %d reported / %d measured; image scratch %d / %d" % (
+        fixed, got_fixed, scratch, got_scratch))
+    slack = 32 << 20
+    assert abs(got_fixed - fixed) <= slack
+    assert abs(got_scratch - scratch) <= slack
+    assert scratch > 2 * 8192 * 8192 * 0.9        # the 2 B/px candidate staging

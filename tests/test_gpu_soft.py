@@ -96,21 +96,26 @@ def test_autograd_wrapper():
 
 
 def test_weight_fit_regresses_defocus():
+    """Calibration against known defocus (sigma_d ~ U[0, 8]): 64 tiles, the
+    17 parameters (16 weights and a bias) fitted on 48 of them by 200 Adam
+    steps, judged on the 16 held out.  The held-out error must be a small
+    part of the targets' variance and the score must order the held-out
+    tiles by their defocus."""
     import paper_2108_12050_gb300 as mhfd
     from paper_2108_12050_gb300 import soft
     tiles, sds = [], []
-    for j in range(16):
-        img, sd = _f32_tile(j, 192, 192)
+    for j in range(64):
+        img, sd = _f32_tile(j, 256, 256)
         tiles.append(torch.from_numpy(img).cuda())
         sds.append(sd)
     det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05)
-    w, b, losses = soft.fit_weights(det, tiles, sds, tau=0.05, steps=200)
-    var = float(np.var(sds))
-    # 16 images and 17 parameters: the least-squares optimum interpolates, so
-    # a converged fit leaves a small fraction of the target variance
-    assert losses[-1] < 0.1 * var, (losses[0], losses[-1], var)
-    assert losses[-1] < losses[0]
+    w, b, losses = soft.fit_weights(det, tiles[:48], sds[:48], tau=0.05, steps=200)
+    assert losses[-1] < 0.2 * float(np.var(sds[:48])) and losses[-1] < losses[0]
     # the returned (w, b) reproduce the fitted predictions through the score
-    pred = np.array([float(soft.soft_score(det, t, w, 0.05, 0.01)[0]) for t in tiles]) + float(b)
-    assert np.mean((pred - np.array(sds)) ** 2) < 0.1 * var
+    _, mse_train, _ = soft.evaluate(det, tiles[:48], sds[:48], w, b, 0.05)
+    assert abs(mse_train - losses[-1]) < 1e-2 * max(1.0, losses[0])
+    _, mse, rho = soft.evaluate(det, tiles[48:], sds[48:], w, b, 0.05)
+    var = float(np.var(sds[48:]))
+    assert mse < 0.3 * var, (mse, var)
+    assert rho > 0.85, rho
     det.close()
