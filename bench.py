@@ -36,8 +36,7 @@ N_LAYERS, T_MIN, T_MAX, THR, OVERLAP = 16, 1.0, 12.0, 0.05, 0.5
 SIGMA_D = (0.0, 1.0, 2.0, 4.0, 8.0)
 H = W = 4096
 METRIC = "Mpixel/s"
-WORKLOAD = ("4096^2 u16 SEM-like tiles, sigma_d sweep {0,1,2,4,8} (5 tiles/step), n=16 "
-            "t=1..12, FP32, tau 0.05, overlap 0.5, Eq. 3 rule")
+WORKLOAD = "4096^2 u16 tiles, sigma_d 0,1,2,4,8 (5/step), n=16 t=1..12, tau .05, overlap .5"
 
 
 def r4(x):
@@ -476,16 +475,15 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r4(total_ms / args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs > L2 (5 x 32 MiB per step)",
+        "config": {"workload": WORKLOAD, "l2": "inputs > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "p50_ms_per_tile": r4(statistics.median(per_tile)), "p99_ms_per_tile": r4(p99),
         "plain": {"value": r4(plain["value"]), "p50_ms_per_tile": r4(plain["p50_ms_per_tile"])}
                  if plain else None,
         "fused_vs_plain": r4(value / world / plain["value"]) if plain else None,
         "roofline": {"bound": "alu", "achieved": r4(achieved), "peak": r4(peak),
-                     "unit": "Tops/s (FP32 FFMA)", "frac": r4(achieved / peak),
+                     "unit": "Tops/s FP32", "frac": r4(achieved / peak),
                      "traffic": traffic, "kernel_ms_avg": r4(k_avg),
-                     "frac_of_probe": r4(achieved / probe),
                      "ffma_side_frac": r4(side / peak) if tc else None},
         "cpu_baseline": {k: r4(v) if isinstance(v, float) else v for k, v in cpu.items()
                          if k != "single_core"} if cpu else None,

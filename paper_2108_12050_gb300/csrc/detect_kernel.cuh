@@ -258,7 +258,11 @@ struct HState {
     float lp[4];  // L of the previous level
     float m[4];   // running max over scales
     int a[4];     // its first argmax
-    LMask mk[4];  // 26-neighbour rule: layers whose response is above the threshold
+    // 26-neighbour rule: layers whose response is above the threshold and
+    // not below either scale neighbour at the same pixel (the only layers
+    // whose 3x3x3 test can pass), and the previous layer's response
+    LMask mk[4];
+    float dp[4];
     // soft-score forward: running sums over the march of sigmoid((D_i -
     // tau) / T) at this item's interior output pixels, per layer
     float soft[NSOFT];
@@ -1043,8 +1047,12 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
             o.w = cx.inb[3] ? d[3] : ninf;
             reinterpret_cast<float4 *>(s_ring + (cx.slot * NDOG + I) * TX2)[cx.q] = o;
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (cx.inb[u] && d[u] > h.thr) st.mk[u] |= LMask(1) << I;
+            for (int u = 0; u < 4; ++u) {
+                if (!cx.inb[u]) continue;
+                if (I > 0 && d[u] > st.dp[u]) st.mk[u] &= ~(LMask(1) << (I > 0 ? I - 1 : 0));
+                if (d[u] > h.thr && (I == 0 || !(st.dp[u] > d[u]))) st.mk[u] |= LMask(1) << I;
+                st.dp[u] = d[u];
+            }
         }
         if (STORE) {
 #pragma unroll
@@ -1207,20 +1215,23 @@ __device__ __forceinline__ bool cand_paper(const float *s_ring, int r, int c, fl
     return !(nb > m);
 }
 
-// 26-neighbour rule on the response ring
+// 26-neighbour rule on the response ring, for a layer whose mask bit is set
+// (above the threshold, not below its scale neighbours at the same pixel):
+// the 8 spatial neighbours of its own layer first, then those of the layers
+// below and above (out-of-image neighbours hold -inf)
 __device__ __forceinline__ bool cand_26(const float *s_ring, int r, int c, int l, float thr,
                                         float *v_out) {
     const float v = s_ring[((r % RING) * NDOG + l) * TX2 + c];
     *v_out = v;
     if (!(v > thr)) return false;
 #pragma unroll
-    for (int dl = -1; dl <= 1; ++dl) {
-        const int ll = l + dl;
+    for (int k = 0; k < 3; ++k) {
+        const int ll = l + (k == 0 ? 0 : k == 1 ? -1 : 1);
         if (ll < 0 || ll >= NDOG) continue;
 #pragma unroll
         for (int dr = -1; dr <= 1; ++dr) {
             const float *row = s_ring + (((r + dr) % RING) * NDOG + ll) * TX2;
-            if (row[c - 1] > v || row[c] > v || row[c + 1] > v) return false;
+            if (row[c - 1] > v || row[c + 1] > v || (dr != 0 && row[c] > v)) return false;
         }
     }
     return true;
