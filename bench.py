@@ -816,6 +816,7 @@ def tile_used(mhfd):
     shape = tuned or mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX, tensor_cores=True)
     return {"width": shape[0], "height": shape[1], "rows_per_step": shape[2],
             "threads": shape[3], "level_groups": shape[4],
+            "rows_per_item": shape[5] if len(shape) > 5 else 1,
             "vertical_pass": "tensor cores",
             "source": "autotuned" if tuned else "heuristic"}
 

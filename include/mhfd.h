@@ -79,13 +79,17 @@ typedef struct {
     int32_t keep_candidates;/* 1: also expose the pre-prune candidate list */
     int32_t tile_override;  /* 0 = built-in tile choice; k > 0 = row k-1 of
                                mhfd_tile_configs() (autotuner use) */
-    int32_t tile_shape[5];  /* explicit fused-kernel geometry when
+    int32_t tile_shape[6];  /* explicit fused-kernel geometry when
                                tile_shape[0] > 0, overriding tile_override:
                                strip width incl. the 2 NMS border columns
                                (multiple of 4), tile height incl. 2 border
                                rows, rows per step (2..16), threads per
-                               block (multiple of 32), level groups; the
-                               same five fields as mhfd_tile_configs.
+                               block (multiple of 32), level groups, rows
+                               per horizontal item (0 or 1: one row of four
+                               outputs; 2: two rows, packed two-lane FMAs
+                               over the row pair; needs an even number of
+                               rows per step); the same six fields as
+                               mhfd_tile_configs.
                                INVALID_ARG when out of range, UNSUPPORTED
                                when it does not fit in shared memory */
     int32_t timing;         /* 1: record CUDA events around the kernels of each
@@ -303,15 +307,15 @@ int mhfd_device_bytes(mhfd_detector *det, int32_t H, int32_t W, int64_t *fixed_b
 
 /* Tile configurations the fused kernel can be specialised with for the
  * ladder of `p` (autotuner menu): returns their count; if `desc` is not NULL
- * writes up to `cap` rows of five int32 (strip width and tile height, both
+ * writes up to `cap` rows of six int32 (strip width and tile height, both
  * including the one-pixel NMS border, rows per step, threads per block,
- * level groups).
+ * level groups, rows per horizontal item).
  * Row k is selected by params.tile_override = k + 1.  Host only. */
 int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap);
 
-/* The configuration mhfd_create_detector would use for `p` (same five
+/* The configuration mhfd_create_detector would use for `p` (same six
  * fields as above).  Host only. */
-int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5);
+int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc6);
 
 /* Compiles the fused kernel for the ladder and tile of `p` (store = 0: the
  * detection kernel of params.nms; 1: the stack-storing variant of

@@ -136,7 +136,7 @@ def _tuned_variants():
             continue
         for best in ent.values():
             shape = best.get("shape")
-            if shape and len(shape) == 5:
+            if shape and len(shape) in (5, 6):
                 nms = 0 if m.group(4) == "paper" else 1
                 log = m.group(5) is not None
                 tc = m.group(6) is not None

@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
         ("device", ctypes.c_int32),
         ("keep_candidates", ctypes.c_int32),
         ("tile_override", ctypes.c_int32),
-        ("tile_shape", ctypes.c_int32 * 5),
+        ("tile_shape", ctypes.c_int32 * 6),
         ("timing", ctypes.c_int32),
         ("response", ctypes.c_int32),
         ("boundary", ctypes.c_int32),
@@ -196,13 +196,13 @@ def tile_configs(**kw):
     n = lib().mhfd_tile_configs(ctypes.byref(p), None, 0)
     if n < 0:
         check(n)
-    buf = (ctypes.c_int32 * (5 * max(n, 1)))()
+    buf = (ctypes.c_int32 * (6 * max(n, 1)))()
     lib().mhfd_tile_configs(ctypes.byref(p), buf, n)
-    return [tuple(buf[5 * k:5 * k + 5]) for k in range(n)]
+    return [tuple(buf[6 * k:6 * k + 6]) for k in range(n)]
 
 
 def chosen_tile(**kw):
     p = make_params(**kw)
-    buf = (ctypes.c_int32 * 5)()
+    buf = (ctypes.c_int32 * 6)()
     check(lib().mhfd_chosen_tile(ctypes.byref(p), buf))
     return tuple(buf)

@@ -492,10 +492,14 @@ int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, Tile
             if (ts[0] % 4 || ts[0] < 8 || ts[0] > 2048 || ts[1] < 3 || ts[1] > 4096 ||
                 ts[4] < 1 || ts[4] > nl)
                 return fail(MHFD_ERR_INVALID_ARG, "tile_shape out of range");
+            if (ts[5] < 0 || ts[5] > 2 || (ts[5] == 2 && ts[2] % 2))
+                return fail(MHFD_ERR_INVALID_ARG, "tile_shape: rows per item must be 1, or 2 "
+                                                  "with an even number of rows per step");
             cfg->tx2 = ts[0];
             cfg->ty2 = ts[1];
             cfg->rb = ts[2];
             cfg->nt = ts[3];
+            cfg->hr = ts[5] == 2 ? 2 : 1;
             cfg->gb.assign(ts[4] + 1, 0);
             for (int g = 0; g <= ts[4]; ++g) cfg->gb[g] = (int)((long long)nl * g / ts[4]);
             cfg->tc = 1;
@@ -519,12 +523,17 @@ int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, Tile
         if (ts[0] % 4 || ts[0] < 8 || ts[0] > 2048 || ts[1] < 3 || ts[1] > 4096 || ts[2] < 2 ||
             ts[2] > 16 || ts[3] % 32 || ts[3] < 32 || ts[3] > 1024 || ts[4] < 1 || ts[4] > nl)
             return fail(MHFD_ERR_INVALID_ARG, "tile_shape out of range");
-        if (ts[2] * (ts[0] / 4) > 2 * ts[3])
-            return fail(MHFD_ERR_INVALID_ARG, "tile_shape: more than two row quads per thread");
+        if (ts[5] < 0 || ts[5] > 2 || (ts[5] == 2 && ts[2] % 2))
+            return fail(MHFD_ERR_INVALID_ARG, "tile_shape: rows per item must be 1, or 2 "
+                                              "with an even number of rows per step");
+        const int hr = ts[5] == 2 ? 2 : 1;
+        if ((ts[2] / hr) * (ts[0] / 4) > 2 * ts[3])
+            return fail(MHFD_ERR_INVALID_ARG, "tile_shape: more than two horizontal items per thread");
         cfg->tx2 = ts[0];
         cfg->ty2 = ts[1];
         cfg->rb = ts[2];
         cfg->nt = ts[3];
+        cfg->hr = hr;
         cfg->gb.assign(ts[4] + 1, 0);
         for (int g = 0; g <= ts[4]; ++g) cfg->gb[g] = (int)((long long)nl * g / ts[4]);
         if (smem_estimate(R, mode, *cfg) > kSmemLimitBytes)
@@ -761,7 +770,7 @@ void mhfd_default_params(mhfd_params *p) {
     p->device = -1;
     p->keep_candidates = 0;
     p->tile_override = 0;
-    for (int k = 0; k < 5; ++k) p->tile_shape[k] = 0;
+    for (int k = 0; k < 6; ++k) p->tile_shape[k] = 0;
     p->timing = 0;
     p->response = MHFD_RESPONSE_DOG;
     p->boundary = MHFD_BOUNDARY_REFLECT;
@@ -1027,18 +1036,19 @@ int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap) {
         p->tensor_cores ? tile_menu_tc(lk.R, mode) : tile_menu(lk.R, mode);
     if (desc) {
         for (int k = 0; k < (int)menu.size() && k < cap; ++k) {
-            desc[5 * k + 0] = menu[k].tx2;
-            desc[5 * k + 1] = menu[k].ty2;
-            desc[5 * k + 2] = menu[k].rb;
-            desc[5 * k + 3] = menu[k].nt;
-            desc[5 * k + 4] = (int)menu[k].gb.size() - 1;
+            desc[6 * k + 0] = menu[k].tx2;
+            desc[6 * k + 1] = menu[k].ty2;
+            desc[6 * k + 2] = menu[k].rb;
+            desc[6 * k + 3] = menu[k].nt;
+            desc[6 * k + 4] = (int)menu[k].gb.size() - 1;
+            desc[6 * k + 5] = menu[k].hr;
         }
     }
     return (int)menu.size();
 }
 
-int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5) {
-    if (!p || !desc5) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
+int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc6) {
+    if (!p || !desc6) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");
     std::vector<double> t;
     std::vector<int> R;
     int rc = build_ladder(*p, &t, &R);
@@ -1048,11 +1058,12 @@ int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc5) {
     int mode = p->nms;
     fused_ladder(*p, t, R, &lk, &mode);
     if ((rc = resolve_tile(lk.R, mode, *p, &c, p->tensor_cores && tc_mode_ok(mode)))) return rc;
-    desc5[0] = c.tx2;
-    desc5[1] = c.ty2;
-    desc5[2] = c.rb;
-    desc5[3] = c.nt;
-    desc5[4] = (int)c.gb.size() - 1;
+    desc6[0] = c.tx2;
+    desc6[1] = c.ty2;
+    desc6[2] = c.rb;
+    desc6[3] = c.nt;
+    desc6[4] = (int)c.gb.size() - 1;
+    desc6[5] = c.hr;
     return MHFD_OK;
 }
 

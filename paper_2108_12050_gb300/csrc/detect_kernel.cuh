@@ -70,10 +70,20 @@ constexpr bool STORE = (MHFD_STORE) != 0;
 #define MHFD_VTC 0
 #endif
 constexpr bool TC = (MHFD_VTC) != 0;
-// horizontal pass on packed two-lane FMAs: measured faster for the
-// tensor-core LoG kernel (2.79 -> 2.61 ms on a 4096^2 tile), slower for the
-// DoG kernels (1.00 -> 1.16 ms tensor-core, 1.51 -> 1.60 ms FFMA)
-constexpr bool HPACK = TC && LOG;
+// Rows per horizontal item: 1 (four outputs of one row), or 2 (four
+// outputs of each of two adjacent rows; the V rows of a step are then
+// stored pair-interleaved, column by column, so that one float4 load holds
+// two columns of both rows and each tap is one packed two-lane FMA over the
+// row pair, the same tap in both lanes).  The detection modes only.
+#ifndef MHFD_HR
+#define MHFD_HR 1
+#endif
+constexpr int HR = MHFD_HR;
+// one-row items on packed two-lane FMAs over column pairs (outputs (0, 1)
+// and (2, 3)): measured faster for the tensor-core LoG kernel (2.79 -> 2.61
+// ms on a 4096^2 tile), slower for the DoG kernels (1.00 -> 1.16 ms
+// tensor-core, 1.51 -> 1.60 ms FFMA)
+constexpr bool HPACK = TC && LOG && HR == 1;
 
 // Kernel radius R_l of Gaussian level l and the level groups [GB(g), GB(g+1)).
 MK_HD constexpr int kR(int l) {
@@ -131,7 +141,7 @@ constexpr int BROWS = MHFD_BROWS;              // rows of the sliding input wind
 constexpr int NT_COLS = (WEXT + MHFD_NT - 1) / MHFD_NT;  // input columns per thread
 constexpr int RING = RB + 2;
 constexpr int NQ4 = TX2 / 4;
-constexpr int HITEMS = RB * NQ4;
+constexpr int HITEMS = (RB / HR) * NQ4;
 // threads that take horizontal items: with the tensor-core pass and a
 // block of whole warpgroups plus one warp, that last warp only issues MMAs
 constexpr int NTW = (TC && NT % 128 == 32) ? NT - 32 : NT;
@@ -175,6 +185,12 @@ MK_HD constexpr int vrow_max() {
 }
 constexpr int NTAPS = tapoff(NL);
 constexpr int VROW = vrow_max();
+// shared-memory index of V row position `col` (voff(l) + column, plus
+// extp(l) for the LoG's second row) of step row j: row after row, or row
+// pairs interleaved column by column for two-row items
+MK_HD constexpr int vidx(int j, int col) {
+    return HR == 1 ? j * VROW + col : (j >> 1) * 2 * VROW + 2 * col + (j & 1);
+}
 
 // Tensor-core vertical pass geometry.  The window holds the centred integer
 // pixels x = clamp(v, lo, hi) - c0 as fp16 (exact while |x| <= 2048) in the
@@ -247,6 +263,7 @@ static_assert(!TC || ((MODE == 0 || (MODE == 1 && !LOG)) && (RB == 4 || RB == 8)
 static_assert(!TC || TC_NMT * TC_NCT <= 512, "tensor memory columns");
 static_assert(!TC || BROWS >= WIN + 2 * RB + 16, "window rows of the tensor-core pass");
 static_assert(!TC || NGROUPS <= 12, "one mbarrier per group in the control block");
+static_assert(HR == 1 || (HR == 2 && RB % 2 == 0 && MODE <= 1), "two-row horizontal items");
 
 struct KParams {
     MhfdKHeader h;
@@ -254,7 +271,8 @@ struct KParams {
 
 constexpr int NSOFT = MODE == 2 ? NDOG : 1;
 
-struct HState {
+// state of one row of a horizontal item (four outputs) across the levels
+struct HRowState {
     float lp[4];  // L of the previous level
     float m[4];   // running max over scales
     int a[4];     // its first argmax
@@ -263,6 +281,9 @@ struct HState {
     // whose 3x3x3 test can pass), and the previous layer's response
     LMask mk[4];
     float dp[4];
+};
+struct HState {
+    HRowState rw[HR];
     // soft-score forward: running sums over the march of sigmoid((D_i -
     // tau) / T) at this item's interior output pixels, per layer
     float soft[NSOFT];
@@ -731,15 +752,20 @@ __device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (
         tc_regs_ready(r[LI]);
         const int cc = c - (RMAX - kRH(L));
         if (cc >= 0 && cc < TX2 + 2 * kRH(L)) {
-            // the raw MMA sums (the horizontal pass applies the scale)
+            // the raw MMA sums (the horizontal pass applies the scale), and
+            // the LoG's g'' (*)_y I row beside them
 #pragma unroll
-            for (int j = 0; j < RB; ++j)
-                s_v[j * VROW + voff(L) + cc] = __uint_as_float(r[LI][j]);
-            // the LoG's g'' (*)_y I row beside it
-            if constexpr (LOG) {
+            for (int pt = 0; pt < TC_P; ++pt) {
+                const int col = voff(L) + pt * extp(L) + cc;
+                if constexpr (HR == 2) {
 #pragma unroll
-                for (int j = 0; j < RB; ++j)
-                    s_v[j * VROW + voff(L) + extp(L) + cc] = __uint_as_float(r[LI][RB + j]);
+                    for (int j = 0; j < RB; j += 2)
+                        *reinterpret_cast<float2 *>(s_v + vidx(j, col)) = make_float2(
+                            __uint_as_float(r[LI][pt * RB + j]), __uint_as_float(r[LI][pt * RB + j + 1]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RB; ++j) s_v[vidx(j, col)] = __uint_as_float(r[LI][pt * RB + j]);
+                }
             }
         }
         tc_st_levels<G, LI + 1>(s_v, r, c, ts);
@@ -830,11 +856,22 @@ __device__ __forceinline__ void vcol(const float *__restrict__ win, float *__res
     for (int l = 0; l < NG; ++l) {
         const int cc = c - (RMAX - kRH(LB + l));
         if (cc >= 0 && cc < TX2 + 2 * kRH(LB + l)) {
+            const int col = voff(LB + l) + cc;
+            if constexpr (HR == 2 && ROWS % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < ROWS; ++j) {
-                s_v[(o0 + j) * VROW + voff(LB + l) + cc] = acc[j][l];
-                if constexpr (LOG)
-                    s_v[(o0 + j) * VROW + voff(LB + l) + extp(LB + l) + cc] = acc2[j][l];
+                for (int j = 0; j < ROWS; j += 2) {
+                    *reinterpret_cast<float2 *>(s_v + vidx(o0 + j, col)) =
+                        make_float2(acc[j][l], acc[j + 1][l]);
+                    if constexpr (LOG)
+                        *reinterpret_cast<float2 *>(s_v + vidx(o0 + j, col + extp(LB + l))) =
+                            make_float2(acc2[j][l], acc2[j + 1][l]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < ROWS; ++j) {
+                    s_v[vidx(o0 + j, col)] = acc[j][l];
+                    if constexpr (LOG) s_v[vidx(o0 + j, col + extp(LB + l))] = acc2[j][l];
+                }
             }
         }
     }
@@ -953,46 +990,121 @@ __device__ __forceinline__ void hquads(const float4 *w, float (&a)[4]) {
     }
 }
 
-struct HCtx {
-    int r;        // tile row of this item
-    int q;        // float4 chunk (outputs 4q .. 4q+3)
-    int slot;     // ring slot of row r
-    int gy;       // image row
-    int gx0;      // image column of output 4q
-    bool inb[4];  // output inside the image
+// one row of a horizontal item
+struct HRowCtx {
+    int r;          // chunk row
+    int slot;       // ring slot of row r
+    int gy;         // image row
+    bool inb[4];    // output inside the image
     bool inter[4];  // output inside the tile interior and the image (stored)
 };
+struct HCtx {
+    int q;          // float4 chunk (outputs 4q .. 4q+3)
+    int j0;         // first step row of the item
+    int gx0;        // image column of output 4q
+    HRowCtx rw[HR];
+};
 
-// The horizontal pass of level L for this item's four outputs, then its
-// response: the DoG of Eq. 2 with the previous level (kept in st.lp), or the
-// scale-normalised Laplacian of the level itself.  `vs` scales the V rows to
-// stretched units (1 for the FFMA kernel; the tensor-core kernel keeps the
-// raw MMA sums, whose offset drops out of the DoG and the LoG because the
-// taps sum to 1 and the second-difference taps to 0).
-template <int L>
-__device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, const HCtx &cx,
-                                       HState &st, float *s_ring, float vs) {
-    constexpr int R = kR(L);
-    float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if constexpr (LOG) {
-        // t^2 (g (*)_x (g'' (*)_y I) + g'' (*)_x (g (*)_y I)): the first row
-        // starts one column before its radius-R window, the second is read
-        // with radius R + 1
-        constexpr int NQA = (2 * R + 4) / 4 + 1;
-        constexpr int NQB = (2 * (R + 1) + 3) / 4 + 1;
-        hquads<R, tapoff(L), NQA, 1, false>(
-            reinterpret_cast<const float4 *>(vrow + voff(L) + extp(L)) + cx.q, a);
-        hquads<R + 1, tapoff2(L), NQB, 0, true>(
-            reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q, a);
-    } else {
-        constexpr int NQ = (2 * R + 3) / 4 + 1;
-        hquads<R, tapoff(L), NQ, 0, false>(
-            reinterpret_cast<const float4 *>(vrow + voff(L)) + cx.q, a);
+// Two-row items: window column M (a float2 of both rows' values) feeds
+// output U of both rows with tap |M - U - R - OFF| (of the second-difference
+// taps when T2): one packed two-lane FMA.
+template <int R, int TO, int M, int U, int OFF, bool T2>
+__device__ __forceinline__ void hacc2u(float2 v, float2 (&a)[4]) {
+    constexpr int k = M - U - R - OFF;
+    if constexpr (k >= -R && k <= R) {
+        constexpr float t = T2 ? kTap2(TO + (k < 0 ? -k : k)) : kTap(TO + (k < 0 ? -k : k));
+        a[U] = __ffma2_rn(make_float2(t, t), v, a[U]);
     }
+}
+template <int R, int TO, int M, int OFF, bool T2>
+__device__ __forceinline__ void hacc2(float2 v, float2 (&a)[4]) {
+    hacc2u<R, TO, M, 0, OFF, T2>(v, a);
+    hacc2u<R, TO, M, 1, OFF, T2>(v, a);
+    hacc2u<R, TO, M, 2, OFF, T2>(v, a);
+    hacc2u<R, TO, M, 3, OFF, T2>(v, a);
+}
+// Columns in the order of the one-row pass (quads of four columns
+// descending, columns ascending within a quad), so that each lane sums
+// exactly as the one-row pass does; a quad is two float4 loads of the
+// pair-interleaved rows (two columns each).
+template <int R, int TO, int Q, int OFF, bool T2>
+struct HQuads2 {
+    static __device__ __forceinline__ void run(const float4 *w, float2 (&a)[4]) {
+        const float4 v0 = w[2 * Q], v1 = w[2 * Q + 1];
+        hacc2<R, TO, 4 * Q + 0, OFF, T2>(make_float2(v0.x, v0.y), a);
+        hacc2<R, TO, 4 * Q + 1, OFF, T2>(make_float2(v0.z, v0.w), a);
+        hacc2<R, TO, 4 * Q + 2, OFF, T2>(make_float2(v1.x, v1.y), a);
+        hacc2<R, TO, 4 * Q + 3, OFF, T2>(make_float2(v1.z, v1.w), a);
+        HQuads2<R, TO, Q - 1, OFF, T2>::run(w, a);
+    }
+};
+template <int R, int TO, int OFF, bool T2>
+struct HQuads2<R, TO, -1, OFF, T2> {
+    static __device__ __forceinline__ void run(const float4 *, float2 (&)[4]) {}
+};
+
+// The horizontal sums of level L for the item's outputs: a[rr][u] for row rr.
+// `vbase` is the item's first row in the V rows (row pair for two-row items).
+template <int L>
+__device__ __forceinline__ void hsums(const float *vbase, int q, float (&a)[HR][4]) {
+    constexpr int R = kR(L);
+    if constexpr (HR == 2) {
+        float2 p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = make_float2(0.0f, 0.0f);
+        const float4 *base = reinterpret_cast<const float4 *>(vbase) + 2 * q;
+        if constexpr (LOG) {
+            constexpr int NQA = (2 * R + 4) / 4 + 1;
+            constexpr int NQB = (2 * (R + 1) + 3) / 4 + 1;
+            HQuads2<R, tapoff(L), NQA - 1, 1, false>::run(base + (voff(L) + extp(L)) / 2, p);
+            HQuads2<R + 1, tapoff2(L), NQB - 1, 0, true>::run(base + voff(L) / 2, p);
+        } else {
+            constexpr int NQ = (2 * R + 3) / 4 + 1;
+            HQuads2<R, tapoff(L), NQ - 1, 0, false>::run(base + voff(L) / 2, p);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[0][u] = p[u].x;
+            a[HR - 1][u] = p[u].y;
+        }
+    } else {
+        float (&a0)[4] = a[0];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a0[u] = 0.0f;
+        if constexpr (LOG) {
+            // t^2 (g (*)_x (g'' (*)_y I) + g'' (*)_x (g (*)_y I)): the first row
+            // starts one column before its radius-R window, the second is read
+            // with radius R + 1
+            constexpr int NQA = (2 * R + 4) / 4 + 1;
+            constexpr int NQB = (2 * (R + 1) + 3) / 4 + 1;
+            hquads<R, tapoff(L), NQA, 1, false>(
+                reinterpret_cast<const float4 *>(vbase + voff(L) + extp(L)) + q, a0);
+            hquads<R + 1, tapoff2(L), NQB, 0, true>(
+                reinterpret_cast<const float4 *>(vbase + voff(L)) + q, a0);
+        } else {
+            constexpr int NQ = (2 * R + 3) / 4 + 1;
+            hquads<R, tapoff(L), NQ, 0, false>(reinterpret_cast<const float4 *>(vbase + voff(L)) + q,
+                                               a0);
+        }
+    }
+}
+
+// The response of level L at one row of the item's outputs from its
+// horizontal sums a: the DoG of Eq. 2 with the previous level (kept in
+// st.lp), or the scale-normalised Laplacian of the level itself; then the
+// running max / argmax, the ring and masks of the 26-neighbour rule, the
+// soft-score sums or the stored stack.  `vs` scales the V rows to stretched
+// units (1 for the FFMA kernel; the tensor-core kernel keeps the raw MMA
+// sums, whose offset drops out of the DoG and the LoG because the taps sum
+// to 1 and the second-difference taps to 0).
+template <int L>
+__device__ __forceinline__ void hrespond(const MhfdKHeader &h, const HCtx &cx, const HRowCtx &w,
+                                         HRowState &st, float *soft, const float (&a)[4],
+                                         float *s_ring, float vs) {
     if (MODE == 3) {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (cx.inter[u]) h.stack_out[(long long)cx.gy * h.W + cx.gx0 + u] += a[u];
+            if (w.inter[u]) h.stack_out[(long long)w.gy * h.W + cx.gx0 + u] += a[u];
     } else if (!LOG && L == 0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -1034,21 +1146,21 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
         } else if (MODE == 2) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (cx.inter[u]) {
+                if (w.inter[u]) {
                     const float z = fminf(fmaxf((d[u] - h.soft_tau) * h.soft_inv_t, -80.0f), 80.0f);
-                    st.soft[I] += __fdividef(1.0f, 1.0f + __expf(-z));
+                    soft[I] += __fdividef(1.0f, 1.0f + __expf(-z));
                 }
         } else {
             const float ninf = -__int_as_float(0x7f800000);
             float4 o;
-            o.x = cx.inb[0] ? d[0] : ninf;
-            o.y = cx.inb[1] ? d[1] : ninf;
-            o.z = cx.inb[2] ? d[2] : ninf;
-            o.w = cx.inb[3] ? d[3] : ninf;
-            reinterpret_cast<float4 *>(s_ring + (cx.slot * NDOG + I) * TX2)[cx.q] = o;
+            o.x = w.inb[0] ? d[0] : ninf;
+            o.y = w.inb[1] ? d[1] : ninf;
+            o.z = w.inb[2] ? d[2] : ninf;
+            o.w = w.inb[3] ? d[3] : ninf;
+            reinterpret_cast<float4 *>(s_ring + (w.slot * NDOG + I) * TX2)[cx.q] = o;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (!cx.inb[u]) continue;
+                if (!w.inb[u]) continue;
                 if (I > 0 && d[u] > st.dp[u]) st.mk[u] &= ~(LMask(1) << (I > 0 ? I - 1 : 0));
                 if (d[u] > h.thr && (I == 0 || !(st.dp[u] > d[u]))) st.mk[u] |= LMask(1) << I;
                 st.dp[u] = d[u];
@@ -1057,20 +1169,29 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vrow, 
         if (STORE) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (cx.inter[u])
-                    h.stack_out[(long long)I * h.plane + (long long)cx.gy * h.W + cx.gx0 + u] =
-                        d[u];
+                if (w.inter[u])
+                    h.stack_out[(long long)I * h.plane + (long long)w.gy * h.W + cx.gx0 + u] = d[u];
         }
     }
 }
 
+template <int L>
+__device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vbase, const HCtx &cx,
+                                       HState &st, float *s_ring, float vs) {
+    float a[HR][4];
+    hsums<L>(vbase, cx.q, a);
+#pragma unroll
+    for (int rr = 0; rr < HR; ++rr)
+        hrespond<L>(h, cx, cx.rw[rr], st.rw[rr], st.soft, a[rr], s_ring, vs);
+}
+
 template <int L, int LE>
 struct HLevels {
-    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *vrow,
+    static __device__ __forceinline__ void run(const MhfdKHeader &h, const float *vbase,
                                                const HCtx &cx, HState &st, float *s_ring,
                                                float vs) {
-        hlevel<L>(h, vrow, cx, st, s_ring, vs);
-        HLevels<L + 1, LE>::run(h, vrow, cx, st, s_ring, vs);
+        hlevel<L>(h, vbase, cx, st, s_ring, vs);
+        HLevels<L + 1, LE>::run(h, vbase, cx, st, s_ring, vs);
     }
 };
 template <int LE>
@@ -1090,18 +1211,23 @@ __device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, const March &m, i
     HCtx cx;
     const int j = item / NQ4;
     cx.q = item - j * NQ4;
-    cx.r = s * RB + j;
-    cx.slot = cx.r % RING;
-    cx.gy = m.yb + cx.r;
+    cx.j0 = HR * j;
     cx.gx0 = m.x0 - 1 + 4 * cx.q;
-    const bool rowin = cx.gy >= 0 && cx.gy < h.H;
-    const bool rowint = rowin && cx.r >= 1 && cx.r <= m.Y;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int gx = cx.gx0 + u;
-        const int c = 4 * cx.q + u;
-        cx.inb[u] = rowin && gx >= 0 && gx < h.W;
-        cx.inter[u] = rowint && c >= 1 && c <= TX2 - 2 && gx < h.W;
+    for (int rr = 0; rr < HR; ++rr) {
+        HRowCtx &w = cx.rw[rr];
+        w.r = s * RB + cx.j0 + rr;
+        w.slot = w.r % RING;
+        w.gy = m.yb + w.r;
+        const bool rowin = w.gy >= 0 && w.gy < h.H;
+        const bool rowint = rowin && w.r >= 1 && w.r <= m.Y;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int gx = cx.gx0 + u;
+            const int c = 4 * cx.q + u;
+            w.inb[u] = rowin && gx >= 0 && gx < h.W;
+            w.inter[u] = rowint && c >= 1 && c <= TX2 - 2 && gx < h.W;
+        }
     }
     return cx;
 }
@@ -1115,36 +1241,41 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
         const int item = threadIdx.x < NTW ? threadIdx.x + it * NTW : HITEMS;
         if (item < HITEMS) {
             const HCtx cx = make_ctx(h, m, item, s);
-            const float *vrow = s_v + (cx.r - s * RB) * VROW;
-            HLevels<kGB(G), kGB(G + 1)>::run(h, vrow, cx, hs[it], s_ring, vs);
-            if (G == NGROUPS - 1 && MODE == 0) {
-                const float ninf = -__int_as_float(0x7f800000);
-                float4 o;
-                o.x = cx.inb[0] ? hs[it].m[0] : ninf;
-                o.y = cx.inb[1] ? hs[it].m[1] : ninf;
-                o.z = cx.inb[2] ? hs[it].m[2] : ninf;
-                o.w = cx.inb[3] ? hs[it].m[3] : ninf;
-                reinterpret_cast<float4 *>(s_ring + cx.slot * TX2)[cx.q] = o;
-                uchar4 ab;
-                ab.x = (unsigned char)hs[it].a[0];
-                ab.y = (unsigned char)hs[it].a[1];
-                ab.z = (unsigned char)hs[it].a[2];
-                ab.w = (unsigned char)hs[it].a[3];
-                reinterpret_cast<uchar4 *>(s_arg + cx.slot * TX2)[cx.q] = ab;
-                if (STORE) {
+            const float *vbase = s_v + vidx(cx.j0, 0);
+            HLevels<kGB(G), kGB(G + 1)>::run(h, vbase, cx, hs[it], s_ring, vs);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (cx.inter[u]) {
-                            const long long o2 = (long long)cx.gy * h.W + cx.gx0 + u;
-                            if (h.m_out) h.m_out[o2] = hs[it].m[u];
-                            if (h.arg_out) h.arg_out[o2] = hs[it].a[u];
-                        }
+            for (int rr = 0; rr < HR; ++rr) {
+                const HRowCtx &w = cx.rw[rr];
+                const HRowState &st = hs[it].rw[rr];
+                if (G == NGROUPS - 1 && MODE == 0) {
+                    const float ninf = -__int_as_float(0x7f800000);
+                    float4 o;
+                    o.x = w.inb[0] ? st.m[0] : ninf;
+                    o.y = w.inb[1] ? st.m[1] : ninf;
+                    o.z = w.inb[2] ? st.m[2] : ninf;
+                    o.w = w.inb[3] ? st.m[3] : ninf;
+                    reinterpret_cast<float4 *>(s_ring + w.slot * TX2)[cx.q] = o;
+                    uchar4 ab;
+                    ab.x = (unsigned char)st.a[0];
+                    ab.y = (unsigned char)st.a[1];
+                    ab.z = (unsigned char)st.a[2];
+                    ab.w = (unsigned char)st.a[3];
+                    reinterpret_cast<uchar4 *>(s_arg + w.slot * TX2)[cx.q] = ab;
+                    if (STORE) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (w.inter[u]) {
+                                const long long o2 = (long long)w.gy * h.W + cx.gx0 + u;
+                                if (h.m_out) h.m_out[o2] = st.m[u];
+                                if (h.arg_out) h.arg_out[o2] = st.a[u];
+                            }
+                    }
                 }
-            }
-            if (G == NGROUPS - 1 && MODE == 1) {
-                LMask *mrow = reinterpret_cast<LMask *>(s_arg) + cx.slot * TX2 + 4 * cx.q;
+                if (G == NGROUPS - 1 && MODE == 1) {
+                    LMask *mrow = reinterpret_cast<LMask *>(s_arg) + w.slot * TX2 + 4 * cx.q;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) mrow[u] = hs[it].mk[u];
+                    for (int u = 0; u < 4; ++u) mrow[u] = st.mk[u];
+                }
             }
         }
     }

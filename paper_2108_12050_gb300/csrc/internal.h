@@ -69,7 +69,10 @@ struct TileConfig {
     int tx2, ty2, rb, nt;
     std::vector<int> gb;   // level-group boundaries
     int tc = 0;            // 1: vertical pass on the tensor cores (tcgen05)
+    int hr = 1;            // rows per horizontal item: 1, or 2 (packed FMAs over row pairs)
 };
+// horizontal items of one step of a shape
+inline int h_items(const TileConfig &c) { return (c.rb / c.hr) * (c.tx2 / 4); }
 
 struct Variant {
     std::string key;

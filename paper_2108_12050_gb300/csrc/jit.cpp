@@ -88,6 +88,7 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_TY2 " << c.ty2 << "\n"
       << "#define MHFD_BROWS " << brows_for(R, smode, c) << "\n"
       << "#define MHFD_RB " << c.rb << "\n"
+      << "#define MHFD_HR " << ((mode & 3) <= 1 ? c.hr : 1) << "\n"
       << "#define MHFD_VTC " << c.tc << "\n"
       << "#define MHFD_NT " << c.nt << "\n"
       << "#define MHFD_MODE " << mode << "\n"
@@ -335,7 +336,8 @@ bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::
     if (!tc_mode_ok(mode)) return no("the tensor-core pass takes the DoG detection modes only");
     if (c.rb != 4 && c.rb != 8) return no("the tensor-core pass takes four or eight rows per step");
     if (c.nt % 32 || c.nt < 128 || c.nt > 1024) return no("threads: whole warps, at least one warpgroup");
-    if (c.rb * (c.tx2 / 4) > 2 * c.nt) return no("more than two row quads per thread");
+    if (c.hr != 1 && c.hr != 2) return no("one or two rows per horizontal item");
+    if (h_items(c) > 2 * c.nt) return no("more than two horizontal items per thread");
     if (c.gb.size() - 1 > 12) return no("at most 12 level groups");
     if (tc_tmem_cols(R, mode, c) > 512) return no("tensor memory holds 512 columns");
     if (brows_for(R, mode, c) < tc_min_rows(R, mode, c) ||
@@ -350,25 +352,30 @@ std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode) {
     const int nl = (int)R.size();
     const int widths[] = {96, 128, 192, 224, 256, 288, 320, 352, 384, 448, 480, 512};
     const int threads[] = {128, 160, 192, 224, 256, 288, 384, 416, 512};
-    // four rows per step (eight rows run, through tile_shape, at about twice
-    // the time on GB300: two items a thread on two warps per scheduler)
-    for (int rb : {4})
-    for (int tx2 : widths)
-        for (int nt : threads) {
-            const int items = rb * (tx2 / 4);
-            if (items > 2 * nt || items <= nt - 128) continue;  // 1..2 items a thread, no idle warpgroup
-            for (int ng = 1; ng <= 6 && ng <= nl; ++ng) {
-                TileConfig c;
-                c.tx2 = tx2;
-                c.ty2 = 2 + 16;
-                c.rb = rb;
-                c.nt = nt;
-                c.gb.assign(ng + 1, 0);
-                for (int g = 0; g <= ng; ++g) c.gb[g] = (int)((long long)nl * g / ng);
-                c.tc = 1;
-                if (tc_shape_ok(R, mode, c, nullptr)) out.push_back(c);
+    // four rows per step on one-row items (eight rows of one-row items ran
+    // at about twice the time on GB300: two items a thread on two warps per
+    // scheduler); four or eight rows on two-row items (packed FMAs)
+    for (int hr : {1, 2})
+    for (int rb : {4, 8}) {
+        if (hr == 1 && rb == 8) continue;
+        for (int tx2 : widths)
+            for (int nt : threads) {
+                const int items = (rb / hr) * (tx2 / 4);
+                if (items > 2 * nt || items <= nt - 128) continue;  // 1..2 items a thread, no idle warpgroup
+                for (int ng = 1; ng <= 6 && ng <= nl; ++ng) {
+                    TileConfig c;
+                    c.tx2 = tx2;
+                    c.ty2 = 2 + 16;
+                    c.rb = rb;
+                    c.nt = nt;
+                    c.hr = hr;
+                    c.gb.assign(ng + 1, 0);
+                    for (int g = 0; g <= ng; ++g) c.gb[g] = (int)((long long)nl * g / ng);
+                    c.tc = 1;
+                    if (tc_shape_ok(R, mode, c, nullptr)) out.push_back(c);
+                }
             }
-        }
+    }
     return out;
 }
 
@@ -415,7 +422,7 @@ bool choose_tile_tc(const std::vector<int> &R, int mode, TileConfig *cfg, std::s
     bool found = false;
     TileConfig comp;
     for (const TileConfig &c : menu) {
-        if (c.rb != 4 || c.tx2 != c.nt - 32 || c.nt * 168 > 65536 ||
+        if (c.rb != 4 || c.hr != 1 || c.tx2 != c.nt - 32 || c.nt * 168 > 65536 ||
             !companion_tile(R, mode, c, &comp))
             continue;
         if (!found || c.tx2 > cfg->tx2 ||

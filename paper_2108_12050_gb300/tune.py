@@ -42,7 +42,8 @@ def load_table():
 
 
 def lookup(n, t_min, t_max, nms, sms, truncate=4.0, response="dog", tensor_cores=False):
-    """Tuned tile shape (the five-field tile_shape of the parameters) for this
+    """Tuned tile shape (the six-field tile_shape of the parameters; a five-field
+    entry means one row per horizontal item) for this
     ladder, response, kernel kind and SM count, or None (the built-in choice
     is used)."""
     ent = load_table().get(ladder_key(n, t_min, t_max, nms, truncate, response, tensor_cores))
@@ -52,9 +53,9 @@ def lookup(n, t_min, t_max, nms, sms, truncate=4.0, response="dog", tensor_cores
     if not best:
         return None
     shape = best.get("shape")
-    if not shape or len(shape) != 5:
+    if not shape or len(shape) not in (5, 6):
         return None
-    return [int(v) for v in shape]
+    return [int(v) for v in shape] + ([1] if len(shape) == 5 else [])
 
 
 def _rmax(n, t_min, t_max, truncate=4.0):
@@ -71,17 +72,17 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0, response="dog"):
                                 tensor_cores=False)
     rmax = _rmax(n, t_min, t_max) + (0 if response in ("dog", 0) else 1)
     seen, out = set(), []
-    for (tx2, ty2, rb, nt, ng) in menu:
+    for (tx2, ty2, rb, nt, ng, hr) in menu:
         if tx2 < min_width:
             continue
         wext = tx2 + 2 * rmax
-        hitems = rb * tx2 // 4
+        hitems = (rb // hr) * tx2 // 4
         if hitems > nt or hitems < 0.85 * nt:
             continue
         vutil = wext / (nt * -(-wext // nt))
         if vutil < 0.75:
             continue
-        key = (tx2, ty2, rb, nt, ng)
+        key = (tx2, ty2, rb, nt, ng, hr)
         if key in seen:
             continue
         seen.add(key)
@@ -90,7 +91,7 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0, response="dog"):
 
 
 def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), groups=(2, 3, 4, 5),
-                     response="dog"):
+                     response="dog", hrs=(1,)):
     """FFMA-kernel shapes off the menu's width grid (strip widths fitted to
     an image width).  Thread counts: at least one per horizontal item and one per
     halo'd column of the vertical pass (a single round), that count plus one
@@ -99,16 +100,16 @@ def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), group
     from . import _native
     rmax = _rmax(n, t_min, t_max) + (0 if response in ("dog", 0) else 1)
     out = []
-    for tx2 in widths:
+    for tx2, rb, hr in [(w, r, h) for w in widths for r in rbs for h in hrs if r % h == 0]:
         ncol = -(-(tx2 + 2 * rmax) // 32) * 32
-        for rb in rbs:
-            hitems = rb * tx2 // 4
+        if True:
+            hitems = (rb // hr) * tx2 // 4
             base = max(-(-hitems // 32) * 32, ncol)
             for nt in sorted({base, base + 32, -(-base // 128) * 128}):
                 if nt > 1024:
                     continue
                 for ng in groups:
-                    shape = (tx2, 18, rb, nt, ng)
+                    shape = (tx2, 18, rb, nt, ng, hr)
                     try:
                         _native.chosen_tile(n=n, t_min=t_min, t_max=t_max, nms=nms,
                                             tile_shape=shape, response=response,
@@ -175,6 +176,7 @@ def main():
     ap.add_argument("--widths", default="", help="extra strip widths off the menu, e.g. 312,344")
     ap.add_argument("--rbs", default="2,3,4,5,6,8", help="rows per step of the extra shapes")
     ap.add_argument("--groups", default="2,3,4,5", help="level groups of the extra shapes")
+    ap.add_argument("--hrs", default="1", help="rows per horizontal item of the extra shapes")
     ap.add_argument("--response", default="dog", choices=["dog", "log"])
     ap.add_argument("--tensor-cores", action="store_true",
                     help="tune the tensor-core kernel (its own shape menu)")
@@ -197,7 +199,8 @@ def main():
                                  [int(w) for w in args.widths.split(",")],
                                  rbs=[int(v) for v in args.rbs.split(",")],
                                  groups=[int(v) for v in args.groups.split(",")],
-                                 response=args.response)
+                                 response=args.response,
+                                 hrs=[int(v) for v in args.hrs.split(",")])
         cands += [c for c in extra if c not in cands]
     t0 = time.time()
     comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands, response=args.response,

@@ -79,8 +79,9 @@ def test_tile_menu_fits_shared_memory(native):
         kw["tensor_cores"] = False
         menu = native.tile_configs(**kw)
         assert len(menu) > 10
-        for tx2, ty2, rb, nt, ng in menu:
+        for tx2, ty2, rb, nt, ng, hr in menu:
             assert tx2 % 4 == 0 and ty2 >= 3 and rb >= 2 and nt % 32 == 0 and ng >= 1
+            assert hr in (1, 2) and rb % hr == 0
         chosen = native.chosen_tile(**kw)
         assert chosen in menu
 
@@ -95,14 +96,17 @@ def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
 
 def test_tensor_core_tile_menu(native):
     """The tensor-core kernel's shapes: four or eight rows per step, whole
-    warps, at least one warpgroup, one or two horizontal items per thread;
+    warps, at least one warpgroup, one or two horizontal items per thread
+    (one-row items at four rows per step, two-row items at four or eight);
     the built-in choice (four rows) leaves exactly one warp free of
     horizontal items (the MMA issuer) and is on the menu."""
     for kw in (dict(n=10, t_min=1, t_max=10), dict(n=16, t_min=1, t_max=12)):
         menu = native.tile_configs(tensor_cores=True, **kw)
         assert len(menu) > 10
-        for tx2, ty2, rb, nt, ng in menu:
-            assert rb in (4, 8) and nt % 32 == 0 and nt >= 128 and rb * tx2 // 4 <= 2 * nt
+        for tx2, ty2, rb, nt, ng, hr in menu:
+            assert rb in (4, 8) and nt % 32 == 0 and nt >= 128
+            assert (rb // hr) * tx2 // 4 <= 2 * nt and (hr == 2 or rb == 4)
+        assert any(s[5] == 2 and s[2] == 8 for s in menu)
         chosen = native.chosen_tile(tensor_cores=True, **kw)
         assert chosen in menu and chosen[0] == chosen[3] - 32
     # the LoG response has tensor-core shapes of its own; the 26-neighbour
@@ -116,25 +120,31 @@ def test_tensor_core_tile_menu(native):
 
 def test_explicit_tensor_core_tile_shape(native):
     kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=True)
-    assert native.chosen_tile(tile_shape=(352, 18, 4, 384, 3), **kw) == (352, 18, 4, 384, 3)
-    # rows per step other than 4 or 8, threads below a warpgroup: unsupported
-    for bad in ((352, 18, 6, 384, 3), (96, 18, 4, 96, 1)):
+    assert native.chosen_tile(tile_shape=(352, 18, 4, 384, 3), **kw) == (352, 18, 4, 384, 3, 1)
+    assert native.chosen_tile(tile_shape=(256, 18, 8, 288, 4, 2), **kw) == (256, 18, 8, 288, 4, 2)
+    # rows per step other than 4 or 8, threads below a warpgroup, eight rows
+    # of two-row items at a width whose accumulators exceed tensor memory:
+    # unsupported
+    for bad in ((352, 18, 6, 384, 3), (96, 18, 4, 96, 1), (352, 18, 8, 384, 3, 2)):
         with pytest.raises(native.MhfdError) as e:
             native.chosen_tile(tile_shape=bad, **kw)
         assert e.value.code == -2, bad
-    with pytest.raises(native.MhfdError) as e:
-        native.chosen_tile(tile_shape=(350, 18, 4, 384, 3), **kw)
-    assert e.value.code == -1
+    # width not a multiple of 4, rows per item not 1 or 2
+    for bad in ((350, 18, 4, 384, 3), (352, 18, 4, 384, 3, 3)):
+        with pytest.raises(native.MhfdError) as e:
+            native.chosen_tile(tile_shape=bad, **kw)
+        assert e.value.code == -1, bad
 
 
 def test_explicit_tile_shape(native):
     kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=False)
-    assert native.chosen_tile(tile_shape=(320, 18, 4, 448, 3), **kw) == (320, 18, 4, 448, 3)
+    assert native.chosen_tile(tile_shape=(320, 18, 4, 448, 3), **kw) == (320, 18, 4, 448, 3, 1)
+    assert native.chosen_tile(tile_shape=(320, 18, 4, 448, 3, 2), **kw) == (320, 18, 4, 448, 3, 2)
     # out of range: width not a multiple of 4, threads not a multiple of 32,
-    # too few rows per step, more groups than levels, more than two row
-    # quads per thread
+    # too few rows per step, more groups than levels, more than two
+    # horizontal items per thread, two-row items on an odd number of rows
     for bad in ((322, 18, 4, 448, 3), (320, 18, 4, 450, 3), (320, 18, 1, 448, 3),
-                (320, 18, 4, 448, 18), (320, 18, 8, 128, 3)):
+                (320, 18, 4, 448, 18), (320, 18, 8, 128, 3), (320, 18, 5, 448, 3, 2)):
         with pytest.raises(native.MhfdError) as e:
             native.chosen_tile(tile_shape=bad, **kw)
         assert e.value.code == -1, bad
@@ -148,7 +158,7 @@ def test_heuristic_tile_is_one_vertical_round(native):
     import math
     for kw in (dict(n=16, t_min=1.0, t_max=12.0), dict(n=10, t_min=1.0, t_max=10.0),
                dict(n=4, t_min=1.0, t_max=4.0)):
-        tx2, ty2, rb, nt, ng = native.chosen_tile(tensor_cores=False, **kw)
+        tx2, ty2, rb, nt, ng, hr = native.chosen_tile(tensor_cores=False, **kw)
         dt = (kw["t_max"] - kw["t_min"]) / kw["n"]
         rmax = max(math.ceil(4 * (kw["t_min"] + i * dt)) for i in range(kw["n"] + 1))
         assert nt >= tx2 + 2 * rmax and rb * tx2 // 4 <= nt
@@ -170,7 +180,7 @@ def test_tuned_shapes_are_valid_for_their_ladders(native):
                   tensor_cores=m.group(6) is not None)
         for best in ent.values():
             shape = tuple(best["shape"])
-            assert native.chosen_tile(tile_shape=shape, **kw) == shape
+            assert native.chosen_tile(tile_shape=shape, **kw) == shape + (1,) * (6 - len(shape))
 
 
 def test_kernel_layout_matches_host_shared_memory_estimate(native, tmp_path, monkeypatch):
@@ -194,6 +204,14 @@ def test_kernel_layout_matches_host_shared_memory_estimate(native, tmp_path, mon
     menu = native.tile_configs(**full)
     for shape in (menu[0], menu[-1]):
         cases.append((dict(tile_shape=shape, **full), 0))
+    # two-row horizontal items: tensor-core and FFMA kernels, DoG and LoG,
+    # the detection and the stack-storing variants
+    cases += [(dict(tile_shape=(256, 18, 8, 288, 4, 2), **full), 0),
+              (dict(tile_shape=(256, 18, 8, 288, 4, 2), **full), 1),
+              (dict(tile_shape=(320, 18, 4, 448, 3, 2), n=16, t_min=1.0, t_max=12.0,
+                    tensor_cores=False), 0),
+              (dict(tile_shape=(96, 18, 4, 160, 1, 2), tensor_cores=True, response="log",
+                    **small), 0)]
     import concurrent.futures as cf
     import multiprocessing as mp
     with cf.ProcessPoolExecutor(max_workers=min(len(cases), os.cpu_count() or 1),

@@ -418,3 +418,41 @@ def test_soft_score_rejects_the_log_response():
     with pytest.raises(mhfd.MhfdError) as e:
         soft.soft_score(det, to_dev(a.astype(np.float32)), torch.ones(4), 0.1)
     assert e.value.code == -2
+
+
+# ------------------------------------------- two-row horizontal items (packed)
+
+@pytest.mark.parametrize("shape,tc", [((256, 18, 8, 288, 4, 2), True),
+                                      ((284, 18, 8, 320, 4, 2), True),
+                                      ((320, 18, 4, 448, 3, 2), False)],
+                         ids=["tc-256x8", "tc-284x8", "ffma-320x4"])
+def test_two_row_items_match_oracle(shape, tc):
+    """Shapes whose horizontal items cover two rows (packed two-lane FMAs
+    over the row pair) on the benchmark ladder: the response stack within
+    the tolerance and the detection under the parity rules."""
+    img = scene(81, 300, 620, "u16")
+    n, tmin, tmax = 16, 1.0, 12.0
+    det = detector(n=n, t_min=tmin, t_max=tmax, threshold=0.05, tile_shape=list(shape),
+                   tensor_cores=tc, keep_candidates=True)
+    assert det.uses_tensor_cores == tc
+    D, _, _, _ = det.debug_stack(to_dev(img), want=("D",))
+    ref, D_ref, tol, t, _ = oracle_reference(img, n, tmin, tmax, 0.05, 0.5)
+    assert_stack_close(D.cpu().numpy(), D_ref, str(shape))
+    res = det(to_dev(img))
+    check_detection(res, ref, D_ref, tol, 0.05, 0.5, "paper", t)
+
+
+@pytest.mark.parametrize("response", ["dog", "log"])
+def test_two_row_items_sum_like_one_row_items(response):
+    """The packed two-row pass takes each lane's taps in the order of the
+    one-row pass, so with the same geometry the FFMA kernel's stack is
+    bit-identical."""
+    img = scene(82, 200, 500, "u16")
+    thr = 0.05 if response == "dog" else 0.05 / 0.6875
+    kw = dict(n=16, t_min=1.0, t_max=12.0, threshold=thr, tensor_cores=False, response=response)
+    one = detector(tile_shape=[320, 18, 4, 448, 4, 1], **kw)
+    two = detector(tile_shape=[320, 18, 4, 448, 4, 2], **kw)
+    D1, M1, A1, r1 = one.debug_stack(to_dev(img))
+    D2, M2, A2, r2 = two.debug_stack(to_dev(img))
+    assert torch.equal(D1, D2) and torch.equal(M1, M2) and torch.equal(A1, A2)
+    assert np.array_equal(r1.blobs, r2.blobs)

@@ -30,9 +30,9 @@ def test_lookup_by_sm_count_with_fallback(tune, tmp_path, monkeypatch):
     path = tmp_path / "tuned.json"
     path.write_text(json.dumps(table))
     monkeypatch.setattr(tune, "TABLE", str(path))
-    assert tune.lookup(16, 1.0, 12.0, 0, 152, tensor_cores=True) == [352, 18, 4, 384, 3]
-    assert tune.lookup(16, 1.0, 12.0, 0, 132, tensor_cores=True) == [320, 18, 4, 352, 3]
-    assert tune.lookup(16, 1.0, 12.0, 0, 148) == [288, 18, 4, 384, 3]
+    assert tune.lookup(16, 1.0, 12.0, 0, 152, tensor_cores=True) == [352, 18, 4, 384, 3, 1]
+    assert tune.lookup(16, 1.0, 12.0, 0, 132, tensor_cores=True) == [320, 18, 4, 352, 3, 1]
+    assert tune.lookup(16, 1.0, 12.0, 0, 148) == [288, 18, 4, 384, 3, 1]
     assert tune.lookup(16, 1.0, 12.0, 0, 152) is None            # no entry, no fallback
     assert tune.lookup(16, 1.0, 12.0, 1, 152) is None            # other rule
     assert tune.lookup(4, 1.0, 4.0, 0, 152) is None
@@ -47,16 +47,17 @@ def test_ffma_candidates_are_balanced_shapes_of_the_ffma_menu(tune):
                                         **kw))
         cands = tune.candidates(16, 1.0, 12.0, 0, **kw)
         assert cands and len(set(cands)) == len(cands)
-        for tx2, ty2, rb, nt, ng in cands:
-            assert (tx2, ty2, rb, nt, ng) in menu
-            assert 0.85 * nt <= rb * tx2 // 4 <= nt
+        for tx2, ty2, rb, nt, ng, hr in cands:
+            assert (tx2, ty2, rb, nt, ng, hr) in menu
+            assert 0.85 * nt <= (rb // hr) * tx2 // 4 <= nt
 
 
 def test_width_candidates_fit_the_ffma_kernel(tune):
     from paper_2108_12050_gb300 import _native
-    shapes = tune.width_candidates(16, 1.0, 12.0, 0, [312, 344], rbs=(2, 4), groups=(3,))
-    assert shapes and {s[0] for s in shapes} == {312, 344}
+    shapes = tune.width_candidates(16, 1.0, 12.0, 0, [312, 344], rbs=(2, 4), groups=(3,),
+                                   hrs=(1, 2))
+    assert shapes and {s[0] for s in shapes} == {312, 344} and {s[5] for s in shapes} == {1, 2}
     for s in shapes:
-        assert s[3] % 32 == 0 and s[2] * s[0] // 4 <= s[3]
+        assert s[3] % 32 == 0 and (s[2] // s[5]) * s[0] // 4 <= s[3]
         assert _native.chosen_tile(n=16, t_min=1.0, t_max=12.0, nms=0, tile_shape=s,
                                    tensor_cores=False) == s
