@@ -251,6 +251,10 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0, metavar="R",
                     help="only run R detections of the sigma_d=0 tile (for ncu captures)")
     ap.add_argument("--plain", action="store_true", help="with --profile-case: plain path")
+    ap.add_argument("--profile-nms", default="paper", choices=["paper", "local26"],
+                    help="with --profile-case: the maximum rule")
+    ap.add_argument("--profile-shape", default="",
+                    help="with --profile-case: tile shape, e.g. 284,18,8,320,4,2")
     ap.add_argument("--side", type=int, default=H, help="with --profile-case: crop side")
     args = ap.parse_args()
     if args.profile_case:
@@ -829,7 +833,9 @@ def profile_case(args):
     torch.cuda.set_device(0)
     img = synth.sweep_tile_4096_u16(0.0)[:args.side, :args.side].copy()
     dev = torch.from_numpy(img.view(np.int16)).cuda()
-    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP, nms="paper")
+    shape = [int(v) for v in args.profile_shape.split(",")] if args.profile_shape else None
+    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP,
+                        nms=args.profile_nms, tile_shape=shape)
     for _ in range(args.profile_case):
         if args.plain:
             det.detect_plain(dev)

@@ -185,11 +185,17 @@ MK_HD constexpr int vrow_max() {
 }
 constexpr int NTAPS = tapoff(NL);
 constexpr int VROW = vrow_max();
-// shared-memory index of V row position `col` (voff(l) + column, plus
-// extp(l) for the LoG's second row) of step row j: row after row, or row
-// pairs interleaved column by column for two-row items
-MK_HD constexpr int vidx(int j, int col) {
-    return HR == 1 ? j * VROW + col : (j >> 1) * 2 * VROW + 2 * col + (j & 1);
+// Shared-memory index of column cc of the V row `part` (1: the LoG's
+// second row) of level L at step row j.  One-row items: rows one after
+// another.  Two-row items: a row pair holds, per level and part, a float2
+// (both rows) per column, the columns ordered by their residue mod 4 -
+// column cc at (cc mod 4) * extp(L) / 4 + cc / 4 - so that the loads of
+// one window column by the warp's items (columns 4q + M, q = item) are
+// contiguous.
+MK_HD constexpr int vidx(int L, int part, int j, int cc) {
+    return HR == 1 ? j * VROW + voff(L) + part * extp(L) + cc
+                   : (j >> 1) * 2 * VROW + 2 * (voff(L) + part * extp(L)) +
+                         2 * ((cc & 3) * (extp(L) >> 2) + (cc >> 2)) + (j & 1);
 }
 
 // Tensor-core vertical pass geometry.  The window holds the centred integer
@@ -756,15 +762,14 @@ __device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (
             // the LoG's g'' (*)_y I row beside them
 #pragma unroll
             for (int pt = 0; pt < TC_P; ++pt) {
-                const int col = voff(L) + pt * extp(L) + cc;
                 if constexpr (HR == 2) {
 #pragma unroll
                     for (int j = 0; j < RB; j += 2)
-                        *reinterpret_cast<float2 *>(s_v + vidx(j, col)) = make_float2(
+                        *reinterpret_cast<float2 *>(s_v + vidx(L, pt, j, cc)) = make_float2(
                             __uint_as_float(r[LI][pt * RB + j]), __uint_as_float(r[LI][pt * RB + j + 1]));
                 } else {
 #pragma unroll
-                    for (int j = 0; j < RB; ++j) s_v[vidx(j, col)] = __uint_as_float(r[LI][pt * RB + j]);
+                    for (int j = 0; j < RB; ++j) s_v[vidx(L, pt, j, cc)] = __uint_as_float(r[LI][pt * RB + j]);
                 }
             }
         }
@@ -856,21 +861,20 @@ __device__ __forceinline__ void vcol(const float *__restrict__ win, float *__res
     for (int l = 0; l < NG; ++l) {
         const int cc = c - (RMAX - kRH(LB + l));
         if (cc >= 0 && cc < TX2 + 2 * kRH(LB + l)) {
-            const int col = voff(LB + l) + cc;
             if constexpr (HR == 2 && ROWS % 2 == 0) {
 #pragma unroll
                 for (int j = 0; j < ROWS; j += 2) {
-                    *reinterpret_cast<float2 *>(s_v + vidx(o0 + j, col)) =
+                    *reinterpret_cast<float2 *>(s_v + vidx(LB + l, 0, o0 + j, cc)) =
                         make_float2(acc[j][l], acc[j + 1][l]);
                     if constexpr (LOG)
-                        *reinterpret_cast<float2 *>(s_v + vidx(o0 + j, col + extp(LB + l))) =
+                        *reinterpret_cast<float2 *>(s_v + vidx(LB + l, 1, o0 + j, cc)) =
                             make_float2(acc2[j][l], acc2[j + 1][l]);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < ROWS; ++j) {
-                    s_v[vidx(o0 + j, col)] = acc[j][l];
-                    if constexpr (LOG) s_v[vidx(o0 + j, col + extp(LB + l))] = acc2[j][l];
+                    s_v[vidx(LB + l, 0, o0 + j, cc)] = acc[j][l];
+                    if constexpr (LOG) s_v[vidx(LB + l, 1, o0 + j, cc)] = acc2[j][l];
                 }
             }
         }
@@ -1025,22 +1029,22 @@ __device__ __forceinline__ void hacc2(float2 v, float2 (&a)[4]) {
 }
 // Columns in the order of the one-row pass (quads of four columns
 // descending, columns ascending within a quad), so that each lane sums
-// exactly as the one-row pass does; a quad is two float4 loads of the
-// pair-interleaved rows (two columns each).
-template <int R, int TO, int Q, int OFF, bool T2>
+// exactly as the one-row pass does.  `w` points at the item's column 4q of
+// the level row in the residue-ordered pair layout (S = extp / 4 entries
+// per residue class): window column M of the item is w[(M % 4) S + M / 4].
+template <int R, int TO, int Q, int OFF, bool T2, int S>
 struct HQuads2 {
-    static __device__ __forceinline__ void run(const float4 *w, float2 (&a)[4]) {
-        const float4 v0 = w[2 * Q], v1 = w[2 * Q + 1];
-        hacc2<R, TO, 4 * Q + 0, OFF, T2>(make_float2(v0.x, v0.y), a);
-        hacc2<R, TO, 4 * Q + 1, OFF, T2>(make_float2(v0.z, v0.w), a);
-        hacc2<R, TO, 4 * Q + 2, OFF, T2>(make_float2(v1.x, v1.y), a);
-        hacc2<R, TO, 4 * Q + 3, OFF, T2>(make_float2(v1.z, v1.w), a);
-        HQuads2<R, TO, Q - 1, OFF, T2>::run(w, a);
+    static __device__ __forceinline__ void run(const float2 *w, float2 (&a)[4]) {
+        hacc2<R, TO, 4 * Q + 0, OFF, T2>(w[0 * S + Q], a);
+        hacc2<R, TO, 4 * Q + 1, OFF, T2>(w[1 * S + Q], a);
+        hacc2<R, TO, 4 * Q + 2, OFF, T2>(w[2 * S + Q], a);
+        hacc2<R, TO, 4 * Q + 3, OFF, T2>(w[3 * S + Q], a);
+        HQuads2<R, TO, Q - 1, OFF, T2, S>::run(w, a);
     }
 };
-template <int R, int TO, int OFF, bool T2>
-struct HQuads2<R, TO, -1, OFF, T2> {
-    static __device__ __forceinline__ void run(const float4 *, float2 (&)[4]) {}
+template <int R, int TO, int OFF, bool T2, int S>
+struct HQuads2<R, TO, -1, OFF, T2, S> {
+    static __device__ __forceinline__ void run(const float2 *, float2 (&)[4]) {}
 };
 
 // The horizontal sums of level L for the item's outputs: a[rr][u] for row rr.
@@ -1052,15 +1056,16 @@ __device__ __forceinline__ void hsums(const float *vbase, int q, float (&a)[HR][
         float2 p[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) p[u] = make_float2(0.0f, 0.0f);
-        const float4 *base = reinterpret_cast<const float4 *>(vbase) + 2 * q;
+        constexpr int S = extp(L) / 4;
+        const float2 *base = reinterpret_cast<const float2 *>(vbase) + q;
         if constexpr (LOG) {
             constexpr int NQA = (2 * R + 4) / 4 + 1;
             constexpr int NQB = (2 * (R + 1) + 3) / 4 + 1;
-            HQuads2<R, tapoff(L), NQA - 1, 1, false>::run(base + (voff(L) + extp(L)) / 2, p);
-            HQuads2<R + 1, tapoff2(L), NQB - 1, 0, true>::run(base + voff(L) / 2, p);
+            HQuads2<R, tapoff(L), NQA - 1, 1, false, S>::run(base + voff(L) + extp(L), p);
+            HQuads2<R + 1, tapoff2(L), NQB - 1, 0, true, S>::run(base + voff(L), p);
         } else {
             constexpr int NQ = (2 * R + 3) / 4 + 1;
-            HQuads2<R, tapoff(L), NQ - 1, 0, false>::run(base + voff(L) / 2, p);
+            HQuads2<R, tapoff(L), NQ - 1, 0, false, S>::run(base + voff(L), p);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -1241,7 +1246,7 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
         const int item = threadIdx.x < NTW ? threadIdx.x + it * NTW : HITEMS;
         if (item < HITEMS) {
             const HCtx cx = make_ctx(h, m, item, s);
-            const float *vbase = s_v + vidx(cx.j0, 0);
+            const float *vbase = s_v + (HR == 1 ? cx.j0 * VROW : (cx.j0 >> 1) * 2 * VROW);
             HLevels<kGB(G), kGB(G + 1)>::run(h, vbase, cx, hs[it], s_ring, vs);
 #pragma unroll
             for (int rr = 0; rr < HR; ++rr) {
