@@ -46,6 +46,8 @@ extern "C" {
 #define MHFD_ERR_CUDA (-4)          /* a CUDA runtime/driver call failed */
 #define MHFD_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up */
 #define MHFD_ERR_JIT (-6)           /* run-time compilation of the kernel failed */
+#define MHFD_ERR_CHECK (-7)         /* debug build (MHFD_DEBUG_CHECKS=1): a bounds check
+                                       failed; the access was skipped */
 
 typedef enum { MHFD_U8 = 0, MHFD_U16 = 1, MHFD_F32 = 2 } mhfd_dtype;
 typedef enum { MHFD_NMS_PAPER = 0, MHFD_NMS_LOCAL26 = 1 } mhfd_nms;

@@ -20,6 +20,7 @@ MHFD_ERR_OOM = -3
 MHFD_ERR_CUDA = -4
 MHFD_ERR_TIMEOUT = -5
 MHFD_ERR_JIT = -6
+MHFD_ERR_CHECK = -7
 
 U8, U16, F32 = 0, 1, 2
 NMS_PAPER, NMS_LOCAL26 = 0, 1

@@ -945,6 +945,10 @@ int mhfd_result_wait(mhfd_detector *d, mhfd_result *out) {
     for (int i = 0; i < 64; ++i) out->per_scale[i] = h.per_scale[i];
     out->lo = h.lo;
     out->hi = h.hi;
+    if (h.c.timeout & 2) {
+        out->status = MHFD_ERR_CHECK;
+        return fail(MHFD_ERR_CHECK, "a bounds check of the debug build failed in the fused kernel");
+    }
     if (h.c.timeout) {
         out->status = MHFD_ERR_TIMEOUT;
         return fail(MHFD_ERR_TIMEOUT,
@@ -1271,10 +1275,15 @@ int mhfd_result_wait_batch(mhfd_detector *d, mhfd_result *outs, int32_t n) {
         for (int i = 0; i < 64; ++i) o.per_scale[i] = h.per_scale[i];
         o.lo = h.lo;
         o.hi = h.hi;
-        o.status = h.c.timeout ? MHFD_ERR_TIMEOUT : (h.c.overflow ? MHFD_WARN_OVERFLOW : MHFD_OK);
-        if (o.status == MHFD_ERR_TIMEOUT) worst = MHFD_ERR_TIMEOUT;
+        o.status = (h.c.timeout & 2) ? MHFD_ERR_CHECK
+                   : h.c.timeout     ? MHFD_ERR_TIMEOUT
+                                     : (h.c.overflow ? MHFD_WARN_OVERFLOW : MHFD_OK);
+        if (o.status == MHFD_ERR_CHECK) worst = MHFD_ERR_CHECK;
+        if (o.status == MHFD_ERR_TIMEOUT && worst != MHFD_ERR_CHECK) worst = MHFD_ERR_TIMEOUT;
         else if (o.status == MHFD_WARN_OVERFLOW && worst == MHFD_OK) worst = MHFD_WARN_OVERFLOW;
     }
+    if (worst == MHFD_ERR_CHECK)
+        return fail(MHFD_ERR_CHECK, "a bounds check of the debug build failed in the fused kernel");
     if (worst == MHFD_ERR_TIMEOUT) return fail(MHFD_ERR_TIMEOUT, "overlap prune did not settle");
     return worst;
 }

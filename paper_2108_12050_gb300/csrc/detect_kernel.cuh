@@ -84,6 +84,22 @@ constexpr int HR = MHFD_HR;
 // ms on a 4096^2 tile), slower for the DoG kernels (1.00 -> 1.16 ms
 // tensor-core, 1.51 -> 1.60 ms FFMA)
 constexpr bool HPACK = TC && LOG && HR == 1;
+// Debug build (MHFD_CHECKS 1): the shared-memory and global indices the
+// kernel forms are checked against their buffers; a failed check sets bit 1
+// of the kernel's flag word (the host reports MHFD_ERR_CHECK) and the
+// access is skipped (a load reads 0) - no trap, the context stays usable.
+#ifndef MHFD_CHECKS
+#define MHFD_CHECKS 0
+#endif
+constexpr bool CHECKS = (MHFD_CHECKS) != 0;
+__shared__ int *mk_chk_flag;
+__device__ __forceinline__ bool mk_ok(bool cond) {
+    if constexpr (CHECKS) {
+        if (!cond && mk_chk_flag) atomicOr(mk_chk_flag, 2);
+        return cond;
+    }
+    return true;
+}
 
 // Kernel radius R_l of Gaussian level l and the level groups [GB(g), GB(g+1)).
 MK_HD constexpr int kR(int l) {
@@ -298,7 +314,7 @@ struct HState {
 // Image index of a position outside [0, n): reflect ("d c b a | a b c d |
 // d c b a", the default) or periodic (MHFD_BOUNDARY 1, the circular
 // convolution of the paper's Fourier formulation).
-__device__ __forceinline__ int reflect_idx(int i, int n) {
+__device__ __forceinline__ int reflect_idx_(int i, int n) {
     if ((unsigned)i < (unsigned)n) return i;
     if constexpr (MHFD_BOUNDARY == 1) {
         const int m = i % n;
@@ -309,6 +325,10 @@ __device__ __forceinline__ int reflect_idx(int i, int n) {
         if (m < 0) m += p;
         return m < n ? m : p - 1 - m;
     }
+}
+__device__ __forceinline__ int reflect_idx(int i, int n) {
+    const int k = reflect_idx_(i, n);
+    return mk_ok((unsigned)k < (unsigned)n) ? k : 0;
 }
 
 // ---------------------------------------------------------------- 1. load
@@ -362,7 +382,8 @@ __device__ __forceinline__ void load_rows_t(const Strip &sp, const MhfdStretch &
                                       gx);
 #pragma unroll
             for (int e = 0; e < LB; ++e)
-                if (r + e < r1) dst[(r + e - base) * WEXTP] = stretch_px<DT>(v[e], st);
+                if (r + e < r1 && mk_ok((unsigned)(r + e - base) < (unsigned)BROWS))
+                    dst[(r + e - base) * WEXTP] = stretch_px<DT>(v[e], st);
         }
     }
 }
@@ -410,7 +431,9 @@ struct Prefetch {
             const int c = threadIdx.x + k * NT;
             if (c < WEXT) {
 #pragma unroll
-                for (int e = 0; e < RB; ++e) s_in[(prow + e) * WEXTP + c] = stretch_px<DT>(v[k][e], st);
+                for (int e = 0; e < RB; ++e)
+                    if (mk_ok((unsigned)(prow + e) < (unsigned)BROWS))
+                        s_in[(prow + e) * WEXTP + c] = stretch_px<DT>(v[k][e], st);
             }
         }
     }
@@ -429,6 +452,7 @@ struct Prefetch {
 // the destination lies below the source, batches are read before written).
 __device__ __forceinline__ void shift_window(float *s_in, int from, int n) {
     constexpr int SB = 8;
+    if (!mk_ok(from >= 0 && n >= 0 && from + n <= BROWS)) return;
     for (int c = threadIdx.x; c < WEXT; c += NT) {
         float *col = s_in + c;
 #pragma unroll 1
@@ -518,6 +542,7 @@ __device__ __forceinline__ unsigned short tc_px(unsigned raw, const TcStretch &t
     return f2h_rn((float)v);
 }
 __device__ __forceinline__ void tc_put(unsigned char *win, int row, int c, unsigned short v) {
+    if (!mk_ok((unsigned)row < (unsigned)BROWS && (unsigned)c < (unsigned)TC_WT)) return;
     *reinterpret_cast<unsigned short *>(win + (c >> 3) * TC_GSTR + row * 16 + (c & 7) * 2) = v;
 }
 
@@ -553,6 +578,7 @@ __device__ __forceinline__ void tc_load_rows(const Strip &sp, const TcStretch &t
 // Move window rows [from, from + n) to [0, n): one thread per column group
 // walks its rows upwards, eight at a time (read before written).
 __device__ __forceinline__ void tc_shift(unsigned char *win, int from, int n) {
+    if (!mk_ok(from >= 0 && n >= 0 && from + n <= BROWS)) return;
     for (int cg = threadIdx.x; cg < TC_CGL; cg += NT) {
         uint4 *col = reinterpret_cast<uint4 *>(win + cg * TC_GSTR);
 #pragma unroll 1
@@ -639,13 +665,16 @@ __device__ __forceinline__ void tc_issue(const TcState &tc, int row0) {
     constexpr int NK = tc_kgp(G) / 16;
     constexpr unsigned IDESC = tc_idesc(tc_ngp(G));
     constexpr unsigned PART = 2u * tc_kgp(G) * tc_ngp(G);
+    // (a failed check issues no MMA but still commits, so the waits end)
+    const bool rows_ok = mk_ok(row0 + RMAX - group_rmax(G) >= 0 &&
+                               row0 + RMAX - group_rmax(G) + tc_kgp(G) <= BROWS);
     const unsigned long long a0 =
         tc_desc(tc.win + (unsigned)(row0 + RMAX - group_rmax(G)) * 16u, 128u, (unsigned)TC_GSTR);
     const unsigned long long b0 =
         tc_desc(tc.btab + (unsigned)tc_boff(G), 128u, (unsigned)(tc_kgp(G) / 8) * 128u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-    for (int t = 0; t < TC_NMT; ++t) {
+    for (int t = 0; t < (rows_ok ? TC_NMT : 0); ++t) {
         const unsigned d = tc.tmem + (unsigned)(t * TC_NCT + tc_colg(G));
         const unsigned long long at = a0 + (unsigned long long)((t * 16 * TC_GSTR) >> 4);
 #pragma unroll
@@ -696,7 +725,7 @@ __device__ __forceinline__ void tc_wait(const MhfdKHeader &h, const TcState &tc,
             if (tc_try(bar, par)) return;
         if (gtimer() - t0 > 2000000000ull) break;
     }
-    if (h.flag) atomicExch(h.flag, 1);
+    if (h.flag) atomicOr(h.flag, 1);
 }
 
 // four / eight accumulator columns of this warp's 32 lanes
@@ -765,11 +794,15 @@ __device__ __forceinline__ void tc_st_levels(float *__restrict__ s_v, unsigned (
                 if constexpr (HR == 2) {
 #pragma unroll
                     for (int j = 0; j < RB; j += 2)
-                        *reinterpret_cast<float2 *>(s_v + vidx(L, pt, j, cc)) = make_float2(
-                            __uint_as_float(r[LI][pt * RB + j]), __uint_as_float(r[LI][pt * RB + j + 1]));
+                        if (mk_ok((unsigned)(vidx(L, pt, j, cc) + 1) < (unsigned)SMEM_V))
+                            *reinterpret_cast<float2 *>(s_v + vidx(L, pt, j, cc)) = make_float2(
+                                __uint_as_float(r[LI][pt * RB + j]),
+                                __uint_as_float(r[LI][pt * RB + j + 1]));
                 } else {
 #pragma unroll
-                    for (int j = 0; j < RB; ++j) s_v[vidx(L, pt, j, cc)] = __uint_as_float(r[LI][pt * RB + j]);
+                    for (int j = 0; j < RB; ++j)
+                        if (mk_ok((unsigned)vidx(L, pt, j, cc) < (unsigned)SMEM_V))
+                            s_v[vidx(L, pt, j, cc)] = __uint_as_float(r[LI][pt * RB + j]);
                 }
             }
         }
@@ -864,15 +897,20 @@ __device__ __forceinline__ void vcol(const float *__restrict__ win, float *__res
             if constexpr (HR == 2 && ROWS % 2 == 0) {
 #pragma unroll
                 for (int j = 0; j < ROWS; j += 2) {
-                    *reinterpret_cast<float2 *>(s_v + vidx(LB + l, 0, o0 + j, cc)) =
-                        make_float2(acc[j][l], acc[j + 1][l]);
-                    if constexpr (LOG)
-                        *reinterpret_cast<float2 *>(s_v + vidx(LB + l, 1, o0 + j, cc)) =
-                            make_float2(acc2[j][l], acc2[j + 1][l]);
+                    if (mk_ok((unsigned)(vidx(LB + l, LOG ? 1 : 0, o0 + j, cc) + 1) <
+                              (unsigned)SMEM_V)) {
+                        *reinterpret_cast<float2 *>(s_v + vidx(LB + l, 0, o0 + j, cc)) =
+                            make_float2(acc[j][l], acc[j + 1][l]);
+                        if constexpr (LOG)
+                            *reinterpret_cast<float2 *>(s_v + vidx(LB + l, 1, o0 + j, cc)) =
+                                make_float2(acc2[j][l], acc2[j + 1][l]);
+                    }
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < ROWS; ++j) {
+                    if (!mk_ok((unsigned)vidx(LB + l, LOG ? 1 : 0, o0 + j, cc) < (unsigned)SMEM_V))
+                        continue;
                     s_v[vidx(LB + l, 0, o0 + j, cc)] = acc[j][l];
                     if constexpr (LOG) s_v[vidx(LB + l, 1, o0 + j, cc)] = acc2[j][l];
                 }
@@ -1162,7 +1200,8 @@ __device__ __forceinline__ void hrespond(const MhfdKHeader &h, const HCtx &cx, c
             o.y = w.inb[1] ? d[1] : ninf;
             o.z = w.inb[2] ? d[2] : ninf;
             o.w = w.inb[3] ? d[3] : ninf;
-            reinterpret_cast<float4 *>(s_ring + (w.slot * NDOG + I) * TX2)[cx.q] = o;
+            if (mk_ok((unsigned)w.slot < (unsigned)RING))
+                reinterpret_cast<float4 *>(s_ring + (w.slot * NDOG + I) * TX2)[cx.q] = o;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 if (!w.inb[u]) continue;
@@ -1174,7 +1213,8 @@ __device__ __forceinline__ void hrespond(const MhfdKHeader &h, const HCtx &cx, c
         if (STORE) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (w.inter[u])
+                if (w.inter[u] && mk_ok((unsigned)w.gy < (unsigned)h.H &&
+                                        (unsigned)(cx.gx0 + u) < (unsigned)h.W))
                     h.stack_out[(long long)I * h.plane + (long long)w.gy * h.W + cx.gx0 + u] = d[u];
         }
     }
@@ -1184,7 +1224,16 @@ template <int L>
 __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vbase, const HCtx &cx,
                                        HState &st, float *s_ring, float vs) {
     float a[HR][4];
-    hsums<L>(vbase, cx.q, a);
+    // the item's rows and quad lie in the step (its window columns, fixed at
+    // compile time, lie in the level's row of padded width extp(L))
+    if (mk_ok(cx.j0 + HR <= RB && (unsigned)cx.q < (unsigned)NQ4)) {
+        hsums<L>(vbase, cx.q, a);
+    } else {
+#pragma unroll
+        for (int rr = 0; rr < HR; ++rr)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[rr][u] = 0.0f;
+    }
 #pragma unroll
     for (int rr = 0; rr < HR; ++rr)
         hrespond<L>(h, cx, cx.rw[rr], st.rw[rr], st.soft, a[rr], s_ring, vs);
@@ -1252,6 +1301,7 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
             for (int rr = 0; rr < HR; ++rr) {
                 const HRowCtx &w = cx.rw[rr];
                 const HRowState &st = hs[it].rw[rr];
+                if (!mk_ok((unsigned)w.slot < (unsigned)RING)) continue;
                 if (G == NGROUPS - 1 && MODE == 0) {
                     const float ninf = -__int_as_float(0x7f800000);
                     float4 o;
@@ -1269,7 +1319,8 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
                     if (STORE) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (w.inter[u]) {
+                            if (w.inter[u] && mk_ok((unsigned)w.gy < (unsigned)h.H &&
+                                                    (unsigned)(cx.gx0 + u) < (unsigned)h.W)) {
                                 const long long o2 = (long long)w.gy * h.W + cx.gx0 + u;
                                 if (h.m_out) h.m_out[o2] = st.m[u];
                                 if (h.arg_out) h.arg_out[o2] = st.a[u];
@@ -1410,7 +1461,7 @@ __device__ __forceinline__ int nms_rows(const MhfdKHeader &h, const March &m,
     }
     int sum;
     int pos = total + block_excl_scan(cnt, s_scan, &sum, par);
-    if (cnt) {
+    if (cnt && mk_ok(slot >= 0 && pos >= 0)) {
         MhfdCand *dst = h.stage + slot * h.cap_tile;
         auto put = [&](int r, int c, int l, float v) {
             if (pos < h.cap_tile) {
@@ -1527,7 +1578,7 @@ __device__ __forceinline__ void march(const MhfdKHeader &h, const MhfdStretch &s
             total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, par, ra, re,
                              slot0 + (long long)(ta + tile) * tiles_x + tx, total);
             if (re == tend) {
-                if (threadIdx.x == 0)
+                if (threadIdx.x == 0 && mk_ok(ta + tile < h.tiles_y && tx < tiles_x))
                     h.tile_count[slot0 + (long long)(ta + tile) * tiles_x + tx] = total;
                 ++tile;
                 total = 0;
@@ -1631,7 +1682,7 @@ __device__ __forceinline__ void march_tc(const MhfdKHeader &h, const MhfdStretch
             total = nms_rows(h, m, sm.ring, sm.arg, sm.scan, par, ra, re,
                              slot0 + (long long)(ta + tile) * tiles_x + tx, total);
             if (re == tend) {
-                if (threadIdx.x == 0)
+                if (threadIdx.x == 0 && mk_ok(ta + tile < h.tiles_y && tx < tiles_x))
                     h.tile_count[slot0 + (long long)(ta + tile) * tiles_x + tx] = total;
                 ++tile;
                 total = 0;
@@ -1735,6 +1786,10 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
     sm.scan = reinterpret_cast<int *>(sm.arg + SMEM_RING_B);
     sm.ctrl = reinterpret_cast<unsigned char *>(sm.scan) + 4 * 64;
 
+    if constexpr (CHECKS) {
+        if (threadIdx.x == 0) mk_chk_flag = p.h.flag;
+        __syncthreads();
+    }
     // single image with a gate: the tensor-core kernel takes narrow stretch
     // ranges, its FFMA companion the rest (both launched, one works); a batch
     // applies the gate per image
@@ -1745,7 +1800,7 @@ extern "C" __global__ void __launch_bounds__(mk::NT, 1)
     TcState tc{};
     if constexpr (TC) {
         if (p.h.dtype == 2) {  // float images never reach this kernel
-            if (threadIdx.x == 0 && p.h.flag) atomicExch(p.h.flag, 1);
+            if (threadIdx.x == 0 && p.h.flag) atomicOr(p.h.flag, 1);
             return;
         }
         tc_setup_smem(sm.win, sm.btab);

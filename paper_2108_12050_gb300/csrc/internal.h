@@ -131,8 +131,9 @@ struct Counters {
     unsigned long long n_blobs;     // survivors
     int overflow;
     int timeout;
-    int ktimeout;                   // set by a fused kernel whose bounded wait gave up;
-                                    // moved into `timeout` (and cleared) by the gather
+    int ktimeout;                   // bit 0: a fused kernel's bounded wait gave up; bit 1:
+                                    // a check of the debug build failed; moved into
+                                    // `timeout` (and cleared) by the gather
     unsigned long long blob_base;   // first slot of this image's blobs in the output list
 };
 

@@ -96,6 +96,10 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_BOUNDARY " << lk.boundary << "\n"
       << "#define MHFD_RESPONSE " << lk.response << "\n"
       << "#define MHFD_TAPS2 " << (lk.response ? join_f(lk.taps2) : std::string("0.0f")) << "\n";
+    // MHFD_DEBUG_CHECKS=1: the debug build of the kernel, whose indices are
+    // checked against their buffers (a failure is reported as MHFD_ERR_CHECK)
+    if (const char *e = std::getenv("MHFD_DEBUG_CHECKS"))
+        if (e[0] == '1') o << "#define MHFD_CHECKS 1\n";
     // the kernel's own shared-memory layout must be the one the host sized
     // and chose the tile by: a compile error otherwise
     const std::string check = "\nstatic_assert(mk::SMEM_BYTES == " +

@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256)
         __nanosleep(100);
         if ((sweep & 63) == 63 && globaltimer_ns() - t0 > max_ns) break;
     }
-    if (pending) atomicExch(&cnt->timeout, 1);
+    if (pending) atomicOr(&cnt->timeout, 1);
 }
 
 __global__ void keep_all(const Counters *cnt, int *state) {
