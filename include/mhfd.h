@@ -86,12 +86,13 @@ typedef struct {
                                strip width incl. the 2 NMS border columns
                                (multiple of 4), tile height incl. 2 border
                                rows, rows per step (2..16), threads per
-                               block (multiple of 32), level groups, rows
-                               per horizontal item (0 or 1: one row of four
-                               outputs; 2: two rows, packed two-lane FMAs
-                               over the row pair; needs an even number of
-                               rows per step); the same six fields as
-                               mhfd_tile_configs.
+                               block (multiple of 32), level groups,
+                               horizontal item kind (0 or 1: one row of four
+                               outputs; 2: two rows of four, packed two-lane
+                               FMAs over the row pair, needs an even number
+                               of rows per step; 3: one row of two outputs,
+                               twice the items per step); the same six
+                               fields as mhfd_tile_configs.
                                INVALID_ARG when out of range, UNSUPPORTED
                                when it does not fit in shared memory */
     int32_t timing;         /* 1: record CUDA events around the kernels of each
@@ -311,7 +312,7 @@ int mhfd_device_bytes(mhfd_detector *det, int32_t H, int32_t W, int64_t *fixed_b
  * ladder of `p` (autotuner menu): returns their count; if `desc` is not NULL
  * writes up to `cap` rows of six int32 (strip width and tile height, both
  * including the one-pixel NMS border, rows per step, threads per block,
- * level groups, rows per horizontal item).
+ * level groups, horizontal item kind).
  * Row k is selected by params.tile_override = k + 1.  Host only. */
 int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap);
 

@@ -492,14 +492,14 @@ int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, Tile
             if (ts[0] % 4 || ts[0] < 8 || ts[0] > 2048 || ts[1] < 3 || ts[1] > 4096 ||
                 ts[4] < 1 || ts[4] > nl)
                 return fail(MHFD_ERR_INVALID_ARG, "tile_shape out of range");
-            if (ts[5] < 0 || ts[5] > 2 || (ts[5] == 2 && ts[2] % 2))
-                return fail(MHFD_ERR_INVALID_ARG, "tile_shape: rows per item must be 1, or 2 "
-                                                  "with an even number of rows per step");
+            if (ts[5] < 0 || ts[5] > 3 || (ts[5] == 2 && ts[2] % 2))
+                return fail(MHFD_ERR_INVALID_ARG, "tile_shape: item kind must be 1, 2 (with an "
+                                                  "even number of rows per step) or 3");
             cfg->tx2 = ts[0];
             cfg->ty2 = ts[1];
             cfg->rb = ts[2];
             cfg->nt = ts[3];
-            cfg->hr = ts[5] == 2 ? 2 : 1;
+            cfg->item = ts[5] == 0 ? 1 : ts[5];
             cfg->gb.assign(ts[4] + 1, 0);
             for (int g = 0; g <= ts[4]; ++g) cfg->gb[g] = (int)((long long)nl * g / ts[4]);
             cfg->tc = 1;
@@ -523,17 +523,20 @@ int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, Tile
         if (ts[0] % 4 || ts[0] < 8 || ts[0] > 2048 || ts[1] < 3 || ts[1] > 4096 || ts[2] < 2 ||
             ts[2] > 16 || ts[3] % 32 || ts[3] < 32 || ts[3] > 1024 || ts[4] < 1 || ts[4] > nl)
             return fail(MHFD_ERR_INVALID_ARG, "tile_shape out of range");
-        if (ts[5] < 0 || ts[5] > 2 || (ts[5] == 2 && ts[2] % 2))
-            return fail(MHFD_ERR_INVALID_ARG, "tile_shape: rows per item must be 1, or 2 "
-                                              "with an even number of rows per step");
-        const int hr = ts[5] == 2 ? 2 : 1;
-        if ((ts[2] / hr) * (ts[0] / 4) > 2 * ts[3])
+        if (ts[5] < 0 || ts[5] > 3 || (ts[5] == 2 && ts[2] % 2))
+            return fail(MHFD_ERR_INVALID_ARG, "tile_shape: item kind must be 1, 2 (with an "
+                                              "even number of rows per step) or 3");
+        TileConfig probe;
+        probe.tx2 = ts[0];
+        probe.rb = ts[2];
+        probe.item = ts[5] == 0 ? 1 : ts[5];
+        if (h_items(probe) > 2 * ts[3])
             return fail(MHFD_ERR_INVALID_ARG, "tile_shape: more than two horizontal items per thread");
         cfg->tx2 = ts[0];
         cfg->ty2 = ts[1];
         cfg->rb = ts[2];
         cfg->nt = ts[3];
-        cfg->hr = hr;
+        cfg->item = probe.item;
         cfg->gb.assign(ts[4] + 1, 0);
         for (int g = 0; g <= ts[4]; ++g) cfg->gb[g] = (int)((long long)nl * g / ts[4]);
         if (smem_estimate(R, mode, *cfg) > kSmemLimitBytes)
@@ -1045,7 +1048,7 @@ int mhfd_tile_configs(const mhfd_params *p, int32_t *desc, int32_t cap) {
             desc[6 * k + 2] = menu[k].rb;
             desc[6 * k + 3] = menu[k].nt;
             desc[6 * k + 4] = (int)menu[k].gb.size() - 1;
-            desc[6 * k + 5] = menu[k].hr;
+            desc[6 * k + 5] = menu[k].item;
         }
     }
     return (int)menu.size();
@@ -1067,7 +1070,7 @@ int mhfd_chosen_tile(const mhfd_params *p, int32_t *desc6) {
     desc6[2] = c.rb;
     desc6[3] = c.nt;
     desc6[4] = (int)c.gb.size() - 1;
-    desc6[5] = c.hr;
+    desc6[5] = c.item;
     return MHFD_OK;
 }
 

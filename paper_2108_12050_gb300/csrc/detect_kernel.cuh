@@ -79,11 +79,18 @@ constexpr bool TC = (MHFD_VTC) != 0;
 #define MHFD_HR 1
 #endif
 constexpr int HR = MHFD_HR;
+// Outputs per row of a horizontal item: 4 (float4 loads, each value feeding
+// four outputs), or 2 (one-row items only: twice the items per step, for
+// shapes whose strips are too narrow to give every thread a four-output item)
+#ifndef MHFD_HW
+#define MHFD_HW 4
+#endif
+constexpr int HW = MHFD_HW;
 // one-row items on packed two-lane FMAs over column pairs (outputs (0, 1)
 // and (2, 3)): measured faster for the tensor-core LoG kernel (2.79 -> 2.61
 // ms on a 4096^2 tile), slower for the DoG kernels (1.00 -> 1.16 ms
 // tensor-core, 1.51 -> 1.60 ms FFMA)
-constexpr bool HPACK = TC && LOG && HR == 1;
+constexpr bool HPACK = TC && LOG && HR == 1 && HW == 4;
 // Debug build (MHFD_CHECKS 1): the shared-memory and global indices the
 // kernel forms are checked against their buffers; a failed check sets bit 1
 // of the kernel's flag word (the host reports MHFD_ERR_CHECK) and the
@@ -156,8 +163,8 @@ constexpr int WIN = RB + 2 * RMAX;             // input rows one step reads
 constexpr int BROWS = MHFD_BROWS;              // rows of the sliding input window
 constexpr int NT_COLS = (WEXT + MHFD_NT - 1) / MHFD_NT;  // input columns per thread
 constexpr int RING = RB + 2;
-constexpr int NQ4 = TX2 / 4;
-constexpr int HITEMS = (RB / HR) * NQ4;
+constexpr int NQW = TX2 / HW;                  // horizontal items per row
+constexpr int HITEMS = (RB / HR) * NQW;
 // threads that take horizontal items: with the tensor-core pass and a
 // block of whole warpgroups plus one warp, that last warp only issues MMAs
 constexpr int NTW = (TC && NT % 128 == 32) ? NT - 32 : NT;
@@ -286,6 +293,7 @@ static_assert(!TC || TC_NMT * TC_NCT <= 512, "tensor memory columns");
 static_assert(!TC || BROWS >= WIN + 2 * RB + 16, "window rows of the tensor-core pass");
 static_assert(!TC || NGROUPS <= 12, "one mbarrier per group in the control block");
 static_assert(HR == 1 || (HR == 2 && RB % 2 == 0 && MODE <= 1), "two-row horizontal items");
+static_assert(HW == 4 || (HW == 2 && HR == 1), "two-output horizontal items have one row");
 
 struct KParams {
     MhfdKHeader h;
@@ -1085,6 +1093,24 @@ struct HQuads2<R, TO, -1, OFF, T2, S> {
     static __device__ __forceinline__ void run(const float2 *, float2 (&)[4]) {}
 };
 
+// Two-output items: window column M feeds outputs 0 and 1; float2 loads (two
+// columns), descending like the four-output pass.
+template <int R, int TO, int P, int OFF, bool T2>
+struct HPairs {
+    static __device__ __forceinline__ void run(const float2 *w, float (&a)[4]) {
+        const float2 v = w[P];
+        hacc1<R, TO, 2 * P, 0, OFF, T2>(v.x, a);
+        hacc1<R, TO, 2 * P, 1, OFF, T2>(v.x, a);
+        hacc1<R, TO, 2 * P + 1, 0, OFF, T2>(v.y, a);
+        hacc1<R, TO, 2 * P + 1, 1, OFF, T2>(v.y, a);
+        HPairs<R, TO, P - 1, OFF, T2>::run(w, a);
+    }
+};
+template <int R, int TO, int OFF, bool T2>
+struct HPairs<R, TO, -1, OFF, T2> {
+    static __device__ __forceinline__ void run(const float2 *, float (&)[4]) {}
+};
+
 // The horizontal sums of level L for the item's outputs: a[rr][u] for row rr.
 // `vbase` is the item's first row in the V rows (row pair for two-row items).
 template <int L>
@@ -1109,6 +1135,18 @@ __device__ __forceinline__ void hsums(const float *vbase, int q, float (&a)[HR][
         for (int u = 0; u < 4; ++u) {
             a[0][u] = p[u].x;
             a[HR - 1][u] = p[u].y;
+        }
+    } else if constexpr (HW == 2) {
+        float (&a0)[4] = a[0];
+        a0[0] = a0[1] = 0.0f;
+        if constexpr (LOG) {
+            HPairs<R, tapoff(L), (2 * R + 4) / 2 - 1, 1, false>::run(
+                reinterpret_cast<const float2 *>(vbase + voff(L) + extp(L)) + q, a0);
+            HPairs<R + 1, tapoff2(L), (2 * R + 5) / 2 - 1, 0, true>::run(
+                reinterpret_cast<const float2 *>(vbase + voff(L)) + q, a0);
+        } else {
+            HPairs<R, tapoff(L), (2 * R + 3) / 2 - 1, 0, false>::run(
+                reinterpret_cast<const float2 *>(vbase + voff(L)) + q, a0);
         }
     } else {
         float (&a0)[4] = a[0];
@@ -1146,11 +1184,11 @@ __device__ __forceinline__ void hrespond(const MhfdKHeader &h, const HCtx &cx, c
                                          float *s_ring, float vs) {
     if (MODE == 3) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < HW; ++u)
             if (w.inter[u]) h.stack_out[(long long)w.gy * h.W + cx.gx0 + u] += a[u];
     } else if (!LOG && L == 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < HW; ++u) {
             st.lp[u] = a[u];
             st.m[u] = -__int_as_float(0x7f800000);
             st.a[u] = 0;
@@ -1163,10 +1201,10 @@ __device__ __forceinline__ void hrespond(const MhfdKHeader &h, const HCtx &cx, c
         float d[4];
         if constexpr (LOG) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) d[u] = tsv * a[u];
+            for (int u = 0; u < HW; ++u) d[u] = tsv * a[u];
             if (L == 0) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < HW; ++u) {
                     st.m[u] = -__int_as_float(0x7f800000);
                     st.a[u] = 0;
                     st.mk[u] = 0;
@@ -1174,36 +1212,39 @@ __device__ __forceinline__ void hrespond(const MhfdKHeader &h, const HCtx &cx, c
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < HW; ++u) {
                 d[u] = tsv * (a[u] - st.lp[u]);
                 st.lp[u] = a[u];
             }
         }
         if (MODE == 0) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < HW; ++u)
                 if (d[u] > st.m[u]) {
                     st.m[u] = d[u];
                     st.a[u] = I;
                 }
         } else if (MODE == 2) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < HW; ++u)
                 if (w.inter[u]) {
                     const float z = fminf(fmaxf((d[u] - h.soft_tau) * h.soft_inv_t, -80.0f), 80.0f);
                     soft[I] += __fdividef(1.0f, 1.0f + __expf(-z));
                 }
         } else {
             const float ninf = -__int_as_float(0x7f800000);
-            float4 o;
-            o.x = w.inb[0] ? d[0] : ninf;
-            o.y = w.inb[1] ? d[1] : ninf;
-            o.z = w.inb[2] ? d[2] : ninf;
-            o.w = w.inb[3] ? d[3] : ninf;
-            if (mk_ok((unsigned)w.slot < (unsigned)RING))
-                reinterpret_cast<float4 *>(s_ring + (w.slot * NDOG + I) * TX2)[cx.q] = o;
+            if (mk_ok((unsigned)w.slot < (unsigned)RING)) {
+                float *row = s_ring + (w.slot * NDOG + I) * TX2;
+                if constexpr (HW == 4)
+                    reinterpret_cast<float4 *>(row)[cx.q] =
+                        make_float4(w.inb[0] ? d[0] : ninf, w.inb[1] ? d[1] : ninf,
+                                    w.inb[2] ? d[2] : ninf, w.inb[3] ? d[3] : ninf);
+                else
+                    reinterpret_cast<float2 *>(row)[cx.q] =
+                        make_float2(w.inb[0] ? d[0] : ninf, w.inb[1] ? d[1] : ninf);
+            }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < HW; ++u) {
                 if (!w.inb[u]) continue;
                 if (I > 0 && d[u] > st.dp[u]) st.mk[u] &= ~(LMask(1) << (I > 0 ? I - 1 : 0));
                 if (d[u] > h.thr && (I == 0 || !(st.dp[u] > d[u]))) st.mk[u] |= LMask(1) << I;
@@ -1212,7 +1253,7 @@ __device__ __forceinline__ void hrespond(const MhfdKHeader &h, const HCtx &cx, c
         }
         if (STORE) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < HW; ++u)
                 if (w.inter[u] && mk_ok((unsigned)w.gy < (unsigned)h.H &&
                                         (unsigned)(cx.gx0 + u) < (unsigned)h.W))
                     h.stack_out[(long long)I * h.plane + (long long)w.gy * h.W + cx.gx0 + u] = d[u];
@@ -1226,13 +1267,13 @@ __device__ __forceinline__ void hlevel(const MhfdKHeader &h, const float *vbase,
     float a[HR][4];
     // the item's rows and quad lie in the step (its window columns, fixed at
     // compile time, lie in the level's row of padded width extp(L))
-    if (mk_ok(cx.j0 + HR <= RB && (unsigned)cx.q < (unsigned)NQ4)) {
+    if (mk_ok(cx.j0 + HR <= RB && (unsigned)cx.q < (unsigned)NQW)) {
         hsums<L>(vbase, cx.q, a);
     } else {
 #pragma unroll
         for (int rr = 0; rr < HR; ++rr)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a[rr][u] = 0.0f;
+            for (int u = 0; u < HW; ++u) a[rr][u] = 0.0f;
     }
 #pragma unroll
     for (int rr = 0; rr < HR; ++rr)
@@ -1263,10 +1304,10 @@ struct March {
 
 __device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, const March &m, int item, int s) {
     HCtx cx;
-    const int j = item / NQ4;
-    cx.q = item - j * NQ4;
+    const int j = item / NQW;
+    cx.q = item - j * NQW;
     cx.j0 = HR * j;
-    cx.gx0 = m.x0 - 1 + 4 * cx.q;
+    cx.gx0 = m.x0 - 1 + HW * cx.q;
 #pragma unroll
     for (int rr = 0; rr < HR; ++rr) {
         HRowCtx &w = cx.rw[rr];
@@ -1276,9 +1317,9 @@ __device__ __forceinline__ HCtx make_ctx(const MhfdKHeader &h, const March &m, i
         const bool rowin = w.gy >= 0 && w.gy < h.H;
         const bool rowint = rowin && w.r >= 1 && w.r <= m.Y;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < HW; ++u) {
             const int gx = cx.gx0 + u;
-            const int c = 4 * cx.q + u;
+            const int c = HW * cx.q + u;
             w.inb[u] = rowin && gx >= 0 && gx < h.W;
             w.inter[u] = rowint && c >= 1 && c <= TX2 - 2 && gx < h.W;
         }
@@ -1304,21 +1345,22 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
                 if (!mk_ok((unsigned)w.slot < (unsigned)RING)) continue;
                 if (G == NGROUPS - 1 && MODE == 0) {
                     const float ninf = -__int_as_float(0x7f800000);
-                    float4 o;
-                    o.x = w.inb[0] ? st.m[0] : ninf;
-                    o.y = w.inb[1] ? st.m[1] : ninf;
-                    o.z = w.inb[2] ? st.m[2] : ninf;
-                    o.w = w.inb[3] ? st.m[3] : ninf;
-                    reinterpret_cast<float4 *>(s_ring + w.slot * TX2)[cx.q] = o;
-                    uchar4 ab;
-                    ab.x = (unsigned char)st.a[0];
-                    ab.y = (unsigned char)st.a[1];
-                    ab.z = (unsigned char)st.a[2];
-                    ab.w = (unsigned char)st.a[3];
-                    reinterpret_cast<uchar4 *>(s_arg + w.slot * TX2)[cx.q] = ab;
+                    if constexpr (HW == 4) {
+                        reinterpret_cast<float4 *>(s_ring + w.slot * TX2)[cx.q] =
+                            make_float4(w.inb[0] ? st.m[0] : ninf, w.inb[1] ? st.m[1] : ninf,
+                                        w.inb[2] ? st.m[2] : ninf, w.inb[3] ? st.m[3] : ninf);
+                        reinterpret_cast<uchar4 *>(s_arg + w.slot * TX2)[cx.q] =
+                            make_uchar4((unsigned char)st.a[0], (unsigned char)st.a[1],
+                                        (unsigned char)st.a[2], (unsigned char)st.a[3]);
+                    } else {
+                        reinterpret_cast<float2 *>(s_ring + w.slot * TX2)[cx.q] =
+                            make_float2(w.inb[0] ? st.m[0] : ninf, w.inb[1] ? st.m[1] : ninf);
+                        reinterpret_cast<uchar2 *>(s_arg + w.slot * TX2)[cx.q] =
+                            make_uchar2((unsigned char)st.a[0], (unsigned char)st.a[1]);
+                    }
                     if (STORE) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
+                        for (int u = 0; u < HW; ++u)
                             if (w.inter[u] && mk_ok((unsigned)w.gy < (unsigned)h.H &&
                                                     (unsigned)(cx.gx0 + u) < (unsigned)h.W)) {
                                 const long long o2 = (long long)w.gy * h.W + cx.gx0 + u;
@@ -1328,9 +1370,9 @@ __device__ __forceinline__ void hpass(const MhfdKHeader &h, const March &m, cons
                     }
                 }
                 if (G == NGROUPS - 1 && MODE == 1) {
-                    LMask *mrow = reinterpret_cast<LMask *>(s_arg) + w.slot * TX2 + 4 * cx.q;
+                    LMask *mrow = reinterpret_cast<LMask *>(s_arg) + w.slot * TX2 + HW * cx.q;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) mrow[u] = st.mk[u];
+                    for (int u = 0; u < HW; ++u) mrow[u] = st.mk[u];
                 }
             }
         }

@@ -69,10 +69,13 @@ struct TileConfig {
     int tx2, ty2, rb, nt;
     std::vector<int> gb;   // level-group boundaries
     int tc = 0;            // 1: vertical pass on the tensor cores (tcgen05)
-    int hr = 1;            // rows per horizontal item: 1, or 2 (packed FMAs over row pairs)
+    int item = 1;          // horizontal item: 1 one row x 4 outputs, 2 two rows x 4
+                           // (packed FMAs over the row pair), 3 one row x 2 outputs
 };
+inline int item_rows(const TileConfig &c) { return c.item == 2 ? 2 : 1; }
+inline int item_cols(const TileConfig &c) { return c.item == 3 ? 2 : 4; }
 // horizontal items of one step of a shape
-inline int h_items(const TileConfig &c) { return (c.rb / c.hr) * (c.tx2 / 4); }
+inline int h_items(const TileConfig &c) { return (c.rb / item_rows(c)) * (c.tx2 / item_cols(c)); }
 
 struct Variant {
     std::string key;

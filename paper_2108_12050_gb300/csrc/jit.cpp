@@ -88,7 +88,8 @@ std::string make_source(const LadderKey &lk, int mode, int store, const TileConf
       << "#define MHFD_TY2 " << c.ty2 << "\n"
       << "#define MHFD_BROWS " << brows_for(R, smode, c) << "\n"
       << "#define MHFD_RB " << c.rb << "\n"
-      << "#define MHFD_HR " << ((mode & 3) <= 1 ? c.hr : 1) << "\n"
+      << "#define MHFD_HR " << ((mode & 3) <= 1 ? item_rows(c) : 1) << "\n"
+      << "#define MHFD_HW " << ((mode & 3) <= 1 ? item_cols(c) : 4) << "\n"
       << "#define MHFD_VTC " << c.tc << "\n"
       << "#define MHFD_NT " << c.nt << "\n"
       << "#define MHFD_MODE " << mode << "\n"
@@ -340,7 +341,7 @@ bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::
     if (!tc_mode_ok(mode)) return no("the tensor-core pass takes the DoG detection modes only");
     if (c.rb != 4 && c.rb != 8) return no("the tensor-core pass takes four or eight rows per step");
     if (c.nt % 32 || c.nt < 128 || c.nt > 1024) return no("threads: whole warps, at least one warpgroup");
-    if (c.hr != 1 && c.hr != 2) return no("one or two rows per horizontal item");
+    if (c.item < 1 || c.item > 3) return no("horizontal item kind 1, 2 or 3");
     if (h_items(c) > 2 * c.nt) return no("more than two horizontal items per thread");
     if (c.gb.size() - 1 > 12) return no("at most 12 level groups");
     if (tc_tmem_cols(R, mode, c) > 512) return no("tensor memory holds 512 columns");
@@ -362,6 +363,7 @@ std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode) {
     for (int hr : {1, 2})
     for (int rb : {4, 8}) {
         if (hr == 1 && rb == 8) continue;
+        const int item = hr;
         for (int tx2 : widths)
             for (int nt : threads) {
                 const int items = (rb / hr) * (tx2 / 4);
@@ -372,7 +374,7 @@ std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode) {
                     c.ty2 = 2 + 16;
                     c.rb = rb;
                     c.nt = nt;
-                    c.hr = hr;
+                    c.item = item;
                     c.gb.assign(ng + 1, 0);
                     for (int g = 0; g <= ng; ++g) c.gb[g] = (int)((long long)nl * g / ng);
                     c.tc = 1;
@@ -426,7 +428,7 @@ bool choose_tile_tc(const std::vector<int> &R, int mode, TileConfig *cfg, std::s
     bool found = false;
     TileConfig comp;
     for (const TileConfig &c : menu) {
-        if (c.rb != 4 || c.hr != 1 || c.tx2 != c.nt - 32 || c.nt * 168 > 65536 ||
+        if (c.rb != 4 || c.item != 1 || c.tx2 != c.nt - 32 || c.nt * 168 > 65536 ||
             !companion_tile(R, mode, c, &comp))
             continue;
         if (!found || c.tx2 > cfg->tx2 ||

@@ -58,6 +58,13 @@ def lookup(n, t_min, t_max, nms, sms, truncate=4.0, response="dog", tensor_cores
     return [int(v) for v in shape] + ([1] if len(shape) == 5 else [])
 
 
+def item_count(tx2, rb, item):
+    """Horizontal items of one step: kind 1 is one row of four outputs, 2 two
+    rows of four, 3 one row of two."""
+    rows, cols = (2, 4) if item == 2 else (1, 2) if item == 3 else (1, 4)
+    return (rb // rows) * (tx2 // cols)
+
+
 def _rmax(n, t_min, t_max, truncate=4.0):
     import math
     dt = (t_max - t_min) / n
@@ -72,17 +79,17 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0, response="dog"):
                                 tensor_cores=False)
     rmax = _rmax(n, t_min, t_max) + (0 if response in ("dog", 0) else 1)
     seen, out = set(), []
-    for (tx2, ty2, rb, nt, ng, hr) in menu:
+    for (tx2, ty2, rb, nt, ng, item) in menu:
         if tx2 < min_width:
             continue
         wext = tx2 + 2 * rmax
-        hitems = (rb // hr) * tx2 // 4
+        hitems = item_count(tx2, rb, item)
         if hitems > nt or hitems < 0.85 * nt:
             continue
         vutil = wext / (nt * -(-wext // nt))
         if vutil < 0.75:
             continue
-        key = (tx2, ty2, rb, nt, ng, hr)
+        key = (tx2, ty2, rb, nt, ng, item)
         if key in seen:
             continue
         seen.add(key)
@@ -91,7 +98,7 @@ def candidates(n, t_min, t_max, nms, limit=None, min_width=0, response="dog"):
 
 
 def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), groups=(2, 3, 4, 5),
-                     response="dog", hrs=(1,)):
+                     response="dog", items=(1,)):
     """FFMA-kernel shapes off the menu's width grid (strip widths fitted to
     an image width).  Thread counts: at least one per horizontal item and one per
     halo'd column of the vertical pass (a single round), that count plus one
@@ -100,16 +107,17 @@ def width_candidates(n, t_min, t_max, nms, widths, rbs=(2, 3, 4, 5, 6, 8), group
     from . import _native
     rmax = _rmax(n, t_min, t_max) + (0 if response in ("dog", 0) else 1)
     out = []
-    for tx2, rb, hr in [(w, r, h) for w in widths for r in rbs for h in hrs if r % h == 0]:
+    for tx2, rb, item in [(w, r, k) for w in widths for r in rbs for k in items
+                          if k != 2 or r % 2 == 0]:
         ncol = -(-(tx2 + 2 * rmax) // 32) * 32
         if True:
-            hitems = (rb // hr) * tx2 // 4
+            hitems = item_count(tx2, rb, item)
             base = max(-(-hitems // 32) * 32, ncol)
             for nt in sorted({base, base + 32, -(-base // 128) * 128}):
                 if nt > 1024:
                     continue
                 for ng in groups:
-                    shape = (tx2, 18, rb, nt, ng, hr)
+                    shape = (tx2, 18, rb, nt, ng, item)
                     try:
                         _native.chosen_tile(n=n, t_min=t_min, t_max=t_max, nms=nms,
                                             tile_shape=shape, response=response,
@@ -176,7 +184,8 @@ def main():
     ap.add_argument("--widths", default="", help="extra strip widths off the menu, e.g. 312,344")
     ap.add_argument("--rbs", default="2,3,4,5,6,8", help="rows per step of the extra shapes")
     ap.add_argument("--groups", default="2,3,4,5", help="level groups of the extra shapes")
-    ap.add_argument("--hrs", default="1", help="rows per horizontal item of the extra shapes")
+    ap.add_argument("--items", default="1",
+                    help="horizontal item kinds of the extra shapes (1: 1x4, 2: 2x4, 3: 1x2)")
     ap.add_argument("--response", default="dog", choices=["dog", "log"])
     ap.add_argument("--tensor-cores", action="store_true",
                     help="tune the tensor-core kernel (its own shape menu)")
@@ -200,7 +209,7 @@ def main():
                                  rbs=[int(v) for v in args.rbs.split(",")],
                                  groups=[int(v) for v in args.groups.split(",")],
                                  response=args.response,
-                                 hrs=[int(v) for v in args.hrs.split(",")])
+                                 items=[int(v) for v in args.items.split(",")])
         cands += [c for c in extra if c not in cands]
     t0 = time.time()
     comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands, response=args.response,

@@ -79,9 +79,9 @@ def test_tile_menu_fits_shared_memory(native):
         kw["tensor_cores"] = False
         menu = native.tile_configs(**kw)
         assert len(menu) > 10
-        for tx2, ty2, rb, nt, ng, hr in menu:
+        for tx2, ty2, rb, nt, ng, item in menu:
             assert tx2 % 4 == 0 and ty2 >= 3 and rb >= 2 and nt % 32 == 0 and ng >= 1
-            assert hr in (1, 2) and rb % hr == 0
+            assert item in (1, 2, 3) and (item != 2 or rb % 2 == 0)
         chosen = native.chosen_tile(**kw)
         assert chosen in menu
 
@@ -103,9 +103,9 @@ def test_tensor_core_tile_menu(native):
     for kw in (dict(n=10, t_min=1, t_max=10), dict(n=16, t_min=1, t_max=12)):
         menu = native.tile_configs(tensor_cores=True, **kw)
         assert len(menu) > 10
-        for tx2, ty2, rb, nt, ng, hr in menu:
-            assert rb in (4, 8) and nt % 32 == 0 and nt >= 128
-            assert (rb // hr) * tx2 // 4 <= 2 * nt and (hr == 2 or rb == 4)
+        for tx2, ty2, rb, nt, ng, item in menu:
+            assert rb in (4, 8) and nt % 32 == 0 and nt >= 128 and item in (1, 2)
+            assert (rb // item) * tx2 // 4 <= 2 * nt and (item == 2 or rb == 4)
         assert any(s[5] == 2 and s[2] == 8 for s in menu)
         chosen = native.chosen_tile(tensor_cores=True, **kw)
         assert chosen in menu and chosen[0] == chosen[3] - 32
@@ -129,8 +129,8 @@ def test_explicit_tensor_core_tile_shape(native):
         with pytest.raises(native.MhfdError) as e:
             native.chosen_tile(tile_shape=bad, **kw)
         assert e.value.code == -2, bad
-    # width not a multiple of 4, rows per item not 1 or 2
-    for bad in ((350, 18, 4, 384, 3), (352, 18, 4, 384, 3, 3)):
+    # width not a multiple of 4, item kind not 1, 2 or 3
+    for bad in ((350, 18, 4, 384, 3), (352, 18, 4, 384, 3, 4)):
         with pytest.raises(native.MhfdError) as e:
             native.chosen_tile(tile_shape=bad, **kw)
         assert e.value.code == -1, bad
@@ -140,6 +140,7 @@ def test_explicit_tile_shape(native):
     kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=False)
     assert native.chosen_tile(tile_shape=(320, 18, 4, 448, 3), **kw) == (320, 18, 4, 448, 3, 1)
     assert native.chosen_tile(tile_shape=(320, 18, 4, 448, 3, 2), **kw) == (320, 18, 4, 448, 3, 2)
+    assert native.chosen_tile(tile_shape=(192, 18, 4, 384, 2, 3), **kw) == (192, 18, 4, 384, 2, 3)
     # out of range: width not a multiple of 4, threads not a multiple of 32,
     # too few rows per step, more groups than levels, more than two
     # horizontal items per thread, two-row items on an odd number of rows
@@ -211,7 +212,12 @@ def test_kernel_layout_matches_host_shared_memory_estimate(native, tmp_path, mon
               (dict(tile_shape=(320, 18, 4, 448, 3, 2), n=16, t_min=1.0, t_max=12.0,
                     tensor_cores=False), 0),
               (dict(tile_shape=(96, 18, 4, 160, 1, 2), tensor_cores=True, response="log",
-                    **small), 0)]
+                    **small), 0),
+              # one-row items of two outputs: 26-neighbour rule, LoG, stack-storing
+              (dict(tile_shape=(192, 18, 4, 384, 2, 3), n=16, t_min=1.0, t_max=12.0,
+                    nms="local26", tensor_cores=False), 0),
+              (dict(tile_shape=(96, 18, 4, 224, 1, 3), response="log", tensor_cores=False,
+                    **small), 1)]
     import concurrent.futures as cf
     import multiprocessing as mp
     with cf.ProcessPoolExecutor(max_workers=min(len(cases), os.cpu_count() or 1),

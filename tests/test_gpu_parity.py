@@ -456,3 +456,24 @@ def test_two_row_items_sum_like_one_row_items(response):
     D2, M2, A2, r2 = two.debug_stack(to_dev(img))
     assert torch.equal(D1, D2) and torch.equal(M1, M2) and torch.equal(A1, A2)
     assert np.array_equal(r1.blobs, r2.blobs)
+
+
+@pytest.mark.parametrize("shape,nms,response", [
+    ((192, 18, 4, 384, 2, 3), "local26", "dog"),
+    ((192, 18, 4, 384, 2, 3), "paper", "dog"),
+    ((160, 18, 4, 352, 3, 3), "paper", "log")], ids=["local26", "paper", "log"])
+def test_two_output_items_match_oracle(shape, nms, response):
+    """Shapes whose horizontal items cover one row of two outputs (twice the
+    items per step, for strips too narrow to give every thread a four-output
+    item) on the benchmark ladder: the stack within the tolerance and the
+    detection under the parity rules, on the FFMA kernel."""
+    img = scene(83, 300, 620, "u16")
+    n, tmin, tmax = 16, 1.0, 12.0
+    thr = 0.05 if response == "dog" else 0.05 / 0.6875
+    det = detector(n=n, t_min=tmin, t_max=tmax, threshold=thr, tile_shape=list(shape),
+                   tensor_cores=False, keep_candidates=True, nms=nms, response=response)
+    D, _, _, _ = det.debug_stack(to_dev(img), want=("D",))
+    ref, D_ref, tol, t, _ = oracle_reference(img, n, tmin, tmax, thr, 0.5, nms, response)
+    assert_stack_close(D.cpu().numpy(), D_ref, str(shape))
+    res = det(to_dev(img))
+    check_detection(res, ref, D_ref, tol, thr, 0.5, nms, t)

@@ -47,17 +47,24 @@ def test_ffma_candidates_are_balanced_shapes_of_the_ffma_menu(tune):
                                         **kw))
         cands = tune.candidates(16, 1.0, 12.0, 0, **kw)
         assert cands and len(set(cands)) == len(cands)
-        for tx2, ty2, rb, nt, ng, hr in cands:
-            assert (tx2, ty2, rb, nt, ng, hr) in menu
-            assert 0.85 * nt <= (rb // hr) * tx2 // 4 <= nt
+        for tx2, ty2, rb, nt, ng, item in cands:
+            assert (tx2, ty2, rb, nt, ng, item) in menu
+            assert 0.85 * nt <= tune.item_count(tx2, rb, item) <= nt
+
+
+def test_item_counts():
+    from paper_2108_12050_gb300 import tune
+    assert tune.item_count(352, 4, 1) == 352
+    assert tune.item_count(256, 8, 2) == 256
+    assert tune.item_count(192, 4, 3) == 384
 
 
 def test_width_candidates_fit_the_ffma_kernel(tune):
     from paper_2108_12050_gb300 import _native
     shapes = tune.width_candidates(16, 1.0, 12.0, 0, [312, 344], rbs=(2, 4), groups=(3,),
-                                   hrs=(1, 2))
-    assert shapes and {s[0] for s in shapes} == {312, 344} and {s[5] for s in shapes} == {1, 2}
+                                   items=(1, 2, 3))
+    assert shapes and {s[0] for s in shapes} == {312, 344} and {s[5] for s in shapes} == {1, 2, 3}
     for s in shapes:
-        assert s[3] % 32 == 0 and (s[2] // s[5]) * s[0] // 4 <= s[3]
+        assert s[3] % 32 == 0 and tune.item_count(s[0], s[2], s[5]) <= s[3]
         assert _native.chosen_tile(n=16, t_min=1.0, t_max=12.0, nms=0, tile_shape=s,
                                    tensor_cores=False) == s
