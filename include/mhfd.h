@@ -111,7 +111,8 @@ typedef struct {
                                FP32 tolerance).  tile_shape / tile_override
                                then describe the tensor-core kernel (four rows
                                per step, at least 128 threads).  The paper
-                               rule (DoG or LoG response) only; 0: FFMA
+                               rule (DoG or LoG response) and the
+                               26-neighbour rule (DoG response); 0: FFMA
                                only.  Default 1 */
 } mhfd_params;
 

@@ -139,7 +139,7 @@ class Detector:
                 from . import tune
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
                 is_log = response in ("log", 1)
-                tc = bool(tensor_cores) and nms in ("paper", 0)
+                tc = bool(tensor_cores) and (nms in ("paper", 0) or not is_log)
                 tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate,
                                          "log" if is_log else "dog", tensor_cores=tc)
         tile_override = tile_override or 0

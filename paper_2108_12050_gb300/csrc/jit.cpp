@@ -328,10 +328,12 @@ namespace {
 double cost_model(const std::vector<int> &R, int mode, const TileConfig &c);
 }
 
-// the paper rule, DoG or LoG response (the 26-neighbour rule runs correctly
-// on the tensor-core kernel too, but its ring of all layers leaves room for
-// 192-wide strips of 256 threads only: 5.5 ms against 3.9 ms on FFMA)
-bool tc_mode_ok(int mode) { return (mode & 3) == 0; }
+// The paper rule, DoG or LoG response; the 26-neighbour rule with the DoG
+// response.  (With the scale-maximum masks and two-output items, the
+// 26-neighbour rule runs faster on the tensor-core kernel at 160-wide
+// strips, 2.23 ms, than on the FFMA kernel, 2.36 ms; its ring of all layers
+// had left the tensor-core kernel 192-wide strips of one-row items, 5.5 ms.)
+bool tc_mode_ok(int mode) { return (mode & 3) == 0 || mode == 1; }
 
 bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why) {
     auto no = [&](const char *m) {
@@ -360,13 +362,12 @@ std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode) {
     // four rows per step on one-row items (eight rows of one-row items ran
     // at about twice the time on GB300: two items a thread on two warps per
     // scheduler); four or eight rows on two-row items (packed FMAs)
-    for (int hr : {1, 2})
+    for (int item : {1, 2, 3})
     for (int rb : {4, 8}) {
-        if (hr == 1 && rb == 8) continue;
-        const int item = hr;
+        if (item != 2 && rb == 8) continue;
         for (int tx2 : widths)
             for (int nt : threads) {
-                const int items = (rb / hr) * (tx2 / 4);
+                const int items = (rb / (item == 2 ? 2 : 1)) * (tx2 / (item == 3 ? 2 : 4));
                 if (items > 2 * nt || items <= nt - 128) continue;  // 1..2 items a thread, no idle warpgroup
                 for (int ng = 1; ng <= 6 && ng <= nl; ++ng) {
                     TileConfig c;

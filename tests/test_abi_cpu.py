@@ -98,21 +98,25 @@ def test_tensor_core_tile_menu(native):
     """The tensor-core kernel's shapes: four or eight rows per step, whole
     warps, at least one warpgroup, one or two horizontal items per thread
     (one-row items at four rows per step, two-row items at four or eight);
+    the 26-neighbour rule (DoG response) has shapes of its own;
     the built-in choice (four rows) leaves exactly one warp free of
     horizontal items (the MMA issuer) and is on the menu."""
     for kw in (dict(n=10, t_min=1, t_max=10), dict(n=16, t_min=1, t_max=12)):
         menu = native.tile_configs(tensor_cores=True, **kw)
         assert len(menu) > 10
         for tx2, ty2, rb, nt, ng, item in menu:
-            assert rb in (4, 8) and nt % 32 == 0 and nt >= 128 and item in (1, 2)
-            assert (rb // item) * tx2 // 4 <= 2 * nt and (item == 2 or rb == 4)
+            assert rb in (4, 8) and nt % 32 == 0 and nt >= 128 and item in (1, 2, 3)
+            rows, cols = (2, 4) if item == 2 else (1, 2) if item == 3 else (1, 4)
+            assert (rb // rows) * tx2 // cols <= 2 * nt and (item == 2 or rb == 4)
         assert any(s[5] == 2 and s[2] == 8 for s in menu)
         chosen = native.chosen_tile(tensor_cores=True, **kw)
         assert chosen in menu and chosen[0] == chosen[3] - 32
-    # the LoG response has tensor-core shapes of its own; the 26-neighbour
-    # rule takes the FFMA kernel (the flag changes nothing for it)
+    # the LoG response and the 26-neighbour rule have tensor-core shapes of
+    # their own; the 26-neighbour rule with the LoG response takes the FFMA
+    # kernel (the flag changes nothing for it)
     assert native.tile_configs(tensor_cores=True, n=16, t_min=1, t_max=12, response=1)
-    kw = dict(n=16, t_min=1, t_max=12, nms=1)
+    assert native.tile_configs(tensor_cores=True, n=16, t_min=1, t_max=12, nms=1)
+    kw = dict(n=16, t_min=1, t_max=12, nms=1, response=1)
     assert not native.tile_configs(tensor_cores=True, **kw)
     assert native.chosen_tile(tensor_cores=True, **kw) == native.chosen_tile(
         tensor_cores=False, **kw)

@@ -83,7 +83,8 @@ def checked_env():
     for _, kw, _ in CASES:
         kw = dict(kw, nms=kw.get("nms", "paper"))
         if "tile_shape" not in kw:   # the shape a Detector takes from the tuned table
-            tc = kw.get("tensor_cores", True) and kw["nms"] == "paper"
+            tc = kw.get("tensor_cores", True) and (kw["nms"] == "paper" or
+                                                   kw.get("response", "dog") == "dog")
             kw["tile_shape"] = tune.lookup(kw["n"], kw["t_min"], kw["t_max"], kw["nms"], sms,
                                            4.0, kw.get("response", "dog"), tensor_cores=tc)
         kws.append(kw)

@@ -191,8 +191,10 @@ def test_tensor_core_pass_is_used_where_it_applies():
     assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1).uses_tensor_cores
     assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
                         tensor_cores=False).uses_tensor_cores
-    assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
-                        nms="local26").uses_tensor_cores
+    assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
+                    nms="local26").uses_tensor_cores
+    assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9, nms="local26",
+                        response="log").uses_tensor_cores
     assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9,
                     response="log").uses_tensor_cores
     assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9, response="log",
