@@ -309,6 +309,16 @@ int mhfd_prune_noalloc(const double *radius, int32_t n_levels, float overlap, co
 int mhfd_device_bytes(mhfd_detector *det, int32_t H, int32_t W, int64_t *fixed_bytes,
                       int64_t *image_bytes);
 
+/* Gives back the device memory a detector grew for the images it has seen:
+ * waits for its work to finish, then frees the per-image scratch (tile
+ * counters, candidate staging, prune grid, plain-path planes, the device
+ * copy of host images, soft-score planes) and any captured batch graph,
+ * keeping what mhfd_create_detector allocated (mhfd_device_bytes' fixed
+ * bytes).  The next detection grows the scratch again.  Results already
+ * read stay valid; a detection enqueued but not yet waited for cannot be
+ * read after this call.  Errors: INVALID_ARG, CUDA. */
+int mhfd_trim(mhfd_detector *det);
+
 /* Tile configurations the fused kernel can be specialised with for the
  * ladder of `p` (autotuner menu): returns their count; if `desc` is not NULL
  * writes up to `cap` rows of six int32 (strip width and tile height, both

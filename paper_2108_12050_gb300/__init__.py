@@ -165,6 +165,11 @@ class Detector:
                                             ctypes.byref(i)))
         return f.value, i.value
 
+    def trim(self):
+        """Give back the per-image device scratch grown so far (waits for the
+        detector's work; the fixed state stays)."""
+        _n.check(_n.lib().mhfd_trim(self._h))
+
     @property
     def uses_tensor_cores(self):
         """Whether the fused kernel's vertical pass runs on the tensor cores."""

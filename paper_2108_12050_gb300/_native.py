@@ -29,7 +29,7 @@ NMS_PAPER, NMS_LOCAL26 = 0, 1
 EXPORTS = [
     "mhfd_default_params", "mhfd_create_detector", "mhfd_destroy_detector", "mhfd_detect",
     "mhfd_result_wait", "mhfd_detect_batch", "mhfd_result_wait_batch", "mhfd_batch_uses_graph",
-    "mhfd_uses_tensor_cores", "mhfd_device_bytes",
+    "mhfd_uses_tensor_cores", "mhfd_device_bytes", "mhfd_trim",
     "mhfd_result_ready", "mhfd_soft_score",
     "mhfd_detect_host", "mhfd_detect_host_async", "mhfd_detect_plain", "mhfd_debug_stack",
     "mhfd_prune", "mhfd_prune_noalloc", "mhfd_tile_configs", "mhfd_chosen_tile", "mhfd_precompile",
@@ -117,6 +117,7 @@ def lib():
         L.mhfd_batch_uses_graph.argtypes = [P]
         L.mhfd_uses_tensor_cores.argtypes = [P]
         L.mhfd_device_bytes.argtypes = [P, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+        L.mhfd_trim.argtypes = [P]
         L.mhfd_result_ready.argtypes = [P]
         L.mhfd_soft_score.argtypes = [P, P, I32, I32, I32, SZ, P, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_float, P, P, P, P, P]

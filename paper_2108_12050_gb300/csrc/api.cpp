@@ -1381,6 +1381,38 @@ int mhfd_result_ready(mhfd_detector *d) {
     return cuda_fail(e, "cudaEventQuery");
 }
 
+int mhfd_trim(mhfd_detector *d) {
+    if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
+    DeviceGuard g(d->device);
+    if (d->ev_done) MHFD_CUDA(cudaEventSynchronize(d->ev_done));
+    // a captured batch graph holds the addresses of the buffers freed here
+    if (d->b.exec) cudaGraphExecDestroy(d->b.exec);
+    d->b.exec = nullptr;
+    d->b.key.clear();
+    void **grown[] = {reinterpret_cast<void **>(&d->tile_count),
+                      reinterpret_cast<void **>(&d->tile_off),
+                      reinterpret_cast<void **>(&d->stage),
+                      reinterpret_cast<void **>(&d->pb.cell_cnt),
+                      reinterpret_cast<void **>(&d->pb.cell_start),
+                      reinterpret_cast<void **>(&d->pI), reinterpret_cast<void **>(&d->pT),
+                      reinterpret_cast<void **>(&d->pL), reinterpret_cast<void **>(&d->pM),
+                      reinterpret_cast<void **>(&d->pD), reinterpret_cast<void **>(&d->pA),
+                      reinterpret_cast<void **>(&d->d_img_copy),
+                      reinterpret_cast<void **>(&d->soft_D)};
+    for (void **p : grown) {
+        if (*p) MHFD_CUDA(cudaFree(*p));
+        *p = nullptr;
+    }
+    d->tiles_cap = 0;
+    d->stage_cap = 0;
+    d->pb.ncells_cap = 0;
+    d->plain_px = 0;
+    d->img_copy_bytes = 0;
+    d->soft_D_px = 0;
+    d->pending = false;
+    return MHFD_OK;
+}
+
 int mhfd_device_bytes(mhfd_detector *d, int32_t H, int32_t W, int64_t *fixed_bytes,
                       int64_t *image_bytes) {
     if (!d || !fixed_bytes || !image_bytes) return fail(MHFD_ERR_INVALID_ARG, "NULL argument");

@@ -150,10 +150,10 @@ class Server:
         return max(0, want - slot["resident"])
 
     def _reset(self, k):
-        """Give a free slot's grown scratch back (fresh detector, no buffer)."""
+        """Give a free slot's grown scratch back (the detector's per-image
+        scratch and the slot's image buffer; its fixed state stays)."""
         slot = self.slots[k]
-        slot["det"].close()
-        slot["det"] = Detector(device=self.device, **self.params)
+        slot["det"].trim()
         slot["buf"] = None
         self.used -= slot["resident"] - self.fixed
         slot["resident"] = self.fixed

@@ -37,8 +37,8 @@ CASES = [
     ("two_row_tc", dict(L16, tile_shape=[256, 18, 8, 288, 4, 2]), (95, 300, 620, "u16")),
     ("two_row_ffma", dict(L16, tensor_cores=False, tile_shape=[320, 18, 4, 448, 4, 2]),
      (95, 300, 620, "u16")),
-    ("two_output_local26", dict(L16, nms="local26", tile_shape=[192, 18, 4, 384, 2, 3]),
-     (92, 260, 333, "u8")),
+    ("two_output_local26_ffma", dict(L16, nms="local26", tensor_cores=False,
+                                     tile_shape=[192, 18, 4, 384, 2, 3]), (92, 260, 333, "u8")),
     ("narrower_than_halo", dict(L16), (96, 90, 40, "u16")),
     ("one_pixel_wide", dict(L4), (97, 40, 1, "u8")),
     ("wide_uint16_range", dict(L16), (98, 180, 260, "u16x9")),

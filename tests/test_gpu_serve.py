@@ -104,14 +104,21 @@ def test_reported_device_bytes_match_the_allocations():
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
     fixed, scratch = det.device_bytes(8192, 8192)
-    det(img)
+    first = det(img)
     torch.cuda.synchronize()
     free2 = torch.cuda.mem_get_info()[0]
+    # trim gives the per-image scratch back; the next detection grows it again
+    det.trim()
+    torch.cuda.synchronize()
+    free3 = torch.cuda.mem_get_info()[0]
+    again = det(img)
     det.close()
     got_fixed, got_scratch = free0 - free1, free1 - free2
-    print("device bytes: fixed %d reported / %d measured; image scratch %d / %d" % (
-        fixed, got_fixed, scratch, got_scratch))
+    print("device bytes: fixed %d reported / %d measured; image scratch %d / %d; "
+          "trim returned %d" % (fixed, got_fixed, scratch, got_scratch, free3 - free2))
     slack = 32 << 20
     assert abs(got_fixed - fixed) <= slack
     assert abs(got_scratch - scratch) <= slack
     assert scratch > 2 * 8192 * 8192 * 0.9        # the 2 B/px candidate staging
+    assert abs((free3 - free2) - scratch) <= slack
+    assert again.n_blobs == first.n_blobs and np.array_equal(again.blobs, first.blobs)
