@@ -457,6 +457,21 @@ def main():
               "median_ms_paper_protocol": statistics.median(paper_ms),
               "clocks": clk.summary()}
     print("# detail " + json.dumps(detail), flush=True)
+    line = headline_line(
+        value=value, world=world, steps=args.steps, warmup=args.warmup, total_ms=total_ms,
+        p50=statistics.median(per_tile), p99=p99, plain=plain, achieved=achieved, peak=peak,
+        traffic=traffic, k_avg=k_avg, side=side if tc else None, cpu=cpu, e2e=e2e,
+        launches=launches_per_tile * len(tiles) * args.steps,
+        clocks={k: v for k, v in clk.summary().items() if k != "samples"}, scores=scores,
+        summary=summary_of(batched, serving, soft_sec, variants))
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def summary_of(batched, serving, soft_sec, variants):
+    """The headline line's digest of the long sections (they are printed in
+    full on the detail line)."""
     summary = {}
     if batched:
         summary["batch256"] = {"tiles_s": r4(batched["tiles_per_s"]),
@@ -474,34 +489,40 @@ def main():
     if variants:
         summary["variant_frac"] = {k[6:]: r4(v["roofline"]["frac"]) for k, v in variants.items()
                                    if "roofline" in v}
-    line = {
+    return summary
+
+
+def headline_line(*, value, world, steps, warmup, total_ms, p50, p99, plain, achieved, peak,
+                  traffic, k_avg, side, cpu, e2e, launches, clocks, scores, summary):
+    """The result line (the last line bench.py prints): the contract's keys,
+    latency, the plain path, the roofline of the fused kernel, the CPU
+    baseline, end to end, and the summary; short enough (under 1500
+    characters) that a reader keeping the tail of the output keeps all of
+    it."""
+    return {
         "metric": METRIC, "value": r4(value), "unit": METRIC, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r4(total_ms / args.steps),
+        "steps": steps, "warmup": warmup, "ms_per_step": r4(total_ms / steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "inputs > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "p50_ms_per_tile": r4(statistics.median(per_tile)), "p99_ms_per_tile": r4(p99),
+        "p50_ms_per_tile": r4(p50), "p99_ms_per_tile": r4(p99),
         "plain": {"value": r4(plain["value"]), "p50_ms_per_tile": r4(plain["p50_ms_per_tile"])}
                  if plain else None,
         "fused_vs_plain": r4(value / world / plain["value"]) if plain else None,
         "roofline": {"bound": "alu", "achieved": r4(achieved), "peak": r4(peak),
                      "unit": "Tops/s FP32", "frac": r4(achieved / peak),
                      "traffic": traffic, "kernel_ms_avg": r4(k_avg),
-                     "ffma_side_frac": r4(side / peak) if tc else None},
+                     "ffma_side_frac": r4(side / peak) if side is not None else None},
         "cpu_baseline": {k: r4(v) if isinstance(v, float) else v for k, v in cpu.items()
                          if k != "single_core"} if cpu else None,
-        "e2e": {k: r4(v) if isinstance(v, float) else v
-                                     for k, v in e2e.items()},
-        "gpu_launches": launches_per_tile * len(tiles) * args.steps,
-        "clocks": {k: v for k, v in clk.summary().items() if k != "samples"},
+        "e2e": {k: r4(v) if isinstance(v, float) else v for k, v in e2e.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
         "focus_scores": [int(x) for x in scores],
         "focus_monotone_drop": all(scores[j] > scores[j + 1] for j in range(len(scores) - 1)),
         "summary": summary,
     }
-    print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
 
 
 def bench_variants(mhfd, torch, stream, tile, reps=5):
