@@ -189,6 +189,10 @@ def main():
     ap.add_argument("--response", default="dog", choices=["dog", "log"])
     ap.add_argument("--tensor-cores", action="store_true",
                     help="tune the tensor-core kernel (its own shape menu)")
+    ap.add_argument("--heights", default="",
+                    help="tile heights (incl. the 2 border rows) to try for every candidate, "
+                         "e.g. 10,14,18: the tiles of an image are split evenly over the "
+                         "resident blocks, so the height sets how evenly")
     ap.add_argument("--write", action="store_true", help="record the winner in tuned_tiles.json")
     args = ap.parse_args()
     nms = 0 if args.nms == "paper" else 1
@@ -211,6 +215,9 @@ def main():
                                  response=args.response,
                                  items=[int(v) for v in args.items.split(",")])
         cands += [c for c in extra if c not in cands]
+    if args.heights:
+        hs = [int(v) for v in args.heights.split(",")]
+        cands = list(dict.fromkeys(tuple(c[:1]) + (h,) + tuple(c[2:]) for c in cands for h in hs))
     t0 = time.time()
     comp = precompile_all(args.n, args.tmin, args.tmax, nms, cands, response=args.response,
                           tensor_cores=args.tensor_cores)
