@@ -140,7 +140,7 @@ class Detector:
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
                 is_log = response in ("log", 1)
                 tc = bool(tensor_cores) and (nms in ("paper", 0) or not is_log)
-                tile_shape = tune.lookup(n, t_min, t_max, nms, sms, truncate,
+                tile_shape = None if tensor_cores == 2 else tune.lookup(n, t_min, t_max, nms, sms, truncate,
                                          "log" if is_log else "dog", tensor_cores=tc)
         tile_override = tile_override or 0
         self.n = int(n)

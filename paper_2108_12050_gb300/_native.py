@@ -183,7 +183,7 @@ def make_params(n=10, t_min=1.0, t_max=10.0, sigmas=None, threshold=0.1, overlap
         boundary = {"reflect": 0, "periodic": 1}[boundary]
     p.response = int(response)
     p.boundary = int(boundary)
-    p.tensor_cores = 1 if tensor_cores else 0
+    p.tensor_cores = 2 if tensor_cores == 2 else (1 if tensor_cores else 0)
     p._keepalive = keep
     return p
 

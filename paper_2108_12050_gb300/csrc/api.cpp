@@ -206,8 +206,8 @@ int validate_params(const mhfd_params &p) {
         return fail(MHFD_ERR_INVALID_ARG, "response must be MHFD_RESPONSE_DOG or MHFD_RESPONSE_LOG");
     if (p.boundary != MHFD_BOUNDARY_REFLECT && p.boundary != MHFD_BOUNDARY_PERIODIC)
         return fail(MHFD_ERR_INVALID_ARG, "boundary must be reflect or periodic");
-    if (p.tensor_cores != 0 && p.tensor_cores != 1)
-        return fail(MHFD_ERR_INVALID_ARG, "tensor_cores must be 0 or 1");
+    if (p.tensor_cores < 0 || p.tensor_cores > 2)
+        return fail(MHFD_ERR_INVALID_ARG, "tensor_cores must be 0, 1 or 2");
     return MHFD_OK;
 }
 
@@ -328,6 +328,7 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
     h.thr = d->p.threshold;
     h.gate = gate;
     h.flag = &d->cnt->ktimeout;
+    h.t2tab = v->t2tab;
     std::memcpy(pb, &h, sizeof(h));
     void *args[] = {pb};
     // one resident wave: every block marches down an equal share of tiles
@@ -485,6 +486,17 @@ void fused_ladder(const mhfd_params &p, const std::vector<double> &t, const std:
 int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, TileConfig *cfg,
                  bool tc = false) {
     std::string why;
+    if (tc && p.tensor_cores == 2 && t2_mode_ok(mode)) {
+        // both blur passes on the tensor cores; tile_shape[0] picks the strip width
+        if (p.tile_shape[0] > 0) {
+            *cfg = t2_config((int)R.size(), p.tile_shape[0]);
+            if (!t2_shape_ok(R, mode, *cfg, &why))
+                return fail(MHFD_ERR_UNSUPPORTED, "tile_shape (two-pass kernel): " + why);
+            return MHFD_OK;
+        }
+        if (!choose_tile_t2(R, mode, cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+        return MHFD_OK;
+    }
     if (tc) {
         if (p.tile_shape[0] > 0) {
             const int *ts = p.tile_shape;
@@ -664,6 +676,7 @@ int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long lo
         h.chunk = batch_chunk(d);
         h.gate = d->use_tc ? (k == 0 ? 1 : 2) : 0;
         h.flag = &d->cnt->ktimeout;
+        h.t2tab = v->t2tab;
         std::memcpy(pv.data(), &h, sizeof(h));
         void *args[] = {pv.data()};
         const long long wave = (long long)sms * v->occupancy;
@@ -1439,7 +1452,7 @@ int mhfd_device_bytes(mhfd_detector *d, int32_t H, int32_t W, int64_t *fixed_byt
 
 int mhfd_uses_tensor_cores(mhfd_detector *d) {
     if (!d) return fail(MHFD_ERR_INVALID_ARG, "NULL detector");
-    return d->use_tc ? 1 : 0;
+    return d->use_tc ? d->cfg_tc.tc : 0;
 }
 
 int mhfd_batch_uses_graph(mhfd_detector *d) {

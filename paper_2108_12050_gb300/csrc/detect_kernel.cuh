@@ -69,7 +69,10 @@ constexpr bool STORE = (MHFD_STORE) != 0;
 #ifndef MHFD_VTC
 #define MHFD_VTC 0
 #endif
-constexpr bool TC = (MHFD_VTC) != 0;
+constexpr bool TC = (MHFD_VTC) == 1;
+// Both blur passes on the tensor cores (MHFD_VTC 2, "two-pass kernel" below):
+// the paper rule with the DoG response, integer images.
+constexpr bool TC2 = (MHFD_VTC) == 2;
 // Rows per horizontal item: 1 (four outputs of one row), or 2 (four
 // outputs of each of two adjacent rows; the V rows of a step are then
 // stored pair-interleaved, column by column, so that one float4 load holds
@@ -277,8 +280,74 @@ MK_HD constexpr int tc_tcols() {
 }
 constexpr int TC_TCOLS = tc_tcols();
 constexpr int TC_CTRL = TC ? 128 : 0;  // mbarriers (one per group) and the TMEM address
+
+// Two-pass kernel geometry: tiles of T2M computed rows (TY outputs and their
+// two NMS neighbours) by TX2 computed columns.  Level l reads window rows
+// [k0, k0 + KV) (K of its vertical product) and window columns [j0, j0 + NV)
+// (its V columns, N of the vertical product, from an 8-aligned column: the
+// horizontal product's column k is V column k + off); its horizontal product
+// has K = KH window columns, of which the first TX2 + 2 R_l are used.
+constexpr int T2M = 128;
+MK_HD constexpr int t2_k0(int l) { return RMAX - kR(l); }
+MK_HD constexpr int t2_j0(int l) { return (RMAX - kR(l)) & ~7; }
+MK_HD constexpr int t2_off(int l) { return (RMAX - kR(l)) & 7; }
+MK_HD constexpr int t2_need(int l) { return TX2 + 2 * kR(l); }
+MK_HD constexpr int t2_kv(int l) { return (T2M + 2 * kR(l) + 15) & ~15; }
+MK_HD constexpr int t2_nv(int l) { return (t2_off(l) + t2_need(l) + 15) & ~15; }
+MK_HD constexpr int t2_kh(int l) { return (t2_need(l) + 15) & ~15; }
+// blocks of 8 x 8 taps of level l's banded tap matrix (both products)
+MK_HD constexpr int t2_s(int l) { return t2_kv(l) / 8 + 15; }
+MK_HD constexpr int t2_maxf(int which) {
+    int m = 0;
+    for (int l = 0; l < NL; ++l) {
+        const int v = which == 0   ? t2_nv(l)
+                      : which == 1 ? t2_kh(l)
+                      : which == 2 ? t2_s(l)
+                      : which == 3 ? t2_k0(l) + t2_kv(l)
+                                   : t2_j0(l) + t2_nv(l);
+        m = v > m ? v : m;
+    }
+    return m;
+}
+constexpr int T2_NVMAX = t2_maxf(0);
+constexpr int T2_KHMAX = t2_maxf(1);
+constexpr int T2_SMAX = t2_maxf(2);
+constexpr int T2_XIMG_R = T2M + 2 * RMAX;   // window rows holding image rows
+constexpr int T2_XIMG_C = TX2 + 2 * RMAX;   // window columns holding image columns
+constexpr int T2_XR = t2_maxf(3) > T2_XIMG_R ? t2_maxf(3) : T2_XIMG_R;  // + zero rows the K padding reads
+constexpr int T2_XC = ((t2_maxf(4) > T2_XIMG_C ? t2_maxf(4) : T2_XIMG_C) + 7) & ~7;
+// column group stride: 16 mod 128, so that eight lanes storing consecutive
+// groups of one row hit distinct banks
+constexpr int T2_XGSTR = ((16 * T2_XR + 127) / 128) * 128 + 16;
+constexpr int T2_X_BYTES = TC2 ? (T2_XC / 8) * T2_XGSTR : 0;
+constexpr int T2_TAB_PART = T2_SMAX * 128;  // one part (hi or lo) of a tap matrix
+constexpr int T2_SBO_H = (T2_KHMAX / 8) * 128;
+constexpr int T2_AH_PART = (T2M / 8) * T2_SBO_H;  // one part of the split V rows
+constexpr int T2_MS = TX2 + 1;                   // row stride of the tile's max plane
+constexpr int T2_OFF_TAB = (T2_X_BYTES + 127) & ~127;
+constexpr int T2_NTAB = 4;                       // tap-matrix buffers (levels l - 1 .. l + 2)
+constexpr int T2_OFF_AH = T2_OFF_TAB + (TC2 ? T2_NTAB * 2 * T2_TAB_PART : 0);
+constexpr int T2_OFF_CTRL = T2_OFF_AH + (TC2 ? 2 * T2_AH_PART : 0);
+// control block: mbarriers, tensor-memory address, fail flag, scan buffer,
+// the window's column map
+constexpr int T2_SMEM = T2_OFF_CTRL + 512 + 4 * ((T2_XC + 3) & ~3);
+constexpr int T2_NW = NT - 32;                    // worker threads (the last warp issues)
+constexpr int T2_DH = 2 * T2_NVMAX;               // tensor-memory column of the L buffers
+constexpr int T2_LP = T2_DH + 2 * TX2;            // of the previous level's L (one copy)
+
 constexpr int SMEM_BYTES =
-    TC_WIN_BYTES + TC_B_BYTES + 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64 + TC_CTRL;
+    TC2 ? T2_SMEM
+        : TC_WIN_BYTES + TC_B_BYTES + 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64 +
+              TC_CTRL;
+static_assert(!TC2 || (MODE == 0 && !LOG), "two-pass kernel: paper rule, DoG response");
+static_assert(!TC2 || (TX2 % 16 == 0 && TX2 >= 16 && TX2 <= 128 && MHFD_TY2 == T2M && NT == 288),
+              "two-pass kernel geometry: 16-multiple strips up to 128, tiles of 128 rows, 288 threads");
+static_assert(!TC2 || T2_LP + TX2 <= 512, "two-pass kernel: tensor memory columns");
+static_assert(!TC2 || T2_NVMAX <= 256, "two-pass kernel: N of the vertical product");
+// after the max plane and argmax plane: the NMS chunk ballots
+constexpr int T2_MASKS = ((T2M * T2_MS * 4 + T2M * TX2) + 15) & ~15;
+constexpr int T2_NCHUNK = (TY * TX + 31) / 32;
+static_assert(!TC2 || T2_MASKS + 4 * T2_NCHUNK <= 2 * T2_AH_PART, "two-pass kernel: max plane");
 
 static_assert(TX2 % 4 == 0, "tile width must be a multiple of 4");
 static_assert(TY >= 1, "tile height");
@@ -1750,6 +1819,699 @@ __device__ __forceinline__ void march_tc(const MhfdKHeader &h, const MhfdStretch
     }
 }
 
+#if MHFD_VTC == 2
+// ------------------------------------------------- two-pass kernel (TC2)
+//
+// Both separable blur passes are tensor-core products, on tiles of T2M = 128
+// computed rows (the TY output rows and their two NMS neighbours) by TX2
+// computed columns.  The window X holds the tile's input rows and columns
+// with a halo of RMAX on every side as exact fp16 integers x = clamp(v, lo,
+// hi) - c0 (MN-major: column group cg of 8 columns at cg * T2_XGSTR, row r at
+// + 16 r).  Per level l (all levels of §2.2's ladder, in order):
+//   vertical    V_l[m, c'] = sum_k G_l[m, k] X[k0 + k, j0 + c']: A = the
+//               level's banded tap matrix (taps g_l[|k - m - R_l|] scaled by
+//               T2_S and split into fp16 hi + lo parts), M = 128 rows in
+//               reverse order, K-major; B = the window, MN-major; N = the V
+//               columns; f32 accumulators in tensor memory;
+//   split       the f32 V_l into fp16 hi + lo parts (hi: V with its low 13
+//               mantissa bits cleared, exact in fp16; lo = V - hi), written
+//               as rows m by columns k = c' - off (K-major) to shared memory;
+//   horizontal  L_l[m, c] = sum_k V_l[m, k] T_l[k, c], T_l[k, c] = g_l[|k - c -
+//               R_l|]: A = the split rows, B = the same banded tap matrix,
+//               N = TX2 computed columns in reverse order; the products hi x
+//               hi, hi x lo and lo x hi;
+//   epilogue    D_{l-1} = t_{l-1} (L_l - L_{l-1}) (Eq. 2) and the running max
+//               over scales with its first argmax (Eq. 3), per pixel in
+//               registers.
+// A banded tap matrix is Toeplitz: with the M (or N) index reversed, an 8 x 8
+// block of it depends only on the sum of its block row and column, so one
+// column of T2_SMAX blocks, addressed with equal leading and stride offsets
+// (128 bytes), serves every M tile and K step of both products.
+// The last warp issues the MMAs (one elected lane of a converged warp: the
+// descriptors stay warp-uniform); the other 8 warps (workers) split, build
+// the tap matrices of the level after next, form the responses and run the
+// NMS and compaction of the tile.  Handoffs go through mbarriers:
+//   VB[b] / HB[b]  vertical / horizontal products of a level done (commit),
+//   SPL            a level's split done (8 worker warps),
+//   XR             the next tile's window and first two tap matrices ready.
+// Level l of the block's g-th level overall uses V buffer (g mod 2), L buffer
+// (g mod 2) and tap-matrix buffer (g mod 3): the tensor core runs level l's
+// horizontal product and level l + 2's vertical one while the workers split
+// level l + 1, so every buffer is free when it is written.  All waits are
+// bounded (2 s of global time); a wait that gives up sets h.flag and makes
+// every later wait of the block return at once.
+
+constexpr float T2_S = 16.0f;  // tap scale: |V| <= 2048 * 16 fits fp16
+
+// Per-level constants, read at run time from constant memory: the level
+// loop is not unrolled (17 unrolled levels overflowed the instruction cache).
+struct T2Lev {
+    int r, kv16, nv, kh16, off, need, j0, k0, s, toff;
+    float tsc;  // t of the response layer this level closes (level - 1)
+};
+struct T2Levs {
+    T2Lev v[NL];
+};
+MK_HD constexpr T2Levs t2_levs() {
+    T2Levs t{};
+    for (int l = 0; l < NL; ++l)
+        t.v[l] = T2Lev{kR(l),       t2_kv(l) / 16, t2_nv(l), t2_kh(l) / 16, t2_off(l), t2_need(l),
+                       t2_j0(l),    t2_k0(l),      t2_s(l),  tapoff(l),     l > 0 ? kTsc(l - 1) : 0.0f};
+    return t;
+}
+__constant__ T2Levs mk_t2_levs = t2_levs();
+MK_HD constexpr int t2_kv16max() {
+    int m = 0;
+    for (int l = 0; l < NL; ++l) m = t2_kv(l) / 16 > m ? t2_kv(l) / 16 : m;
+    return m;
+}
+constexpr int T2_CP = (T2_NW / 32) / 4;  // column parts: worker warps per tensor-memory lane group
+constexpr int T2_CQ = TX2 / T2_CP;       // L columns of a worker thread
+
+// the block's dynamic shared memory (the same array as the kernel's)
+extern __shared__ __align__(16) unsigned char mk_t2_smem[];
+struct T2State {
+    unsigned tmem;      // tensor-memory base (lane 0, column 0)
+    unsigned ph;        // mbarrier parities: VB0 VB1 HB0 HB1 (workers), SPL XR (issuer)
+    unsigned g;         // levels run by this block so far
+    // shared-memory regions: window, tap matrices, split rows, control block
+    __device__ __forceinline__ unsigned char *xp() const { return mk_t2_smem; }
+    __device__ __forceinline__ unsigned char *tabp() const { return mk_t2_smem + T2_OFF_TAB; }
+    __device__ __forceinline__ unsigned char *ahp() const { return mk_t2_smem + T2_OFF_AH; }
+    __device__ __forceinline__ unsigned char *ctrl() const { return mk_t2_smem + T2_OFF_CTRL; }
+    __device__ __forceinline__ unsigned x() const { return smem_addr(xp()); }
+    __device__ __forceinline__ unsigned tab() const { return smem_addr(tabp()); }
+    __device__ __forceinline__ unsigned ah() const { return smem_addr(ahp()); }
+    __device__ __forceinline__ int *scan() const { return reinterpret_cast<int *>(ctrl() + 128); }
+    __device__ __forceinline__ int *cmap() const { return reinterpret_cast<int *>(ctrl() + 512); }
+    __device__ __forceinline__ volatile int *fail() const {
+        return reinterpret_cast<volatile int *>(ctrl() + 100);
+    }
+};
+__device__ __forceinline__ unsigned t2_bar(const T2State &t, int i) { return smem_addr(t.ctrl()) + 8u * i; }
+// mbarriers: VB0 VB1 HB0 HB1 (product commits), SPL and XR (worker warps),
+// TB0..TB3 (tap-matrix copies into buffer 0..3)
+enum { T2_VB = 0, T2_HB = 2, T2_SPL = 4, T2_XRB = 5, T2_TB = 6 };
+
+__device__ __forceinline__ void t2_wait(const MhfdKHeader &h, T2State &t, int i) {
+    const unsigned bar = t2_bar(t, i), par = (t.ph >> i) & 1u;
+    t.ph ^= 1u << i;
+    if (tc_try(bar, par) || *t.fail()) return;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+#pragma unroll 1
+        for (int k = 0; k < 256; ++k)
+            if (tc_try(bar, par)) return;
+        if (*t.fail()) return;
+        if (gtimer() - t0 > 2000000000ull) break;
+    }
+    *t.fail() = 1;
+    if (h.flag) atomicOr(h.flag, 1);
+}
+
+__device__ __forceinline__ void t2_mma(unsigned d, unsigned long long a, unsigned long long b,
+                                       unsigned idesc, unsigned acc) {
+    asm volatile(
+        "{\n.reg .pred q, e;\nsetp.ne.b32 q, %4, 0;\nelect.sync _|e, 0xffffffff;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// the same with the descriptors formed inside the statement (base + constant
+// offsets): unrolled K loops then keep only the two bases in registers
+template <unsigned long long OA, unsigned long long OB, unsigned ACC>
+__device__ __forceinline__ void t2_mma_o(unsigned d, unsigned long long a0, unsigned long long b0,
+                                         unsigned idesc) {
+    asm volatile(
+        "{\n.reg .pred q, e;\n.reg .b64 a, b;\nadd.u64 a, %1, %4;\nadd.u64 b, %2, %5;\n"
+        "setp.ne.b32 q, %6, 0;\nelect.sync _|e, 0xffffffff;\n"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n}\n" ::"r"(d),
+        "l"(a0), "l"(b0), "r"(idesc), "n"(OA), "n"(OB), "n"(ACC)
+        : "memory");
+}
+// K steps KK .. NKMAX - 1 of a product, those below nk issued (a warp-uniform
+// branch per step; the offsets stay compile-time constants)
+template <int KK, int NKMAX>
+struct T2VK {  // vertical: (hi, window), (lo, window)
+    static __device__ __forceinline__ void run(unsigned d, unsigned long long a0, unsigned long long b0,
+                                               unsigned id, int nk) {
+        if constexpr (KK < NKMAX) {
+            if (KK < nk) {
+                t2_mma_o<(unsigned long long)(KK * 16), (unsigned long long)(KK * 16), KK ? 1u : 0u>(d, a0, b0,
+                                                                                                   id);
+                t2_mma_o<(unsigned long long)(KK * 16 + (T2_TAB_PART >> 4)), (unsigned long long)(KK * 16),
+                         1u>(d, a0, b0, id);
+                T2VK<KK + 1, NKMAX>::run(d, a0, b0, id, nk);
+            }
+        }
+    }
+};
+template <int KK, int NKMAX>
+struct T2HK {  // horizontal: hi x hi, hi x lo, lo x hi
+    static __device__ __forceinline__ void run(unsigned d, unsigned long long a0, unsigned long long b0,
+                                               unsigned id, int nk) {
+        if constexpr (KK < NKMAX) {
+            if (KK < nk) {
+                t2_mma_o<(unsigned long long)(KK * 16), (unsigned long long)(KK * 16), KK ? 1u : 0u>(d, a0, b0,
+                                                                                                   id);
+                t2_mma_o<(unsigned long long)(KK * 16), (unsigned long long)(KK * 16 + (T2_TAB_PART >> 4)),
+                         1u>(d, a0, b0, id);
+                t2_mma_o<(unsigned long long)(KK * 16 + (T2_AH_PART >> 4)), (unsigned long long)(KK * 16),
+                         1u>(d, a0, b0, id);
+                T2HK<KK + 1, NKMAX>::run(d, a0, b0, id, nk);
+            }
+        }
+    }
+};
+__device__ __forceinline__ void t2_commit(unsigned bar) {
+    asm volatile(
+        "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(bar)
+        : "memory");
+}
+// one arrival per worker warp, after every lane's shared-memory writes (made
+// visible to the tensor core) and tensor-memory reads
+__device__ __forceinline__ void t2_arrive(unsigned bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0)
+        asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar)
+                     : "memory");
+}
+__device__ __forceinline__ void t2_wsync() { asm volatile("bar.sync 1, %0;" ::"n"(T2_NW) : "memory"); }
+
+__device__ __forceinline__ unsigned t2_tabb(const T2State &t, unsigned gl) {
+    return t.tab() + (gl % (unsigned)T2_NTAB) * (unsigned)(2 * T2_TAB_PART);
+}
+// Copy level l's tap matrices (built once per detector in global memory by
+// mhfd_t2_tables) into buffer gl mod T2_NTAB with the bulk-copy engine; the
+// buffer's mbarrier completes when the bytes have landed.
+__device__ __forceinline__ void t2_fetch_tab(const MhfdKHeader &h, const T2State &t, int l, unsigned gl) {
+    const unsigned b = gl % (unsigned)T2_NTAB;
+    const unsigned bar = t2_bar(t, T2_TB + (int)b);
+    const unsigned dst = t2_tabb(t, gl);
+    const char *src = reinterpret_cast<const char *>(h.t2tab) + (long long)l * (2 * T2_TAB_PART);
+    asm volatile(
+        "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+        "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+        "@e cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%2], [%3], %1, [%0];\n}\n" ::"r"(bar),
+        "n"(2 * T2_TAB_PART), "r"(dst), "l"(src)
+        : "memory");
+}
+
+// vertical product of level l into V buffer column dcol
+__device__ __forceinline__ void t2_issue_v(const T2State &t, int l, unsigned tabb, unsigned dcol) {
+    const T2Lev &lv = mk_t2_levs.v[l];
+    const unsigned id =
+        (1u << 4) | (1u << 16) | ((unsigned)(lv.nv >> 3) << 17) | ((unsigned)(T2M >> 4) << 24);
+    const unsigned long long a0 = tc_desc(tabb, 128u, 128u);
+    const unsigned long long b0 =
+        tc_desc(t.x() + (unsigned)((lv.j0 / 8) * T2_XGSTR + lv.k0 * 16), 128u, (unsigned)T2_XGSTR);
+    // unrolled with constant descriptor offsets: the issue keeps the tensor
+    // core's pace (a rolled loop issued one MMA per ~70 cycles on GB300)
+    T2VK<0, t2_kv16max()>::run(t.tmem + dcol, a0, b0, id, lv.kv16);
+}
+// horizontal product of level l into L buffer column dcol
+__device__ __forceinline__ void t2_issue_h(const T2State &t, int l, unsigned tabb, unsigned dcol) {
+    constexpr unsigned ID = (1u << 4) | ((unsigned)(TX2 >> 3) << 17) | ((unsigned)(T2M >> 4) << 24);
+    constexpr int BOFF = 16 - TX2 / 8;  // reversed N: block row + column - BOFF = 15 at the diagonal
+    const unsigned long long a0 = tc_desc(t.ah(), 128u, (unsigned)T2_SBO_H);
+    const unsigned long long b0 = tc_desc(tabb + BOFF * 128, 128u, 128u);
+    T2HK<0, T2_KHMAX / 16>::run(t.tmem + dcol, a0, b0, ID, mk_t2_levs.v[l].kh16);
+}
+
+// The banded tap matrix of level l: block s, row a, column b holds
+// g_l[|8 s + a + b - 127 - R_l|] * T2_S (0 beyond R_l), hi part then lo part.
+__device__ __forceinline__ void t2_build_tab(unsigned char *tab, int l, int wt) {
+    const T2Lev &lv = mk_t2_levs.v[l];
+    const int R = lv.r, S = lv.s, toff = lv.toff;
+#pragma unroll 1
+    for (int it = wt; it < S * 8; it += T2_NW) {
+        const int s = it >> 3, a = it & 7;
+        unsigned hi[4], lo[4];
+#pragma unroll
+        for (int b = 0; b < 8; b += 2) {
+            unsigned short h2[2], l2[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                int d = 8 * s + a + b + e - 127 - R;
+                d = d < 0 ? -d : d;
+                const float v = d <= R ? mk_taps_rt[toff + d] * T2_S : 0.0f;
+                h2[e] = f2h_rn(v);
+                l2[e] = f2h_rn(v - h2f(h2[e]));
+            }
+            hi[b >> 1] = (unsigned)h2[0] | ((unsigned)h2[1] << 16);
+            lo[b >> 1] = (unsigned)l2[0] | ((unsigned)l2[1] << 16);
+        }
+        if (mk_ok(s < T2_SMAX)) {
+            *reinterpret_cast<uint4 *>(tab + s * 128 + a * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(tab + T2_TAB_PART + s * 128 + a * 16) =
+                make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned t2_pack(float lo_half, float hi_half) {
+    unsigned r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi_half), "f"(lo_half));
+    return r;
+}
+
+// Split of level l: V buffer column dcol (tensor memory, lane = row) into the
+// hi and lo rows of the horizontal product's A operand.  Worker warp w takes
+// lanes 32 (w mod 4) .. + 31 and part w / 4 of the 8-column blocks.  OFF
+// (the level's V column of A column 0) selects registers, so it is a
+// template parameter; t2_split dispatches on it.
+template <int OFF>
+__device__ __forceinline__ void t2_split_o(const T2State &t, unsigned dcol, int kb, int need, int wt) {
+    const int w = wt >> 5, g = w & 3, q = w >> 2;
+    const int row = 32 * g + (wt & 31);
+    const unsigned taddr = t.tmem + ((unsigned)(32 * g) << 16) + dcol;
+    unsigned char *dst = t.ahp() + (row >> 3) * T2_SBO_H + (row & 7) * 16;
+    const int jb = q * kb / T2_CP, je = (q + 1) * kb / T2_CP;
+#pragma unroll 1
+    for (int j = jb; j < je; ++j) {
+        unsigned r0[8], r1[8];
+        tc_ld8(taddr + (unsigned)(8 * j), r0);
+        if constexpr (OFF != 0) tc_ld8(taddr + (unsigned)(8 * j + 8), r1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 8; e += 4) {
+            asm volatile("" : "+r"(r0[e]), "+r"(r0[e + 1]), "+r"(r0[e + 2]), "+r"(r0[e + 3]));
+            if constexpr (OFF != 0)
+                asm volatile("" : "+r"(r1[e]), "+r"(r1[e + 1]), "+r"(r1[e + 2]), "+r"(r1[e + 3]));
+        }
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(OFF + e < 8 ? r0[OFF + e] : r1[(OFF + e) & 7]);
+        if (8 * j + 8 > need) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (8 * j + e >= need) v[e] = 0.0f;
+        }
+        unsigned hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const float h0 = __uint_as_float(__float_as_uint(v[e]) & 0xFFFFE000u);
+            const float h1 = __uint_as_float(__float_as_uint(v[e + 1]) & 0xFFFFE000u);
+            hi[e >> 1] = t2_pack(h0, h1);
+            lo[e >> 1] = t2_pack(v[e] - h0, v[e + 1] - h1);
+        }
+        if (mk_ok(j < T2_KHMAX / 8 && row < T2M)) {
+            *reinterpret_cast<uint4 *>(dst + j * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(dst + T2_AH_PART + j * 128) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+__device__ __forceinline__ void t2_split(const T2State &t, int l, unsigned dcol, int wt) {
+    const T2Lev &lv = mk_t2_levs.v[l];
+    const int kb = 2 * lv.kh16, need = lv.need;
+    switch (lv.off) {
+        case 0: t2_split_o<0>(t, dcol, kb, need, wt); break;
+        case 1: t2_split_o<1>(t, dcol, kb, need, wt); break;
+        case 2: t2_split_o<2>(t, dcol, kb, need, wt); break;
+        case 3: t2_split_o<3>(t, dcol, kb, need, wt); break;
+        case 4: t2_split_o<4>(t, dcol, kb, need, wt); break;
+        case 5: t2_split_o<5>(t, dcol, kb, need, wt); break;
+        case 6: t2_split_o<6>(t, dcol, kb, need, wt); break;
+        default: t2_split_o<7>(t, dcol, kb, need, wt); break;
+    }
+}
+
+// per-thread state of the responses: T2_CQ computed columns of one row
+struct T2Px {
+    float mx[T2_CQ];          // running max over scales
+    unsigned ag[T2_CQ / 4];   // its first argmax, one byte per column
+};
+__device__ __forceinline__ int t2_ag(const T2Px &px, int u) { return (px.ag[u >> 2] >> (8 * (u & 3))) & 0xFF; }
+struct T2Tile {
+    int oy, ox;   // first output row / column of the tile
+};
+
+// Epilogue of level l: L buffer column dcol into the responses.  The
+// thread's row is lane 32 (w mod 4) + lane (computed row 127 - that), its
+// columns part w / 4 of the reversed columns.
+__device__ __forceinline__ void t2_epi(const MhfdKHeader &h, const T2State &t, int l, unsigned dcol, int wt,
+                                       T2Px &px, float sc, const T2Tile &tl) {
+    const int w = wt >> 5, g = w & 3, q = w >> 2;
+    const unsigned taddr = t.tmem + ((unsigned)(32 * g) << 16) + dcol + (unsigned)(T2_CQ * q);
+    // the previous level's L: a copy in tensor memory (column T2_LP + the
+    // same offset), replaced by this level's
+    const unsigned paddr = t.tmem + ((unsigned)(32 * g) << 16) + (unsigned)(T2_LP + T2_CQ * q);
+    const bool first = l == 0, last = l + 1 == NL;
+    const int I = l - 1;
+    const float ts = mk_t2_levs.v[l].tsc * sc;
+    constexpr int EC = 4;  // columns per load round
+    static_assert(T2_CQ % EC == 0, "whole load rounds");
+#pragma unroll
+    for (int i0 = 0; i0 < T2_CQ; i0 += EC) {
+        unsigned r[EC], rp[EC];
+        tc_ld4(taddr + (unsigned)i0, r);
+        tc_ld4(paddr + (unsigned)i0, rp);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < EC; e += 4) {
+            asm volatile("" : "+r"(r[e]), "+r"(r[e + 1]), "+r"(r[e + 2]), "+r"(r[e + 3]));
+            asm volatile("" : "+r"(rp[e]), "+r"(rp[e + 1]), "+r"(rp[e + 2]), "+r"(rp[e + 3]));
+        }
+        if (!last) {
+#pragma unroll
+            for (int e = 0; e < EC; e += 4)
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                                 paddr + (unsigned)(i0 + e)),
+                             "r"(r[e]), "r"(r[e + 1]), "r"(r[e + 2]), "r"(r[e + 3])
+                             : "memory");
+        }
+        if (first) {
+#pragma unroll
+            for (int e = 0; e < EC; ++e) px.mx[i0 + e] = -__int_as_float(0x7f800000);
+#pragma unroll
+            for (int e = 0; e < EC; e += 4) px.ag[(i0 + e) >> 2] = 0;
+        } else {
+#pragma unroll
+            for (int e = 0; e < EC; ++e) {
+                const int u = i0 + e;
+                const float d = ts * (__uint_as_float(r[e]) - __uint_as_float(rp[e]));
+                if (d > px.mx[u]) {
+                    px.mx[u] = d;
+                    px.ag[u >> 2] = (px.ag[u >> 2] & ~(0xFFu << (8 * (u & 3)))) | ((unsigned)I << (8 * (u & 3)));
+                }
+                if (STORE) {
+                    const int m = T2M - 1 - (32 * g + (wt & 31));
+                    const int c = TX2 - 1 - (T2_CQ * q + u);
+                    const int gy = tl.oy - 1 + m, gx = tl.ox - 1 + c;
+                    if (m >= 1 && m <= T2M - 2 && c >= 1 && c <= TX2 - 2 && gy < h.H && gx < h.W &&
+                        mk_ok(gy >= 0 && gx >= 0))
+                        h.stack_out[(long long)I * h.plane + (long long)gy * h.W + gx] = d;
+                }
+            }
+        }
+    }
+    if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+template <int DT>
+__device__ __forceinline__ void t2_load_x_t(const MhfdKHeader &h, const TcStretch &ts,
+                                            unsigned char *x, const int *cmap, int oy, int wt) {
+    constexpr int NCG = (T2_XIMG_C + 7) / 8;
+    constexpr int ITEMS = T2_XIMG_R * NCG;
+    constexpr int U = 2;
+    const char *img = reinterpret_cast<const char *>(h.img);
+#pragma unroll 1
+    for (int i0 = wt; i0 < ITEMS; i0 += U * T2_NW) {
+        unsigned raw[U][8];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = i0 + u * T2_NW;
+            if (it < ITEMS) {
+                const int k = it / NCG, cg = it - k * NCG;
+                const char *row = img + (long long)reflect_idx(oy - 1 - RMAX + k, h.H) * h.pitch;
+                // image columns of the group's window columns (reflected or
+                // wrapped once per tile into cmap); a group inside the image
+                // reads 8 consecutive pixels
+                const int gx0 = cmap[8 * cg];
+                if (cmap[8 * cg + 7] == gx0 + 7 && gx0 >= 0) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) raw[u][e] = raw_px<DT>(row, gx0 + e);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int gx = cmap[8 * cg + e];
+                        raw[u][e] = gx >= 0 ? raw_px<DT>(row, gx) : (unsigned)ts.c0;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = i0 + u * T2_NW;
+            if (it < ITEMS) {
+                const int k = it / NCG, cg = it - k * NCG;
+                unsigned pk[4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2)
+                    pk[e >> 1] = (unsigned)tc_px(raw[u][e], ts) | ((unsigned)tc_px(raw[u][e + 1], ts) << 16);
+                if (mk_ok(cg < T2_XC / 8 && k < T2_XR))
+                    *reinterpret_cast<uint4 *>(x + cg * T2_XGSTR + k * 16) =
+                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+    }
+}
+// The tile's window: the column map first (image column of every window
+// column, -1 past the window's image columns), then the rows.
+__device__ __forceinline__ void t2_load_x(const MhfdKHeader &h, const TcStretch &ts, const T2State &t,
+                                          int oy, int ox, int wt) {
+    int *cmap = t.cmap();
+    for (int j = wt; j < T2_XC; j += T2_NW)
+        cmap[j] = j < T2_XIMG_C ? reflect_idx(ox - 1 - RMAX + j, h.W) : -1;
+    t2_wsync();
+    if (h.dtype == 0)
+        t2_load_x_t<0>(h, ts, t.xp(), cmap, oy, wt);
+    else
+        t2_load_x_t<1>(h, ts, t.xp(), cmap, oy, wt);
+}
+
+// exclusive scan over the worker threads (named barrier 1)
+__device__ __forceinline__ int t2_scan(int v, int *buf, int *sum, int wt) {
+    constexpr int NWW = T2_NW / 32;
+    const int lane = wt & 31, warp = wt >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) buf[warp] = x;
+    t2_wsync();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < NWW; ++w) {
+        const int tt = buf[w];
+        before += w < warp ? tt : 0;
+        total += tt;
+    }
+    *sum = total;
+    return before + x - v;
+}
+
+__device__ __forceinline__ bool t2_cand(const float *mp, int m, int c, float thr, float *v) {
+    const float *row = mp + m * T2_MS;
+    const float x = row[c];
+    *v = x;
+    if (!(x > thr)) return false;
+    const float *up = row - T2_MS, *dn = row + T2_MS;
+    const float nb = fmaxf(fmaxf(fmaxf(up[c - 1], up[c]), fmaxf(up[c + 1], row[c - 1])),
+                           fmaxf(fmaxf(row[c + 1], dn[c - 1]), fmaxf(dn[c], dn[c + 1])));
+    return !(nb > x);
+}
+
+// The tile's maxima (Eq. 3 with the 3x3 test of §3) in row-major order into
+// its candidate slots; the true count into tile_count.  The tile's output
+// pixels are cut into row-major chunks of 32 (one per lane), each worker
+// warp a contiguous run of chunks; a first pass records each chunk's ballot
+// of candidates, a scan over the warps gives the offsets, a second pass
+// writes the chunks that have candidates.
+__device__ __forceinline__ void t2_nms(const MhfdKHeader &h, const T2State &t, const T2Tile &tl,
+                                       long long slot, int wt) {
+    constexpr int NWW = T2_NW / 32;
+    const float *mp = reinterpret_cast<const float *>(t.ahp());
+    const unsigned char *ap = t.ahp() + T2M * T2_MS * 4;
+    unsigned *masks = reinterpret_cast<unsigned *>(t.ahp() + T2_MASKS);
+    const int ny = min(TY, h.H - tl.oy), nx = min(TX, h.W - tl.ox);
+    const int items = ny * nx;
+    const int nch = (items + 31) / 32;
+    const int warp = wt >> 5, lane = wt & 31;
+    const int cb = warp * nch / NWW, ce = (warp + 1) * nch / NWW;
+    const float thr = h.thr;
+    int cnt = 0;
+#pragma unroll 1
+    for (int c = cb; c < ce; ++c) {
+        const int p = 32 * c + lane;
+        bool f = false;
+        if (p < items) {
+            const int r = p / nx;
+            float v;
+            f = t2_cand(mp, 1 + r, 1 + p - r * nx, thr, &v);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0 && mk_ok(c < T2_NCHUNK)) masks[c] = m;
+        cnt += __popc(m);
+    }
+    int *buf = t.scan();
+    if (lane == 0) buf[warp] = cnt;
+    t2_wsync();
+    int pos = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < NWW; ++w) {
+        const int tt = buf[w];
+        pos += w < warp ? tt : 0;
+        total += tt;
+    }
+    if (mk_ok(slot >= 0)) {
+        MhfdCand *dst = h.stage + slot * h.cap_tile;
+#pragma unroll 1
+        for (int c = cb; c < ce; ++c) {
+            const unsigned m = masks[c];
+            if (m & (1u << lane)) {
+                const int p = 32 * c + lane;
+                const int r = p / nx, cx = p - r * nx;
+                const int idx = pos + __popc(m & ((1u << lane) - 1u));
+                if (idx < h.cap_tile) {
+                    MhfdCand cd;
+                    cd.x = tl.ox + cx;
+                    cd.y = tl.oy + r;
+                    cd.i = ap[(1 + r) * TX2 + 1 + cx];
+                    cd.resp = mp[(1 + r) * T2_MS + 1 + cx];
+                    dst[idx] = cd;
+                }
+            }
+            pos += __popc(m);
+        }
+    }
+    if (wt == 0) h.tile_count[slot] = total;
+}
+
+// worker levels: wait for level l's V, split it, build level l + 2's tap
+// matrix, hand over; then the responses of level l - 1
+__device__ __forceinline__ void t2_work(const MhfdKHeader &h, T2State &t, const TcStretch &ts, T2Px &px,
+                                        const T2Tile &tl, int wt) {
+#pragma unroll 1
+    for (int l = 0; l < NL; ++l) {
+        const unsigned gl = t.g + (unsigned)l;
+        t2_wait(h, t, T2_VB + (int)(gl & 1u));
+        if (l > 0) t2_wait(h, t, T2_HB + (int)((gl - 1u) & 1u));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        t2_split(t, l, (gl & 1u) * (unsigned)T2_NVMAX, wt);
+        t2_arrive(t2_bar(t, T2_SPL));
+        if (l > 0)
+            t2_epi(h, t, l - 1, (unsigned)T2_DH + ((gl - 1u) & 1u) * (unsigned)TX2, wt, px, ts.a, tl);
+    }
+}
+
+// issuer levels: after level l's split, level l's horizontal product and
+// level l + 2's vertical one
+// (level l's tap matrices are fetched three levels ahead, into the buffer
+// that level l - 1 used: its horizontal product is done once the workers
+// have split level l; the last three levels fetch the next tile's first)
+__device__ __forceinline__ void t2_issue(const MhfdKHeader &h, T2State &t, bool next) {
+#pragma unroll 1
+    for (int l = 0; l < NL; ++l) {
+        const unsigned gl = t.g + (unsigned)l;
+        t2_wait(h, t, T2_SPL);
+        __syncwarp();  // converged for elect.sync
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (l + 3 < NL)
+            t2_fetch_tab(h, t, l + 3, gl + 3u);
+        else if (next)
+            t2_fetch_tab(h, t, l + 3 - NL, gl + 3u);
+        t2_issue_h(t, l, t2_tabb(t, gl), (unsigned)T2_DH + (gl & 1u) * (unsigned)TX2);
+        t2_commit(t2_bar(t, T2_HB + (int)(gl & 1u)));
+        if (l + 2 < NL) {
+            t2_wait(h, t, T2_TB + (int)((gl + 2u) % (unsigned)T2_NTAB));
+            __syncwarp();
+            t2_issue_v(t, l + 2, t2_tabb(t, gl + 2u), (gl & 1u) * (unsigned)T2_NVMAX);
+            t2_commit(t2_bar(t, T2_VB + (int)(gl & 1u)));
+        }
+    }
+}
+
+__device__ __forceinline__ T2Tile t2_tile(long long k, int tiles_y) {
+    T2Tile tl;
+    const int tx = (int)(k / tiles_y), ty = (int)(k - (long long)tx * tiles_y);
+    tl.oy = ty * TY;
+    tl.ox = tx * TX;
+    return tl;
+}
+
+// Tiles [k0, k1) of an image (strip-major order), tile k's candidates into
+// slot slot0 + (its tile row) * tiles_x + (its strip).
+__device__ __forceinline__ void t2_range(const MhfdKHeader &h, long long k0, long long k1, int tiles_x,
+                                         int tiles_y, long long slot0, T2State &t) {
+    if (k0 >= k1) return;
+    const MhfdStretch st = *h.st;
+    TcStretch ts = tc_stretch(st);
+    ts.a = st.inv * (1.0f / (T2_S * T2_S));
+    if (threadIdx.x >= T2_NW) {
+#pragma unroll 1
+        // the first tile's first three tap matrices (the buffers are free:
+        // the previous range's products are done)
+        for (int l = 0; l < 3; ++l) t2_fetch_tab(h, t, l, t.g + (unsigned)l);
+        for (long long k = k0; k < k1; ++k) {
+            t2_wait(h, t, T2_XRB);
+            __syncwarp();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            t2_wait(h, t, T2_TB + (int)(t.g % (unsigned)T2_NTAB));
+            __syncwarp();
+            t2_issue_v(t, 0, t2_tabb(t, t.g), ((t.g & 1u) * (unsigned)T2_NVMAX));
+            t2_commit(t2_bar(t, T2_VB + (int)(t.g & 1u)));
+            t2_wait(h, t, T2_TB + (int)((t.g + 1u) % (unsigned)T2_NTAB));
+            __syncwarp();
+            t2_issue_v(t, 1, t2_tabb(t, t.g + 1u), (((t.g + 1u) & 1u) * (unsigned)T2_NVMAX));
+            t2_commit(t2_bar(t, T2_VB + (int)((t.g + 1u) & 1u)));
+            t2_issue(h, t, k + 1 < k1);
+            t.g += NL;
+        }
+        return;
+    }
+    const int wt = threadIdx.x;
+    {
+        const T2Tile t0 = t2_tile(k0, tiles_y);
+        t2_load_x(h, ts, t, t0.oy, t0.ox, wt);
+        t2_arrive(t2_bar(t, T2_XRB));
+    }
+#pragma unroll 1
+    for (long long k = k0; k < k1; ++k) {
+        const T2Tile tl = t2_tile(k, tiles_y);
+        const bool next = k + 1 < k1;
+        const T2Tile tn = t2_tile(next ? k + 1 : k, tiles_y);
+        T2Px px;
+        t2_work(h, t, ts, px, tl, wt);
+        const unsigned gl = t.g + NL - 1;
+        t2_wait(h, t, T2_HB + (int)(gl & 1u));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        t2_epi(h, t, NL - 1, ((unsigned)T2_DH + ((gl) & 1u) * (unsigned)TX2), wt, px, ts.a, tl);
+        // the tile's max plane (natural order; -inf outside the image) in the
+        // split rows' space, free once the last horizontal product is done
+        {
+            float *mp = reinterpret_cast<float *>(t.ahp());
+            unsigned char *ap = t.ahp() + T2M * T2_MS * 4;
+            const int w = wt >> 5, g = w & 3, q = w >> 2;
+            const int m = T2M - 1 - (32 * g + (wt & 31));
+            const int gy = tl.oy - 1 + m;
+            const bool rowin = gy >= 0 && gy < h.H;
+#pragma unroll
+            for (int u = 0; u < T2_CQ; ++u) {
+                const int c = TX2 - 1 - (T2_CQ * q + u);
+                const int gx = tl.ox - 1 + c;
+                const bool in = rowin && gx >= 0 && gx < h.W;
+                mp[m * T2_MS + c] = in ? px.mx[u] : -__int_as_float(0x7f800000);
+                ap[m * TX2 + c] = (unsigned char)t2_ag(px, u);
+                if (STORE && in && m >= 1 && m <= T2M - 2 && c >= 1 && c <= TX2 - 2) {
+                    const long long o2 = (long long)gy * h.W + gx;
+                    if (h.m_out) h.m_out[o2] = px.mx[u];
+                    if (h.arg_out) h.arg_out[o2] = t2_ag(px, u);
+                }
+            }
+        }
+        // the next tile's window and first two tap matrices (the last
+        // vertical product is done; the responses are in the max plane, so
+        // the loads have the registers), then this tile's maxima while the
+        // tensor core starts the next tile
+        if (next) {
+            t2_load_x(h, ts, t, tn.oy, tn.ox, wt);
+            t2_arrive(t2_bar(t, T2_XRB));
+        }
+        t2_wsync();
+        const int tx = (int)(k / tiles_y), ty = (int)(k - (long long)tx * tiles_y);
+        t2_nms(h, t, tl, slot0 + (long long)ty * tiles_x + tx, wt);
+        t2_wsync();
+        t.g += NL;
+    }
+}
+#endif  // MHFD_VTC == 2
+
 // Tiles [k0, k1) of an image in strip-major order (k -> strip k / tiles_y,
 // tile row k % tiles_y), as one march per strip touched.
 __device__ __forceinline__ void run_range(const MhfdKHeader &h, long long k0, long long k1,
@@ -1808,10 +2570,116 @@ __device__ __forceinline__ void batch_loop(const KParams &p, const Smem &sm, TcS
 
 }  // namespace mk
 
+#if MHFD_VTC == 2
+namespace mk {
+// The two-pass kernel's block: shared-memory layout, mbarriers and tensor
+// memory, then a single image's share of tiles or the batch queue.
+__device__ __forceinline__ void t2_kernel(const KParams &p, unsigned char *base) {
+    __shared__ int s_item;
+    if (p.h.dtype == 2) {  // float images never reach this kernel
+        if (threadIdx.x == 0 && p.h.flag) atomicOr(p.h.flag, 1);
+        return;
+    }
+    T2State t;
+    unsigned char *ctrl = t.ctrl();  // 10 mbarriers, TMEM address (+96), fail flag (+100)
+    // the window's padding rows and columns stay zero
+    for (int i = threadIdx.x; i < T2_X_BYTES / 16; i += NT)
+        reinterpret_cast<uint4 *>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 10; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(ctrl + 8 * b)),
+                         "r"(b == T2_SPL || b == T2_XRB ? T2_NW / 32 : 1)
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *reinterpret_cast<volatile int *>(ctrl + 100) = 0;
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(ctrl + 96)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    t.tmem = *reinterpret_cast<volatile unsigned *>(ctrl + 96);
+    t.ph = 0;
+    t.g = 0;
+    if (p.h.jobs == nullptr) {
+        const bool run = p.h.gate == 0 || ((p.h.gate == 1) == tc_narrow(p.h.dtype, *p.h.st));
+        const long long T = (long long)p.h.tiles_x * p.h.tiles_y;
+        const long long k0 = T * blockIdx.x / gridDim.x;
+        const long long k1 = T * (blockIdx.x + 1) / gridDim.x;
+        if (run) t2_range(p.h, k0, k1, p.h.tiles_x, p.h.tiles_y, 0, t);
+    } else {
+#pragma unroll 1
+        for (;;) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_item = atomicAdd(p.h.queue, 1);
+            __syncthreads();
+            const int item = s_item;
+            if (item >= p.h.total_items) break;
+            int lo = 0, hi = p.h.n_jobs - 1;  // last job with chunk_base <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.h.jobs[mid].chunk_base <= item) lo = mid; else hi = mid - 1;
+            }
+            const MhfdJob job = p.h.jobs[lo];
+            if (p.h.gate != 0 && (p.h.gate == 1) != tc_narrow(job.dtype, *job.st)) continue;
+            MhfdKHeader h = p.h;
+            h.img = job.img;
+            h.st = job.st;
+            h.pitch = job.pitch;
+            h.H = job.H;
+            h.W = job.W;
+            h.dtype = job.dtype;
+            h.tiles_x = job.tiles_x;
+            h.tiles_y = job.tiles_y;
+            h.plane = (long long)job.H * job.W;
+            const long long n_tiles = (long long)job.tiles_x * job.tiles_y;
+            const long long k0 = (long long)(item - job.chunk_base) * p.h.chunk;
+            const long long k1 = min(n_tiles, k0 + p.h.chunk);
+            if (job.dtype == 2) continue;
+            t2_range(h, k0, k1, job.tiles_x, job.tiles_y, job.tile_base, t);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem), "r"(512u)
+                     : "memory");
+}
+}  // namespace mk
+#endif
+
+#if MHFD_VTC == 2
+// The two-pass kernel's banded tap matrices of every level, in the layout of
+// its shared-memory buffers (hi part, then lo part at T2_TAB_PART): block l
+// writes level l.  Run once per detector; the kernel copies one level at a
+// time.
+extern "C" __constant__ int mhfd_t2_tab_bytes = mk::NL * 2 * mk::T2_TAB_PART;
+extern "C" __global__ void __launch_bounds__(mk::T2_NW) mhfd_t2_tables(unsigned char *out) {
+    using namespace mk;
+    const int l = blockIdx.x;
+    if (l >= NL || blockDim.x != T2_NW) return;
+    unsigned char *tab = out + (long long)l * (2 * T2_TAB_PART);
+    for (int i = threadIdx.x; i < 2 * T2_TAB_PART / 16; i += T2_NW)
+        reinterpret_cast<uint4 *>(tab)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    t2_build_tab(tab, l, threadIdx.x);
+}
+#endif
+
 extern "C" __global__ void __launch_bounds__(mk::NT, 1)
     mhfd_fused_detect(const __grid_constant__ mk::KParams p) {
     using namespace mk;
     extern __shared__ __align__(16) float smem[];
+#if MHFD_VTC == 2
+    t2_kernel(p, reinterpret_cast<unsigned char *>(smem));
+    return;
+#endif
     Smem sm;
     if constexpr (TC) {
         sm.win = reinterpret_cast<unsigned char *>(smem);

@@ -68,7 +68,7 @@ int enqueue_stretch_batch(const MhfdJob *d_jobs, int n_jobs, int max_passes, int
 struct TileConfig {
     int tx2, ty2, rb, nt;
     std::vector<int> gb;   // level-group boundaries
-    int tc = 0;            // 1: vertical pass on the tensor cores (tcgen05)
+    int tc = 0;            // 1: vertical pass on the tensor cores (tcgen05); 2: both passes
     int item = 1;          // horizontal item: 1 one row x 4 outputs, 2 two rows x 4
                            // (packed FMAs over the row pair), 3 one row x 2 outputs
 };
@@ -86,6 +86,7 @@ struct Variant {
     int ntaps = 0;
     int occupancy = 1;  // resident blocks per SM
     TileConfig cfg;
+    void *t2tab = nullptr;  // two-pass kernel: its levels' tap matrices (device, built at load)
 };
 
 // The ladder as the fused kernel is specialised on: radii, f32 taps (level
@@ -118,6 +119,14 @@ int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c);
 bool tc_mode_ok(int mode);
 bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why);
 std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode);
+// The two-pass kernel (both blur passes on the tensor cores): its shared
+// memory, whether it takes a mode and shape, its configuration for a strip
+// width, and the built-in choice.
+int t2_smem(const std::vector<int> &R, const TileConfig &c);
+bool t2_mode_ok(int mode);
+bool t2_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why);
+TileConfig t2_config(int nl, int tx2);
+bool choose_tile_t2(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why);
 bool choose_tile_tc(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why);
 // The FFMA kernel's shape on a tensor-core shape's tile grid (the kernel
 // that takes the images the tensor-core pass cannot hold exactly).

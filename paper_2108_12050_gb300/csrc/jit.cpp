@@ -11,6 +11,7 @@
 #include <sys/stat.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -302,6 +303,7 @@ int tc_min_rows(const std::vector<int> &R, int mode, const TileConfig &c) {
 // The tensor-core variant also holds the rows of the step after next and 16
 // rows of K padding, and takes up to six steps of slack.
 int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
+    if (c.tc == 2) return c.rb + 2 * halo_of(R, mode);  // the two-pass kernel has no row window
     if (c.tc) {
         const int lo = tc_min_rows(R, mode, c);
         const int fixed = smem_fixed(R, mode, c) + tc_b_bytes(R, mode, c) + 128;
@@ -318,6 +320,7 @@ int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
 }
 
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
+    if (c.tc == 2) return t2_smem(R, c);
     if (c.tc)
         return smem_fixed(R, mode, c) + tc_b_bytes(R, mode, c) + 128 +
                tc_window_bytes(R, mode, c, brows_for(R, mode, c));
@@ -326,6 +329,91 @@ int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
 
 namespace {
 double cost_model(const std::vector<int> &R, int mode, const TileConfig &c);
+}
+
+// Two-pass kernel (tc = 2): its shared memory as the kernel lays it out (the
+// fp16 window with zero padding rows and columns for the K and N padding of
+// every level's products, three tap-matrix buffers of hi and lo parts, the
+// split V rows, the control block) and its tensor-memory columns (two V and
+// two L buffers).
+namespace {
+struct T2Geom {
+    int nvmax = 0, khmax = 0, smax = 0, xr = 0, xc = 0;
+};
+T2Geom t2_geom(const std::vector<int> &R, const TileConfig &c) {
+    T2Geom g;
+    const int rmax = rmax_of(R);
+    auto c16 = [](int v) { return (v + 15) & ~15; };
+    g.xr = 128 + 2 * rmax;
+    int xc = c.tx2 + 2 * rmax;
+    for (int r : R) {
+        const int k0 = rmax - r, j0 = (rmax - r) & ~7, off = (rmax - r) & 7;
+        const int need = c.tx2 + 2 * r;
+        const int kv = c16(128 + 2 * r), nv = c16(off + need), kh = c16(need);
+        g.nvmax = std::max(g.nvmax, nv);
+        g.khmax = std::max(g.khmax, kh);
+        g.smax = std::max(g.smax, kv / 8 + 15);
+        g.xr = std::max(g.xr, k0 + kv);
+        xc = std::max(xc, j0 + nv);
+    }
+    g.xc = (xc + 7) & ~7;
+    return g;
+}
+}  // namespace
+
+int t2_smem(const std::vector<int> &R, const TileConfig &c) {
+    const T2Geom g = t2_geom(R, c);
+    const int xgstr = ((16 * g.xr + 127) / 128) * 128 + 16;
+    const int x_bytes = (g.xc / 8) * xgstr;
+    const int tab_part = g.smax * 128;
+    const int ah_part = 16 * (g.khmax / 8) * 128;
+    return ((x_bytes + 127) & ~127) + 8 * tab_part + 2 * ah_part + 512 + 4 * ((g.xc + 3) & ~3);
+}
+
+bool t2_mode_ok(int mode) { return mode == 0; }  // paper rule, DoG response
+
+bool t2_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why) {
+    auto no = [&](const char *m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (!t2_mode_ok(mode)) return no("the two-pass kernel takes the paper rule with the DoG response");
+    if (c.tx2 % 16 || c.tx2 < 16 || c.tx2 > 128)
+        return no("the two-pass kernel's strips are 16 to 128 columns, a multiple of 16");
+    if (c.ty2 != 128 || c.nt != 288) return no("the two-pass kernel: tiles of 128 rows, 288 threads");
+    const T2Geom g = t2_geom(R, c);
+    if (g.nvmax > 256 || 2 * g.nvmax + 2 * c.tx2 > 512)
+        return no("the two-pass kernel's V and L buffers exceed tensor memory for this ladder");
+    const int plane = ((128 * (c.tx2 + 1) * 4 + 128 * c.tx2) + 15) & ~15;
+    if (plane + 4 * ((126 * (c.tx2 - 2) + 31) / 32) > 2 * 16 * (g.khmax / 8) * 128)
+        return no("the tile's max plane does not fit the split rows' space");
+    if (t2_smem(R, c) > kSmemLimitBytes) return no("does not fit in shared memory");
+    return true;
+}
+
+TileConfig t2_config(int nl, int tx2) {
+    TileConfig c;
+    c.tx2 = tx2;
+    c.ty2 = 128;
+    c.rb = 4;
+    c.nt = 288;
+    c.gb = {0, nl};
+    c.tc = 2;
+    c.item = 1;
+    return c;
+}
+
+// 64-column strips (62 x 126 outputs per tile: the per-thread responses of
+// wider strips exceed the registers), else the first that fits
+bool choose_tile_t2(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why) {
+    for (int tx2 : {64, 80, 48, 96, 112, 128, 32, 16}) {
+        const TileConfig c = t2_config((int)R.size(), tx2);
+        if (t2_shape_ok(R, mode, c, why)) {
+            *cfg = c;
+            return true;
+        }
+    }
+    return false;
 }
 
 // The paper rule, DoG or LoG response; the 26-neighbour rule with the DoG
@@ -632,9 +720,31 @@ int get_variant(const LadderKey &lk, int mode, int store, const TileConfig &cfg,
     r = drv().occupancy(&v->occupancy, v->fn, cfg.nt, (size_t)v->smem_bytes);
     if (r != CUDA_SUCCESS) return drv_fail(r, "cuOccupancyMaxActiveBlocksPerMultiprocessor");
     if (v->occupancy < 1) return fail(MHFD_ERR_UNSUPPORTED, "fused kernel does not fit on an SM");
+    if (cfg.tc == 2) {
+        // the two-pass kernel copies each level's tap matrices from global
+        // memory: build them once, here (the module's setup kernel)
+        CUfunction fset;
+        r = drv().moduleGetFunction(&fset, v->mod, "mhfd_t2_tables");
+        if (r != CUDA_SUCCESS) return drv_fail(r, "cuModuleGetFunction");
+        int tab_bytes = 0;
+        r = drv().moduleGetGlobal(&gp, &gsz, v->mod, "mhfd_t2_tab_bytes");
+        if (r != CUDA_SUCCESS) return drv_fail(r, "cuModuleGetGlobal");
+        r = drv().memcpyDtoH(&tab_bytes, gp, sizeof(int));
+        if (r != CUDA_SUCCESS) return drv_fail(r, "cuMemcpyDtoH");
+        cudaError_t e = cudaMalloc(&v->t2tab, (size_t)tab_bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (tap matrices)");
+        void *targ = v->t2tab;
+        void *args[] = {&targ};
+        r = drv().launchKernel(fset, (unsigned)R.size(), 1, 1, (unsigned)(cfg.nt - 32), 1, 1, 0, nullptr,
+                               args, nullptr);
+        if (r != CUDA_SUCCESS) return drv_fail(r, "cuLaunchKernel (tap matrices)");
+        e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (tap matrices)");
+    }
     std::lock_guard<std::mutex> guard(g_mu);
     auto it = g_variants.find(key);
     if (it != g_variants.end()) {  // another thread won the race
+        if (v->t2tab) cudaFree(v->t2tab);
         drv().moduleUnload(v->mod);
         delete v;
         *out = it->second;

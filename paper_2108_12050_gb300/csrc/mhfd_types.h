@@ -66,6 +66,8 @@ struct MhfdKHeader {
                               // for the others (per image in a batch)
     double *soft_part;        //   per-block, per-layer sums (zeroed before launch)
     int *flag;                // set to 1 when a bounded wait gives up (or null)
+    const void *t2tab;        // two-pass kernel: every level's banded tap
+                              // matrices, as its shared-memory buffer holds them
 };
 
 #endif  // MHFD_TYPES_H
