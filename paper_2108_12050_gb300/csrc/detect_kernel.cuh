@@ -340,8 +340,9 @@ constexpr int SMEM_BYTES =
         : TC_WIN_BYTES + TC_B_BYTES + 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64 +
               TC_CTRL;
 static_assert(!TC2 || (MODE == 0 && !LOG), "two-pass kernel: paper rule, DoG response");
-static_assert(!TC2 || (TX2 % 16 == 0 && TX2 >= 16 && TX2 <= 128 && MHFD_TY2 == T2M && NT == 288),
-              "two-pass kernel geometry: 16-multiple strips up to 128, tiles of 128 rows, 288 threads");
+static_assert(!TC2 || (TX2 % 16 == 0 && TX2 >= 16 && TX2 <= 128 && MHFD_TY2 == T2M &&
+                       (NT == 288 || NT == 544) && TX2 % (4 * ((NT - 32) / 128)) == 0),
+              "two-pass kernel geometry: 16-multiple strips up to 128, tiles of 128 rows, 8 or 16 worker warps");
 static_assert(!TC2 || T2_LP + TX2 <= 512, "two-pass kernel: tensor memory columns");
 static_assert(!TC2 || T2_NVMAX <= 256, "two-pass kernel: N of the vertical product");
 // after the max plane and argmax plane: the NMS chunk ballots
@@ -2220,6 +2221,9 @@ __device__ __forceinline__ void t2_load_x_t(const MhfdKHeader &h, const TcStretc
     const char *img = reinterpret_cast<const char *>(h.img);
 #pragma unroll 1
     for (int i0 = wt; i0 < ITEMS; i0 += U * T2_NW) {
+        // a group of 8 window columns maps to 8 consecutive image columns,
+        // ascending, or (reflected at an edge) descending; only a group that
+        // straddles an edge takes each column's index from the map
         unsigned raw[U][8];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -2227,13 +2231,11 @@ __device__ __forceinline__ void t2_load_x_t(const MhfdKHeader &h, const TcStretc
             if (it < ITEMS) {
                 const int k = it / NCG, cg = it - k * NCG;
                 const char *row = img + (long long)reflect_idx(oy - 1 - RMAX + k, h.H) * h.pitch;
-                // image columns of the group's window columns (reflected or
-                // wrapped once per tile into cmap); a group inside the image
-                // reads 8 consecutive pixels
-                const int gx0 = cmap[8 * cg];
-                if (cmap[8 * cg + 7] == gx0 + 7 && gx0 >= 0) {
+                const int g0 = cmap[8 * cg], g7 = cmap[8 * cg + 7];
+                const int step = g0 >= 0 && g7 == g0 + 7 ? 1 : (MHFD_BOUNDARY == 0 && g7 >= 0 && g7 == g0 - 7 ? -1 : 0);
+                if (step != 0) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) raw[u][e] = raw_px<DT>(row, gx0 + e);
+                    for (int e = 0; e < 8; ++e) raw[u][e] = raw_px<DT>(row, g0 + step * e);
                 } else {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
@@ -2325,19 +2327,30 @@ __device__ __forceinline__ void t2_nms(const MhfdKHeader &h, const T2State &t, c
     const int warp = wt >> 5, lane = wt & 31;
     const int cb = warp * nch / NWW, ce = (warp + 1) * nch / NWW;
     const float thr = h.thr;
+    // pixel p of the chunk run: row r, column cx, advanced by 32 per chunk
+    // (nx >= 1; at most 32 / nx rows a step) instead of a division per pixel
+    int p = 32 * cb + lane;
+    int r = p / nx, cx = p - r * nx;
     int cnt = 0;
 #pragma unroll 1
-    for (int c = cb; c < ce; ++c) {
-        const int p = 32 * c + lane;
-        bool f = false;
-        if (p < items) {
-            const int r = p / nx;
-            float v;
-            f = t2_cand(mp, 1 + r, 1 + p - r * nx, thr, &v);
+    for (int c = cb; c < ce; c += 2) {
+        bool f0 = false, f1 = false;
+        int r1 = r, cx1 = cx + 32;
+        while (cx1 >= nx) { cx1 -= nx; ++r1; }
+        float v;
+        if (p < items) f0 = t2_cand(mp, 1 + r, 1 + cx, thr, &v);
+        if (c + 1 < ce && p + 32 < items) f1 = t2_cand(mp, 1 + r1, 1 + cx1, thr, &v);
+        const unsigned m0 = __ballot_sync(0xffffffffu, f0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, f1);
+        if (lane == 0 && mk_ok(c + 1 < T2_NCHUNK || (c < T2_NCHUNK && c + 1 >= ce))) {
+            masks[c] = m0;
+            if (c + 1 < ce) masks[c + 1] = m1;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, f);
-        if (lane == 0 && mk_ok(c < T2_NCHUNK)) masks[c] = m;
-        cnt += __popc(m);
+        cnt += __popc(m0) + (c + 1 < ce ? __popc(m1) : 0);
+        p += 64;
+        r = r1;
+        cx = cx1 + 32;
+        while (cx >= nx) { cx -= nx; ++r; }
     }
     int *buf = t.scan();
     if (lane == 0) buf[warp] = cnt;

@@ -380,7 +380,9 @@ bool t2_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::
     if (!t2_mode_ok(mode)) return no("the two-pass kernel takes the paper rule with the DoG response");
     if (c.tx2 % 16 || c.tx2 < 16 || c.tx2 > 128)
         return no("the two-pass kernel's strips are 16 to 128 columns, a multiple of 16");
-    if (c.ty2 != 128 || c.nt != 288) return no("the two-pass kernel: tiles of 128 rows, 288 threads");
+    if (c.ty2 != 128 || (c.nt != 288 && c.nt != 544))
+        return no("the two-pass kernel: tiles of 128 rows, 288 or 544 threads");
+    if (c.tx2 % (4 * ((c.nt - 32) / 128))) return no("the two-pass kernel: whole column parts of 4");
     const T2Geom g = t2_geom(R, c);
     if (g.nvmax > 256 || 2 * g.nvmax + 2 * c.tx2 > 512)
         return no("the two-pass kernel's V and L buffers exceed tensor memory for this ladder");
