@@ -2212,11 +2212,12 @@ __device__ __forceinline__ void t2_epi(const MhfdKHeader &h, const T2State &t, i
     if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// Window rows [k_lo, T2_XIMG_R) of the tile whose first output row is oy.
 template <int DT>
 __device__ __forceinline__ void t2_load_x_t(const MhfdKHeader &h, const TcStretch &ts,
-                                            unsigned char *x, const int *cmap, int oy, int wt) {
+                                            unsigned char *x, const int *cmap, int oy, int k_lo, int wt) {
     constexpr int NCG = (T2_XIMG_C + 7) / 8;
-    constexpr int ITEMS = T2_XIMG_R * NCG;
+    const int ITEMS = (T2_XIMG_R - k_lo) * NCG;
     constexpr int U = 2;
     const char *img = reinterpret_cast<const char *>(h.img);
 #pragma unroll 1
@@ -2229,7 +2230,7 @@ __device__ __forceinline__ void t2_load_x_t(const MhfdKHeader &h, const TcStretc
         for (int u = 0; u < U; ++u) {
             const int it = i0 + u * T2_NW;
             if (it < ITEMS) {
-                const int k = it / NCG, cg = it - k * NCG;
+                const int kk = it / NCG, cg = it - kk * NCG, k = k_lo + kk;
                 const char *row = img + (long long)reflect_idx(oy - 1 - RMAX + k, h.H) * h.pitch;
                 const int g0 = cmap[8 * cg], g7 = cmap[8 * cg + 7];
                 const int step = g0 >= 0 && g7 == g0 + 7 ? 1 : (MHFD_BOUNDARY == 0 && g7 >= 0 && g7 == g0 - 7 ? -1 : 0);
@@ -2249,7 +2250,7 @@ __device__ __forceinline__ void t2_load_x_t(const MhfdKHeader &h, const TcStretc
         for (int u = 0; u < U; ++u) {
             const int it = i0 + u * T2_NW;
             if (it < ITEMS) {
-                const int k = it / NCG, cg = it - k * NCG;
+                const int kk = it / NCG, cg = it - kk * NCG, k = k_lo + kk;
                 unsigned pk[4];
 #pragma unroll
                 for (int e = 0; e < 8; e += 2)
@@ -2262,17 +2263,35 @@ __device__ __forceinline__ void t2_load_x_t(const MhfdKHeader &h, const TcStretc
     }
 }
 // The tile's window: the column map first (image column of every window
-// column, -1 past the window's image columns), then the rows.
+// column, -1 past the window's image columns), then the rows.  When the
+// tile is the one below the previous tile of the same strip (`below`), the
+// previous window's rows from T2M - 2 on are this one's first rows: they move
+// up in shared memory and only the rest is read from the image.
 __device__ __forceinline__ void t2_load_x(const MhfdKHeader &h, const TcStretch &ts, const T2State &t,
-                                          int oy, int ox, int wt) {
+                                          int oy, int ox, bool below, int wt) {
+    constexpr int KEEP = T2_XIMG_R - (T2M - 2);  // rows shared with the tile above
     int *cmap = t.cmap();
-    for (int j = wt; j < T2_XC; j += T2_NW)
-        cmap[j] = j < T2_XIMG_C ? reflect_idx(ox - 1 - RMAX + j, h.W) : -1;
+    if (!below)
+        for (int j = wt; j < T2_XC; j += T2_NW)
+            cmap[j] = j < T2_XIMG_C ? reflect_idx(ox - 1 - RMAX + j, h.W) : -1;
+    int k_lo = 0;
+    if (below && KEEP > 0) {
+        // rows [T2M - 2, T2_XIMG_R) to [0, KEEP): disjoint ranges, 16 bytes a row
+        constexpr int NCG = (T2_XIMG_C + 7) / 8;
+        unsigned char *x = t.xp();
+        for (int i = wt; i < KEEP * NCG; i += T2_NW) {
+            const int k = i % KEEP, cg = i / KEEP;
+            if (mk_ok(cg < T2_XC / 8 && k + T2M - 2 < T2_XR))
+                *reinterpret_cast<uint4 *>(x + cg * T2_XGSTR + k * 16) =
+                    *reinterpret_cast<const uint4 *>(x + cg * T2_XGSTR + (k + T2M - 2) * 16);
+        }
+        k_lo = KEEP;
+    }
     t2_wsync();
     if (h.dtype == 0)
-        t2_load_x_t<0>(h, ts, t.xp(), cmap, oy, wt);
+        t2_load_x_t<0>(h, ts, t.xp(), cmap, oy, k_lo, wt);
     else
-        t2_load_x_t<1>(h, ts, t.xp(), cmap, oy, wt);
+        t2_load_x_t<1>(h, ts, t.xp(), cmap, oy, k_lo, wt);
 }
 
 // exclusive scan over the worker threads (named barrier 1)
@@ -2298,15 +2317,14 @@ __device__ __forceinline__ int t2_scan(int v, int *buf, int *sum, int wt) {
     return before + x - v;
 }
 
+// (no early exit: the nine loads are independent and issue together)
 __device__ __forceinline__ bool t2_cand(const float *mp, int m, int c, float thr, float *v) {
-    const float *row = mp + m * T2_MS;
-    const float x = row[c];
+    const float *row = mp + m * T2_MS + c;
+    const float x = row[0];
     *v = x;
-    if (!(x > thr)) return false;
-    const float *up = row - T2_MS, *dn = row + T2_MS;
-    const float nb = fmaxf(fmaxf(fmaxf(up[c - 1], up[c]), fmaxf(up[c + 1], row[c - 1])),
-                           fmaxf(fmaxf(row[c + 1], dn[c - 1]), fmaxf(dn[c], dn[c + 1])));
-    return !(nb > x);
+    const float nb = fmaxf(fmaxf(fmaxf(row[-T2_MS - 1], row[-T2_MS]), fmaxf(row[-T2_MS + 1], row[-1])),
+                           fmaxf(fmaxf(row[1], row[T2_MS - 1]), fmaxf(row[T2_MS], row[T2_MS + 1])));
+    return x > thr && !(nb > x);
 }
 
 // The tile's maxima (Eq. 3 with the 3x3 test of §3) in row-major order into
@@ -2329,28 +2347,30 @@ __device__ __forceinline__ void t2_nms(const MhfdKHeader &h, const T2State &t, c
     const float thr = h.thr;
     // pixel p of the chunk run: row r, column cx, advanced by 32 per chunk
     // (nx >= 1; at most 32 / nx rows a step) instead of a division per pixel
+    constexpr int CU = 4;  // chunks per iteration
     int p = 32 * cb + lane;
     int r = p / nx, cx = p - r * nx;
     int cnt = 0;
 #pragma unroll 1
-    for (int c = cb; c < ce; c += 2) {
-        bool f0 = false, f1 = false;
-        int r1 = r, cx1 = cx + 32;
-        while (cx1 >= nx) { cx1 -= nx; ++r1; }
-        float v;
-        if (p < items) f0 = t2_cand(mp, 1 + r, 1 + cx, thr, &v);
-        if (c + 1 < ce && p + 32 < items) f1 = t2_cand(mp, 1 + r1, 1 + cx1, thr, &v);
-        const unsigned m0 = __ballot_sync(0xffffffffu, f0);
-        const unsigned m1 = __ballot_sync(0xffffffffu, f1);
-        if (lane == 0 && mk_ok(c + 1 < T2_NCHUNK || (c < T2_NCHUNK && c + 1 >= ce))) {
-            masks[c] = m0;
-            if (c + 1 < ce) masks[c + 1] = m1;
+    for (int c = cb; c < ce; c += CU) {
+        bool f[CU];
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            float v;
+            f[u] = c + u < ce && p < items && t2_cand(mp, 1 + r, 1 + cx, thr, &v);
+            p += 32;
+            cx += 32;
+            while (cx >= nx) {
+                cx -= nx;
+                ++r;
+            }
         }
-        cnt += __popc(m0) + (c + 1 < ce ? __popc(m1) : 0);
-        p += 64;
-        r = r1;
-        cx = cx1 + 32;
-        while (cx >= nx) { cx -= nx; ++r; }
+#pragma unroll
+        for (int u = 0; u < CU; ++u) {
+            const unsigned m = __ballot_sync(0xffffffffu, f[u]);
+            if (lane == 0 && c + u < ce && mk_ok(c + u < T2_NCHUNK)) masks[c + u] = m;
+            cnt += __popc(m);
+        }
     }
     int *buf = t.scan();
     if (lane == 0) buf[warp] = cnt;
@@ -2471,7 +2491,7 @@ __device__ __forceinline__ void t2_range(const MhfdKHeader &h, long long k0, lon
     const int wt = threadIdx.x;
     {
         const T2Tile t0 = t2_tile(k0, tiles_y);
-        t2_load_x(h, ts, t, t0.oy, t0.ox, wt);
+        t2_load_x(h, ts, t, t0.oy, t0.ox, false, wt);
         t2_arrive(t2_bar(t, T2_XRB));
     }
 #pragma unroll 1
@@ -2513,7 +2533,7 @@ __device__ __forceinline__ void t2_range(const MhfdKHeader &h, long long k0, lon
         // the loads have the registers), then this tile's maxima while the
         // tensor core starts the next tile
         if (next) {
-            t2_load_x(h, ts, t, tn.oy, tn.ox, wt);
+            t2_load_x(h, ts, t, tn.oy, tn.ox, tn.ox == tl.ox && tn.oy == tl.oy + TY, wt);
             t2_arrive(t2_bar(t, T2_XRB));
         }
         t2_wsync();
