@@ -323,7 +323,6 @@ constexpr int T2_X_BYTES = TC2 ? (T2_XC / 8) * T2_XGSTR : 0;
 constexpr int T2_TAB_PART = T2_SMAX * 128;  // one part (hi or lo) of a tap matrix
 constexpr int T2_SBO_H = (T2_KHMAX / 8) * 128;
 constexpr int T2_AH_PART = (T2M / 8) * T2_SBO_H;  // one part of the split V rows
-constexpr int T2_MS = TX2 + 1;                   // row stride of the tile's max plane
 constexpr int T2_OFF_TAB = (T2_X_BYTES + 127) & ~127;
 constexpr int T2_NTAB = 4;                       // tap-matrix buffers (levels l - 1 .. l + 2)
 constexpr int T2_OFF_AH = T2_OFF_TAB + (TC2 ? T2_NTAB * 2 * T2_TAB_PART : 0);
@@ -345,10 +344,13 @@ static_assert(!TC2 || (TX2 % 16 == 0 && TX2 >= 16 && TX2 <= 128 && MHFD_TY2 == T
               "two-pass kernel geometry: 16-multiple strips up to 128, tiles of 128 rows, 8 or 16 worker warps");
 static_assert(!TC2 || T2_LP + TX2 <= 512, "two-pass kernel: tensor memory columns");
 static_assert(!TC2 || T2_NVMAX <= 256, "two-pass kernel: N of the vertical product");
-// after the max plane and argmax plane: the NMS chunk ballots
-constexpr int T2_MASKS = ((T2M * T2_MS * 4 + T2M * TX2) + 15) & ~15;
-constexpr int T2_NCHUNK = (TY * TX + 31) / 32;
-static_assert(!TC2 || T2_MASKS + 4 * T2_NCHUNK <= 2 * T2_AH_PART, "two-pass kernel: max plane");
+// the tile-end maxima test's exchange arrays (segment edges, boundary rows,
+// counts and their prefix), then its stashed responses and argmaxes, in the
+// split rows' space
+constexpr int T2_NMS_VALS = 8192;
+static_assert(!TC2 || (4 * (T2M * 2 * 2 + 8 * TX2 + 2 * T2M * 2) <= T2_NMS_VALS &&
+                       T2_NMS_VALS + 5 * TX2 * T2M <= 2 * T2_AH_PART),
+              "two-pass kernel: tile-end maxima space");
 
 static_assert(TX2 % 4 == 0, "tile width must be a multiple of 4");
 static_assert(TY >= 1, "tile height");
@@ -2317,93 +2319,157 @@ __device__ __forceinline__ int t2_scan(int v, int *buf, int *sum, int wt) {
     return before + x - v;
 }
 
-// (no early exit: the nine loads are independent and issue together)
-__device__ __forceinline__ bool t2_cand(const float *mp, int m, int c, float thr, float *v) {
-    const float *row = mp + m * T2_MS + c;
-    const float x = row[0];
-    *v = x;
-    const float nb = fmaxf(fmaxf(fmaxf(row[-T2_MS - 1], row[-T2_MS]), fmaxf(row[-T2_MS + 1], row[-1])),
-                           fmaxf(fmaxf(row[1], row[T2_MS - 1]), fmaxf(row[T2_MS], row[T2_MS + 1])));
-    return x > thr && !(nb > x);
-}
-
-// The tile's maxima (Eq. 3 with the 3x3 test of §3) in row-major order into
-// its candidate slots; the true count into tile_count.  The tile's output
-// pixels are cut into row-major chunks of 32 (one per lane), each worker
-// warp a contiguous run of chunks; a first pass records each chunk's ballot
-// of candidates, a scan over the warps gives the offsets, a second pass
-// writes the chunks that have candidates.
-__device__ __forceinline__ void t2_nms(const MhfdKHeader &h, const T2State &t, const T2Tile &tl,
-                                       long long slot, int wt) {
-    constexpr int NWW = T2_NW / 32;
-    const float *mp = reinterpret_cast<const float *>(t.ahp());
-    const unsigned char *ap = t.ahp() + T2M * T2_MS * 4;
-    unsigned *masks = reinterpret_cast<unsigned *>(t.ahp() + T2_MASKS);
-    const int ny = min(TY, h.H - tl.oy), nx = min(TX, h.W - tl.ox);
-    const int items = ny * nx;
-    const int nch = (items + 31) / 32;
-    const int warp = wt >> 5, lane = wt & 31;
-    const int cb = warp * nch / NWW, ce = (warp + 1) * nch / NWW;
-    const float thr = h.thr;
-    // pixel p of the chunk run: row r, column cx, advanced by 32 per chunk
-    // (nx >= 1; at most 32 / nx rows a step) instead of a division per pixel
-    constexpr int CU = 4;  // chunks per iteration
-    int p = 32 * cb + lane;
-    int r = p / nx, cx = p - r * nx;
-    int cnt = 0;
-#pragma unroll 1
-    for (int c = cb; c < ce; c += CU) {
-        bool f[CU];
+// The tile's maxima (Eq. 3 with the 3x3 test of §3) from the running max
+// each worker thread holds for its row segment (TMEM lane m' = computed row
+// 127 - m', columns CQ q .. CQ q + CQ - 1 reversed): the rows above and below
+// are the neighbouring lanes (warp shuffles), the segment edges and the rows
+// at the lane-group boundaries pass through shared memory (the split rows'
+// space, free once the last horizontal product is done).  Candidates go to
+// the tile's slots in row-major order (a scan of the per-segment counts in
+// that order); the true count to tile_count.
+__device__ __forceinline__ void t2_nms_regs(const MhfdKHeader &h, const T2State &t, const T2Tile &tl,
+                                            T2Px &px, long long slot, int wt) {
+    constexpr int CQ = T2_CQ;
+    const float ninf = -__int_as_float(0x7f800000);
+    float *xc = reinterpret_cast<float *>(t.ahp());  // [128 lanes][CP][2] segment edges
+    float *xr = xc + T2M * T2_CP * 2;                 // [4 groups][2 ends][CP][CQ] boundary rows
+    int *cnt = reinterpret_cast<int *>(xr + 8 * T2_CP * CQ);  // [128 rows][CP] counts, row-major
+    int *pre = cnt + T2M * T2_CP;                              // their exclusive prefix
+    const int w = wt >> 5, lane = wt & 31, g = w & 3, q = w >> 2;
+    const int mr = 32 * g + lane;        // tensor-memory lane
+    const int m = T2M - 1 - mr;          // computed row
+    const int gy = tl.oy - 1 + m;
+    const bool rowin = gy >= 0 && gy < h.H;
+    // out-of-image pixels compare as -inf
 #pragma unroll
-        for (int u = 0; u < CU; ++u) {
-            float v;
-            f[u] = c + u < ce && p < items && t2_cand(mp, 1 + r, 1 + cx, thr, &v);
-            p += 32;
-            cx += 32;
-            while (cx >= nx) {
-                cx -= nx;
-                ++r;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < CU; ++u) {
-            const unsigned m = __ballot_sync(0xffffffffu, f[u]);
-            if (lane == 0 && c + u < ce && mk_ok(c + u < T2_NCHUNK)) masks[c + u] = m;
-            cnt += __popc(m);
-        }
+    for (int u = 0; u < CQ; ++u) {
+        const int gx = tl.ox - 1 + (TX2 - 1 - (CQ * q + u));
+        if (!(rowin && gx >= 0 && gx < h.W)) px.mx[u] = ninf;
     }
-    int *buf = t.scan();
-    if (lane == 0) buf[warp] = cnt;
+    if (mk_ok(mr < T2M && q < T2_CP)) {
+        xc[(mr * T2_CP + q) * 2 + 0] = px.mx[0];
+        xc[(mr * T2_CP + q) * 2 + 1] = px.mx[CQ - 1];
+    }
+    if (lane == 0 || lane == 31) {
+        float *dst = xr + ((g * 2 + (lane == 31 ? 1 : 0)) * T2_CP + q) * CQ;
+#pragma unroll
+        for (int u = 0; u < CQ; ++u) dst[u] = px.mx[u];
+    }
     t2_wsync();
-    int pos = 0, total = 0;
+    // neighbour rows of lanes 0 and 31 (other lane groups; -inf past the tile)
+    const float *rup = lane == 0 && g > 0 ? xr + (((g - 1) * 2 + 1) * T2_CP + q) * CQ : nullptr;
+    const float *rdn = lane == 31 && g < 3 ? xr + (((g + 1) * 2 + 0) * T2_CP + q) * CQ : nullptr;
+    // column max of the three rows just outside the segment (other part)
+    auto edge = [&](int qq, int e) {
+        if (qq < 0 || qq >= T2_CP) return ninf;
+        float v = xc[(mr * T2_CP + qq) * 2 + e];
+        if (mr > 0) v = fmaxf(v, xc[((mr - 1) * T2_CP + qq) * 2 + e]);
+        if (mr < T2M - 1) v = fmaxf(v, xc[((mr + 1) * T2_CP + qq) * 2 + e]);
+        return v;
+    };
+    float cprev = edge(q - 1, 1);  // n' = CQ q - 1
+    const float cend = edge(q + 1, 0);  // n' = CQ q + CQ
+    const float thr = h.thr;
+    const bool rowint = rowin && m >= 1 && m <= T2M - 2;
+    unsigned flags = 0;
+    float vcur = 0.0f, ccur = 0.0f;  // column u: max of the rows above and below; of all three
 #pragma unroll
-    for (int w = 0; w < NWW; ++w) {
-        const int tt = buf[w];
-        pos += w < warp ? tt : 0;
-        total += tt;
+    for (int u = 0; u <= CQ; ++u) {
+        float vn = 0.0f, cn = cend;
+        if (u < CQ) {
+            // (volatile: the shuffles stay in column order, so the compiler
+            // does not hold all of them in registers at once)
+            float up, dn;
+            asm volatile("shfl.sync.up.b32 %0, %1, 1, 0, 0xffffffff;" : "=f"(up) : "f"(px.mx[u]));
+            asm volatile("shfl.sync.down.b32 %0, %1, 1, 31, 0xffffffff;" : "=f"(dn) : "f"(px.mx[u]));
+            if (lane == 0) up = rup ? rup[u] : ninf;
+            if (lane == 31) dn = rdn ? rdn[u] : ninf;
+            vn = fmaxf(up, dn);
+            cn = fmaxf(vn, px.mx[u]);
+        }
+        if (u > 0) {
+            // pixel u - 1: its neighbours are the column maxima at u - 2 and u
+            // and the rows above and below at u - 1
+            const int uu = u - 1;
+            const float x = px.mx[uu];
+            const float nb = fmaxf(fmaxf(cprev, cn), vcur);
+            const int c = TX2 - 1 - (CQ * q + uu);
+            if (rowint && c >= 1 && c <= TX2 - 2 && x > thr && !(nb > x)) flags |= 1u << uu;
+            cprev = ccur;
+        }
+        vcur = vn;
+        ccur = cn;
     }
-    if (mk_ok(slot >= 0)) {
+    // the flagged responses and argmaxes to shared memory (column u of
+    // thread wt at [u][wt]), so that the writes below take a rolled loop
+    float *smx = reinterpret_cast<float *>(t.ahp() + T2_NMS_VALS);
+    unsigned char *sag = t.ahp() + T2_NMS_VALS + 4 * CQ * T2_NW;
+#pragma unroll
+    for (int u = 0; u < CQ; ++u)
+        if (flags & (1u << u)) {
+            smx[u * T2_NW + wt] = px.mx[u];
+            sag[u * T2_NW + wt] = (unsigned char)t2_ag(px, u);
+        }
+    // positions: segments in row-major order (row m ascending, column
+    // ascending = part descending)
+    const int rank = m * T2_CP + (T2_CP - 1 - q);
+    if (mk_ok(rank >= 0 && rank < T2M * T2_CP)) cnt[rank] = __popc(flags);
+    t2_wsync();
+    {
+        constexpr int NWW = T2_NW / 32;
+        static_assert(T2M * T2_CP == T2_NW, "one count per worker thread");
+        const int v = cnt[wt];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        int *buf = t.scan();
+        if (lane == 31) buf[w] = x;
+        t2_wsync();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int ww = 0; ww < NWW; ++ww) {
+            const int tt = buf[ww];
+            before += ww < w ? tt : 0;
+            total += tt;
+        }
+        pre[wt] = before + x - v;
+        if (wt == 0) h.tile_count[slot] = total;
+    }
+    t2_wsync();
+    int pos = pre[rank];
+    if (flags && mk_ok(slot >= 0)) {
         MhfdCand *dst = h.stage + slot * h.cap_tile;
+        // set bits from the highest column index u (lowest image column)
 #pragma unroll 1
-        for (int c = cb; c < ce; ++c) {
-            const unsigned m = masks[c];
-            if (m & (1u << lane)) {
-                const int p = 32 * c + lane;
-                const int r = p / nx, cx = p - r * nx;
-                const int idx = pos + __popc(m & ((1u << lane) - 1u));
-                if (idx < h.cap_tile) {
-                    MhfdCand cd;
-                    cd.x = tl.ox + cx;
-                    cd.y = tl.oy + r;
-                    cd.i = ap[(1 + r) * TX2 + 1 + cx];
-                    cd.resp = mp[(1 + r) * T2_MS + 1 + cx];
-                    dst[idx] = cd;
-                }
+        for (unsigned f = flags; f; ++pos) {
+            const int uu = 31 - __clz(f);
+            f &= ~(1u << uu);
+            if (pos < h.cap_tile) {
+                MhfdCand cd;
+                cd.x = tl.ox - 1 + (TX2 - 1 - (CQ * q + uu));
+                cd.y = gy;
+                cd.i = sag[uu * T2_NW + wt];
+                cd.resp = smx[uu * T2_NW + wt];
+                dst[pos] = cd;
             }
-            pos += __popc(m);
         }
     }
-    if (wt == 0) h.tile_count[slot] = total;
+    if (STORE && rowint) {
+#pragma unroll
+        for (int uu = 0; uu < CQ; ++uu) {
+            const int c = TX2 - 1 - (CQ * q + uu);
+            const int gx = tl.ox - 1 + c;
+            if (c >= 1 && c <= TX2 - 2 && gx < h.W && mk_ok(gx >= 0)) {
+                const long long o2 = (long long)gy * h.W + gx;
+                if (h.m_out) h.m_out[o2] = px.mx[uu];
+                if (h.arg_out) h.arg_out[o2] = t2_ag(px, uu);
+            }
+        }
+    }
+    t2_wsync();  // the exchange space is the next tile's split rows
 }
 
 // worker levels: wait for level l's V, split it, build level l + 2's tap
@@ -2505,41 +2571,14 @@ __device__ __forceinline__ void t2_range(const MhfdKHeader &h, long long k0, lon
         t2_wait(h, t, T2_HB + (int)(gl & 1u));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         t2_epi(h, t, NL - 1, ((unsigned)T2_DH + ((gl) & 1u) * (unsigned)TX2), wt, px, ts.a, tl);
-        // the tile's max plane (natural order; -inf outside the image) in the
-        // split rows' space, free once the last horizontal product is done
-        {
-            float *mp = reinterpret_cast<float *>(t.ahp());
-            unsigned char *ap = t.ahp() + T2M * T2_MS * 4;
-            const int w = wt >> 5, g = w & 3, q = w >> 2;
-            const int m = T2M - 1 - (32 * g + (wt & 31));
-            const int gy = tl.oy - 1 + m;
-            const bool rowin = gy >= 0 && gy < h.H;
-#pragma unroll
-            for (int u = 0; u < T2_CQ; ++u) {
-                const int c = TX2 - 1 - (T2_CQ * q + u);
-                const int gx = tl.ox - 1 + c;
-                const bool in = rowin && gx >= 0 && gx < h.W;
-                mp[m * T2_MS + c] = in ? px.mx[u] : -__int_as_float(0x7f800000);
-                ap[m * TX2 + c] = (unsigned char)t2_ag(px, u);
-                if (STORE && in && m >= 1 && m <= T2M - 2 && c >= 1 && c <= TX2 - 2) {
-                    const long long o2 = (long long)gy * h.W + gx;
-                    if (h.m_out) h.m_out[o2] = px.mx[u];
-                    if (h.arg_out) h.arg_out[o2] = t2_ag(px, u);
-                }
-            }
-        }
-        // the next tile's window and first two tap matrices (the last
-        // vertical product is done; the responses are in the max plane, so
-        // the loads have the registers), then this tile's maxima while the
-        // tensor core starts the next tile
+        // the tile's maxima (Eq. 3 with the 3x3 test of §3) from the
+        // responses in registers, then the next tile's window
+        const int tx = (int)(k / tiles_y), ty = (int)(k - (long long)tx * tiles_y);
+        t2_nms_regs(h, t, tl, px, slot0 + (long long)ty * tiles_x + tx, wt);
         if (next) {
             t2_load_x(h, ts, t, tn.oy, tn.ox, tn.ox == tl.ox && tn.oy == tl.oy + TY, wt);
             t2_arrive(t2_bar(t, T2_XRB));
         }
-        t2_wsync();
-        const int tx = (int)(k / tiles_y), ty = (int)(k - (long long)tx * tiles_y);
-        t2_nms(h, t, tl, slot0 + (long long)ty * tiles_x + tx, wt);
-        t2_wsync();
         t.g += NL;
     }
 }

@@ -386,9 +386,8 @@ bool t2_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::
     const T2Geom g = t2_geom(R, c);
     if (g.nvmax > 256 || 2 * g.nvmax + 2 * c.tx2 > 512)
         return no("the two-pass kernel's V and L buffers exceed tensor memory for this ladder");
-    const int plane = ((128 * (c.tx2 + 1) * 4 + 128 * c.tx2) + 15) & ~15;
-    if (plane + 4 * ((126 * (c.tx2 - 2) + 31) / 32) > 2 * 16 * (g.khmax / 8) * 128)
-        return no("the tile's max plane does not fit the split rows' space");
+    if (8192 + 5 * c.tx2 * 128 > 2 * 16 * (g.khmax / 8) * 128)
+        return no("the tile-end maxima test does not fit the split rows' space");
     if (t2_smem(R, c) > kSmemLimitBytes) return no("does not fit in shared memory");
     return true;
 }
