@@ -83,6 +83,34 @@ def variant_ops_per_px(variant):
     return algorithmic_ops_per_px()
 
 
+def two_pass_mma_flops(H, W, tx2=64):
+    """Tensor-core flops one launch of the two-pass kernel issues on an H x W
+    image (the MMA shapes as issued: band zeros, fp16 hi/lo parts and tile
+    halos included): per 128-row tile and level, the vertical product (M 128,
+    N = the level's V columns, K = 128 + 2R rows, two tap parts) and the
+    horizontal one (N = tx2, K = tx2 + 2R columns, three part products)."""
+    _, R = ladder_radii()
+    rmax = max(R)
+    c16 = lambda v: (v + 15) & ~15  # noqa: E731
+    per_tile = 0
+    for r in R:
+        off = (rmax - r) & 7
+        per_tile += 2 * 2 * 128 * c16(off + tx2 + 2 * r) * c16(128 + 2 * r)
+        per_tile += 3 * 2 * 128 * tx2 * c16(tx2 + 2 * r)
+    tiles = -(-W // (tx2 - 2)) * -(-H // 126)
+    return per_tile * tiles
+
+
+def measured_bf16_peak():
+    """Dense bf16 tensor TFLOP/s measured on the GB300s (fp16 runs at
+    the same rate); None without the record."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def nominal_alu_peak():
     """FP32 FFMA lane-ops per second from unit counts and the maximum clock:
     152 SMs x 128 FP32 lanes x 2.07 GHz."""
@@ -380,17 +408,26 @@ def main():
     peak = nominal_alu_peak() / 1e12
     probe = mhfd.probe_ffma_peak() / 1e12
     traffic = profiled_traffic()
-    tc = dets[0].uses_tensor_cores
+    kern = dets[0].tensor_core_kernel
+    tc = kern == 1
     side = ffma_side_ops_per_px() * H * W / (k_avg * 1e-3) / 1e12
+    tpeak = measured_bf16_peak()
+    tflops = two_pass_mma_flops(H, W) / (k_avg * 1e-3) / 1e12 if kern == 2 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 FFMA)",
             "frac": achieved / peak, "traffic": traffic,
             "peak_note": "152 SMs x 128 FP32 lanes x 2.07 GHz (nominal; no FP32 figure in "
                          "MEASURED_PEAKS)", "probe_measured_peak": probe,
             "frac_of_probe": achieved / probe, "ops_per_px": algorithmic_ops_per_px(),
-            "vertical_pass": "tensor cores (tcgen05 MMA, fp16 parts, f32 accumulate)" if tc
-                             else "FP32 FFMA",
+            "blur_passes": ("both on the tensor cores (tcgen05 MMA, fp16 parts, f32 "
+                            "accumulate)" if kern == 2 else
+                            "vertical on the tensor cores, horizontal FFMA" if tc else "FFMA"),
             "ffma_side": {"ops_per_px": ffma_side_ops_per_px(), "achieved": side,
                           "frac": side / peak} if tc else None,
+            "tensor": {"issued_tflops": tflops, "peak": tpeak, "unit": "TFLOP/s f16",
+                       "frac": tflops / tpeak if tpeak else None,
+                       "peak_note": "measured bf16 burst (MEASURED_PEAKS), f16 the same rate",
+                       "issued_note": "MMA work as issued: band zeros, hi/lo parts, halos"}
+                      if kern == 2 else None,
             "kernel_ms_avg": k_avg,
             "kernel_timing": "CUDA events on the launching stream around each fused launch "
                              "(with the tensor-core kernel also its gated FFMA companion, "
@@ -460,7 +497,8 @@ def main():
     line = headline_line(
         value=value, world=world, steps=args.steps, warmup=args.warmup, total_ms=total_ms,
         p50=statistics.median(per_tile), p99=p99, plain=plain, achieved=achieved, peak=peak,
-        traffic=traffic, k_avg=k_avg, side=side if tc else None, cpu=cpu, e2e=e2e,
+        traffic=traffic, k_avg=k_avg, side=side if tc else None,
+        tensor=(tflops, tpeak) if tflops is not None else None, cpu=cpu, e2e=e2e,
         launches=launches_per_tile * len(tiles) * args.steps,
         clocks={k: v for k, v in clk.summary().items() if k != "samples"}, scores=scores,
         summary=summary_of(batched, serving, soft_sec, variants))
@@ -493,7 +531,7 @@ def summary_of(batched, serving, soft_sec, variants):
 
 
 def headline_line(*, value, world, steps, warmup, total_ms, p50, p99, plain, achieved, peak,
-                  traffic, k_avg, side, cpu, e2e, launches, clocks, scores, summary):
+                  traffic, k_avg, side, cpu, e2e, launches, clocks, scores, summary, tensor=None):
     """The result line (the last line bench.py prints): the contract's keys,
     latency, the plain path, the roofline of the fused kernel, the CPU
     baseline, end to end, and the summary; short enough (under 1500
@@ -510,10 +548,13 @@ def headline_line(*, value, world, steps, warmup, total_ms, p50, p99, plain, ach
         "plain": {"value": r4(plain["value"]), "p50_ms_per_tile": r4(plain["p50_ms_per_tile"])}
                  if plain else None,
         "fused_vs_plain": r4(value / world / plain["value"]) if plain else None,
-        "roofline": {"bound": "alu", "achieved": r4(achieved), "peak": r4(peak),
-                     "unit": "Tops/s FP32", "frac": r4(achieved / peak),
-                     "traffic": traffic, "kernel_ms_avg": r4(k_avg),
-                     "ffma_side_frac": r4(side / peak) if side is not None else None},
+        "roofline": {k: v for k, v in (
+            ("bound", "alu"), ("achieved", r4(achieved)), ("peak", r4(peak)),
+            ("unit", "Tops/s FP32"), ("frac", r4(achieved / peak)), ("traffic", traffic),
+            ("kernel_ms_avg", r4(k_avg)),
+            ("ffma_side_frac", r4(side / peak) if side is not None else None),
+            ("tensor_frac", r4(tensor[0] / tensor[1]) if tensor and tensor[1] else None))
+            if v is not None or k == "traffic"},
         "cpu_baseline": {k: r4(v) if isinstance(v, float) else v for k, v in cpu.items()
                          if k != "single_core"} if cpu else None,
         "e2e": {k: r4(v) if isinstance(v, float) else v for k, v in e2e.items()},
@@ -560,6 +601,8 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
     kw = dict(threshold=THR, overlap=OVERLAP, nms="paper")
     return {
         "fused_reflect": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), False),
+        "fused_reflect_vtc": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, tensor_cores=2,
+                                                 **kw), False),
         "fused_reflect_ffma": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, tensor_cores=False,
                                                   **kw), False),
         "fused_periodic": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, boundary="periodic",
@@ -591,7 +634,10 @@ def bench_soft(mhfd, torch, stream, count=64, held_out=16):
     render_s = time.perf_counter() - t0
     imgs = [torch.from_numpy(p[0]).cuda() for p in pairs]
     sds = [p[1] for p in pairs]
-    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR)
+    # float tiles take the FFMA kernel; tensor_cores=2 gives it the wide
+    # strips of the vertical-pass kernel's grid (the two-pass kernel's grid
+    # has 64-column strips)
+    det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, tensor_cores=2)
     w = torch.linspace(-0.5, 1.5, N_LAYERS, device="cuda")
     tau, temp = THR, 0.01
 
@@ -837,8 +883,13 @@ def tile_used(mhfd):
     import torch
     from paper_2108_12050_gb300 import tune
     sms = torch.cuda.get_device_properties(0).multi_processor_count
+    shape = mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX, tensor_cores=True)
+    if shape[1] == 128:  # the two-pass kernel (the default for this workload)
+        return {"kernel": "two-pass (both blur passes on the tensor cores)",
+                "strip_width": shape[0], "tile_rows": shape[1], "threads": shape[3],
+                "source": "built-in"}
     tuned = tune.lookup(N_LAYERS, T_MIN, T_MAX, "paper", sms, tensor_cores=True)
-    shape = tuned or mhfd.chosen_tile(n=N_LAYERS, t_min=T_MIN, t_max=T_MAX, tensor_cores=True)
+    shape = tuned or shape
     return {"width": shape[0], "height": shape[1], "rows_per_step": shape[2],
             "threads": shape[3], "level_groups": shape[4],
             "rows_per_item": shape[5] if len(shape) > 5 else 1,

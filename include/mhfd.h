@@ -101,19 +101,30 @@ typedef struct {
                                score (DoG only) supports both */
     int32_t boundary;       /* mhfd_boundary; every entry point but the soft
                                score (reflect only) supports both */
-    int32_t tensor_cores;   /* 1: the fused kernel's vertical blur runs on the
-                               tensor cores (tcgen05, fp16 operands that hold
-                               the window exactly and the taps as two parts,
-                               f32 accumulation) for detection of uint8
-                               images and of uint16 images whose stretch range
-                               hi - lo is at most 4095; other images and modes
-                               take the FFMA kernel (same results within the
-                               FP32 tolerance).  tile_shape / tile_override
-                               then describe the tensor-core kernel (four rows
-                               per step, at least 128 threads).  The paper
-                               rule (DoG or LoG response) and the
-                               26-neighbour rule (DoG response); 0: FFMA
-                               only.  Default 1 */
+    int32_t tensor_cores;   /* detection of uint8 images and of uint16
+                               images whose stretch range hi - lo is at most
+                               4095 runs on the tensor cores (tcgen05, fp16
+                               operands that hold the window exactly and the
+                               taps as two parts, f32 accumulation); other
+                               images take the FFMA kernel (same results
+                               within the FP32 tolerance).
+                               1 (default): the paper rule with the DoG
+                               response runs both blur passes as products
+                               (the two-pass kernel: tiles of 126 output rows,
+                               the V rows split into fp16 hi + lo parts for
+                               the horizontal product); tile_shape[0] > 0
+                               then sets its strip width (a multiple of 16,
+                               at most 128, incl. the 2 NMS border columns).
+                               The LoG response, the 26-neighbour rule and
+                               ladders too wide for the two-pass kernel take
+                               the vertical-pass kernel of 2.
+                               2: the vertical blur on the tensor cores, the
+                               horizontal on FFMA (the vertical-pass kernel:
+                               the paper rule with either response, the
+                               26-neighbour rule with the DoG response);
+                               tile_shape / tile_override then describe it
+                               (four rows per step, at least 128 threads).
+                               0: FFMA only. */
 } mhfd_params;
 
 /* A detected feature.  scale_idx is the 0-based DoG layer i-1; sigma = t_i,
@@ -192,9 +203,9 @@ int mhfd_detect_batch(mhfd_detector *det, int32_t n, const void *const *d_imgs,
  * MHFD_WARN_OVERFLOW if any image overflowed, or an error. */
 int mhfd_result_wait_batch(mhfd_detector *det, mhfd_result *outs, int32_t n);
 
-/* 1 if the detector runs the tensor-core vertical pass (params.tensor_cores
- * and the paper rule, DoG or LoG response), 0 if not, negative on error.
- * Host only. */
+/* 2 if the detector's narrow-range detections run the two-pass
+ * tensor-core kernel, 1 if they run the vertical-pass tensor-core kernel,
+ * 0 if FFMA only (see params.tensor_cores), negative on error.  Host only. */
 int mhfd_uses_tensor_cores(mhfd_detector *det);
 
 /* 1 if the last batch ran from a captured CUDA graph, 0 if its kernels were

@@ -118,11 +118,11 @@ class Detector:
     maximum rule (``"paper"``: argmax over scales then 3x3 max-pool;
     ``"local26"``: 3x3x3 scale-space maxima), the kernel truncation and the
     stretch saturation fraction.  ``sigmas`` gives an explicit ladder of
-    ``n+1`` scales instead.  ``tensor_cores`` (default) runs the vertical
-    blur of the fused kernel on the tensor cores for the paper rule (DoG or
-    LoG response) on uint8 images and on uint16 images whose stretch range
-    is at most 4095; the FFMA kernel takes everything else (``False``: FFMA
-    only).
+    ``n+1`` scales instead.  ``tensor_cores`` (default ``True``) runs
+    detections of uint8 images and of uint16 images whose stretch range is
+    at most 4095 on the tensor cores: both blur passes for the paper rule
+    with the DoG response, the vertical pass otherwise (``2``: the
+    vertical-pass kernel for every mode; ``False``: FFMA only).
     """
 
     def __init__(self, n=10, t_min=1.0, t_max=10.0, *, sigmas=None, threshold=0.1, overlap=0.5,
@@ -140,7 +140,11 @@ class Detector:
                 sms = torch.cuda.get_device_properties(device).multi_processor_count
                 is_log = response in ("log", 1)
                 tc = bool(tensor_cores) and (nms in ("paper", 0) or not is_log)
-                tile_shape = None if tensor_cores == 2 else tune.lookup(n, t_min, t_max, nms, sms, truncate,
+                # the tuned shapes are the vertical-pass kernel's: the default
+                # for the paper rule with the DoG response is the two-pass kernel
+                two_pass = tensor_cores is True or tensor_cores == 1
+                two_pass = two_pass and nms in ("paper", 0) and not is_log
+                tile_shape = None if two_pass else tune.lookup(n, t_min, t_max, nms, sms, truncate,
                                          "log" if is_log else "dog", tensor_cores=tc)
         tile_override = tile_override or 0
         self.n = int(n)
@@ -172,8 +176,13 @@ class Detector:
 
     @property
     def uses_tensor_cores(self):
-        """Whether the fused kernel's vertical pass runs on the tensor cores."""
+        """Whether the fused kernel runs on the tensor cores (either kernel)."""
         return bool(_n.lib().mhfd_uses_tensor_cores(self._h))
+
+    @property
+    def tensor_core_kernel(self):
+        """2: both blur passes on the tensor cores; 1: the vertical pass; 0: FFMA."""
+        return int(_n.lib().mhfd_uses_tensor_cores(self._h))
 
     # --------------------------------------------------------------- core
     def close(self):

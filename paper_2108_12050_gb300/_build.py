@@ -139,10 +139,12 @@ def _tuned_variants():
             if shape and len(shape) in (5, 6):
                 nms = 0 if m.group(4) == "paper" else 1
                 log = m.group(5) is not None
-                tc = m.group(6) is not None
+                # (tensor-core shapes are the vertical-pass kernel's: 2)
+                tc = 2 if m.group(6) is not None else False
                 # an FFMA shape of the paper rule serves detectors built with
-                # tensor_cores=False; a tensor-core shape, with its companion
-                # (which the soft score also uses), the default ones
+                # tensor_cores=False; a vertical-pass tensor-core shape, with
+                # its companion, detectors built with tensor_cores=2 (and the
+                # default ones of the LoG response and the 26-neighbour rule)
                 stores = (0, 1) if (nms == 1 or log) else (0, 1, 2)
                 for store in stores:
                     out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)), nms,

@@ -486,16 +486,17 @@ void fused_ladder(const mhfd_params &p, const std::vector<double> &t, const std:
 int resolve_tile(const std::vector<int> &R, int mode, const mhfd_params &p, TileConfig *cfg,
                  bool tc = false) {
     std::string why;
-    if (tc && p.tensor_cores == 2 && t2_mode_ok(mode)) {
-        // both blur passes on the tensor cores; tile_shape[0] picks the strip width
+    if (tc && p.tensor_cores == 1 && t2_mode_ok(mode)) {
+        // both blur passes on the tensor cores (the default for the paper
+        // rule with the DoG response); tile_shape[0] picks the strip width;
+        // a ladder too wide for it takes the vertical-pass kernel below
         if (p.tile_shape[0] > 0) {
             *cfg = t2_config((int)R.size(), p.tile_shape[0]);
             if (!t2_shape_ok(R, mode, *cfg, &why))
                 return fail(MHFD_ERR_UNSUPPORTED, "tile_shape (two-pass kernel): " + why);
             return MHFD_OK;
         }
-        if (!choose_tile_t2(R, mode, cfg, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
-        return MHFD_OK;
+        if (choose_tile_t2(R, mode, cfg, &why)) return MHFD_OK;
     }
     if (tc) {
         if (p.tile_shape[0] > 0) {
@@ -1115,7 +1116,12 @@ int mhfd_precompile(const mhfd_params *p, int32_t store) {
     }
     if ((store == 2 || store == 3) && lk.response)
         return fail(MHFD_ERR_UNSUPPORTED, "the soft score uses the DoG response");
-    if (store == 2) return precompile_variant(lk, 2, 0, cfg);  // soft-score forward
+    if (store == 2) {  // soft-score forward (its own FFMA shape)
+        TileConfig cs;
+        std::string why;
+        if (!choose_tile(lk.R, 2, &cs, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+        return precompile_variant(lk, 2, 0, cs);
+    }
     if (store == 3) {  // the soft-score adjoint's single-level blurs
         for (size_t l = 0; l < R.size(); ++l) {
             LadderKey l1;
@@ -1347,10 +1353,17 @@ int mhfd_soft_score(mhfd_detector *d, const void *img, int32_t dtype, int32_t H,
         return enqueue_soft_mask(img, dtype, H, W, (long long)pitch, d->st, d->pI, d_dimg, s);
     }
     // forward only: the fused kernel accumulates the sigmoids per block
-    if (!d->var_soft && (rc = get_variant(d->lk, 2, 0, d->cfg, &d->var_soft))) return rc;
+    // (its own FFMA shape: it stores no candidates, so it need not share the
+    // detection kernels' tile grid)
+    if (!d->var_soft) {
+        TileConfig cs;
+        std::string why;
+        if (!choose_tile(d->lk.R, 2, &cs, &why)) return fail(MHFD_ERR_UNSUPPORTED, why);
+        if ((rc = get_variant(d->lk, 2, 0, cs, &d->var_soft))) return rc;
+    }
     Variant *v = d->var_soft;
-    int tx, ty;
-    const int n_tiles = tiles_of(d, H, W, &tx, &ty);
+    const int tx = (W + v->cfg.tx2 - 3) / (v->cfg.tx2 - 2), ty = (H + v->cfg.ty2 - 3) / (v->cfg.ty2 - 2);
+    const int n_tiles = tx * ty;
     int dev = 0, sms = 1;
     MHFD_CUDA(cudaGetDevice(&dev));
     MHFD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -94,8 +94,25 @@ def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
     assert any(f.endswith(".cubin") for f in files)
 
 
+def test_two_pass_tile_choice(native):
+    """The default for the paper rule with the DoG response is the two-pass
+    kernel: tiles of 128 computed rows, strips of 16-multiple width (64 by
+    default), 288 threads; tile_shape[0] sets the strip width; the LoG
+    response and the 26-neighbour rule keep the vertical-pass kernel."""
+    kw = dict(n=16, t_min=1.0, t_max=12.0)
+    assert native.chosen_tile(tensor_cores=True, **kw) == (64, 128, 4, 288, 1, 1)
+    assert native.chosen_tile(tensor_cores=True, tile_shape=(48, 0, 0, 0, 1), **kw)[:2] == (48, 128)
+    for bad in ((72, 0, 0, 0, 1), (144, 0, 0, 0, 1)):  # not a multiple of 16; wider than 128
+        with pytest.raises(native.MhfdError) as e:
+            native.chosen_tile(tensor_cores=True, tile_shape=bad, **kw)
+        assert e.value.code == -2, bad
+    assert native.chosen_tile(tensor_cores=True, response=1, **kw)[1] != 128
+    assert native.chosen_tile(tensor_cores=True, nms=1, **kw)[1] != 128
+    assert native.chosen_tile(tensor_cores=True, **kw) != native.chosen_tile(tensor_cores=2, **kw)
+
+
 def test_tensor_core_tile_menu(native):
-    """The tensor-core kernel's shapes: four or eight rows per step, whole
+    """The vertical-pass tensor-core kernel's shapes (tensor_cores=2): four or eight rows per step, whole
     warps, at least one warpgroup, one or two horizontal items per thread
     (one-row items at four rows per step, two-row items at four or eight);
     the 26-neighbour rule (DoG response) has shapes of its own;
@@ -109,7 +126,7 @@ def test_tensor_core_tile_menu(native):
             rows, cols = (2, 4) if item == 2 else (1, 2) if item == 3 else (1, 4)
             assert (rb // rows) * tx2 // cols <= 2 * nt and (item == 2 or rb == 4)
         assert any(s[5] == 2 and s[2] == 8 for s in menu)
-        chosen = native.chosen_tile(tensor_cores=True, **kw)
+        chosen = native.chosen_tile(tensor_cores=2, **kw)
         assert chosen in menu and chosen[0] == chosen[3] - 32
     # the LoG response and the 26-neighbour rule have tensor-core shapes of
     # their own; the 26-neighbour rule with the LoG response takes the FFMA
@@ -123,7 +140,7 @@ def test_tensor_core_tile_menu(native):
 
 
 def test_explicit_tensor_core_tile_shape(native):
-    kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=True)
+    kw = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=2)
     assert native.chosen_tile(tile_shape=(352, 18, 4, 384, 3), **kw) == (352, 18, 4, 384, 3, 1)
     assert native.chosen_tile(tile_shape=(256, 18, 8, 288, 4, 2), **kw) == (256, 18, 8, 288, 4, 2)
     # rows per step other than 4 or 8, threads below a warpgroup, eight rows
@@ -182,7 +199,7 @@ def test_tuned_shapes_are_valid_for_their_ladders(native):
         assert m, key
         kw = dict(n=int(m.group(1)), t_min=float(m.group(2)), t_max=float(m.group(3)),
                   nms=m.group(4), response="log" if m.group(5) else "dog",
-                  tensor_cores=m.group(6) is not None)
+                  tensor_cores=2 if m.group(6) else False)  # the vertical-pass kernel's shapes
         for best in ent.values():
             shape = tuple(best["shape"])
             assert native.chosen_tile(tile_shape=shape, **kw) == shape + (1,) * (6 - len(shape))
@@ -197,15 +214,20 @@ def test_kernel_layout_matches_host_shared_memory_estimate(native, tmp_path, mon
     monkeypatch.setenv("MHFD_JIT_CACHE", str(tmp_path))
     small = dict(n=4, t_min=1.0, t_max=4.0)
     cases = [
-        (dict(tensor_cores=True, **small), 0),                     # paper rule, tensor cores
+        (dict(tensor_cores=True, **small), 0),                     # paper rule, two-pass kernel
+        (dict(tensor_cores=True, **small), 1),                     # its stack-storing variant
+        (dict(tensor_cores=2, **small), 0),                        # paper rule, vertical pass
         (dict(tensor_cores=True, response="log", **small), 0),     # LoG on tensor cores
         (dict(tensor_cores=False, nms="local26", **small), 0),     # 26-neighbour rule
         (dict(tensor_cores=False, boundary="periodic", **small), 1),  # stack-storing variant
         (dict(tensor_cores=False, **small), 2),                    # soft-score forward
         (dict(tensor_cores=False, **small), 3),                    # level blur of the adjoint
     ]
-    # first and last shapes of the tensor-core menu of the n = 16 ladder
-    full = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=True)
+    # the two-pass kernel at strip widths 48 and 64 on the n = 16 ladder;
+    # first and last shapes of the vertical-pass kernel's menu
+    cases += [(dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=True, tile_shape=(w, 0, 0, 0, 1)), 0)
+              for w in (48, 64)]
+    full = dict(n=16, t_min=1.0, t_max=12.0, tensor_cores=2)
     menu = native.tile_configs(**full)
     for shape in (menu[0], menu[-1]):
         cases.append((dict(tile_shape=shape, **full), 0))
@@ -215,7 +237,7 @@ def test_kernel_layout_matches_host_shared_memory_estimate(native, tmp_path, mon
               (dict(tile_shape=(256, 18, 8, 288, 4, 2), **full), 1),
               (dict(tile_shape=(320, 18, 4, 448, 3, 2), n=16, t_min=1.0, t_max=12.0,
                     tensor_cores=False), 0),
-              (dict(tile_shape=(96, 18, 4, 160, 1, 2), tensor_cores=True, response="log",
+              (dict(tile_shape=(96, 18, 4, 160, 1, 2), tensor_cores=2, response="log",
                     **small), 0),
               # one-row items of two outputs: 26-neighbour rule, LoG, stack-storing
               (dict(tile_shape=(192, 18, 4, 384, 2, 3), n=16, t_min=1.0, t_max=12.0,

@@ -57,7 +57,7 @@ def _batch_images():
     return imgs
 
 
-@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
+@pytest.mark.parametrize("tc", [True, 2, False], ids=["tc", "vtc", "ffma"])
 def test_batch_equals_single_detections(tc):
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
@@ -67,7 +67,7 @@ def test_batch_equals_single_detections(tc):
     devs = [_dev(i) for i in imgs]
     det = mhfd.Detector(16, 1.0, 12.0, threshold=0.05, overlap=0.5, tensor_cores=tc,
                         keep_candidates=True)
-    assert det.uses_tensor_cores == tc
+    assert det.uses_tensor_cores == bool(tc)
     singles = [det(d) for d in devs]
     for img, s in zip(imgs, singles):
         _held_to_oracle(img, s)

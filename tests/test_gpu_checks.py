@@ -29,12 +29,14 @@ L4 = dict(n=4, t_min=1.0, t_max=4.0, threshold=0.1)
 
 # (name, detector parameters, image (seed, H, W, dtype))
 CASES = [
-    ("tc_default", dict(L16), (91, 300, 420, "u16")),
+    ("tc_default", dict(L16), (91, 300, 420, "u16")),          # the two-pass kernel
+    ("vtc", dict(L16, tensor_cores=2), (91, 300, 420, "u16")),  # the vertical-pass kernel
     ("ffma", dict(L16, tensor_cores=False), (91, 300, 420, "u16")),
     ("local26", dict(L16, nms="local26"), (92, 260, 333, "u8")),
     ("log_tc", dict(L10, threshold=0.1 / 0.9, response="log"), (93, 200, 270, "u16")),
     ("periodic", dict(L10, boundary="periodic"), (94, 70, 45, "u16")),
-    ("two_row_tc", dict(L16, tile_shape=[256, 18, 8, 288, 4, 2]), (95, 300, 620, "u16")),
+    ("two_row_tc", dict(L16, tensor_cores=2, tile_shape=[256, 18, 8, 288, 4, 2]),
+     (95, 300, 620, "u16")),
     ("two_row_ffma", dict(L16, tensor_cores=False, tile_shape=[320, 18, 4, 448, 4, 2]),
      (95, 300, 620, "u16")),
     ("two_output_local26_ffma", dict(L16, nms="local26", tensor_cores=False,
@@ -82,7 +84,9 @@ def checked_env():
     kws = []
     for _, kw, _ in CASES:
         kw = dict(kw, nms=kw.get("nms", "paper"))
-        if "tile_shape" not in kw:   # the shape a Detector takes from the tuned table
+        two_pass = (kw.get("tensor_cores", True) in (True, 1) and kw["nms"] == "paper" and
+                    kw.get("response", "dog") == "dog")
+        if "tile_shape" not in kw and not two_pass:  # the shape a Detector takes from the table
             tc = kw.get("tensor_cores", True) and (kw["nms"] == "paper" or
                                                    kw.get("response", "dog") == "dog")
             kw["tile_shape"] = tune.lookup(kw["n"], kw["t_min"], kw["t_max"], kw["nms"], sms,

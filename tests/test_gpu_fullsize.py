@@ -73,12 +73,17 @@ def _detector(response, tc, thr):
                          tensor_cores=tc, response=response)
 
 
-@pytest.mark.parametrize("path", ["tc", "ffma", "plain"])
+# tc: the default (the two-pass kernel for the DoG, the vertical-pass kernel
+# for the LoG); vtc: the vertical-pass kernel; ffma; plain
+_TC = {"tc": True, "vtc": 2, "ffma": False, "plain": False}
+
+
+@pytest.mark.parametrize("path", ["tc", "vtc", "ffma", "plain"])
 def test_full_tile_detection_against_oracle(reference, path):
     r = reference
     img, ref, D_ref, t, thr = r["img"], r["ref"], r["D"], r["t"], r["thr"]
-    det = _detector(r["response"], path == "tc", thr)
-    assert det.uses_tensor_cores == (path == "tc")
+    det = _detector(r["response"], _TC[path], thr)
+    assert det.uses_tensor_cores == bool(_TC[path])
     dev = torch.from_numpy(img.view(np.int16)).cuda()
     if path == "plain":
         det.detect_plain(dev)
@@ -102,7 +107,7 @@ def test_full_tile_detection_against_oracle(reference, path):
     print("FULLSIZE " + json.dumps(stats))
 
 
-@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
+@pytest.mark.parametrize("tc", [True, 2, False], ids=["tc", "vtc", "ffma"])
 def test_full_tile_stack_within_tolerance(reference, tc):
     r = reference
     if r["sigma_d"] != 0.0:

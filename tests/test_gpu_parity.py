@@ -93,7 +93,7 @@ STACK_CASES = [
 ]
 
 
-@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
+@pytest.mark.parametrize("tc", [True, 2, False], ids=["tc", "vtc", "ffma"])
 @pytest.mark.parametrize("case", STACK_CASES, ids=lambda c: c[0])
 def test_response_stack_within_tolerance(case, tc):
     name, seed, H, W, dtype, n, tmin, tmax = case
@@ -149,7 +149,7 @@ def _check_detection(img, n, tmin, tmax, thr, overlap, nms, response="dog",
     return res, ref
 
 
-@pytest.mark.parametrize("tc", [True, False], ids=["tc", "ffma"])
+@pytest.mark.parametrize("tc", [True, 2, False], ids=["tc", "vtc", "ffma"])
 @pytest.mark.parametrize("which", ["A", "B"])
 def test_pair_512_uint8_end_to_end(which, tc):
     a, b = synth.pair512_u8(seed=1)
@@ -188,6 +188,15 @@ def test_headline_ladder_end_to_end(shape, dtype, sigma_d):
 # ------------------------------------------------ tensor-core vertical pass
 
 def test_tensor_core_pass_is_used_where_it_applies():
+    # both passes for the paper rule with the DoG response, the vertical pass
+    # for the other tensor-core modes and on request
+    assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1).tensor_core_kernel == 2
+    assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
+                    tensor_cores=2).tensor_core_kernel == 1
+    assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
+                    nms="local26").tensor_core_kernel == 1
+    assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9,
+                    response="log").tensor_core_kernel == 1
     assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1).uses_tensor_cores
     assert not detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
                         tensor_cores=False).uses_tensor_cores
@@ -424,8 +433,8 @@ def test_soft_score_rejects_the_log_response():
 
 # ------------------------------------------- two-row horizontal items (packed)
 
-@pytest.mark.parametrize("shape,tc", [((256, 18, 8, 288, 4, 2), True),
-                                      ((284, 18, 8, 320, 4, 2), True),
+@pytest.mark.parametrize("shape,tc", [((256, 18, 8, 288, 4, 2), 2),
+                                      ((284, 18, 8, 320, 4, 2), 2),
                                       ((320, 18, 4, 448, 3, 2), False)],
                          ids=["tc-256x8", "tc-284x8", "ffma-320x4"])
 def test_two_row_items_match_oracle(shape, tc):
@@ -436,7 +445,7 @@ def test_two_row_items_match_oracle(shape, tc):
     n, tmin, tmax = 16, 1.0, 12.0
     det = detector(n=n, t_min=tmin, t_max=tmax, threshold=0.05, tile_shape=list(shape),
                    tensor_cores=tc, keep_candidates=True)
-    assert det.uses_tensor_cores == tc
+    assert det.uses_tensor_cores == bool(tc)
     D, _, _, _ = det.debug_stack(to_dev(img), want=("D",))
     ref, D_ref, tol, t, _ = oracle_reference(img, n, tmin, tmax, 0.05, 0.5)
     assert_stack_close(D.cpu().numpy(), D_ref, str(shape))
