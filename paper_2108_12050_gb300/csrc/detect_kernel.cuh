@@ -2474,8 +2474,12 @@ __device__ __forceinline__ void t2_nms_regs(const MhfdKHeader &h, const T2State 
 
 // worker levels: wait for level l's V, split it, build level l + 2's tap
 // matrix, hand over; then the responses of level l - 1
+// (after the last level's split, the last vertical product is done: the
+// next tile's window loads then, so the tensor core runs this tile's last
+// horizontal product and the next tile's first vertical ones while the
+// workers finish this tile's responses and maxima)
 __device__ __forceinline__ void t2_work(const MhfdKHeader &h, T2State &t, const TcStretch &ts, T2Px &px,
-                                        const T2Tile &tl, int wt) {
+                                        const T2Tile &tl, bool next, const T2Tile &tn, int wt) {
 #pragma unroll 1
     for (int l = 0; l < NL; ++l) {
         const unsigned gl = t.g + (unsigned)l;
@@ -2484,6 +2488,10 @@ __device__ __forceinline__ void t2_work(const MhfdKHeader &h, T2State &t, const 
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         t2_split(t, l, (gl & 1u) * (unsigned)T2_NVMAX, wt);
         t2_arrive(t2_bar(t, T2_SPL));
+        if (l == NL - 1 && next) {
+            t2_load_x(h, ts, t, tn.oy, tn.ox, tn.ox == tl.ox && tn.oy == tl.oy + TY, wt);
+            t2_arrive(t2_bar(t, T2_XRB));
+        }
         if (l > 0)
             t2_epi(h, t, l - 1, (unsigned)T2_DH + ((gl - 1u) & 1u) * (unsigned)TX2, wt, px, ts.a, tl);
     }
@@ -2566,19 +2574,15 @@ __device__ __forceinline__ void t2_range(const MhfdKHeader &h, long long k0, lon
         const bool next = k + 1 < k1;
         const T2Tile tn = t2_tile(next ? k + 1 : k, tiles_y);
         T2Px px;
-        t2_work(h, t, ts, px, tl, wt);
+        t2_work(h, t, ts, px, tl, next, tn, wt);
         const unsigned gl = t.g + NL - 1;
         t2_wait(h, t, T2_HB + (int)(gl & 1u));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         t2_epi(h, t, NL - 1, ((unsigned)T2_DH + ((gl) & 1u) * (unsigned)TX2), wt, px, ts.a, tl);
         // the tile's maxima (Eq. 3 with the 3x3 test of §3) from the
-        // responses in registers, then the next tile's window
+        // responses in registers
         const int tx = (int)(k / tiles_y), ty = (int)(k - (long long)tx * tiles_y);
         t2_nms_regs(h, t, tl, px, slot0 + (long long)ty * tiles_x + tx, wt);
-        if (next) {
-            t2_load_x(h, ts, t, tn.oy, tn.ox, tn.ox == tl.ox && tn.oy == tl.oy + TY, wt);
-            t2_arrive(t2_bar(t, T2_XRB));
-        }
         t.g += NL;
     }
 }
