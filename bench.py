@@ -284,6 +284,9 @@ def main():
     ap.add_argument("--profile-shape", default="",
                     help="with --profile-case: tile shape, e.g. 284,18,8,320,4,2")
     ap.add_argument("--side", type=int, default=H, help="with --profile-case: crop side")
+    ap.add_argument("--profile-tc", type=int, default=1, choices=[0, 1, 2],
+                    help="with --profile-case: params.tensor_cores (1 the default kernels, "
+                         "2 the vertical-pass kernel, 0 FFMA)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args)
@@ -907,7 +910,8 @@ def profile_case(args):
     dev = torch.from_numpy(img.view(np.int16)).cuda()
     shape = [int(v) for v in args.profile_shape.split(",")] if args.profile_shape else None
     det = mhfd.Detector(N_LAYERS, T_MIN, T_MAX, threshold=THR, overlap=OVERLAP,
-                        nms=args.profile_nms, tile_shape=shape)
+                        nms=args.profile_nms, tile_shape=shape,
+                        tensor_cores={0: False, 1: True, 2: 2}[args.profile_tc])
     for _ in range(args.profile_case):
         if args.plain:
             det.detect_plain(dev)
