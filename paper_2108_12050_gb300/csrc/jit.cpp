@@ -405,9 +405,11 @@ TileConfig t2_config(int nl, int tx2) {
 }
 
 // 64-column strips (62 x 126 outputs per tile: the per-thread responses of
-// wider strips exceed the registers), else the first that fits
+// wider strips exceed the registers), else 48; a ladder whose halo leaves
+// narrower strips only (tensor memory) takes the vertical-pass kernel, which
+// wastes less on halos there
 bool choose_tile_t2(const std::vector<int> &R, int mode, TileConfig *cfg, std::string *why) {
-    for (int tx2 : {64, 80, 48, 96, 112, 128, 32, 16}) {
+    for (int tx2 : {64, 48}) {
         const TileConfig c = t2_config((int)R.size(), tx2);
         if (t2_shape_ok(R, mode, c, why)) {
             *cfg = c;

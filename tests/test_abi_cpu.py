@@ -106,6 +106,14 @@ def test_two_pass_tile_choice(native):
         with pytest.raises(native.MhfdError) as e:
             native.chosen_tile(tensor_cores=True, tile_shape=bad, **kw)
         assert e.value.code == -2, bad
+    # a ladder whose halo leaves no 48-column strip in tensor memory (R up to
+    # 64: V columns 48 + 128 + padding, twice, plus the L buffers) takes the
+    # vertical-pass kernel; so does one beyond it
+    for t_max in (16.0, 20.0):
+        wide = dict(n=16, t_min=1.0, t_max=t_max)
+        assert native.chosen_tile(tensor_cores=True, **wide) == native.chosen_tile(tensor_cores=2,
+                                                                                 **wide)
+    assert native.chosen_tile(tensor_cores=True, n=16, t_min=1.0, t_max=14.0)[:2] == (64, 128)
     assert native.chosen_tile(tensor_cores=True, response=1, **kw)[1] != 128
     assert native.chosen_tile(tensor_cores=True, nms=1, **kw)[1] != 128
     assert native.chosen_tile(tensor_cores=True, **kw) != native.chosen_tile(tensor_cores=2, **kw)
