@@ -612,6 +612,8 @@ def bench_variants(mhfd, torch, stream, tile, reps=5):
                                               **kw), False),
         "fused_local26": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX,
                                              **dict(kw, nms="local26")), False, "local26"),
+        "fused_local26_vtc": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, tensor_cores=2,
+                                                 **dict(kw, nms="local26")), False, "local26"),
         "plain_dog": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX, **kw), True),
         "plain_local26": timed(mhfd.Detector(N_LAYERS, T_MIN, T_MAX,
                                              **dict(kw, nms="local26")), True),

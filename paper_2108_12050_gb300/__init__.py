@@ -141,9 +141,10 @@ class Detector:
                 is_log = response in ("log", 1)
                 tc = bool(tensor_cores) and (nms in ("paper", 0) or not is_log)
                 # the tuned shapes are the vertical-pass kernel's: the default
-                # for the paper rule with the DoG response is the two-pass kernel
-                two_pass = tensor_cores is True or tensor_cores == 1
-                two_pass = two_pass and nms in ("paper", 0) and not is_log
+                # for detection with the DoG response (the 26-neighbour rule
+                # up to 16 layers) is the two-pass kernel
+                two_pass = (tensor_cores is True or tensor_cores == 1) and not is_log
+                two_pass = two_pass and (nms in ("paper", 0) or (nms in ("local26", 1) and n <= 16))
                 tile_shape = None if two_pass else tune.lookup(n, t_min, t_max, nms, sms, truncate,
                                          "log" if is_log else "dog", tensor_cores=tc)
         tile_override = tile_override or 0

@@ -74,6 +74,10 @@ struct mhfd_detector {
     double *soft_part = nullptr;   // per-block layer sums of the soft score
     long long cap = 0;           // candidate list capacity
     MhfdCand *cand = nullptr;
+    // two-pass kernel, 26-neighbour rule: per resident block, the responses
+    // of the tile's kept items ([layer][128 x strip width])
+    float *l26val = nullptr;
+    size_t l26val_n = 0;
     // grown with the image
     int cap_tile = 0;
     size_t tiles_cap = 0;
@@ -329,6 +333,7 @@ int launch_fused(mhfd_detector *d, Variant *v, const void *img, int dtype, int H
     h.gate = gate;
     h.flag = &d->cnt->ktimeout;
     h.t2tab = v->t2tab;
+    h.l26val = d->l26val;
     std::memcpy(pb, &h, sizeof(h));
     void *args[] = {pb};
     // one resident wave: every block marches down an equal share of tiles
@@ -421,7 +426,7 @@ void release(mhfd_detector *d) {
                         d->tile_off, d->stage, d->pb.cell_cnt, d->pb.cell_start, d->pb.cell_items,
                         d->pb.state, d->pb.nb_idx, d->pb.nb_cnt, d->d_blobs, d->d_cands,
                         d->soft_part, d->pI, d->pT, d->pL, d->pM, d->pD, d->pA, d->d_img_copy,
-                        d->soft_D};
+                        d->soft_D, d->l26val};
     for (void *p : dev_ptrs)
         if (p) cudaFree(p);
     free_conflict_table(&d->ct);
@@ -678,6 +683,7 @@ int batch_enqueue(mhfd_detector *d, int n, int max_passes, int max_rows, long lo
         h.gate = d->use_tc ? (k == 0 ? 1 : 2) : 0;
         h.flag = &d->cnt->ktimeout;
         h.t2tab = v->t2tab;
+        h.l26val = d->l26val;
         std::memcpy(pv.data(), &h, sizeof(h));
         void *args[] = {pv.data()};
         const long long wave = (long long)sms * v->occupancy;
@@ -872,6 +878,18 @@ int mhfd_create_detector(const mhfd_params *pp, mhfd_detector **out) {
         (d->p.keep_candidates && (rc = dalloc(&d->d_cands, (size_t)d->cap)))) {
         release(d);
         return rc;
+    }
+    if (d->use_tc && d->cfg_tc.tc == 2 && d->p.nms == MHFD_NMS_LOCAL26) {
+        int sms = 1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device) != cudaSuccess) {
+            release(d);
+            return fail(MHFD_ERR_CUDA, "cudaDeviceGetAttribute failed");
+        }
+        d->l26val_n = (size_t)sms * d->var_tc->occupancy * (size_t)(nl - 1) * 128 * d->cfg_tc.tx2;
+        if ((rc = dalloc(&d->l26val, d->l26val_n))) {
+            release(d);
+            return rc;
+        }
     }
     if (cudaMemset(d->cnt, 0, sizeof(Counters)) ||
         cudaMemcpy(d->d_radius, rad.data(), 64 * sizeof(double), cudaMemcpyHostToDevice) ||
@@ -1451,7 +1469,7 @@ int mhfd_device_bytes(mhfd_detector *d, int32_t H, int32_t W, int64_t *fixed_byt
     // candidate list, prune grid items, states, 16 neighbours, counts, blob list
     fixed += cap * (sizeof(MhfdCand) + 3 * sizeof(int) + 16 * sizeof(int) + sizeof(mhfd_blob));
     if (d->p.keep_candidates) fixed += cap * sizeof(mhfd_blob);
-    fixed += d->ct.bytes;
+    fixed += d->ct.bytes + d->l26val_n * sizeof(float);
     *fixed_bytes = (int64_t)fixed;
     *image_bytes = 0;
     if (H > 0 && W > 0) {

@@ -329,7 +329,13 @@ constexpr int T2_OFF_AH = T2_OFF_TAB + (TC2 ? T2_NTAB * 2 * T2_TAB_PART : 0);
 constexpr int T2_OFF_CTRL = T2_OFF_AH + (TC2 ? 2 * T2_AH_PART : 0);
 // control block: mbarriers, tensor-memory address, fail flag, scan buffer,
 // the window's column map
-constexpr int T2_SMEM = T2_OFF_CTRL + 512 + 4 * ((T2_XC + 3) & ~3);
+constexpr int T2_OFF_L26 = T2_OFF_CTRL + 512 + 4 * ((T2_XC + 3) & ~3);
+// 26-neighbour rule: two exchange buffers of a layer's segment ends and
+// lane-group boundary rows (T2M x parts x 2 and 8 x TX2 floats), then the
+// per-pixel masks of kept layers (16 bits, [thread column][worker thread])
+constexpr bool T2_L26 = TC2 && MODE == 1;
+constexpr int T2_L26_XB = 4 * (T2M * (((NT - 32) / 32) / 4) * 2 + 8 * TX2);
+constexpr int T2_SMEM = T2_OFF_L26 + (T2_L26 ? 2 * T2_L26_XB + 2 * TX2 * T2M : 0);
 constexpr int T2_NW = NT - 32;                    // worker threads (the last warp issues)
 constexpr int T2_DH = 2 * T2_NVMAX;               // tensor-memory column of the L buffers
 constexpr int T2_LP = T2_DH + 2 * TX2;            // of the previous level's L (one copy)
@@ -338,7 +344,8 @@ constexpr int SMEM_BYTES =
     TC2 ? T2_SMEM
         : TC_WIN_BYTES + TC_B_BYTES + 4 * (SMEM_IN + SMEM_V + SMEM_RING_F) + SMEM_RING_B + 4 * 64 +
               TC_CTRL;
-static_assert(!TC2 || (MODE == 0 && !LOG), "two-pass kernel: paper rule, DoG response");
+static_assert(!TC2 || ((MODE == 0 || MODE == 1) && !LOG), "two-pass kernel: detection with the DoG response");
+static_assert(!T2_L26 || NL - 1 <= 16, "two-pass kernel, 26-neighbour rule: 16-bit layer masks");
 static_assert(!TC2 || (TX2 % 16 == 0 && TX2 >= 16 && TX2 <= 128 && MHFD_TY2 == T2M &&
                        (NT == 288 || NT == 544) && TX2 % (4 * ((NT - 32) / 128)) == 0),
               "two-pass kernel geometry: 16-multiple strips up to 128, tiles of 128 rows, 8 or 16 worker warps");
@@ -1907,6 +1914,13 @@ struct T2State {
     __device__ __forceinline__ unsigned ah() const { return smem_addr(ahp()); }
     __device__ __forceinline__ int *scan() const { return reinterpret_cast<int *>(ctrl() + 128); }
     __device__ __forceinline__ int *cmap() const { return reinterpret_cast<int *>(ctrl() + 512); }
+    // 26-neighbour rule: exchange buffer b, kept-layer masks
+    __device__ __forceinline__ float *l26x(int b) const {
+        return reinterpret_cast<float *>(mk_t2_smem + T2_OFF_L26 + b * T2_L26_XB);
+    }
+    __device__ __forceinline__ unsigned short *l26m() const {
+        return reinterpret_cast<unsigned short *>(mk_t2_smem + T2_OFF_L26 + 2 * T2_L26_XB);
+    }
     __device__ __forceinline__ volatile int *fail() const {
         return reinterpret_cast<volatile int *>(ctrl() + 100);
     }
@@ -2144,8 +2158,13 @@ __device__ __forceinline__ void t2_split(const T2State &t, int l, unsigned dcol,
 
 // per-thread state of the responses: T2_CQ computed columns of one row
 struct T2Px {
-    float mx[T2_CQ];          // running max over scales
-    unsigned ag[T2_CQ / 4];   // its first argmax, one byte per column
+    float mx[T2_CQ];          // paper rule: running max over scales;
+                              // 26-neighbour rule: the previous layer's 3x3 maxima
+    unsigned ag[T2_CQ / 4];   // paper rule: first argmax, one byte per column
+    // 26-neighbour rule, one bit per column: items of the previous layer
+    // waiting for the layer above, columns with a kept item in this tile,
+    // pixels inside the image, output pixels
+    unsigned fl, any, ci, cv;
 };
 __device__ __forceinline__ int t2_ag(const T2Px &px, int u) { return (px.ag[u >> 2] >> (8 * (u & 3))) & 0xFF; }
 struct T2Tile {
@@ -2212,6 +2231,191 @@ __device__ __forceinline__ void t2_epi(const MhfdKHeader &h, const T2State &t, i
         }
     }
     if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// 26-neighbour rule (the 3x3x3 test of §3 on the layers of Eq. 2), one layer
+// at a time, in the epilogue of level l (layer I = l - 1).  With S_I the 3x3
+// maximum of D_I around a pixel (neighbours outside the image compare as
+// -inf), an item (pixel, I) is kept when D_I > thr, D_I is not below any of
+// its 8 neighbours in layer I (so D_I = S_I there), and not below S_{I-1} or
+// S_{I+1}.  So once D_I is formed: an item of layer I - 1 flagged one level
+// earlier is kept if its response (px.mx, which is S_{I-1} there) is not
+// below S_I; the items of layer I that pass the first three tests are
+// flagged to wait for the layer above (the top layer keeps them at once);
+// px.mx becomes S_I.  D_I replaces L_l in its tensor-memory buffer (free
+// until level l + 2's horizontal product, issued after the workers' next
+// split) and is read back a round at a time for the test.  The 3x3 maxima
+// take the rows above and below from the neighbouring lanes (warp
+// shuffles), the segment ends and the lane-group boundary rows from an
+// exchange buffer in shared memory (two, alternating by layer: one barrier
+// per layer).  A kept item sets bit I of its pixel's mask in shared memory
+// and stores its response in the block's scratch, both read at the tile end.
+__device__ __forceinline__ void t2_epi26(const MhfdKHeader &h, const T2State &t, int l, unsigned dcol,
+                                         int wt, T2Px &px, float sc, const T2Tile &tl) {
+    constexpr int CQ = T2_CQ, CP = T2_CP;
+    const float ninf = -__int_as_float(0x7f800000);
+    const int w = wt >> 5, lane = wt & 31, g = w & 3, q = w >> 2;
+    const int mr = 32 * g + lane, m = T2M - 1 - mr;
+    const unsigned taddr = t.tmem + ((unsigned)(32 * g) << 16) + dcol + (unsigned)(CQ * q);
+    const unsigned paddr = t.tmem + ((unsigned)(32 * g) << 16) + (unsigned)(T2_LP + CQ * q);
+    const bool first = l == 0, last = l + 1 == NL;
+    const int I = l - 1;
+    const float ts = mk_t2_levs.v[l].tsc * sc;
+    if (first) {
+        // the tile's pixels inside the image, and its output pixels
+        const int gy = tl.oy - 1 + m;
+        const bool rowin = gy >= 0 && gy < h.H, rowint = rowin && m >= 1 && m <= T2M - 2;
+        unsigned ci = 0, cv = 0;
+#pragma unroll
+        for (int u = 0; u < CQ; ++u) {
+            const int c = TX2 - 1 - (CQ * q + u), gx = tl.ox - 1 + c;
+            const bool in = rowin && gx >= 0 && gx < h.W;
+            ci |= (unsigned)in << u;
+            cv |= (unsigned)(in && rowint && c >= 1 && c <= TX2 - 2) << u;
+        }
+        px.ci = ci;
+        px.cv = cv;
+        px.fl = 0;
+        px.any = 0;
+    }
+    float *xc = t.l26x(I & 1);      // [T2M lanes][CP parts][2 ends]
+    float *xr = xc + T2M * CP * 2;  // [4 lane groups][2 ends][CP parts][CQ]
+    float d0 = 0.0f, dl = 0.0f;     // the segment's ends
+    constexpr int EC = 4;
+    static_assert(CQ % 8 == 0, "whole load rounds");
+#pragma unroll
+    for (int i0 = 0; i0 < CQ; i0 += EC) {
+        unsigned r[EC], rp[EC];
+        tc_ld4(taddr + (unsigned)i0, r);
+        tc_ld4(paddr + (unsigned)i0, rp);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]));
+        asm volatile("" : "+r"(rp[0]), "+r"(rp[1]), "+r"(rp[2]), "+r"(rp[3]));
+        if (!last)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                             paddr + (unsigned)i0),
+                         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
+                         : "memory");
+        if (!first) {
+            float dv[EC];
+#pragma unroll
+            for (int e = 0; e < EC; ++e) {
+                const int u = i0 + e;
+                const float v = ts * (__uint_as_float(r[e]) - __uint_as_float(rp[e]));
+                if (STORE) {
+                    const int c = TX2 - 1 - (CQ * q + u);
+                    const int gy = tl.oy - 1 + m, gx = tl.ox - 1 + c;
+                    if ((px.cv >> u) & 1u)
+                        h.stack_out[(long long)I * h.plane + (long long)gy * h.W + gx] = v;
+                }
+                dv[e] = (px.ci >> u) & 1u ? v : ninf;
+            }
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                             taddr + (unsigned)i0),
+                         "f"(dv[0]), "f"(dv[1]), "f"(dv[2]), "f"(dv[3])
+                         : "memory");
+            if (i0 == 0) d0 = dv[0];
+            if (i0 + EC == CQ) dl = dv[EC - 1];
+            // the whole rows of lanes 0 and 31
+            if (lane == 0 || lane == 31)
+                *reinterpret_cast<float4 *>(xr + ((g * 2 + (lane == 31 ? 1 : 0)) * CP + q) * CQ + i0) =
+                    make_float4(dv[0], dv[1], dv[2], dv[3]);
+        }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    if (first) return;
+    if (mk_ok(mr < T2M && q < CP)) {
+        xc[(mr * CP + q) * 2 + 0] = d0;
+        xc[(mr * CP + q) * 2 + 1] = dl;
+    }
+    t2_wsync();
+    // the neighbour row of lane 0 (above) or 31 (below) in the next lane
+    // group; none past the tile
+    const float *rx = lane == 0 && g > 0    ? xr + (((g - 1) * 2 + 1) * CP + q) * CQ
+                      : lane == 31 && g < 3 ? xr + (((g + 1) * 2 + 0) * CP + q) * CQ
+                                            : nullptr;
+    const unsigned rxh = rx != nullptr, rxa = rx ? smem_addr(rx) : 0u;
+    // column max of the three rows just outside the segment (other part)
+    auto edge = [&](int qq, int e) {
+        if (qq < 0 || qq >= CP) return ninf;
+        float v = xc[(mr * CP + qq) * 2 + e];
+        if (mr > 0) v = fmaxf(v, xc[((mr - 1) * CP + qq) * 2 + e]);
+        if (mr < T2M - 1) v = fmaxf(v, xc[((mr + 1) * CP + qq) * 2 + e]);
+        return v;
+    };
+    const float thr = h.thr;
+    const bool top = I + 2 == NL;  // the last layer: no layer above
+    // the block's scratch: [layer][column u][worker thread]
+    constexpr int LAY = CQ * T2_NW;
+    const int gvb = ((int)blockIdx.x * (NL - 1) + (I > 0 ? I - 1 : 0)) * LAY + wt;
+    const int gvc = ((int)blockIdx.x * (NL - 1) + I) * LAY + wt;
+    unsigned fin = 0, nf = 0;
+    // pixel uu: its 8 neighbours are the column maxima (three rows) at uu - 1
+    // and uu + 1 and the rows above and below at uu (ud, which may also hold
+    // the pixel itself)
+    auto test = [&](int uu, float x, float cl, float cr, float ud) {
+        const float nb = fmaxf(fmaxf(cl, cr), ud);
+        const float s = fmaxf(nb, x);
+        if (((px.fl >> uu) & 1u) && !(s > px.mx[uu])) {
+            fin |= 1u << uu;
+            h.l26val[gvb + uu * T2_NW] = px.mx[uu];
+        }
+        if (((px.cv >> uu) & 1u) && x > thr && !(nb > x) && (I == 0 || !(px.mx[uu] > x))) {
+            nf |= 1u << uu;
+            if (top) h.l26val[gvc + uu * T2_NW] = x;
+        }
+        px.mx[uu] = s;
+    };
+    float cprev = edge(q - 1, 1);  // column max at u - 2 (n' = CQ q - 1 at first)
+    float ccur = 0.0f, vcur = 0.0f, xcur = 0.0f;  // at u - 1: column max, rows above and below, D
+#pragma unroll
+    for (int i0 = 0; i0 < CQ; i0 += 4) {
+        unsigned r[4];
+        tc_ld4(taddr + (unsigned)i0, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int u = i0 + e;
+            const float x = __uint_as_float(r[e]);
+            // rows above and below: lanes 0 and 31 get their own value from
+            // the shuffles (which leaves the tests unchanged: a pixel is not
+            // below itself) and the other lane group's row from shared memory
+            // (volatile: the shuffles and the boundary row's load stay in
+            // column order, so that they do not all occupy registers at once)
+            float up, dn, ev = ninf;
+            asm volatile("shfl.sync.up.b32 %0, %1, 1, 0, 0xffffffff;" : "=f"(up) : "f"(x));
+            asm volatile("shfl.sync.down.b32 %0, %1, 1, 31, 0xffffffff;" : "=f"(dn) : "f"(x));
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %2, 0;\n@p ld.shared.f32 %0, [%1];\n}\n"
+                         : "+f"(ev)
+                         : "r"(rxa + 4u * (unsigned)u), "r"(rxh));
+            const float vn = fmaxf(fmaxf(up, dn), ev), cn = fmaxf(vn, x);
+            if (u > 0) {
+                test(u - 1, xcur, cprev, cn, vcur);
+                cprev = ccur;
+            }
+            xcur = x;
+            vcur = vn;
+            ccur = cn;
+        }
+    }
+    test(CQ - 1, xcur, cprev, edge(q + 1, 0), vcur);  // n' = CQ q + CQ past the segment
+    px.fl = top ? 0u : nf;
+    unsigned short *msk = t.l26m() + wt;  // [column u][worker thread]
+#pragma unroll 1
+    for (unsigned f = fin; f; f &= f - 1) {
+        const int uu = __ffs(f) - 1;
+        if (mk_ok(uu < CQ && wt < T2_NW))
+            msk[uu * T2_NW] = (unsigned short)(msk[uu * T2_NW] | (1u << (I - 1)));
+    }
+    if (top) {
+#pragma unroll 1
+        for (unsigned f = nf; f; f &= f - 1) {
+            const int uu = __ffs(f) - 1;
+            if (mk_ok(uu < CQ && wt < T2_NW)) msk[uu * T2_NW] = (unsigned short)(msk[uu * T2_NW] | (1u << I));
+        }
+        px.any |= nf;
+    }
+    px.any |= fin;
 }
 
 // Window rows [k_lo, T2_XIMG_R) of the tile whose first output row is oy.
@@ -2296,27 +2500,40 @@ __device__ __forceinline__ void t2_load_x(const MhfdKHeader &h, const TcStretch 
         t2_load_x_t<1>(h, ts, t.xp(), cmap, oy, k_lo, wt);
 }
 
-// exclusive scan over the worker threads (named barrier 1)
-__device__ __forceinline__ int t2_scan(int v, int *buf, int *sum, int wt) {
-    constexpr int NWW = T2_NW / 32;
-    const int lane = wt & 31, warp = wt >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) buf[warp] = x;
+// The tile's candidate positions: each worker thread's count n goes to its
+// row segment's rank in row-major order (cnt), a block scan forms their
+// exclusive prefix (pre); returns the thread's first position, and the
+// tile's total goes to tile_count[slot].
+__device__ __forceinline__ int t2_count_scan(const MhfdKHeader &h, const T2State &t, int *cnt, int *pre, int n,
+                                             int rank, long long slot, int wt) {
+    const int w = wt >> 5, lane = wt & 31;
+    if (mk_ok(rank >= 0 && rank < T2M * T2_CP)) cnt[rank] = n;
     t2_wsync();
-    int before = 0, total = 0;
+    {
+        constexpr int NWW = T2_NW / 32;
+        static_assert(T2M * T2_CP == T2_NW, "one count per worker thread");
+        const int v = cnt[wt];
+        int x = v;
 #pragma unroll
-    for (int w = 0; w < NWW; ++w) {
-        const int tt = buf[w];
-        before += w < warp ? tt : 0;
-        total += tt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        int *buf = t.scan();
+        if (lane == 31) buf[w] = x;
+        t2_wsync();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int ww = 0; ww < NWW; ++ww) {
+            const int tt = buf[ww];
+            before += ww < w ? tt : 0;
+            total += tt;
+        }
+        pre[wt] = before + x - v;
+        if (wt == 0) h.tile_count[slot] = total;
     }
-    *sum = total;
-    return before + x - v;
+    t2_wsync();
+    return pre[rank];
 }
 
 // The tile's maxima (Eq. 3 with the 3x3 test of §3) from the running max
@@ -2412,34 +2629,7 @@ __device__ __forceinline__ void t2_nms_regs(const MhfdKHeader &h, const T2State 
         }
     // positions: segments in row-major order (row m ascending, column
     // ascending = part descending)
-    const int rank = m * T2_CP + (T2_CP - 1 - q);
-    if (mk_ok(rank >= 0 && rank < T2M * T2_CP)) cnt[rank] = __popc(flags);
-    t2_wsync();
-    {
-        constexpr int NWW = T2_NW / 32;
-        static_assert(T2M * T2_CP == T2_NW, "one count per worker thread");
-        const int v = cnt[wt];
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        int *buf = t.scan();
-        if (lane == 31) buf[w] = x;
-        t2_wsync();
-        int before = 0, total = 0;
-#pragma unroll
-        for (int ww = 0; ww < NWW; ++ww) {
-            const int tt = buf[ww];
-            before += ww < w ? tt : 0;
-            total += tt;
-        }
-        pre[wt] = before + x - v;
-        if (wt == 0) h.tile_count[slot] = total;
-    }
-    t2_wsync();
-    int pos = pre[rank];
+    int pos = t2_count_scan(h, t, cnt, pre, __popc(flags), m * T2_CP + (T2_CP - 1 - q), slot, wt);
     if (flags && mk_ok(slot >= 0)) {
         MhfdCand *dst = h.stage + slot * h.cap_tile;
         // set bits from the highest column index u (lowest image column)
@@ -2472,6 +2662,49 @@ __device__ __forceinline__ void t2_nms_regs(const MhfdKHeader &h, const T2State 
     t2_wsync();  // the exchange space is the next tile's split rows
 }
 
+// The tile's kept items of the 26-neighbour rule to its slots: row-major
+// order, layers ascending within a pixel (the order of the other kernels),
+// by a scan of the per-segment counts; responses from the block's scratch.
+// The masks are cleared for the next tile.  The counts use the split rows'
+// space, free once the last horizontal product is done.
+__device__ __forceinline__ void t2_out26(const MhfdKHeader &h, const T2State &t, const T2Tile &tl, T2Px &px,
+                                         long long slot, int wt) {
+    constexpr int CQ = T2_CQ;
+    const int w = wt >> 5, lane = wt & 31, g = w & 3, q = w >> 2;
+    const int m = T2M - 1 - (32 * g + lane);
+    int *cnt = reinterpret_cast<int *>(t.ahp());  // [128 rows][CP] counts, row-major
+    int *pre = cnt + T2M * T2_CP;                 // their exclusive prefix
+    unsigned short *msk = t.l26m() + wt;
+    constexpr long long LAY = (long long)CQ * T2_NW;
+    const float *gv = h.l26val + (long long)blockIdx.x * (NL - 1) * LAY + wt;
+    int n = 0;
+#pragma unroll 1
+    for (unsigned f = px.any; f; f &= f - 1) n += __popc(msk[(__ffs(f) - 1) * T2_NW]);
+    int pos = t2_count_scan(h, t, cnt, pre, n, m * T2_CP + (T2_CP - 1 - q), slot, wt);
+    MhfdCand *dst = h.stage + slot * h.cap_tile;
+    // columns from the highest u (lowest image column)
+#pragma unroll 1
+    for (unsigned f = px.any; f;) {
+        const int uu = 31 - __clz(f);
+        f &= ~(1u << uu);
+        unsigned mm = msk[uu * T2_NW];
+        msk[uu * T2_NW] = 0;
+#pragma unroll 1
+        for (; mm; mm &= mm - 1, ++pos)
+            if (pos < h.cap_tile && mk_ok(slot >= 0)) {
+                const int i = __ffs(mm) - 1;
+                MhfdCand cd;
+                cd.x = tl.ox - 1 + (TX2 - 1 - (CQ * q + uu));
+                cd.y = tl.oy - 1 + m;
+                cd.i = i;
+                cd.resp = gv[i * LAY + uu * T2_NW];
+                dst[pos] = cd;
+            }
+    }
+    px.any = 0;
+    t2_wsync();  // the count space is the next tile's split rows
+}
+
 // worker levels: wait for level l's V, split it, build level l + 2's tap
 // matrix, hand over; then the responses of level l - 1
 // (after the last level's split, the last vertical product is done: the
@@ -2492,8 +2725,13 @@ __device__ __forceinline__ void t2_work(const MhfdKHeader &h, T2State &t, const 
             t2_load_x(h, ts, t, tn.oy, tn.ox, tn.ox == tl.ox && tn.oy == tl.oy + TY, wt);
             t2_arrive(t2_bar(t, T2_XRB));
         }
-        if (l > 0)
-            t2_epi(h, t, l - 1, (unsigned)T2_DH + ((gl - 1u) & 1u) * (unsigned)TX2, wt, px, ts.a, tl);
+        if (l > 0) {
+            const unsigned dcol = (unsigned)T2_DH + ((gl - 1u) & 1u) * (unsigned)TX2;
+            if constexpr (T2_L26)
+                t2_epi26(h, t, l - 1, dcol, wt, px, ts.a, tl);
+            else
+                t2_epi(h, t, l - 1, dcol, wt, px, ts.a, tl);
+        }
     }
 }
 
@@ -2578,11 +2816,19 @@ __device__ __forceinline__ void t2_range(const MhfdKHeader &h, long long k0, lon
         const unsigned gl = t.g + NL - 1;
         t2_wait(h, t, T2_HB + (int)(gl & 1u));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        t2_epi(h, t, NL - 1, ((unsigned)T2_DH + ((gl) & 1u) * (unsigned)TX2), wt, px, ts.a, tl);
-        // the tile's maxima (Eq. 3 with the 3x3 test of §3) from the
-        // responses in registers
+        const unsigned dcol = (unsigned)T2_DH + (gl & 1u) * (unsigned)TX2;
         const int tx = (int)(k / tiles_y), ty = (int)(k - (long long)tx * tiles_y);
-        t2_nms_regs(h, t, tl, px, slot0 + (long long)ty * tiles_x + tx, wt);
+        const long long slot = slot0 + (long long)ty * tiles_x + tx;
+        if constexpr (T2_L26) {
+            // the top layer's items, then the tile's kept items to its slots
+            t2_epi26(h, t, NL - 1, dcol, wt, px, ts.a, tl);
+            t2_out26(h, t, tl, px, slot, wt);
+        } else {
+            // the tile's maxima (Eq. 3 with the 3x3 test of §3) from the
+            // responses in registers
+            t2_epi(h, t, NL - 1, dcol, wt, px, ts.a, tl);
+            t2_nms_regs(h, t, tl, px, slot, wt);
+        }
         t.g += NL;
     }
 }
@@ -2658,9 +2904,13 @@ __device__ __forceinline__ void t2_kernel(const KParams &p, unsigned char *base)
     }
     T2State t;
     unsigned char *ctrl = t.ctrl();  // 10 mbarriers, TMEM address (+96), fail flag (+100)
-    // the window's padding rows and columns stay zero
+    // the window's padding rows and columns stay zero; the 26-neighbour
+    // rule's layer masks start empty (each tile's end clears what it read)
     for (int i = threadIdx.x; i < T2_X_BYTES / 16; i += NT)
         reinterpret_cast<uint4 *>(base)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (T2_L26)
+        for (int i = threadIdx.x; i < 2 * TX2 * T2M / 16; i += NT)
+            reinterpret_cast<uint4 *>(t.l26m())[i] = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x == 0) {
         for (int b = 0; b < 10; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(ctrl + 8 * b)),

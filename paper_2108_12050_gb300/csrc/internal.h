@@ -122,7 +122,7 @@ std::vector<TileConfig> tile_menu_tc(const std::vector<int> &R, int mode);
 // The two-pass kernel (both blur passes on the tensor cores): its shared
 // memory, whether it takes a mode and shape, its configuration for a strip
 // width, and the built-in choice.
-int t2_smem(const std::vector<int> &R, const TileConfig &c);
+int t2_smem(const std::vector<int> &R, int mode, const TileConfig &c);
 bool t2_mode_ok(int mode);
 bool t2_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why);
 TileConfig t2_config(int nl, int tx2);

@@ -320,7 +320,7 @@ int brows_for(const std::vector<int> &R, int mode, const TileConfig &c) {
 }
 
 int smem_estimate(const std::vector<int> &R, int mode, const TileConfig &c) {
-    if (c.tc == 2) return t2_smem(R, c);
+    if (c.tc == 2) return t2_smem(R, mode, c);
     if (c.tc)
         return smem_fixed(R, mode, c) + tc_b_bytes(R, mode, c) + 128 +
                tc_window_bytes(R, mode, c, brows_for(R, mode, c));
@@ -361,23 +361,30 @@ T2Geom t2_geom(const std::vector<int> &R, const TileConfig &c) {
 }
 }  // namespace
 
-int t2_smem(const std::vector<int> &R, const TileConfig &c) {
+int t2_smem(const std::vector<int> &R, int mode, const TileConfig &c) {
     const T2Geom g = t2_geom(R, c);
     const int xgstr = ((16 * g.xr + 127) / 128) * 128 + 16;
     const int x_bytes = (g.xc / 8) * xgstr;
     const int tab_part = g.smax * 128;
     const int ah_part = 16 * (g.khmax / 8) * 128;
-    return ((x_bytes + 127) & ~127) + 8 * tab_part + 2 * ah_part + 512 + 4 * ((g.xc + 3) & ~3);
+    int b = ((x_bytes + 127) & ~127) + 8 * tab_part + 2 * ah_part + 512 + 4 * ((g.xc + 3) & ~3);
+    // 26-neighbour rule: two exchange buffers, the 16-bit layer masks
+    if (mode == MHFD_NMS_LOCAL26)
+        b += 2 * 4 * (128 * (((c.nt - 32) / 32) / 4) * 2 + 8 * c.tx2) + 2 * c.tx2 * 128;
+    return b;
 }
 
-bool t2_mode_ok(int mode) { return mode == 0; }  // paper rule, DoG response
+// detection with the DoG response: the paper rule or the 26-neighbour rule
+bool t2_mode_ok(int mode) { return mode == MHFD_NMS_PAPER || mode == MHFD_NMS_LOCAL26; }
 
 bool t2_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why) {
     auto no = [&](const char *m) {
         if (why) *why = m;
         return false;
     };
-    if (!t2_mode_ok(mode)) return no("the two-pass kernel takes the paper rule with the DoG response");
+    if (!t2_mode_ok(mode)) return no("the two-pass kernel takes detection with the DoG response");
+    if (mode == MHFD_NMS_LOCAL26 && R.size() - 1 > 16)
+        return no("the two-pass kernel's 26-neighbour rule takes up to 16 layers");
     if (c.tx2 % 16 || c.tx2 < 16 || c.tx2 > 128)
         return no("the two-pass kernel's strips are 16 to 128 columns, a multiple of 16");
     if (c.ty2 != 128 || (c.nt != 288 && c.nt != 544))
@@ -388,7 +395,7 @@ bool t2_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::
         return no("the two-pass kernel's V and L buffers exceed tensor memory for this ladder");
     if (8192 + 5 * c.tx2 * 128 > 2 * 16 * (g.khmax / 8) * 128)
         return no("the tile-end maxima test does not fit the split rows' space");
-    if (t2_smem(R, c) > kSmemLimitBytes) return no("does not fit in shared memory");
+    if (t2_smem(R, mode, c) > kSmemLimitBytes) return no("does not fit in shared memory");
     return true;
 }
 

@@ -68,6 +68,8 @@ struct MhfdKHeader {
     int *flag;                // set to 1 when a bounded wait gives up (or null)
     const void *t2tab;        // two-pass kernel: every level's banded tap
                               // matrices, as its shared-memory buffer holds them
+    float *l26val;            // two-pass kernel, 26-neighbour rule: per block,
+                              // the responses of kept items ([layer][column][thread])
 };
 
 #endif  // MHFD_TYPES_H

@@ -95,10 +95,11 @@ def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
 
 
 def test_two_pass_tile_choice(native):
-    """The default for the paper rule with the DoG response is the two-pass
+    """The default for detection with the DoG response is the two-pass
     kernel: tiles of 128 computed rows, strips of 16-multiple width (64 by
     default), 288 threads; tile_shape[0] sets the strip width; the LoG
-    response and the 26-neighbour rule keep the vertical-pass kernel."""
+    response, and the 26-neighbour rule beyond 16 layers (its 16-bit layer
+    masks), keep the vertical-pass kernel."""
     kw = dict(n=16, t_min=1.0, t_max=12.0)
     assert native.chosen_tile(tensor_cores=True, **kw) == (64, 128, 4, 288, 1, 1)
     assert native.chosen_tile(tensor_cores=True, tile_shape=(48, 0, 0, 0, 1), **kw)[:2] == (48, 128)
@@ -115,7 +116,10 @@ def test_two_pass_tile_choice(native):
                                                                                  **wide)
     assert native.chosen_tile(tensor_cores=True, n=16, t_min=1.0, t_max=14.0)[:2] == (64, 128)
     assert native.chosen_tile(tensor_cores=True, response=1, **kw)[1] != 128
-    assert native.chosen_tile(tensor_cores=True, nms=1, **kw)[1] != 128
+    assert native.chosen_tile(tensor_cores=True, nms=1, **kw) == (64, 128, 4, 288, 1, 1)
+    l17 = dict(n=17, t_min=1.0, t_max=12.0, nms=1)
+    assert native.chosen_tile(tensor_cores=True, **l17) == native.chosen_tile(tensor_cores=2, **l17)
+    assert native.chosen_tile(tensor_cores=True, **l17)[1] != 128
     assert native.chosen_tile(tensor_cores=True, **kw) != native.chosen_tile(tensor_cores=2, **kw)
 
 

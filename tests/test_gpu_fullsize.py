@@ -107,6 +107,32 @@ def test_full_tile_detection_against_oracle(reference, path):
     print("FULLSIZE " + json.dumps(stats))
 
 
+@pytest.mark.parametrize("tc", [True, 2], ids=["tc", "vtc"])
+def test_full_tile_local26_against_oracle(reference, tc):
+    """The 26-neighbour rule on the in-focus tile (the two-pass kernel by
+    default, the vertical-pass kernel on request): the whole candidate set
+    against the oracle's 3x3x3 maxima of the same stack, then the prune."""
+    r = reference
+    if r["response"] != "dog" or r["sigma_d"] != 0.0:
+        pytest.skip("the 26-neighbour rule on the in-focus DoG tile")
+    import paper_2108_12050_gb300 as mhfd
+    if "ref26" not in r:
+        ref26 = oracle.detect_from_stack(r["D"], r["t"], r["thr"], OVERLAP, mode=1)
+        ref26["lo"], ref26["hi"] = r["ref"].lo, r["ref"].hi
+        r["ref26"] = ref26
+    ref26 = r["ref26"]
+    det = mhfd.Detector(N, TMIN, TMAX, threshold=r["thr"], overlap=OVERLAP, nms="local26",
+                        keep_candidates=True, tensor_cores=tc)
+    assert det.tensor_core_kernel == (2 if tc is True else 1)
+    res = det(torch.from_numpy(r["img"].view(np.int16)).cuda())
+    det.close()
+    assert (res.lo, res.hi) == (ref26.lo, ref26.hi)
+    assert res.n_candidates == res.n_candidates_true > 10000
+    stats = check_detection(res, ref26, r["D"], r["tol"], r["thr"], OVERLAP, "local26", r["t"])
+    stats.update(path="local26", tc=tc)
+    print("FULLSIZE " + json.dumps(stats))
+
+
 @pytest.mark.parametrize("tc", [True, 2, False], ids=["tc", "vtc", "ffma"])
 def test_full_tile_stack_within_tolerance(reference, tc):
     r = reference

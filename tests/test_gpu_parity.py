@@ -157,9 +157,27 @@ def test_pair_512_uint8_end_to_end(which, tc):
     _check_detection(img, 10, 1.0, 10.0, 0.1, 0.5, "paper", tc=tc)
 
 
-def test_pair_512_uint8_local26_end_to_end():
+@pytest.mark.parametrize("tc", [True, 2, False], ids=["tc", "vtc", "ffma"])
+def test_pair_512_uint8_local26_end_to_end(tc):
     a, _ = synth.pair512_u8(seed=1, H=256, W=300)
-    _check_detection(a, 10, 1.0, 10.0, 0.1, 0.5, "local26")
+    _check_detection(a, 10, 1.0, 10.0, 0.1, 0.5, "local26", tc=tc)
+
+
+@pytest.mark.parametrize("tc", [True, 2, False], ids=["tc", "vtc", "ffma"])
+def test_local26_plateau_keeps_every_item(tc):
+    """A constant image has D = 0 in every layer: with a negative threshold
+    every (pixel, layer) item is a 26-neighbour maximum (ties count), so the
+    candidate list is the whole stack in row-major order, layers ascending
+    within a pixel (several kept layers per pixel, one tile's worth)."""
+    img = np.full((40, 37), 9, np.uint8)
+    det = detector(n=2, t_min=1.0, t_max=2.0, threshold=-0.5, overlap=1.0, nms="local26",
+                   keep_candidates=True, tensor_cores=tc)
+    res = det(to_dev(img))
+    assert res.n_candidates_true == 2 * 40 * 37 and not res.overflow
+    c = res.candidates
+    yy, xx, ii = np.meshgrid(np.arange(40), np.arange(37), np.arange(2), indexing="ij")
+    assert np.array_equal(c["x"], xx.ravel()) and np.array_equal(c["y"], yy.ravel())
+    assert np.array_equal(c["scale_idx"], ii.ravel()) and np.all(c["response"] == 0.0)
 
 
 @pytest.mark.parametrize("shape,dtype", [((257, 383), "u16"), ((64, 64), "u8"),
@@ -169,6 +187,7 @@ def test_small_ladder_end_to_end(shape, dtype):
     _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "paper")
     _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "paper", tc=False)
     _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "local26")
+    _check_detection(img, 4, 1.0, 4.0, 0.05, 0.5, "local26", tc=2)
 
 
 @pytest.mark.parametrize("shape,dtype,sigma_d", [((300, 420), "u16", 0.0),
@@ -183,17 +202,21 @@ def test_headline_ladder_end_to_end(shape, dtype, sigma_d):
     _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, "paper")
     _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, "paper", tc=False)
     _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, "local26")
+    _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, "local26", tc=2)
 
 
 # ------------------------------------------------ tensor-core vertical pass
 
 def test_tensor_core_pass_is_used_where_it_applies():
-    # both passes for the paper rule with the DoG response, the vertical pass
-    # for the other tensor-core modes and on request
+    # both passes for detection with the DoG response (the 26-neighbour rule
+    # up to 16 layers), the vertical pass for the other tensor-core modes and
+    # on request
     assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1).tensor_core_kernel == 2
     assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
                     tensor_cores=2).tensor_core_kernel == 1
     assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1,
+                    nms="local26").tensor_core_kernel == 2
+    assert detector(n=17, t_min=1.0, t_max=10.0, threshold=0.1,
                     nms="local26").tensor_core_kernel == 1
     assert detector(n=10, t_min=1.0, t_max=10.0, threshold=0.1 / 0.9,
                     response="log").tensor_core_kernel == 1
