@@ -331,10 +331,13 @@ constexpr int T2_OFF_CTRL = T2_OFF_AH + (TC2 ? 2 * T2_AH_PART : 0);
 // the window's column map
 constexpr int T2_OFF_L26 = T2_OFF_CTRL + 512 + 4 * ((T2_XC + 3) & ~3);
 // 26-neighbour rule: two exchange buffers of a layer's segment ends and
-// lane-group boundary rows (T2M x parts x 2 and 8 x TX2 floats), then the
-// per-pixel masks of kept layers (16 bits, [thread column][worker thread])
+// lane-group boundary rows (parts x 2 x T2M floats; 8 x parts rows of a
+// thread's columns + 4, so that the two boundary lanes' loads take distinct
+// banks), then the per-pixel masks of kept layers (16 bits, [thread
+// column][worker thread])
 constexpr bool T2_L26 = TC2 && MODE == 1;
-constexpr int T2_L26_XB = 4 * (T2M * (((NT - 32) / 32) / 4) * 2 + 8 * TX2);
+constexpr int T2_L26_CP = ((NT - 32) / 32) / 4;
+constexpr int T2_L26_XB = 4 * (T2M * T2_L26_CP * 2 + 8 * (TX2 + 4 * T2_L26_CP));
 constexpr int T2_SMEM = T2_OFF_L26 + (T2_L26 ? 2 * T2_L26_XB + 2 * TX2 * T2M : 0);
 constexpr int T2_NW = NT - 32;                    // worker threads (the last warp issues)
 constexpr int T2_DH = 2 * T2_NVMAX;               // tensor-memory column of the L buffers
@@ -2251,9 +2254,14 @@ __device__ __forceinline__ void t2_epi(const MhfdKHeader &h, const T2State &t, i
 // per layer).  A kept item sets bit I of its pixel's mask in shared memory
 // and stores its response in the block's scratch, both read at the tile end.
 __device__ __forceinline__ void t2_epi26(const MhfdKHeader &h, const T2State &t, int l, unsigned dcol,
-                                         int wt, T2Px &px, float sc, const T2Tile &tl) {
+                                         T2Px &px, float sc, const T2Tile &tl) {
     constexpr int CQ = T2_CQ, CP = T2_CP;
     const float ninf = -__int_as_float(0x7f800000);
+    // the worker thread's index read afresh (volatile): what derives from it
+    // is not hoisted out of the level loop, where it would hold registers
+    // through the split and the window load
+    int wt;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(wt));
     const int w = wt >> 5, lane = wt & 31, g = w & 3, q = w >> 2;
     const int mr = 32 * g + lane, m = T2M - 1 - mr;
     const unsigned taddr = t.tmem + ((unsigned)(32 * g) << 16) + dcol + (unsigned)(CQ * q);
@@ -2278,11 +2286,12 @@ __device__ __forceinline__ void t2_epi26(const MhfdKHeader &h, const T2State &t,
         px.fl = 0;
         px.any = 0;
     }
-    float *xc = t.l26x(I & 1);      // [T2M lanes][CP parts][2 ends]
-    float *xr = xc + T2M * CP * 2;  // [4 lane groups][2 ends][CP parts][CQ]
+    float *xc = t.l26x(I & 1);      // [CP parts][2 ends][T2M lanes]
+    float *xr = xc + T2M * CP * 2;  // [4 lane groups][2 ends][CP parts][CQ + 4]
+    constexpr int XRS = CQ + 4;
     float d0 = 0.0f, dl = 0.0f;     // the segment's ends
     constexpr int EC = 4;
-    static_assert(CQ % 8 == 0, "whole load rounds");
+    static_assert(CQ % EC == 0, "whole load rounds");
 #pragma unroll
     for (int i0 = 0; i0 < CQ; i0 += EC) {
         unsigned r[EC], rp[EC];
@@ -2318,51 +2327,57 @@ __device__ __forceinline__ void t2_epi26(const MhfdKHeader &h, const T2State &t,
             if (i0 + EC == CQ) dl = dv[EC - 1];
             // the whole rows of lanes 0 and 31
             if (lane == 0 || lane == 31)
-                *reinterpret_cast<float4 *>(xr + ((g * 2 + (lane == 31 ? 1 : 0)) * CP + q) * CQ + i0) =
+                *reinterpret_cast<float4 *>(xr + ((g * 2 + (lane == 31 ? 1 : 0)) * CP + q) * XRS + i0) =
                     make_float4(dv[0], dv[1], dv[2], dv[3]);
         }
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    if (first) return;
+    if (first) {
+        // no layer below the first
+#pragma unroll
+        for (int u = 0; u < CQ; ++u) px.mx[u] = ninf;
+        return;
+    }
     if (mk_ok(mr < T2M && q < CP)) {
-        xc[(mr * CP + q) * 2 + 0] = d0;
-        xc[(mr * CP + q) * 2 + 1] = dl;
+        xc[(q * 2 + 0) * T2M + mr] = d0;
+        xc[(q * 2 + 1) * T2M + mr] = dl;
     }
     t2_wsync();
     // the neighbour row of lane 0 (above) or 31 (below) in the next lane
     // group; none past the tile
-    const float *rx = lane == 0 && g > 0    ? xr + (((g - 1) * 2 + 1) * CP + q) * CQ
-                      : lane == 31 && g < 3 ? xr + (((g + 1) * 2 + 0) * CP + q) * CQ
+    const float *rx = lane == 0 && g > 0    ? xr + (((g - 1) * 2 + 1) * CP + q) * XRS
+                      : lane == 31 && g < 3 ? xr + (((g + 1) * 2 + 0) * CP + q) * XRS
                                             : nullptr;
     const unsigned rxh = rx != nullptr, rxa = rx ? smem_addr(rx) : 0u;
     // column max of the three rows just outside the segment (other part)
     auto edge = [&](int qq, int e) {
         if (qq < 0 || qq >= CP) return ninf;
-        float v = xc[(mr * CP + qq) * 2 + e];
-        if (mr > 0) v = fmaxf(v, xc[((mr - 1) * CP + qq) * 2 + e]);
-        if (mr < T2M - 1) v = fmaxf(v, xc[((mr + 1) * CP + qq) * 2 + e]);
+        const float *c = xc + (qq * 2 + e) * T2M;
+        float v = c[mr];
+        if (mr > 0) v = fmaxf(v, c[mr - 1]);
+        if (mr < T2M - 1) v = fmaxf(v, c[mr + 1]);
         return v;
     };
-    const float thr = h.thr;
+    // D > thr as D >= the next float up, so that the threshold joins the
+    // maxima the response must reach
+    const float thrp = nextafterf(h.thr, __int_as_float(0x7f800000));
     const bool top = I + 2 == NL;  // the last layer: no layer above
     // the block's scratch: [layer][column u][worker thread]
     constexpr int LAY = CQ * T2_NW;
-    const int gvb = ((int)blockIdx.x * (NL - 1) + (I > 0 ? I - 1 : 0)) * LAY + wt;
     const int gvc = ((int)blockIdx.x * (NL - 1) + I) * LAY + wt;
-    unsigned fin = 0, nf = 0;
+    unsigned ge = 0, nf = 0;
     // pixel uu: its 8 neighbours are the column maxima (three rows) at uu - 1
     // and uu + 1 and the rows above and below at uu (ud, which may also hold
-    // the pixel itself)
+    // the pixel itself).  ge: not below S_I (for an item flagged one layer
+    // down, whose response is px.mx); nf: above the threshold and not below
+    // its 8 neighbours or S_{I-1} (its response to the scratch at once)
     auto test = [&](int uu, float x, float cl, float cr, float ud) {
         const float nb = fmaxf(fmaxf(cl, cr), ud);
         const float s = fmaxf(nb, x);
-        if (((px.fl >> uu) & 1u) && !(s > px.mx[uu])) {
-            fin |= 1u << uu;
-            h.l26val[gvb + uu * T2_NW] = px.mx[uu];
-        }
-        if (((px.cv >> uu) & 1u) && x > thr && !(nb > x) && (I == 0 || !(px.mx[uu] > x))) {
+        if (!(s > px.mx[uu])) ge |= 1u << uu;
+        if (!(fmaxf(fmaxf(nb, px.mx[uu]), thrp) > x)) {
             nf |= 1u << uu;
-            if (top) h.l26val[gvc + uu * T2_NW] = x;
+            h.l26val[gvc + uu * T2_NW] = x;
         }
         px.mx[uu] = s;
     };
@@ -2372,23 +2387,27 @@ __device__ __forceinline__ void t2_epi26(const MhfdKHeader &h, const T2State &t,
     for (int i0 = 0; i0 < CQ; i0 += 4) {
         unsigned r[4];
         tc_ld4(taddr + (unsigned)i0, r);
+        // this round's columns of the other lane group's row (lanes 0 and
+        // 31: the row above or below; -inf elsewhere)
+        float ev[4] = {ninf, ninf, ninf, ninf};
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %5, 0;\n@p ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n}\n"
+            : "+f"(ev[0]), "+f"(ev[1]), "+f"(ev[2]), "+f"(ev[3])
+            : "r"(rxa + 4u * (unsigned)i0), "r"(rxh)
+            : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int u = i0 + e;
             const float x = __uint_as_float(r[e]);
             // rows above and below: lanes 0 and 31 get their own value from
-            // the shuffles (which leaves the tests unchanged: a pixel is not
-            // below itself) and the other lane group's row from shared memory
-            // (volatile: the shuffles and the boundary row's load stay in
-            // column order, so that they do not all occupy registers at once)
-            float up, dn, ev = ninf;
+            // the shuffles, which leaves the tests unchanged (a pixel is not
+            // below itself); volatile: the shuffles stay in column order, so
+            // that they do not all occupy registers at once
+            float up, dn;
             asm volatile("shfl.sync.up.b32 %0, %1, 1, 0, 0xffffffff;" : "=f"(up) : "f"(x));
             asm volatile("shfl.sync.down.b32 %0, %1, 1, 31, 0xffffffff;" : "=f"(dn) : "f"(x));
-            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %2, 0;\n@p ld.shared.f32 %0, [%1];\n}\n"
-                         : "+f"(ev)
-                         : "r"(rxa + 4u * (unsigned)u), "r"(rxh));
-            const float vn = fmaxf(fmaxf(up, dn), ev), cn = fmaxf(vn, x);
+            const float vn = fmaxf(fmaxf(up, dn), ev[e]), cn = fmaxf(vn, x);
             if (u > 0) {
                 test(u - 1, xcur, cprev, cn, vcur);
                 cprev = ccur;
@@ -2399,6 +2418,10 @@ __device__ __forceinline__ void t2_epi26(const MhfdKHeader &h, const T2State &t,
         }
     }
     test(CQ - 1, xcur, cprev, edge(q + 1, 0), vcur);  // n' = CQ q + CQ past the segment
+    // kept: the flagged items of layer I - 1 not below S_I; flags only on
+    // output pixels
+    const unsigned fin = px.fl & ge;
+    nf &= px.cv;
     px.fl = top ? 0u : nf;
     unsigned short *msk = t.l26m() + wt;  // [column u][worker thread]
 #pragma unroll 1
@@ -2728,7 +2751,7 @@ __device__ __forceinline__ void t2_work(const MhfdKHeader &h, T2State &t, const 
         if (l > 0) {
             const unsigned dcol = (unsigned)T2_DH + ((gl - 1u) & 1u) * (unsigned)TX2;
             if constexpr (T2_L26)
-                t2_epi26(h, t, l - 1, dcol, wt, px, ts.a, tl);
+                t2_epi26(h, t, l - 1, dcol, px, ts.a, tl);
             else
                 t2_epi(h, t, l - 1, dcol, wt, px, ts.a, tl);
         }
@@ -2821,7 +2844,7 @@ __device__ __forceinline__ void t2_range(const MhfdKHeader &h, long long k0, lon
         const long long slot = slot0 + (long long)ty * tiles_x + tx;
         if constexpr (T2_L26) {
             // the top layer's items, then the tile's kept items to its slots
-            t2_epi26(h, t, NL - 1, dcol, wt, px, ts.a, tl);
+            t2_epi26(h, t, NL - 1, dcol, px, ts.a, tl);
             t2_out26(h, t, tl, px, slot, wt);
         } else {
             // the tile's maxima (Eq. 3 with the 3x3 test of §3) from the

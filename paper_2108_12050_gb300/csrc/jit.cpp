@@ -369,8 +369,9 @@ int t2_smem(const std::vector<int> &R, int mode, const TileConfig &c) {
     const int ah_part = 16 * (g.khmax / 8) * 128;
     int b = ((x_bytes + 127) & ~127) + 8 * tab_part + 2 * ah_part + 512 + 4 * ((g.xc + 3) & ~3);
     // 26-neighbour rule: two exchange buffers, the 16-bit layer masks
+    const int cp = ((c.nt - 32) / 32) / 4;
     if (mode == MHFD_NMS_LOCAL26)
-        b += 2 * 4 * (128 * (((c.nt - 32) / 32) / 4) * 2 + 8 * c.tx2) + 2 * c.tx2 * 128;
+        b += 2 * 4 * (128 * cp * 2 + 8 * (c.tx2 + 4 * cp)) + 2 * c.tx2 * 128;
     return b;
 }
 
