@@ -32,7 +32,8 @@ CASES = [
     ("tc_default", dict(L16), (91, 300, 420, "u16")),          # the two-pass kernel
     ("vtc", dict(L16, tensor_cores=2), (91, 300, 420, "u16")),  # the vertical-pass kernel
     ("ffma", dict(L16, tensor_cores=False), (91, 300, 420, "u16")),
-    ("local26", dict(L16, nms="local26"), (92, 260, 333, "u8")),
+    ("local26", dict(L16, nms="local26"), (92, 260, 333, "u8")),              # two-pass
+    ("local26_vtc", dict(L16, nms="local26", tensor_cores=2), (92, 260, 333, "u8")),
     ("log_tc", dict(L10, threshold=0.1 / 0.9, response="log"), (93, 200, 270, "u16")),
     ("periodic", dict(L10, boundary="periodic"), (94, 70, 45, "u16")),
     ("two_row_tc", dict(L16, tensor_cores=2, tile_shape=[256, 18, 8, 288, 4, 2]),
@@ -84,8 +85,10 @@ def checked_env():
     kws = []
     for _, kw, _ in CASES:
         kw = dict(kw, nms=kw.get("nms", "paper"))
-        two_pass = (kw.get("tensor_cores", True) in (True, 1) and kw["nms"] == "paper" and
-                    kw.get("response", "dog") == "dog")
+        # the two-pass kernel (the default for detection with the DoG
+        # response; the 26-neighbour rule up to 16 layers) takes no tuned shape
+        two_pass = (kw.get("tensor_cores", True) in (True, 1) and kw.get("response", "dog") == "dog"
+                    and (kw["nms"] == "paper" or kw["n"] <= 16))
         if "tile_shape" not in kw and not two_pass:  # the shape a Detector takes from the table
             tc = kw.get("tensor_cores", True) and (kw["nms"] == "paper" or
                                                    kw.get("response", "dog") == "dog")
