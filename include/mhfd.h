@@ -108,14 +108,16 @@ typedef struct {
                                taps as two parts, f32 accumulation); other
                                images take the FFMA kernel (same results
                                within the FP32 tolerance).
-                               1 (default): the paper rule with the DoG
-                               response runs both blur passes as products
-                               (the two-pass kernel: tiles of 126 output rows,
+                               1 (default): detection with the DoG response
+                               runs both blur passes as products (the
+                               two-pass kernel: tiles of 126 output rows,
                                the V rows split into fp16 hi + lo parts for
-                               the horizontal product); tile_shape[0] > 0
-                               then sets its strip width (a multiple of 16,
-                               at most 128, incl. the 2 NMS border columns).
-                               The LoG response, the 26-neighbour rule and
+                               the horizontal product; the 26-neighbour rule
+                               tested one layer at a time, up to n = 16);
+                               tile_shape[0] > 0 then sets its strip width
+                               (a multiple of 16, at most 128, incl. the 2
+                               NMS border columns).  The LoG response, the
+                               26-neighbour rule beyond 16 layers and
                                ladders too wide for the two-pass kernel take
                                the vertical-pass kernel of 2.
                                2: the vertical blur on the tensor cores, the
@@ -310,7 +312,9 @@ int mhfd_prune_noalloc(const double *radius, int32_t n_levels, float overlap, co
 /* Device memory of a detector, for callers that budget HBM (the serving
  * loop admits requests by it; not in the paper).  *fixed_bytes receives the
  * bytes mhfd_create_detector allocated (candidate list and prune buffers
- * sized by params.max_candidates, ladder tables); *image_bytes the bytes a
+ * sized by params.max_candidates, ladder tables; for the 26-neighbour rule
+ * on the two-pass kernel, a response scratch of SMs x n x 128 x strip
+ * width floats); *image_bytes the bytes a
  * fused detection (mhfd_detect) of an H x W image adds: tile counters,
  * candidate staging (about 2 B per pixel) and the prune grid.  Those grow to
  * the largest image detected and stay until mhfd_destroy_detector.  The
