@@ -127,13 +127,14 @@ def test_pitched_rows_match_contiguous():
 # ------------------------------------------------------------- detections
 
 def _check_detection(img, n, tmin, tmax, thr, overlap, nms, response="dog",
-                     boundary="reflect", plain=False, tc=True):
+                     boundary="reflect", plain=False, tc=True, **kw):
     """One detection through the C ABI against the oracle's, under the
     ambiguity rules with per-layer tolerances (the 5-point LoG stencil of
-    the plain path gets its derived, wider tolerance)."""
+    the plain path gets its derived, wider tolerance).  Further keywords go
+    to the detector (a tile shape)."""
     det = detector(n=n, t_min=tmin, t_max=tmax, threshold=thr, overlap=overlap, nms=nms,
                    keep_candidates=True, response=response, boundary=boundary,
-                   tensor_cores=tc)
+                   tensor_cores=tc, **kw)
     if plain:
         det.detect_plain(to_dev(img))
         res = det.wait()
@@ -203,6 +204,21 @@ def test_headline_ladder_end_to_end(shape, dtype, sigma_d):
     _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, "paper", tc=False)
     _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, "local26")
     _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, "local26", tc=2)
+
+
+@pytest.mark.parametrize("nms", ["paper", "local26"])
+def test_two_pass_48_column_strips_match_oracle(nms):
+    """The two-pass kernel at 48-column strips (24 columns a worker thread,
+    the chooser's fallback for wide halos) on the benchmark ladder, both
+    rules, and its response stack."""
+    img = scene(64, 300, 333, "u16")
+    kw = dict(tile_shape=[48, 0, 0, 0, 1])
+    _check_detection(img, 16, 1.0, 12.0, 0.05, 0.5, nms, **kw)
+    det = detector(n=16, t_min=1.0, t_max=12.0, threshold=0.05, nms=nms, **kw)
+    assert det.tensor_core_kernel == 2
+    D, _, _, _ = det.debug_stack(to_dev(img), want=("D",))
+    D_ref, _, _ = ref_stack(img, 16, 1.0, 12.0)
+    assert_stack_close(D.cpu().numpy(), D_ref, "48-column strips " + nms)
 
 
 # ------------------------------------------------ tensor-core vertical pass
