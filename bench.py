@@ -195,7 +195,7 @@ def cpu_baseline(img, side=2048, side1=1024):
     oracle.set_threads(threads)
     return {"value": crop.size / dt / 1e6, "unit": METRIC, "cores": cores,
             "kind": "oracle",
-            "sample": "%d^2 crop of the sd=0 tile, whole method, %.1f s" % (side, dt),
+            "sample": "%d^2 crop, sd=0 tile, whole method, %.1f s" % (side, dt),
             "single_core": {"value": crop1.size / dt1 / 1e6, "unit": METRIC, "cores": 1,
                             "sample": "%dx%d crop, %.1f s" % (side1, side1, dt1)}}
 
@@ -495,6 +495,8 @@ def main():
               "sweep_batched": sweep_batched, "serving": serving, "soft": soft_sec,
               "variants": variants, "latency_samples": len(per_tile),
               "median_ms_paper_protocol": statistics.median(paper_ms),
+              "focus_monotone_drop": all(scores[j] > scores[j + 1]
+                                         for j in range(len(scores) - 1)),
               "clocks": clk.summary()}
     print("# detail " + json.dumps(detail), flush=True)
     line = headline_line(
@@ -528,8 +530,11 @@ def summary_of(batched, serving, soft_sec, variants):
                                    "var": r4(f["held_out_target_var"]),
                                    "spearman": r4(f["held_out_spearman"])}
     if variants:
-        summary["variant_frac"] = {k[6:]: r4(v["roofline"]["frac"]) for k, v in variants.items()
-                                   if "roofline" in v}
+        # the default kernels' variants (the vertical-pass ones stay in the
+        # detail line)
+        summary["variant_frac"] = {k[6:]: round(v["roofline"]["frac"], 3)
+                                   for k, v in variants.items()
+                                   if "roofline" in v and not k.endswith("_vtc")}
     return summary
 
 
@@ -564,7 +569,6 @@ def headline_line(*, value, world, steps, warmup, total_ms, p50, p99, plain, ach
         "gpu_launches": launches,
         "clocks": clocks,
         "focus_scores": [int(x) for x in scores],
-        "focus_monotone_drop": all(scores[j] > scores[j + 1] for j in range(len(scores) - 1)),
         "summary": summary,
     }
 

@@ -74,22 +74,24 @@ def test_headline_line_fits_the_kept_tail(bench):
     serving = {"rates": {str(r): rate(r) for r in (100, 500, 2000)},
                "sequential_plain": {str(r): rate(r + 1) for r in (100, 500, 2000)}}
     variants = {"fused_" + k: {"ms": x, "roofline": {"frac": x / 1e4}}
-                for k in ("reflect", "reflect_ffma", "periodic", "local26", "log")}
+                for k in ("reflect", "reflect_vtc", "reflect_ffma", "periodic", "local26",
+                          "local26_vtc", "log")}
     variants.update({"plain_" + k: {"ms": x} for k in ("dog", "local26", "log")})
     summary = bench.summary_of({"tiles_per_s": x, "speedup_vs_plain": x / 100}, serving,
                                {"fit": {"held_out_mse": x / 1e5, "held_out_target_var": x / 1e3,
                                         "held_out_spearman": x / 4e3}}, variants)
     cpu = {"value": x / 1e3, "unit": "Mpixel/s", "cores": 16, "kind": "oracle",
-           "sample": "2048^2 crop of the sd=0 tile, whole method, 1.4 s",
+           "sample": "2048^2 crop, sd=0 tile, whole method, 1.4 s",
            "single_core": {"value": x}}
     e2e = {"value": x * 10, "unit": "Mpixel/s", "h2d_bytes_per_step": 167772160,
            "d2h_bytes_per_step": 4227376}
     line = bench.headline_line(
         value=x * 10, world=1, steps=20, warmup=5, total_ms=x / 100, p50=x / 1e3, p99=x / 900,
         plain={"value": x / 3, "p50_ms_per_tile": x / 70}, achieved=x / 100, peak=40.27392,
-        traffic=33751552, k_avg=x / 3800, side=x / 200, cpu=cpu, e2e=e2e, launches=1800,
+        traffic=33911552, k_avg=x / 3800, side=x / 200, cpu=cpu, e2e=e2e, launches=3600,
         clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]},
-        scores=[77964.0, 54646.0, 26709.0, 11418.0, 5337.0], summary=summary)
+        scores=[77964.0, 54646.0, 26709.0, 11418.0, 5337.0], summary=summary,
+        tensor=(x / 3, x / 1.5))
     text = json.dumps(line)
     assert len(text) < 1500, len(text)
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
