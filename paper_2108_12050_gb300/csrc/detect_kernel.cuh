@@ -2136,7 +2136,10 @@ __device__ __forceinline__ void t2_split_o(const T2State &t, unsigned dcol, int 
             const float h0 = __uint_as_float(__float_as_uint(v[e]) & 0xFFFFE000u);
             const float h1 = __uint_as_float(__float_as_uint(v[e + 1]) & 0xFFFFE000u);
             hi[e >> 1] = t2_pack(h0, h1);
-            lo[e >> 1] = t2_pack(v[e] - h0, v[e + 1] - h1);
+            // v - hi, two at a time (exact: the remainder fits f32)
+            const float2 l2 = __ffma2_rn(make_float2(h0, h1), make_float2(-1.0f, -1.0f),
+                                         make_float2(v[e], v[e + 1]));
+            lo[e >> 1] = t2_pack(l2.x, l2.y);
         }
         if (mk_ok(j < T2_KHMAX / 8 && row < T2M)) {
             *reinterpret_cast<uint4 *>(dst + j * 128) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -2214,10 +2217,23 @@ __device__ __forceinline__ void t2_epi(const MhfdKHeader &h, const T2State &t, i
 #pragma unroll
             for (int e = 0; e < EC; e += 4) px.ag[(i0 + e) >> 2] = 0;
         } else {
+            // the DoG two columns at a time: (L_l - L_{l-1}) rounded once,
+            // then the scale, as the scalar form rounds them
+            float dd[EC];
+#pragma unroll
+            for (int e = 0; e < EC; e += 2) {
+                const float2 df = __fmul2_rn(
+                    make_float2(ts, ts),
+                    __ffma2_rn(make_float2(__uint_as_float(rp[e]), __uint_as_float(rp[e + 1])),
+                               make_float2(-1.0f, -1.0f),
+                               make_float2(__uint_as_float(r[e]), __uint_as_float(r[e + 1]))));
+                dd[e] = df.x;
+                dd[e + 1] = df.y;
+            }
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
                 const int u = i0 + e;
-                const float d = ts * (__uint_as_float(r[e]) - __uint_as_float(rp[e]));
+                const float d = dd[e];
                 if (d > px.mx[u]) {
                     px.mx[u] = d;
                     px.ag[u >> 2] = (px.ag[u >> 2] & ~(0xFFu << (8 * (u & 3)))) | ((unsigned)I << (8 * (u & 3)));
@@ -2306,11 +2322,21 @@ __device__ __forceinline__ void t2_epi26(const MhfdKHeader &h, const T2State &t,
                          "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3])
                          : "memory");
         if (!first) {
-            float dv[EC];
+            float dv[EC], dd[EC];
+#pragma unroll
+            for (int e = 0; e < EC; e += 2) {
+                const float2 df = __fmul2_rn(
+                    make_float2(ts, ts),
+                    __ffma2_rn(make_float2(__uint_as_float(rp[e]), __uint_as_float(rp[e + 1])),
+                               make_float2(-1.0f, -1.0f),
+                               make_float2(__uint_as_float(r[e]), __uint_as_float(r[e + 1]))));
+                dd[e] = df.x;
+                dd[e + 1] = df.y;
+            }
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
                 const int u = i0 + e;
-                const float v = ts * (__uint_as_float(r[e]) - __uint_as_float(rp[e]));
+                const float v = dd[e];
                 if (STORE) {
                     const int c = TX2 - 1 - (CQ * q + u);
                     const int gy = tl.oy - 1 + m, gx = tl.ox - 1 + c;
