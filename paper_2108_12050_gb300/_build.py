@@ -144,7 +144,8 @@ def _tuned_variants():
                 # an FFMA shape of the paper rule serves detectors built with
                 # tensor_cores=False; a vertical-pass tensor-core shape, with
                 # its companion, detectors built with tensor_cores=2 (and the
-                # default ones of the LoG response and the 26-neighbour rule)
+                # default ones of the LoG response and of 26-neighbour ladders
+                # beyond 16 layers)
                 stores = (0, 1) if (nms == 1 or log) else (0, 1, 2)
                 for store in stores:
                     out.append((int(m.group(1)), float(m.group(2)), float(m.group(3)), nms,
