@@ -71,7 +71,8 @@ constexpr bool STORE = (MHFD_STORE) != 0;
 #endif
 constexpr bool TC = (MHFD_VTC) == 1;
 // Both blur passes on the tensor cores (MHFD_VTC 2, "two-pass kernel" below):
-// the paper rule with the DoG response, integer images.
+// detection with the DoG response (the paper rule, the 26-neighbour rule up
+// to 16 layers), integer images.
 constexpr bool TC2 = (MHFD_VTC) == 2;
 // Rows per horizontal item: 1 (four outputs of one row), or 2 (four
 // outputs of each of two adjacent rows; the V rows of a step are then

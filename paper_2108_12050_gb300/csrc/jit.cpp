@@ -427,11 +427,12 @@ bool choose_tile_t2(const std::vector<int> &R, int mode, TileConfig *cfg, std::s
     return false;
 }
 
-// The paper rule, DoG or LoG response; the 26-neighbour rule with the DoG
-// response.  (With the scale-maximum masks and two-output items, the
-// 26-neighbour rule runs faster on the tensor-core kernel at 160-wide
+// The vertical-pass kernel: the paper rule, DoG or LoG response; the
+// 26-neighbour rule with the DoG response.  (With the scale-maximum masks and
+// two-output items, the 26-neighbour rule runs faster on it at 160-wide
 // strips, 2.23 ms, than on the FFMA kernel, 2.36 ms; its ring of all layers
-// had left the tensor-core kernel 192-wide strips of one-row items, 5.5 ms.)
+// had left it 192-wide strips of one-row items, 5.5 ms.  The two-pass kernel
+// takes the rule by default up to 16 layers, 0.85 ms.)
 bool tc_mode_ok(int mode) { return (mode & 3) == 0 || mode == 1; }
 
 bool tc_shape_ok(const std::vector<int> &R, int mode, const TileConfig &c, std::string *why) {
