@@ -945,11 +945,20 @@ def profiled_traffic():
     return None
 
 
-def kernel_digest():
+def kernel_digest(paths=None):
+    """Digest of the fused kernel's source (its header and the kernel file),
+    comments and layout whitespace left out: a comment edit leaves the
+    compiled kernel, and so its counters, as they were."""
     import hashlib
+    import re
     h = hashlib.sha1()
-    for f in ("detect_kernel.cuh", "mhfd_types.h"):
-        h.update(open(os.path.join(ROOT, "paper_2108_12050_gb300", "csrc", f), "rb").read())
+    paths = paths or [os.path.join(ROOT, "paper_2108_12050_gb300", "csrc", f)
+                      for f in ("detect_kernel.cuh", "mhfd_types.h")]
+    for path in paths:
+        text = open(path, encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

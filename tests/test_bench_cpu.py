@@ -100,3 +100,18 @@ def test_headline_line_fits_the_kept_tail(bench):
                 "cpu_baseline", "e2e", "gpu_launches", "clocks"):
         assert key in line, key
     assert "single_core" not in line["cpu_baseline"]
+
+
+def test_kernel_digest_ignores_comments_only(bench, tmp_path):
+    """The digest that ties the committed ncu counters to the kernel source
+    changes with the code, not with its comments or layout."""
+    src = "int f(int a) {\n    return a + 1;  // one more\n}\n/* block\n comment */\n"
+    paths = []
+    for k, text in enumerate([src, src.replace("one more", "the next"),
+                              src.replace("    return", "  return"),
+                              src.replace("a + 1", "a + 2")]):
+        p = tmp_path / ("k%d.cuh" % k)
+        p.write_text(text)
+        paths.append(str(p))
+    d = [bench.kernel_digest([p]) for p in paths]
+    assert d[0] == d[1] == d[2] != d[3]
