@@ -94,15 +94,18 @@ def test_precompile_small_ladder_without_gpu(native, tmp_path, monkeypatch):
     assert any(f.endswith(".cubin") for f in files)
 
 
-@pytest.mark.parametrize("store", [0, 1])
-def test_precompile_two_pass_local26_without_gpu(native, tmp_path, monkeypatch, store):
+@pytest.mark.parametrize("store,width", [(0, 0), (1, 0), (0, 48)])
+def test_precompile_two_pass_local26_without_gpu(native, tmp_path, monkeypatch, store, width):
     """The two-pass kernel with the 26-neighbour rule at the benchmark
-    ladder (16 layers, the most its layer masks take) compiles with NVRTC;
-    the kernel's own static checks hold its shared-memory layout to the
-    host's estimate (the exchange buffers and masks included)."""
+    ladder (16 layers, the most its layer masks take) compiles with NVRTC,
+    at the default 64-column strips and at 48; the kernel's own static
+    checks hold its shared-memory layout to the host's estimate (the
+    exchange buffers and masks included)."""
     monkeypatch.setenv("MHFD_JIT_CACHE", str(tmp_path))
     kw = dict(n=16, t_min=1.0, t_max=12.0, nms=1)
-    assert native.chosen_tile(tensor_cores=True, **kw)[:2] == (64, 128)
+    if width:
+        kw["tile_shape"] = (width, 0, 0, 0, 1)
+    assert native.chosen_tile(tensor_cores=True, **kw)[:2] == (width or 64, 128)
     assert native.precompile(store=store, **kw) == 0
     assert any(f.endswith(".cubin") for f in os.listdir(tmp_path))
 
